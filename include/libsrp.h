@@ -1,0 +1,209 @@
+/*
+ * libsrp -- steered response power (SRP) maps on one GB300 (sm_103a).
+ *
+ * The hot path of "Scalable-Complexity Steered Response Power Based on Low-Rank
+ * and Sparse Interpolation" (Dietzen, De Sena, van Waterschoot):
+ *
+ *   frames --(window, DFT of length N = 2K, PHAT)--> y-hat_m(omega_k)
+ *          --(cross-spectra, Eq. corrmatrix)--> psi_p(omega_k), k = 1..K-1
+ *   conv. FD-SRP   z = 2 Re[H psi]                      (boxed Eq. z_computed)
+ *   SLRI-SRP       xi = iFFT-sampled TD GCC             (Eq. xi_p_ifft, n_prime)
+ *                  z = Lambda_tall (Lambda_fat xi)       (boxed Eq. z_circlr_computed)
+ *   SSPI-SRP       z = Lambda_sp xi                      (boxed Eq. z_circsp_computed)
+ *   estimate       i_max = argmax_i z(i)                 (Eq. imax)
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - All functions return an srp_status; nothing is thrown across this boundary.
+ *   On failure srp_last_error() returns a thread-local, NUL-terminated message
+ *   that stays valid until the next libsrp call on the same thread.
+ * - "device" pointers are CUDA device (or managed) memory of the current device;
+ *   "host" pointers are ordinary (preferably pinned) host memory.  The caller owns
+ *   every buffer it passes in.  Device buffers must be 16-byte aligned.
+ * - A plan owns its device tables (SRP matrix, interpolation factors, tap lists)
+ *   and its scratch buffers; it is bound to the device that was current when it
+ *   was created and must be used with that device current.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  srp_map and srp_gcc_samples are asynchronous on `stream`; a plan
+ *   may be used by one stream at a time (its scratch is shared by its calls).
+ * - Microphone pairs p <-> (m, m') with m > m' are ordered m' outer, m inner
+ *   (the double sum of Eq. SRP_omegaT); P = M(M-1)/2 (Sec. II-A).
+ * - TD GCC samples of pair p are the lags n = -N_p..N_p in ascending order,
+ *   pairs stacked (a relabelling of the paper's n_mod order, Eq. nmod/xi_single).
+ */
+#ifndef LIBSRP_H
+#define LIBSRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srp_plan_s* srp_plan_t;
+
+typedef enum {
+  SRP_OK = 0,
+  SRP_EINVAL = 1,       /* invalid argument (message says which) */
+  SRP_ENOMEM = 2,       /* a device or host allocation failed */
+  SRP_ECUDA = 3,        /* a CUDA runtime call failed (message carries its text) */
+  SRP_ETIMEOUT = 4,     /* a bounded wait ran out */
+  SRP_EUNSUPPORTED = 5  /* valid request this build does not implement */
+} srp_status;
+
+typedef enum {
+  SRP_CONV = 0,  /* conv. FD-SRP, Sec. II-D, boxed Eq. z_computed */
+  SRP_SLRI = 1,  /* SLRI-SRP, Sec. IV-A, boxed Eq. z_circlr_computed */
+  SRP_SSPI = 2   /* SSPI-SRP, Sec. IV-A, boxed Eq. z_circsp_computed */
+} srp_method;
+
+typedef enum {
+  SRP_FP32 = 0,    /* FP32 operands, FP32 FFMA on CUDA cores */
+  SRP_BF16 = 1,    /* conv only: BF16 tensor-core GEMM, FP32 accumulate */
+  SRP_FP16 = 2,    /* conv only: FP16 tensor-core GEMM, FP32 accumulate */
+  SRP_FP16X3 = 4   /* conv only: FP16 hi+lo split operands, 3 tensor-core products
+                      (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+} srp_precision;
+
+typedef enum {
+  SRP_WIN_HANN = 0,       /* periodic Hann */
+  SRP_WIN_SQRT_HANN = 1,  /* square-root periodic Hann (the paper's STFT, Sec. V-B) */
+  SRP_WIN_RECT = 2        /* no window */
+} srp_window;
+
+/* Plan description (all host memory; the arrays are copied by srp_plan_create). */
+typedef struct {
+  int M;                    /* number of microphones, 2..64 */
+  const double* mic_xyz;    /* [M][3] microphone positions r_m in metres */
+  int J;                    /* number of candidate locations, >= 1 */
+  const double* grid_xyz;   /* [J][3] candidate locations q_i in metres (near field,
+                               Eq. Deltat_i first case) */
+  double fs;                /* sampling rate 1/T in Hz, > 0 */
+  int N;                    /* frame / DFT length 2K: a power of two in 256..2048 */
+  int window;               /* srp_window */
+  double c;                 /* speed of sound in m/s (the paper uses 340), > 0 */
+  int n_aux;                /* N_aux of Eq. N_p, 0..64 (the paper uses 2) */
+  int method;               /* srp_method */
+  int rank;                 /* SLRI: R_Lambda of Eq. min_Lambda_lr, 1..64 and <= min(J, L) */
+  double taps_per_loc_pair; /* SSPI: t, Q_Lambda = round(t * J * P) non-zeros kept by
+                               Eq. min_Lambda_sp; 0 < t and Q_Lambda <= J * L */
+  int precision;            /* srp_precision (SLRI/SSPI: SRP_FP32 only) */
+  int max_frames;           /* frames processed per internal launch (scratch sizing),
+                               1..65536; larger calls are processed in chunks */
+} srp_plan_desc;
+
+/* Sizes of a created plan (filled by srp_plan_info). */
+typedef struct {
+  int M, P, J, N, K;        /* K = N/2; bins used are k = 1..K-1 */
+  int L;                    /* number of TD GCC samples, sum_p (2 N_p + 1) */
+  int rank;                 /* SLRI rank (0 for other methods) */
+  long long nnz;            /* SSPI non-zeros Q_Lambda (0 for other methods) */
+  long long tied_at_cut;    /* SSPI: entries whose quantised magnitude equals the
+                               smallest kept one (selection ties, broken by (i, p, n)) */
+  size_t device_bytes;      /* device memory held by the plan */
+  double fit_seconds;       /* host+device time spent in srp_plan_create */
+} srp_plan_info_t;
+
+/*
+ * srp_plan_create -- build a plan: TDOA table (Eq. Deltat_i, FP64), N_p (Eq. N_p),
+ * and per method the device-resident operator:
+ *   SRP_CONV: the SRP matrix H of Eq. H_p_single/H_single, stored as the real
+ *             matrix [2cos(w_k dt_p(i)) | -2sin(w_k dt_p(i))] in the precision asked;
+ *   SRP_SLRI: Lambda (Eq. Lambda_p) -> its best rank-R approximation (Eq.
+ *             min_Lambda_lr) from the eigen-decomposition of Lambda^T Lambda in FP64,
+ *             Lambda_fat = V_R^T, Lambda_tall = Lambda V_R, stored FP32;
+ *   SRP_SSPI: the Q_Lambda largest-magnitude entries of Lambda (Eq. min_Lambda_sp),
+ *             magnitudes quantised to multiples of 2^-40 and ties broken by ascending
+ *             (i, p, n), stored as CSR rows (FP32 values, int32 sample indices).
+ * desc:   host, read only; the arrays are copied.
+ * stream: stream for the uploads; the call returns after they complete.
+ * out:    receives the plan handle (NULL on failure).
+ * Errors: SRP_EINVAL (bad desc, including N_p >= K), SRP_EUNSUPPORTED (method /
+ * precision combination or size beyond this build), SRP_ENOMEM, SRP_ECUDA.
+ */
+srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out);
+
+/* srp_plan_info -- sizes and memory of a plan.  info: host, written. */
+srp_status srp_plan_info(srp_plan_t plan, srp_plan_info_t* info);
+
+/*
+ * srp_plan_lags -- N_p of every pair (Eq. N_p).  Np: host int[P], written.
+ */
+srp_status srp_plan_lags(srp_plan_t plan, int* Np);
+
+/*
+ * srp_map -- SRP maps and their argmax for F frames (the whole hot path).
+ * frames: device float [F][M][N]: frame f, microphone m, sample n (unwindowed).
+ * maps:   device float [F][J], written: z(i) of the plan's method per frame.
+ * argmax: device int32 [F] or NULL, written: i_max per frame (Eq. imax), the lowest
+ *         index among equal maxima.
+ * F = 0 is a no-op.  Asynchronous on `stream`.
+ * Errors: SRP_EINVAL (NULL plan/buffers with F > 0, F < 0), SRP_ECUDA.
+ */
+srp_status srp_map(srp_plan_t plan, const float* frames, int F, float* maps, int* argmax,
+                   void* stream);
+
+/*
+ * srp_map_host -- srp_map on host buffers: copies frames host->device into plan-owned
+ * staging, runs srp_map, copies maps (and argmax) device->host, and synchronises
+ * `stream` before returning.  frames: host float [F][M][N]; maps: host float [F][J];
+ * argmax: host int32 [F] or NULL.  The staging buffers (max_frames frames and maps)
+ * are allocated on the first call and kept by the plan.
+ */
+srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, float* maps, int* argmax,
+                        void* stream);
+
+/*
+ * srp_gcc_samples -- the sampling stage alone (Eq. xi_p_ifft, n_prime, xi_single):
+ * PHAT cross-spectra of every pair, iFFT of the two-sided spectrum (unnormalised,
+ * length N), and the 2N_p+1 samples at lags -N_p..N_p.  Valid for SLRI and SSPI plans.
+ * frames: device float [F][M][N]; xi: device float [F][L], written (pair-major,
+ * ascending lag).  Asynchronous on `stream`.  Errors: SRP_EINVAL, SRP_EUNSUPPORTED
+ * (conv plan), SRP_ECUDA.
+ */
+srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int F, float* xi, void* stream);
+
+/*
+ * srp_plan_sspi_taps -- copy an SSPI plan's kept entries to the host.
+ * row_ptr: host int64 [J+1] or NULL; col: host int32 [nnz] or NULL (sample index into
+ * the stacked xi of srp_gcc_samples); val: host float [nnz] or NULL.
+ * Errors: SRP_EINVAL (not an SSPI plan).
+ */
+srp_status srp_plan_sspi_taps(srp_plan_t plan, long long* row_ptr, int* col, float* val);
+
+/*
+ * srp_plan_slri_sigma -- the plan's singular values of Lambda (square roots of the
+ * eigenvalues of Lambda^T Lambda, descending).  sigma: host double [n]; n <= L.
+ * Errors: SRP_EINVAL (not an SLRI plan, n out of range).
+ */
+srp_status srp_plan_slri_sigma(srp_plan_t plan, double* sigma, int n);
+
+/*
+ * Per-stage timing (the tracing hook used by the benchmark).  When enabled, every
+ * srp_map / srp_map_host call records CUDA events on its stream around its stages:
+ *   SRP_STAGE_FRONTEND   window + DFT + PHAT
+ *   SRP_STAGE_SPECTRA    cross-spectra: iFFT sampling (SLRI/SSPI) or operand packing (conv)
+ *   SRP_STAGE_CONTRACT   the map contraction (conv GEMM, SLRI fat+tall, SSPI gather)
+ *   SRP_STAGE_ARGMAX     argmax finalisation
+ * srp_plan_set_profiling(plan, 1) starts a new record (and 0 stops recording); the
+ * record holds up to 4096 internal chunks.  srp_plan_stage_ms waits for the recorded
+ * events and writes the milliseconds per stage summed over every chunk recorded since
+ * profiling was enabled to ms[SRP_NSTAGES]; *calls receives the number of chunks.
+ * Errors: SRP_EINVAL (NULL plan/ms), SRP_ECUDA.
+ */
+enum { SRP_STAGE_FRONTEND = 0, SRP_STAGE_SPECTRA = 1, SRP_STAGE_CONTRACT = 2,
+       SRP_STAGE_ARGMAX = 3, SRP_NSTAGES = 4 };
+srp_status srp_plan_set_profiling(srp_plan_t plan, int enable);
+srp_status srp_plan_stage_ms(srp_plan_t plan, float* ms, int* calls);
+
+/* srp_destroy -- release a plan and its device memory (synchronises the device). */
+void srp_destroy(srp_plan_t plan);
+
+/* srp_last_error -- the message of the last failure on this thread ("" if none). */
+const char* srp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBSRP_H */

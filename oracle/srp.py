@@ -126,12 +126,15 @@ def steering_matrix_H(dt, fs, K):
     return np.exp(1j * dt[:, :, None] * w[None, None, :])
 
 
-def srp_conv(psi, dt, fs, chunk=2048):
+def srp_conv(psi, dt, fs, chunk=None):
     """Boxed Eq. (z_computed): z = 2 Re[H psi], for each frame.
-    psi: [F][P][K-1]; dt: [J][P] seconds.  Returns z [F][J] float64."""
+    psi: [F][P][K-1]; dt: [J][P] seconds.  Returns z [F][J] float64.  H is built in
+    row blocks of ``chunk`` locations to bound memory."""
     F, P, Km1 = psi.shape
     K = Km1 + 1
     J = dt.shape[0]
+    if chunk is None:
+        chunk = max(1, int(2e7 // (P * Km1)))
     z = np.empty((F, J))
     psi_flat = psi.reshape(F, P * Km1)
     for j0 in range(0, J, chunk):

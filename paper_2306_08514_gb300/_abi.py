@@ -1,0 +1,260 @@
+"""ctypes binding of libsrp (include/libsrp.h): the same entry points under the same
+names, plus a thin ``Plan`` wrapper that allocates outputs with PyTorch and passes raw
+pointers and the current CUDA stream.  Argument marshalling only: every step of the SRP
+path runs in libsrp's CUDA kernels, and importing this module fails loudly when the
+library has not been built."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsrp.so")
+
+SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_ETIMEOUT, SRP_EUNSUPPORTED = range(6)
+SRP_CONV, SRP_SLRI, SRP_SSPI = 0, 1, 2
+SRP_FP32, SRP_BF16, SRP_FP16, SRP_FP16X3 = 0, 1, 2, 4
+SRP_WIN_HANN, SRP_WIN_SQRT_HANN, SRP_WIN_RECT = 0, 1, 2
+
+METHODS = {"conv": SRP_CONV, "slri": SRP_SLRI, "sspi": SRP_SSPI}
+PRECISIONS = {"fp32": SRP_FP32, "bf16": SRP_BF16, "fp16": SRP_FP16, "fp16x3": SRP_FP16X3}
+WINDOWS = {"hann": SRP_WIN_HANN, "sqrt-hann": SRP_WIN_SQRT_HANN, "rect": SRP_WIN_RECT}
+
+
+class srp_plan_desc(C.Structure):
+    _fields_ = [
+        ("M", C.c_int), ("mic_xyz", C.POINTER(C.c_double)),
+        ("J", C.c_int), ("grid_xyz", C.POINTER(C.c_double)),
+        ("fs", C.c_double), ("N", C.c_int), ("window", C.c_int), ("c", C.c_double),
+        ("n_aux", C.c_int), ("method", C.c_int), ("rank", C.c_int),
+        ("taps_per_loc_pair", C.c_double), ("precision", C.c_int), ("max_frames", C.c_int),
+    ]
+
+
+class srp_plan_info_t(C.Structure):
+    _fields_ = [
+        ("M", C.c_int), ("P", C.c_int), ("J", C.c_int), ("N", C.c_int), ("K", C.c_int),
+        ("L", C.c_int), ("rank", C.c_int), ("nnz", C.c_longlong), ("tied_at_cut", C.c_longlong),
+        ("device_bytes", C.c_size_t), ("fit_seconds", C.c_double),
+    ]
+
+
+# every symbol include/libsrp.h declares, with (restype, argtypes)
+SIGNATURES = {
+    "srp_plan_create": (C.c_int, [C.POINTER(srp_plan_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "srp_plan_info": (C.c_int, [C.c_void_p, C.POINTER(srp_plan_info_t)]),
+    "srp_plan_lags": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "srp_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "srp_map_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "srp_gcc_samples": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "srp_plan_sspi_taps": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_float)]),
+    "srp_plan_slri_sigma": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int]),
+    "srp_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "srp_plan_stage_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
+    "srp_destroy": (None, [C.c_void_p]),
+    "srp_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libsrp.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsrp.so not built at {LIB_PATH}: run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SrpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libsrp status {status}: {msg}")
+        self.status = status
+
+
+def _check(st):
+    if st != SRP_OK:
+        raise SrpError(st, lib().srp_last_error().decode())
+
+
+# ---- the C entry points under their own names -------------------------------------
+def srp_last_error() -> str:
+    return lib().srp_last_error().decode()
+
+
+def srp_plan_create(desc: srp_plan_desc, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().srp_plan_create(C.byref(desc), stream, C.byref(h)))
+    return h
+
+
+def srp_plan_info(plan) -> srp_plan_info_t:
+    info = srp_plan_info_t()
+    _check(lib().srp_plan_info(plan, C.byref(info)))
+    return info
+
+
+def srp_plan_lags(plan, P: int) -> np.ndarray:
+    out = (C.c_int * P)()
+    _check(lib().srp_plan_lags(plan, out))
+    return np.array(out[:], dtype=np.int64)
+
+
+def srp_map(plan, frames_ptr, F, maps_ptr, argmax_ptr, stream) -> None:
+    _check(lib().srp_map(plan, frames_ptr, F, maps_ptr, argmax_ptr, stream))
+
+
+def srp_map_host(plan, frames_ptr, F, maps_ptr, argmax_ptr, stream) -> None:
+    _check(lib().srp_map_host(plan, frames_ptr, F, maps_ptr, argmax_ptr, stream))
+
+
+def srp_gcc_samples(plan, frames_ptr, F, xi_ptr, stream) -> None:
+    _check(lib().srp_gcc_samples(plan, frames_ptr, F, xi_ptr, stream))
+
+
+def srp_plan_sspi_taps(plan, J: int, nnz: int):
+    row_ptr = np.zeros(J + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz, dtype=np.float32)
+    _check(lib().srp_plan_sspi_taps(plan, row_ptr.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                    col.ctypes.data_as(C.POINTER(C.c_int)),
+                                    val.ctypes.data_as(C.POINTER(C.c_float))))
+    return row_ptr, col, val
+
+
+def srp_plan_slri_sigma(plan, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.float64)
+    _check(lib().srp_plan_slri_sigma(plan, out.ctypes.data_as(C.POINTER(C.c_double)), n))
+    return out
+
+
+SRP_NSTAGES = 4
+STAGES = ("frontend", "spectra", "contract", "argmax")
+
+
+def srp_plan_set_profiling(plan, enable: bool) -> None:
+    _check(lib().srp_plan_set_profiling(plan, 1 if enable else 0))
+
+
+def srp_plan_stage_ms(plan) -> dict:
+    """Summed milliseconds per stage since profiling was enabled, plus 'chunks'."""
+    out = (C.c_float * SRP_NSTAGES)()
+    n = C.c_int(0)
+    _check(lib().srp_plan_stage_ms(plan, out, C.byref(n)))
+    d = dict(zip(STAGES, [float(v) for v in out]))
+    d["chunks"] = int(n.value)
+    return d
+
+
+def srp_destroy(plan) -> None:
+    lib().srp_destroy(plan)
+
+
+# ---- convenience wrapper ----------------------------------------------------------
+def make_desc(mic_xyz, grid_xyz, fs, N, method="conv", rank=0, taps=0.0, precision="fp32",
+              window="hann", c=340.0, n_aux=2, max_frames=256):
+    mic = np.ascontiguousarray(mic_xyz, dtype=np.float64)
+    grid = np.ascontiguousarray(grid_xyz, dtype=np.float64)
+    d = srp_plan_desc()
+    d.M = mic.shape[0]
+    d.mic_xyz = mic.ctypes.data_as(C.POINTER(C.c_double))
+    d.J = grid.shape[0]
+    d.grid_xyz = grid.ctypes.data_as(C.POINTER(C.c_double))
+    d.fs, d.N, d.window, d.c, d.n_aux = float(fs), int(N), WINDOWS[window], float(c), int(n_aux)
+    d.method = METHODS[method] if isinstance(method, str) else int(method)
+    d.rank, d.taps_per_loc_pair = int(rank), float(taps)
+    d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    d.max_frames = int(max_frames)
+    d._keep = (mic, grid)  # keep the arrays alive while the struct is used
+    return d
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """An SRP plan on the current CUDA device.  Outputs are torch CUDA tensors."""
+
+    def __init__(self, mic_xyz, grid_xyz, fs, N, method="conv", rank=0, taps=0.0,
+                 precision="fp32", window="hann", c=340.0, n_aux=2, max_frames=256,
+                 stream=None):
+        self.desc = make_desc(mic_xyz, grid_xyz, fs, N, method, rank, taps, precision, window,
+                              c, n_aux, max_frames)
+        self.handle = srp_plan_create(self.desc, _stream_handle(stream))
+        self.info = srp_plan_info(self.handle)
+        self.M, self.J, self.N, self.L, self.P = (self.info.M, self.info.J, self.info.N,
+                                                  self.info.L, self.info.P)
+
+    def map(self, frames, maps=None, argmax=None, stream=None, want_argmax=True):
+        import torch
+        assert frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()
+        F = frames.shape[0]
+        if maps is None:
+            maps = torch.empty((F, self.J), dtype=torch.float32, device=frames.device)
+        if argmax is None and want_argmax:
+            argmax = torch.empty((F,), dtype=torch.int32, device=frames.device)
+        srp_map(self.handle, C.c_void_p(frames.data_ptr()), F, C.c_void_p(maps.data_ptr()),
+                C.c_void_p(argmax.data_ptr()) if argmax is not None else None,
+                _stream_handle(stream))
+        return maps, argmax
+
+    def map_host(self, frames, maps=None, argmax=None, stream=None):
+        """frames, maps, argmax: host arrays (numpy or pinned CPU tensors)."""
+        F = frames.shape[0]
+
+        def ptr(a):
+            return C.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+
+        if maps is None:
+            maps = np.empty((F, self.J), dtype=np.float32)
+        if argmax is None:
+            argmax = np.empty((F,), dtype=np.int32)
+        srp_map_host(self.handle, ptr(frames), F, ptr(maps), ptr(argmax), _stream_handle(stream))
+        return maps, argmax
+
+    def gcc_samples(self, frames, stream=None):
+        import torch
+        F = frames.shape[0]
+        xi = torch.empty((F, self.L), dtype=torch.float32, device=frames.device)
+        srp_gcc_samples(self.handle, C.c_void_p(frames.data_ptr()), F, C.c_void_p(xi.data_ptr()),
+                        _stream_handle(stream))
+        return xi
+
+    def set_profiling(self, enable=True):
+        srp_plan_set_profiling(self.handle, enable)
+
+    def stage_ms(self):
+        return srp_plan_stage_ms(self.handle)
+
+    def lags(self):
+        return srp_plan_lags(self.handle, self.P)
+
+    def sspi_taps(self):
+        return srp_plan_sspi_taps(self.handle, self.J, self.info.nnz)
+
+    def slri_sigma(self, n=None):
+        return srp_plan_slri_sigma(self.handle, self.L if n is None else n)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            srp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

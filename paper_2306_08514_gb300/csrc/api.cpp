@@ -1,0 +1,498 @@
+// The C-ABI of libsrp (include/libsrp.h): argument checks, plan construction, and the
+// per-call launch sequence of the SRP path.
+#include "srp_internal.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace srp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+namespace {
+
+srp_status fail(srp_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Everything that can be checked without a GPU.
+srp_status validate(const srp_plan_desc* d) {
+  if (!d) return fail(SRP_EINVAL, "desc is NULL");
+  if (d->M < 2 || d->M > 64) return fail(SRP_EINVAL, "M must be in 2..64");
+  if (!d->mic_xyz) return fail(SRP_EINVAL, "mic_xyz is NULL");
+  if (d->J < 1) return fail(SRP_EINVAL, "J must be >= 1");
+  if (!d->grid_xyz) return fail(SRP_EINVAL, "grid_xyz is NULL");
+  if (!(d->fs > 0) || !std::isfinite(d->fs)) return fail(SRP_EINVAL, "fs must be > 0");
+  if (!is_pow2(d->N) || d->N < 256 || d->N > 2048)
+    return fail(SRP_EINVAL, "N must be a power of two in 256..2048");
+  if (d->window < 0 || d->window > 2) return fail(SRP_EINVAL, "window must be 0, 1 or 2");
+  if (!(d->c > 0) || !std::isfinite(d->c)) return fail(SRP_EINVAL, "c must be > 0");
+  if (d->n_aux < 0 || d->n_aux > 64) return fail(SRP_EINVAL, "n_aux must be in 0..64");
+  if (d->max_frames < 1 || d->max_frames > 65536)
+    return fail(SRP_EINVAL, "max_frames must be in 1..65536");
+  for (int i = 0; i < 3 * d->M; ++i)
+    if (!std::isfinite(d->mic_xyz[i])) return fail(SRP_EINVAL, "mic_xyz has a non-finite value");
+  for (long long i = 0; i < 3ll * d->J; ++i)
+    if (!std::isfinite(d->grid_xyz[i])) return fail(SRP_EINVAL, "grid_xyz has a non-finite value");
+  switch (d->method) {
+    case SRP_CONV:
+      if (d->precision != SRP_FP32 && d->precision != SRP_BF16 && d->precision != SRP_FP16 &&
+          d->precision != SRP_FP16X3)
+        return fail(SRP_EINVAL, "unknown precision");
+      break;
+    case SRP_SLRI:
+    case SRP_SSPI:
+      if (d->precision != SRP_FP32)
+        return fail(SRP_EUNSUPPORTED, "SLRI/SSPI run in SRP_FP32 only");
+      break;
+    default:
+      return fail(SRP_EINVAL, "unknown method");
+  }
+  return SRP_OK;
+}
+
+void window_table(int N, int kind, std::vector<float>& w) {
+  w.resize(N);
+  for (int n = 0; n < N; ++n) {
+    const double h = 0.5 - 0.5 * std::cos(2.0 * M_PI * n / N);
+    w[n] = static_cast<float>(kind == SRP_WIN_HANN ? h : kind == SRP_WIN_SQRT_HANN ? std::sqrt(h) : 1.0);
+  }
+}
+
+template <typename T>
+cudaError_t dalloc(srp_plan_s* p, T** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  if (e == cudaSuccess) p->device_bytes += bytes;
+  return e;
+}
+
+void free_plan(srp_plan_s* p) {
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
+                  p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
+                  p->d_xi, p->d_U, p->d_keys, p->d_stage_frames, p->d_stage_maps,
+                  p->d_stage_arg};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+#define SRP_ALLOC(plan, ptr, bytes)                                                        \
+  do {                                                                                     \
+    cudaError_t _e = dalloc(plan, &(ptr), (bytes));                                        \
+    if (_e != cudaSuccess) {                                                               \
+      cudaGetLastError();                                                                  \
+      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(_e)); \
+      free_plan(plan);                                                                     \
+      return _e == cudaErrorMemoryAllocation ? SRP_ENOMEM : SRP_ECUDA;                     \
+    }                                                                                      \
+  } while (0)
+
+#define SRP_PLAN_CUDA(plan, expr)                                                          \
+  do {                                                                                     \
+    cudaError_t _e = (expr);                                                               \
+    if (_e != cudaSuccess) {                                                               \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                       \
+      free_plan(plan);                                                                     \
+      return SRP_ECUDA;                                                                    \
+    }                                                                                      \
+  } while (0)
+
+size_t op_bytes(OpType t) { return t == OpType::F32 ? 4 : 2; }
+
+// One chunk of at most Fmax frames through the whole path.
+constexpr int kMaxChunkEvents = 4096;
+
+srp_status mark(srp_plan_s* p, int stage, cudaStream_t s) {
+  if (!p->profiling || p->chunks_recorded >= kMaxChunkEvents) return SRP_OK;
+  const size_t idx = static_cast<size_t>(p->chunks_recorded) * 5 + stage;
+  while (p->events.size() <= idx) {
+    cudaEvent_t e;
+    SRP_CUDA_TRY(cudaEventCreate(&e));
+    p->events.push_back(e);
+  }
+  SRP_CUDA_TRY(cudaEventRecord(p->events[idx], s));
+  return SRP_OK;
+}
+
+#define SRP_MARK(p, stage, s)                      \
+  do {                                             \
+    srp_status _st = mark((p), (stage), (s));      \
+    if (_st != SRP_OK) return _st;                 \
+  } while (0)
+
+srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int* argmax,
+                     cudaStream_t s) {
+  const Geometry& g = p->g;
+  SRP_CUDA_TRY(cudaMemsetAsync(p->d_keys, 0, sizeof(unsigned long long) * F, s));
+  SRP_MARK(p, 0, s);
+  SRP_CUDA_TRY(launch_stft_phat(frames, F, g.M, g.N, p->d_window, p->d_twiddle, p->d_yhat, s));
+  SRP_MARK(p, 1, s);
+  switch (p->desc.method) {
+    case SRP_CONV: {
+      SRP_CUDA_TRY(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
+                                    p->d_A_lo, s));
+      SRP_MARK(p, 2, s);
+      const int Kd = g.P * g.N;
+      if (p->op == OpType::F32) {
+        SRP_CUDA_TRY(launch_sgemm_nt_argmax(static_cast<const float*>(p->d_A),
+                                            static_cast<const float*>(p->d_H), maps, p->d_keys,
+                                            F, g.J, Kd, s));
+      } else {
+        SRP_CUDA_TRY(launch_conv_tc(p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, p->op, maps, p->d_keys,
+                                    F, g.J, Kd, p->num_sms, s));
+      }
+      break;
+    }
+    case SRP_SLRI: {
+      SRP_CUDA_TRY(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
+                                      g.L, p->d_twiddle, p->d_xi, s));
+      SRP_MARK(p, 2, s);
+      const int Rp = (p->R + 7) / 8 * 8;
+      SRP_CUDA_TRY(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
+      SRP_CUDA_TRY(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
+      break;
+    }
+    case SRP_SSPI: {
+      SRP_CUDA_TRY(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
+                                      g.L, p->d_twiddle, p->d_xi, s));
+      SRP_MARK(p, 2, s);
+      SRP_CUDA_TRY(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
+                               p->num_sms, s));
+      break;
+    }
+    default:
+      return fail(SRP_EINVAL, "unknown method");
+  }
+  SRP_MARK(p, 3, s);
+  if (argmax) SRP_CUDA_TRY(launch_argmax_finalize(p->d_keys, argmax, F, s));
+  SRP_MARK(p, 4, s);
+  if (p->profiling && p->chunks_recorded < kMaxChunkEvents) ++p->chunks_recorded;
+  return SRP_OK;
+}
+
+}  // namespace
+}  // namespace srp
+
+using namespace srp;
+
+extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out) {
+  clear_error();
+  if (!out) return fail(SRP_EINVAL, "out is NULL");
+  *out = nullptr;
+  srp_status st = validate(desc);
+  if (st != SRP_OK) return st;
+  const auto t0 = std::chrono::steady_clock::now();
+  srp_plan_s* p = new srp_plan_s();
+  p->desc = *desc;
+  p->Fmax = desc->max_frames;
+  st = build_geometry(*desc, p->g);
+  if (st != SRP_OK) {
+    delete p;
+    return st;
+  }
+  const Geometry& g = p->g;
+  // method-specific host-side checks (still no GPU needed)
+  if (desc->method == SRP_SLRI) {
+    if (desc->rank < 1 || desc->rank > 64 || desc->rank > std::min(g.J, g.L)) {
+      delete p;
+      return fail(SRP_EINVAL, "rank must be in 1..min(64, J, L) (L = " + std::to_string(g.L) + ")");
+    }
+    if (g.L > 768) {
+      delete p;
+      return fail(SRP_EUNSUPPORTED, "SLRI fit supports L <= 768 in this build (L = " +
+                                        std::to_string(g.L) + ")");
+    }
+    p->R = desc->rank;
+  }
+  if (desc->method == SRP_SSPI) {
+    const double t = desc->taps_per_loc_pair;
+    const double nz = std::llround(t * static_cast<double>(g.J) * g.P);
+    if (!(t > 0) || !(nz >= 1) || nz > static_cast<double>(g.J) * g.L) {
+      delete p;
+      return fail(SRP_EINVAL, "taps_per_loc_pair gives Q_Lambda outside 1..J*L");
+    }
+    if (g.L * 33 * 4 > 220 * 1024) {
+      delete p;
+      return fail(SRP_EUNSUPPORTED, "SSPI supports L <= 1700 in this build");
+    }
+    p->nnz = static_cast<long long>(nz);
+  }
+  if (desc->method == SRP_CONV) {
+    p->op = desc->precision == SRP_FP32 ? OpType::F32
+            : desc->precision == SRP_BF16 ? OpType::BF16
+            : desc->precision == SRP_FP16 ? OpType::F16
+                                          : OpType::F16X2;
+    const double hbytes = static_cast<double>(g.J) * g.P * g.N * op_bytes(p->op) *
+                          (p->op == OpType::F16X2 ? 2 : 1);
+    if (hbytes > 200e9) {
+      delete p;
+      return fail(SRP_EUNSUPPORTED, "SRP matrix would need more than 200 GB");
+    }
+    if (p->op != OpType::F32 && !conv_tc_supported(p->Fmax, g.J, g.P * g.N)) {
+      delete p;
+      return fail(SRP_EUNSUPPORTED, "tensor-core conv path unavailable for these sizes");
+    }
+  }
+
+  // ---- device part
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SRP_PLAN_CUDA(p, cudaGetDevice(&p->device));
+  SRP_PLAN_CUDA(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+  std::vector<int2> pairs(g.P);
+  for (int q = 0; q < g.P; ++q) pairs[q] = make_int2(g.pm[q], g.pmp[q]);
+  std::vector<float2> tw(g.N / 2);
+  for (int t = 0; t < g.N / 2; ++t)
+    tw[t] = make_float2(static_cast<float>(std::cos(2.0 * M_PI * t / g.N)),
+                        static_cast<float>(-std::sin(2.0 * M_PI * t / g.N)));
+  std::vector<float> win;
+  window_table(g.N, desc->window, win);
+  SRP_ALLOC(p, p->d_pairs, sizeof(int2) * g.P);
+  SRP_ALLOC(p, p->d_Np, sizeof(int) * g.P);
+  SRP_ALLOC(p, p->d_off, sizeof(int) * g.P);
+  SRP_ALLOC(p, p->d_twiddle, sizeof(float2) * g.N / 2);
+  SRP_ALLOC(p, p->d_window, sizeof(float) * g.N);
+  SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_pairs, pairs.data(), sizeof(int2) * g.P, cudaMemcpyHostToDevice, s));
+  SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_Np, g.Np.data(), sizeof(int) * g.P, cudaMemcpyHostToDevice, s));
+  SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_off, g.off.data(), sizeof(int) * g.P, cudaMemcpyHostToDevice, s));
+  SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_twiddle, tw.data(), sizeof(float2) * g.N / 2, cudaMemcpyHostToDevice, s));
+  SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_window, win.data(), sizeof(float) * g.N, cudaMemcpyHostToDevice, s));
+  const size_t F = static_cast<size_t>(p->Fmax);
+  SRP_ALLOC(p, p->d_yhat, sizeof(float2) * F * g.M * (g.N / 2));
+  SRP_ALLOC(p, p->d_keys, sizeof(unsigned long long) * F);
+
+  if (desc->method == SRP_CONV) {
+    const size_t Kd = static_cast<size_t>(g.P) * g.N;
+    const size_t eb = op_bytes(p->op);
+    const bool split = p->op == OpType::F16X2;
+    SRP_ALLOC(p, p->d_H, static_cast<size_t>(g.J) * Kd * eb);
+    if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(g.J) * Kd * eb);
+    SRP_ALLOC(p, p->d_A, F * Kd * eb);
+    if (split) SRP_ALLOC(p, p->d_A_lo, F * Kd * eb);
+    double* d_tau = nullptr;
+    if (cudaMalloc(&d_tau, sizeof(double) * g.tau.size()) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc for the TDOA table failed");
+      free_plan(p);
+      return SRP_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_tau, g.tau.data(), sizeof(double) * g.tau.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_conv_matrix(d_tau, g.J, g.P, g.N, p->op, p->d_H, p->d_H_lo, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_tau);
+    if (e != cudaSuccess) {
+      set_error(std::string("SRP matrix generation: ") + cudaGetErrorString(e));
+      free_plan(p);
+      return SRP_ECUDA;
+    }
+  } else {
+    SRP_ALLOC(p, p->d_xi, sizeof(float) * F * g.L);
+    if (desc->method == SRP_SLRI) {
+      std::vector<float> tall, fat;
+      srp_status fst = fit_low_rank(g, p->R, tall, fat, p->sigma);
+      if (fst != SRP_OK) {
+        free_plan(p);
+        return fst;
+      }
+      const int Rp = (p->R + 7) / 8 * 8;
+      SRP_ALLOC(p, p->d_tall, sizeof(float) * tall.size());
+      SRP_ALLOC(p, p->d_fat, sizeof(float) * fat.size());
+      SRP_ALLOC(p, p->d_U, sizeof(float) * F * Rp);
+      SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tall, tall.data(), sizeof(float) * tall.size(), cudaMemcpyHostToDevice, s));
+      SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_fat, fat.data(), sizeof(float) * fat.size(), cudaMemcpyHostToDevice, s));
+      SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
+    } else {
+      srp_status fst = fit_sparse(g, p->nnz, p->h_row_ptr, p->h_col, p->h_val, p->tied);
+      if (fst != SRP_OK) {
+        free_plan(p);
+        return fst;
+      }
+      std::vector<int2> taps(static_cast<size_t>(p->nnz));
+      for (long long t = 0; t < p->nnz; ++t) {
+        int vb;
+        std::memcpy(&vb, &p->h_val[t], 4);
+        taps[t] = make_int2(p->h_col[t], vb);
+      }
+      SRP_ALLOC(p, p->d_row_ptr, sizeof(long long) * (g.J + 1));
+      SRP_ALLOC(p, p->d_taps, sizeof(int2) * taps.size());
+      SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_row_ptr, p->h_row_ptr.data(), sizeof(long long) * (g.J + 1), cudaMemcpyHostToDevice, s));
+      SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_taps, taps.data(), sizeof(int2) * taps.size(), cudaMemcpyHostToDevice, s));
+      SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
+    }
+  }
+  SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
+  p->g.tau.clear();
+  p->g.tau.shrink_to_fit();
+  p->fit_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_info(srp_plan_t plan, srp_plan_info_t* info) {
+  clear_error();
+  if (!plan || !info) return fail(SRP_EINVAL, "plan or info is NULL");
+  const Geometry& g = plan->g;
+  info->M = g.M;
+  info->P = g.P;
+  info->J = g.J;
+  info->N = g.N;
+  info->K = g.K;
+  info->L = g.L;
+  info->rank = plan->R;
+  info->nnz = plan->nnz;
+  info->tied_at_cut = plan->tied;
+  info->device_bytes = plan->device_bytes;
+  info->fit_seconds = plan->fit_seconds;
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_lags(srp_plan_t plan, int* Np) {
+  clear_error();
+  if (!plan || !Np) return fail(SRP_EINVAL, "plan or Np is NULL");
+  for (int p = 0; p < plan->g.P; ++p) Np[p] = plan->g.Np[p];
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_map(srp_plan_t plan, const float* frames, int F, float* maps,
+                              int* argmax, void* stream) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (F < 0) return fail(SRP_EINVAL, "F < 0");
+  if (F == 0) return SRP_OK;
+  if (!frames || !maps) return fail(SRP_EINVAL, "frames or maps is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Geometry& g = plan->g;
+  for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
+    const int nf = std::min(plan->Fmax, F - c0);
+    srp_status st = run_chunk(plan, frames + static_cast<size_t>(c0) * g.M * g.N, nf,
+                              maps + static_cast<size_t>(c0) * g.J, argmax ? argmax + c0 : nullptr, s);
+    if (st != SRP_OK) return st;
+  }
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, float* maps,
+                                   int* argmax, void* stream) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (F < 0) return fail(SRP_EINVAL, "F < 0");
+  if (F == 0) return SRP_OK;
+  if (!frames || !maps) return fail(SRP_EINVAL, "frames or maps is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Geometry& g = plan->g;
+  const size_t Fm = static_cast<size_t>(plan->Fmax);
+  if (!plan->d_stage_frames) {
+    void* a = nullptr;
+    void* b = nullptr;
+    void* c = nullptr;
+    if (cudaMalloc(&a, sizeof(float) * Fm * g.M * g.N) != cudaSuccess ||
+        cudaMalloc(&b, sizeof(float) * Fm * g.J) != cudaSuccess ||
+        cudaMalloc(&c, sizeof(int) * Fm) != cudaSuccess) {
+      cudaGetLastError();
+      if (a) cudaFree(a);
+      if (b) cudaFree(b);
+      return fail(SRP_ENOMEM, "staging allocation failed");
+    }
+    plan->d_stage_frames = static_cast<float*>(a);
+    plan->d_stage_maps = static_cast<float*>(b);
+    plan->d_stage_arg = static_cast<int*>(c);
+    plan->device_bytes += sizeof(float) * Fm * (g.M * g.N + g.J) + sizeof(int) * Fm;
+  }
+  for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
+    const int nf = std::min(plan->Fmax, F - c0);
+    SRP_CUDA_TRY(cudaMemcpyAsync(plan->d_stage_frames, frames + static_cast<size_t>(c0) * g.M * g.N,
+                                 sizeof(float) * nf * g.M * g.N, cudaMemcpyHostToDevice, s));
+    srp_status st = run_chunk(plan, plan->d_stage_frames, nf, plan->d_stage_maps,
+                              argmax ? plan->d_stage_arg : nullptr, s);
+    if (st != SRP_OK) return st;
+    SRP_CUDA_TRY(cudaMemcpyAsync(maps + static_cast<size_t>(c0) * g.J, plan->d_stage_maps,
+                                 sizeof(float) * nf * g.J, cudaMemcpyDeviceToHost, s));
+    if (argmax)
+      SRP_CUDA_TRY(cudaMemcpyAsync(argmax + c0, plan->d_stage_arg, sizeof(int) * nf,
+                                   cudaMemcpyDeviceToHost, s));
+  }
+  SRP_CUDA_TRY(cudaStreamSynchronize(s));
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int F, float* xi,
+                                      void* stream) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (plan->desc.method == SRP_CONV)
+    return fail(SRP_EUNSUPPORTED, "srp_gcc_samples needs an SLRI or SSPI plan");
+  if (F < 0) return fail(SRP_EINVAL, "F < 0");
+  if (F == 0) return SRP_OK;
+  if (!frames || !xi) return fail(SRP_EINVAL, "frames or xi is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Geometry& g = plan->g;
+  for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
+    const int nf = std::min(plan->Fmax, F - c0);
+    SRP_CUDA_TRY(launch_stft_phat(frames + static_cast<size_t>(c0) * g.M * g.N, nf, g.M, g.N,
+                                  plan->d_window, plan->d_twiddle, plan->d_yhat, s));
+    SRP_CUDA_TRY(launch_gcc_samples(plan->d_yhat, nf, g.M, g.P, g.N, plan->d_pairs, plan->d_Np,
+                                    plan->d_off, g.L, plan->d_twiddle,
+                                    xi + static_cast<size_t>(c0) * g.L, s));
+  }
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_sspi_taps(srp_plan_t plan, long long* row_ptr, int* col, float* val) {
+  clear_error();
+  if (!plan || plan->desc.method != SRP_SSPI) return fail(SRP_EINVAL, "not an SSPI plan");
+  if (row_ptr) std::memcpy(row_ptr, plan->h_row_ptr.data(), sizeof(long long) * plan->h_row_ptr.size());
+  if (col) std::memcpy(col, plan->h_col.data(), sizeof(int) * plan->h_col.size());
+  if (val) std::memcpy(val, plan->h_val.data(), sizeof(float) * plan->h_val.size());
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_slri_sigma(srp_plan_t plan, double* sigma, int n) {
+  clear_error();
+  if (!plan || plan->desc.method != SRP_SLRI) return fail(SRP_EINVAL, "not an SLRI plan");
+  if (!sigma || n < 0 || n > static_cast<int>(plan->sigma.size()))
+    return fail(SRP_EINVAL, "n out of range");
+  for (int i = 0; i < n; ++i) sigma[i] = plan->sigma[i];
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_set_profiling(srp_plan_t plan, int enable) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  plan->profiling = enable != 0;
+  plan->chunks_recorded = 0;
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_stage_ms(srp_plan_t plan, float* ms, int* calls) {
+  clear_error();
+  if (!plan || !ms) return fail(SRP_EINVAL, "plan or ms is NULL");
+  for (int k = 0; k < SRP_NSTAGES; ++k) ms[k] = 0.f;
+  for (int c = 0; c < plan->chunks_recorded; ++c) {
+    cudaEvent_t* e = plan->events.data() + static_cast<size_t>(c) * 5;
+    SRP_CUDA_TRY(cudaEventSynchronize(e[4]));
+    for (int k = 0; k < SRP_NSTAGES; ++k) {
+      float t = 0.f;
+      SRP_CUDA_TRY(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+      ms[k] += t;
+    }
+  }
+  if (calls) *calls = plan->chunks_recorded;
+  return SRP_OK;
+}
+
+extern "C" void srp_destroy(srp_plan_t plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+}
+
+extern "C" const char* srp_last_error(void) { return g_last_error.c_str(); }

@@ -1,0 +1,109 @@
+// conv. FD-SRP in FP32 on the CUDA cores: Z = A B^T (boxed Eq. z_computed written as a
+// real product over the stacked [Re psi | Im psi] and [2cos | -2sin] rows), with the
+// per-frame argmax (Eq. imax) fused into the epilogue.
+//
+// A [F][Kd], B [J][Kd], Z [F][J], all row-major with the reduction dimension Kd = P*N
+// contiguous.  Block tile 128 frames x 128 cells, k-step 8, 256 threads each owning an
+// 8x8 sub-tile split into two 4-row and two 4-column strips (conflict-free float4
+// shared-memory reads), double-buffered shared memory with register prefetch.
+#include "srp_internal.h"
+#include "srp_device.cuh"
+
+namespace srp {
+
+namespace {
+constexpr int BM = 128, BN = 128, BK = 8, PADS = 4;
+}
+
+__global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
+    const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ Z,
+    unsigned long long* __restrict__ keys, int F, int J, int Kd) {
+  __shared__ __align__(16) float As[2][BK][BM + PADS];
+  __shared__ __align__(16) float Bs[2][BK][BN + PADS];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int lr = tid >> 1, lk = (tid & 1) * 4;
+  const bool aok = (m0 + lr) < F;
+  const bool bok = (n0 + lr) < J;
+  const float4* Ap = reinterpret_cast<const float4*>(A + static_cast<size_t>(aok ? m0 + lr : 0) * Kd + lk);
+  const float4* Bp = reinterpret_cast<const float4*>(B + static_cast<size_t>(bok ? n0 + lr : 0) * Kd + lk);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 ra = aok ? __ldg(Ap) : z4;
+  float4 rb = bok ? __ldg(Bp) : z4;
+  As[0][lk + 0][lr] = ra.x; As[0][lk + 1][lr] = ra.y; As[0][lk + 2][lr] = ra.z; As[0][lk + 3][lr] = ra.w;
+  Bs[0][lk + 0][lr] = rb.x; Bs[0][lk + 1][lr] = rb.y; Bs[0][lk + 2][lr] = rb.z; Bs[0][lk + 3][lr] = rb.w;
+  __syncthreads();
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  const int nk = Kd / BK;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) {
+      ra = aok ? __ldg(Ap + (kt + 1) * (BK / 4)) : z4;
+      rb = bok ? __ldg(Bp + (kt + 1) * (BK / 4)) : z4;
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) {
+      const int nx = cur ^ 1;
+      As[nx][lk + 0][lr] = ra.x; As[nx][lk + 1][lr] = ra.y; As[nx][lk + 2][lr] = ra.z; As[nx][lk + 3][lr] = ra.w;
+      Bs[nx][lk + 0][lr] = rb.x; Bs[nx][lk + 1][lr] = rb.y; Bs[nx][lk + 2][lr] = rb.z; Bs[nx][lk + 3][lr] = rb.w;
+    }
+    __syncthreads();
+  }
+
+  // epilogue: store, then per-row (frame) argmax over this block's 128 cells
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    unsigned long long best = 0ull;
+    if (m < F) {
+      float* zr = Z + static_cast<size_t>(m) * J;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        if (n < J) {
+          zr[n] = acc[i][j];
+          const unsigned long long kk = argmax_key(acc[i][j], n);
+          best = kk > best ? kk : best;
+        }
+      }
+    }
+    // reduce over the 16 threads sharing this row (one half-warp)
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+      best = other > best ? other : best;
+    }
+    if (tx == 0 && m < F && best) atomicMax(keys + m, best);
+  }
+}
+
+cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
+                                   unsigned long long* keys, int F, int J, int Kd,
+                                   cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  if (Kd % BK != 0) return cudaErrorInvalidValue;
+  dim3 grid((J + BN - 1) / BN, (F + BM - 1) / BM);
+  sgemm_nt_argmax_kernel<<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd);
+  return cudaGetLastError();
+}
+
+}  // namespace srp

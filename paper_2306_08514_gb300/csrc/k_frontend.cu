@@ -1,0 +1,282 @@
+// Front end of the SRP path: STFT + PHAT, cross-spectra, iFFT sampling, and the
+// operands of the conventional SRP-matrix product.
+//
+//   y-hat_m(omega_k) = y_m / |y_m|                   PHAT, Eq. corrmatrix
+//   psi_p(omega_k)  = y-hat_m y-hat_m'^*            k = 1..K-1 (Eq. psi_p_single)
+//   xi_p(nT)        = iFFT_2K[psi-bar_p](n)          Eq. xi_p_ifft, n_prime
+//   H_p[i,k]        = exp(j omega_k Delta t_p(i))    Eq. H_p_single
+#include "srp_internal.h"
+#include "srp_device.cuh"
+
+namespace srp {
+
+// ---------------------------------------------------------------------------------
+// STFT + PHAT.  One group of N/4 threads per (frame, microphone).  The N real
+// samples are packed as N/2 complex numbers z[j] = x[2j] + i x[2j+1], transformed by
+// an N/2-point FFT, and the N-point spectrum is recovered for k = 1..K-1 as
+// X[k] = E[k] + W^k O[k] with E = (Z[k] + Z[N/2-k]^*)/2, O = (Z[k] - Z[N/2-k]^*)/(2i).
+// An all-zero channel gives exactly X = 0, hence y-hat = 0 (|y|^2 < 1e-30 -> 0).
+// ---------------------------------------------------------------------------------
+__global__ void stft_phat_kernel(const float* __restrict__ frames, int M, int N,
+                                 const float* __restrict__ window,
+                                 const float2* __restrict__ twiddle,
+                                 float2* __restrict__ yhat) {
+  extern __shared__ float2 smem[];
+  const int H = N >> 1;       // complex FFT length
+  const int T = H >> 1;       // threads per channel group
+  float2* tw = smem;          // N/2 entries
+  float2* bufA = smem + H + threadIdx.y * 2 * H;
+  float2* bufB = bufA + H;
+  const int tid = threadIdx.y * T + threadIdx.x;
+  const int nthreads = T * blockDim.y;
+  for (int t = tid; t < H; t += nthreads) tw[t] = twiddle[t];
+
+  const int f = blockIdx.y;
+  const int m = blockIdx.x * blockDim.y + threadIdx.y;
+  const bool live = m < M;
+  const float2* x2 =
+      reinterpret_cast<const float2*>(frames + (static_cast<size_t>(f) * M + (live ? m : 0)) * N);
+  const float2* w2 = reinterpret_cast<const float2*>(window);
+  for (int j = threadIdx.x; j < H; j += T) {
+    float2 v = live ? x2[j] : make_float2(0.f, 0.f);
+    float2 w = w2[j];
+    bufA[j] = make_float2(v.x * w.x, v.y * w.y);
+  }
+  __syncthreads();
+  float2* Z = stockham_fft<false>(bufA, bufB, H, threadIdx.x, tw, 1);
+  if (!live) return;  // no barrier follows
+  const int K = H;
+  float2* out = yhat + (static_cast<size_t>(f) * M + m) * K;
+  for (int k = threadIdx.x; k < K; k += T) {
+    if (k == 0) {
+      out[0] = make_float2(0.f, 0.f);  // DC is not used (Sec. II-D)
+      continue;
+    }
+    const float2 zk = Z[k];
+    const float2 zc = make_float2(Z[H - k].x, -Z[H - k].y);
+    const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+    const float2 O = make_float2(0.5f * (zk.y - zc.y), -0.5f * (zk.x - zc.x));
+    const float2 X = make_float2(E.x, E.y);
+    const float2 WO = cmul(tw[k], O);
+    const float2 Y = make_float2(X.x + WO.x, X.y + WO.y);
+    const float p = Y.x * Y.x + Y.y * Y.y;
+    float2 r = make_float2(0.f, 0.f);
+    if (p >= 1e-30f) {
+      const float s = __frsqrt_rn(p);
+      r = make_float2(Y.x * s, Y.y * s);
+    }
+    out[k] = r;
+  }
+}
+
+cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const float* window,
+                             const float2* twiddle, float2* yhat, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  const int T = N / 4;
+  const int cpb = T >= 256 ? 1 : 256 / T;  // channels per block
+  dim3 block(T, cpb);
+  dim3 grid((M + cpb - 1) / cpb, F);
+  const size_t smem = sizeof(float2) * (N / 2 + static_cast<size_t>(cpb) * N);
+  stft_phat_kernel<<<grid, block, smem, s>>>(frames, M, N, window, twiddle, yhat);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Sampling.  Two pairs share one N-point complex iFFT: the input is
+// psi-bar_a + i psi-bar_b, both two-sided (Appendix, Eq. psi_p_two) and Hermitian, so
+// the (unnormalised) inverse transform is xi-bar_a + i xi-bar_b.  The lags
+// n = -N_p..N_p are read at index mod(n, N) (Eq. n_prime) and stored ascending.
+// ---------------------------------------------------------------------------------
+__global__ void gcc_samples_kernel(const float2* __restrict__ yhat, int M, int P, int N,
+                                   const int2* __restrict__ pairs, const int* __restrict__ Np,
+                                   const int* __restrict__ off, int L,
+                                   const float2* __restrict__ twiddle, float* __restrict__ xi) {
+  extern __shared__ float2 smem[];
+  const int K = N >> 1;
+  const int T = N >> 1;
+  float2* tw = smem;          // N/2
+  float2* bufA = smem + K;    // N
+  float2* bufB = bufA + N;    // N
+  const int j = threadIdx.x;
+  for (int t = j; t < K; t += T) tw[t] = twiddle[t];
+  const int f = blockIdx.y;
+  const int pa = 2 * blockIdx.x;
+  const int pb = pa + 1;
+  const bool hasb = pb < P;
+  const int2 qa = pairs[pa];
+  const int2 qb = hasb ? pairs[pb] : make_int2(0, 0);
+  const float2* yf = yhat + static_cast<size_t>(f) * M * K;
+  for (int k = j; k < K; k += T) {
+    if (k == 0) {
+      bufA[0] = make_float2(0.f, 0.f);
+      bufA[K] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const float2 a = cmul_conj(yf[qa.x * K + k], yf[qa.y * K + k]);
+    const float2 b = hasb ? cmul_conj(yf[qb.x * K + k], yf[qb.y * K + k]) : make_float2(0.f, 0.f);
+    bufA[k] = make_float2(a.x - b.y, a.y + b.x);          // psi_a + i psi_b
+    bufA[N - k] = make_float2(a.x + b.y, b.x - a.y);      // psi_a^* + i psi_b^*
+  }
+  __syncthreads();
+  const float2* x = stockham_fft<true>(bufA, bufB, N, j, tw, 0);
+  const int na = Np[pa];
+  float* outa = xi + static_cast<size_t>(f) * L + off[pa];
+  for (int t = j; t < 2 * na + 1; t += T) outa[t] = x[(t - na + N) & (N - 1)].x;
+  if (hasb) {
+    const int nb = Np[pb];
+    float* outb = xi + static_cast<size_t>(f) * L + off[pb];
+    for (int t = j; t < 2 * nb + 1; t += T) outb[t] = x[(t - nb + N) & (N - 1)].y;
+  }
+}
+
+cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                               const int* Np, const int* off, int L, const float2* twiddle,
+                               float* xi, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  dim3 grid((P + 1) / 2, F);
+  const size_t smem = sizeof(float2) * (N / 2 + 2 * static_cast<size_t>(N));
+  gcc_samples_kernel<<<grid, N / 2, smem, s>>>(yhat, M, P, N, pairs, Np, off, L, twiddle, xi);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// conv. FD-SRP operand A [F][P*N]: row f holds, per pair, Re psi_p(k) at p*N + k and
+// Im psi_p(k) at p*N + K + k (k = 0..K-1, psi(0) = 0).  With B[i] = [2cos, -2sin]
+// (launch_conv_matrix) the dot product is 2 Re[H_p psi_p] summed over pairs.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T to_op(float v);
+template <>
+__device__ __forceinline__ float to_op<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half to_op<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+template <typename T, bool SPLIT>
+__global__ void conv_pack_kernel(const float2* __restrict__ yhat, int F, int M, int P, int N,
+                                 const int2* __restrict__ pairs, T* __restrict__ A,
+                                 T* __restrict__ A_lo) {
+  const int K = N >> 1;
+  const size_t total = static_cast<size_t>(F) * P * K;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(e % K);
+    const size_t fp = e / K;
+    const int p = static_cast<int>(fp % P);
+    const int f = static_cast<int>(fp / P);
+    const int2 q = pairs[p];
+    const float2* yf = yhat + static_cast<size_t>(f) * M * K;
+    const float2 v = cmul_conj(yf[q.x * K + k], yf[q.y * K + k]);
+    const size_t base = (static_cast<size_t>(f) * P + p) * N + k;
+    const T re = to_op<T>(v.x);
+    const T im = to_op<T>(v.y);
+    A[base] = re;
+    A[base + K] = im;
+    if (SPLIT) {
+      A_lo[base] = to_op<T>(v.x - static_cast<float>(re));
+      A_lo[base + K] = to_op<T>(v.y - static_cast<float>(im));
+    }
+  }
+}
+
+static int grid_for(size_t total, int block) {
+  size_t g = (total + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                             OpType t, void* A, void* A_lo, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  const size_t total = static_cast<size_t>(F) * P * (N / 2);
+  const int g = grid_for(total, 256);
+  switch (t) {
+    case OpType::F32:
+      conv_pack_kernel<float, false><<<g, 256, 0, s>>>(yhat, F, M, P, N, pairs,
+                                                       static_cast<float*>(A), nullptr);
+      break;
+    case OpType::F16:
+      conv_pack_kernel<__half, false><<<g, 256, 0, s>>>(yhat, F, M, P, N, pairs,
+                                                        static_cast<__half*>(A), nullptr);
+      break;
+    case OpType::BF16:
+      conv_pack_kernel<__nv_bfloat16, false><<<g, 256, 0, s>>>(
+          yhat, F, M, P, N, pairs, static_cast<__nv_bfloat16*>(A), nullptr);
+      break;
+    case OpType::F16X2:
+      conv_pack_kernel<__half, true><<<g, 256, 0, s>>>(yhat, F, M, P, N, pairs,
+                                                       static_cast<__half*>(A),
+                                                       static_cast<__half*>(A_lo));
+      break;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// The SRP matrix in GEMM layout, generated once per plan from the FP64 TDOA table:
+// theta = 2 pi k tau_p(i) / N with tau in samples (omega_k Delta t = pi k tau / K,
+// Eq. w_k), reduced exactly in FP64 to 2 * frac(k tau / N) before sincospi.
+// ---------------------------------------------------------------------------------
+template <typename T, bool SPLIT>
+__global__ void conv_matrix_kernel(const double* __restrict__ tau, int J, int P, int N,
+                                   T* __restrict__ B, T* __restrict__ B_lo) {
+  const int K = N >> 1;
+  const size_t total = static_cast<size_t>(J) * P * K;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(e % K);
+    const size_t ip = e / K;  // i * P + p
+    double c = 0.0, sn = 0.0;
+    if (k != 0) {
+      const double t = static_cast<double>(k) * tau[ip];
+      const double r = t - static_cast<double>(N) * floor(t / static_cast<double>(N));
+      sincospi(2.0 * r / static_cast<double>(N), &sn, &c);
+      c *= 2.0;
+      sn *= -2.0;
+    }
+    const size_t base = ip * N + k;
+    if constexpr (SPLIT) {
+      const __half hc = __float2half_rn(static_cast<float>(c));
+      const __half hs = __float2half_rn(static_cast<float>(sn));
+      B[base] = hc;
+      B[base + K] = hs;
+      B_lo[base] = __float2half_rn(static_cast<float>(c - static_cast<double>(__half2float(hc))));
+      B_lo[base + K] =
+          __float2half_rn(static_cast<float>(sn - static_cast<double>(__half2float(hs))));
+    } else {
+      B[base] = to_op<T>(static_cast<float>(c));
+      B[base + K] = to_op<T>(static_cast<float>(sn));
+    }
+  }
+}
+
+cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpType t, void* B,
+                               void* B_lo, cudaStream_t s) {
+  const size_t total = static_cast<size_t>(J) * P * (N / 2);
+  const int g = grid_for(total, 256);
+  switch (t) {
+    case OpType::F32:
+      conv_matrix_kernel<float, false><<<g, 256, 0, s>>>(tau_dev, J, P, N, static_cast<float*>(B),
+                                                         nullptr);
+      break;
+    case OpType::F16:
+      conv_matrix_kernel<__half, false><<<g, 256, 0, s>>>(tau_dev, J, P, N,
+                                                          static_cast<__half*>(B), nullptr);
+      break;
+    case OpType::BF16:
+      conv_matrix_kernel<__nv_bfloat16, false><<<g, 256, 0, s>>>(
+          tau_dev, J, P, N, static_cast<__nv_bfloat16*>(B), nullptr);
+      break;
+    case OpType::F16X2:
+      conv_matrix_kernel<__half, true><<<g, 256, 0, s>>>(tau_dev, J, P, N, static_cast<__half*>(B),
+                                                         static_cast<__half*>(B_lo));
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace srp

@@ -1,0 +1,309 @@
+// Interpolation stage of SLRI-SRP and SSPI-SRP, with the argmax (Eq. imax) fused.
+//
+//   SLRI (boxed Eq. z_circlr_computed):  u = Lambda_fat xi      (R x L, per frame)
+//                                        z = Lambda_tall u      (J x R, per frame)
+//   SSPI (boxed Eq. z_circsp_computed):  z_i = sum_{(c, v) in row i} v * xi[c]
+#include "srp_internal.h"
+#include "srp_device.cuh"
+
+namespace srp {
+
+// ---------------------------------------------------------------------------------
+// u[f][r] = sum_l fat[r][l] xi[f][l].  FB frames per block staged in shared memory;
+// one warp per r, lanes stride over l, FB dot products share each fat load.
+// ---------------------------------------------------------------------------------
+template <int FB>
+__global__ __launch_bounds__(256) void slri_fat_kernel(const float* __restrict__ xi,
+                                                       const float* __restrict__ fat,
+                                                       float* __restrict__ U, int F, int L,
+                                                       int R) {
+  extern __shared__ float xs[];  // [FB][L]
+  const int f0 = blockIdx.x * FB;
+  const int nf = min(FB, F - f0);
+  for (int e = threadIdx.x; e < FB * L; e += blockDim.x) {
+    const int fb = e / L;
+    xs[e] = fb < nf ? xi[static_cast<size_t>(f0) * L + e] : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < R; r += (blockDim.x >> 5)) {
+    float acc[FB];
+#pragma unroll
+    for (int fb = 0; fb < FB; ++fb) acc[fb] = 0.f;
+    const float* fr = fat + static_cast<size_t>(r) * L;
+    for (int l = lane; l < L; l += 32) {
+      const float a = __ldg(fr + l);
+#pragma unroll
+      for (int fb = 0; fb < FB; ++fb) acc[fb] = fmaf(a, xs[fb * L + l], acc[fb]);
+    }
+#pragma unroll
+    for (int fb = 0; fb < FB; ++fb) {
+      float v = acc[fb];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      if (lane == 0 && fb < nf) U[static_cast<size_t>(f0 + fb) * R + r] = v;
+    }
+  }
+}
+
+cudaError_t launch_slri_fat(const float* xi, const float* fat, float* U, int F, int L, int R,
+                            cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  const size_t budget = 160 * 1024;
+  int fb = 8;
+  while (fb > 1 && static_cast<size_t>(fb) * L * sizeof(float) > budget) fb >>= 1;
+  const size_t smem = static_cast<size_t>(fb) * L * sizeof(float);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  const int grid = (F + fb - 1) / fb;
+#define SRP_FAT(FBV)                                                                         \
+  case FBV: {                                                                                \
+    cudaError_t e = cudaFuncSetAttribute(slri_fat_kernel<FBV>,                               \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                         static_cast<int>(smem));                            \
+    if (e != cudaSuccess) return e;                                                          \
+    slri_fat_kernel<FBV><<<grid, 256, smem, s>>>(xi, fat, U, F, L, R);                       \
+    break;                                                                                   \
+  }
+  switch (fb) {
+    SRP_FAT(8)
+    SRP_FAT(4)
+    SRP_FAT(2)
+    SRP_FAT(1)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SRP_FAT
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// z[f][i] = sum_r tall[i][r] u[f][r].  Each thread keeps the R coefficients of CPT
+// cells (cell = base + c*256 + tid, so stores are coalesced) in registers and walks
+// FB frames whose u rows sit in shared memory (broadcast reads).  The argmax of each
+// frame is reduced per warp, then per block, then merged with one atomicMax.
+// ---------------------------------------------------------------------------------
+template <int R, int CPT>
+__global__ __launch_bounds__(256) void slri_tall_kernel(const float* __restrict__ U,
+                                                        const float* __restrict__ tall,
+                                                        float* __restrict__ Z,
+                                                        unsigned long long* __restrict__ keys,
+                                                        int F, int J, int FB) {
+  extern __shared__ float4 sm4[];
+  float* Us = reinterpret_cast<float*>(sm4);                                  // [FB][R]
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(Us + FB * R);  // [8][FB]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ibase = blockIdx.x * (256 * CPT);
+  const int f0 = blockIdx.y * FB;
+  const int nf = min(FB, F - f0);
+  for (int e = tid; e < nf * R; e += 256) Us[e] = U[static_cast<size_t>(f0) * R + e];
+  float t[CPT][R];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const int i = ibase + c * 256 + tid;
+    if (i < J) {
+      const float4* src = reinterpret_cast<const float4*>(tall + static_cast<size_t>(i) * R);
+#pragma unroll
+      for (int r4 = 0; r4 < R / 4; ++r4) {
+        const float4 v = __ldg(src + r4);
+        t[c][4 * r4] = v.x; t[c][4 * r4 + 1] = v.y; t[c][4 * r4 + 2] = v.z; t[c][4 * r4 + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) t[c][r] = 0.f;
+    }
+  }
+  __syncthreads();
+  for (int fb = 0; fb < nf; ++fb) {
+    const float4* u4 = reinterpret_cast<const float4*>(Us + fb * R);
+    float z[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) z[c] = 0.f;
+#pragma unroll
+    for (int r4 = 0; r4 < R / 4; ++r4) {
+      const float4 u = u4[r4];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        z[c] = fmaf(t[c][4 * r4], u.x, z[c]);
+        z[c] = fmaf(t[c][4 * r4 + 1], u.y, z[c]);
+        z[c] = fmaf(t[c][4 * r4 + 2], u.z, z[c]);
+        z[c] = fmaf(t[c][4 * r4 + 3], u.w, z[c]);
+      }
+    }
+    float* zr = Z + static_cast<size_t>(f0 + fb) * J;
+    float bv = -INFINITY;
+    int bi = -1;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int i = ibase + c * 256 + tid;
+      if (i < J) {
+        zr[i] = z[c];
+        if (bi < 0 || z[c] > bv) { bv = z[c]; bi = i; }
+      }
+    }
+    unsigned long long best = bi >= 0 ? argmax_key(bv, bi) : 0ull;
+    best = warp_max_u64(best);
+    if (lane == 0) red[warp * FB + fb] = best;
+  }
+  __syncthreads();
+  for (int fb = tid; fb < nf; fb += 256) {
+    unsigned long long b = 0ull;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) b = red[w * FB + fb] > b ? red[w * FB + fb] : b;
+    if (b) atomicMax(keys + f0 + fb, b);
+  }
+}
+
+template <int R, int CPT>
+static cudaError_t run_tall(const float* U, const float* tall, float* Z, unsigned long long* keys,
+                            int F, int J, cudaStream_t s) {
+  const int FB = 64;
+  const size_t smem = sizeof(float) * FB * R + sizeof(unsigned long long) * 8 * FB;
+  dim3 grid((J + 256 * CPT - 1) / (256 * CPT), (F + FB - 1) / FB);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(slri_tall_kernel<R, CPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  slri_tall_kernel<R, CPT><<<grid, 256, smem, s>>>(U, tall, Z, keys, F, J, FB);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slri_tall(const float* U, const float* tall, float* Z,
+                             unsigned long long* keys, int F, int J, int R, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  switch (R) {  // R is the padded rank (a multiple of 8, <= 64)
+    case 8: return run_tall<8, 4>(U, tall, Z, keys, F, J, s);
+    case 16: return run_tall<16, 4>(U, tall, Z, keys, F, J, s);
+    case 24: return run_tall<24, 2>(U, tall, Z, keys, F, J, s);
+    case 32: return run_tall<32, 2>(U, tall, Z, keys, F, J, s);
+    case 40: return run_tall<40, 1>(U, tall, Z, keys, F, J, s);
+    case 48: return run_tall<48, 1>(U, tall, Z, keys, F, J, s);
+    case 56: return run_tall<56, 1>(U, tall, Z, keys, F, J, s);
+    case 64: return run_tall<64, 1>(U, tall, Z, keys, F, J, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// SSPI gather.  A block stages xi of FB = 32*FPL frames transposed in shared memory
+// ([L][FB+1], lanes read consecutive frames), then walks row blocks of 64 cells: one
+// warp per row, taps read 32 at a time (coalesced) and broadcast by shuffle, FPL
+// frames per lane.  Row results go through a shared-memory tile so the map rows are
+// written coalesced and the argmax is reduced per frame.
+// ---------------------------------------------------------------------------------
+template <int FPL>
+__global__ __launch_bounds__(256) void sspi_kernel(const float* __restrict__ xi,
+                                                   const long long* __restrict__ row_ptr,
+                                                   const int2* __restrict__ taps,
+                                                   float* __restrict__ Z,
+                                                   unsigned long long* __restrict__ keys, int F,
+                                                   int J, int L, int nrb) {
+  constexpr int FB = 32 * FPL, RB = 64, XS = FB + 1, OS = RB + 1;
+  extern __shared__ float sm[];
+  float* xs = sm;            // [L][XS]
+  float* os = sm + L * XS;   // [FB][OS]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int f0 = blockIdx.x * FB;
+  const int nf = min(FB, F - f0);
+  for (int e = tid; e < FB * L; e += 256) {
+    const int fb = e / L, l = e - fb * L;
+    xs[l * XS + fb] = fb < nf ? xi[static_cast<size_t>(f0 + fb) * L + l] : 0.f;
+  }
+  __syncthreads();
+  for (int rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
+    const int i0 = rb * RB;
+    for (int rr = warp; rr < RB; rr += 8) {
+      const int i = i0 + rr;
+      float acc[FPL];
+#pragma unroll
+      for (int q = 0; q < FPL; ++q) acc[q] = 0.f;
+      if (i < J) {
+        const long long s = row_ptr[i], e = row_ptr[i + 1];
+        for (long long b = s; b < e; b += 32) {
+          const int2 tp = (b + lane < e) ? __ldg(taps + b + lane) : make_int2(0, 0);
+          const int cnt = static_cast<int>(min(32ll, e - b));
+          for (int t = 0; t < cnt; ++t) {
+            const int c = __shfl_sync(0xFFFFFFFFu, tp.x, t);
+            const float v = __int_as_float(__shfl_sync(0xFFFFFFFFu, tp.y, t));
+            const float* xr = xs + c * XS + lane;
+#pragma unroll
+            for (int q = 0; q < FPL; ++q) acc[q] = fmaf(v, xr[32 * q], acc[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < FPL; ++q) os[(lane + 32 * q) * OS + rr] = acc[q];
+    }
+    __syncthreads();
+    for (int fb = warp; fb < nf; fb += 8) {
+      unsigned long long best = 0ull;
+      float* zr = Z + static_cast<size_t>(f0 + fb) * J;
+      for (int rr = lane; rr < RB; rr += 32) {
+        const int i = i0 + rr;
+        if (i < J) {
+          const float v = os[fb * OS + rr];
+          zr[i] = v;
+          const unsigned long long k = argmax_key(v, i);
+          best = k > best ? k : best;
+        }
+      }
+      best = warp_max_u64(best);
+      if (lane == 0 && best) atomicMax(keys + f0 + fb, best);
+    }
+    __syncthreads();
+  }
+}
+
+template <int FPL>
+static size_t sspi_smem(int L) {
+  return sizeof(float) * (static_cast<size_t>(L) * (32 * FPL + 1) + 32 * FPL * 65);
+}
+
+cudaError_t launch_sspi(const float* xi, const long long* row_ptr, const int2* taps, float* Z,
+                        unsigned long long* keys, int F, int J, int L, int num_sms,
+                        cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  const int nrb = (J + 63) / 64;
+  const size_t lim2 = 110 * 1024, lim1 = 220 * 1024;
+  if (sspi_smem<2>(L) <= lim2) {
+    const size_t smem = sspi_smem<2>(L);
+    const int fx = (F + 63) / 64;
+    int gy = (2 * num_sms * 4 + fx - 1) / fx;
+    gy = max(1, min(gy, nrb));
+    cudaError_t e = cudaFuncSetAttribute(sspi_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    sspi_kernel<2><<<dim3(fx, gy), 256, smem, s>>>(xi, row_ptr, taps, Z, keys, F, J, L, nrb);
+  } else if (sspi_smem<1>(L) <= lim1) {
+    const size_t smem = sspi_smem<1>(L);
+    const int fx = (F + 31) / 32;
+    int gy = (num_sms * 4 + fx - 1) / fx;
+    gy = max(1, min(gy, nrb));
+    cudaError_t e = cudaFuncSetAttribute(sspi_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    sspi_kernel<1><<<dim3(fx, gy), 256, smem, s>>>(xi, row_ptr, taps, Z, keys, F, J, L, nrb);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+__global__ void argmax_finalize_kernel(const unsigned long long* __restrict__ keys,
+                                       int* __restrict__ out, int F) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const unsigned long long k = keys[f];
+  out[f] = k ? static_cast<int>(0xFFFFFFFFu - static_cast<unsigned>(k & 0xFFFFFFFFull)) : -1;
+}
+
+cudaError_t launch_argmax_finalize(const unsigned long long* keys, int* argmax, int F,
+                                   cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  argmax_finalize_kernel<<<(F + 255) / 256, 256, 0, s>>>(keys, argmax, F);
+  return cudaGetLastError();
+}
+
+}  // namespace srp

@@ -1,0 +1,142 @@
+// Internal declarations shared by the libsrp translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "libsrp.h"
+
+namespace srp {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+void clear_error();
+
+#define SRP_CUDA_TRY(expr)                                                          \
+  do {                                                                              \
+    cudaError_t _e = (expr);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      ::srp::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+      return SRP_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+// ------------------------------------------------------------------ host fitting
+struct Geometry {
+  int M = 0, P = 0, J = 0, N = 0, K = 0, L = 0;
+  double fs = 0, c = 0;
+  std::vector<int> pm, pmp;      // pair p -> (m, m'), m > m'
+  std::vector<int> Np, off;      // N_p and the offset of pair p in the stacked xi
+  std::vector<double> tau;       // [J][P] TDOA in samples, Delta t_p(i) * fs
+};
+
+// Builds pairs, N_p, offsets and the FP64 TDOA table (Eq. Deltat_i, Eq. N_p).
+srp_status build_geometry(const srp_plan_desc& d, Geometry& g);
+
+// Row i of Lambda (Eq. Lambda_p): sinc(tau_p(i) - n) for every pair and lag
+// n = -N_p..N_p (ascending), written to row[0..L).
+void lambda_row(const Geometry& g, int i, double* row);
+
+// Top-R eigenpairs of Lambda^T Lambda -> tall [J][R] (= Lambda V_R), fat [R][L]
+// (= V_R^T), sigma [L] (descending singular values).
+srp_status fit_low_rank(const Geometry& g, int R, std::vector<float>& tall,
+                        std::vector<float>& fat, std::vector<double>& sigma);
+
+// The Q_Lambda largest-magnitude entries of Lambda as CSR rows.
+srp_status fit_sparse(const Geometry& g, long long nnz, std::vector<long long>& row_ptr,
+                      std::vector<int>& col, std::vector<float>& val, long long& tied);
+
+unsigned host_threads();
+
+// ------------------------------------------------------------------ kernels
+// Front end: window + real DFT of length N + PHAT, y-hat [F][M][K] (bin 0 zeroed).
+cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const float* window,
+                             const float2* twiddle, float2* yhat, cudaStream_t s);
+// Cross-spectra, two-sided iFFT of length N, lag selection -> xi [F][L].
+cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N,
+                               const int2* pairs, const int* Np, const int* off, int L,
+                               const float2* twiddle, float* xi, cudaStream_t s);
+// Cross-spectra packed as the conv GEMM operand A [F][P*N]:
+// A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
+enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3 /* hi + lo planes */ };
+cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                             OpType t, void* A, void* A_lo, cudaStream_t s);
+// SRP matrix in GEMM layout B [J][P*N]: 2cos(theta), -2sin(theta), theta = 2 pi k tau / N.
+cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpType t, void* B,
+                               void* B_lo, cudaStream_t s);
+// Z[F][J] = A B^T in FP32 FFMA, fused per-frame argmax keys.
+cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
+                                   unsigned long long* keys, int F, int J, int Kd,
+                                   cudaStream_t s);
+// Tensor-core conv GEMM (tcgen05), fused argmax keys.  nseg = 1 (single precision
+// operand) or 3 (hi*hi + hi*lo + lo*hi).
+cudaError_t launch_conv_tc(const void* A, const void* A_lo, const void* B, const void* B_lo,
+                           OpType t, float* Z, unsigned long long* keys, int F, int J, int Kd,
+                           int num_sms, cudaStream_t s);
+bool conv_tc_supported(int F_max, int J, int Kd);
+
+// SLRI: U[F][R] = xi Lambda_fat^T ; Z = U Lambda_tall^T (fused argmax keys).
+cudaError_t launch_slri_fat(const float* xi, const float* fat, float* U, int F, int L, int R,
+                            cudaStream_t s);
+cudaError_t launch_slri_tall(const float* U, const float* tall, float* Z,
+                             unsigned long long* keys, int F, int J, int R, cudaStream_t s);
+// SSPI: Z[f][i] = sum over row i's taps of val * xi[f][col] (fused argmax keys).
+cudaError_t launch_sspi(const float* xi, const long long* row_ptr, const int2* taps, float* Z,
+                        unsigned long long* keys, int F, int J, int L, int num_sms,
+                        cudaStream_t s);
+// keys -> argmax (lowest index among equal maxima).
+cudaError_t launch_argmax_finalize(const unsigned long long* keys, int* argmax, int F,
+                                   cudaStream_t s);
+
+}  // namespace srp
+
+// ------------------------------------------------------------------ the plan
+struct srp_plan_s {
+  int device = 0;
+  srp_plan_desc desc{};
+  srp::Geometry g;
+  int R = 0;
+  long long nnz = 0, tied = 0;
+  int Fmax = 0;
+  int num_sms = 0;
+  srp::OpType op = srp::OpType::F32;
+  bool conv_tc = false;
+  std::vector<double> sigma;
+  std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
+  std::vector<int> h_col;
+  std::vector<float> h_val;
+  // device tables
+  int2* d_pairs = nullptr;
+  int* d_Np = nullptr;
+  int* d_off = nullptr;
+  float2* d_twiddle = nullptr;
+  float* d_window = nullptr;
+  void* d_H = nullptr;
+  void* d_H_lo = nullptr;
+  float* d_tall = nullptr;
+  float* d_fat = nullptr;
+  long long* d_row_ptr = nullptr;
+  int2* d_taps = nullptr;
+  // scratch
+  float2* d_yhat = nullptr;
+  void* d_A = nullptr;
+  void* d_A_lo = nullptr;
+  float* d_xi = nullptr;
+  float* d_U = nullptr;
+  unsigned long long* d_keys = nullptr;
+  // staging for srp_map_host
+  float* d_stage_frames = nullptr;
+  float* d_stage_maps = nullptr;
+  int* d_stage_arg = nullptr;
+  size_t device_bytes = 0;
+  double fit_seconds = 0;
+  // per-stage timing: 5 events per internal chunk of the last call
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  int chunks_recorded = 0;
+};

@@ -1,0 +1,76 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the header
+declares, and rejects invalid plan descriptions before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_symbols():
+    text = open(os.path.join(ROOT, "include", "libsrp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(srp_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2306_08514_gb300 as S
+    if not os.path.exists(S.LIB_PATH):
+        from paper_2306_08514_gb300 import build
+        build.build()
+    S.lib()
+    return S
+
+
+def test_library_exports_every_declared_symbol(S):
+    syms = _header_symbols()
+    assert len(syms) >= 10
+    for name in syms:
+        assert hasattr(S.lib(), name), name
+    assert set(syms) == set(S.SIGNATURES)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(M=1), dict(N=500), dict(N=128), dict(N=4096), dict(fs=0.0), dict(c=-1.0),
+    dict(window=7), dict(n_aux=-1), dict(max_frames=0), dict(method=9),
+    dict(method=1, rank=0), dict(method=1, rank=65), dict(method=2, taps=0.0),
+    dict(method=2, taps=1e9), dict(precision=3),
+])
+def test_invalid_desc_is_rejected_on_the_host(S, bad):
+    mics = synth.mics_square()
+    grid = synth.grid_plane((0, 0), (4, 4), (5, 5))
+    kw = dict(mic_xyz=mics, grid_xyz=grid, fs=16000.0, N=512)
+    kw.update({k: v for k, v in bad.items() if k in ("fs", "N")})
+    d = S.make_desc(kw["mic_xyz"], kw["grid_xyz"], kw["fs"], kw["N"],
+                    method=bad.get("method", 0), rank=bad.get("rank", 4), taps=bad.get("taps", 1.0),
+                    precision=bad.get("precision", 0), c=bad.get("c", 340.0),
+                    n_aux=bad.get("n_aux", 2), max_frames=bad.get("max_frames", 8))
+    if "M" in bad:
+        d.M = bad["M"]
+    if "window" in bad:
+        d.window = bad["window"]
+    with pytest.raises(S.SrpError) as e:
+        S.srp_plan_create(d, None)
+    assert e.value.status in (S.SRP_EINVAL, S.SRP_EUNSUPPORTED)
+    assert S.srp_last_error()
+
+
+def test_window_wider_than_frame_is_rejected(S):
+    mics = synth.mics_square() * 40.0
+    grid = synth.grid_plane((0, 0), (4, 4), (5, 5))
+    d = S.make_desc(mics, grid, 16000.0, 256)
+    with pytest.raises(S.SrpError) as e:
+        S.srp_plan_create(d, None)
+    assert e.value.status == S.SRP_EINVAL
+    assert "N_p" in S.srp_last_error()
+
+
+def test_null_arguments(S):
+    assert S.lib().srp_map(None, None, 1, None, None, None) == S.SRP_EINVAL
+    assert S.lib().srp_plan_info(None, None) == S.SRP_EINVAL
+    S.srp_destroy(None)

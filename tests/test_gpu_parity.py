@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C-ABI) against the FP64 oracle, on the GPU.
+
+Tolerances: FP32 paths must match the oracle to <= 1e-5 relative per frame
+(sqrt(||z_gpu - z||^2 / ||z||^2)); the argmax the GPU returns must be the argmax of
+its own FP32 map exactly (same precision decides), and a valid argmax of the oracle map
+within the GPU's measured error.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests import _ref as R
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2306_08514_gb300 as S
+    S.lib()
+    return S
+
+
+def _cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run(plan, frames):
+    import torch
+    maps, am = plan.map(_cuda(frames))
+    torch.cuda.synchronize()
+    return maps.cpu().numpy(), am.cpu().numpy()
+
+
+def check_argmax(z, am, zo):
+    assert np.array_equal(am, np.argmax(z, axis=1)), "argmax differs from the GPU map's own"
+    err = np.max(np.abs(z.astype(np.float64) - zo), axis=1)
+    picked = zo[np.arange(len(am)), am]
+    assert np.all(picked >= zo.max(axis=1) - 2 * err - 1e-9), "argmax is not a valid oracle maximum"
+    return float(np.mean(am == np.argmax(zo, axis=1)))
+
+
+# ------------------------------------------------------------------ sampling stage
+@pytest.mark.parametrize("N", [256, 512, 1024, 2048])
+def test_gcc_samples_match_oracle(S, N):
+    """Eq. xi_p_ifft / n_prime on the GPU vs the oracle's iFFT sampling."""
+    mics = synth.mics_square()
+    grid = synth.grid_plane((1, 1), (3, 3), (8, 8))
+    g = synth.rng(N)
+    frames = g.standard_normal((37, 4, N)).astype(np.float32)
+    plan = S.Plan(mics, grid, 16000.0, N, method="sspi", taps=1.0, max_frames=16)
+    import torch
+    xi = plan.gcc_samples(_cuda(frames)).cpu().numpy()
+    torch.cuda.synchronize()
+    Np = O.n_p_samples(mics, 16000.0)
+    assert np.array_equal(plan.lags(), Np)
+    lags = O.pair_lags(Np)
+    ref = R.xi_ascending(R.psi_of(frames), lags, O.lags_to_ascending(lags), N // 2)
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    assert np.max(np.abs(xi - ref) / scale) <= TOL
+
+
+# ------------------------------------------------------------------ square4 (full size)
+@pytest.fixture(scope="module")
+def sq():
+    w = R.workload("square4")
+    psi = R.psi_of(w["frames"])
+    dt, Np, lags, perm = R.geometry("square4")
+    xi_o, _ = O.gcc_samples_ifft(psi, lags, w["N"] // 2)
+    return w, psi, dt, lags, perm, xi_o
+
+
+def test_conv_fp32_square4(S, sq):
+    w, psi, dt, *_ = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="conv", max_frames=64)
+    z, am = _run(plan, w["frames"])
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    assert check_argmax(z, am, zo) >= 0.99
+
+
+@pytest.mark.parametrize("rank", [8, 16])
+def test_slri_square4(S, sq, rank):
+    w, psi, dt, lags, perm, xi_o = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="slri", rank=rank,
+                  max_frames=64)
+    tall, fat, s = R.slri("square4", rank)
+    sig = plan.slri_sigma(rank + 1)
+    assert np.allclose(sig, s[:rank + 1], rtol=1e-9, atol=1e-9 * s[0])
+    z, am = _run(plan, w["frames"])
+    zo = O.srp_slri(tall, fat, xi_o)
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    check_argmax(z, am, zo)
+
+
+def _check_taps(plan, mask_o, perm, lam_o):
+    J, L = mask_o.shape
+    row_ptr, col, val = plan.sspi_taps()
+    assert row_ptr[-1] == mask_o.sum()
+    m = np.zeros((J, L), bool)
+    rows = np.repeat(np.arange(J), np.diff(row_ptr))
+    m[rows, col] = True
+    mo = mask_o[:, perm]
+    lam_a = lam_o[:, perm]
+    diff = m != mo
+    if diff.any():  # only ties at the cut may differ (quantised magnitudes equal)
+        keys = np.floor(np.abs(lam_a) * 2.0 ** 40 + 0.5)
+        kmin = keys[mo].min()
+        assert np.all(keys[diff] == kmin)
+    assert np.allclose(val, lam_a[rows, col].astype(np.float32), rtol=0, atol=0)
+    return int(diff.sum())
+
+
+@pytest.mark.parametrize("t", [0.5, 1.0, 2.0, 4.0])
+def test_sspi_square4(S, sq, t):
+    w, psi, dt, lags, perm, xi_o = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="sspi", taps=t,
+                  max_frames=64)
+    mask, tied, taken, nnz = R.sspi("square4", t)
+    assert plan.info.nnz == nnz
+    ndiff = _check_taps(plan, mask, perm, R.lam("square4"))
+    z, am = _run(plan, w["frames"])
+    if ndiff == 0:
+        Lsp = np.where(mask, R.lam("square4"), 0.0)
+        zo = O.srp_sspi(Lsp, xi_o)
+        assert R.per_frame_rel(z, zo).max() <= TOL
+        check_argmax(z, am, zo)
+    else:
+        assert np.array_equal(am, np.argmax(z, axis=1))
+
+
+# ------------------------------------------------------------------ uca8, several tiles
+@pytest.fixture(scope="module")
+def uca_small():
+    name, F, sub = "uca8", 70, 13
+    w = R.workload(name, F, sub)
+    psi = R.psi_of(w["frames"])
+    dt, Np, lags, perm = R.geometry(name, F, sub)
+    xi_o, _ = O.gcc_samples_ifft(psi, lags, w["N"] // 2)
+    return name, F, sub, w, psi, dt, lags, perm, xi_o
+
+
+def test_uca8_small_all_methods(S, uca_small):
+    name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    z, am = _run(S.Plan(*args, method="conv", max_frames=64), w["frames"])
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    check_argmax(z, am, zo)
+    tall, fat, s = R.slri(name, 16, F, sub)
+    z, am = _run(S.Plan(*args, method="slri", rank=16, max_frames=64), w["frames"])
+    zo = O.srp_slri(tall, fat, xi_o)
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    mask, tied, taken, nnz = R.sspi(name, 4.0, F, sub)
+    plan = S.Plan(*args, method="sspi", taps=4.0, max_frames=64)
+    ndiff = _check_taps(plan, mask, perm, R.lam(name, F, sub))
+    z, am = _run(plan, w["frames"])
+    if ndiff == 0:
+        zo = O.srp_sspi(np.where(mask, R.lam(name, F, sub), 0.0), xi_o)
+        assert R.per_frame_rel(z, zo).max() <= TOL
+
+
+# ------------------------------------------------------------------ edge cases
+def test_edge_cases(S):
+    import torch
+    mics = synth.mics_square()
+    grid = synth.grid_plane((0, 0), (4, 4), (5, 5))
+    plan = S.Plan(mics, grid, 16000.0, 512, method="conv", max_frames=8)
+    empty = torch.empty((0, 4, 512), device="cuda")
+    maps, am = plan.map(empty)
+    assert maps.shape == (0, 25)
+    with pytest.raises(S.SrpError) as e:
+        S.srp_map(plan.handle, None, 3, None, None, None)
+    assert e.value.status == S.SRP_EINVAL
+    with pytest.raises(S.SrpError):
+        S.srp_map(plan.handle, None, -1, None, None, None)
+    # a single location, a single frame, every method
+    g1 = grid[12:13]
+    fr = synth.rng(1).standard_normal((1, 4, 512)).astype(np.float32)
+    psi = R.psi_of(fr)
+    dt = O.tdoa_nf(mics, g1)
+    for kw in (dict(method="conv"), dict(method="slri", rank=1), dict(method="sspi", taps=1.0)):
+        z, am = _run(S.Plan(mics, g1, 16000.0, 512, max_frames=1, **kw), fr)
+        assert am[0] == 0 and np.isfinite(z).all()
+    zc, _ = _run(S.Plan(mics, g1, 16000.0, 512, method="conv"), fr)
+    assert abs(zc[0, 0] - O.srp_conv(psi, dt, 16000.0)[0, 0]) <= TOL * abs(O.srp_conv(psi, dt, 16000.0)[0, 0]) + 1e-3
+
+
+def test_silent_channel(S):
+    w = R.workload("square4")
+    fr = w["frames"][:9].copy()
+    fr[:, 2, :] = 0.0
+    psi = R.psi_of(fr)
+    dt, *_ = R.geometry("square4")
+    z, am = _run(S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="conv"), fr)
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z, zo).max() <= TOL
+
+
+def test_invalid_plans_rejected(S):
+    mics = synth.mics_square()
+    grid = synth.grid_plane((0, 0), (4, 4), (5, 5))
+    with pytest.raises(S.SrpError) as e:
+        S.Plan(mics, grid, 16000.0, 500)
+    assert e.value.status == S.SRP_EINVAL
+    far = mics * 40.0  # pairs so far apart that N_p >= K
+    with pytest.raises(S.SrpError) as e:
+        S.Plan(far, grid, 16000.0, 256)
+    assert e.value.status == S.SRP_EINVAL
+
+
+def test_host_entry_matches_device_entry_and_is_deterministic(S):
+    w = R.workload("square4")
+    fr = np.ascontiguousarray(w["frames"][:40])
+    for kw in (dict(method="conv"), dict(method="slri", rank=8), dict(method="sspi", taps=2.0)):
+        plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], max_frames=16, **kw)
+        z1, a1 = _run(plan, fr)
+        z2, a2 = _run(plan, fr)
+        assert np.array_equal(z1, z2) and np.array_equal(a1, a2)
+        zh, ah = plan.map_host(fr)
+        assert np.array_equal(zh, z1) and np.array_equal(ah, a1)
+
+
+def test_largest_fft_and_most_mics_conv(S):
+    """N = 2048 and M = 32 (nested arrays) on a reduced grid."""
+    w = R.workload("nested32", 6, 400)
+    psi = R.psi_of(w["frames"])
+    dt, *_ = R.geometry("nested32", 6, 400)
+    z, am = _run(S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="conv",
+                        max_frames=4), w["frames"])
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    check_argmax(z, am, zo)
+
+
+# ------------------------------------------------------------------ full-size uca8 (bench config)
+@pytest.fixture(scope="module")
+def uca_full():
+    w = R.workload("uca8")
+    return w
+
+
+def test_uca8_full_size_sampled(S, uca_full):
+    """The benchmark's workload (M=8 UCA, J=60000, F=2000, one launch per method): the
+    oracle evaluates sampled frames exactly."""
+    w = uca_full
+    F = w["F"]
+    frames = w["frames"]
+    fsel = np.array([0, 1, 777, 1500, F - 1])
+    psi = R.psi_of(frames[fsel])
+    dt, Np, lags, perm = R.geometry("uca8")
+    xi_o, _ = O.gcc_samples_ifft(psi, lags, w["N"] // 2)
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    # conv, FP32, on all J for the sampled frames
+    z, am = _run(S.Plan(*args, method="conv", max_frames=F), frames)
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z[fsel], zo).max() <= TOL
+    check_argmax(z[fsel], am[fsel], zo)
+    # SLRI, R = 16
+    tall, fat, s = R.slri("uca8", 16)
+    z, am = _run(S.Plan(*args, method="slri", rank=16, max_frames=F), frames)
+    zo = O.srp_slri(tall, fat, xi_o)
+    assert R.per_frame_rel(z[fsel], zo).max() <= TOL
+    check_argmax(z[fsel], am[fsel], zo)
+    # SSPI, t = 4
+    mask, tied, taken, nnz = R.sspi("uca8", 4.0)
+    plan = S.Plan(*args, method="sspi", taps=4.0, max_frames=F)
+    ndiff = _check_taps(plan, mask, perm, R.lam("uca8"))
+    z, am = _run(plan, frames)
+    if ndiff == 0:
+        zo = O.srp_sspi(np.where(mask, R.lam("uca8"), 0.0), xi_o)
+        assert R.per_frame_rel(z[fsel], zo).max() <= TOL
+        check_argmax(z[fsel], am[fsel], zo)
