@@ -78,7 +78,7 @@ void free_plan(srp_plan_s* p) {
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
-                  p->d_xi, p->d_U, p->d_keys, p->d_stage_frames, p->d_stage_maps,
+                  p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_stage_frames, p->d_stage_maps,
                   p->d_stage_arg};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -145,7 +145,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       if (p->op == OpType::F32) {
         SRP_CUDA_TRY(launch_sgemm_nt_argmax(static_cast<const float*>(p->d_A),
                                             static_cast<const float*>(p->d_H), maps, p->d_keys,
-                                            F, g.J, Kd, s));
+                                            F, g.J, Kd, p->d_split, s));
       } else {
         SRP_CUDA_TRY(launch_conv_tc(p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, p->op, maps, p->d_keys,
                                     F, g.J, Kd, p->num_sms, s));
@@ -277,6 +277,9 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(g.J) * Kd * eb);
     SRP_ALLOC(p, p->d_A, F * Kd * eb);
     if (split) SRP_ALLOC(p, p->d_A_lo, F * Kd * eb);
+    const int nsplit = sgemm_split_count(static_cast<int>(Kd));
+    if (p->op == OpType::F32 && nsplit > 1)
+      SRP_ALLOC(p, p->d_split, sizeof(float) * nsplit * F * static_cast<size_t>(g.J));
     double* d_tau = nullptr;
     if (cudaMalloc(&d_tau, sizeof(double) * g.tau.size()) != cudaSuccess) {
       cudaGetLastError();

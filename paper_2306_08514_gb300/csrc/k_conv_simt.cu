@@ -15,9 +15,12 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 8, PADS = 4;
 }
 
+// With kslice < Kd the reduction is split: block z covers k-tiles
+// [z*kslice, (z+1)*kslice) and writes its partial map to Z + z*F*J without the argmax
+// (the partials are summed by split_reduce_argmax_kernel).
 __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
     const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ Z,
-    unsigned long long* __restrict__ keys, int F, int J, int Kd) {
+    unsigned long long* __restrict__ keys, int F, int J, int Kd, int kslice) {
   __shared__ __align__(16) float As[2][BK][BM + PADS];
   __shared__ __align__(16) float Bs[2][BK][BN + PADS];
   const int tid = threadIdx.x;
@@ -26,8 +29,12 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
   const int lr = tid >> 1, lk = (tid & 1) * 4;
   const bool aok = (m0 + lr) < F;
   const bool bok = (n0 + lr) < J;
-  const float4* Ap = reinterpret_cast<const float4*>(A + static_cast<size_t>(aok ? m0 + lr : 0) * Kd + lk);
-  const float4* Bp = reinterpret_cast<const float4*>(B + static_cast<size_t>(bok ? n0 + lr : 0) * Kd + lk);
+  const int kbeg = blockIdx.z * kslice;
+  const int kend = min(Kd, kbeg + kslice);
+  const bool split = kslice < Kd;
+  if (split) Z += static_cast<size_t>(blockIdx.z) * F * J;
+  const float4* Ap = reinterpret_cast<const float4*>(A + static_cast<size_t>(aok ? m0 + lr : 0) * Kd + kbeg + lk);
+  const float4* Bp = reinterpret_cast<const float4*>(B + static_cast<size_t>(bok ? n0 + lr : 0) * Kd + kbeg + lk);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 ra = aok ? __ldg(Ap) : z4;
   float4 rb = bok ? __ldg(Bp) : z4;
@@ -41,7 +48,7 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-  const int nk = Kd / BK;
+  const int nk = (kend - kbeg) / BK;
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
     if (kt + 1 < nk) {
@@ -92,17 +99,63 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
       const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
       best = other > best ? other : best;
     }
-    if (tx == 0 && m < F && best) atomicMax(keys + m, best);
+    if (!split && tx == 0 && m < F && best) atomicMax(keys + m, best);
   }
+}
+
+// Z[f][i] = sum over the nsplit partial maps (summed in FP64), plus the argmax keys.
+__global__ __launch_bounds__(256) void split_reduce_argmax_kernel(const float* __restrict__ part,
+                                                                  int nsplit, float* __restrict__ Z,
+                                                                  unsigned long long* __restrict__ keys,
+                                                                  int F, int J) {
+  __shared__ unsigned long long red[8];
+  const int f = blockIdx.y;
+  const size_t FJ = static_cast<size_t>(F) * J;
+  unsigned long long best = 0ull;
+  for (int i = blockIdx.x * 1024 + threadIdx.x; i < min(J, (blockIdx.x + 1) * 1024); i += 256) {
+    const size_t idx = static_cast<size_t>(f) * J + i;
+    double acc = 0.0;
+    for (int z = 0; z < nsplit; ++z) acc += static_cast<double>(part[z * FJ + idx]);
+    const float v = static_cast<float>(acc);
+    Z[idx] = v;
+    const unsigned long long k = argmax_key(v, i);
+    best = k > best ? k : best;
+  }
+  best = warp_max_u64(best);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0ull;
+    for (int w = 0; w < 8; ++w) b = red[w] > b ? red[w] : b;
+    if (b) atomicMax(keys + f, b);
+  }
+}
+
+int sgemm_split_count(int Kd) {
+  const int per = 16384;  // reduction terms accumulated sequentially in FP32 per slice
+  return Kd <= per ? 1 : (Kd + per - 1) / per;
 }
 
 cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
                                    unsigned long long* keys, int F, int J, int Kd,
-                                   cudaStream_t s) {
+                                   float* split_ws, cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
   if (Kd % BK != 0) return cudaErrorInvalidValue;
-  dim3 grid((J + BN - 1) / BN, (F + BM - 1) / BM);
-  sgemm_nt_argmax_kernel<<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd);
+  const int nsplit = sgemm_split_count(Kd);
+  if (nsplit == 1) {
+    dim3 grid((J + BN - 1) / BN, (F + BM - 1) / BM, 1);
+    sgemm_nt_argmax_kernel<<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd, Kd);
+    return cudaGetLastError();
+  }
+  if (!split_ws) return cudaErrorInvalidValue;
+  int kslice = (Kd / BK + nsplit - 1) / nsplit * BK;
+  const int nz = (Kd + kslice - 1) / kslice;
+  dim3 grid((J + BN - 1) / BN, (F + BM - 1) / BM, nz);
+  sgemm_nt_argmax_kernel<<<grid, 256, 0, s>>>(A, B, split_ws, keys, F, J, Kd, kslice);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 g2((J + 1023) / 1024, F);
+  split_reduce_argmax_kernel<<<g2, 256, 0, s>>>(split_ws, nz, Z, keys, F, J);
   return cudaGetLastError();
 }
 

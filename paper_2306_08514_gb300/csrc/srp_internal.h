@@ -69,10 +69,13 @@ cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, con
 // SRP matrix in GEMM layout B [J][P*N]: 2cos(theta), -2sin(theta), theta = 2 pi k tau / N.
 cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpType t, void* B,
                                void* B_lo, cudaStream_t s);
-// Z[F][J] = A B^T in FP32 FFMA, fused per-frame argmax keys.
+// Z[F][J] = A B^T in FP32 FFMA, fused per-frame argmax keys.  For long reductions
+// (sgemm_split_count(Kd) > 1) the k range is split into slices of <= 16384 terms whose
+// partial maps go to split_ws [nsplit][F][J] and are summed in FP64.
+int sgemm_split_count(int Kd);
 cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
                                    unsigned long long* keys, int F, int J, int Kd,
-                                   cudaStream_t s);
+                                   float* split_ws, cudaStream_t s);
 // Tensor-core conv GEMM (tcgen05), fused argmax keys.  nseg = 1 (single precision
 // operand) or 3 (hi*hi + hi*lo + lo*hi).
 cudaError_t launch_conv_tc(const void* A, const void* A_lo, const void* B, const void* B_lo,
@@ -126,6 +129,7 @@ struct srp_plan_s {
   float2* d_yhat = nullptr;
   void* d_A = nullptr;
   void* d_A_lo = nullptr;
+  float* d_split = nullptr;  // conv FP32 split-reduction partial maps
   float* d_xi = nullptr;
   float* d_U = nullptr;
   unsigned long long* d_keys = nullptr;
