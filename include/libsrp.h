@@ -197,6 +197,33 @@ enum { SRP_STAGE_FRONTEND = 0, SRP_STAGE_SPECTRA = 1, SRP_STAGE_CONTRACT = 2,
 srp_status srp_plan_set_profiling(srp_plan_t plan, int enable);
 srp_status srp_plan_stage_ms(srp_plan_t plan, float* ms, int* calls);
 
+/*
+ * srp_slri_apply_static -- the SLRI interpolation of one batch, u = Lambda_fat xi then
+ * z = Lambda_tall u and the argmax per frame, without allocating any memory.  The paper
+ * has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory when they process frames, e.g. a real-time audio thread with a per-frame
+ * deadline (cudaMalloc may block and synchronise the whole device) or a host whose
+ * device memory is owned and budgeted by its own pool, which forbids allocations
+ * outside it.  Such a caller brings its own factors (e.g. computed offline) and buffers.
+ *   xi:     device float [F][L], TD GCC samples (as written by srp_gcc_samples).
+ *   fat:    device float [R][L], Lambda_fat.
+ *   tall:   device float [J][R], Lambda_tall, 16-byte aligned.
+ *   R:      8, 16, 24, ..., 64 (pad a smaller rank with zero rows/columns).
+ *   maps:   device float [F][J], written.   argmax: device int32 [F] or NULL, written.
+ * Limits: F <= 65536, F * R <= 1048576, 1 <= L <= 50000; larger requests return
+ * SRP_EINVAL with a message.  F = 0 is a no-op.  Asynchronous on `stream`.
+ * Scratch: the intermediate u and the argmax keys live in one file-scope device array of
+ * 4.5 MiB; every GPU that loads libsrp holds it until the process exits.  All calls on
+ * a device share it and each call overwrites it (the keys are cleared by the call), so
+ * calls whose execution overlaps on the GPU (different streams, or different host
+ * threads without ordering) race and give wrong results: serialise them.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Errors: SRP_EINVAL, SRP_ECUDA, SRP_EUNSUPPORTED (device index > 63).
+ */
+srp_status srp_slri_apply_static(const float* xi, const float* fat, const float* tall, int F,
+                                 int L, int R, int J, float* maps, int* argmax, void* stream);
+
 /* srp_destroy -- release a plan and its device memory (synchronises the device). */
 void srp_destroy(srp_plan_t plan);
 

@@ -54,6 +54,8 @@ SIGNATURES = {
     "srp_plan_slri_sigma": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int]),
     "srp_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "srp_plan_stage_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
+    "srp_slri_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                        C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "srp_destroy": (None, [C.c_void_p]),
     "srp_last_error": (C.c_char_p, []),
 }
@@ -154,6 +156,13 @@ def srp_plan_stage_ms(plan) -> dict:
     d = dict(zip(STAGES, [float(v) for v in out]))
     d["chunks"] = int(n.value)
     return d
+
+
+def srp_slri_apply_static(xi_ptr, fat_ptr, tall_ptr, F, L, R, J, maps_ptr, argmax_ptr,
+                          stream) -> None:
+    """Allocation-free SLRI interpolation (pointers are device addresses)."""
+    _check(lib().srp_slri_apply_static(xi_ptr, fat_ptr, tall_ptr, F, L, R, J, maps_ptr,
+                                       argmax_ptr, stream))
 
 
 def srp_destroy(plan) -> None:

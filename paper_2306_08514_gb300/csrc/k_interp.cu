@@ -6,6 +6,9 @@
 #include "srp_internal.h"
 #include "srp_device.cuh"
 
+#include <cstdint>
+#include <mutex>
+
 namespace srp {
 
 // ---------------------------------------------------------------------------------
@@ -307,3 +310,94 @@ cudaError_t launch_argmax_finalize(const unsigned long long* keys, int* argmax, 
 }
 
 }  // namespace srp
+
+// ---------------------------------------------------------------------------------
+// Allocation-free SLRI interpolation (srp_slri_apply_static in include/libsrp.h).
+// The intermediate u = Lambda_fat xi and the argmax keys live in one file-scope device
+// array instead of plan scratch: u at offset 0 (kStaticUFloats floats), keys after it.
+// Host code must not pass the array's name to a kernel (on the host it is only a
+// stand-in): the device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, and cached.
+// ---------------------------------------------------------------------------------
+namespace srp {
+namespace {
+constexpr size_t kStaticUFloats = size_t(1) << 20;  // F * R <= 1,048,576 (4 MiB)
+constexpr int kStaticMaxFrames = 65536;             // argmax keys (512 KiB)
+constexpr size_t kStaticBytes =
+    kStaticUFloats * sizeof(float) + kStaticMaxFrames * sizeof(unsigned long long);
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_slri_static_scratch[kStaticBytes];
+
+static srp_status static_scratch(void** out) {
+  int dev = 0;
+  SRP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("srp_slri_apply_static: device index beyond 63");
+    return SRP_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_slri_static_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("srp_slri_apply_static: cudaGetSymbolAddress failed: ") +
+                cudaGetErrorString(e));
+      return SRP_ECUDA;
+    }
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return SRP_OK;
+}
+
+}  // namespace srp
+
+extern "C" srp_status srp_slri_apply_static(const float* xi, const float* fat, const float* tall,
+                                            int F, int L, int R, int J, float* maps, int* argmax,
+                                            void* stream) {
+  using namespace srp;
+  clear_error();
+  if (F < 0) {
+    set_error("srp_slri_apply_static: F < 0");
+    return SRP_EINVAL;
+  }
+  if (F == 0) return SRP_OK;
+  if (!xi || !fat || !tall || !maps) {
+    set_error("srp_slri_apply_static: xi, fat, tall or maps is NULL");
+    return SRP_EINVAL;
+  }
+  if (L < 1 || L > 50000 || J < 1) {
+    set_error("srp_slri_apply_static: need 1 <= L <= 50000 and J >= 1");
+    return SRP_EINVAL;
+  }
+  if (R < 8 || R > 64 || R % 8 != 0) {
+    set_error("srp_slri_apply_static: R must be one of 8, 16, ..., 64 (pad factors with zeros)");
+    return SRP_EINVAL;
+  }
+  if (F > kStaticMaxFrames || static_cast<size_t>(F) * R > kStaticUFloats) {
+    set_error("srp_slri_apply_static: F = " + std::to_string(F) + ", R = " + std::to_string(R) +
+              " exceeds the static scratch (F <= 65536 and F * R <= 1048576)");
+    return SRP_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(tall) % 16 != 0) {
+    set_error("srp_slri_apply_static: tall must be 16-byte aligned");
+    return SRP_EINVAL;
+  }
+  void* base = nullptr;
+  srp_status st = static_scratch(&base);
+  if (st != SRP_OK) return st;
+  float* U = static_cast<float*>(base);
+  unsigned long long* keys =
+      reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(base) +
+                                            kStaticUFloats * sizeof(float));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SRP_CUDA_TRY(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * F, s));
+  SRP_CUDA_TRY(launch_slri_fat(xi, fat, U, F, L, R, s));
+  SRP_CUDA_TRY(launch_slri_tall(U, tall, maps, keys, F, J, R, s));
+  if (argmax) SRP_CUDA_TRY(launch_argmax_finalize(keys, argmax, F, s));
+  return SRP_OK;
+}
