@@ -198,6 +198,15 @@ srp_status srp_plan_set_profiling(srp_plan_t plan, int enable);
 srp_status srp_plan_stage_ms(srp_plan_t plan, float* ms, int* calls);
 
 /*
+ * srp_plan_status -- failure detection for the kernels' bounded waits.  Synchronises
+ * `stream`, then returns SRP_ETIMEOUT (and clears the record) if a wait inside one of
+ * the plan's kernels ran out since the last query: the kernel then abandoned its tile
+ * loop, released its resources and returned, and the maps of that call are invalid.
+ * Returns SRP_OK otherwise.  Errors: SRP_EINVAL (NULL plan), SRP_ECUDA.
+ */
+srp_status srp_plan_status(srp_plan_t plan, void* stream);
+
+/*
  * srp_slri_apply_static -- the SLRI interpolation of one batch, u = Lambda_fat xi then
  * z = Lambda_tall u and the argmax per frame, without allocating any memory.  The paper
  * has no counterpart: this entry point exists for callers that cannot allocate device

@@ -7,7 +7,7 @@ this package is its Python binding.
 """
 from ._abi import (  # noqa: F401
     Plan, SrpError, srp_plan_create, srp_plan_info, srp_plan_lags, srp_map, srp_map_host,
-    srp_gcc_samples, srp_plan_sspi_taps, srp_plan_slri_sigma, srp_plan_set_profiling, srp_plan_stage_ms, srp_slri_apply_static,
+    srp_gcc_samples, srp_plan_sspi_taps, srp_plan_slri_sigma, srp_plan_set_profiling, srp_plan_stage_ms, srp_plan_status, srp_slri_apply_static,
     srp_destroy, srp_last_error,
     make_desc, lib, SIGNATURES, LIB_PATH,
     SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_ETIMEOUT, SRP_EUNSUPPORTED,

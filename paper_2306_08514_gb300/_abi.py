@@ -54,6 +54,7 @@ SIGNATURES = {
     "srp_plan_slri_sigma": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int]),
     "srp_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "srp_plan_stage_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
+    "srp_plan_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "srp_slri_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                         C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "srp_destroy": (None, [C.c_void_p]),
@@ -158,6 +159,11 @@ def srp_plan_stage_ms(plan) -> dict:
     return d
 
 
+def srp_plan_status(plan, stream=None) -> None:
+    """Raise SrpError(SRP_ETIMEOUT) if a bounded wait in one of the plan's kernels ran out."""
+    _check(lib().srp_plan_status(plan, stream))
+
+
 def srp_slri_apply_static(xi_ptr, fat_ptr, tall_ptr, F, L, R, J, maps_ptr, argmax_ptr,
                           stream) -> None:
     """Allocation-free SLRI interpolation (pointers are device addresses)."""
@@ -247,6 +253,9 @@ class Plan:
 
     def stage_ms(self):
         return srp_plan_stage_ms(self.handle)
+
+    def status(self, stream=None):
+        srp_plan_status(self.handle, _stream_handle(stream))
 
     def lags(self):
         return srp_plan_lags(self.handle, self.P)

@@ -78,7 +78,7 @@ void free_plan(srp_plan_s* p) {
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
-                  p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_stage_frames, p->d_stage_maps,
+                  p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
                   p->d_stage_arg};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -148,7 +148,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
                                             F, g.J, Kd, p->d_split, s));
       } else {
         SRP_CUDA_TRY(launch_conv_tc(p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, p->op, maps, p->d_keys,
-                                    F, g.J, Kd, p->num_sms, s));
+                                    F, g.J, Kd, p->num_sms, p->d_split, p->d_err, s));
       }
       break;
     }
@@ -268,6 +268,8 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   const size_t F = static_cast<size_t>(p->Fmax);
   SRP_ALLOC(p, p->d_yhat, sizeof(float2) * F * g.M * (g.N / 2));
   SRP_ALLOC(p, p->d_keys, sizeof(unsigned long long) * F);
+  SRP_ALLOC(p, p->d_err, sizeof(int));
+  SRP_PLAN_CUDA(p, cudaMemsetAsync(p->d_err, 0, sizeof(int), s));
 
   if (desc->method == SRP_CONV) {
     const size_t Kd = static_cast<size_t>(g.P) * g.N;
@@ -277,9 +279,15 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(g.J) * Kd * eb);
     SRP_ALLOC(p, p->d_A, F * Kd * eb);
     if (split) SRP_ALLOC(p, p->d_A_lo, F * Kd * eb);
-    const int nsplit = sgemm_split_count(static_cast<int>(Kd));
-    if (p->op == OpType::F32 && nsplit > 1)
-      SRP_ALLOC(p, p->d_split, sizeof(float) * nsplit * F * static_cast<size_t>(g.J));
+    size_t ws_floats = 0;
+    if (p->op == OpType::F32) {
+      const int nsplit = sgemm_split_count(static_cast<int>(Kd));
+      if (nsplit > 1) ws_floats = static_cast<size_t>(nsplit) * F * g.J;
+    } else {
+      ws_floats = conv_tc_workspace_floats(p->Fmax, g.J, static_cast<int>(Kd), split ? 3 : 1,
+                                           p->num_sms);
+    }
+    if (ws_floats > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws_floats);
     double* d_tau = nullptr;
     if (cudaMalloc(&d_tau, sizeof(double) * g.tau.size()) != cudaSuccess) {
       cudaGetLastError();
@@ -489,6 +497,22 @@ extern "C" srp_status srp_plan_stage_ms(srp_plan_t plan, float* ms, int* calls) 
     }
   }
   if (calls) *calls = plan->chunks_recorded;
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_status(srp_plan_t plan, void* stream) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int code = 0;
+  SRP_CUDA_TRY(cudaMemcpyAsync(&code, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SRP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (code != 0) {
+    SRP_CUDA_TRY(cudaMemsetAsync(plan->d_err, 0, sizeof(int), s));
+    SRP_CUDA_TRY(cudaStreamSynchronize(s));
+    return fail(SRP_ETIMEOUT, "a bounded wait inside a kernel ran out (code " + std::to_string(code) +
+                                  "); its maps are invalid");
+  }
   return SRP_OK;
 }
 

@@ -18,6 +18,9 @@ constexpr int BM = 128, BN = 128, BK = 8, PADS = 4;
 // With kslice < Kd the reduction is split: block z covers k-tiles
 // [z*kslice, (z+1)*kslice) and writes its partial map to Z + z*F*J without the argmax
 // (the partials are summed by split_reduce_argmax_kernel).
+// Frame tiles run fastest (blockIdx.x) so the CTAs in flight share the B (SRP matrix)
+// tiles through L2.
+template <bool SPLIT>
 __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
     const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ Z,
     unsigned long long* __restrict__ keys, int F, int J, int Kd, int kslice) {
@@ -25,14 +28,13 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
   __shared__ __align__(16) float Bs[2][BK][BN + PADS];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int lr = tid >> 1, lk = (tid & 1) * 4;
   const bool aok = (m0 + lr) < F;
   const bool bok = (n0 + lr) < J;
-  const int kbeg = blockIdx.z * kslice;
-  const int kend = min(Kd, kbeg + kslice);
-  const bool split = kslice < Kd;
-  if (split) Z += static_cast<size_t>(blockIdx.z) * F * J;
+  const int kbeg = SPLIT ? blockIdx.z * kslice : 0;
+  const int kend = SPLIT ? min(Kd, kbeg + kslice) : Kd;
+  if (SPLIT) Z += static_cast<size_t>(blockIdx.z) * F * J;
   const float4* Ap = reinterpret_cast<const float4*>(A + static_cast<size_t>(aok ? m0 + lr : 0) * Kd + kbeg + lk);
   const float4* Bp = reinterpret_cast<const float4*>(B + static_cast<size_t>(bok ? n0 + lr : 0) * Kd + kbeg + lk);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -88,18 +90,21 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
         const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
         if (n < J) {
           zr[n] = acc[i][j];
-          const unsigned long long kk = argmax_key(acc[i][j], n);
-          best = kk > best ? kk : best;
+          if (!SPLIT) {
+            const unsigned long long kk = argmax_key(acc[i][j], n);
+            best = kk > best ? kk : best;
+          }
         }
       }
     }
-    // reduce over the 16 threads sharing this row (one half-warp)
+    if (!SPLIT) {  // reduce over the 16 threads sharing this row (one half-warp)
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-      best = other > best ? other : best;
+      for (int o = 8; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        best = other > best ? other : best;
+      }
+      if (tx == 0 && m < F && best) atomicMax(keys + m, best);
     }
-    if (!split && tx == 0 && m < F && best) atomicMax(keys + m, best);
   }
 }
 
@@ -109,10 +114,10 @@ __global__ __launch_bounds__(256) void split_reduce_argmax_kernel(const float* _
                                                                   unsigned long long* __restrict__ keys,
                                                                   int F, int J) {
   __shared__ unsigned long long red[8];
-  const int f = blockIdx.y;
+  const int f = blockIdx.x;
   const size_t FJ = static_cast<size_t>(F) * J;
   unsigned long long best = 0ull;
-  for (int i = blockIdx.x * 1024 + threadIdx.x; i < min(J, (blockIdx.x + 1) * 1024); i += 256) {
+  for (int i = blockIdx.y * 1024 + threadIdx.x; i < min(J, (blockIdx.y + 1) * 1024); i += 256) {
     const size_t idx = static_cast<size_t>(f) * J + i;
     double acc = 0.0;
     for (int z = 0; z < nsplit; ++z) acc += static_cast<double>(part[z * FJ + idx]);
@@ -143,19 +148,24 @@ cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
   if (Kd % BK != 0) return cudaErrorInvalidValue;
   const int nsplit = sgemm_split_count(Kd);
   if (nsplit == 1) {
-    dim3 grid((J + BN - 1) / BN, (F + BM - 1) / BM, 1);
-    sgemm_nt_argmax_kernel<<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd, Kd);
+    dim3 grid((F + BM - 1) / BM, (J + BN - 1) / BN, 1);
+    sgemm_nt_argmax_kernel<false><<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd, Kd);
     return cudaGetLastError();
   }
   if (!split_ws) return cudaErrorInvalidValue;
   int kslice = (Kd / BK + nsplit - 1) / nsplit * BK;
   const int nz = (Kd + kslice - 1) / kslice;
-  dim3 grid((J + BN - 1) / BN, (F + BM - 1) / BM, nz);
-  sgemm_nt_argmax_kernel<<<grid, 256, 0, s>>>(A, B, split_ws, keys, F, J, Kd, kslice);
+  dim3 grid((F + BM - 1) / BM, (J + BN - 1) / BN, nz);
+  sgemm_nt_argmax_kernel<true><<<grid, 256, 0, s>>>(A, B, split_ws, keys, F, J, Kd, kslice);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 g2((J + 1023) / 1024, F);
-  split_reduce_argmax_kernel<<<g2, 256, 0, s>>>(split_ws, nz, Z, keys, F, J);
+  return launch_split_reduce(split_ws, nz, Z, keys, F, J, s);
+}
+
+cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long long* keys,
+                                int F, int J, cudaStream_t s) {
+  dim3 g2(F, (J + 1023) / 1024);
+  split_reduce_argmax_kernel<<<g2, 256, 0, s>>>(ws, nz, Z, keys, F, J);
   return cudaGetLastError();
 }
 

@@ -1,14 +1,385 @@
-// Tensor-core conv. FD-SRP GEMM (tcgen05).  Not built yet: the plan rejects tensor
-// precisions until this path exists.
+// conv. FD-SRP on the 5th-generation tensor cores (tcgen05): Z = A B^T (boxed Eq.
+// z_computed as one real product over [Re psi | Im psi] x [2cos | -2sin]), FP32
+// accumulation in TMEM, per-frame argmax (Eq. imax) fused into the epilogue.
+//
+// Persistent, warp-specialised kernel, one CTA per SM:
+//   warp 0      TMA producer: 128x64 tile of A (frames) and 256x64 tile of B (cells) per
+//               k-block into a 4-stage, 128-byte-swizzled shared-memory ring;
+//   warp 1      TMEM owner and single-thread MMA issuer: 4 x tcgen05.mma (M128 N256 K16)
+//               per k-block into one of two 128x256 FP32 accumulators (512 TMEM columns);
+//   warps 2-9   epilogue: two warps per TMEM lane quarter, each owning 128 of the 256
+//               columns of 32 frame rows.
+// The tensor cores round every accumulation step towards zero, which biases long sums
+// (about -2e-5 relative after 600 K=16 steps).  So a tile's reduction is cut into
+// chunks of KB_PER_CHUNK k-blocks: each chunk starts a fresh TMEM accumulator (the two
+// accumulators alternate, so the MMAs of chunk c+1 overlap the drain of chunk c), and the
+// epilogue adds every finished chunk into FP32 registers (round to nearest).  At the end
+// of the tile it stores the row segment and merges the row maximum with atomicMax.
+// Tiles run m-fastest so the CTAs in flight share the tiles of B (the SRP matrix).
+// Operands are F16 or BF16; the FP16 hi+lo mode runs three products per tile
+// (A_hi B_hi, A_hi B_lo, A_lo B_hi) as one longer reduction.  When the output tiles are
+// too few to fill the GPU the reduction is also split into slices written to a
+// workspace and summed in FP64 (split_reduce in k_conv_simt.cu).  Every mbarrier wait is
+// bounded (2 s); on a timeout the CTA records an error code, drains its own copies and
+// MMAs, frees its TMEM and returns.
 #include "srp_internal.h"
+#include "srp_device.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
 
 namespace srp {
 
-bool conv_tc_supported(int, int, int) { return false; }
+namespace {
+constexpr int TM = 128, TN = 256, TK = 64;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = TM * TK * 2;
+constexpr int B_BYTES = TN * TK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NEPI = 8;                       // epilogue warps
+constexpr int NTHREADS = 64 + 32 * NEPI;
+constexpr int EPI_COLS = TN / 2;              // columns per epilogue thread
+constexpr int KB_PER_CHUNK = 8;               // 32 K=16 steps per accumulator chunk
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr int MIN_KB_PER_SLICE = 32;
+}  // namespace
 
-cudaError_t launch_conv_tc(const void*, const void*, const void*, const void*, OpType, float*,
-                           unsigned long long*, int, int, int, int, cudaStream_t) {
-  return cudaErrorNotSupported;
+struct ConvTcParams {
+  int F, J;
+  int kb_per_seg, nseg;  // k-blocks of 64 per operand segment, number of segments
+  int nM, nN, nslices, kb_per_slice;
+  float* Z;  // maps [F][J] (nslices == 1) or partial maps [nslices][F][J]
+  unsigned long long* keys;
+  int* err;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                   const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+                   const ConvTcParams p, const uint32_t idesc) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sA = smem_u32(smem);
+  const uint32_t sB = sA + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 32 * NEPI);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int per_slice = p.nM * p.nN;
+  const int total = per_slice * p.nslices;
+  const int kb_total = p.kb_per_seg * p.nseg;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&tmA0);
+      prefetch_tmap(&tmB0);
+      if (p.nseg > 1) {
+        prefetch_tmap(&tmA1);
+        prefetch_tmap(&tmB1);
+      }
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t filled = 0, filled_par = 0;  // per stage: loaded at least once, its parity
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int slice = t / per_slice;
+        const int rem = t - slice * per_slice;
+        const int n = rem / p.nM, m = rem - (rem / p.nM) * p.nM;
+        const int kb0 = slice * p.kb_per_slice;
+        const int kb1 = min(kb_total, kb0 + p.kb_per_slice);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, 1, WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          const int seg = kb / p.kb_per_seg;
+          const int kx = (kb - seg * p.kb_per_seg) * TK;
+          const CUtensorMap* ta = seg == 2 ? &tmA1 : &tmA0;
+          const CUtensorMap* tb = seg == 1 ? &tmB1 : &tmB0;
+          mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
+          tma_load_2d(sA + stage * A_BYTES, ta, kx, m * TM, full_bar(stage));
+          tma_load_2d(sB + stage * B_BYTES, tb, kx, n * TN, full_bar(stage));
+          filled |= 1u << stage;
+          filled_par = (filled_par & ~(1u << stage)) | (phase << stage);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {  // let this CTA's own loads in flight land before it exits
+        volatile int dummy = 0;
+        for (int s = 0; s < STAGES; ++s)
+          if ((filled >> s) & 1u)
+            mbar_wait_bounded(full_bar(s), (filled_par >> s) & 1u, &dummy, 1, WAIT_NS / 10);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int gc = 0;  // chunks issued by this CTA (selects the accumulator and its phase)
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int slice = t / per_slice;
+        const int kb0 = slice * p.kb_per_slice;
+        const int kb1 = min(kb_total, kb0 + p.kb_per_slice);
+        for (int c0 = kb0; c0 < kb1 && ok; c0 += KB_PER_CHUNK, ++gc) {
+          const int acc = gc & 1;
+          const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
+          if (!mbar_wait_bounded(tempty_bar(acc), aph ^ 1u, abort_flag, 3, WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem_base + static_cast<uint32_t>(acc * TN);
+          const int c1 = min(kb1, c0 + KB_PER_CHUNK);
+          for (int kb = c0; kb < c1; ++kb) {
+            if (!mbar_wait_bounded(full_bar(stage), phase, abort_flag, 2, WAIT_NS)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t ad = sdesc_k128(sA + stage * A_BYTES);
+            const uint64_t bd = sdesc_k128(sB + stage * B_BYTES);
+#pragma unroll
+            for (int k = 0; k < TK / 16; ++k)
+              mma_f16(d, ad + static_cast<uint64_t>((k * 32) >> 4),
+                      bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
+                      (kb > c0 || k > 0) ? 1u : 0u);
+            mma_commit(empty_bar(stage));
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (ok) mma_commit(tfull_bar(acc));
+        }
+      }
+      // all MMAs this thread issued must finish before TMEM is released
+      mma_commit(drain_bar);
+      volatile int dummy = 0;
+      mbar_wait_bounded(drain_bar, 0u, &dummy, 1, WAIT_NS);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2..9)
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;       // which 128 of the 256 columns
+    const int row = q * 32 + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    int gc = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const int slice = t / per_slice;
+      const int rem = t - slice * per_slice;
+      const int n = rem / p.nM, m = rem - (rem / p.nM) * p.nM;
+      const int kb0 = slice * p.kb_per_slice;
+      const int kb1 = min(kb_total, kb0 + p.kb_per_slice);
+      float sum[EPI_COLS];
+#pragma unroll
+      for (int j = 0; j < EPI_COLS; ++j) sum[j] = 0.f;
+      for (int c0 = kb0; c0 < kb1; c0 += KB_PER_CHUNK, ++gc) {
+        const int acc = gc & 1;
+        const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
+        const bool got = mbar_wait_bounded(tfull_bar(acc), aph, abort_flag, 4, WAIT_NS);
+        if (!__all_sync(0xFFFFFFFFu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t col0 = tmem_base + static_cast<uint32_t>(acc * TN + half * EPI_COLS) + lane_off;
+#pragma unroll
+        for (int c = 0; c < EPI_COLS; c += 16) {
+          uint32_t r[16];
+          tmem_ld_32x32b_x16(col0 + static_cast<uint32_t>(c), r);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sum[c + j] += __uint_as_float(r[j]);
+        }
+        tc_fence_before();
+        mbar_arrive(tempty_bar(acc));
+      }
+      if (!ok) break;
+      const int f = m * TM + row;
+      if (f < p.F) {
+        const int n0 = n * TN + half * EPI_COLS;
+        float* zrow = p.Z + (static_cast<size_t>(slice) * p.F + f) * p.J + n0;
+        if ((p.J & 3) == 0 && n0 + EPI_COLS <= p.J) {
+          float4* dst = reinterpret_cast<float4*>(zrow);
+#pragma unroll
+          for (int j = 0; j < EPI_COLS / 4; ++j)
+            dst[j] = make_float4(sum[4 * j], sum[4 * j + 1], sum[4 * j + 2], sum[4 * j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < EPI_COLS; ++j)
+            if (n0 + j < p.J) zrow[j] = sum[j];
+        }
+        if (p.nslices == 1) {
+          float bv = -INFINITY;
+          int bi = -1;
+#pragma unroll
+          for (int j = 0; j < EPI_COLS; ++j)
+            if (n0 + j < p.J && (bi < 0 || sum[j] > bv)) {
+              bv = sum[j];
+              bi = n0 + j;
+            }
+          if (bi >= 0) atomicMax(p.keys + f, argmax_key(bv, bi));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 512);
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(p.err, *abort_flag);
+}
+
+// ------------------------------------------------------------------------------------
+namespace {
+std::mutex g_enc_mu;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t get_encode() {
+  std::lock_guard<std::mutex> lock(g_enc_mu);
+  if (g_encode) return cudaSuccess;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return cudaSuccess;
+}
+
+// 2-D K-major tensor map: inner dimension Kd (contiguous), outer `rows`, box 64 x box_rows,
+// 128-byte swizzle; out-of-range rows read as zero.
+cudaError_t make_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, uint64_t Kd,
+                     uint64_t rows, uint32_t box_rows) {
+  cuuint64_t dims[2] = {Kd, rows};
+  cuuint64_t strides[1] = {Kd * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(TK), box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace
+
+// Reduction slices for F frames: 1 while the output tiles fill the GPU; otherwise enough
+// slices (of at least MIN_KB_PER_SLICE k-blocks) to give every SM a tile.
+int conv_tc_slices(int F, int J, int Kd, int nseg, int num_sms) {
+  if (F <= 0) return 1;
+  const long long tiles = static_cast<long long>((F + TM - 1) / TM) * ((J + TN - 1) / TN);
+  if (tiles >= num_sms) return 1;
+  const int kb_total = Kd / TK * nseg;
+  const long long want = (num_sms + tiles - 1) / tiles;
+  const int cap = kb_total / MIN_KB_PER_SLICE > 1 ? kb_total / MIN_KB_PER_SLICE : 1;
+  return static_cast<int>(want < cap ? want : cap);
+}
+
+size_t conv_tc_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms) {
+  size_t need = 0;
+  for (int F = 1; F <= F_max; ++F) {
+    const int ns = conv_tc_slices(F, J, Kd, nseg, num_sms);
+    if (ns > 1) need = std::max(need, static_cast<size_t>(ns) * F * static_cast<size_t>(J));
+  }
+  return need;
+}
+
+bool conv_tc_supported(int, int, int Kd) { return Kd % TK == 0 && Kd / TK >= 1; }
+
+cudaError_t launch_conv_tc(const void* A, const void* A_lo, const void* B, const void* B_lo,
+                           OpType t, float* Z, unsigned long long* keys, int F, int J, int Kd,
+                           int num_sms, float* split_ws, int* err, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  if (Kd % TK != 0) return cudaErrorInvalidValue;
+  cudaError_t e = get_encode();
+  if (e != cudaSuccess) return e;
+  const bool split3 = t == OpType::F16X2;
+  const CUtensorMapDataType dt = t == OpType::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMap mA0, mA1, mB0, mB1;
+  if ((e = make_map(&mA0, A, dt, Kd, F, TM)) != cudaSuccess) return e;
+  if ((e = make_map(&mB0, B, dt, Kd, J, TN)) != cudaSuccess) return e;
+  if (split3) {
+    if ((e = make_map(&mA1, A_lo, dt, Kd, F, TM)) != cudaSuccess) return e;
+    if ((e = make_map(&mB1, B_lo, dt, Kd, J, TN)) != cudaSuccess) return e;
+  } else {
+    mA1 = mA0;
+    mB1 = mB0;
+  }
+  ConvTcParams p;
+  p.F = F;
+  p.J = J;
+  p.kb_per_seg = Kd / TK;
+  p.nseg = split3 ? 3 : 1;
+  p.nM = (F + TM - 1) / TM;
+  p.nN = (J + TN - 1) / TN;
+  p.nslices = conv_tc_slices(F, J, Kd, p.nseg, num_sms);
+  const int kb_total = p.kb_per_seg * p.nseg;
+  p.kb_per_slice = (kb_total + p.nslices - 1) / p.nslices;
+  p.nslices = (kb_total + p.kb_per_slice - 1) / p.kb_per_slice;
+  p.keys = keys;
+  p.err = err;
+  if (p.nslices > 1) {
+    if (!split_ws) return cudaErrorInvalidValue;
+    p.Z = split_ws;
+  } else {
+    p.Z = Z;
+  }
+  const uint32_t idesc = tc::idesc_f16(t == OpType::BF16 ? 1u : 0u, TM, TN);
+  const int total = p.nM * p.nN * p.nslices;
+  const int grid = total < num_sms ? total : num_sms;
+  e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  conv_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(mA0, mA1, mB0, mB1, p, idesc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || p.nslices == 1) return e;
+  return launch_split_reduce(split_ws, p.nslices, Z, keys, F, J, s);
 }
 
 }  // namespace srp

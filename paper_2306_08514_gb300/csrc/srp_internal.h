@@ -76,12 +76,20 @@ int sgemm_split_count(int Kd);
 cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
                                    unsigned long long* keys, int F, int J, int Kd,
                                    float* split_ws, cudaStream_t s);
-// Tensor-core conv GEMM (tcgen05), fused argmax keys.  nseg = 1 (single precision
-// operand) or 3 (hi*hi + hi*lo + lo*hi).
+// Sums nz partial maps [nz][F][J] in FP64 into Z and merges the argmax keys.
+cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long long* keys,
+                                int F, int J, cudaStream_t s);
+// Tensor-core conv GEMM (tcgen05), fused argmax keys.  F16/BF16 operands, or F16 hi+lo
+// (three products, nseg = 3).  When the output tiles do not fill the GPU the reduction
+// is split into conv_tc_slices(...) slices written to split_ws [slices][F][J] (at most
+// conv_tc_workspace_floats(...) floats for any F <= F_max).  A bounded wait that runs
+// out stores a non-zero code in *err.
 cudaError_t launch_conv_tc(const void* A, const void* A_lo, const void* B, const void* B_lo,
                            OpType t, float* Z, unsigned long long* keys, int F, int J, int Kd,
-                           int num_sms, cudaStream_t s);
+                           int num_sms, float* split_ws, int* err, cudaStream_t s);
 bool conv_tc_supported(int F_max, int J, int Kd);
+int conv_tc_slices(int F, int J, int Kd, int nseg, int num_sms);
+size_t conv_tc_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms);
 
 // SLRI: U[F][R] = xi Lambda_fat^T ; Z = U Lambda_tall^T (fused argmax keys).
 cudaError_t launch_slri_fat(const float* xi, const float* fat, float* U, int F, int L, int R,
@@ -133,6 +141,7 @@ struct srp_plan_s {
   float* d_xi = nullptr;
   float* d_U = nullptr;
   unsigned long long* d_keys = nullptr;
+  int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
   // staging for srp_map_host
   float* d_stage_frames = nullptr;
   float* d_stage_maps = nullptr;

@@ -85,6 +85,24 @@ def test_conv_fp32_square4(S, sq):
     assert check_argmax(z, am, zo) >= 0.99
 
 
+# Tensor-core conv bounds: FP16 hi+lo meets the FP32 bar; single FP16 / BF16 operands
+# carry a relative rounding of 2^-11 / 2^-8 per operand, i.e. about sqrt(2/3) u of map
+# error for sums of many terms: stated bounds 2e-3 (FP16) and 1.5e-2 (BF16).
+TC_CASES = [("fp16x3", TOL), ("fp16", 2e-3), ("bf16", 1.5e-2)]
+
+
+@pytest.mark.parametrize("prec,tol", TC_CASES)
+def test_conv_tensor_core_square4(S, sq, prec, tol):
+    w, psi, dt, *_ = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="conv", precision=prec,
+                  max_frames=64)
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z, zo).max() <= tol
+    check_argmax(z, am, zo)
+
+
 @pytest.mark.parametrize("rank", [8, 16])
 def test_slri_square4(S, sq, rank):
     w, psi, dt, lags, perm, xi_o = sq
@@ -153,6 +171,12 @@ def test_uca8_small_all_methods(S, uca_small):
     zo = O.srp_conv(psi, dt, w["fs"])
     assert R.per_frame_rel(z, zo).max() <= TOL
     check_argmax(z, am, zo)
+    for prec, tol in TC_CASES:  # ragged frame tile (70 = 64 + 6) and cell tile (4616 cells)
+        plan = S.Plan(*args, method="conv", precision=prec, max_frames=64)
+        z, am = _run(plan, w["frames"])
+        plan.status()
+        assert R.per_frame_rel(z, zo).max() <= tol, prec
+        check_argmax(z, am, zo)
     tall, fat, s = R.slri(name, 16, F, sub)
     z, am = _run(S.Plan(*args, method="slri", rank=16, max_frames=64), w["frames"])
     zo = O.srp_slri(tall, fat, xi_o)
@@ -237,6 +261,13 @@ def test_largest_fft_and_most_mics_conv(S):
     zo = O.srp_conv(psi, dt, w["fs"])
     assert R.per_frame_rel(z, zo).max() <= TOL
     check_argmax(z, am, zo)
+    # tensor cores, FP16 hi+lo: 3 output tiles, so the reduction is split into slices summed in FP64
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="conv",
+                  precision="fp16x3", max_frames=4)
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    check_argmax(z, am, zo)
 
 
 # ------------------------------------------------------------------ full-size uca8 (bench config)
@@ -260,6 +291,12 @@ def test_uca8_full_size_sampled(S, uca_full):
     # conv, FP32, on all J for the sampled frames
     z, am = _run(S.Plan(*args, method="conv", max_frames=F), frames)
     zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z[fsel], zo).max() <= TOL
+    check_argmax(z[fsel], am[fsel], zo)
+    # conv on the tensor cores, FP16 hi+lo, in the benchmark's launch configuration
+    plan = S.Plan(*args, method="conv", precision="fp16x3", max_frames=F)
+    z, am = _run(plan, frames)
+    plan.status()
     assert R.per_frame_rel(z[fsel], zo).max() <= TOL
     check_argmax(z[fsel], am[fsel], zo)
     # SLRI, R = 16
