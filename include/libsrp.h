@@ -10,6 +10,8 @@
  *   SLRI-SRP       xi = iFFT-sampled TD GCC             (Eq. xi_p_ifft, n_prime)
  *                  z = Lambda_tall (Lambda_fat xi)       (boxed Eq. z_circlr_computed)
  *   SSPI-SRP       z = Lambda_sp xi                      (boxed Eq. z_circsp_computed)
+ *   SI-SRP         z = Lambda xi                         (boxed Eq. z_circ_computed)
+ *   conv. TD-SRP   z(i) = sum_p xi_p(round(Delta t_p(i)/T))  (Eq. TD_SRP)
  *   estimate       i_max = argmax_i z(i)                 (Eq. imax)
  *
  * Conventions used by every entry point
@@ -55,15 +57,22 @@ typedef enum {
 typedef enum {
   SRP_CONV = 0,  /* conv. FD-SRP, Sec. II-D, boxed Eq. z_computed */
   SRP_SLRI = 1,  /* SLRI-SRP, Sec. IV-A, boxed Eq. z_circlr_computed */
-  SRP_SSPI = 2   /* SSPI-SRP, Sec. IV-A, boxed Eq. z_circsp_computed */
+  SRP_SSPI = 2,  /* SSPI-SRP, Sec. IV-A, boxed Eq. z_circsp_computed */
+  SRP_SI = 3,    /* SI-SRP, Sec. III-B, boxed Eq. z_circ_computed (full sinc Lambda) */
+  SRP_TD = 4     /* conv. TD-SRP, Sec. II-D, Eq. TD_SRP (nearest-sample GCC lookup) */
 } srp_method;
 
+/* Arithmetic of the map contraction (the front end -- DFT, PHAT, iFFT sampling -- is FP32
+ * in every case).  The tensor-core precisions run every method on tcgen05 GEMMs:
+ * conv over the SRP matrix; SI, TD and SSPI over a dense [J][L] interpolation operand
+ * (SSPI and TD skip the all-zero 64-column blocks of each 256-cell tile); SLRI's
+ * Lambda_tall product (Lambda_fat xi stays FP32). */
 typedef enum {
   SRP_FP32 = 0,    /* FP32 operands, FP32 FFMA on CUDA cores */
-  SRP_BF16 = 1,    /* conv only: BF16 tensor-core GEMM, FP32 accumulate */
-  SRP_FP16 = 2,    /* conv only: FP16 tensor-core GEMM, FP32 accumulate */
-  SRP_FP16X3 = 4   /* conv only: FP16 hi+lo split operands, 3 tensor-core products
-                      (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+  SRP_BF16 = 1,    /* BF16 tensor-core GEMM, FP32 accumulate */
+  SRP_FP16 = 2,    /* FP16 tensor-core GEMM, FP32 accumulate */
+  SRP_FP16X3 = 4   /* FP16 hi+lo split operands, 3 tensor-core products
+                      (hi*hi + hi*lo + lo*hi), FP32 accumulate: FP32-class maps */
 } srp_precision;
 
 typedef enum {
@@ -88,7 +97,7 @@ typedef struct {
   int rank;                 /* SLRI: R_Lambda of Eq. min_Lambda_lr, 1..64 and <= min(J, L) */
   double taps_per_loc_pair; /* SSPI: t, Q_Lambda = round(t * J * P) non-zeros kept by
                                Eq. min_Lambda_sp; 0 < t and Q_Lambda <= J * L */
-  int precision;            /* srp_precision (SLRI/SSPI: SRP_FP32 only) */
+  int precision;            /* srp_precision */
   int max_frames;           /* frames processed per internal launch (scratch sizing),
                                1..65536; larger calls are processed in chunks */
 } srp_plan_desc;
@@ -115,12 +124,17 @@ typedef struct {
  *             Lambda_fat = V_R^T, Lambda_tall = Lambda V_R, stored FP32;
  *   SRP_SSPI: the Q_Lambda largest-magnitude entries of Lambda (Eq. min_Lambda_sp),
  *             magnitudes quantised to multiples of 2^-40 and ties broken by ascending
- *             (i, p, n), stored as CSR rows (FP32 values, int32 sample indices).
+ *             (i, p, n), stored as CSR rows (FP32 values, int32 sample indices) for the
+ *             FP32 gather, or densely as [J][L] for the tensor cores;
+ *   SRP_SI:   Lambda itself (Eq. Lambda_p, sinc evaluated in FP64), dense [J][L];
+ *   SRP_TD:   the one-hot Lambda of conv. TD-SRP, 1 at n = round(Delta t_p(i)/T) with
+ *             halves rounded away from zero (needs n_aux >= 1), dense [J][L].
  * desc:   host, read only; the arrays are copied.
  * stream: stream for the uploads; the call returns after they complete.
  * out:    receives the plan handle (NULL on failure).
- * Errors: SRP_EINVAL (bad desc, including N_p >= K), SRP_EUNSUPPORTED (method /
- * precision combination or size beyond this build), SRP_ENOMEM, SRP_ECUDA.
+ * Errors: SRP_EINVAL (bad desc, including N_p >= K), SRP_EUNSUPPORTED (size beyond
+ * this build: SLRI with L > 768, the FP32 SSPI gather with L > 1700, a device operand
+ * above 200 GB), SRP_ENOMEM, SRP_ECUDA.
  */
 srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out);
 
@@ -157,10 +171,10 @@ srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, float* maps
 /*
  * srp_gcc_samples -- the sampling stage alone (Eq. xi_p_ifft, n_prime, xi_single):
  * PHAT cross-spectra of every pair, iFFT of the two-sided spectrum (unnormalised,
- * length N), and the 2N_p+1 samples at lags -N_p..N_p.  Valid for SLRI and SSPI plans.
+ * length N), and the 2N_p+1 samples at lags -N_p..N_p.  Valid for every plan but conv.
  * frames: device float [F][M][N]; xi: device float [F][L], written (pair-major,
- * ascending lag).  Asynchronous on `stream`.  Errors: SRP_EINVAL, SRP_EUNSUPPORTED
- * (conv plan), SRP_ECUDA.
+ * ascending lag).  Valid for every plan but conv.  Asynchronous on `stream`.
+ * Errors: SRP_EINVAL, SRP_EUNSUPPORTED (conv plan), SRP_ECUDA.
  */
 srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int F, float* xi, void* stream);
 

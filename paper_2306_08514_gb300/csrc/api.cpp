@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 namespace srp {
 
@@ -41,20 +42,12 @@ srp_status validate(const srp_plan_desc* d) {
     if (!std::isfinite(d->mic_xyz[i])) return fail(SRP_EINVAL, "mic_xyz has a non-finite value");
   for (long long i = 0; i < 3ll * d->J; ++i)
     if (!std::isfinite(d->grid_xyz[i])) return fail(SRP_EINVAL, "grid_xyz has a non-finite value");
-  switch (d->method) {
-    case SRP_CONV:
-      if (d->precision != SRP_FP32 && d->precision != SRP_BF16 && d->precision != SRP_FP16 &&
-          d->precision != SRP_FP16X3)
-        return fail(SRP_EINVAL, "unknown precision");
-      break;
-    case SRP_SLRI:
-    case SRP_SSPI:
-      if (d->precision != SRP_FP32)
-        return fail(SRP_EUNSUPPORTED, "SLRI/SSPI run in SRP_FP32 only");
-      break;
-    default:
-      return fail(SRP_EINVAL, "unknown method");
-  }
+  if (d->method < SRP_CONV || d->method > SRP_TD) return fail(SRP_EINVAL, "unknown method");
+  if (d->precision != SRP_FP32 && d->precision != SRP_BF16 && d->precision != SRP_FP16 &&
+      d->precision != SRP_FP16X3)
+    return fail(SRP_EINVAL, "unknown precision");
+  if (d->method == SRP_TD && d->n_aux < 1)
+    return fail(SRP_EINVAL, "conv. TD-SRP needs n_aux >= 1 (the rounded lag must be sampled)");
   return SRP_OK;
 }
 
@@ -79,7 +72,7 @@ void free_plan(srp_plan_s* p) {
   void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
                   p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
-                  p->d_stage_arg};
+                  p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -108,6 +101,10 @@ void free_plan(srp_plan_s* p) {
 
 size_t op_bytes(OpType t) { return t == OpType::F32 ? 4 : 2; }
 
+// Contraction depth of the tensor-core SLRI product (R <= 64 padded to one k-block); also
+// the multiple that pads L for the dense interpolation operands.
+constexpr int kSlriKd = 64;
+
 // One chunk of at most Fmax frames through the whole path.
 constexpr int kMaxChunkEvents = 4096;
 
@@ -129,6 +126,30 @@ srp_status mark(srp_plan_s* p, int stage, cudaStream_t s) {
     if (_st != SRP_OK) return _st;                 \
   } while (0)
 
+// Z = A B^T with the plan's operand type: FP32 FFMA (SIMT) or the tensor cores.
+cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void* B, const void* B_lo,
+                     int Kd, const int* kb_ptr, const int* kb_idx, int F, float* maps, cudaStream_t s) {
+  if (p->op == OpType::F32)
+    return launch_sgemm_nt_argmax(static_cast<const float*>(A), static_cast<const float*>(B), maps,
+                                  p->d_keys, F, p->g.J, Kd, p->d_split, s);
+  TcGemm tg;
+  tg.A = A;
+  tg.A_lo = A_lo;
+  tg.B = B;
+  tg.B_lo = B_lo;
+  tg.t = p->op;
+  tg.F = F;
+  tg.J = p->g.J;
+  tg.Kd = Kd;
+  tg.kb_ptr = kb_ptr;
+  tg.kb_idx = kb_idx;
+  tg.Z = maps;
+  tg.keys = p->d_keys;
+  tg.split_ws = p->d_split;
+  tg.err = p->d_err;
+  return launch_tc_gemm(tg, p->num_sms, s);
+}
+
 srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int* argmax,
                      cudaStream_t s) {
   const Geometry& g = p->g;
@@ -141,15 +162,8 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       SRP_CUDA_TRY(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
                                     p->d_A_lo, s));
       SRP_MARK(p, 2, s);
-      const int Kd = g.P * g.N;
-      if (p->op == OpType::F32) {
-        SRP_CUDA_TRY(launch_sgemm_nt_argmax(static_cast<const float*>(p->d_A),
-                                            static_cast<const float*>(p->d_H), maps, p->d_keys,
-                                            F, g.J, Kd, p->d_split, s));
-      } else {
-        SRP_CUDA_TRY(launch_conv_tc(p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, p->op, maps, p->d_keys,
-                                    F, g.J, Kd, p->num_sms, p->d_split, p->d_err, s));
-      }
+      SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, nullptr, nullptr,
+                            F, maps, s));
       break;
     }
     case SRP_SLRI: {
@@ -158,15 +172,30 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       SRP_MARK(p, 2, s);
       const int Rp = (p->R + 7) / 8 * 8;
       SRP_CUDA_TRY(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
-      SRP_CUDA_TRY(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
+      if (p->op == OpType::F32) {
+        SRP_CUDA_TRY(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
+      } else {
+        SRP_CUDA_TRY(launch_pack16(p->d_U, F, Rp, kSlriKd, std::ldexp(1.f, -p->slri_exp), p->op,
+                                   p->d_A, p->d_A_lo, s));
+        SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, kSlriKd, nullptr, nullptr,
+                              F, maps, s));
+      }
       break;
     }
-    case SRP_SSPI: {
+    case SRP_SSPI:
+    case SRP_SI:
+    case SRP_TD: {
       SRP_CUDA_TRY(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
                                       g.L, p->d_twiddle, p->d_xi, s));
       SRP_MARK(p, 2, s);
-      SRP_CUDA_TRY(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
-                               p->num_sms, s));
+      if (p->desc.method == SRP_SSPI && p->op == OpType::F32) {
+        SRP_CUDA_TRY(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
+                                 p->num_sms, s));
+      } else {
+        SRP_CUDA_TRY(launch_pack16(p->d_xi, F, g.L, p->Lpad, 1.f, p->op, p->d_A, p->d_A_lo, s));
+        SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, p->Lpad, p->d_kb_ptr,
+                              p->d_kb_idx, F, maps, s));
+      }
       break;
     }
     default:
@@ -220,26 +249,33 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       delete p;
       return fail(SRP_EINVAL, "taps_per_loc_pair gives Q_Lambda outside 1..J*L");
     }
-    if (g.L * 33 * 4 > 220 * 1024) {
+    if (desc->precision == SRP_FP32 && g.L * 33 * 4 > 220 * 1024) {
       delete p;
-      return fail(SRP_EUNSUPPORTED, "SSPI supports L <= 1700 in this build");
+      return fail(SRP_EUNSUPPORTED,
+                  "the FP32 SSPI gather supports L <= 1700 (use a tensor-core precision)");
     }
     p->nnz = static_cast<long long>(nz);
   }
+  p->op = desc->precision == SRP_FP32 ? OpType::F32
+          : desc->precision == SRP_BF16 ? OpType::BF16
+          : desc->precision == SRP_FP16 ? OpType::F16
+                                        : OpType::F16X2;
+  p->Lpad = (g.L + kSlriKd - 1) / kSlriKd * kSlriKd;
+  if (desc->method == SRP_SI || desc->method == SRP_TD ||
+      (desc->method == SRP_SSPI && p->op != OpType::F32)) {
+    const double bbytes = static_cast<double>(g.J) * p->Lpad * op_bytes(p->op) *
+                          (p->op == OpType::F16X2 ? 2 : 1);
+    if (bbytes > 200e9) {
+      delete p;
+      return fail(SRP_EUNSUPPORTED, "dense interpolation operand would need more than 200 GB");
+    }
+  }
   if (desc->method == SRP_CONV) {
-    p->op = desc->precision == SRP_FP32 ? OpType::F32
-            : desc->precision == SRP_BF16 ? OpType::BF16
-            : desc->precision == SRP_FP16 ? OpType::F16
-                                          : OpType::F16X2;
     const double hbytes = static_cast<double>(g.J) * g.P * g.N * op_bytes(p->op) *
                           (p->op == OpType::F16X2 ? 2 : 1);
     if (hbytes > 200e9) {
       delete p;
       return fail(SRP_EUNSUPPORTED, "SRP matrix would need more than 200 GB");
-    }
-    if (p->op != OpType::F32 && !conv_tc_supported(p->Fmax, g.J, g.P * g.N)) {
-      delete p;
-      return fail(SRP_EUNSUPPORTED, "tensor-core conv path unavailable for these sizes");
     }
   }
 
@@ -284,7 +320,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       const int nsplit = sgemm_split_count(static_cast<int>(Kd));
       if (nsplit > 1) ws_floats = static_cast<size_t>(nsplit) * F * g.J;
     } else {
-      ws_floats = conv_tc_workspace_floats(p->Fmax, g.J, static_cast<int>(Kd), split ? 3 : 1,
+      ws_floats = tc_gemm_workspace_floats(p->Fmax, g.J, static_cast<int>(Kd), split ? 3 : 1,
                                            p->num_sms);
     }
     if (ws_floats > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws_floats);
@@ -307,6 +343,8 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     }
   } else {
     SRP_ALLOC(p, p->d_xi, sizeof(float) * F * g.L);
+    const size_t eb = op_bytes(p->op);
+    const bool split = p->op == OpType::F16X2;
     if (desc->method == SRP_SLRI) {
       std::vector<float> tall, fat;
       srp_status fst = fit_low_rank(g, p->R, tall, fat, p->sigma);
@@ -320,23 +358,131 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       SRP_ALLOC(p, p->d_U, sizeof(float) * F * Rp);
       SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tall, tall.data(), sizeof(float) * tall.size(), cudaMemcpyHostToDevice, s));
       SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_fat, fat.data(), sizeof(float) * fat.size(), cudaMemcpyHostToDevice, s));
+      if (p->op != OpType::F32) {
+        // u = Lambda_fat xi has |u_r| <= ||xi||_2 <= 2K sqrt(P) (Parseval over the 2K lags of
+        // each pair, |psi| <= 1): scale u by 2^-e into the FP16 range and Lambda_tall by 2^e.
+        const double ubound = 2.0 * g.K * std::sqrt(static_cast<double>(g.P));
+        p->slri_exp = std::max(0, static_cast<int>(std::ceil(std::log2(ubound / 16384.0))));
+        SRP_ALLOC(p, p->d_B, static_cast<size_t>(g.J) * kSlriKd * eb);
+        if (split) SRP_ALLOC(p, p->d_B_lo, static_cast<size_t>(g.J) * kSlriKd * eb);
+        SRP_ALLOC(p, p->d_A, F * kSlriKd * eb);
+        if (split) SRP_ALLOC(p, p->d_A_lo, F * kSlriKd * eb);
+        SRP_PLAN_CUDA(p, launch_pack16(p->d_tall, g.J, Rp, kSlriKd, std::ldexp(1.f, p->slri_exp),
+                                       p->op, p->d_B, p->d_B_lo, s));
+        const size_t ws = tc_gemm_workspace_floats(p->Fmax, g.J, kSlriKd, split ? 3 : 1, p->num_sms);
+        if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
+      }
       SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
     } else {
-      srp_status fst = fit_sparse(g, p->nnz, p->h_row_ptr, p->h_col, p->h_val, p->tied);
-      if (fst != SRP_OK) {
-        free_plan(p);
-        return fst;
+      const int Lpad = p->Lpad;
+      const int kb_n = Lpad / kSlriKd;
+      const int tile = tc_gemm_cell_tile();
+      const int ntiles = (g.J + tile - 1) / tile;
+      std::vector<int> kb_ptr, kb_idx;  // non-zero k-blocks of each cell tile (block-sparse B)
+      auto add_lists = [&](const std::function<void(int, std::vector<char>&)>& mark_cells) {
+        kb_ptr.assign(1, 0);
+        std::vector<char> used(kb_n);
+        for (int n = 0; n < ntiles; ++n) {
+          std::fill(used.begin(), used.end(), 0);
+          for (int i = n * tile; i < std::min(g.J, (n + 1) * tile); ++i) mark_cells(i, used);
+          for (int k = 0; k < kb_n; ++k)
+            if (used[k]) kb_idx.push_back(k);
+          kb_ptr.push_back(static_cast<int>(kb_idx.size()));
+        }
+      };
+      if (desc->method == SRP_SSPI) {
+        srp_status fst = fit_sparse(g, p->nnz, p->h_row_ptr, p->h_col, p->h_val, p->tied);
+        if (fst != SRP_OK) {
+          free_plan(p);
+          return fst;
+        }
+        std::vector<int2> taps(static_cast<size_t>(p->nnz));
+        for (long long t = 0; t < p->nnz; ++t) {
+          int vb;
+          std::memcpy(&vb, &p->h_val[t], 4);
+          taps[t] = make_int2(p->h_col[t], vb);
+        }
+        SRP_ALLOC(p, p->d_row_ptr, sizeof(long long) * (g.J + 1));
+        SRP_ALLOC(p, p->d_taps, sizeof(int2) * taps.size());
+        SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_row_ptr, p->h_row_ptr.data(), sizeof(long long) * (g.J + 1), cudaMemcpyHostToDevice, s));
+        SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_taps, taps.data(), sizeof(int2) * taps.size(), cudaMemcpyHostToDevice, s));
+        if (p->op != OpType::F32) {
+          SRP_ALLOC(p, p->d_B, static_cast<size_t>(g.J) * Lpad * eb);
+          if (split) SRP_ALLOC(p, p->d_B_lo, static_cast<size_t>(g.J) * Lpad * eb);
+          SRP_PLAN_CUDA(p, launch_csr_to_dense(p->d_row_ptr, p->d_taps, g.J, Lpad, p->op, p->d_B,
+                                               p->d_B_lo, s));
+          add_lists([&](int i, std::vector<char>& used) {
+            for (long long t = p->h_row_ptr[i]; t < p->h_row_ptr[i + 1]; ++t)
+              used[p->h_col[t] / kSlriKd] = 1;
+          });
+          SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
+          cudaFree(p->d_row_ptr);  // the dense operand replaces the tap list on the device
+          cudaFree(p->d_taps);
+          p->device_bytes -= sizeof(long long) * (g.J + 1) + sizeof(int2) * taps.size();
+          p->d_row_ptr = nullptr;
+          p->d_taps = nullptr;
+        }
+      } else {
+        // SI-SRP (Eq. Lambda) or conv. TD-SRP (Eq. TD_SRP): dense operand from the TDOAs.
+        std::vector<int> col_pair(g.L), col_lag(g.L);
+        for (int q = 0; q < g.P; ++q)
+          for (int n = -g.Np[q]; n <= g.Np[q]; ++n) {
+            col_pair[g.off[q] + n + g.Np[q]] = q;
+            col_lag[g.off[q] + n + g.Np[q]] = n;
+          }
+        SRP_ALLOC(p, p->d_B, static_cast<size_t>(g.J) * Lpad * eb);
+        if (split) SRP_ALLOC(p, p->d_B_lo, static_cast<size_t>(g.J) * Lpad * eb);
+        double* d_tau = nullptr;
+        int* d_cols = nullptr;
+        cudaError_t e = cudaMalloc(&d_tau, sizeof(double) * g.tau.size());
+        if (e == cudaSuccess) e = cudaMalloc(&d_cols, sizeof(int) * 2 * g.L);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_tau, g.tau.data(), sizeof(double) * g.tau.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_cols, col_pair.data(), sizeof(int) * g.L, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_cols + g.L, col_lag.data(), sizeof(int) * g.L, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+          e = launch_interp_dense(d_tau, g.J, g.P, d_cols, d_cols + g.L, g.L, Lpad,
+                                  desc->method == SRP_TD, p->op, p->d_B, p->d_B_lo, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (d_tau) cudaFree(d_tau);
+        if (d_cols) cudaFree(d_cols);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          set_error(std::string("interpolation operand: ") + cudaGetErrorString(e));
+          free_plan(p);
+          return SRP_ECUDA;
+        }
+        if (desc->method == SRP_TD && p->op != OpType::F32) {
+          add_lists([&](int i, std::vector<char>& used) {
+            for (int q = 0; q < g.P; ++q) {
+              const double t = g.tau[static_cast<size_t>(i) * g.P + q];
+              const double r = t < 0.0 ? -std::floor(-t + 0.5) : std::floor(t + 0.5);
+              used[(g.off[q] + static_cast<int>(r) + g.Np[q]) / kSlriKd] = 1;
+            }
+          });
+        }
       }
-      std::vector<int2> taps(static_cast<size_t>(p->nnz));
-      for (long long t = 0; t < p->nnz; ++t) {
-        int vb;
-        std::memcpy(&vb, &p->h_val[t], 4);
-        taps[t] = make_int2(p->h_col[t], vb);
+      if (!kb_ptr.empty()) {
+        SRP_ALLOC(p, p->d_kb_ptr, sizeof(int) * kb_ptr.size());
+        SRP_ALLOC(p, p->d_kb_idx, sizeof(int) * std::max<size_t>(1, kb_idx.size()));
+        SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_kb_ptr, kb_ptr.data(), sizeof(int) * kb_ptr.size(), cudaMemcpyHostToDevice, s));
+        if (!kb_idx.empty())
+          SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_kb_idx, kb_idx.data(), sizeof(int) * kb_idx.size(), cudaMemcpyHostToDevice, s));
       }
-      SRP_ALLOC(p, p->d_row_ptr, sizeof(long long) * (g.J + 1));
-      SRP_ALLOC(p, p->d_taps, sizeof(int2) * taps.size());
-      SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_row_ptr, p->h_row_ptr.data(), sizeof(long long) * (g.J + 1), cudaMemcpyHostToDevice, s));
-      SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_taps, taps.data(), sizeof(int2) * taps.size(), cudaMemcpyHostToDevice, s));
+      if (desc->method != SRP_SSPI || p->op != OpType::F32) {
+        SRP_ALLOC(p, p->d_A, F * Lpad * eb);
+        if (split) SRP_ALLOC(p, p->d_A_lo, F * Lpad * eb);
+        size_t ws = 0;
+        if (p->op == OpType::F32) {
+          const int nsplit = sgemm_split_count(Lpad);
+          if (nsplit > 1) ws = static_cast<size_t>(nsplit) * F * g.J;
+        } else if (kb_ptr.empty()) {
+          ws = tc_gemm_workspace_floats(p->Fmax, g.J, Lpad, split ? 3 : 1, p->num_sms);
+        }
+        if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
+      }
       SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
     }
   }

@@ -1,27 +1,34 @@
-// conv. FD-SRP on the 5th-generation tensor cores (tcgen05): Z = A B^T (boxed Eq.
-// z_computed as one real product over [Re psi | Im psi] x [2cos | -2sin]), FP32
-// accumulation in TMEM, per-frame argmax (Eq. imax) fused into the epilogue.
+// The map contractions on the 5th-generation tensor cores (tcgen05):
+//
+//   Z[F][J] = A B^T,   A [F][Kd] (one row per frame), B [J][Kd] (one row per cell),
+//
+// 16-bit operands (F16 or BF16) with FP32 accumulation in TMEM and the per-frame argmax
+// (Eq. imax) fused into the epilogue.  It serves every method:
+//   conv. FD-SRP  A = [Re psi | Im psi] per pair, B = [2cos | -2sin] (boxed Eq. z_computed);
+//   SSPI-SRP      A = xi, B = Lambda_sp stored densely; zero k-blocks of a cell tile are
+//                 skipped through a per-tile k-block list (boxed Eq. z_circsp_computed);
+//   SLRI-SRP      A = u = Lambda_fat xi, B = Lambda_tall (boxed Eq. z_circlr_computed).
+// The FP16 hi+lo mode runs three products (A_hi B_hi, A_hi B_lo, A_lo B_hi) as one longer
+// reduction, which carries about 22 significant bits per operand.
 //
 // Persistent, warp-specialised kernel, one CTA per SM:
-//   warp 0      TMA producer: 128x64 tile of A (frames) and 256x64 tile of B (cells) per
-//               k-block into a 4-stage, 128-byte-swizzled shared-memory ring;
+//   warp 0      TMA producer: 128x64 tile of A and 256x64 tile of B per k-block into a
+//               4-stage, 128-byte-swizzled shared-memory ring;
 //   warp 1      TMEM owner and single-thread MMA issuer: 4 x tcgen05.mma (M128 N256 K16)
 //               per k-block into one of two 128x256 FP32 accumulators (512 TMEM columns);
 //   warps 2-9   epilogue: two warps per TMEM lane quarter, each owning 128 of the 256
-//               columns of 32 frame rows.
+//               columns of 32 frame rows; results leave through swizzled shared-memory
+//               boxes and TMA tensor stores (coalesced, asynchronous).
 // The tensor cores round every accumulation step towards zero, which biases long sums
 // (about -2e-5 relative after 600 K=16 steps).  So a tile's reduction is cut into
 // chunks of KB_PER_CHUNK k-blocks: each chunk starts a fresh TMEM accumulator (the two
 // accumulators alternate, so the MMAs of chunk c+1 overlap the drain of chunk c), and the
-// epilogue adds every finished chunk into FP32 registers (round to nearest).  At the end
-// of the tile it stores the row segment and merges the row maximum with atomicMax.
-// Tiles run m-fastest so the CTAs in flight share the tiles of B (the SRP matrix).
-// Operands are F16 or BF16; the FP16 hi+lo mode runs three products per tile
-// (A_hi B_hi, A_hi B_lo, A_lo B_hi) as one longer reduction.  When the output tiles are
-// too few to fill the GPU the reduction is also split into slices written to a
-// workspace and summed in FP64 (split_reduce in k_conv_simt.cu).  Every mbarrier wait is
-// bounded (2 s); on a timeout the CTA records an error code, drains its own copies and
-// MMAs, frees its TMEM and returns.
+// epilogue adds every finished chunk into FP32 registers (round to nearest).
+// Tiles run m-fastest so the CTAs in flight share the tiles of B.  When the output
+// tiles are too few to fill the GPU the (dense) reduction is also split into slices
+// written to a workspace and summed in FP64 (split_reduce in k_conv_simt.cu).  Every
+// mbarrier wait is bounded (2 s); on a timeout the CTA records an error code, drains its
+// own copies and MMAs, frees its TMEM and returns.
 #include "srp_internal.h"
 #include "srp_device.cuh"
 #include "tc_ptx.cuh"
@@ -43,32 +50,57 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NEPI = 8;                       // epilogue warps
 constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr int EPI_COLS = TN / 2;              // columns per epilogue thread
+constexpr int OUT_BOX = 32 * 32 * 4;          // one 32x32 FP32 output box per epilogue warp
 constexpr int KB_PER_CHUNK = 8;               // 32 K=16 steps per accumulator chunk
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + NEPI * OUT_BOX + BAR_BYTES + 1024;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int MIN_KB_PER_SLICE = 32;
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 }  // namespace
 
-struct ConvTcParams {
+struct TcParams {
   int F, J;
-  int kb_per_seg, nseg;  // k-blocks of 64 per operand segment, number of segments
+  int kb_per_seg, nseg;  // dense k-blocks of 64 per operand segment, number of segments
+  const int* kb_ptr;     // block-sparse: k-block list of cell tile n is
+  const int* kb_idx;     //   kb_idx[kb_ptr[n] .. kb_ptr[n+1]); NULL = dense
   int nM, nN, nslices, kb_per_slice;
-  float* Z;  // maps [F][J] (nslices == 1) or partial maps [nslices][F][J]
+  int tma_out;           // 1: results leave by TMA store through tmZ; 0: plain stores
+  float* Z;              // maps [F][J] (nslices == 1) or partial maps [nslices][F][J]
   unsigned long long* keys;
   int* err;
 };
 
+// The k-step range [s0, s1) of tile t, and the tile's coordinates.
+struct TileWork {
+  int slice, m, n, s0, s1, m_len;
+};
+
+__device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
+  TileWork w;
+  const int per_slice = p.nM * p.nN;
+  w.slice = t / per_slice;
+  const int rem = t - w.slice * per_slice;
+  w.n = rem / p.nM;
+  w.m = rem - w.n * p.nM;
+  w.m_len = p.kb_ptr ? __ldg(p.kb_ptr + w.n + 1) - __ldg(p.kb_ptr + w.n) : p.kb_per_seg;
+  const int nsteps = w.m_len * p.nseg;
+  w.s0 = min(nsteps, w.slice * p.kb_per_slice);
+  w.s1 = min(nsteps, w.s0 + p.kb_per_slice);
+  return w;
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
-    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-                   const ConvTcParams p, const uint32_t idesc) {
+                   const __grid_constant__ CUtensorMap tmZ, const TcParams p, const uint32_t idesc) {
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sA = smem_u32(smem);
   const uint32_t sB = sA + STAGES * A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint8_t* out_smem = smem + STAGES * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(out_smem + NEPI * OUT_BOX);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
@@ -100,10 +132,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-
-  const int per_slice = p.nM * p.nN;
-  const int total = per_slice * p.nslices;
-  const int kb_total = p.kb_per_seg * p.nseg;
+  const int total = p.nM * p.nN * p.nslices;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -119,23 +148,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t filled = 0, filled_par = 0;  // per stage: loaded at least once, its parity
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        const int slice = t / per_slice;
-        const int rem = t - slice * per_slice;
-        const int n = rem / p.nM, m = rem - (rem / p.nM) * p.nM;
-        const int kb0 = slice * p.kb_per_slice;
-        const int kb1 = min(kb_total, kb0 + p.kb_per_slice);
-        for (int kb = kb0; kb < kb1; ++kb) {
+        const TileWork w = tile_work(p, t);
+        const int* list = p.kb_ptr ? p.kb_idx + __ldg(p.kb_ptr + w.n) : nullptr;
+        for (int s = w.s0; s < w.s1; ++s) {
           if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, 1, WAIT_NS)) {
             ok = false;
             break;
           }
-          const int seg = kb / p.kb_per_seg;
-          const int kx = (kb - seg * p.kb_per_seg) * TK;
+          const int seg = s / w.m_len;
+          const int loc = s - seg * w.m_len;
+          const int kx = (list ? __ldg(list + loc) : loc) * TK;
           const CUtensorMap* ta = seg == 2 ? &tmA1 : &tmA0;
           const CUtensorMap* tb = seg == 1 ? &tmB1 : &tmB0;
           mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
-          tma_load_2d(sA + stage * A_BYTES, ta, kx, m * TM, full_bar(stage));
-          tma_load_2d(sB + stage * B_BYTES, tb, kx, n * TN, full_bar(stage));
+          tma_load_2d(sA + stage * A_BYTES, ta, kx, w.m * TM, full_bar(stage));
+          tma_load_2d(sB + stage * B_BYTES, tb, kx, w.n * TN, full_bar(stage));
           filled |= 1u << stage;
           filled_par = (filled_par & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -160,10 +187,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       int gc = 0;  // chunks issued by this CTA (selects the accumulator and its phase)
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        const int slice = t / per_slice;
-        const int kb0 = slice * p.kb_per_slice;
-        const int kb1 = min(kb_total, kb0 + p.kb_per_slice);
-        for (int c0 = kb0; c0 < kb1 && ok; c0 += KB_PER_CHUNK, ++gc) {
+        const TileWork w = tile_work(p, t);
+        for (int c0 = w.s0; c0 < w.s1 && ok; c0 += KB_PER_CHUNK, ++gc) {
           const int acc = gc & 1;
           const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
           if (!mbar_wait_bounded(tempty_bar(acc), aph ^ 1u, abort_flag, 3, WAIT_NS)) {
@@ -172,8 +197,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem_base + static_cast<uint32_t>(acc * TN);
-          const int c1 = min(kb1, c0 + KB_PER_CHUNK);
-          for (int kb = c0; kb < c1; ++kb) {
+          const int c1 = min(w.s1, c0 + KB_PER_CHUNK);
+          for (int s = c0; s < c1; ++s) {
             if (!mbar_wait_bounded(full_bar(stage), phase, abort_flag, 2, WAIT_NS)) {
               ok = false;
               break;
@@ -185,7 +210,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int k = 0; k < TK / 16; ++k)
               mma_f16(d, ad + static_cast<uint64_t>((k * 32) >> 4),
                       bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
-                      (kb > c0 || k > 0) ? 1u : 0u);
+                      (s > c0 || k > 0) ? 1u : 0u);
             mma_commit(empty_bar(stage));
             if (++stage == STAGES) {
               stage = 0;
@@ -205,20 +230,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ epilogue (warps 2..9)
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;       // which 128 of the 256 columns
-    const int row = q * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    uint8_t* box = out_smem + (warp - 2) * OUT_BOX;  // 32 rows x 128 bytes, 128B-swizzled
+    const uint32_t box_s = smem_u32(box);
     int gc = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const int slice = t / per_slice;
-      const int rem = t - slice * per_slice;
-      const int n = rem / p.nM, m = rem - (rem / p.nM) * p.nM;
-      const int kb0 = slice * p.kb_per_slice;
-      const int kb1 = min(kb_total, kb0 + p.kb_per_slice);
+      const TileWork w = tile_work(p, t);
       float sum[EPI_COLS];
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) sum[j] = 0.f;
-      for (int c0 = kb0; c0 < kb1; c0 += KB_PER_CHUNK, ++gc) {
+      for (int c0 = w.s0; c0 < w.s1; c0 += KB_PER_CHUNK, ++gc) {
         const int acc = gc & 1;
         const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
         const bool got = mbar_wait_bounded(tfull_bar(acc), aph, abort_flag, 4, WAIT_NS);
@@ -240,33 +262,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_arrive(tempty_bar(acc));
       }
       if (!ok) break;
-      const int f = m * TM + row;
-      if (f < p.F) {
-        const int n0 = n * TN + half * EPI_COLS;
-        float* zrow = p.Z + (static_cast<size_t>(slice) * p.F + f) * p.J + n0;
-        if ((p.J & 3) == 0 && n0 + EPI_COLS <= p.J) {
-          float4* dst = reinterpret_cast<float4*>(zrow);
+      const int f0 = w.m * TM + q * 32;  // first frame row of this warp
+      const int f = f0 + lane;
+      const int n0 = w.n * TN + half * EPI_COLS;
+      if (p.nslices == 1) {
+        float bv = -INFINITY;
+        int bi = -1;
 #pragma unroll
-          for (int j = 0; j < EPI_COLS / 4; ++j)
-            dst[j] = make_float4(sum[4 * j], sum[4 * j + 1], sum[4 * j + 2], sum[4 * j + 3]);
-        } else {
+        for (int j = 0; j < EPI_COLS; ++j)
+          if (n0 + j < p.J && (bi < 0 || sum[j] > bv)) {
+            bv = sum[j];
+            bi = n0 + j;
+          }
+        if (f < p.F && bi >= 0) atomicMax(p.keys + f, argmax_key(bv, bi));
+      }
+      if (p.tma_out) {
+        // 32x32 boxes: row = lane, 16-byte chunk c4 stored at chunk c4 ^ (lane & 7) (the
+        // tensor map's 128-byte swizzle), so the eight lanes of each store phase hit
+        // distinct banks.  Rows >= F and columns >= J are clipped by the TMA unit.
 #pragma unroll
-          for (int j = 0; j < EPI_COLS; ++j)
-            if (n0 + j < p.J) zrow[j] = sum[j];
+        for (int b = 0; b < EPI_COLS / 32; ++b) {
+          if (f0 >= p.F || n0 + b * 32 >= p.J) continue;  // box wholly outside the map
+          if (lane == 0) bulk_wait_read<0>();  // the previous box has left shared memory
+          __syncwarp();
+#pragma unroll
+          for (int c4 = 0; c4 < 8; ++c4) {
+            float4* dst = reinterpret_cast<float4*>(box + lane * 128 + ((c4 ^ (lane & 7)) << 4));
+            *dst = make_float4(sum[b * 32 + 4 * c4], sum[b * 32 + 4 * c4 + 1],
+                               sum[b * 32 + 4 * c4 + 2], sum[b * 32 + 4 * c4 + 3]);
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_3d(&tmZ, box_s, n0 + b * 32, f0, w.slice);
+            bulk_commit();
+          }
         }
-        if (p.nslices == 1) {
-          float bv = -INFINITY;
-          int bi = -1;
+      } else if (f < p.F) {
+        float* zrow = p.Z + (static_cast<size_t>(w.slice) * p.F + f) * p.J + n0;
 #pragma unroll
-          for (int j = 0; j < EPI_COLS; ++j)
-            if (n0 + j < p.J && (bi < 0 || sum[j] > bv)) {
-              bv = sum[j];
-              bi = n0 + j;
-            }
-          if (bi >= 0) atomicMax(p.keys + f, argmax_key(bv, bi));
-        }
+        for (int j = 0; j < EPI_COLS; ++j)
+          if (n0 + j < p.J) zrow[j] = sum[j];
       }
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -294,10 +334,10 @@ cudaError_t get_encode() {
   return cudaSuccess;
 }
 
-// 2-D K-major tensor map: inner dimension Kd (contiguous), outer `rows`, box 64 x box_rows,
+// 2-D K-major operand map: inner dimension Kd (contiguous), outer `rows`, box 64 x box_rows,
 // 128-byte swizzle; out-of-range rows read as zero.
-cudaError_t make_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, uint64_t Kd,
-                     uint64_t rows, uint32_t box_rows) {
+cudaError_t make_operand_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, uint64_t Kd,
+                             uint64_t rows, uint32_t box_rows) {
   cuuint64_t dims[2] = {Kd, rows};
   cuuint64_t strides[1] = {Kd * 2};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(TK), box_rows};
@@ -307,11 +347,23 @@ cudaError_t make_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, u
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+// 3-D FP32 output map over [slices][F][J], box 32 x 32 x 1, 128-byte swizzle.
+cudaError_t make_output_map(CUtensorMap* m, float* base, uint64_t J, uint64_t F, uint64_t slices) {
+  cuuint64_t dims[3] = {J, F, slices};
+  cuuint64_t strides[2] = {J * 4, J * F * 4};
+  cuuint32_t box[3] = {32, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 }  // namespace
 
-// Reduction slices for F frames: 1 while the output tiles fill the GPU; otherwise enough
-// slices (of at least MIN_KB_PER_SLICE k-blocks) to give every SM a tile.
-int conv_tc_slices(int F, int J, int Kd, int nseg, int num_sms) {
+// Reduction slices for F frames (dense operands): 1 while the output tiles fill the GPU;
+// otherwise enough slices (of at least MIN_KB_PER_SLICE k-blocks) to give every SM a tile.
+int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms) {
   if (F <= 0) return 1;
   const long long tiles = static_cast<long long>((F + TM - 1) / TM) * ((J + TN - 1) / TN);
   if (tiles >= num_sms) return 1;
@@ -321,65 +373,77 @@ int conv_tc_slices(int F, int J, int Kd, int nseg, int num_sms) {
   return static_cast<int>(want < cap ? want : cap);
 }
 
-size_t conv_tc_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms) {
+size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms) {
   size_t need = 0;
   for (int F = 1; F <= F_max; ++F) {
-    const int ns = conv_tc_slices(F, J, Kd, nseg, num_sms);
+    const int ns = tc_gemm_slices(F, J, Kd, nseg, num_sms);
     if (ns > 1) need = std::max(need, static_cast<size_t>(ns) * F * static_cast<size_t>(J));
   }
   return need;
 }
 
-bool conv_tc_supported(int, int, int Kd) { return Kd % TK == 0 && Kd / TK >= 1; }
+int tc_gemm_cell_tile() { return TN; }
+int tc_gemm_k_block() { return TK; }
 
-cudaError_t launch_conv_tc(const void* A, const void* A_lo, const void* B, const void* B_lo,
-                           OpType t, float* Z, unsigned long long* keys, int F, int J, int Kd,
-                           int num_sms, float* split_ws, int* err, cudaStream_t s) {
-  if (F <= 0) return cudaSuccess;
-  if (Kd % TK != 0) return cudaErrorInvalidValue;
+cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
+  if (g.F <= 0) return cudaSuccess;
+  if (g.Kd % TK != 0 || g.Kd <= 0) return cudaErrorInvalidValue;
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
-  const bool split3 = t == OpType::F16X2;
-  const CUtensorMapDataType dt = t == OpType::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  CUtensorMap mA0, mA1, mB0, mB1;
-  if ((e = make_map(&mA0, A, dt, Kd, F, TM)) != cudaSuccess) return e;
-  if ((e = make_map(&mB0, B, dt, Kd, J, TN)) != cudaSuccess) return e;
+  const bool split3 = g.t == OpType::F16X2;
+  const CUtensorMapDataType dt = g.t == OpType::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMap mA0, mA1, mB0, mB1, mZ;
+  if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, TM)) != cudaSuccess) return e;
+  if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, TN)) != cudaSuccess) return e;
   if (split3) {
-    if ((e = make_map(&mA1, A_lo, dt, Kd, F, TM)) != cudaSuccess) return e;
-    if ((e = make_map(&mB1, B_lo, dt, Kd, J, TN)) != cudaSuccess) return e;
+    if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, TM)) != cudaSuccess) return e;
+    if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, TN)) != cudaSuccess) return e;
   } else {
     mA1 = mA0;
     mB1 = mB0;
   }
-  ConvTcParams p;
-  p.F = F;
-  p.J = J;
-  p.kb_per_seg = Kd / TK;
+  TcParams p;
+  p.F = g.F;
+  p.J = g.J;
+  p.kb_per_seg = g.Kd / TK;
   p.nseg = split3 ? 3 : 1;
-  p.nM = (F + TM - 1) / TM;
-  p.nN = (J + TN - 1) / TN;
-  p.nslices = conv_tc_slices(F, J, Kd, p.nseg, num_sms);
+  p.kb_ptr = g.kb_ptr;
+  p.kb_idx = g.kb_idx;
+  p.nM = (g.F + TM - 1) / TM;
+  p.nN = (g.J + TN - 1) / TN;
+  p.nslices = g.kb_ptr ? 1 : tc_gemm_slices(g.F, g.J, g.Kd, p.nseg, num_sms);
   const int kb_total = p.kb_per_seg * p.nseg;
-  p.kb_per_slice = (kb_total + p.nslices - 1) / p.nslices;
-  p.nslices = (kb_total + p.kb_per_slice - 1) / p.kb_per_slice;
-  p.keys = keys;
-  p.err = err;
   if (p.nslices > 1) {
-    if (!split_ws) return cudaErrorInvalidValue;
-    p.Z = split_ws;
+    p.kb_per_slice = (kb_total + p.nslices - 1) / p.nslices;
+    p.nslices = (kb_total + p.kb_per_slice - 1) / p.kb_per_slice;
   } else {
-    p.Z = Z;
+    p.kb_per_slice = 1 << 30;
   }
-  const uint32_t idesc = tc::idesc_f16(t == OpType::BF16 ? 1u : 0u, TM, TN);
+  p.keys = g.keys;
+  p.err = g.err;
+  if (p.nslices > 1) {
+    if (!g.split_ws) return cudaErrorInvalidValue;
+    p.Z = g.split_ws;
+  } else {
+    p.Z = g.Z;
+  }
+  // TMA output needs 16-byte row strides and a 16-byte aligned base.
+  p.tma_out = (g.J % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Z) % 16 == 0);
+  if (p.tma_out) {
+    if ((e = make_output_map(&mZ, p.Z, g.J, g.F, p.nslices)) != cudaSuccess) return e;
+  } else {
+    mZ = mA0;  // unused
+  }
+  const uint32_t idesc = tc::idesc_f16(g.t == OpType::BF16 ? 1u : 0u, TM, TN);
   const int total = p.nM * p.nN * p.nslices;
   const int grid = total < num_sms ? total : num_sms;
-  e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  conv_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(mA0, mA1, mB0, mB1, p, idesc);
+  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
   e = cudaGetLastError();
   if (e != cudaSuccess || p.nslices == 1) return e;
-  return launch_split_reduce(split_ws, p.nslices, Z, keys, F, J, s);
+  return launch_split_reduce(g.split_ws, p.nslices, g.Z, g.keys, g.F, g.J, s);
 }
 
 }  // namespace srp

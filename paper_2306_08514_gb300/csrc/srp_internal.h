@@ -79,17 +79,45 @@ cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
 // Sums nz partial maps [nz][F][J] in FP64 into Z and merges the argmax keys.
 cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long long* keys,
                                 int F, int J, cudaStream_t s);
-// Tensor-core conv GEMM (tcgen05), fused argmax keys.  F16/BF16 operands, or F16 hi+lo
-// (three products, nseg = 3).  When the output tiles do not fill the GPU the reduction
-// is split into conv_tc_slices(...) slices written to split_ws [slices][F][J] (at most
-// conv_tc_workspace_floats(...) floats for any F <= F_max).  A bounded wait that runs
-// out stores a non-zero code in *err.
-cudaError_t launch_conv_tc(const void* A, const void* A_lo, const void* B, const void* B_lo,
-                           OpType t, float* Z, unsigned long long* keys, int F, int J, int Kd,
-                           int num_sms, float* split_ws, int* err, cudaStream_t s);
-bool conv_tc_supported(int F_max, int J, int Kd);
-int conv_tc_slices(int F, int J, int Kd, int nseg, int num_sms);
-size_t conv_tc_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms);
+// Tensor-core contraction (tcgen05, k_tc_gemm.cu): Z[F][J] = A B^T with 16-bit K-major
+// operands A [F][Kd], B [J][Kd] (Kd a multiple of tc_gemm_k_block()), FP32 accumulation,
+// fused argmax keys.  t = F16X2 runs three products over hi and lo planes.  With kb_ptr
+// (device, [ceil(J / tc_gemm_cell_tile()) + 1]) and kb_idx, cell tile n only visits the
+// k-blocks kb_idx[kb_ptr[n] .. kb_ptr[n+1]) (block-sparse B).  Dense reductions whose
+// output tiles do not fill the GPU are split into tc_gemm_slices(...) slices written to
+// split_ws (tc_gemm_workspace_floats(...) floats suffice for any F <= F_max) and summed
+// in FP64.  A bounded wait that runs out stores a non-zero code in *err.
+struct TcGemm {
+  const void* A = nullptr;
+  const void* A_lo = nullptr;
+  const void* B = nullptr;
+  const void* B_lo = nullptr;
+  OpType t = OpType::F16;
+  int F = 0, J = 0, Kd = 0;
+  const int* kb_ptr = nullptr;
+  const int* kb_idx = nullptr;
+  float* Z = nullptr;
+  unsigned long long* keys = nullptr;
+  float* split_ws = nullptr;
+  int* err = nullptr;
+};
+cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s);
+int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms);
+size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms);
+int tc_gemm_cell_tile();
+int tc_gemm_k_block();
+
+// Operand preparation (k_pack.cu).  pack16: X [rows][C] FP32 -> [rows][Cpad] (zero
+// padded) in type t after multiplying by scale; csr_to_dense: CSR taps -> zeroed dense
+// [J][Cpad]; interp_dense: SI sinc (td = false) or TD one-hot (td = true) entries from the
+// FP64 TDOA table tau [J][P], column l < L being pair col_pair[l] at lag col_lag[l].
+cudaError_t launch_pack16(const float* X, int rows, int C, int Cpad, float scale, OpType t,
+                          void* hi, void* lo, cudaStream_t s);
+cudaError_t launch_csr_to_dense(const long long* row_ptr, const int2* taps, int J, int Cpad,
+                                OpType t, void* hi, void* lo, cudaStream_t s);
+cudaError_t launch_interp_dense(const double* tau, int J, int P, const int* col_pair,
+                                const int* col_lag, int L, int Cpad, bool td, OpType t, void* hi,
+                                void* lo, cudaStream_t s);
 
 // SLRI: U[F][R] = xi Lambda_fat^T ; Z = U Lambda_tall^T (fused argmax keys).
 cudaError_t launch_slri_fat(const float* xi, const float* fat, float* U, int F, int L, int R,
@@ -116,7 +144,8 @@ struct srp_plan_s {
   int Fmax = 0;
   int num_sms = 0;
   srp::OpType op = srp::OpType::F32;
-  bool conv_tc = false;
+  int Lpad = 0;       // L rounded up to a multiple of 64 (dense interpolation operands)
+  int slri_exp = 0;   // tensor-core SLRI: u is scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp
   std::vector<double> sigma;
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
   std::vector<int> h_col;
@@ -133,6 +162,10 @@ struct srp_plan_s {
   float* d_fat = nullptr;
   long long* d_row_ptr = nullptr;
   int2* d_taps = nullptr;
+  void* d_B = nullptr;     // dense interpolation operand [J][Lpad] (SI, TD, tensor-core SSPI)
+  void* d_B_lo = nullptr;  //   or Lambda_tall as [J][64] (tensor-core SLRI); lo plane for FP16X2
+  int* d_kb_ptr = nullptr;  // block-sparse k-block lists per cell tile of d_B
+  int* d_kb_idx = nullptr;
   // scratch
   float2* d_yhat = nullptr;
   void* d_A = nullptr;

@@ -1,0 +1,134 @@
+"""Parity of the tensor-core precisions of every method, and of SI-SRP and conv. TD-SRP,
+against the FP64 oracle (through the C-ABI, on the GPU).
+
+Bounds: FP16 hi+lo and FP32 must meet 1e-5 relative per frame; single FP16 / BF16
+operands round each operand to 2^-11 / 2^-8 relative, which over sums of many terms gives
+about sqrt(2/3) u of map error: stated bounds 2e-3 (FP16) and 1.5e-2 (BF16).  The argmax
+returned must be the argmax of the GPU's own map, and a valid maximum of the oracle map
+within the measured error.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import _ref as R
+from tests.test_gpu_parity import S, _run, check_argmax, _check_taps, sq, uca_small  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+PRECS = [("fp32", TOL), ("fp16x3", TOL), ("fp16", 2e-3), ("bf16", 1.5e-2)]
+TC_PRECS = PRECS[1:]
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+def test_si_square4(S, sq, prec, tol):
+    w, psi, dt, lags, perm, xi_o = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="si", precision=prec,
+                  max_frames=64)
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    zo = O.srp_si(R.lam("square4"), xi_o)
+    assert R.per_frame_rel(z, zo).max() <= tol
+    check_argmax(z, am, zo)
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+def test_td_square4(S, sq, prec, tol):
+    w, psi, dt, lags, perm, xi_o = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="td", precision=prec,
+                  max_frames=64)
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    zo = xi_o @ O.td_matrix(dt, w["fs"], lags).T
+    assert R.per_frame_rel(z, zo).max() <= tol
+    check_argmax(z, am, zo)
+
+
+@pytest.mark.parametrize("prec,tol", TC_PRECS)
+@pytest.mark.parametrize("rank", [8, 16])
+def test_slri_tensor_cores_square4(S, sq, prec, tol, rank):
+    w, psi, dt, lags, perm, xi_o = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="slri", rank=rank,
+                  precision=prec, max_frames=64)
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    tall, fat, s = R.slri("square4", rank)
+    zo = O.srp_slri(tall, fat, xi_o)
+    assert R.per_frame_rel(z, zo).max() <= tol
+    check_argmax(z, am, zo)
+
+
+@pytest.mark.parametrize("prec,tol", TC_PRECS)
+@pytest.mark.parametrize("t", [0.5, 2.0, 4.0])
+def test_sspi_tensor_cores_square4(S, sq, prec, tol, t):
+    w, psi, dt, lags, perm, xi_o = sq
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="sspi", taps=t,
+                  precision=prec, max_frames=64)
+    mask, tied, taken, nnz = R.sspi("square4", t)
+    ndiff = _check_taps(plan, mask, perm, R.lam("square4"))
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    if ndiff == 0:
+        zo = O.srp_sspi(np.where(mask, R.lam("square4"), 0.0), xi_o)
+        assert R.per_frame_rel(z, zo).max() <= tol
+        check_argmax(z, am, zo)
+    else:
+        assert np.array_equal(am, np.argmax(z, axis=1))
+
+
+def test_uca8_small_tensor_cores_all_methods(S, uca_small):
+    """Ragged frame tile (70 = 64 + 6) and cell tile (4616 cells), block-sparse SSPI/TD."""
+    name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    Lam = R.lam(name, F, sub)
+    tall, fat, s = R.slri(name, 16, F, sub)
+    mask, tied, taken, nnz = R.sspi(name, 4.0, F, sub)
+    refs = {
+        "si": (dict(method="si"), O.srp_si(Lam, xi_o)),
+        "td": (dict(method="td"), xi_o @ O.td_matrix(dt, w["fs"], lags).T),
+        "slri": (dict(method="slri", rank=16), O.srp_slri(tall, fat, xi_o)),
+        "sspi": (dict(method="sspi", taps=4.0), O.srp_sspi(np.where(mask, Lam, 0.0), xi_o)),
+    }
+    for prec, tol in PRECS:
+        for m, (kw, zo) in refs.items():
+            if m in ("slri", "sspi") and prec == "fp32":
+                continue  # covered by test_gpu_parity
+            plan = S.Plan(*args, precision=prec, max_frames=64, **kw)
+            if m == "sspi" and _check_taps(plan, mask, perm, Lam) != 0:
+                continue
+            z, am = _run(plan, w["frames"])
+            plan.status()
+            assert R.per_frame_rel(z, zo).max() <= tol, (m, prec)
+            check_argmax(z, am, zo)
+
+
+def test_uca8_full_size_tensor_cores_sampled(S):
+    """The benchmark's workload (J=60000, F=2000, one launch per method), tensor-core
+    SLRI / SSPI in FP16 hi+lo: sampled frames against the oracle."""
+    w = R.workload("uca8")
+    F = w["F"]
+    frames = w["frames"]
+    fsel = np.array([0, 3, 999, 1998, F - 1])
+    psi = R.psi_of(frames[fsel])
+    dt, Np, lags, perm = R.geometry("uca8")
+    xi_o, _ = O.gcc_samples_ifft(psi, lags, w["N"] // 2)
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    tall, fat, s = R.slri("uca8", 16)
+    plan = S.Plan(*args, method="slri", rank=16, precision="fp16x3", max_frames=F)
+    z, am = _run(plan, frames)
+    plan.status()
+    zo = O.srp_slri(tall, fat, xi_o)
+    assert R.per_frame_rel(z[fsel], zo).max() <= TOL
+    check_argmax(z[fsel], am[fsel], zo)
+    mask, tied, taken, nnz = R.sspi("uca8", 4.0)
+    plan = S.Plan(*args, method="sspi", taps=4.0, precision="fp16x3", max_frames=F)
+    ndiff = _check_taps(plan, mask, perm, R.lam("uca8"))
+    z, am = _run(plan, frames)
+    plan.status()
+    if ndiff == 0:
+        zo = O.srp_sspi(np.where(mask, R.lam("uca8"), 0.0), xi_o)
+        assert R.per_frame_rel(z[fsel], zo).max() <= TOL
+        check_argmax(z[fsel], am[fsel], zo)
+    else:
+        assert np.array_equal(am, np.argmax(z, axis=1))
