@@ -4,12 +4,17 @@
 Workload (default): M=8 uniform circular array (r=5 cm), 3-D grid of 0.1 m cells over
 5x4x3 m (J=60000), N=512 Hann frames, F=2000 frames per step, AR(10) speech-like source
 with on/off envelope and 10 dB diffuse noise (synthetic, seeded).  One step computes,
-for the whole batch, the maps of all three methods -- conv. FD-SRP, SLRI-SRP (R=16) and
-SSPI-SRP (t=4 taps per location and pair) -- each through the full path (STFT + PHAT,
-cross-spectra / iFFT sampling, contraction, argmax).  ``value`` counts every map cell
-produced: 3 * J * F per step and rank.
+for the whole batch, the maps of conv. FD-SRP, SLRI-SRP (R=16) and SSPI-SRP (t=4 taps
+per location and pair), each through the full path (STFT + PHAT, cross-spectra / iFFT
+sampling, contraction, argmax).  ``value`` counts every map cell produced: 3 * J * F per
+step and rank.  The default precision is BF16 on the tensor cores for every method: the
+conv. point is then the fastest conv. FD-SRP whose map error (vs the FP64 oracle) stays
+far below the approximation error of SLRI/SSPI, i.e. the matched-error comparison;
+``--precision fp16x3`` gives FP32-class maps (<= 1e-5 of the oracle).
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+Timing: every step is bracketed by CUDA events on the launching stream, with an L2 flush
+(a 512 MB write) before each step outside the events.  Prints one JSON line (rank 0).
+``--impl reference`` times the FP64 CPU oracle instead.
 """
 from __future__ import annotations
 
@@ -30,9 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "SRP map cells·frames/s, SLRI/SSPI vs conv FD-SRP at matched error; p50/p99 latency"
 UNIT = "cells*frames/s"
 FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS = 6800.0, 1900.0
+FFMA_LANES = 152 * 128  # SMs x FP32 lanes
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -42,10 +48,15 @@ def parse():
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--rank", type=int, default=16, help="SLRI rank R")
     ap.add_argument("--taps", type=float, default=4.0, help="SSPI taps per location and pair")
-    ap.add_argument("--conv-precision", default="fp32")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="bf16", help="fp32 | bf16 | fp16 | fp16x3")
+    ap.add_argument("--conv-precision", default=None)
+    ap.add_argument("--slri-precision", default=None)
+    ap.add_argument("--sspi-precision", default=None)
     ap.add_argument("--methods", default="conv,slri,sspi")
-    return ap.parse_args()
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -73,7 +84,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -131,33 +142,48 @@ def reduce_max(values, world, device):
 
 
 # ------------------------------------------------------------------------------------
-def cpu_baseline(w, R, t, n_frames=1):
-    """The FP64 oracle as it stands, per-frame work of all three methods on a bounded
-    sample (n_frames frames, every grid cell); plan-time fits are excluded like the GPU's."""
-    import oracle as O
-    fs, K = w["fs"], w["N"] // 2
-    dt = O.tdoa_nf(w["mic_xyz"], w["grid_xyz"])
-    lags = O.pair_lags(O.n_p_samples(w["mic_xyz"], fs))
-    Lam = O.interp_matrix(dt, fs, lags)
-    tall, fat, _ = O.slri_factors(Lam, R)
-    Lsp = O.sspi_matrix(Lam, lags, int(round(t * Lam.shape[0] * len(lags))))
-    fr = w["frames"][:n_frames]
+class OracleRefs:
+    """FP64 oracle maps of sampled frames (CPU), for the error report."""
+
+    def __init__(self, w, R, t):
+        import oracle as O
+        self.O = O
+        self.w = w
+        self.fs, self.K = w["fs"], w["N"] // 2
+        self.dt = O.tdoa_nf(w["mic_xyz"], w["grid_xyz"])
+        self.lags = O.pair_lags(O.n_p_samples(w["mic_xyz"], self.fs))
+        self.Lam = O.interp_matrix(self.dt, self.fs, self.lags)
+        self.tall, self.fat, _ = O.slri_factors(self.Lam, R)
+        self.Lsp = O.sspi_matrix(self.Lam, self.lags, int(round(t * self.Lam.shape[0] * len(self.lags))))
+
+    def maps(self, method, frames):
+        O = self.O
+        psi = O.gcc_phat(O.stft(frames, "hann"))
+        if method == "conv":
+            return O.srp_conv(psi, self.dt, self.fs)
+        xi, _ = O.gcc_samples_ifft(psi, self.lags, self.K)
+        if method == "slri":
+            return O.srp_slri(self.tall, self.fat, xi)
+        return O.srp_sspi(self.Lsp, xi)
+
+
+def cpu_baseline(refs, frames):
+    """The FP64 oracle as it stands: per-frame work of all three methods on a bounded
+    sample (every grid cell); plan-time fits are excluded like the GPU's."""
     t0 = time.perf_counter()
-    psi = O.gcc_phat(O.stft(fr, "hann"))
-    O.srp_conv(psi, dt, fs)
-    xi, _ = O.gcc_samples_ifft(psi, lags, K)
-    O.srp_slri(tall, fat, xi)
-    O.srp_sspi(Lsp, xi)
+    out = {m: refs.maps(m, frames) for m in ("conv", "slri", "sspi")}
     el = time.perf_counter() - t0
-    J = w["grid_xyz"].shape[0]
+    J = refs.w["grid_xyz"].shape[0]
     try:
         import threadpoolctl
         cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
     except Exception:
         cores = os.cpu_count()
-    return {"value": 3 * J * n_frames / el, "unit": UNIT, "cores": int(cores), "kind": "oracle",
-            "sample": f"{n_frames} frame(s) x {J} cells x 3 methods (conv FP64 H, SLRI R={R}, "
-                      f"SSPI t={t}); plan-time SVD/selection excluded", "seconds": el}
+    n = frames.shape[0]
+    return out, {"value": 3 * J * n / el, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+                 "sample": f"{n} frame(s) x {J} cells x 3 methods (FP64 conv H, SLRI, SSPI "
+                           f"from the oracle's factors); plan-time SVD/selection excluded",
+                 "seconds": el}
 
 
 def run_reference(a):
@@ -166,12 +192,12 @@ def run_reference(a):
         return
     import synth
     w = synth.workload(a.workload, F=max(4, a.warmup + a.steps))
+    refs = OracleRefs(w, a.rank, a.taps)
     J = w["grid_xyz"].shape[0]
     times = []
+    r = None
     for s in range(a.warmup + a.steps):
-        sub = dict(w)
-        sub["frames"] = w["frames"][s:s + 1]
-        r = cpu_baseline(sub, a.rank, a.taps, 1)
+        _, r = cpu_baseline(refs, w["frames"][s:s + 1])
         if s >= a.warmup:
             times.append(r["seconds"])
     ms = 1e3 * float(np.mean(times))
@@ -187,6 +213,22 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------------------------------
+def contraction_work(m, prec, info, F, R):
+    """(kind, amount per launch) of the dominant kernel of method m: algorithmic FLOPs of
+    the contraction (a split-precision FP16 hi+lo run executes three products) or bytes."""
+    J, P, K, L = info.J, info.P, info.K, info.L
+    x3 = 3.0 if prec == "fp16x3" else 1.0
+    if m == "conv":
+        return "flop", x3 * 4.0 * J * P * (K - 1) * F  # 2JP(K-1) real MACs per frame
+    if m == "slri":
+        return "byte", 4.0 * J * F  # the map write; 2R(J+L) flop per frame is far below
+    if m == "sspi":
+        if prec == "fp32":
+            return "flop", 2.0 * info.nnz * F
+        return "byte", 4.0 * J * F
+    return "byte", 4.0 * J * F
+
+
 def run_libsrp(a):
     import torch
     rank, world, local = dist_env()
@@ -202,13 +244,15 @@ def run_libsrp(a):
     F, J, N, M = w["F"], w["grid_xyz"].shape[0], w["N"], w["mic_xyz"].shape[0]
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], N)
     methods = [m for m in a.methods.split(",") if m]
-    kw = {"conv": dict(method="conv", precision=a.conv_precision),
-          "slri": dict(method="slri", rank=a.rank), "sspi": dict(method="sspi", taps=a.taps)}
-    plans = {m: S.Plan(*args, max_frames=F, **kw[m]) for m in methods}
+    prec = {m: getattr(a, f"{m}_precision", None) or a.precision for m in methods}
+    kw = {"conv": dict(method="conv"), "slri": dict(method="slri", rank=a.rank),
+          "sspi": dict(method="sspi", taps=a.taps)}
+    plans = {m: S.Plan(*args, max_frames=F, precision=prec[m], **kw[m]) for m in methods}
     frames = torch.from_numpy(w["frames"]).to(dev)
     maps = {m: torch.empty((F, J), dtype=torch.float32, device=dev) for m in methods}
     am = {m: torch.empty((F,), dtype=torch.int32, device=dev) for m in methods}
     stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
 
     def step():
         for m in methods:
@@ -218,46 +262,43 @@ def run_libsrp(a):
         step()
     torch.cuda.synchronize()
     for m in methods:
+        plans[m].status()
         plans[m].set_profiling(True)
+    launches0 = {m: plans[m].info_now().launches for m in methods}
     clocks = Clocks(local)
     if rank == 0:
         clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
     t0 = time.perf_counter()
-    e0.record(stream)
-    for _ in range(a.steps):
+    for e0, e1 in ev:
+        if not a.no_flush:
+            flush.fill_(1.0)  # L2 flush, outside the events
+        e0.record(stream)
         step()
-    e1.record(stream)
+        e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
     ck = clocks.stop() if rank == 0 else None
-    dev_ms = e0.elapsed_time(e1) / a.steps
+    dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps
+    launches = sum(plans[m].info_now().launches - launches0[m] for m in methods)
     stages = {m: plans[m].stage_ms() for m in methods}
     for m in methods:
         plans[m].set_profiling(False)
+        plans[m].status()
     dev_ms, wall = reduce_max([dev_ms, wall], world, dev)
 
-    # per-method device time for the breakdown (sum of its stages per step)
     per = {}
     for m in methods:
         st = stages[m]
         ms_m = sum(st[k] for k in ("frontend", "spectra", "contract", "argmax")) / a.steps
-        per[m] = {"ms_per_step": ms_m, "cells_frames_per_s": J * F / (ms_m / 1e3),
+        per[m] = {"precision": prec[m], "ms_per_step": ms_m, "cells_frames_per_s": J * F / (ms_m / 1e3),
                   "stage_ms": {k: st[k] / a.steps for k in ("frontend", "spectra", "contract", "argmax")}}
-    # map error of SLRI/SSPI relative to the GPU's conv FP32 map (eps_z of Sec. V-A)
-    if "conv" in methods:
-        zc = maps["conv"].double()
-        for m in methods:
-            if m == "conv":
-                continue
-            d = ((maps[m].double() - zc) ** 2).sum(1) / (zc ** 2).sum(1)
-            per[m]["eps_z_vs_conv_db_median"] = float(10 * torch.log10(d).median())
-            per[m]["argmax_agree_vs_conv"] = float((am[m] == am["conv"]).float().mean())
 
     # e2e through the host-buffer entry point (H2D frames + D2H maps inside the timing)
     hframes = torch.from_numpy(w["frames"]).pin_memory()
@@ -281,61 +322,80 @@ def run_libsrp(a):
     cells = len(methods) * J * F * world
     value = cells / (dev_ms / 1e3)
     hbm, bf16, bf16s, smmax, src = peaks()
-    # dominant kernel: the contraction with the largest time
+
+    # dominant kernel: the contraction with the largest time (its CUDA-event duration on the
+    # launching stream, per launch; one launch per method and step)
     dom = max(methods, key=lambda m: per[m]["stage_ms"]["contract"])
-    K = N // 2
-    P = M * (M - 1) // 2
     t_launch = per[dom]["stage_ms"]["contract"] / 1e3
     info = plans[dom].info
-    if dom == "conv":
-        flops = 4.0 * J * P * (K - 1) * F  # 2 J P (K-1) real MACs per frame (Eq. SRPomp)
-        if a.conv_precision == "fp32":
-            peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": flops / t_launch / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+    kind, work = contraction_work(dom, prec[dom], info, F, a.rank)
+    if kind == "flop":
+        if prec[dom] == "fp32":
+            peak = FFMA_LANES * 2 * smmax * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": work / t_launch / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
         else:
-            roof = {"bound": "tensor", "achieved": flops / t_launch / 1e12, "peak": bf16s,
-                    "unit": "TFLOP/s", "peak_source": f"{src} bf16 sustained"}
-    elif dom == "slri":
-        R = a.rank
-        byts = 4.0 * J * F + 4.0 * F * R + 4.0 * J * R  # map write + u read + factors
-        roof = {"bound": "hbm", "achieved": byts / t_launch / 1e9, "peak": hbm, "unit": "GB/s",
-                "peak_source": f"{src} copy"}
+            roof = {"bound": "tensor", "achieved": work / t_launch / 1e12, "peak": bf16s,
+                    "unit": "TFLOP/s", "peak_source": f"{src} bf16 sustained (FP16 runs at the BF16 rate)"}
     else:
-        nnz = info.nnz
-        flops = 2.0 * nnz * F
-        peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / t_launch / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+        roof = {"bound": "hbm", "achieved": work / t_launch / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_source": f"{src} copy"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["kernel"] = {"conv": "conv GEMM", "slri": "SLRI fat+tall", "sspi": "SSPI gather"}[dom]
-    per_launch = {"conv": 4, "slri": 5, "sspi": 4}
+    roof["kernel"] = {"conv": "tc_gemm_kernel (conv SRP matrix)" if prec[dom] != "fp32" else "sgemm_nt_argmax_kernel",
+                      "slri": "SLRI fat + pack + tc_gemm_kernel" if prec[dom] != "fp32" else "SLRI fat + tall",
+                      "sspi": "SSPI pack + tc_gemm_kernel" if prec[dom] != "fp32" else "sspi_kernel"}[dom]
+    roof["work_per_launch"] = {"kind": kind, "amount": work}
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{a.workload}: M={M} UCA r=5cm, J={J} (0.1 m grid), N={N} Hann, "
-                               f"F={F} frames/step/rank; conv FD-SRP {a.conv_precision} + SLRI R={a.rank} "
-                               f"+ SSPI t={a.taps}",
-                   "maps_per_frame": len(methods), "l2": "working set per step > L2 (SRP matrix "
-                   f"{plans['conv'].info.device_bytes / 1e9:.1f} GB, maps {len(methods) * 4 * J * F / 1e9:.2f} GB); no flush"
-                   if "conv" in plans else "maps written per step exceed L2"},
+        "vs_baseline": None, "dtype": "/".join(sorted(set(prec.values()))), "data": "synthetic",
+        "config": {"workload": f"{a.workload}: M={M}, J={J}, N={N} Hann, F={F} frames/step/rank; "
+                               + ", ".join(f"{m} {prec[m]}" for m in methods)
+                               + f" (SLRI R={a.rank}, SSPI t={a.taps})",
+                   "maps_per_frame": len(methods),
+                   "l2": "flushed before every step (512 MB write, outside the timed events)"
+                   if not a.no_flush else "not flushed"},
         "wall_ms_per_step": 1e3 * wall / a.steps,
         "methods": per,
         "roofline": roof,
         "e2e": {"value": cells / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": len(methods) * F * M * N * 4,
                 "d2h_bytes_per_step": len(methods) * F * (J * 4 + 4)},
-        "gpu_launches": sum(per_launch[m] for m in methods) * a.steps,
+        "gpu_launches": launches // a.steps * a.steps,
         "clocks": ck,
     }
-    if "conv" in per and "slri" in per:
-        out["speedup_slri_vs_conv"] = per["slri"]["cells_frames_per_s"] / per["conv"]["cells_frames_per_s"]
-    if "conv" in per and "sspi" in per:
-        out["speedup_sspi_vs_conv"] = per["sspi"]["cells_frames_per_s"] / per["conv"]["cells_frames_per_s"]
-    if world == 1 and not a.no_cpu_baseline:
-        out["cpu_baseline"] = {k: v for k, v in cpu_baseline(w, a.rank, a.taps, 1).items() if k != "seconds"}
+    for m in ("slri", "sspi"):
+        if "conv" in per and m in per:
+            out[f"speedup_{m}_vs_conv"] = per[m]["cells_frames_per_s"] / per["conv"]["cells_frames_per_s"]
+
+    if world == 1 and not (a.no_oracle_check and a.no_cpu_baseline):
+        import oracle as O
+        refs = OracleRefs(w, a.rank, a.taps)
+        z = {m: maps[m].cpu().numpy() for m in methods}
+        idx = {m: am[m].cpu().numpy() for m in methods}
+        sel = np.array([0, F // 2])
+        zo, cb = cpu_baseline(refs, w["frames"][sel[:1]])
+        if not a.no_cpu_baseline:
+            out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
+        if not a.no_oracle_check:
+            rep = {}
+            rc = refs.maps("conv", w["frames"][sel]) if "conv" in methods else None
+            for m in methods:
+                fsel = sel if m == "conv" else np.arange(0, F, max(1, F // 200))
+                ref = rc if m == "conv" else refs.maps(m, w["frames"][fsel])
+                rel = O.rel_err(z[m][fsel].astype(np.float64), ref, axis=-1)
+                err = np.max(np.abs(z[m][fsel].astype(np.float64) - ref), axis=1)
+                picked = ref[np.arange(len(fsel)), idx[m][fsel]]
+                rep[m] = {"frames_checked": int(len(fsel)), "rel_err_max": float(rel.max()),
+                          "rel_err_median": float(np.median(rel)),
+                          "argmax_exact": float(np.mean(idx[m][fsel] == np.argmax(ref, axis=1))),
+                          "argmax_within_error": float(np.mean(picked >= ref.max(axis=1) - 2 * err - 1e-9))}
+                if m != "conv" and rc is not None:
+                    ro = refs.maps(m, w["frames"][sel])
+                    rep[m]["eps_z_vs_conv_db"] = float(np.median(O.eps_db(ro, rc, axis=-1)))
+            out["vs_oracle"] = rep
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -112,6 +112,8 @@ typedef struct {
                                smallest kept one (selection ties, broken by (i, p, n)) */
   size_t device_bytes;      /* device memory held by the plan */
   double fit_seconds;       /* host+device time spent in srp_plan_create */
+  long long launches;       /* kernels launched by this plan's srp_map / srp_map_host /
+                               srp_gcc_samples calls so far (memsets and copies excluded) */
 } srp_plan_info_t;
 
 /*

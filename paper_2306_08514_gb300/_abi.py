@@ -37,7 +37,7 @@ class srp_plan_info_t(C.Structure):
     _fields_ = [
         ("M", C.c_int), ("P", C.c_int), ("J", C.c_int), ("N", C.c_int), ("K", C.c_int),
         ("L", C.c_int), ("rank", C.c_int), ("nnz", C.c_longlong), ("tied_at_cut", C.c_longlong),
-        ("device_bytes", C.c_size_t), ("fit_seconds", C.c_double),
+        ("device_bytes", C.c_size_t), ("fit_seconds", C.c_double), ("launches", C.c_longlong),
     ]
 
 
@@ -250,6 +250,10 @@ class Plan:
 
     def set_profiling(self, enable=True):
         srp_plan_set_profiling(self.handle, enable)
+
+    def info_now(self):
+        """srp_plan_info as of now (launch counter included)."""
+        return srp_plan_info(self.handle)
 
     def stage_ms(self):
         return srp_plan_stage_ms(self.handle)

@@ -129,9 +129,13 @@ srp_status mark(srp_plan_s* p, int stage, cudaStream_t s) {
 // Z = A B^T with the plan's operand type: FP32 FFMA (SIMT) or the tensor cores.
 cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void* B, const void* B_lo,
                      int Kd, const int* kb_ptr, const int* kb_idx, int F, float* maps, cudaStream_t s) {
-  if (p->op == OpType::F32)
+  if (p->op == OpType::F32) {
+    p->launches += sgemm_split_count(Kd) > 1 ? 2 : 1;
     return launch_sgemm_nt_argmax(static_cast<const float*>(A), static_cast<const float*>(B), maps,
                                   p->d_keys, F, p->g.J, Kd, p->d_split, s);
+  }
+  const int nseg = p->op == OpType::F16X2 ? 3 : 1;
+  p->launches += (!kb_ptr && tc_gemm_slices(F, p->g.J, Kd, nseg, p->num_sms) > 1) ? 2 : 1;
   TcGemm tg;
   tg.A = A;
   tg.A_lo = A_lo;
@@ -150,16 +154,23 @@ cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void*
   return launch_tc_gemm(tg, p->num_sms, s);
 }
 
+// A counted kernel launch of the per-call path.
+#define SRP_LAUNCH(expr)  \
+  do {                    \
+    ++p->launches;        \
+    SRP_CUDA_TRY(expr);   \
+  } while (0)
+
 srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int* argmax,
                      cudaStream_t s) {
   const Geometry& g = p->g;
   SRP_CUDA_TRY(cudaMemsetAsync(p->d_keys, 0, sizeof(unsigned long long) * F, s));
   SRP_MARK(p, 0, s);
-  SRP_CUDA_TRY(launch_stft_phat(frames, F, g.M, g.N, p->d_window, p->d_twiddle, p->d_yhat, s));
+  SRP_LAUNCH(launch_stft_phat(frames, F, g.M, g.N, p->d_window, p->d_twiddle, p->d_yhat, s));
   SRP_MARK(p, 1, s);
   switch (p->desc.method) {
     case SRP_CONV: {
-      SRP_CUDA_TRY(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
+      SRP_LAUNCH(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
                                     p->d_A_lo, s));
       SRP_MARK(p, 2, s);
       SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, nullptr, nullptr,
@@ -167,15 +178,15 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       break;
     }
     case SRP_SLRI: {
-      SRP_CUDA_TRY(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
+      SRP_LAUNCH(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
                                       g.L, p->d_twiddle, p->d_xi, s));
       SRP_MARK(p, 2, s);
       const int Rp = (p->R + 7) / 8 * 8;
-      SRP_CUDA_TRY(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
+      SRP_LAUNCH(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
       if (p->op == OpType::F32) {
-        SRP_CUDA_TRY(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
+        SRP_LAUNCH(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
       } else {
-        SRP_CUDA_TRY(launch_pack16(p->d_U, F, Rp, kSlriKd, std::ldexp(1.f, -p->slri_exp), p->op,
+        SRP_LAUNCH(launch_pack16(p->d_U, F, Rp, kSlriKd, std::ldexp(1.f, -p->slri_exp), p->op,
                                    p->d_A, p->d_A_lo, s));
         SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, kSlriKd, nullptr, nullptr,
                               F, maps, s));
@@ -185,14 +196,14 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     case SRP_SSPI:
     case SRP_SI:
     case SRP_TD: {
-      SRP_CUDA_TRY(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
+      SRP_LAUNCH(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
                                       g.L, p->d_twiddle, p->d_xi, s));
       SRP_MARK(p, 2, s);
       if (p->desc.method == SRP_SSPI && p->op == OpType::F32) {
-        SRP_CUDA_TRY(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
+        SRP_LAUNCH(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
                                  p->num_sms, s));
       } else {
-        SRP_CUDA_TRY(launch_pack16(p->d_xi, F, g.L, p->Lpad, 1.f, p->op, p->d_A, p->d_A_lo, s));
+        SRP_LAUNCH(launch_pack16(p->d_xi, F, g.L, p->Lpad, 1.f, p->op, p->d_A, p->d_A_lo, s));
         SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, p->Lpad, p->d_kb_ptr,
                               p->d_kb_idx, F, maps, s));
       }
@@ -202,7 +213,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       return fail(SRP_EINVAL, "unknown method");
   }
   SRP_MARK(p, 3, s);
-  if (argmax) SRP_CUDA_TRY(launch_argmax_finalize(p->d_keys, argmax, F, s));
+  if (argmax) SRP_LAUNCH(launch_argmax_finalize(p->d_keys, argmax, F, s));
   SRP_MARK(p, 4, s);
   if (p->profiling && p->chunks_recorded < kMaxChunkEvents) ++p->chunks_recorded;
   return SRP_OK;
@@ -509,6 +520,7 @@ extern "C" srp_status srp_plan_info(srp_plan_t plan, srp_plan_info_t* info) {
   info->tied_at_cut = plan->tied;
   info->device_bytes = plan->device_bytes;
   info->fit_seconds = plan->fit_seconds;
+  info->launches = plan->launches;
   return SRP_OK;
 }
 
@@ -594,6 +606,7 @@ extern "C" srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int 
   const Geometry& g = plan->g;
   for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
     const int nf = std::min(plan->Fmax, F - c0);
+    plan->launches += 2;
     SRP_CUDA_TRY(launch_stft_phat(frames + static_cast<size_t>(c0) * g.M * g.N, nf, g.M, g.N,
                                   plan->d_window, plan->d_twiddle, plan->d_yhat, s));
     SRP_CUDA_TRY(launch_gcc_samples(plan->d_yhat, nf, g.M, g.P, g.N, plan->d_pairs, plan->d_Np,

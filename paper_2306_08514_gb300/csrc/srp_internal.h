@@ -181,6 +181,7 @@ struct srp_plan_s {
   int* d_stage_arg = nullptr;
   size_t device_bytes = 0;
   double fit_seconds = 0;
+  long long launches = 0;  // kernels launched by srp_map / srp_map_host / srp_gcc_samples
   // per-stage timing: 5 events per internal chunk of the last call
   bool profiling = false;
   std::vector<cudaEvent_t> events;
