@@ -2,6 +2,7 @@
 // per-call launch sequence of the SRP path.
 #include "srp_internal.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -154,6 +155,17 @@ cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void*
   return launch_tc_gemm(tg, p->num_sms, s);
 }
 
+// Sampling stage (Eq. xi_p_ifft / xi_computed): direct summation for short lag windows,
+// the two-pairs-per-iFFT kernel otherwise.
+cudaError_t sample_gcc(srp_plan_s* p, const float2* yhat, int F, float* xi, cudaStream_t s) {
+  const Geometry& g = p->g;
+  if (p->max_Np <= gcc_direct_max_lag())
+    return launch_gcc_direct(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L,
+                             p->max_Np, p->d_twiddle, xi, s);
+  return launch_gcc_samples(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L,
+                            p->d_twiddle, xi, s);
+}
+
 // A counted kernel launch of the per-call path.
 #define SRP_LAUNCH(expr)  \
   do {                    \
@@ -178,8 +190,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       break;
     }
     case SRP_SLRI: {
-      SRP_LAUNCH(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
-                                      g.L, p->d_twiddle, p->d_xi, s));
+      SRP_LAUNCH(sample_gcc(p, p->d_yhat, F, p->d_xi, s));
       SRP_MARK(p, 2, s);
       const int Rp = (p->R + 7) / 8 * 8;
       SRP_LAUNCH(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
@@ -196,8 +207,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     case SRP_SSPI:
     case SRP_SI:
     case SRP_TD: {
-      SRP_LAUNCH(launch_gcc_samples(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off,
-                                      g.L, p->d_twiddle, p->d_xi, s));
+      SRP_LAUNCH(sample_gcc(p, p->d_yhat, F, p->d_xi, s));
       SRP_MARK(p, 2, s);
       if (p->desc.method == SRP_SSPI && p->op == OpType::F32) {
         SRP_LAUNCH(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
@@ -272,6 +282,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
           : desc->precision == SRP_FP16 ? OpType::F16
                                         : OpType::F16X2;
   p->Lpad = (g.L + kSlriKd - 1) / kSlriKd * kSlriKd;
+  p->max_Np = *std::max_element(g.Np.begin(), g.Np.end());
   if (desc->method == SRP_SI || desc->method == SRP_TD ||
       (desc->method == SRP_SSPI && p->op != OpType::F32)) {
     const double bbytes = static_cast<double>(g.J) * p->Lpad * op_bytes(p->op) *
@@ -609,9 +620,7 @@ extern "C" srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int 
     plan->launches += 2;
     SRP_CUDA_TRY(launch_stft_phat(frames + static_cast<size_t>(c0) * g.M * g.N, nf, g.M, g.N,
                                   plan->d_window, plan->d_twiddle, plan->d_yhat, s));
-    SRP_CUDA_TRY(launch_gcc_samples(plan->d_yhat, nf, g.M, g.P, g.N, plan->d_pairs, plan->d_Np,
-                                    plan->d_off, g.L, plan->d_twiddle,
-                                    xi + static_cast<size_t>(c0) * g.L, s));
+    SRP_CUDA_TRY(sample_gcc(plan, plan->d_yhat, nf, xi + static_cast<size_t>(c0) * g.L, s));
   }
   return SRP_OK;
 }

@@ -140,6 +140,99 @@ cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, c
 }
 
 // ---------------------------------------------------------------------------------
+// Sampling by direct summation, for short lag windows (N_p <= NQ): the same samples as
+// the iFFT route, xi_p(n) = 2 sum_{k=1}^{K-1} Re[psi_p(k) e^{j pi k n / K}] (Eq.
+// xi_computed with the sampling matrix S_p of Eq. S_p), evaluated as
+//   xi_p(+-n) = 2 (C_n -+ S_n),  C_n = sum_k Re psi cos(pi k n/K),  S_n = sum_k Im psi sin(..)
+// One CTA per frame, one warp per pair (strided), lanes over bins.  e^{j pi k n / K} is
+// advanced by a rotation per lag and re-anchored from the twiddle table every 8 lags.
+// No barrier and no shared memory: a frame's y-hat (M*K*8 bytes) stays in L1.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float2 tw_pos(const float2* __restrict__ tw, int u, int K) {
+  // e^{+j pi u / K} for 0 <= u < 2K from tw[t] = e^{-j pi t / K}, t < K
+  const float2 w = __ldg(tw + (u < K ? u : u - K));
+  return u < K ? make_float2(w.x, -w.y) : make_float2(-w.x, w.y);
+}
+
+template <int NQ>
+__global__ __launch_bounds__(256) void gcc_direct_kernel(const float2* __restrict__ yhat, int M,
+                                                         int P, int K, const int2* __restrict__ pairs,
+                                                         const int* __restrict__ Np,
+                                                         const int* __restrict__ off, int L,
+                                                         const float2* __restrict__ tw,
+                                                         float* __restrict__ xi) {
+  const int f = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float2* yf = yhat + static_cast<size_t>(f) * M * K;
+  const int twoK = 2 * K;
+  for (int q = warp; q < P; q += nw) {
+    const int nq = Np[q];
+    const int2 pr = pairs[q];
+    float c[NQ + 1], sn[NQ + 1];
+#pragma unroll
+    for (int n = 0; n <= NQ; ++n) c[n] = sn[n] = 0.f;
+    for (int k = 1 + lane; k < K; k += 32) {
+      const float2 psi = cmul_conj(__ldg(yf + pr.x * K + k), __ldg(yf + pr.y * K + k));
+      const float2 step = tw_pos(tw, k, K);
+      float2 e = make_float2(1.f, 0.f);
+      c[0] += psi.x;
+#pragma unroll
+      for (int n = 1; n <= NQ; ++n) {
+        if (n > nq) break;
+        if ((n & 7) == 0) {
+          e = tw_pos(tw, (k * n) & (twoK - 1), K);
+        } else {
+          e = cmul(e, step);
+        }
+        c[n] = fmaf(psi.x, e.x, c[n]);
+        sn[n] = fmaf(psi.y, e.y, sn[n]);
+      }
+    }
+#pragma unroll
+    for (int n = 0; n <= NQ; ++n) {
+      if (n > nq) break;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        c[n] += __shfl_xor_sync(0xFFFFFFFFu, c[n], o);
+        sn[n] += __shfl_xor_sync(0xFFFFFFFFu, sn[n], o);
+      }
+    }
+    float* out = xi + static_cast<size_t>(f) * L + off[q] + nq;  // lag 0
+#pragma unroll
+    for (int n = 0; n <= NQ; ++n) {
+      if (n > nq) break;
+      if (lane == n % 32) {
+        out[n] = 2.f * (c[n] - sn[n]);
+        if (n > 0) out[-n] = 2.f * (c[n] + sn[n]);
+      }
+    }
+  }
+}
+
+int gcc_direct_max_lag() { return 32; }
+
+cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                              const int* Np, const int* off, int L, int max_Np,
+                              const float2* twiddle, float* xi, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  const int K = N / 2;
+  const int threads = P >= 8 ? 256 : 32 * P;
+#define SRP_GD(NQV)                                                                         \
+  gcc_direct_kernel<NQV><<<F, threads, 0, s>>>(yhat, M, P, K, pairs, Np, off, L, twiddle, xi)
+  if (max_Np <= 8) {
+    SRP_GD(8);
+  } else if (max_Np <= 16) {
+    SRP_GD(16);
+  } else if (max_Np <= 32) {
+    SRP_GD(32);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+#undef SRP_GD
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
 // conv. FD-SRP operand A [F][P*N]: row f holds, per pair, Re psi_p(k) at p*N + k and
 // Im psi_p(k) at p*N + K + k (k = 0..K-1, psi(0) = 0).  With B[i] = [2cos, -2sin]
 // (launch_conv_matrix) the dot product is 2 Re[H_p psi_p] summed over pairs.

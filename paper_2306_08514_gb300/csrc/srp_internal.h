@@ -61,6 +61,11 @@ cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const flo
 cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N,
                                const int2* pairs, const int* Np, const int* off, int L,
                                const float2* twiddle, float* xi, cudaStream_t s);
+// The same samples by direct summation over the bins (N_p <= gcc_direct_max_lag()).
+int gcc_direct_max_lag();
+cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                              const int* Np, const int* off, int L, int max_Np,
+                              const float2* twiddle, float* xi, cudaStream_t s);
 // Cross-spectra packed as the conv GEMM operand A [F][P*N]:
 // A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
 enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3 /* hi + lo planes */ };
@@ -145,7 +150,8 @@ struct srp_plan_s {
   int num_sms = 0;
   srp::OpType op = srp::OpType::F32;
   int Lpad = 0;       // L rounded up to a multiple of 64 (dense interpolation operands)
-  int slri_exp = 0;   // tensor-core SLRI: u is scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp
+  int slri_exp = 0;
+  int max_Np = 0;     // largest N_p over the pairs   // tensor-core SLRI: u is scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp
   std::vector<double> sigma;
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
   std::vector<int> h_col;

@@ -47,14 +47,18 @@ def check_argmax(z, am, zo):
 
 
 # ------------------------------------------------------------------ sampling stage
-@pytest.mark.parametrize("N", [256, 512, 1024, 2048])
-def test_gcc_samples_match_oracle(S, N):
-    """Eq. xi_p_ifft / n_prime on the GPU vs the oracle's iFFT sampling."""
-    mics = synth.mics_square()
+@pytest.mark.parametrize("N,half", [(256, 0.1), (512, 0.1), (1024, 0.1), (2048, 0.1),
+                                    (512, 0.02), (512, 0.2), (1024, 0.2), (512, 1.0), (1024, 1.0),
+                                    (2048, 1.5)])
+def test_gcc_samples_match_oracle(S, N, half):
+    """Eq. xi_p_ifft / n_prime on the GPU vs the oracle's iFFT sampling.  Square arrays of
+    half-side `half` give max N_p of 4 (0.02), 15 (0.1), 28 (0.2) -- direct summation with 8,
+    16 and 32 lag registers -- and 135 / 201 (1.0 / 1.5): the iFFT kernel."""
+    mics = synth.mics_square(half=half)
     grid = synth.grid_plane((1, 1), (3, 3), (8, 8))
     g = synth.rng(N)
     frames = g.standard_normal((37, 4, N)).astype(np.float32)
-    plan = S.Plan(mics, grid, 16000.0, N, method="sspi", taps=1.0, max_frames=16)
+    plan = S.Plan(mics, grid, 16000.0, N, method="si", max_frames=16)
     import torch
     xi = plan.gcc_samples(_cuda(frames)).cpu().numpy()
     torch.cuda.synchronize()
