@@ -56,6 +56,9 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--sessions", type=int, default=64)
+    ap.add_argument("--seconds", type=float, default=10.0)
     return ap.parse_args(argv)
 
 
@@ -401,10 +404,175 @@ def run_libsrp(a):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------
+def serving_sessions(n, seed=1005, Ms=(4, 8, 16, 32)):
+    """Seeded session mix of the serving workload: per session M in Ms (geometries of the
+    square4 / uca8 / walls16 / nested32 workloads), J log-uniform in [2500, 100000] (box
+    grids over the workload's room, or a plane grid for the square), N in {512, 1024}
+    (1024 where the array needs it), hop 256, SLRI (R in {16, 32}) where L <= 768, else
+    SSPI (t in {2, 4}); a white source at a random position plus 20 dB sensor noise."""
+    import synth
+    g = synth.rng(seed)
+    out = []
+    for i in range(n):
+        M = int(g.choice(Ms))
+        J = int(round(np.exp(g.uniform(np.log(2500), np.log(100000)))))
+        N = int(g.choice([512, 1024]))
+        if M == 4:
+            mics = synth.mics_square()
+            side = int(round(np.sqrt(J)))
+            grid = synth.grid_plane((0.0, 0.0), (4.0, 4.0), (side, side))
+            room = (4.0, 4.0, 0.0)
+        elif M == 8:
+            mics = synth.mics_uca(8, 0.05, (2.5, 2.0, 1.5))
+            room = (5.0, 4.0, 3.0)
+        elif M == 16:
+            room = (6.0, 4.0, 3.0)
+            mics = synth.mics_walls(g, room)
+            N = 1024
+        else:
+            mics = synth.mics_nested_uca(16, 0.04, 16, 0.12, (2.0, 1.5, 1.25))
+            room = (4.0, 3.0, 2.5)
+        if M != 4:
+            h = (np.prod(room) / J) ** (1.0 / 3.0)
+            grid = synth.grid_box((0, 0, 0), room, h)
+        d = np.linalg.norm(mics[:, None, :] - mics[None, :, :], axis=-1)
+        iu = np.triu_indices(M, 1)
+        L = int(np.sum(2 * (np.floor(d[iu] * 16000.0 / 340.0).astype(int) + 2) + 1))
+        if L <= 768 and g.uniform() < 0.5:
+            kw = dict(method="slri", rank=int(g.choice([16, 32])))
+        else:
+            kw = dict(method="sspi", taps=float(g.choice([2.0, 4.0])))
+        out.append(dict(M=M, mics=mics, grid=grid, N=N, hop=256, kw=kw, room=room,
+                        seed=seed * 1000 + i))
+    return out
+
+
+def session_signal(sess, seconds, fs=16000.0):
+    import synth
+    g = synth.rng(sess["seed"])
+    n = int(seconds * fs) + sess["N"]
+    lo = np.array([0.3, 0.3, 0.0 if sess["M"] == 4 else 0.3])
+    hi = np.maximum(np.array(sess["room"]) - 0.3, lo + 1e-3)
+    src = g.uniform(lo, hi)
+    x = synth.propagate([(synth.white(g, n), src)], fs, sess["mics"], n)
+    x = synth.add_noise_snr(x, g.standard_normal(x.shape), 20.0)
+    return np.ascontiguousarray(x.astype(np.float32))
+
+
+def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_batch=16,
+                Ms=(4, 8, 16, 32), quiet=False):
+    """Serving workload: `sessions` sessions with Poisson frame arrivals (`rate` frames/s
+    each) pushed in real time by a feeder thread, results drained (argmax and latency) by a
+    poller thread.  Returns the serving summary."""
+    import threading
+    import torch
+    import paper_2306_08514_gb300 as S
+    torch.cuda.set_device(0)
+    mix = serving_sessions(sessions, Ms=Ms)
+    # hop 256 at 16 kHz: 62.5 frames/s is real time; Poisson counts stay below 1.5x the mean
+    sigs = [session_signal(s, 1.5 * seconds * rate * s["hop"] / 16000.0 + 1.0) for s in mix]
+    free, total = torch.cuda.mem_get_info()
+    srv = S.Server(hbm_budget=int(0.6 * free), max_sessions=sessions, max_batch=max_batch,
+                   streams=8, slots_per_session=3, pending_frames=16 * max_batch)
+    t_build = time.perf_counter()
+    sids = [srv.open(s["mics"], s["grid"], 16000.0, s["N"], s["hop"], precision=precision, **s["kw"])
+            for s in mix]
+    while True:
+        infos = [srv.session_info(x)["state"] for x in sids]
+        if all(st == "active" for st in infos):
+            break
+        if time.perf_counter() - t_build > 600:
+            raise RuntimeError(f"sessions not admitted: {infos}")
+        time.sleep(0.05)
+    build_s = time.perf_counter() - t_build
+    # the first frame of every session (the window of N samples) before the clock starts
+    pos = []
+    for sid, s, x in zip(sids, mix, sigs):
+        srv.push(sid, x[:, :s["N"] - s["hop"]])
+        pos.append(s["N"] - s["hop"])
+    rng = np.random.default_rng(7)
+    events = []
+    for k, s in enumerate(mix):
+        t = rng.exponential(1.0 / rate)
+        while t < seconds:
+            events.append((t, k))
+            t += rng.exponential(1.0 / rate)
+    events.sort()
+    Js = [s["grid"].shape[0] for s in mix]
+    done = {"frames": 0, "cells": 0}
+    stop = threading.Event()
+
+    errors = {}
+
+    def poller():
+        while not stop.is_set():
+            for k, sid in enumerate(sids):
+                try:
+                    _, am, idx, lat = srv.poll(sid, max_frames=16 * max_batch, want_maps=False)
+                except S.SrpError as e:  # a failed session: record it, keep serving the rest
+                    errors.setdefault(k, str(e))
+                    continue
+                done["frames"] += len(idx)
+                done["cells"] += len(idx) * Js[k]
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    srv.reset_stats()
+    t0 = S.srp_server_now()
+    w0 = time.perf_counter()
+    refused = 0
+    for t, k in events:
+        while S.srp_server_now() < t0 + t:
+            time.sleep(0.0001)
+        s = mix[k]
+        seg = sigs[k][:, pos[k]:pos[k] + s["hop"]]
+        if k in errors:
+            continue
+        try:
+            while not srv.push(sids[k], seg, t0 + t):
+                refused += 1
+                time.sleep(0.0002)
+        except S.SrpError as e:
+            errors.setdefault(k, str(e))
+        pos[k] += s["hop"]
+    # let the last frames finish
+    deadline = time.perf_counter() + 30
+    while done["frames"] < len(events) and time.perf_counter() < deadline and not errors:
+        time.sleep(0.01)
+    wall = time.perf_counter() - w0
+    stop.set()
+    th.join()
+    st = srv.stats()
+    srv.close()
+    res = {"sessions": sessions, "seconds": seconds, "rate_frames_per_s_per_session": rate,
+           "precision": precision, "max_batch": max_batch, "frames": st["frames_done"],
+           "frames_expected": len(events), "cells_frames_per_s": done["cells"] / wall,
+           "frames_per_s": st["frames_done"] / wall,
+           "latency_p50_ms": 1e3 * st["latency_p50_s"], "latency_p99_ms": 1e3 * st["latency_p99_s"],
+           "latency_max_ms": 1e3 * st["latency_max_s"], "launches": st["launches"],
+           "graph_launches": st["graph_launches"],
+           "mean_frames_per_launch": st["frames_launched"] / max(1, st["launches"]),
+           "admission_build_s": build_s, "push_retries": refused,
+           "failed_sessions": {str(k): v for k, v in errors.items()},
+           "mix": {"M": [s["M"] for s in mix], "J": Js, "N": [s["N"] for s in mix],
+                   "method": [s["kw"]["method"] for s in mix]}}
+    return res
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serving:
+        res = run_serving(a, sessions=a.sessions, seconds=a.seconds, precision=a.precision)
+        out = {"metric": "serving: map cells*frames/s and frame-to-map latency", "value": res["cells_frames_per_s"],
+               "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": a.precision,
+               "data": "synthetic", "config": {"workload": f"serving: {a.sessions} sessions, Poisson "
+                                               f"62.5 frames/s each, {a.seconds} s"},
+               "serving": res}
+        print(json.dumps(out), flush=True)
     else:
         run_libsrp(a)
 

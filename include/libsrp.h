@@ -51,7 +51,8 @@ typedef enum {
   SRP_ENOMEM = 2,       /* a device or host allocation failed */
   SRP_ECUDA = 3,        /* a CUDA runtime call failed (message carries its text) */
   SRP_ETIMEOUT = 4,     /* a bounded wait ran out */
-  SRP_EUNSUPPORTED = 5  /* valid request this build does not implement */
+  SRP_EUNSUPPORTED = 5, /* valid request this build does not implement */
+  SRP_EAGAIN = 6        /* a bounded queue is full: retry after draining results */
 } srp_status;
 
 typedef enum {
@@ -139,6 +140,15 @@ typedef struct {
  * above 200 GB), SRP_ENOMEM, SRP_ECUDA.
  */
 srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out);
+
+/*
+ * srp_plan_estimate_bytes -- device memory a plan for `desc` would hold (tables, operands
+ * and scratch for desc->max_frames frames), computed on the host from the pair distances
+ * without building anything; used to admit work by HBM footprint.  The estimate covers
+ * the allocations of srp_plan_create (within a few KB) but not the staging buffers that
+ * srp_map_host adds on its first call.  Errors: SRP_EINVAL (as srp_plan_create).
+ */
+srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t* bytes);
 
 /* srp_plan_info -- sizes and memory of a plan.  info: host, written. */
 srp_status srp_plan_info(srp_plan_t plan, srp_plan_info_t* info);
@@ -248,6 +258,95 @@ srp_status srp_plan_status(srp_plan_t plan, void* stream);
  */
 srp_status srp_slri_apply_static(const float* xi, const float* fat, const float* tall, int F,
                                  int L, int R, int J, float* maps, int* argmax, void* stream);
+
+/* ==================================================================================
+ * Serving: many concurrent sessions on one GPU (the paper has no serving layer; this is
+ * the runtime around the per-frame path above).  A session is one microphone array with
+ * its own plan description (geometry, grid, method, rank / taps, precision) and hop size.
+ *   - Admission by HBM footprint: srp_server_open queues the session; a builder thread
+ *     creates its plan once srp_plan_estimate_bytes + its launch buffers fit into
+ *     hbm_budget next to the admitted sessions and fewer than max_sessions are active.
+ *     Sessions are admitted in arrival order.
+ *   - srp_server_push appends samples; frames of N samples are cut every `hop` samples
+ *     (the last N - hop samples of each channel carry over) and queue as pending.
+ *   - Continuous batching: a scheduler thread moves each session's pending frames (up to
+ *     max_batch, a power of two) into a free launch slot as soon as one is free; frames
+ *     arriving meanwhile join a later launch.  Sessions are spread round-robin over
+ *     `streams` CUDA streams, so their launches overlap on the device.
+ *   - use_graphs: each (slot, batch size) launch sequence -- H2D frames, the SRP path,
+ *     D2H maps and argmax, a completion callback -- is captured once and replayed.
+ *   - Latency of a frame = completion of its map's D2H copy - its arrival time (the time
+ *     its last sample was pushed, or the caller's t_arrival).
+ * All functions are thread-safe.  The server owns its threads, streams and buffers.
+ * ================================================================================== */
+typedef struct srp_server_s* srp_server_t;
+
+typedef struct {
+  size_t hbm_budget;      /* device bytes the sessions may hold together */
+  int max_sessions;       /* active sessions at most, 1..4096 */
+  int max_batch;          /* frames per launch, a power of two in 1..4096 */
+  int streams;            /* CUDA streams the sessions are spread over, 1..64 */
+  int slots_per_session;  /* launches a session may have in flight or awaiting poll, 1..16 */
+  int pending_frames;     /* pending-frame queue per session (>= max_batch) */
+  int use_graphs;         /* 1: replay captured CUDA graphs; 0: issue launches directly */
+} srp_server_desc;
+
+typedef struct {
+  long long frames_done;      /* frames whose maps were returned by srp_server_poll */
+  long long frames_launched;  /* frames submitted to the GPU */
+  long long launches;         /* batch launches (each: one srp_map of b frames) */
+  long long graph_launches;   /* of which replayed CUDA graphs */
+  size_t device_bytes;        /* device memory held (or reserved) by admitted sessions */
+  int sessions_active, sessions_queued;
+  double latency_p50_s, latency_p99_s, latency_max_s;  /* over frames polled since reset */
+} srp_server_stats_t;
+
+enum { SRP_SESSION_QUEUED = 0, SRP_SESSION_ACTIVE = 1, SRP_SESSION_CLOSING = 2,
+       SRP_SESSION_CLOSED = 3, SRP_SESSION_FAILED = 4 };
+
+/* srp_server_create -- start a server on the current device.  desc: host, read.
+ * Errors: SRP_EINVAL (a field out of range), SRP_ECUDA. */
+srp_status srp_server_create(const srp_server_desc* desc, srp_server_t* out);
+
+/* srp_server_open -- queue a session.  desc: as for srp_plan_create (copied;
+ * desc->max_frames must be >= max_batch); hop: 1..N samples between frames.
+ * session: receives the id.  Errors: SRP_EINVAL, SRP_ENOMEM (the session alone exceeds
+ * hbm_budget).  A plan that fails to build puts the session in SRP_SESSION_FAILED. */
+srp_status srp_server_open(srp_server_t server, const srp_plan_desc* desc, int hop, int* session);
+
+/* srp_server_push -- append n samples per channel.  samples: host float [M][n] (channel
+ * major), copied.  t_arrival: arrival time in seconds on the steady clock of
+ * srp_server_now, or < 0 for now.  Errors: SRP_EAGAIN (the pending queue would
+ * overflow: poll and retry), SRP_EINVAL (unknown or closed session), SRP_ECUDA (failed). */
+srp_status srp_server_push(srp_server_t server, int session, const float* samples, int n,
+                           double t_arrival);
+
+/* srp_server_poll -- take the session's finished frames, oldest first, whole launches
+ * only.  max_frames >= max_batch.  maps: host float [max_frames][J] or NULL; argmax,
+ * frame_index (0-based frame number of the session's stream), latency_s: host arrays of
+ * max_frames or NULL.  *n_out receives the number of frames written. */
+srp_status srp_server_poll(srp_server_t server, int session, int max_frames, float* maps,
+                           int* argmax, long long* frame_index, double* latency_s, int* n_out);
+
+/* srp_server_session_info -- state (SRP_SESSION_*), device bytes held, frames pending or in
+ * flight.  Returns SRP_ECUDA with the failure message for a failed session. */
+srp_status srp_server_session_info(srp_server_t server, int session, int* state,
+                                   size_t* device_bytes, int* pending);
+
+/* srp_server_close -- stop a session: pending frames and unpolled results are dropped and
+ * its memory is released once its launches in flight finish (queued sessions may then be
+ * admitted). */
+srp_status srp_server_close(srp_server_t server, int session);
+
+/* srp_server_stats / srp_server_reset_stats -- counters and latency percentiles. */
+srp_status srp_server_stats(srp_server_t server, srp_server_stats_t* stats);
+srp_status srp_server_reset_stats(srp_server_t server);
+
+/* srp_server_now -- the clock of t_arrival and of the latencies, in seconds. */
+double srp_server_now(void);
+
+/* srp_server_destroy -- stop the threads, wait for launches in flight, free everything. */
+void srp_server_destroy(srp_server_t server);
 
 /* srp_destroy -- release a plan and its device memory (synchronises the device). */
 void srp_destroy(srp_plan_t plan);

@@ -13,7 +13,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsrp.so")
 
-SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_ETIMEOUT, SRP_EUNSUPPORTED = range(6)
+SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_ETIMEOUT, SRP_EUNSUPPORTED, SRP_EAGAIN = 0, 1, 2, 3, 4, 5, 6
 SRP_CONV, SRP_SLRI, SRP_SSPI, SRP_SI, SRP_TD = 0, 1, 2, 3, 4
 SRP_FP32, SRP_BF16, SRP_FP16, SRP_FP16X3 = 0, 1, 2, 4
 SRP_WIN_HANN, SRP_WIN_SQRT_HANN, SRP_WIN_RECT = 0, 1, 2
@@ -41,6 +41,25 @@ class srp_plan_info_t(C.Structure):
     ]
 
 
+class srp_server_desc(C.Structure):
+    _fields_ = [
+        ("hbm_budget", C.c_size_t), ("max_sessions", C.c_int), ("max_batch", C.c_int),
+        ("streams", C.c_int), ("slots_per_session", C.c_int), ("pending_frames", C.c_int),
+        ("use_graphs", C.c_int),
+    ]
+
+
+class srp_server_stats_t(C.Structure):
+    _fields_ = [
+        ("frames_done", C.c_longlong), ("frames_launched", C.c_longlong),
+        ("launches", C.c_longlong), ("graph_launches", C.c_longlong),
+        ("device_bytes", C.c_size_t), ("sessions_active", C.c_int), ("sessions_queued", C.c_int),
+        ("latency_p50_s", C.c_double), ("latency_p99_s", C.c_double), ("latency_max_s", C.c_double),
+    ]
+
+
+SESSION_STATES = {0: "queued", 1: "active", 2: "closing", 3: "closed", 4: "failed"}
+
 # every symbol include/libsrp.h declares, with (restype, argtypes)
 SIGNATURES = {
     "srp_plan_create": (C.c_int, [C.POINTER(srp_plan_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -57,6 +76,19 @@ SIGNATURES = {
     "srp_plan_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "srp_slri_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                         C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "srp_plan_estimate_bytes": (C.c_int, [C.POINTER(srp_plan_desc), C.POINTER(C.c_size_t)]),
+    "srp_server_create": (C.c_int, [C.POINTER(srp_server_desc), C.POINTER(C.c_void_p)]),
+    "srp_server_open": (C.c_int, [C.c_void_p, C.POINTER(srp_plan_desc), C.c_int, C.POINTER(C.c_int)]),
+    "srp_server_push": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double]),
+    "srp_server_poll": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.POINTER(C.c_int)]),
+    "srp_server_session_info": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                          C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "srp_server_close": (C.c_int, [C.c_void_p, C.c_int]),
+    "srp_server_stats": (C.c_int, [C.c_void_p, C.POINTER(srp_server_stats_t)]),
+    "srp_server_reset_stats": (C.c_int, [C.c_void_p]),
+    "srp_server_now": (C.c_double, []),
+    "srp_server_destroy": (None, [C.c_void_p]),
     "srp_destroy": (None, [C.c_void_p]),
     "srp_last_error": (C.c_char_p, []),
 }
@@ -273,6 +305,98 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             srp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- serving ----------------------------------------------------------------------
+def srp_plan_estimate_bytes(desc: srp_plan_desc) -> int:
+    b = C.c_size_t()
+    _check(lib().srp_plan_estimate_bytes(C.byref(desc), C.byref(b)))
+    return b.value
+
+
+def srp_server_now() -> float:
+    return lib().srp_server_now()
+
+
+class Server:
+    """Many concurrent SRP sessions on the current CUDA device (libsrp's serving runtime):
+    admission by HBM footprint, host framing with overlap, continuous batching over
+    streams, CUDA-graph replay.  Host numpy in, host numpy out."""
+
+    def __init__(self, hbm_budget=8 << 30, max_sessions=64, max_batch=16, streams=8,
+                 slots_per_session=2, pending_frames=None, use_graphs=True):
+        d = srp_server_desc()
+        d.hbm_budget, d.max_sessions, d.max_batch = int(hbm_budget), int(max_sessions), int(max_batch)
+        d.streams, d.slots_per_session = int(streams), int(slots_per_session)
+        d.pending_frames = int(pending_frames or 8 * max_batch)
+        d.use_graphs = 1 if use_graphs else 0
+        self.desc = d
+        self.handle = C.c_void_p()
+        _check(lib().srp_server_create(C.byref(d), C.byref(self.handle)))
+        self.sessions = {}
+
+    def open(self, mic_xyz, grid_xyz, fs, N, hop, method="slri", rank=0, taps=0.0,
+             precision="bf16", window="hann", c=340.0, n_aux=2):
+        desc = make_desc(mic_xyz, grid_xyz, fs, N, method, rank, taps, precision, window, c,
+                         n_aux, max_frames=self.desc.max_batch)
+        sid = C.c_int()
+        _check(lib().srp_server_open(self.handle, C.byref(desc), int(hop), C.byref(sid)))
+        self.sessions[sid.value] = (desc.M, desc.J)
+        return sid.value
+
+    def push(self, sid, samples, t_arrival=-1.0):
+        """samples: [M][n] float32 (channel major).  Returns False if the queue is full."""
+        a = np.ascontiguousarray(samples, dtype=np.float32)
+        st = lib().srp_server_push(self.handle, sid, C.c_void_p(a.ctypes.data), a.shape[1],
+                                   float(t_arrival))
+        if st == SRP_EAGAIN:
+            return False
+        _check(st)
+        return True
+
+    def poll(self, sid, max_frames=None, want_maps=True):
+        """-> (maps [n][J] or None, argmax [n], frame_index [n], latency_s [n])"""
+        M, J = self.sessions[sid]
+        n = int(max_frames or 4 * self.desc.max_batch)
+        maps = np.empty((n, J), np.float32) if want_maps else None
+        am = np.empty((n,), np.int32)
+        idx = np.empty((n,), np.int64)
+        lat = np.empty((n,), np.float64)
+        got = C.c_int()
+        _check(lib().srp_server_poll(self.handle, sid, n,
+                                     C.c_void_p(maps.ctypes.data) if want_maps else None,
+                                     C.c_void_p(am.ctypes.data), C.c_void_p(idx.ctypes.data),
+                                     C.c_void_p(lat.ctypes.data), C.byref(got)))
+        k = got.value
+        return (maps[:k] if want_maps else None), am[:k], idx[:k], lat[:k]
+
+    def session_info(self, sid):
+        st, b, pend = C.c_int(), C.c_size_t(), C.c_int()
+        _check(lib().srp_server_session_info(self.handle, sid, C.byref(st), C.byref(b), C.byref(pend)))
+        return {"state": SESSION_STATES.get(st.value, st.value), "device_bytes": b.value,
+                "pending": pend.value}
+
+    def close_session(self, sid):
+        _check(lib().srp_server_close(self.handle, sid))
+
+    def stats(self):
+        s = srp_server_stats_t()
+        _check(lib().srp_server_stats(self.handle, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def reset_stats(self):
+        _check(lib().srp_server_reset_stats(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().srp_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -304,6 +304,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   // ---- device part
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   SRP_PLAN_CUDA(p, cudaGetDevice(&p->device));
+  if (p->op != OpType::F32) SRP_PLAN_CUDA(p, tc_gemm_prepare());
   SRP_PLAN_CUDA(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
   std::vector<int2> pairs(g.P);
   for (int q = 0; q < g.P; ++q) pairs[q] = make_int2(g.pm[q], g.pmp[q]);
@@ -513,6 +514,60 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   p->g.tau.shrink_to_fit();
   p->fit_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t* bytes) {
+  clear_error();
+  if (!bytes) return fail(SRP_EINVAL, "bytes is NULL");
+  srp_status st = validate(desc);
+  if (st != SRP_OK) return st;
+  const srp_plan_desc& d = *desc;
+  // N_p and L from the pair distances (Eq. N_p), without the TDOA table.
+  long long L = 0;
+  int maxNp = 0;
+  for (int mp = 0; mp < d.M - 1; ++mp)
+    for (int m = mp + 1; m < d.M; ++m) {
+      const double* a = d.mic_xyz + 3 * m;
+      const double* b = d.mic_xyz + 3 * mp;
+      const double dist = std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
+                                    (a[2] - b[2]) * (a[2] - b[2]));
+      const int np = static_cast<int>(std::floor(dist / d.c * d.fs)) + d.n_aux;
+      maxNp = std::max(maxNp, np);
+      L += 2 * np + 1;
+    }
+  if (maxNp >= d.N / 2) return fail(SRP_EINVAL, "N_p >= K: the sample window is wider than the frame");
+  const double J = d.J, P = d.M * (d.M - 1) / 2.0, N = d.N, K = d.N / 2.0, F = d.max_frames;
+  const double eb = d.precision == SRP_FP32 ? 4.0 : 2.0;
+  const double planes = d.precision == SRP_FP16X3 ? 2.0 : 1.0;
+  const double Lpad = std::ceil(L / 64.0) * 64.0;
+  double b = F * d.M * K * 8.0 + F * 8.0 + 4096.0;  // y-hat, argmax keys, small tables
+  switch (d.method) {
+    case SRP_CONV:
+      b += (J + F) * P * N * eb * planes;
+      if (d.precision == SRP_FP32 && P * N > 16384) b += std::ceil(P * N / 16384.0) * F * J * 4.0;
+      break;
+    case SRP_SLRI: {
+      const double Rp = std::ceil(d.rank / 8.0) * 8.0;
+      b += F * L * 4.0 + (J + L + F) * Rp * 4.0;
+      if (d.precision != SRP_FP32) b += (J + F) * 64.0 * eb * planes;
+      break;
+    }
+    case SRP_SSPI: {
+      const double nnz = std::llround(d.taps_per_loc_pair * J * P);
+      b += F * L * 4.0;
+      if (d.precision == SRP_FP32)
+        b += nnz * 8.0 + (J + 1) * 8.0;
+      else
+        b += (J + F) * Lpad * eb * planes + (J / 256.0 + 1) * 4.0 + J / 256.0 * Lpad / 64.0 * 4.0;
+      break;
+    }
+    default:  // SI, TD
+      b += F * L * 4.0 + (J + F) * Lpad * eb * planes;
+      if (d.precision == SRP_FP32 && Lpad > 16384) b += std::ceil(Lpad / 16384.0) * F * J * 4.0;
+      break;
+  }
+  *bytes = static_cast<size_t>(b);
   return SRP_OK;
 }
 

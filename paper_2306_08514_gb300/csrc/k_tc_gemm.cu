@@ -382,6 +382,12 @@ size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms)
   return need;
 }
 
+cudaError_t tc_gemm_prepare() {
+  cudaError_t e = get_encode();
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
 int tc_gemm_cell_tile() { return TN; }
 int tc_gemm_k_block() { return TK; }
 

@@ -110,6 +110,9 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s);
 int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms);
 size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms);
 int tc_gemm_cell_tile();
+// Resolves the tensor-map encoder and sets the kernel's shared-memory attribute on the
+// current device (done at plan creation, so that later launches can be graph-captured).
+cudaError_t tc_gemm_prepare();
 int tc_gemm_k_block();
 
 // Operand preparation (k_pack.cu).  pack16: X [rows][C] FP32 -> [rows][Cpad] (zero
