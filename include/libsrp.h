@@ -123,7 +123,9 @@ typedef struct {
  *   SRP_CONV: the SRP matrix H of Eq. H_p_single/H_single, stored as the real
  *             matrix [2cos(w_k dt_p(i)) | -2sin(w_k dt_p(i))] in the precision asked;
  *   SRP_SLRI: Lambda (Eq. Lambda_p) -> its best rank-R approximation (Eq.
- *             min_Lambda_lr) from the eigen-decomposition of Lambda^T Lambda in FP64,
+ *             min_Lambda_lr) from the eigen-decomposition of Lambda^T Lambda in FP64
+ *             (L <= 768: Jacobi on the Gram matrix; longer: subspace iteration with
+ *             Rayleigh-Ritz whose products Lambda X, Lambda^T Y run on the device in FP64),
  *             Lambda_fat = V_R^T, Lambda_tall = Lambda V_R, stored FP32;
  *   SRP_SSPI: the Q_Lambda largest-magnitude entries of Lambda (Eq. min_Lambda_sp),
  *             magnitudes quantised to multiples of 2^-40 and ties broken by ascending
@@ -136,8 +138,8 @@ typedef struct {
  * stream: stream for the uploads; the call returns after they complete.
  * out:    receives the plan handle (NULL on failure).
  * Errors: SRP_EINVAL (bad desc, including N_p >= K), SRP_EUNSUPPORTED (size beyond
- * this build: SLRI with L > 768, the FP32 SSPI gather with L > 1700, a device operand
- * above 200 GB), SRP_ENOMEM, SRP_ECUDA.
+ * this build: the FP32 SSPI gather with L > 1700, a device operand above 200 GB, a
+ * low-rank fit that does not converge), SRP_ENOMEM, SRP_ECUDA.
  */
 srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out);
 
@@ -200,7 +202,8 @@ srp_status srp_plan_sspi_taps(srp_plan_t plan, long long* row_ptr, int* col, flo
 
 /*
  * srp_plan_slri_sigma -- the plan's singular values of Lambda (square roots of the
- * eigenvalues of Lambda^T Lambda, descending).  sigma: host double [n]; n <= L.
+ * eigenvalues of Lambda^T Lambda, descending).  sigma: host double [n]; n <= L when
+ * L <= 768, else n <= min(L, R + 32) (the values the subspace iteration resolves).
  * Errors: SRP_EINVAL (not an SLRI plan, n out of range).
  */
 srp_status srp_plan_slri_sigma(srp_plan_t plan, double* sigma, int n);

@@ -106,6 +106,9 @@ size_t op_bytes(OpType t) { return t == OpType::F32 ? 4 : 2; }
 // the multiple that pads L for the dense interpolation operands.
 constexpr int kSlriKd = 64;
 
+// Largest L for which the low-rank fit eigen-decomposes the L x L Gram matrix on the host.
+constexpr int kGramMaxL = 768;
+
 // One chunk of at most Fmax frames through the whole path.
 constexpr int kMaxChunkEvents = 4096;
 
@@ -256,11 +259,6 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       delete p;
       return fail(SRP_EINVAL, "rank must be in 1..min(64, J, L) (L = " + std::to_string(g.L) + ")");
     }
-    if (g.L > 768) {
-      delete p;
-      return fail(SRP_EUNSUPPORTED, "SLRI fit supports L <= 768 in this build (L = " +
-                                        std::to_string(g.L) + ")");
-    }
     p->R = desc->rank;
   }
   if (desc->method == SRP_SSPI) {
@@ -370,7 +368,10 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     const bool split = p->op == OpType::F16X2;
     if (desc->method == SRP_SLRI) {
       std::vector<float> tall, fat;
-      srp_status fst = fit_low_rank(g, p->R, tall, fat, p->sigma);
+      // exact Gram eigen-decomposition for short sample vectors, device subspace
+      // iteration beyond (the L x L Jacobi solve grows as L^3)
+      srp_status fst = g.L <= kGramMaxL ? fit_low_rank(g, p->R, tall, fat, p->sigma)
+                                        : fit_low_rank_device(g, p->R, tall, fat, p->sigma, s);
       if (fst != SRP_OK) {
         free_plan(p);
         return fst;

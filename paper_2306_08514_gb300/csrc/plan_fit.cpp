@@ -112,8 +112,8 @@ void lambda_row(const Geometry& g, int i, double* row) {
 // one off-diagonal element at a time, Jacobi 1846 / Rutishauser's formulation).
 // A: n x n row-major, destroyed.  V: eigenvectors as columns.  d: eigenvalues.
 // -----------------------------------------------------------------------------------
-static void jacobi_eigen(int n, std::vector<double>& A, std::vector<double>& V,
-                         std::vector<double>& d) {
+void jacobi_eigen(int n, std::vector<double>& A, std::vector<double>& V,
+                  std::vector<double>& d) {
   V.assign(static_cast<size_t>(n) * n, 0.0);
   for (int i = 0; i < n; ++i) V[static_cast<size_t>(i) * n + i] = 1.0;
   for (int sweep = 0; sweep < 100; ++sweep) {
@@ -238,128 +238,173 @@ srp_status fit_low_rank(const Geometry& g, int R, std::vector<float>& tall,
 // -----------------------------------------------------------------------------------
 // Eq. min_Lambda_sp: keep the nnz entries of largest magnitude.  Magnitudes are compared
 // as integer keys round(|lambda| * 2^40); ties at the cut are taken in ascending
-// (i, p, n) order, which is the row-major order of Lambda here.  Selection is done in
-// three streaming passes (histogram of key >> 24, exact cut inside the bucket, fill),
-// so Lambda is never stored.
+// (i, p, n) order, which is the row-major order of Lambda here.  Lambda is never stored.
+//
+// Window: |sinc(x)| <= 1 / (pi |x|), so every entry with |tau_p(i) - n| > W has a key of
+// at most k_out(W) = key(1 / (pi W)).  Selecting among the entries inside the window
+// (a subset) gives a cut key k_W <= the true cut; when k_out(W) + 2 < k_W no entry outside
+// the window can reach the cut and the selection inside the window is exact (ties
+// included: they all carry the key k_W and lie inside).  Otherwise W doubles, up to the
+// whole of Lambda.  The window makes the cost O(J P W) instead of O(J L).
+// Selection inside the window: histogram of key >> 24, exact cut inside the bucket,
+// per-row counts, fill -- all in parallel over rows.
 // -----------------------------------------------------------------------------------
 static inline uint64_t sparse_key(double v) {
   return static_cast<uint64_t>(std::floor(std::fabs(v) * 1099511627776.0 + 0.5));  // 2^40
 }
 
+// Calls fn(l, value) for the entries of row i with |tau_p(i) - n| <= W (all when W < 0),
+// in ascending column order.
+template <typename Fn>
+static inline void window_row(const Geometry& g, int i, double W, Fn&& fn) {
+  const double* t = g.tau.data() + static_cast<size_t>(i) * g.P;
+  for (int p = 0; p < g.P; ++p) {
+    const int np = g.Np[p];
+    int n0 = -np, n1 = np;
+    if (W >= 0) {
+      n0 = std::max(n0, static_cast<int>(std::ceil(t[p] - W)));
+      n1 = std::min(n1, static_cast<int>(std::floor(t[p] + W)));
+    }
+    for (int n = n0; n <= n1; ++n) {
+      const double x = t[p] - static_cast<double>(n);
+      fn(g.off[p] + n + np, sinc_pi(x));
+    }
+  }
+}
+
 srp_status fit_sparse(const Geometry& g, long long nnz, std::vector<long long>& row_ptr,
                       std::vector<int>& col, std::vector<float>& val, long long& tied) {
-  const int L = g.L, J = g.J;
+  const int J = g.J;
   const int SHIFT = 24;
   const size_t NB = (size_t(1) << 16) + 2;
   const unsigned T = host_threads();
-  // pass 1: histogram of the top key bits
-  std::vector<std::vector<long long>> hist(T, std::vector<long long>(NB, 0));
-  {
-    std::vector<std::thread> th;
-    const long long chunk = (J + T - 1) / T;
-    for (unsigned t = 0; t < T; ++t) {
-      th.emplace_back([&, t] {
-        std::vector<double> row(L);
-        const long long b = t * chunk, e = std::min<long long>(J, b + chunk);
-        for (long long i = b; i < e; ++i) {
-          lambda_row(g, static_cast<int>(i), row.data());
-          for (int l = 0; l < L; ++l) hist[t][sparse_key(row[l]) >> SHIFT]++;
-        }
-      });
+  int maxNp = 0;
+  for (int p = 0; p < g.P; ++p) maxNp = std::max(maxNp, g.Np[p]);
+  for (double W = 8.0;; W *= 2.0) {
+    const bool full = W > 2.0 * maxNp + 2.0;  // the window covers every lag
+    const double Wuse = full ? -1.0 : W;
+    // pass 1: histogram of the top key bits (and the candidate count)
+    std::vector<std::vector<long long>> hist(T, std::vector<long long>(NB, 0));
+    {
+      std::vector<std::thread> th;
+      const long long chunk = (J + T - 1) / T;
+      for (unsigned t = 0; t < T; ++t)
+        th.emplace_back([&, t] {
+          const long long b = t * chunk, e = std::min<long long>(J, b + chunk);
+          for (long long i = b; i < e; ++i)
+            window_row(g, static_cast<int>(i), Wuse,
+                       [&](int, double v) { hist[t][sparse_key(v) >> SHIFT]++; });
+        });
+      for (auto& x : th) x.join();
     }
-    for (auto& x : th) x.join();
-  }
-  std::vector<long long> H(NB, 0);
-  for (unsigned t = 0; t < T; ++t)
-    for (size_t b = 0; b < NB; ++b) H[b] += hist[t][b];
-  hist.clear();
-  long long above = 0;
-  size_t bstar = NB - 1;
-  for (size_t b = NB; b-- > 0;) {
-    if (above + H[b] >= nnz) {
-      bstar = b;
-      break;
+    std::vector<long long> H(NB, 0);
+    long long cand = 0;
+    for (unsigned t = 0; t < T; ++t)
+      for (size_t b = 0; b < NB; ++b) H[b] += hist[t][b];
+    hist.clear();
+    for (size_t b = 0; b < NB; ++b) cand += H[b];
+    if (cand < nnz) {
+      if (full) {
+        set_error("internal: fewer entries than Q_Lambda");
+        return SRP_EINVAL;
+      }
+      continue;
     }
-    above += H[b];
-  }
-  // pass 2: exact cut inside bucket bstar
-  std::vector<uint64_t> inb;
-  inb.reserve(static_cast<size_t>(H[bstar]));
-  {
-    std::vector<double> row(L);
+    long long above = 0;
+    size_t bstar = NB - 1;
+    for (size_t b = NB; b-- > 0;) {
+      if (above + H[b] >= nnz) {
+        bstar = b;
+        break;
+      }
+      above += H[b];
+    }
+    // pass 2: exact cut inside bucket bstar
+    std::vector<std::vector<uint64_t>> inb_t(T);
+    {
+      std::vector<std::thread> th;
+      const long long chunk = (J + T - 1) / T;
+      for (unsigned t = 0; t < T; ++t)
+        th.emplace_back([&, t] {
+          const long long b = t * chunk, e = std::min<long long>(J, b + chunk);
+          for (long long i = b; i < e; ++i)
+            window_row(g, static_cast<int>(i), Wuse, [&](int, double v) {
+              const uint64_t k = sparse_key(v);
+              if ((k >> SHIFT) == bstar) inb_t[t].push_back(k);
+            });
+        });
+      for (auto& x : th) x.join();
+    }
+    std::vector<uint64_t> inb;
+    inb.reserve(static_cast<size_t>(H[bstar]));
+    for (auto& v : inb_t) inb.insert(inb.end(), v.begin(), v.end());
+    inb_t.clear();
+    const long long need_in_bucket = nnz - above;  // >= 1
+    std::nth_element(inb.begin(), inb.begin() + (inb.size() - need_in_bucket), inb.end());
+    const uint64_t kth = inb[inb.size() - need_in_bucket];
+    if (!full) {
+      const uint64_t k_out = sparse_key(1.0 / (M_PI * W));
+      if (k_out + 2 >= kth) continue;  // an entry outside the window could reach the cut
+    }
+    long long gt_in_bucket = 0, eq = 0;
+    for (uint64_t k : inb) {
+      gt_in_bucket += (k > kth);
+      eq += (k == kth);
+    }
+    inb.clear();
+    inb.shrink_to_fit();
+    const long long take_ties = need_in_bucket - gt_in_bucket;
+    tied = eq;
+    // pass 3: per-row counts, then fill in row order with the tie budget
+    std::vector<int> cnt_gt(J, 0), cnt_eq(J, 0);
+    parallel_for(J, [&](long long b, long long e) {
+      for (long long i = b; i < e; ++i) {
+        int a = 0, q = 0;
+        window_row(g, static_cast<int>(i), Wuse, [&](int, double v) {
+          const uint64_t k = sparse_key(v);
+          a += (k > kth);
+          q += (k == kth);
+        });
+        cnt_gt[i] = a;
+        cnt_eq[i] = q;
+      }
+    });
+    std::vector<int> ties_row(J, 0);
+    long long budget = take_ties;
+    row_ptr.assign(static_cast<size_t>(J) + 1, 0);
     for (int i = 0; i < J; ++i) {
-      lambda_row(g, i, row.data());
-      for (int l = 0; l < L; ++l) {
-        const uint64_t k = sparse_key(row[l]);
-        if ((k >> SHIFT) == bstar) inb.push_back(k);
-      }
+      const int tk = static_cast<int>(std::min<long long>(budget, cnt_eq[i]));
+      ties_row[i] = tk;
+      budget -= tk;
+      row_ptr[i + 1] = row_ptr[i] + cnt_gt[i] + tk;
     }
-  }
-  const long long need_in_bucket = nnz - above;  // >= 1
-  std::nth_element(inb.begin(), inb.begin() + (inb.size() - need_in_bucket), inb.end());
-  const uint64_t kth = inb[inb.size() - need_in_bucket];
-  long long gt_in_bucket = 0, eq = 0;
-  for (uint64_t k : inb) {
-    gt_in_bucket += (k > kth);
-    eq += (k == kth);
-  }
-  inb.clear();
-  inb.shrink_to_fit();
-  const long long take_ties = need_in_bucket - gt_in_bucket;
-  tied = eq;
-  // pass 3: per-row counts (parallel), then fill in row order with the tie budget
-  std::vector<int> cnt_gt(J, 0), cnt_eq(J, 0);
-  parallel_for(J, [&](long long b, long long e) {
-    std::vector<double> row(L);
-    for (long long i = b; i < e; ++i) {
-      lambda_row(g, static_cast<int>(i), row.data());
-      int a = 0, q = 0;
-      for (int l = 0; l < L; ++l) {
-        const uint64_t k = sparse_key(row[l]);
-        a += (k > kth);
-        q += (k == kth);
-      }
-      cnt_gt[i] = a;
-      cnt_eq[i] = q;
+    if (row_ptr[J] != nnz) {
+      set_error("internal: sparse selection count mismatch");
+      return SRP_EINVAL;
     }
-  });
-  std::vector<int> ties_row(J, 0);
-  long long budget = take_ties;
-  row_ptr.assign(static_cast<size_t>(J) + 1, 0);
-  for (int i = 0; i < J; ++i) {
-    const int tk = static_cast<int>(std::min<long long>(budget, cnt_eq[i]));
-    ties_row[i] = tk;
-    budget -= tk;
-    row_ptr[i + 1] = row_ptr[i] + cnt_gt[i] + tk;
-  }
-  if (row_ptr[J] != nnz) {
-    set_error("internal: sparse selection count mismatch");
-    return SRP_EINVAL;
-  }
-  col.assign(static_cast<size_t>(nnz), 0);
-  val.assign(static_cast<size_t>(nnz), 0.f);
-  parallel_for(J, [&](long long b, long long e) {
-    std::vector<double> row(L);
-    for (long long i = b; i < e; ++i) {
-      lambda_row(g, static_cast<int>(i), row.data());
-      long long w = row_ptr[i];
-      int ties = ties_row[i];
-      for (int l = 0; l < L; ++l) {
-        const uint64_t k = sparse_key(row[l]);
-        bool keep = k > kth;
-        if (!keep && k == kth && ties > 0) {
-          keep = true;
-          --ties;
-        }
-        if (keep) {
-          col[w] = l;
-          val[w] = static_cast<float>(row[l]);
-          ++w;
-        }
+    col.assign(static_cast<size_t>(nnz), 0);
+    val.assign(static_cast<size_t>(nnz), 0.f);
+    parallel_for(J, [&](long long b, long long e) {
+      for (long long i = b; i < e; ++i) {
+        long long w = row_ptr[i];
+        int ties = ties_row[i];
+        window_row(g, static_cast<int>(i), Wuse, [&](int l, double v) {
+          const uint64_t k = sparse_key(v);
+          bool keep = k > kth;
+          if (!keep && k == kth && ties > 0) {
+            keep = true;
+            --ties;
+          }
+          if (keep) {
+            col[w] = l;
+            val[w] = static_cast<float>(v);
+            ++w;
+          }
+        });
       }
-    }
-  });
-  return SRP_OK;
+    });
+    return SRP_OK;
+  }
 }
 
 }  // namespace srp

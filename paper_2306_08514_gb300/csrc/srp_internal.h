@@ -47,6 +47,17 @@ void lambda_row(const Geometry& g, int i, double* row);
 srp_status fit_low_rank(const Geometry& g, int R, std::vector<float>& tall,
                         std::vector<float>& fat, std::vector<double>& sigma);
 
+// Large L: the same factors from a subspace iteration on Lambda^T Lambda whose products
+// Lambda X and Lambda^T Y run on the device in FP64 (k_fit.cu); sigma holds the leading
+// singular values that the iteration resolves (at least R).
+srp_status fit_low_rank_device(const Geometry& g, int R, std::vector<float>& tall,
+                               std::vector<float>& fat, std::vector<double>& sigma,
+                               cudaStream_t s);
+
+// Symmetric eigen-decomposition (cyclic Jacobi).  A: n x n row-major, destroyed;
+// V: eigenvectors as columns; d: eigenvalues (unsorted).
+void jacobi_eigen(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& d);
+
 // The Q_Lambda largest-magnitude entries of Lambda as CSR rows.
 srp_status fit_sparse(const Geometry& g, long long nnz, std::vector<long long>& row_ptr,
                       std::vector<int>& col, std::vector<float>& val, long long& tied);

@@ -132,3 +132,26 @@ def test_uca8_full_size_tensor_cores_sampled(S):
         check_argmax(z[fsel], am[fsel], zo)
     else:
         assert np.array_equal(am, np.argmax(z, axis=1))
+
+
+@pytest.mark.parametrize("name,F,sub,rank,prec", [
+    ("nested32", 6, 400, 8, "fp32"), ("nested32", 6, 400, 32, "fp16x3"),
+    ("walls16", 4, 300, 8, "fp32"), ("walls16", 4, 300, 16, "bf16"),
+])
+def test_slri_long_sample_vectors(S, name, F, sub, rank, prec):
+    """L = 7408 (nested32) and 43326 (walls16): the low-rank fit runs as a device subspace
+    iteration; its singular values and maps match the oracle's SVD."""
+    w = R.workload(name, F, sub)
+    dt, Np, lags, perm = R.geometry(name, F, sub)
+    xi_o, _ = O.gcc_samples_ifft(R.psi_of(w["frames"]), lags, w["N"] // 2)
+    tall, fat, s = R.slri(name, rank, F, sub)
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="slri", rank=rank,
+                  precision=prec, max_frames=4)
+    sig = plan.slri_sigma(rank + 1)
+    assert np.allclose(sig, s[:rank + 1], rtol=1e-8, atol=1e-8 * s[0])
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    zo = O.srp_slri(tall, fat, xi_o)
+    tol = dict(PRECS)[prec]
+    assert R.per_frame_rel(z, zo).max() <= tol
+    check_argmax(z, am, zo)
