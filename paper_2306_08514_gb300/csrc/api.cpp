@@ -181,9 +181,42 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
   const Geometry& g = p->g;
   SRP_CUDA_TRY(cudaMemsetAsync(p->d_keys, 0, sizeof(unsigned long long) * F, s));
   SRP_MARK(p, 0, s);
+  const int method = p->desc.method;
+  const int Rp = (p->R + 7) / 8 * 8;
+  if (p->use_front) {
+    // one fused launch: STFT + PHAT + sampling (+ Lambda_fat for SLRI) -> the operand
+    const bool tc = p->op != OpType::F32;
+    const bool slri = method == SRP_SLRI;
+    void* out = slri ? (tc ? p->d_A : p->d_U)
+                     : ((method == SRP_SSPI && !tc) ? static_cast<void*>(p->d_xi) : p->d_A);
+    const int cols = slri ? (tc ? kSlriKd : Rp) : ((method == SRP_SSPI && !tc) ? g.L : p->Lpad);
+    const float scale = slri && tc ? std::ldexp(1.f, -p->slri_exp) : 1.f;
+    SRP_LAUNCH(launch_front(frames, F, g.M, g.N, p->d_window, p->d_twiddle, g.P, p->d_pairs,
+                            p->d_Np, p->d_off, g.L, p->max_Np, slri ? p->d_fat : nullptr, Rp,
+                            cols, scale, p->op, out, p->d_A_lo, s));
+    SRP_MARK(p, 1, s);
+    SRP_MARK(p, 2, s);
+    if (slri && !tc) {
+      SRP_LAUNCH(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
+    } else if (slri) {
+      SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, kSlriKd, nullptr, nullptr,
+                            F, maps, s));
+    } else if (method == SRP_SSPI && !tc) {
+      SRP_LAUNCH(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
+                             p->num_sms, s));
+    } else {
+      SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, p->Lpad, p->d_kb_ptr,
+                            p->d_kb_idx, F, maps, s));
+    }
+    SRP_MARK(p, 3, s);
+    if (argmax) SRP_LAUNCH(launch_argmax_finalize(p->d_keys, argmax, F, s));
+    SRP_MARK(p, 4, s);
+    if (p->profiling && p->chunks_recorded < kMaxChunkEvents) ++p->chunks_recorded;
+    return SRP_OK;
+  }
   SRP_LAUNCH(launch_stft_phat(frames, F, g.M, g.N, p->d_window, p->d_twiddle, p->d_yhat, s));
   SRP_MARK(p, 1, s);
-  switch (p->desc.method) {
+  switch (method) {
     case SRP_CONV: {
       SRP_LAUNCH(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
                                     p->d_A_lo, s));
@@ -195,7 +228,6 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     case SRP_SLRI: {
       SRP_LAUNCH(sample_gcc(p, p->d_yhat, F, p->d_xi, s));
       SRP_MARK(p, 2, s);
-      const int Rp = (p->R + 7) / 8 * 8;
       SRP_LAUNCH(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
       if (p->op == OpType::F32) {
         SRP_LAUNCH(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
@@ -212,7 +244,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     case SRP_TD: {
       SRP_LAUNCH(sample_gcc(p, p->d_yhat, F, p->d_xi, s));
       SRP_MARK(p, 2, s);
-      if (p->desc.method == SRP_SSPI && p->op == OpType::F32) {
+      if (method == SRP_SSPI && p->op == OpType::F32) {
         SRP_LAUNCH(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
                                  p->num_sms, s));
       } else {
@@ -281,6 +313,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
                                         : OpType::F16X2;
   p->Lpad = (g.L + kSlriKd - 1) / kSlriKd * kSlriKd;
   p->max_Np = *std::max_element(g.Np.begin(), g.Np.end());
+  p->use_front = desc->method != SRP_CONV && front_supported(g.M, g.N, g.L, p->max_Np);
   if (desc->method == SRP_SI || desc->method == SRP_TD ||
       (desc->method == SRP_SSPI && p->op != OpType::F32)) {
     const double bbytes = static_cast<double>(g.J) * p->Lpad * op_bytes(p->op) *
@@ -673,6 +706,14 @@ extern "C" srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int 
   const Geometry& g = plan->g;
   for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
     const int nf = std::min(plan->Fmax, F - c0);
+    if (plan->use_front) {
+      plan->launches += 1;
+      SRP_CUDA_TRY(launch_front(frames + static_cast<size_t>(c0) * g.M * g.N, nf, g.M, g.N,
+                                plan->d_window, plan->d_twiddle, g.P, plan->d_pairs, plan->d_Np,
+                                plan->d_off, g.L, plan->max_Np, nullptr, 0, g.L, 1.f, OpType::F32,
+                                xi + static_cast<size_t>(c0) * g.L, nullptr, s));
+      continue;
+    }
     plan->launches += 2;
     SRP_CUDA_TRY(launch_stft_phat(frames + static_cast<size_t>(c0) * g.M * g.N, nf, g.M, g.N,
                                   plan->d_window, plan->d_twiddle, plan->d_yhat, s));

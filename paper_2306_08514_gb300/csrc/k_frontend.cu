@@ -233,6 +233,249 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 }
 
 // ---------------------------------------------------------------------------------
+// Fused front end for the interpolation methods: one CTA per frame runs the STFT + PHAT
+// of every channel (the half-length Stockham FFT of stft_phat_kernel, channel groups of
+// N/4 threads) into shared memory, samples every pair by direct summation (the
+// arithmetic of gcc_direct_kernel, reading y-hat from shared memory), and writes the
+// operand the contraction needs: xi in FP32 [F][L] (FP32 SSPI gather), xi as 16-bit
+// [F][Lpad] (tensor-core SI / TD / SSPI), or u = Lambda_fat xi (SLRI) as FP32 [F][Rp] or
+// 16-bit [F][64] scaled by `scale`.  Saves the y-hat round trip through global memory and
+// the separate packing and Lambda_fat launches.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T f2op(float v);
+template <>
+__device__ __forceinline__ __half f2op<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 f2op<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename T>
+__device__ __forceinline__ float op2f(T v);
+template <>
+__device__ __forceinline__ float op2f<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float op2f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// out[idx] = v as FP32, 16-bit, or 16-bit hi + lo
+template <int OT>
+__device__ __forceinline__ void put_op(void* hi, void* lo, size_t idx, float v) {
+  if constexpr (OT == 0) {
+    static_cast<float*>(hi)[idx] = v;
+  } else if constexpr (OT == 1) {
+    static_cast<__half*>(hi)[idx] = f2op<__half>(v);
+  } else if constexpr (OT == 2) {
+    static_cast<__nv_bfloat16*>(hi)[idx] = f2op<__nv_bfloat16>(v);
+  } else {
+    const __half h = f2op<__half>(v);
+    static_cast<__half*>(hi)[idx] = h;
+    static_cast<__half*>(lo)[idx] = f2op<__half>(v - op2f<__half>(h));
+  }
+}
+
+struct FrontParams {
+  const float* frames;
+  int M, N, P, L;
+  const float* window;
+  const float2* twiddle;
+  const int2* pairs;
+  const int* Np;
+  const int* off;
+  const float* fat;  // SLRI: [Rp][L]; NULL: write xi
+  int Rp;
+  int out_cols;      // row length of the output (L, Lpad, Rp or 64)
+  float scale;       // applied to u before packing
+  void* out;
+  void* out_lo;
+};
+
+template <int NQ, int OT>
+__global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const FrontParams a) {
+  extern __shared__ float2 sm[];
+  const int N = a.N, H = N >> 1, K = H, M = a.M;
+  const int Tg = H >> 1;                // threads per channel group
+  const int groups = blockDim.x / Tg;   // channels transformed at once
+  float2* tw = sm;                                   // H
+  float2* yh = tw + H;                               // M*K
+  float2* fbuf = yh + static_cast<size_t>(M) * K;    // groups * 2H
+  float* xis = reinterpret_cast<float*>(fbuf + static_cast<size_t>(groups) * 2 * H);  // L
+  const int tid = threadIdx.x;
+  const int f = blockIdx.x;
+  for (int t = tid; t < H; t += blockDim.x) tw[t] = a.twiddle[t];
+  const int grp = tid / Tg, j = tid - grp * Tg;
+  float2* bufA = fbuf + grp * 2 * H;
+  float2* bufB = bufA + H;
+  const float2* w2 = reinterpret_cast<const float2*>(a.window);
+  for (int m0 = 0; m0 < M; m0 += groups) {
+    const int m = m0 + grp;
+    const bool live = grp < groups && m < M;
+    __syncthreads();  // twiddles ready / previous round's buffers consumed
+    if (grp < groups) {
+      const float2* x2 = reinterpret_cast<const float2*>(a.frames + (static_cast<size_t>(f) * M + (live ? m : 0)) * N);
+      for (int jj = j; jj < H; jj += Tg) {
+        const float2 v = live ? __ldg(x2 + jj) : make_float2(0.f, 0.f);
+        const float2 ww = __ldg(w2 + jj);
+        bufA[jj] = make_float2(v.x * ww.x, v.y * ww.y);
+      }
+    }
+    __syncthreads();
+    // every thread of the block takes part in the FFT's barriers
+    const float2* Z = stockham_fft<false>(bufA, bufB, H, grp < groups ? j : 0, tw, 1);
+    if (live) {
+      float2* out = yh + static_cast<size_t>(m) * K;
+      for (int k = j; k < K; k += Tg) {
+        if (k == 0) {
+          out[0] = make_float2(0.f, 0.f);
+          continue;
+        }
+        const float2 zk = Z[k];
+        const float2 zc = make_float2(Z[H - k].x, -Z[H - k].y);
+        const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+        const float2 O = make_float2(0.5f * (zk.y - zc.y), -0.5f * (zk.x - zc.x));
+        const float2 WO = cmul(tw[k], O);
+        const float2 Y = make_float2(E.x + WO.x, E.y + WO.y);
+        const float p = Y.x * Y.x + Y.y * Y.y;
+        float2 r = make_float2(0.f, 0.f);
+        if (p >= 1e-30f) {
+          const float sc = __frsqrt_rn(p);
+          r = make_float2(Y.x * sc, Y.y * sc);
+        }
+        out[k] = r;
+      }
+    }
+  }
+  __syncthreads();
+  // direct sampling: one warp per group of G pairs, lanes over bins; the rotation
+  // e^{j pi k n / K} depends on (k, n) only and is shared by the G pairs
+  constexpr int G = NQ <= 8 ? 2 : 1;
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int twoK = 2 * K;
+  for (int q0 = warp * G; q0 < a.P; q0 += nw * G) {
+    int nq[G], mA[G], mB[G];
+    int nqmax = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const bool ok = q0 + g < a.P;
+      nq[g] = ok ? a.Np[q0 + g] : -1;
+      const int2 pr = ok ? a.pairs[q0 + g] : make_int2(0, 0);
+      mA[g] = pr.x * K;
+      mB[g] = pr.y * K;
+      nqmax = max(nqmax, nq[g]);
+    }
+    float c[G][NQ + 1], sn[G][NQ + 1];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int n = 0; n <= NQ; ++n) c[g][n] = sn[g][n] = 0.f;
+    for (int k = 1 + lane; k < K; k += 32) {
+      float2 psi[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        psi[g] = cmul_conj(yh[mA[g] + k], yh[mB[g] + k]);
+        c[g][0] += psi[g].x;
+      }
+      const float2 w0 = tw[k];
+      const float2 step = make_float2(w0.x, -w0.y);  // e^{+j pi k / K}
+      float2 e = make_float2(1.f, 0.f);
+#pragma unroll
+      for (int n = 1; n <= NQ; ++n) {
+        if (n > nqmax) break;
+        if ((n & 7) == 0) {
+          const int u = (k * n) & (twoK - 1);
+          const float2 wv = tw[u < K ? u : u - K];
+          e = u < K ? make_float2(wv.x, -wv.y) : make_float2(-wv.x, wv.y);
+        } else {
+          e = cmul(e, step);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          c[g][n] = fmaf(psi[g].x, e.x, c[g][n]);
+          sn[g][n] = fmaf(psi[g].y, e.y, sn[g][n]);
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+#pragma unroll
+      for (int n = 0; n <= NQ; ++n) {
+        if (n > nq[g]) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          c[g][n] += __shfl_xor_sync(0xFFFFFFFFu, c[g][n], o);
+          sn[g][n] += __shfl_xor_sync(0xFFFFFFFFu, sn[g][n], o);
+        }
+      }
+      if (nq[g] < 0) continue;
+      float* xo = xis + a.off[q0 + g] + nq[g];
+#pragma unroll
+      for (int n = 0; n <= NQ; ++n) {
+        if (n > nq[g]) break;
+        if (lane == n % 32) {
+          xo[n] = 2.f * (c[g][n] - sn[g][n]);
+          if (n > 0) xo[-n] = 2.f * (c[g][n] + sn[g][n]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const size_t row = static_cast<size_t>(f) * a.out_cols;
+  if (!a.fat) {
+    for (int l = tid; l < a.out_cols; l += blockDim.x)
+      put_op<OT>(a.out, a.out_lo, row + l, l < a.L ? xis[l] : 0.f);
+    return;
+  }
+  // u_r = sum_l fat[r][l] xi[l], one warp per r
+  for (int r = warp; r < a.out_cols; r += nw) {
+    float acc = 0.f;
+    if (r < a.Rp) {
+      const float* fr = a.fat + static_cast<size_t>(r) * a.L;
+      for (int l = lane; l < a.L; l += 32) acc = fmaf(__ldg(fr + l), xis[l], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    }
+    if (lane == 0) put_op<OT>(a.out, a.out_lo, row + r, acc * a.scale);
+  }
+}
+
+int front_max_N() { return 1024; }
+
+size_t front_smem_bytes(int M, int N, int L) {
+  const int H = N / 2, Tg = H / 2;
+  const int groups = 256 / Tg;
+  return sizeof(float2) * (H + static_cast<size_t>(M) * H + static_cast<size_t>(groups) * 2 * H) +
+         sizeof(float) * L;
+}
+
+bool front_supported(int M, int N, int L, int max_Np) {
+  return N >= 256 && N <= front_max_N() && max_Np <= gcc_direct_max_lag() &&
+         front_smem_bytes(M, N, L) <= 200 * 1024;
+}
+
+cudaError_t launch_front(const float* frames, int F, int M, int N, const float* window,
+                         const float2* twiddle, int P, const int2* pairs, const int* Np,
+                         const int* off, int L, int max_Np, const float* fat, int Rp,
+                         int out_cols, float scale, OpType t, void* out, void* out_lo,
+                         cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  if (!front_supported(M, N, L, max_Np)) return cudaErrorNotSupported;
+  FrontParams a{frames, M, N, P, L, window, twiddle, pairs, Np, off, fat, Rp, out_cols, scale, out, out_lo};
+  const size_t smem = front_smem_bytes(M, N, L);
+  const int NQ = max_Np <= 8 ? 8 : max_Np <= 16 ? 16 : 32;
+  const int OT = t == OpType::F32 ? 0 : t == OpType::F16 ? 1 : t == OpType::BF16 ? 2 : 3;
+  // one dispatch table entry per (NQ, operand type)
+  void (*kern)(const FrontParams) = nullptr;
+#define SRP_FRONT(NQV, OTV) if (NQ == NQV && OT == OTV) kern = front_kernel<NQV, OTV>;
+  SRP_FRONT(8, 0) SRP_FRONT(8, 1) SRP_FRONT(8, 2) SRP_FRONT(8, 3)
+  SRP_FRONT(16, 0) SRP_FRONT(16, 1) SRP_FRONT(16, 2) SRP_FRONT(16, 3)
+  SRP_FRONT(32, 0) SRP_FRONT(32, 1) SRP_FRONT(32, 2) SRP_FRONT(32, 3)
+#undef SRP_FRONT
+  if (!kern) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<F, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
 // conv. FD-SRP operand A [F][P*N]: row f holds, per pair, Re psi_p(k) at p*N + k and
 // Im psi_p(k) at p*N + K + k (k = 0..K-1, psi(0) = 0).  With B[i] = [2cos, -2sin]
 // (launch_conv_matrix) the dot product is 2 Re[H_p psi_p] summed over pairs.

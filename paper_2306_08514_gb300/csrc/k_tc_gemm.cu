@@ -13,12 +13,14 @@
 //
 // Persistent, warp-specialised kernel, one CTA per SM:
 //   warp 0      TMA producer: 128x64 tile of A and 256x64 tile of B per k-block into a
-//               4-stage, 128-byte-swizzled shared-memory ring;
+//               4-stage (2-stage for <= 3 k-blocks per tile) 128-byte-swizzled
+//               shared-memory ring;
 //   warp 1      TMEM owner and single-thread MMA issuer: 4 x tcgen05.mma (M128 N256 K16)
 //               per k-block into one of two 128x256 FP32 accumulators (512 TMEM columns);
 //   warps 2-9   epilogue: two warps per TMEM lane quarter, each owning 128 of the 256
 //               columns of 32 frame rows; results leave through swizzled shared-memory
-//               boxes and TMA tensor stores (coalesced, asynchronous).
+//               boxes (1 per warp, or 4 with the 2-stage ring) and TMA tensor stores
+//               (coalesced, asynchronous).
 // The tensor cores round every accumulation step towards zero, which biases long sums
 // (about -2e-5 relative after 600 K=16 steps).  So a tile's reduction is cut into
 // chunks of KB_PER_CHUNK k-blocks: each chunk starts a fresh TMEM accumulator (the two
@@ -43,7 +45,6 @@ namespace srp {
 
 namespace {
 constexpr int TM = 128, TN = 256, TK = 64;
-constexpr int STAGES = 4;
 constexpr int A_BYTES = TM * TK * 2;
 constexpr int B_BYTES = TN * TK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -53,10 +54,20 @@ constexpr int EPI_COLS = TN / 2;              // columns per epilogue thread
 constexpr int OUT_BOX = 32 * 32 * 4;          // one 32x32 FP32 output box per epilogue warp
 constexpr int KB_PER_CHUNK = 8;               // 32 K=16 steps per accumulator chunk
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + NEPI * OUT_BOX + BAR_BYTES + 1024;
+// Two shared-memory splits: reductions of more than SHORT_MAX_STEPS k-blocks per tile keep
+// 4 operand stages and one output box per epilogue warp; shorter ones (bound by the map
+// write) keep 2 stages and 4 boxes per warp, so a warp's four boxes of a tile leave
+// without waiting for one another.
+template <int STAGES, int BOXES>
+constexpr int smem_bytes() {
+  return STAGES * STAGE_BYTES + NEPI * BOXES * OUT_BOX + BAR_BYTES + 1024;
+}
+static_assert(smem_bytes<4, 1>() <= 232448 && smem_bytes<2, 4>() <= 232448, "shared memory budget");
+// k-steps per tile up to which 2 stages + 4 boxes are used (measured on uca8: SLRI's one
+// k-block per tile 0.112 -> 0.085 ms; SSPI's five k-blocks run faster with 4 stages)
+constexpr int SHORT_MAX_STEPS = 3;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int MIN_KB_PER_SLICE = 32;
-static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 }  // namespace
 
 struct TcParams {
@@ -90,6 +101,7 @@ __device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
   return w;
 }
 
+template <int STAGES, int BOXES>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
@@ -100,7 +112,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t sA = smem_u32(smem);
   const uint32_t sB = sA + STAGES * A_BYTES;
   uint8_t* out_smem = smem + STAGES * STAGE_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(out_smem + NEPI * OUT_BOX);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(out_smem + NEPI * BOXES * OUT_BOX);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
@@ -151,13 +163,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const TileWork w = tile_work(p, t);
         const int* list = p.kb_ptr ? p.kb_idx + __ldg(p.kb_ptr + w.n) : nullptr;
         for (int s = w.s0; s < w.s1; ++s) {
+          const int seg = s / w.m_len;
+          const int loc = s - seg * w.m_len;
+          const int kx = (list ? __ldg(list + loc) : loc) * TK;  // load overlaps the wait
           if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, 1, WAIT_NS)) {
             ok = false;
             break;
           }
-          const int seg = s / w.m_len;
-          const int loc = s - seg * w.m_len;
-          const int kx = (list ? __ldg(list + loc) : loc) * TK;
           const CUtensorMap* ta = seg == 2 ? &tmA1 : &tmA0;
           const CUtensorMap* tb = seg == 1 ? &tmB1 : &tmB0;
           mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
@@ -231,8 +243,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;       // which 128 of the 256 columns
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-    uint8_t* box = out_smem + (warp - 2) * OUT_BOX;  // 32 rows x 128 bytes, 128B-swizzled
-    const uint32_t box_s = smem_u32(box);
+    // BOXES boxes of 32 rows x 128 bytes, 128B-swizzled, owned by this warp
+    uint8_t* boxes = out_smem + (warp - 2) * BOXES * OUT_BOX;
     int gc = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
@@ -283,7 +295,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int b = 0; b < EPI_COLS / 32; ++b) {
           if (f0 >= p.F || n0 + b * 32 >= p.J) continue;  // box wholly outside the map
-          if (lane == 0) bulk_wait_read<0>();  // the previous box has left shared memory
+          uint8_t* box = boxes + (b % BOXES) * OUT_BOX;
+          // the box's previous store must have read it: before a tile's first box, every
+          // store of the previous tile; later, all but the BOXES - 1 newest stores
+          if (lane == 0) {
+            if (b == 0)
+              bulk_wait_read<0>();
+            else if (b >= BOXES)
+              bulk_wait_read<BOXES - 1>();
+          }
           __syncwarp();
 #pragma unroll
           for (int c4 = 0; c4 < 8; ++c4) {
@@ -294,7 +314,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
-            tma_store_3d(&tmZ, box_s, n0 + b * 32, f0, w.slice);
+            tma_store_3d(&tmZ, smem_u32(box), n0 + b * 32, f0, w.slice);
             bulk_commit();
           }
         }
@@ -385,7 +405,11 @@ size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms)
 cudaError_t tc_gemm_prepare() {
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  e = cudaFuncSetAttribute(tc_gemm_kernel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem_bytes<4, 1>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_gemm_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_bytes<2, 4>());
 }
 
 int tc_gemm_cell_tile() { return TN; }
@@ -444,9 +468,17 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   const uint32_t idesc = tc::idesc_f16(g.t == OpType::BF16 ? 1u : 0u, TM, TN);
   const int total = p.nM * p.nN * p.nslices;
   const int grid = total < num_sms ? total : num_sms;
-  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e != cudaSuccess) return e;
-  tc_gemm_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+  if (kb_total <= SHORT_MAX_STEPS) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<2, 4>());
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<2, 4><<<grid, NTHREADS, smem_bytes<2, 4>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+  } else {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<4, 1>());
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<4, 1><<<grid, NTHREADS, smem_bytes<4, 1>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess || p.nslices == 1) return e;
   return launch_split_reduce(g.split_ws, p.nslices, g.Z, g.keys, g.F, g.J, s);

@@ -80,6 +80,17 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 // Cross-spectra packed as the conv GEMM operand A [F][P*N]:
 // A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
 enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3 /* hi + lo planes */ };
+// Fused STFT + PHAT + direct sampling (+ Lambda_fat) per frame: writes xi (fat == NULL)
+// or u = fat xi * scale, rows of out_cols entries (zero padded) in operand type t.
+// Returns cudaErrorNotSupported where front_supported() is false (the caller then runs
+// the separate kernels).
+bool front_supported(int M, int N, int L, int max_Np);
+cudaError_t launch_front(const float* frames, int F, int M, int N, const float* window,
+                         const float2* twiddle, int P, const int2* pairs, const int* Np,
+                         const int* off, int L, int max_Np, const float* fat, int Rp,
+                         int out_cols, float scale, OpType t, void* out, void* out_lo,
+                         cudaStream_t s);
+
 cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
                              OpType t, void* A, void* A_lo, cudaStream_t s);
 // SRP matrix in GEMM layout B [J][P*N]: 2cos(theta), -2sin(theta), theta = 2 pi k tau / N.
@@ -165,7 +176,8 @@ struct srp_plan_s {
   srp::OpType op = srp::OpType::F32;
   int Lpad = 0;       // L rounded up to a multiple of 64 (dense interpolation operands)
   int slri_exp = 0;
-  int max_Np = 0;     // largest N_p over the pairs   // tensor-core SLRI: u is scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp
+  int max_Np = 0;     // largest N_p over the pairs
+  bool use_front = false;  // interpolation methods: one fused front-end launch per chunk   // tensor-core SLRI: u is scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp
   std::vector<double> sigma;
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
   std::vector<int> h_col;
