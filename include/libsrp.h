@@ -183,6 +183,23 @@ srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, float* maps
                         void* stream);
 
 /*
+ * srp_stream_push -- srp_map on a continuous multichannel stream (Sec. V-B: frames of N
+ * samples every hop samples).  hops: device float [B][M][hop], B consecutive blocks of hop
+ * new samples per channel.  The plan keeps the last N - hop samples of every channel
+ * between calls (in device memory, allocated by the first push), so each block completes
+ * one frame: frame b is the N samples ending with block b.  The stream starts from a
+ * silent (zero) history.  maps: device float [B][J]; argmax: device int32 [B] or NULL.
+ * hop is fixed for the stream: a different hop fails until srp_stream_reset.  B = 0 is a
+ * no-op.  Asynchronous on `stream`; pushes must be ordered on one stream.
+ * Errors: SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA.
+ */
+srp_status srp_stream_push(srp_plan_t plan, const float* hops, int B, int hop, float* maps,
+                           int* argmax, void* stream);
+
+/* srp_stream_reset -- forget the stream's history; the next push starts a new stream. */
+srp_status srp_stream_reset(srp_plan_t plan);
+
+/*
  * srp_gcc_samples -- the sampling stage alone (Eq. xi_p_ifft, n_prime, xi_single):
  * PHAT cross-spectra of every pair, iFFT of the two-sided spectrum (unnormalised,
  * length N), and the 2N_p+1 samples at lags -N_p..N_p.  Valid for every plan but conv.

@@ -76,6 +76,9 @@ SIGNATURES = {
     "srp_plan_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "srp_slri_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                         C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "srp_stream_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    "srp_stream_reset": (C.c_int, [C.c_void_p]),
     "srp_plan_estimate_bytes": (C.c_int, [C.POINTER(srp_plan_desc), C.POINTER(C.c_size_t)]),
     "srp_server_create": (C.c_int, [C.POINTER(srp_server_desc), C.POINTER(C.c_void_p)]),
     "srp_server_open": (C.c_int, [C.c_void_p, C.POINTER(srp_plan_desc), C.c_int, C.POINTER(C.c_int)]),
@@ -271,6 +274,24 @@ class Plan:
             argmax = np.empty((F,), dtype=np.int32)
         srp_map_host(self.handle, ptr(frames), F, ptr(maps), ptr(argmax), _stream_handle(stream))
         return maps, argmax
+
+    def stream_push(self, hops, maps=None, argmax=None, stream=None):
+        """hops: CUDA float32 [B][M][hop] (consecutive blocks of new samples); the plan keeps
+        the overlap between calls (srp_stream_push)."""
+        import torch
+        assert hops.is_cuda and hops.dtype == torch.float32 and hops.is_contiguous()
+        B, hop = hops.shape[0], hops.shape[2]
+        if maps is None:
+            maps = torch.empty((B, self.J), dtype=torch.float32, device=hops.device)
+        if argmax is None:
+            argmax = torch.empty((B,), dtype=torch.int32, device=hops.device)
+        _check(lib().srp_stream_push(self.handle, C.c_void_p(hops.data_ptr()), B, hop,
+                                     C.c_void_p(maps.data_ptr()), C.c_void_p(argmax.data_ptr()),
+                                     _stream_handle(stream)))
+        return maps, argmax
+
+    def stream_reset(self):
+        _check(lib().srp_stream_reset(self.handle))
 
     def gcc_samples(self, frames, stream=None):
         import torch

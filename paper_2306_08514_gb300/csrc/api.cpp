@@ -73,7 +73,8 @@ void free_plan(srp_plan_s* p) {
   void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
                   p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
-                  p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx};
+                  p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
+                  p->d_hist[1], p->d_stream_frames};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -690,6 +691,59 @@ extern "C" srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, 
                                    cudaMemcpyDeviceToHost, s));
   }
   SRP_CUDA_TRY(cudaStreamSynchronize(s));
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_stream_push(srp_plan_t plan, const float* hops, int B, int hop,
+                                      float* maps, int* argmax, void* stream) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (B < 0) return fail(SRP_EINVAL, "B < 0");
+  const Geometry& g = plan->g;
+  if (hop < 1 || hop > g.N) return fail(SRP_EINVAL, "hop must be in 1..N");
+  if (plan->stream_hop != 0 && plan->stream_hop != hop)
+    return fail(SRP_EINVAL, "hop differs from the stream's (srp_stream_reset first)");
+  if (B == 0) return SRP_OK;
+  if (!hops || !maps) return fail(SRP_EINVAL, "hops or maps is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t Hn = static_cast<size_t>(g.N - hop);
+  if (plan->stream_hop == 0) {  // first push: silent history, buffers sized for this hop
+    for (int k = 0; k < 2; ++k) {
+      if (plan->d_hist[k]) cudaFree(plan->d_hist[k]);
+      plan->d_hist[k] = nullptr;
+      if (cudaMalloc(&plan->d_hist[k], sizeof(float) * std::max<size_t>(1, g.M * Hn)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SRP_ENOMEM, "stream history allocation failed");
+      }
+    }
+    if (!plan->d_stream_frames &&
+        cudaMalloc(&plan->d_stream_frames, sizeof(float) * plan->Fmax * g.M * g.N) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SRP_ENOMEM, "stream frame staging allocation failed");
+    }
+    SRP_CUDA_TRY(cudaMemsetAsync(plan->d_hist[0], 0, sizeof(float) * g.M * Hn, s));
+    plan->stream_cur = 0;
+    plan->stream_hop = hop;
+  }
+  for (int c0 = 0; c0 < B; c0 += plan->Fmax) {
+    const int nb = std::min(plan->Fmax, B - c0);
+    const int cur = plan->stream_cur;
+    ++plan->launches;
+    SRP_CUDA_TRY(launch_stream_frames(hops + static_cast<size_t>(c0) * g.M * hop, nb, g.M, hop, g.N,
+                                      plan->d_hist[cur], plan->d_stream_frames,
+                                      plan->d_hist[1 - cur], s));
+    plan->stream_cur = 1 - cur;
+    srp_status st = run_chunk(plan, plan->d_stream_frames, nb, maps + static_cast<size_t>(c0) * g.J,
+                              argmax ? argmax + c0 : nullptr, s);
+    if (st != SRP_OK) return st;
+  }
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_stream_reset(srp_plan_t plan) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  plan->stream_hop = 0;  // the next push starts from a silent history
   return SRP_OK;
 }
 

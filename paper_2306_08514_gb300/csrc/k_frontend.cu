@@ -6,6 +6,8 @@
 //   xi_p(nT)        = iFFT_2K[psi-bar_p](n)          Eq. xi_p_ifft, n_prime
 //   H_p[i,k]        = exp(j omega_k Delta t_p(i))    Eq. H_p_single
 #include "srp_internal.h"
+
+#include <algorithm>
 #include "srp_device.cuh"
 
 namespace srp {
@@ -472,6 +474,60 @@ cudaError_t launch_front(const float* frames, int F, int M, int N, const float* 
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   kern<<<F, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Streaming front: frames from consecutive hops with overlap state.  The concatenation
+// [hist (N - hop samples per channel) | hop 0 | hop 1 | ... | hop B-1] is cut into B frames
+// of N samples with stride hop; the last N - hop samples become the next history.
+// hops: [B][M][hop]; hist_in / hist_out: [M][N - hop]; frames: [B][M][N].
+// ---------------------------------------------------------------------------------
+__global__ void stream_frames_kernel(const float* __restrict__ hops, int B, int M, int hop, int N,
+                                     const float* __restrict__ hist_in, float* __restrict__ frames,
+                                     float* __restrict__ hist_out) {
+  const int Hn = N - hop;
+  const size_t total = static_cast<size_t>(B) * M * N;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int n = static_cast<int>(e % N);
+    const size_t bm = e / N;
+    const int m = static_cast<int>(bm % M);
+    const int b = static_cast<int>(bm / M);
+    const long long c = static_cast<long long>(b) * hop + n;  // index in the concatenation
+    float v;
+    if (c < Hn) {
+      v = hist_in[static_cast<size_t>(m) * Hn + c];
+    } else {
+      const long long h = c - Hn;
+      v = hops[(static_cast<size_t>(h / hop) * M + m) * hop + (h % hop)];
+    }
+    frames[e] = v;
+  }
+  // new history: concatenation positions [B hop, B hop + Hn)
+  const size_t th = static_cast<size_t>(M) * Hn;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < th;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int m = static_cast<int>(e / Hn);
+    const long long c = static_cast<long long>(B) * hop + static_cast<long long>(e % Hn);
+    float v;
+    if (c < Hn) {
+      v = hist_in[static_cast<size_t>(m) * Hn + c];
+    } else {
+      const long long h = c - Hn;
+      v = hops[(static_cast<size_t>(h / hop) * M + m) * hop + (h % hop)];
+    }
+    hist_out[e] = v;
+  }
+}
+
+cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N,
+                                 const float* hist_in, float* frames, float* hist_out,
+                                 cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  size_t total = static_cast<size_t>(B) * M * N;
+  int g = static_cast<int>(std::min<size_t>((total + 255) / 256, 152 * 16));
+  stream_frames_kernel<<<g, 256, 0, s>>>(hops, B, M, hop, N, hist_in, frames, hist_out);
   return cudaGetLastError();
 }
 

@@ -77,6 +77,10 @@ int gcc_direct_max_lag();
 cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
                               const int* Np, const int* off, int L, int max_Np,
                               const float2* twiddle, float* xi, cudaStream_t s);
+// Frames from consecutive hops [B][M][hop] and the history [M][N - hop] (streaming front).
+cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N,
+                                 const float* hist_in, float* frames, float* hist_out,
+                                 cudaStream_t s);
 // Cross-spectra packed as the conv GEMM operand A [F][P*N]:
 // A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
 enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3 /* hi + lo planes */ };
@@ -209,6 +213,11 @@ struct srp_plan_s {
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
   // staging for srp_map_host
   float* d_stage_frames = nullptr;
+  // streaming (srp_stream_push): hop size, two history buffers [M][N - hop], frame staging
+  int stream_hop = 0;
+  int stream_cur = 0;
+  float* d_hist[2] = {nullptr, nullptr};
+  float* d_stream_frames = nullptr;
   float* d_stage_maps = nullptr;
   int* d_stage_arg = nullptr;
   size_t device_bytes = 0;

@@ -318,3 +318,39 @@ def test_uca8_full_size_sampled(S, uca_full):
         zo = O.srp_sspi(np.where(mask, R.lam("uca8"), 0.0), xi_o)
         assert R.per_frame_rel(z[fsel], zo).max() <= TOL
         check_argmax(z[fsel], am[fsel], zo)
+
+
+@pytest.mark.parametrize("method,kw,hop", [("conv", {}, 256), ("sspi", dict(taps=2.0, precision="bf16"), 128),
+                                           ("slri", dict(rank=8, precision="fp16x3"), 512)])
+def test_stream_push_keeps_overlap(S, method, kw, hop):
+    """srp_stream_push on a signal pushed in uneven blocks = srp_map on the frames cut from the
+    zero-padded stream (frame b = the N samples ending with block b)."""
+    import torch
+    w = R.workload("square4")
+    N, M = w["N"], w["mic_xyz"].shape[0]
+    x = synth.rng(77).standard_normal((M, 41 * hop)).astype(np.float32)
+    cat = np.concatenate([np.zeros((M, N - hop), np.float32), x], axis=1)
+    nb = x.shape[1] // hop
+    frames = np.stack([cat[:, b * hop:b * hop + N] for b in range(nb)])
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], N, method=method, max_frames=16, **kw)
+    zr, ar = _run(plan, frames)
+    hops = np.ascontiguousarray(x.reshape(M, nb, hop).transpose(1, 0, 2))
+    out, outa, b0 = [], [], 0
+    for B in [1, 3, 20, 0, 7, 10]:  # 20 > max_frames: chunked inside
+        B = min(B, nb - b0)
+        m, a = plan.stream_push(_cuda(hops[b0:b0 + B]))
+        torch.cuda.synchronize()
+        out.append(m.cpu().numpy())
+        outa.append(a.cpu().numpy())
+        b0 += B
+    z = np.concatenate(out)
+    am = np.concatenate(outa)
+    assert z.shape == zr.shape
+    assert np.array_equal(z, zr) or R.per_frame_rel(z, zr.astype(np.float64)).max() <= 1e-6
+    assert np.array_equal(am, np.argmax(z, axis=1))
+    with pytest.raises(S.SrpError):
+        plan.stream_push(_cuda(np.zeros((1, M, hop // 2), np.float32)))  # hop changed
+    plan.stream_reset()
+    m, a = plan.stream_push(_cuda(hops[:2]))
+    torch.cuda.synchronize()
+    assert np.array_equal(m.cpu().numpy(), zr[:2])
