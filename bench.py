@@ -56,6 +56,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--seconds", type=float, default=10.0)
@@ -251,6 +252,7 @@ def run_libsrp(a):
     kw = {"conv": dict(method="conv"), "slri": dict(method="slri", rank=a.rank),
           "sspi": dict(method="sspi", taps=a.taps)}
     plans = {m: S.Plan(*args, max_frames=F, precision=prec[m], **kw[m]) for m in methods}
+    tuned = {m: plans[m].autotune(F) for m in methods} if not a.no_autotune else {}
     frames = torch.from_numpy(w["frames"]).to(dev)
     maps = {m: torch.empty((F, J), dtype=torch.float32, device=dev) for m in methods}
     am = {m: torch.empty((F,), dtype=torch.int32, device=dev) for m in methods}
@@ -362,6 +364,7 @@ def run_libsrp(a):
                    if not a.no_flush else "not flushed"},
         "wall_ms_per_step": 1e3 * wall / a.steps,
         "methods": per,
+        "autotune": tuned,
         "roofline": roof,
         "e2e": {"value": cells / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": len(methods) * F * M * N * 4,

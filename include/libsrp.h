@@ -210,6 +210,30 @@ srp_status srp_stream_reset(srp_plan_t plan);
 srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int F, float* xi, void* stream);
 
 /*
+ * srp_plan_autotune -- pick the tensor-core kernel variant of this plan by timing them on
+ * the device: 128x256-cell tiles with 4 operand stages (long reductions), 128x256 with 2
+ * stages and 4 output boxes per epilogue warp (short reductions, map-write bound), and
+ * 128x128 tiles (twice the tiles for small grids or batches).  Each variant runs the whole
+ * srp_map path 2 + 5 times on F frames of a synthetic input (plan-owned temporary
+ * buffers); the fastest is kept by the plan for later calls.  Until a plan is tuned a
+ * heuristic picks by reduction length.  FP32 plans have nothing to tune (variant -1).
+ * F: 1..max_frames, the batch size the plan will serve.  Synchronises `stream`.
+ * report: host, written (or NULL): the chosen variant and the mean milliseconds per
+ * srp_map call of every variant (-1 where not run).  Errors: SRP_EINVAL, SRP_ENOMEM,
+ * SRP_ECUDA.
+ */
+enum { SRP_TUNE_MAX = 4 };
+typedef struct {
+  int variant;
+  float ms[SRP_TUNE_MAX];
+} srp_tune_report_t;
+srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream, srp_tune_report_t* report);
+
+/* srp_plan_set_variant -- pin the tensor-core variant (0..2 as in srp_plan_autotune) or
+ * return to the heuristic (-1).  Errors: SRP_EINVAL (out of range, or an FP32 plan). */
+srp_status srp_plan_set_variant(srp_plan_t plan, int variant);
+
+/*
  * srp_plan_sspi_taps -- copy an SSPI plan's kept entries to the host.
  * row_ptr: host int64 [J+1] or NULL; col: host int32 [nnz] or NULL (sample index into
  * the stacked xi of srp_gcc_samples); val: host float [nnz] or NULL.

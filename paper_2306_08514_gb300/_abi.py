@@ -60,6 +60,13 @@ class srp_server_stats_t(C.Structure):
 
 SESSION_STATES = {0: "queued", 1: "active", 2: "closing", 3: "closed", 4: "failed"}
 
+
+class srp_tune_report_t(C.Structure):
+    _fields_ = [("variant", C.c_int), ("ms", C.c_float * 4)]
+
+
+TUNE_VARIANTS = {-1: "fp32", 0: "128x256 4-stage", 1: "128x256 2-stage 4-box", 2: "128x128 4-stage"}
+
 # every symbol include/libsrp.h declares, with (restype, argtypes)
 SIGNATURES = {
     "srp_plan_create": (C.c_int, [C.POINTER(srp_plan_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -79,6 +86,8 @@ SIGNATURES = {
     "srp_stream_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "srp_stream_reset": (C.c_int, [C.c_void_p]),
+    "srp_plan_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(srp_tune_report_t)]),
+    "srp_plan_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "srp_plan_estimate_bytes": (C.c_int, [C.POINTER(srp_plan_desc), C.POINTER(C.c_size_t)]),
     "srp_server_create": (C.c_int, [C.POINTER(srp_server_desc), C.POINTER(C.c_void_p)]),
     "srp_server_open": (C.c_int, [C.c_void_p, C.POINTER(srp_plan_desc), C.c_int, C.POINTER(C.c_int)]),
@@ -274,6 +283,18 @@ class Plan:
             argmax = np.empty((F,), dtype=np.int32)
         srp_map_host(self.handle, ptr(frames), F, ptr(maps), ptr(argmax), _stream_handle(stream))
         return maps, argmax
+
+    def autotune(self, F=None, stream=None):
+        """srp_plan_autotune: time the tensor-core variants at F frames, keep the fastest.
+        Returns {"variant": name, "ms": {name: ms}}."""
+        rep = srp_tune_report_t()
+        F = int(F or self.desc.max_frames)
+        _check(lib().srp_plan_autotune(self.handle, F, _stream_handle(stream), C.byref(rep)))
+        return {"variant": TUNE_VARIANTS.get(rep.variant, rep.variant),
+                "ms": {TUNE_VARIANTS[v]: rep.ms[v] for v in range(3) if rep.ms[v] >= 0}}
+
+    def set_variant(self, variant):
+        _check(lib().srp_plan_set_variant(self.handle, int(variant)))
 
     def stream_push(self, hops, maps=None, argmax=None, stream=None):
         """hops: CUDA float32 [B][M][hop] (consecutive blocks of new samples); the plan keeps

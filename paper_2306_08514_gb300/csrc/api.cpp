@@ -156,6 +156,7 @@ cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void*
   tg.keys = p->d_keys;
   tg.split_ws = p->d_split;
   tg.err = p->d_err;
+  tg.variant = p->tc_variant;
   return launch_tc_gemm(tg, p->num_sms, s);
 }
 
@@ -744,6 +745,79 @@ extern "C" srp_status srp_stream_reset(srp_plan_t plan) {
   clear_error();
   if (!plan) return fail(SRP_EINVAL, "plan is NULL");
   plan->stream_hop = 0;  // the next push starts from a silent history
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream,
+                                        srp_tune_report_t* report) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (F < 1 || F > plan->Fmax) return fail(SRP_EINVAL, "F must be in 1..max_frames");
+  srp_tune_report_t rep{};
+  rep.variant = -1;
+  for (int v = 0; v < SRP_TUNE_MAX; ++v) rep.ms[v] = -1.f;
+  if (plan->op == OpType::F32) {  // nothing to choose on the FP32 path
+    if (report) *report = rep;
+    return SRP_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Geometry& g = plan->g;
+  float* d_frames = nullptr;
+  float* d_maps = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  srp_status st = SRP_OK;
+  const bool prof = plan->profiling;
+  plan->profiling = false;
+  const int saved = plan->tc_variant;
+  const long long launches = plan->launches;
+  if (cudaMalloc(&d_frames, sizeof(float) * F * g.M * g.N) != cudaSuccess ||
+      cudaMalloc(&d_maps, sizeof(float) * F * static_cast<size_t>(g.J)) != cudaSuccess) {
+    cudaGetLastError();
+    st = fail(SRP_ENOMEM, "autotune buffers");
+  }
+  // a deterministic non-silent input: the timing of every stage is data independent
+  if (st == SRP_OK && (cudaMemsetAsync(d_frames, 0x3C, sizeof(float) * F * g.M * g.N, s) != cudaSuccess ||
+                       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    st = fail(SRP_ECUDA, "autotune set-up");
+  float best = 0.f;
+  for (int v = 0; v < TC_NVARIANTS && st == SRP_OK; ++v) {
+    plan->tc_variant = v;
+    for (int it = 0; it < 2 && st == SRP_OK; ++it)  // warm-up
+      st = run_chunk(plan, d_frames, F, d_maps, nullptr, s);
+    if (st != SRP_OK) break;
+    if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(SRP_ECUDA, "event");
+    for (int it = 0; it < 5 && st == SRP_OK; ++it) st = run_chunk(plan, d_frames, F, d_maps, nullptr, s);
+    if (st != SRP_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = fail(SRP_ECUDA, "autotune timing");
+      break;
+    }
+    rep.ms[v] = ms / 5.f;
+    if (rep.variant < 0 || rep.ms[v] < best) {
+      best = rep.ms[v];
+      rep.variant = v;
+    }
+  }
+  plan->tc_variant = st == SRP_OK ? rep.variant : saved;
+  plan->profiling = prof;
+  plan->launches = launches;  // the tuning launches are not the caller's
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d_frames) cudaFree(d_frames);
+  if (d_maps) cudaFree(d_maps);
+  if (st == SRP_OK && report) *report = rep;
+  return st;
+}
+
+extern "C" srp_status srp_plan_set_variant(srp_plan_t plan, int variant) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (variant < -1 || variant >= TC_NVARIANTS) return fail(SRP_EINVAL, "variant must be in -1..2");
+  if (plan->op == OpType::F32 && variant != -1)
+    return fail(SRP_EINVAL, "FP32 plans have no tensor-core variant");
+  plan->tc_variant = variant;
   return SRP_OK;
 }
 

@@ -44,27 +44,29 @@
 namespace srp {
 
 namespace {
-constexpr int TM = 128, TN = 256, TK = 64;
+constexpr int TM = 128, TK = 64;
+constexpr int LIST_TILE = 256;                // cells per block-sparse k-block list
 constexpr int A_BYTES = TM * TK * 2;
-constexpr int B_BYTES = TN * TK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NEPI = 8;                       // epilogue warps
 constexpr int NTHREADS = 64 + 32 * NEPI;
-constexpr int EPI_COLS = TN / 2;              // columns per epilogue thread
-constexpr int OUT_BOX = 32 * 32 * 4;          // one 32x32 FP32 output box per epilogue warp
+constexpr int OUT_BOX = 32 * 32 * 4;          // one 32x32 FP32 output box
 constexpr int KB_PER_CHUNK = 8;               // 32 K=16 steps per accumulator chunk
 constexpr int BAR_BYTES = 256;
-// Two shared-memory splits: reductions of more than SHORT_MAX_STEPS k-blocks per tile keep
-// 4 operand stages and one output box per epilogue warp; shorter ones (bound by the map
-// write) keep 2 stages and 4 boxes per warp, so a warp's four boxes of a tile leave
-// without waiting for one another.
-template <int STAGES, int BOXES>
+template <int TN>
+constexpr int stage_bytes() { return A_BYTES + TN * TK * 2; }
+// Shared-memory splits (variants): STAGES operand stages and BOXES output boxes per
+// epilogue warp.  Long reductions keep 4 stages and one box; short ones (bound by the map
+// write) keep 2 stages and 4 boxes, so a warp's boxes of a tile leave without waiting for
+// one another.  TN is the cell width of a tile (256, or 128 for small grids).
+template <int STAGES, int BOXES, int TN>
 constexpr int smem_bytes() {
-  return STAGES * STAGE_BYTES + NEPI * BOXES * OUT_BOX + BAR_BYTES + 1024;
+  return STAGES * stage_bytes<TN>() + NEPI * BOXES * OUT_BOX + BAR_BYTES + 1024;
 }
-static_assert(smem_bytes<4, 1>() <= 232448 && smem_bytes<2, 4>() <= 232448, "shared memory budget");
-// k-steps per tile up to which 2 stages + 4 boxes are used (measured on uca8: SLRI's one
-// k-block per tile 0.112 -> 0.085 ms; SSPI's five k-blocks run faster with 4 stages)
+static_assert(smem_bytes<4, 1, 256>() <= 232448 && smem_bytes<2, 4, 256>() <= 232448 &&
+                  smem_bytes<4, 2, 128>() <= 232448,
+              "shared memory budget");
+// k-steps per tile up to which the heuristic picks 2 stages + 4 boxes (measured on uca8:
+// SLRI's one k-block per tile 0.112 -> 0.085 ms; SSPI's five k-blocks run faster with 4)
 constexpr int SHORT_MAX_STEPS = 3;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int MIN_KB_PER_SLICE = 32;
@@ -77,6 +79,7 @@ struct TcParams {
   const int* kb_idx;     //   kb_idx[kb_ptr[n] .. kb_ptr[n+1]); NULL = dense
   int nM, nN, nslices, kb_per_slice;
   int tma_out;           // 1: results leave by TMA store through tmZ; 0: plain stores
+  int tn;                // cell width of a tile
   float* Z;              // maps [F][J] (nslices == 1) or partial maps [nslices][F][J]
   unsigned long long* keys;
   int* err;
@@ -84,7 +87,7 @@ struct TcParams {
 
 // The k-step range [s0, s1) of tile t, and the tile's coordinates.
 struct TileWork {
-  int slice, m, n, s0, s1, m_len;
+  int slice, m, n, s0, s1, m_len, list;
 };
 
 __device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
@@ -94,19 +97,24 @@ __device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
   const int rem = t - w.slice * per_slice;
   w.n = rem / p.nM;
   w.m = rem - w.n * p.nM;
-  w.m_len = p.kb_ptr ? __ldg(p.kb_ptr + w.n + 1) - __ldg(p.kb_ptr + w.n) : p.kb_per_seg;
+  w.list = p.kb_ptr ? (w.n * p.tn) / LIST_TILE : 0;
+  w.m_len = p.kb_ptr ? __ldg(p.kb_ptr + w.list + 1) - __ldg(p.kb_ptr + w.list) : p.kb_per_seg;
   const int nsteps = w.m_len * p.nseg;
   w.s0 = min(nsteps, w.slice * p.kb_per_slice);
   w.s1 = min(nsteps, w.s0 + p.kb_per_slice);
   return w;
 }
 
-template <int STAGES, int BOXES>
+template <int STAGES, int BOXES, int TN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
                    const __grid_constant__ CUtensorMap tmZ, const TcParams p, const uint32_t idesc) {
   using namespace tc;
+  constexpr int B_BYTES = TN * TK * 2;
+  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int EPI_COLS = TN / 2;           // columns per epilogue thread
+  constexpr uint32_t TMEM_COLS = 2 * TN;     // two accumulators
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sA = smem_u32(smem);
@@ -137,7 +145,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -161,7 +169,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const TileWork w = tile_work(p, t);
-        const int* list = p.kb_ptr ? p.kb_idx + __ldg(p.kb_ptr + w.n) : nullptr;
+        const int* list = p.kb_ptr ? p.kb_idx + __ldg(p.kb_ptr + w.list) : nullptr;
         for (int s = w.s0; s < w.s1; ++s) {
           const int seg = s / w.m_len;
           const int loc = s - seg * w.m_len;
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, 512);
+    tmem_dealloc(tmem_base, TMEM_COLS);
   }
   if (threadIdx.x == 0 && *abort_flag) atomicExch(p.err, *abort_flag);
 }
@@ -383,9 +391,9 @@ cudaError_t make_output_map(CUtensorMap* m, float* base, uint64_t J, uint64_t F,
 
 // Reduction slices for F frames (dense operands): 1 while the output tiles fill the GPU;
 // otherwise enough slices (of at least MIN_KB_PER_SLICE k-blocks) to give every SM a tile.
-int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms) {
+static int slices_for(int F, int J, int Kd, int nseg, int num_sms, int tn) {
   if (F <= 0) return 1;
-  const long long tiles = static_cast<long long>((F + TM - 1) / TM) * ((J + TN - 1) / TN);
+  const long long tiles = static_cast<long long>((F + TM - 1) / TM) * ((J + tn - 1) / tn);
   if (tiles >= num_sms) return 1;
   const int kb_total = Kd / TK * nseg;
   const long long want = (num_sms + tiles - 1) / tiles;
@@ -393,42 +401,61 @@ int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms) {
   return static_cast<int>(want < cap ? want : cap);
 }
 
+int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms) {
+  return slices_for(F, J, Kd, nseg, num_sms, 256);
+}
+
 size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms) {
-  size_t need = 0;
+  size_t need = 0;  // the 256-cell variants need the most slices
   for (int F = 1; F <= F_max; ++F) {
-    const int ns = tc_gemm_slices(F, J, Kd, nseg, num_sms);
+    const int ns = slices_for(F, J, Kd, nseg, num_sms, 256);
     if (ns > 1) need = std::max(need, static_cast<size_t>(ns) * F * static_cast<size_t>(J));
   }
   return need;
 }
 
+namespace {
+template <int STAGES, int BOXES, int TN>
+cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(tc_gemm_kernel<STAGES, BOXES, TN>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_bytes<STAGES, BOXES, TN>());
+}
+}  // namespace
+
 cudaError_t tc_gemm_prepare() {
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tc_gemm_kernel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem_bytes<4, 1>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_gemm_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem_bytes<2, 4>());
+  if ((e = set_smem_attr<4, 1, 256>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<2, 4, 256>()) != cudaSuccess) return e;
+  return set_smem_attr<4, 2, 128>();
 }
 
-int tc_gemm_cell_tile() { return TN; }
+int tc_gemm_cell_tile() { return LIST_TILE; }
 int tc_gemm_k_block() { return TK; }
+
+int tc_gemm_default_variant(int Kd, OpType t) {
+  const int steps = Kd / TK * (t == OpType::F16X2 ? 3 : 1);
+  return steps <= SHORT_MAX_STEPS ? TC_SHORT_256 : TC_LONG_256;
+}
 
 cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   if (g.F <= 0) return cudaSuccess;
   if (g.Kd % TK != 0 || g.Kd <= 0) return cudaErrorInvalidValue;
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
+  const int variant = g.variant >= 0 ? g.variant : tc_gemm_default_variant(g.Kd, g.t);
+  if (variant < 0 || variant >= TC_NVARIANTS) return cudaErrorInvalidValue;
+  const int tn = variant == TC_LONG_128 ? 128 : 256;
   const bool split3 = g.t == OpType::F16X2;
   const CUtensorMapDataType dt = g.t == OpType::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   CUtensorMap mA0, mA1, mB0, mB1, mZ;
   if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, TM)) != cudaSuccess) return e;
-  if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, TN)) != cudaSuccess) return e;
+  if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, tn)) != cudaSuccess) return e;
   if (split3) {
     if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, TM)) != cudaSuccess) return e;
-    if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, TN)) != cudaSuccess) return e;
+    if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, tn)) != cudaSuccess) return e;
   } else {
     mA1 = mA0;
     mB1 = mB0;
@@ -436,13 +463,14 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   TcParams p;
   p.F = g.F;
   p.J = g.J;
+  p.tn = tn;
   p.kb_per_seg = g.Kd / TK;
   p.nseg = split3 ? 3 : 1;
   p.kb_ptr = g.kb_ptr;
   p.kb_idx = g.kb_idx;
   p.nM = (g.F + TM - 1) / TM;
-  p.nN = (g.J + TN - 1) / TN;
-  p.nslices = g.kb_ptr ? 1 : tc_gemm_slices(g.F, g.J, g.Kd, p.nseg, num_sms);
+  p.nN = (g.J + tn - 1) / tn;
+  p.nslices = g.kb_ptr ? 1 : slices_for(g.F, g.J, g.Kd, p.nseg, num_sms, tn);
   const int kb_total = p.kb_per_seg * p.nseg;
   if (p.nslices > 1) {
     p.kb_per_slice = (kb_total + p.nslices - 1) / p.nslices;
@@ -465,19 +493,23 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   } else {
     mZ = mA0;  // unused
   }
-  const uint32_t idesc = tc::idesc_f16(g.t == OpType::BF16 ? 1u : 0u, TM, TN);
+  const uint32_t idesc = tc::idesc_f16(g.t == OpType::BF16 ? 1u : 0u, TM, tn);
   const int total = p.nM * p.nN * p.nslices;
-  const int grid = total < num_sms ? total : num_sms;
-  if (kb_total <= SHORT_MAX_STEPS) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem_bytes<2, 4>());
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<2, 4><<<grid, NTHREADS, smem_bytes<2, 4>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
-  } else {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem_bytes<4, 1>());
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<4, 1><<<grid, NTHREADS, smem_bytes<4, 1>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+  int grid = total < num_sms ? total : num_sms;
+  if (g.max_ctas > 0 && grid > g.max_ctas) grid = g.max_ctas;
+  switch (variant) {
+    case TC_SHORT_256:
+      if ((e = set_smem_attr<2, 4, 256>()) != cudaSuccess) return e;
+      tc_gemm_kernel<2, 4, 256><<<grid, NTHREADS, smem_bytes<2, 4, 256>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+      break;
+    case TC_LONG_128:
+      if ((e = set_smem_attr<4, 2, 128>()) != cudaSuccess) return e;
+      tc_gemm_kernel<4, 2, 128><<<grid, NTHREADS, smem_bytes<4, 2, 128>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+      break;
+    default:
+      if ((e = set_smem_attr<4, 1, 256>()) != cudaSuccess) return e;
+      tc_gemm_kernel<4, 1, 256><<<grid, NTHREADS, smem_bytes<4, 1, 256>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+      break;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || p.nslices == 1) return e;

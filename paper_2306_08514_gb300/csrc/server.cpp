@@ -277,6 +277,8 @@ void builder_loop(Server* sv) {
     srp_plan_t plan = nullptr;
     std::string err;
     srp_status st = srp_plan_create(&pick->desc, sv->build_stream, &plan);
+    // tile shape for this session's batch size (the autotuner times the variants)
+    if (st == SRP_OK) st = srp_plan_autotune(plan, sv->desc.max_batch, sv->build_stream, nullptr);
     std::vector<std::unique_ptr<Slot>> slots;
     size_t bytes = 0;
     if (st != SRP_OK) {

@@ -113,8 +113,8 @@ cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long
 // Tensor-core contraction (tcgen05, k_tc_gemm.cu): Z[F][J] = A B^T with 16-bit K-major
 // operands A [F][Kd], B [J][Kd] (Kd a multiple of tc_gemm_k_block()), FP32 accumulation,
 // fused argmax keys.  t = F16X2 runs three products over hi and lo planes.  With kb_ptr
-// (device, [ceil(J / tc_gemm_cell_tile()) + 1]) and kb_idx, cell tile n only visits the
-// k-blocks kb_idx[kb_ptr[n] .. kb_ptr[n+1]) (block-sparse B).  Dense reductions whose
+// (device, [ceil(J / tc_gemm_cell_tile()) + 1]) and kb_idx, the cells of list tile n only
+// visit the k-blocks kb_idx[kb_ptr[n] .. kb_ptr[n+1]) (block-sparse B).  Dense reductions whose
 // output tiles do not fill the GPU are split into tc_gemm_slices(...) slices written to
 // split_ws (tc_gemm_workspace_floats(...) floats suffice for any F <= F_max) and summed
 // in FP64.  A bounded wait that runs out stores a non-zero code in *err.
@@ -131,7 +131,15 @@ struct TcGemm {
   unsigned long long* keys = nullptr;
   float* split_ws = nullptr;
   int* err = nullptr;
+  int variant = -1;   // TC_* kernel variant, -1: the heuristic's choice
+  int max_ctas = 0;   // cap on the persistent grid (0: one CTA per SM)
 };
+// Kernel variants (tile width and shared-memory split) the autotuner chooses from.
+enum { TC_LONG_256 = 0,   // 128x256 tiles, 4 operand stages, 1 output box per epilogue warp
+       TC_SHORT_256 = 1,  // 128x256 tiles, 2 stages, 4 boxes (short reductions)
+       TC_LONG_128 = 2,   // 128x128 tiles, 4 stages, 2 boxes (small grids: twice the tiles)
+       TC_NVARIANTS = 3 };
+int tc_gemm_default_variant(int Kd, OpType t);
 cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s);
 int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms);
 size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms);
@@ -181,6 +189,7 @@ struct srp_plan_s {
   int Lpad = 0;       // L rounded up to a multiple of 64 (dense interpolation operands)
   int slri_exp = 0;
   int max_Np = 0;     // largest N_p over the pairs
+  int tc_variant = -1;  // tensor-core kernel variant chosen by srp_plan_autotune (-1: heuristic)
   bool use_front = false;  // interpolation methods: one fused front-end launch per chunk   // tensor-core SLRI: u is scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp
   std::vector<double> sigma;
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export

@@ -155,3 +155,36 @@ def test_slri_long_sample_vectors(S, name, F, sub, rank, prec):
     tol = dict(PRECS)[prec]
     assert R.per_frame_rel(z, zo).max() <= tol
     check_argmax(z, am, zo)
+
+
+@pytest.mark.parametrize("method,kw", [("conv", {}), ("slri", dict(rank=16)), ("sspi", dict(taps=4.0)),
+                                       ("td", {})])
+def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
+    """The three tcgen05 variants (128x256 4-stage, 128x256 2-stage 4-box, 128x128) give the
+    oracle's maps on ragged tiles; srp_plan_autotune times them and keeps one."""
+    name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    Lam = R.lam(name, F, sub)
+    if method == "conv":
+        zo = O.srp_conv(psi, dt, w["fs"])
+    elif method == "slri":
+        tall, fat, s = R.slri(name, 16, F, sub)
+        zo = O.srp_slri(tall, fat, xi_o)
+    elif method == "sspi":
+        mask, tied, taken, nnz = R.sspi(name, 4.0, F, sub)
+        zo = O.srp_sspi(np.where(mask, Lam, 0.0), xi_o)
+    else:
+        zo = xi_o @ O.td_matrix(dt, w["fs"], lags).T
+    plan = S.Plan(*args, method=method, precision="fp16x3", max_frames=64, **kw)
+    if method == "sspi" and _check_taps(plan, mask, perm, Lam) != 0:
+        pytest.skip("selection ties at the cut")
+    for v in (0, 1, 2, -1):
+        plan.set_variant(v)
+        z, am = _run(plan, w["frames"])
+        plan.status()
+        assert R.per_frame_rel(z, zo).max() <= TOL, v
+        check_argmax(z, am, zo)
+    rep = plan.autotune(F=64)
+    assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 3
+    z, am = _run(plan, w["frames"])
+    assert R.per_frame_rel(z, zo).max() <= TOL
