@@ -88,7 +88,7 @@ typedef struct {
   const double* mic_xyz;    /* [M][3] microphone positions r_m in metres */
   int J;                    /* number of candidate locations, >= 1 */
   const double* grid_xyz;   /* [J][3] candidate locations q_i in metres (near field,
-                               Eq. Deltat_i first case) */
+                               Eq. Deltat_i first case), or unit vectors (far_field) */
   double fs;                /* sampling rate 1/T in Hz, > 0 */
   int N;                    /* frame / DFT length 2K: a power of two in 256..2048 */
   int window;               /* srp_window */
@@ -101,6 +101,9 @@ typedef struct {
   int precision;            /* srp_precision */
   int max_frames;           /* frames processed per internal launch (scratch sizing),
                                1..65536; larger calls are processed in chunks */
+  int far_field;            /* 0: grid_xyz are locations q_i (near field); 1: grid_xyz are
+                               unit incident directions (far field, Eq. Deltat_i second
+                               case: Delta t_p(i) = (r_m - r_m')^T q_i / c) */
 } srp_plan_desc;
 
 /* Sizes of a created plan (filled by srp_plan_info). */

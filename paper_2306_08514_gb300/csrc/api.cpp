@@ -39,10 +39,17 @@ srp_status validate(const srp_plan_desc* d) {
   if (d->n_aux < 0 || d->n_aux > 64) return fail(SRP_EINVAL, "n_aux must be in 0..64");
   if (d->max_frames < 1 || d->max_frames > 65536)
     return fail(SRP_EINVAL, "max_frames must be in 1..65536");
+  if (d->far_field != 0 && d->far_field != 1) return fail(SRP_EINVAL, "far_field must be 0 or 1");
   for (int i = 0; i < 3 * d->M; ++i)
     if (!std::isfinite(d->mic_xyz[i])) return fail(SRP_EINVAL, "mic_xyz has a non-finite value");
   for (long long i = 0; i < 3ll * d->J; ++i)
     if (!std::isfinite(d->grid_xyz[i])) return fail(SRP_EINVAL, "grid_xyz has a non-finite value");
+  if (d->far_field)
+    for (long long i = 0; i < d->J; ++i) {
+      const double* q = d->grid_xyz + 3 * i;
+      if (std::fabs(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] - 1.0) > 1e-9)
+        return fail(SRP_EINVAL, "far-field grid rows must be unit vectors");
+    }
   if (d->method < SRP_CONV || d->method > SRP_TD) return fail(SRP_EINVAL, "unknown method");
   if (d->precision != SRP_FP32 && d->precision != SRP_BF16 && d->precision != SRP_FP16 &&
       d->precision != SRP_FP16X3)

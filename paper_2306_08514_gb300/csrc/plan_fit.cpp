@@ -72,9 +72,24 @@ srp_status build_geometry(const srp_plan_desc& d, Geometry& g) {
     L += 2 * g.Np[p] + 1;
   }
   g.L = L;
-  // Eq. Deltat_i (near field) in samples: ((||r_m - q_i|| - ||r_m' - q_i||) / c) * fs.
+  // Eq. Deltat_i in samples: near field ((||r_m - q_i|| - ||r_m' - q_i||) / c) * fs;
+  // far field ((r_m - r_m')^T q_i / c) * fs with q_i a unit incident direction.
   g.tau.assign(static_cast<size_t>(g.J) * g.P, 0.0);
   const int M = d.M;
+  if (d.far_field) {
+    parallel_for(g.J, [&](long long b, long long e) {
+      for (long long i = b; i < e; ++i) {
+        const double* q = d.grid_xyz + 3 * i;
+        double* t = g.tau.data() + static_cast<size_t>(i) * g.P;
+        for (int p = 0; p < g.P; ++p) {
+          const double* a = d.mic_xyz + 3 * g.pm[p];
+          const double* c = d.mic_xyz + 3 * g.pmp[p];
+          t[p] = (((a[0] - c[0]) * q[0] + (a[1] - c[1]) * q[1] + (a[2] - c[2]) * q[2]) / d.c) * d.fs;
+        }
+      }
+    });
+    return SRP_OK;
+  }
   parallel_for(g.J, [&](long long b, long long e) {
     std::vector<double> dist(M);
     for (long long i = b; i < e; ++i) {

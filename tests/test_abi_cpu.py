@@ -39,7 +39,8 @@ def test_library_exports_every_declared_symbol(S):
     dict(M=1), dict(N=500), dict(N=128), dict(N=4096), dict(fs=0.0), dict(c=-1.0),
     dict(window=7), dict(n_aux=-1), dict(max_frames=0), dict(method=9),
     dict(method=1, rank=0), dict(method=1, rank=65), dict(method=2, taps=0.0),
-    dict(method=2, taps=1e9), dict(precision=3),
+    dict(method=2, taps=1e9), dict(precision=3), dict(far_field=2), dict(far_field=1),
+    dict(method=4, n_aux=0),
 ])
 def test_invalid_desc_is_rejected_on_the_host(S, bad):
     mics = synth.mics_square()
@@ -54,6 +55,8 @@ def test_invalid_desc_is_rejected_on_the_host(S, bad):
         d.M = bad["M"]
     if "window" in bad:
         d.window = bad["window"]
+    if "far_field" in bad:  # 2 is out of range; 1 with a grid of locations, not unit vectors
+        d.far_field = bad["far_field"]
     with pytest.raises(S.SrpError) as e:
         S.srp_plan_create(d, None)
     assert e.value.status in (S.SRP_EINVAL, S.SRP_EUNSUPPORTED)
@@ -74,3 +77,18 @@ def test_null_arguments(S):
     assert S.lib().srp_map(None, None, 1, None, None, None) == S.SRP_EINVAL
     assert S.lib().srp_plan_info(None, None) == S.SRP_EINVAL
     S.srp_destroy(None)
+
+
+def test_plan_estimate_needs_no_gpu(S):
+    """srp_plan_estimate_bytes (admission by footprint) is host arithmetic: it scales with the
+    operands a plan would hold."""
+    mics = synth.mics_uca(8, 0.05, (2.5, 2.0, 1.5))
+    grid = synth.grid_box((0, 0, 0), (5.0, 4.0, 3.0), 0.1)
+    conv16 = S.srp_plan_estimate_bytes(S.make_desc(mics, grid, 16000.0, 512, precision="bf16", max_frames=64))
+    conv32 = S.srp_plan_estimate_bytes(S.make_desc(mics, grid, 16000.0, 512, max_frames=64))
+    slri = S.srp_plan_estimate_bytes(S.make_desc(mics, grid, 16000.0, 512, method="slri", rank=16,
+                                                 max_frames=64))
+    J, P, N = grid.shape[0], 28, 512
+    assert abs(conv32 - 2 * conv16) < 0.02 * conv32
+    assert J * P * N * 4 <= conv32 <= 1.1 * J * P * N * 4
+    assert slri < conv16 / 50

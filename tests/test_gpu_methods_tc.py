@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import synth
 from tests import _ref as R
 from tests.test_gpu_parity import S, _run, check_argmax, _check_taps, sq, uca_small  # noqa: F401
 
@@ -188,3 +189,42 @@ def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
     assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 3
     z, am = _run(plan, w["frames"])
     assert R.per_frame_rel(z, zo).max() <= TOL
+
+
+@pytest.mark.parametrize("method,kw,prec,tol", [
+    ("conv", {}, "fp32", TOL), ("conv", {}, "fp16x3", TOL), ("slri", dict(rank=20), "fp16x3", TOL),
+    ("sspi", dict(taps=2.0), "fp32", TOL), ("si", {}, "bf16", 1.5e-2), ("td", {}, "fp16x3", TOL),
+])
+def test_far_field_grid(S, method, kw, prec, tol):
+    """Far field (Eq. Deltat_i second case) on the paper's 2-degree half-sphere grid
+    (J = 8101) with the uca8 array."""
+    w = R.workload("uca8", 24, 13)
+    dirs = synth.grid_ff_halfsphere(2.0)
+    dt = O.tdoa_ff(w["mic_xyz"], dirs)
+    Np = O.n_p_samples(w["mic_xyz"], w["fs"])
+    lags = O.pair_lags(Np)
+    psi = R.psi_of(w["frames"])
+    xi_o, _ = O.gcc_samples_ifft(psi, lags, w["N"] // 2)
+    Lam = O.interp_matrix(dt, w["fs"], lags)
+    plan = S.Plan(w["mic_xyz"], dirs, w["fs"], w["N"], method=method, precision=prec,
+                  max_frames=16, far_field=True, **kw)
+    perm = O.lags_to_ascending(lags)
+    if method == "conv":
+        zo = O.srp_conv(psi, dt, w["fs"])
+    elif method == "slri":
+        tall, fat, s = O.slri_factors(Lam, 20)  # sigma_16 = sigma_17 here (symmetric array): R = 20 has a gap
+        zo = O.srp_slri(tall, fat, xi_o)
+    elif method == "sspi":
+        nnz = int(round(2.0 * Lam.shape[0] * len(lags)))
+        mask, tied, taken = O.sspi_select(Lam, lags, nnz)
+        if _check_taps(plan, mask, perm, Lam) != 0:
+            pytest.skip("selection ties at the cut")
+        zo = O.srp_sspi(np.where(mask, Lam, 0.0), xi_o)
+    elif method == "si":
+        zo = O.srp_si(Lam, xi_o)
+    else:
+        zo = xi_o @ O.td_matrix(dt, w["fs"], lags).T
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    assert R.per_frame_rel(z, zo).max() <= tol
+    check_argmax(z, am, zo)
