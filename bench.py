@@ -217,6 +217,33 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------------------------------
+def measured_traffic(workload, F, method, prec):
+    """DRAM bytes (read + write) per launch of the method's contraction from the committed
+    ncu capture (profiles/traffic_*.json), or None when there is no capture of this launch
+    or its kernel source changed since (sha256 mismatch)."""
+    import glob
+    import hashlib
+    key = f"{workload}:F{F}:{method}:{prec}"
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "traffic_*.json"))):
+        try:
+            d = json.load(open(path))
+        except Exception:
+            continue
+        rec = d.get("launches", {}).get(key)
+        if not rec:
+            continue
+        src = rec["source"]
+        want = d.get("sources_sha256", {}).get(src)
+        try:
+            have = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+        except OSError:
+            return None
+        if want != have:
+            return None
+        return rec["dram_read"] + rec["dram_write"]
+    return None
+
+
 def contraction_work(m, prec, info, F, R):
     """(kind, amount per launch) of the dominant kernel of method m: algorithmic FLOPs of
     the contraction (a split-precision FP16 hi+lo run executes three products) or bytes."""
@@ -346,7 +373,7 @@ def run_libsrp(a):
         roof = {"bound": "hbm", "achieved": work / t_launch / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": f"{src} copy"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(a.workload, F, dom, prec[dom])
     roof["kernel"] = {"conv": "tc_gemm_kernel (conv SRP matrix)" if prec[dom] != "fp32" else "sgemm_nt_argmax_kernel",
                       "slri": "SLRI fat + pack + tc_gemm_kernel" if prec[dom] != "fp32" else "SLRI fat + tall",
                       "sspi": "SSPI pack + tc_gemm_kernel" if prec[dom] != "fp32" else "sspi_kernel"}[dom]
