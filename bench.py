@@ -332,6 +332,23 @@ def run_libsrp(a):
         per[m] = {"precision": prec[m], "ms_per_step": ms_m, "cells_frames_per_s": J * F / (ms_m / 1e3),
                   "stage_ms": {k: st[k] / a.steps for k in ("frontend", "spectra", "contract", "argmax")}}
 
+    # estimates only (srp_map with maps = NULL: argmax per frame, no map written)
+    for m in methods:
+        for _ in range(2):
+            plans[m].map(frames, None, am[m], stream=stream, want_maps=False)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(5):
+            plans[m].map(frames, None, am[m], stream=stream, want_maps=False)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        per_est = q0.elapsed_time(q1) / 5
+        per[m]["estimates_only_ms"] = per_est
+        per[m]["estimates_only_frames_per_s"] = F / (per_est / 1e3)
+    for m in methods:  # the maps of the last full step are restored for the error report
+        plans[m].map(frames, maps[m], am[m], stream=stream)
+    torch.cuda.synchronize()
+
     # e2e through the host-buffer entry point (H2D frames + D2H maps inside the timing)
     hframes = torch.from_numpy(w["frames"]).pin_memory()
     hmaps = {m: torch.empty((F, J), dtype=torch.float32).pin_memory() for m in methods}

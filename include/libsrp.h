@@ -166,11 +166,16 @@ srp_status srp_plan_lags(srp_plan_t plan, int* Np);
 /*
  * srp_map -- SRP maps and their argmax for F frames (the whole hot path).
  * frames: device float [F][M][N]: frame f, microphone m, sample n (unwindowed).
- * maps:   device float [F][J], written: z(i) of the plan's method per frame.
+ * maps:   device float [F][J], written: z(i) of the plan's method per frame; or NULL for
+ *         estimates only (argmax must then be given): on the tensor-core precisions no map
+ *         is written at all (the contraction's epilogue keeps only the per-frame maximum),
+ *         which removes the F*J*4-byte map write that bounds SLRI / SSPI; FP32 plans write
+ *         into plan scratch allocated by the first such call.
  * argmax: device int32 [F] or NULL, written: i_max per frame (Eq. imax), the lowest
  *         index among equal maxima.
  * F = 0 is a no-op.  Asynchronous on `stream`.
- * Errors: SRP_EINVAL (NULL plan/buffers with F > 0, F < 0), SRP_ECUDA.
+ * Errors: SRP_EINVAL (NULL plan/frames, maps and argmax both NULL, F < 0), SRP_ENOMEM,
+ * SRP_ECUDA.
  */
 srp_status srp_map(srp_plan_t plan, const float* frames, int F, float* maps, int* argmax,
                    void* stream);

@@ -259,15 +259,18 @@ class Plan:
         self.M, self.J, self.N, self.L, self.P = (self.info.M, self.info.J, self.info.N,
                                                   self.info.L, self.info.P)
 
-    def map(self, frames, maps=None, argmax=None, stream=None, want_argmax=True):
+    def map(self, frames, maps=None, argmax=None, stream=None, want_argmax=True,
+            want_maps=True):
+        """want_maps=False: estimates only (argmax, no map written; srp_map with maps NULL)."""
         import torch
         assert frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()
         F = frames.shape[0]
-        if maps is None:
+        if maps is None and want_maps:
             maps = torch.empty((F, self.J), dtype=torch.float32, device=frames.device)
-        if argmax is None and want_argmax:
+        if argmax is None and (want_argmax or not want_maps):
             argmax = torch.empty((F,), dtype=torch.int32, device=frames.device)
-        srp_map(self.handle, C.c_void_p(frames.data_ptr()), F, C.c_void_p(maps.data_ptr()),
+        srp_map(self.handle, C.c_void_p(frames.data_ptr()), F,
+                C.c_void_p(maps.data_ptr()) if maps is not None else None,
                 C.c_void_p(argmax.data_ptr()) if argmax is not None else None,
                 _stream_handle(stream))
         return maps, argmax

@@ -81,7 +81,7 @@ void free_plan(srp_plan_s* p) {
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
                   p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
-                  p->d_hist[1], p->d_stream_frames};
+                  p->d_hist[1], p->d_stream_frames, p->d_est_maps};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -646,13 +646,25 @@ extern "C" srp_status srp_map(srp_plan_t plan, const float* frames, int F, float
   if (!plan) return fail(SRP_EINVAL, "plan is NULL");
   if (F < 0) return fail(SRP_EINVAL, "F < 0");
   if (F == 0) return SRP_OK;
-  if (!frames || !maps) return fail(SRP_EINVAL, "frames or maps is NULL");
+  if (!frames || (!maps && !argmax)) return fail(SRP_EINVAL, "frames, or both maps and argmax, NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geometry& g = plan->g;
+  float* sink = nullptr;  // estimates only on the FP32 kernels: maps go to plan scratch
+  if (!maps && plan->op == OpType::F32) {
+    if (!plan->d_est_maps) {
+      if (cudaMalloc(&plan->d_est_maps, sizeof(float) * plan->Fmax * static_cast<size_t>(g.J)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SRP_ENOMEM, "estimate-only scratch allocation failed");
+      }
+      plan->device_bytes += sizeof(float) * plan->Fmax * static_cast<size_t>(g.J);
+    }
+    sink = plan->d_est_maps;
+  }
   for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
     const int nf = std::min(plan->Fmax, F - c0);
-    srp_status st = run_chunk(plan, frames + static_cast<size_t>(c0) * g.M * g.N, nf,
-                              maps + static_cast<size_t>(c0) * g.J, argmax ? argmax + c0 : nullptr, s);
+    float* out = maps ? maps + static_cast<size_t>(c0) * g.J : sink;
+    srp_status st = run_chunk(plan, frames + static_cast<size_t>(c0) * g.M * g.N, nf, out,
+                              argmax ? argmax + c0 : nullptr, s);
     if (st != SRP_OK) return st;
   }
   return SRP_OK;

@@ -122,7 +122,7 @@ __global__ __launch_bounds__(256) void split_reduce_argmax_kernel(const float* _
     double acc = 0.0;
     for (int z = 0; z < nsplit; ++z) acc += static_cast<double>(part[z * FJ + idx]);
     const float v = static_cast<float>(acc);
-    Z[idx] = v;
+    if (Z) Z[idx] = v;  // Z == NULL: estimates only
     const unsigned long long k = argmax_key(v, i);
     best = k > best ? k : best;
   }

@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         if (f < p.F && bi >= 0) atomicMax(p.keys + f, argmax_key(bv, bi));
       }
+      if (!p.Z) continue;  // estimates only: the argmax is all that leaves
       if (p.tma_out) {
         // 32x32 boxes: row = lane, 16-byte chunk c4 stored at chunk c4 ^ (lane & 7) (the
         // tensor map's 128-byte swizzle), so the eight lanes of each store phase hit
@@ -487,7 +488,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
     p.Z = g.Z;
   }
   // TMA output needs 16-byte row strides and a 16-byte aligned base.
-  p.tma_out = (g.J % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Z) % 16 == 0);
+  p.tma_out = p.Z && (g.J % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Z) % 16 == 0);
   if (p.tma_out) {
     if ((e = make_output_map(&mZ, p.Z, g.J, g.F, p.nslices)) != cudaSuccess) return e;
   } else {

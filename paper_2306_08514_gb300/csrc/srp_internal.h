@@ -227,6 +227,7 @@ struct srp_plan_s {
   int stream_cur = 0;
   float* d_hist[2] = {nullptr, nullptr};
   float* d_stream_frames = nullptr;
+  float* d_est_maps = nullptr;  // estimates-only calls of FP32 plans: map scratch [Fmax][J]
   float* d_stage_maps = nullptr;
   int* d_stage_arg = nullptr;
   size_t device_bytes = 0;

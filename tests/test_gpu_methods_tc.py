@@ -228,3 +228,22 @@ def test_far_field_grid(S, method, kw, prec, tol):
     plan.status()
     assert R.per_frame_rel(z, zo).max() <= tol
     check_argmax(z, am, zo)
+
+
+@pytest.mark.parametrize("method,kw,prec", [("conv", {}, "bf16"), ("slri", dict(rank=16), "fp16x3"),
+                                            ("sspi", dict(taps=4.0), "bf16"), ("sspi", dict(taps=4.0), "fp32"),
+                                            ("conv", {}, "fp32")])
+def test_estimates_only(S, uca_small, method, kw, prec):
+    """srp_map with maps = NULL: the argmax equals the argmax of the full map call (on the
+    tensor cores no map is written at all)."""
+    import torch
+    name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method=method, precision=prec,
+                  max_frames=64, **kw)
+    frames = torch.from_numpy(np.ascontiguousarray(w["frames"])).cuda()
+    z, am = plan.map(frames)
+    _, am2 = plan.map(frames, want_maps=False)
+    torch.cuda.synchronize()
+    plan.status()
+    assert np.array_equal(am.cpu().numpy(), am2.cpu().numpy())
+    assert np.array_equal(am2.cpu().numpy(), np.argmax(z.cpu().numpy(), axis=1))
