@@ -11,6 +11,7 @@
  *                  z = Lambda_tall (Lambda_fat xi)       (boxed Eq. z_circlr_computed)
  *   SSPI-SRP       z = Lambda_sp xi                      (boxed Eq. z_circsp_computed)
  *   SI-SRP         z = Lambda xi                         (boxed Eq. z_circ_computed)
+ *   LR-SRP         z = 2 Re[H_tall (H_fat psi)]          (boxed Eq. z_lr)
  *   conv. TD-SRP   z(i) = sum_p xi_p(round(Delta t_p(i)/T))  (Eq. TD_SRP)
  *   estimate       i_max = argmax_i z(i)                 (Eq. imax)
  *
@@ -60,7 +61,8 @@ typedef enum {
   SRP_SLRI = 1,  /* SLRI-SRP, Sec. IV-A, boxed Eq. z_circlr_computed */
   SRP_SSPI = 2,  /* SSPI-SRP, Sec. IV-A, boxed Eq. z_circsp_computed */
   SRP_SI = 3,    /* SI-SRP, Sec. III-B, boxed Eq. z_circ_computed (full sinc Lambda) */
-  SRP_TD = 4     /* conv. TD-SRP, Sec. II-D, Eq. TD_SRP (nearest-sample GCC lookup) */
+  SRP_TD = 4,    /* conv. TD-SRP, Sec. II-D, Eq. TD_SRP (nearest-sample GCC lookup) */
+  SRP_LR = 5     /* LR-SRP, Sec. III-A, boxed Eq. z_lr (rank-R factors of H) */
 } srp_method;
 
 /* Arithmetic of the map contraction (the front end -- DFT, PHAT, iFFT sampling -- is FP32
@@ -95,7 +97,8 @@ typedef struct {
   double c;                 /* speed of sound in m/s (the paper uses 340), > 0 */
   int n_aux;                /* N_aux of Eq. N_p, 0..64 (the paper uses 2) */
   int method;               /* srp_method */
-  int rank;                 /* SLRI: R_Lambda of Eq. min_Lambda_lr, 1..64 and <= min(J, L) */
+  int rank;                 /* SLRI: R_Lambda of Eq. min_Lambda_lr, 1..64 and <= min(J, L);
+                               LR: R_H of Eq. min_lr, 1..64 and <= min(J, P(K-1)) */
   double taps_per_loc_pair; /* SSPI: t, Q_Lambda = round(t * J * P) non-zeros kept by
                                Eq. min_Lambda_sp; 0 < t and Q_Lambda <= J * L */
   int precision;            /* srp_precision */
@@ -136,7 +139,11 @@ typedef struct {
  *             FP32 gather, or densely as [J][L] for the tensor cores;
  *   SRP_SI:   Lambda itself (Eq. Lambda_p, sinc evaluated in FP64), dense [J][L];
  *   SRP_TD:   the one-hot Lambda of conv. TD-SRP, 1 at n = round(Delta t_p(i)/T) with
- *             halves rounded away from zero (needs n_aux >= 1), dense [J][L].
+ *             halves rounded away from zero (needs n_aux >= 1), dense [J][L];
+ *   SRP_LR:   the best rank-R approximation (R = rank, 1..64) of the complex SRP matrix H
+ *             (Eq. min_lr) from a device subspace iteration on H^H H in FP64,
+ *             H_fat = V_R^H and H_tall = H V_R, stored as the real products
+ *             [Re | -Im ; Im | Re] H_fat (2R x P N) and [2 Re | -2 Im] H_tall (J x 2R).
  * desc:   host, read only; the arrays are copied.
  * stream: stream for the uploads; the call returns after they complete.
  * out:    receives the plan handle (NULL on failure).

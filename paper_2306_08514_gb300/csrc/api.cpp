@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <functional>
 
@@ -50,7 +51,7 @@ srp_status validate(const srp_plan_desc* d) {
       if (std::fabs(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] - 1.0) > 1e-9)
         return fail(SRP_EINVAL, "far-field grid rows must be unit vectors");
     }
-  if (d->method < SRP_CONV || d->method > SRP_TD) return fail(SRP_EINVAL, "unknown method");
+  if (d->method < SRP_CONV || d->method > SRP_LR) return fail(SRP_EINVAL, "unknown method");
   if (d->precision != SRP_FP32 && d->precision != SRP_BF16 && d->precision != SRP_FP16 &&
       d->precision != SRP_FP16X3)
     return fail(SRP_EINVAL, "unknown precision");
@@ -81,7 +82,8 @@ void free_plan(srp_plan_s* p) {
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
                   p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
-                  p->d_hist[1], p->d_stream_frames, p->d_est_maps};
+                  p->d_hist[1], p->d_stream_frames, p->d_est_maps, p->d_A2, p->d_A2_lo,
+                  p->d_keys2};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -139,15 +141,16 @@ srp_status mark(srp_plan_s* p, int stage, cudaStream_t s) {
   } while (0)
 
 // Z = A B^T with the plan's operand type: FP32 FFMA (SIMT) or the tensor cores.
-cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void* B, const void* B_lo,
-                     int Kd, const int* kb_ptr, const int* kb_idx, int F, float* maps, cudaStream_t s) {
+cudaError_t contract_to(srp_plan_s* p, const void* A, const void* A_lo, const void* B,
+                        const void* B_lo, int Kd, const int* kb_ptr, const int* kb_idx, int F,
+                        float* out, int Jout, unsigned long long* keys, cudaStream_t s) {
   if (p->op == OpType::F32) {
     p->launches += sgemm_split_count(Kd) > 1 ? 2 : 1;
-    return launch_sgemm_nt_argmax(static_cast<const float*>(A), static_cast<const float*>(B), maps,
-                                  p->d_keys, F, p->g.J, Kd, p->d_split, s);
+    return launch_sgemm_nt_argmax(static_cast<const float*>(A), static_cast<const float*>(B), out,
+                                  keys, F, Jout, Kd, p->d_split, s);
   }
   const int nseg = p->op == OpType::F16X2 ? 3 : 1;
-  p->launches += (!kb_ptr && tc_gemm_slices(F, p->g.J, Kd, nseg, p->num_sms) > 1) ? 2 : 1;
+  p->launches += (!kb_ptr && tc_gemm_slices(F, Jout, Kd, nseg, p->num_sms) > 1) ? 2 : 1;
   TcGemm tg;
   tg.A = A;
   tg.A_lo = A_lo;
@@ -155,16 +158,22 @@ cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void*
   tg.B_lo = B_lo;
   tg.t = p->op;
   tg.F = F;
-  tg.J = p->g.J;
+  tg.J = Jout;
   tg.Kd = Kd;
   tg.kb_ptr = kb_ptr;
   tg.kb_idx = kb_idx;
-  tg.Z = maps;
-  tg.keys = p->d_keys;
+  tg.Z = out;
+  tg.keys = keys;
   tg.split_ws = p->d_split;
   tg.err = p->d_err;
   tg.variant = p->tc_variant;
   return launch_tc_gemm(tg, p->num_sms, s);
+}
+
+// Z = A B^T into the maps, argmax keys of the plan.
+cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void* B, const void* B_lo,
+                     int Kd, const int* kb_ptr, const int* kb_idx, int F, float* maps, cudaStream_t s) {
+  return contract_to(p, A, A_lo, B, B_lo, Kd, kb_ptr, kb_idx, F, maps, p->g.J, p->d_keys, s);
 }
 
 // Sampling stage (Eq. xi_p_ifft / xi_computed): direct summation for short lag windows,
@@ -231,6 +240,20 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
                                     p->d_A_lo, s));
       SRP_MARK(p, 2, s);
       SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, nullptr, nullptr,
+                            F, maps, s));
+      break;
+    }
+    case SRP_LR: {
+      // u = H_fat psi as a real product over the conv operand (rows u_re, u_im), then
+      // z = 2 Re[H_tall u] = [2 Re H_tall | -2 Im H_tall] [u_re; u_im] (boxed Eq. z_lr)
+      SRP_LAUNCH(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
+                                  p->d_A_lo, s));
+      SRP_MARK(p, 2, s);
+      SRP_CUDA_TRY(contract_to(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, nullptr, nullptr,
+                               F, p->d_U, 2 * p->R, p->d_keys2, s));
+      SRP_LAUNCH(launch_pack16(p->d_U, F, 2 * p->R, p->lr_kd, std::ldexp(1.f, p->slri_exp), p->op,
+                               p->d_A2, p->d_A2_lo, s));
+      SRP_CUDA_TRY(contract(p, p->d_A2, p->d_A2_lo, p->d_B, p->d_B_lo, p->lr_kd, nullptr, nullptr,
                             F, maps, s));
       break;
     }
@@ -302,6 +325,14 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     }
     p->R = desc->rank;
   }
+  if (desc->method == SRP_LR) {
+    const int D = g.P * (g.K - 1);
+    if (desc->rank < 1 || desc->rank > 64 || desc->rank > std::min(g.J, D)) {
+      delete p;
+      return fail(SRP_EINVAL, "rank must be in 1..min(64, J, P(K-1))");
+    }
+    p->R = desc->rank;
+  }
   if (desc->method == SRP_SSPI) {
     const double t = desc->taps_per_loc_pair;
     const double nz = std::llround(t * static_cast<double>(g.J) * g.P);
@@ -322,7 +353,8 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
                                         : OpType::F16X2;
   p->Lpad = (g.L + kSlriKd - 1) / kSlriKd * kSlriKd;
   p->max_Np = *std::max_element(g.Np.begin(), g.Np.end());
-  p->use_front = desc->method != SRP_CONV && front_supported(g.M, g.N, g.L, p->max_Np);
+  p->use_front = desc->method != SRP_CONV && desc->method != SRP_LR &&
+                 front_supported(g.M, g.N, g.L, p->max_Np);
   if (desc->method == SRP_SI || desc->method == SRP_TD ||
       (desc->method == SRP_SSPI && p->op != OpType::F32)) {
     const double bbytes = static_cast<double>(g.J) * p->Lpad * op_bytes(p->op) *
@@ -404,6 +436,90 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       free_plan(p);
       return SRP_ECUDA;
     }
+  } else if (desc->method == SRP_LR) {
+    // LR-SRP (Sec. III-A): rank-R fit of H, then the real-ified factors
+    //   fat  B1 [2R][P N]: row r     = [Re Hf_r at k, -Im Hf_r at K + k] per pair (u_re)
+    //                      row R + r = [Im Hf_r at k,  Re Hf_r at K + k] per pair (u_im)
+    //   tall B2 [J][lr_kd]: [2 Re Ht | -2 Im Ht] * 2^-e, zero padded to lr_kd columns
+    const int R = p->R, D = g.P * (g.K - 1);
+    const size_t Kd = static_cast<size_t>(g.P) * g.N;
+    const size_t eb = op_bytes(p->op);
+    const bool split = p->op == OpType::F16X2;
+    std::vector<std::complex<double>> ht, hf;
+    srp_status fst = fit_lr_device(g, R, ht, hf, p->sigma, s);
+    if (fst != SRP_OK) {
+      free_plan(p);
+      return fst;
+    }
+    p->lr_kd = (2 * R + kSlriKd - 1) / kSlriKd * kSlriKd;
+    if (p->op != OpType::F32) {
+      // |u| <= ||psi||_2 <= sqrt(D) (rows of H_fat are orthonormal, |psi| <= 1); the tall
+      // entries are at most 2 sigma_1: scale them by 2^-e into the FP16 range
+      p->slri_exp = std::max(0, static_cast<int>(std::ceil(std::log2(2.0 * p->sigma[0] / 16384.0))));
+      if (std::sqrt(static_cast<double>(D)) * std::ldexp(1.0, p->slri_exp) > 16384.0) {
+        free_plan(p);
+        return fail(SRP_EUNSUPPORTED, "LR-SRP operands exceed the FP16 range (use SRP_FP32)");
+      }
+    }
+    std::vector<float> b1(static_cast<size_t>(2 * R) * Kd, 0.f), b2(static_cast<size_t>(g.J) * 2 * R);
+    for (int r = 0; r < R; ++r)
+      for (int q = 0; q < g.P; ++q)
+        for (int k = 1; k < g.K; ++k) {
+          const std::complex<double> v = hf[static_cast<size_t>(r) * D + q * (g.K - 1) + (k - 1)];
+          const size_t c = static_cast<size_t>(q) * g.N + k;
+          b1[r * Kd + c] = static_cast<float>(v.real());
+          b1[r * Kd + c + g.K] = static_cast<float>(-v.imag());
+          b1[(R + r) * Kd + c] = static_cast<float>(v.imag());
+          b1[(R + r) * Kd + c + g.K] = static_cast<float>(v.real());
+        }
+    const double sc = std::ldexp(1.0, -p->slri_exp);
+    for (int i = 0; i < g.J; ++i)
+      for (int r = 0; r < R; ++r) {
+        const std::complex<double> v = ht[static_cast<size_t>(i) * R + r];
+        b2[static_cast<size_t>(i) * 2 * R + r] = static_cast<float>(2.0 * v.real() * sc);
+        b2[static_cast<size_t>(i) * 2 * R + R + r] = static_cast<float>(-2.0 * v.imag() * sc);
+      }
+    float* d_tmp = nullptr;
+    const size_t tmp_n = std::max(b1.size(), b2.size());
+    if (cudaMalloc(&d_tmp, sizeof(float) * tmp_n) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(p);
+      return fail(SRP_ENOMEM, "LR factor staging");
+    }
+    SRP_ALLOC(p, p->d_H, static_cast<size_t>(2 * R) * Kd * eb);
+    if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(2 * R) * Kd * eb);
+    SRP_ALLOC(p, p->d_B, static_cast<size_t>(g.J) * p->lr_kd * eb);
+    if (split) SRP_ALLOC(p, p->d_B_lo, static_cast<size_t>(g.J) * p->lr_kd * eb);
+    cudaError_t e = cudaMemcpyAsync(d_tmp, b1.data(), sizeof(float) * b1.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_pack16(d_tmp, 2 * R, static_cast<int>(Kd), static_cast<int>(Kd), 1.f, p->op, p->d_H, p->d_H_lo, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_tmp, b2.data(), sizeof(float) * b2.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_pack16(d_tmp, g.J, 2 * R, p->lr_kd, 1.f, p->op, p->d_B, p->d_B_lo, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_tmp);
+    if (e != cudaSuccess) {
+      set_error(std::string("LR factors: ") + cudaGetErrorString(e));
+      free_plan(p);
+      return SRP_ECUDA;
+    }
+    SRP_ALLOC(p, p->d_A, F * Kd * eb);
+    if (split) SRP_ALLOC(p, p->d_A_lo, F * Kd * eb);
+    SRP_ALLOC(p, p->d_U, sizeof(float) * F * 2 * R);
+    SRP_ALLOC(p, p->d_A2, F * p->lr_kd * eb);
+    if (split) SRP_ALLOC(p, p->d_A2_lo, F * p->lr_kd * eb);
+    SRP_ALLOC(p, p->d_keys2, sizeof(unsigned long long) * F);
+    size_t ws = 0;
+    if (p->op == OpType::F32) {
+      const int nsplit = sgemm_split_count(static_cast<int>(Kd));
+      if (nsplit > 1) ws = static_cast<size_t>(nsplit) * F * 2 * R;
+    } else {
+      ws = std::max(tc_gemm_workspace_floats(p->Fmax, 2 * R, static_cast<int>(Kd), split ? 3 : 1, p->num_sms),
+                    tc_gemm_workspace_floats(p->Fmax, g.J, p->lr_kd, split ? 3 : 1, p->num_sms));
+    }
+    if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
   } else {
     SRP_ALLOC(p, p->d_xi, sizeof(float) * F * g.L);
     const size_t eb = op_bytes(p->op);
@@ -603,6 +719,16 @@ extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t*
         b += nnz * 8.0 + (J + 1) * 8.0;
       else
         b += (J + F) * Lpad * eb * planes + (J / 256.0 + 1) * 4.0 + J / 256.0 * Lpad / 64.0 * 4.0;
+      break;
+    }
+    case SRP_LR: {
+      const double kd2 = std::ceil(2.0 * d.rank / 64.0) * 64.0;
+      b += (2.0 * d.rank + F) * P * N * eb * planes + (J + F) * kd2 * eb * planes +
+           F * 2.0 * d.rank * 4.0 + F * 8.0;
+      if (d.precision == SRP_FP32 && P * N > 16384)
+        b += std::ceil(P * N / 16384.0) * F * 2.0 * d.rank * 4.0;
+      else if (d.precision != SRP_FP32)
+        b += 152.0 * 128.0 * 2.0 * d.rank * 4.0;  // split-K partial products of the fat GEMM
       break;
     }
     default:  // SI, TD
@@ -844,8 +970,8 @@ extern "C" srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int 
                                       void* stream) {
   clear_error();
   if (!plan) return fail(SRP_EINVAL, "plan is NULL");
-  if (plan->desc.method == SRP_CONV)
-    return fail(SRP_EUNSUPPORTED, "srp_gcc_samples needs an SLRI or SSPI plan");
+  if (plan->desc.method == SRP_CONV || plan->desc.method == SRP_LR)
+    return fail(SRP_EUNSUPPORTED, "srp_gcc_samples needs a plan that samples the TD GCC");
   if (F < 0) return fail(SRP_EINVAL, "F < 0");
   if (F == 0) return SRP_OK;
   if (!frames || !xi) return fail(SRP_EINVAL, "frames or xi is NULL");
@@ -880,7 +1006,8 @@ extern "C" srp_status srp_plan_sspi_taps(srp_plan_t plan, long long* row_ptr, in
 
 extern "C" srp_status srp_plan_slri_sigma(srp_plan_t plan, double* sigma, int n) {
   clear_error();
-  if (!plan || plan->desc.method != SRP_SLRI) return fail(SRP_EINVAL, "not an SLRI plan");
+  if (!plan || (plan->desc.method != SRP_SLRI && plan->desc.method != SRP_LR))
+    return fail(SRP_EINVAL, "not an SLRI or LR plan");
   if (!sigma || n < 0 || n > static_cast<int>(plan->sigma.size()))
     return fail(SRP_EINVAL, "n out of range");
   for (int i = 0; i < n; ++i) sigma[i] = plan->sigma[i];

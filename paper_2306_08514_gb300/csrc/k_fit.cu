@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <random>
 
 namespace srp {
@@ -293,7 +294,299 @@ srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
   return SRP_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// LR-SRP (Sec. III-A): the best rank-R approximation of the complex SRP matrix H
+// (J x D, D = P (K-1), [H]_{i,(p,k)} = e^{j omega_k Delta t_p(i)}, Eq. H_p_single), from the
+// same subspace iteration on H^H H with complex FP64 products; H entries are generated on
+// the fly from the FP64 TDOA table as e^{j 2 pi frac(k tau / N)}.
+// ------------------------------------------------------------------------------------
+constexpr int LR_ROWS = 32;   // rows of H per chunk (H X)
+constexpr int LR_COLS = 16;   // columns of H per chunk
+constexpr int LR_ROWS_T = 16; // rows of H per chunk (H^H Y)
+
+__device__ __forceinline__ double2 h_entry(const double* __restrict__ tau, int P, int K, int i, int d) {
+  const int q = d / (K - 1);
+  const int k = d - q * (K - 1) + 1;
+  const double t = static_cast<double>(k) * tau[static_cast<size_t>(i) * P + q];
+  const double N = 2.0 * K;
+  const double r = t - N * floor(t / N);  // k tau mod N, exact reduction in FP64
+  double sn, cs;
+  sincospi(2.0 * r / N, &sn, &cs);
+  return make_double2(cs, sn);
+}
+
+// Y[i][c] = sum_d H[i][d] X[d][c] (complex), rows of this block.
+template <int KT>
+__global__ __launch_bounds__(256) void lr_apply_kernel(const double* __restrict__ tau, int J, int P,
+                                                       int K, int D, const double2* __restrict__ X,
+                                                       double2* __restrict__ Y) {
+  __shared__ double2 hs[LR_ROWS][LR_COLS + 1];
+  __shared__ double2 xs[LR_COLS][KT];
+  const int t = threadIdx.x;
+  const int i0 = blockIdx.x * LR_ROWS;
+  const int r = t >> 3, cq = t & 7;
+  double2 acc[KT / 8];
+#pragma unroll
+  for (int j = 0; j < KT / 8; ++j) acc[j] = make_double2(0.0, 0.0);
+  for (int d0 = 0; d0 < D; d0 += LR_COLS) {
+    for (int e = t; e < LR_ROWS * LR_COLS; e += 256) {
+      const int rr = e / LR_COLS, dd = e % LR_COLS;
+      hs[rr][dd] = (i0 + rr < J && d0 + dd < D) ? h_entry(tau, P, K, i0 + rr, d0 + dd)
+                                                 : make_double2(0.0, 0.0);
+    }
+    for (int e = t; e < LR_COLS * KT; e += 256) {
+      const int dd = e / KT, c = e % KT;
+      xs[dd][c] = (d0 + dd < D) ? X[static_cast<size_t>(d0 + dd) * KT + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int dd = 0; dd < LR_COLS; ++dd) {
+      const double2 h = hs[r][dd];
+#pragma unroll
+      for (int j = 0; j < KT / 8; ++j) {
+        const double2 x = xs[dd][cq + 8 * j];
+        acc[j].x = fma(h.x, x.x, fma(-h.y, x.y, acc[j].x));
+        acc[j].y = fma(h.x, x.y, fma(h.y, x.x, acc[j].y));
+      }
+    }
+    __syncthreads();
+  }
+  const int i = i0 + r;
+  if (i < J)
+#pragma unroll
+    for (int j = 0; j < KT / 8; ++j) Y[static_cast<size_t>(i) * KT + cq + 8 * j] = acc[j];
+}
+
+// Zpart[s][d][c] = sum_{i in split s} conj(H[i][d]) Y[i][c].
+template <int KT>
+__global__ __launch_bounds__(256) void lr_t_apply_kernel(const double* __restrict__ tau, int J,
+                                                         int P, int K, int D,
+                                                         const double2* __restrict__ Y,
+                                                         int rows_per_split,
+                                                         double2* __restrict__ Zpart) {
+  __shared__ double2 hs[LR_ROWS_T][LR_COLS + 1];
+  __shared__ double2 ys[LR_ROWS_T][KT];
+  const int t = threadIdx.x;
+  const int d0 = blockIdx.x * LR_COLS;
+  const int ib = blockIdx.y * rows_per_split;
+  const int ie = min(J, ib + rows_per_split);
+  const int dc = t >> 4, cq = t & 15;
+  double2 acc[KT / 16];
+#pragma unroll
+  for (int j = 0; j < KT / 16; ++j) acc[j] = make_double2(0.0, 0.0);
+  for (int i0 = ib; i0 < ie; i0 += LR_ROWS_T) {
+    for (int e = t; e < LR_ROWS_T * LR_COLS; e += 256) {
+      const int rr = e / LR_COLS, dd = e % LR_COLS;
+      hs[rr][dd] = (i0 + rr < ie && d0 + dd < D) ? h_entry(tau, P, K, i0 + rr, d0 + dd)
+                                                  : make_double2(0.0, 0.0);
+    }
+    for (int e = t; e < LR_ROWS_T * KT; e += 256) {
+      const int rr = e / KT, c = e % KT;
+      ys[rr][c] = (i0 + rr < ie) ? Y[static_cast<size_t>(i0 + rr) * KT + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < LR_ROWS_T; ++rr) {
+      const double2 h = hs[rr][dc];  // conj(h) * y
+#pragma unroll
+      for (int j = 0; j < KT / 16; ++j) {
+        const double2 y = ys[rr][cq + 16 * j];
+        acc[j].x = fma(h.x, y.x, fma(h.y, y.y, acc[j].x));
+        acc[j].y = fma(h.x, y.y, fma(-h.y, y.x, acc[j].y));
+      }
+    }
+    __syncthreads();
+  }
+  const int d = d0 + dc;
+  if (d < D)
+#pragma unroll
+    for (int j = 0; j < KT / 16; ++j)
+      Zpart[(static_cast<size_t>(blockIdx.y) * D + d) * KT + cq + 16 * j] = acc[j];
+}
+
+using cplx = std::complex<double>;
+
+// Modified Gram-Schmidt, twice, on the columns of a complex rows x cols matrix.
+void orthonormalise_c(std::vector<cplx>& A, int rows, int cols) {
+  for (int pass = 0; pass < 2; ++pass)
+    for (int c = 0; c < cols; ++c) {
+      for (int b = 0; b < c; ++b) {
+        cplx d = 0.0;
+        for (int r = 0; r < rows; ++r) d += std::conj(A[static_cast<size_t>(r) * cols + b]) * A[static_cast<size_t>(r) * cols + c];
+        for (int r = 0; r < rows; ++r) A[static_cast<size_t>(r) * cols + c] -= d * A[static_cast<size_t>(r) * cols + b];
+      }
+      double nn = 0.0;
+      for (int r = 0; r < rows; ++r) nn += std::norm(A[static_cast<size_t>(r) * cols + c]);
+      nn = std::sqrt(nn);
+      const double inv = nn > 0 ? 1.0 / nn : 0.0;
+      for (int r = 0; r < rows; ++r) A[static_cast<size_t>(r) * cols + c] *= inv;
+    }
+}
+
+// Eigen-decomposition of a k x k Hermitian T through the real symmetric 2k x 2k matrix
+// [[Re T, -Im T], [Im T, Re T]], whose eigenvalues are those of T, each twice; from each
+// pair one complex eigenvector x + jy is kept (the other is j times it).
+void hermitian_eigen(int k, const std::vector<cplx>& T, std::vector<cplx>& W, std::vector<double>& th) {
+  const int n = 2 * k;
+  std::vector<double> A(static_cast<size_t>(n) * n), V, ev;
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < k; ++b) {
+      const cplx t = T[static_cast<size_t>(a) * k + b];
+      A[static_cast<size_t>(a) * n + b] = t.real();
+      A[static_cast<size_t>(a) * n + k + b] = -t.imag();
+      A[static_cast<size_t>(k + a) * n + b] = t.imag();
+      A[static_cast<size_t>(k + a) * n + k + b] = t.real();
+    }
+  jacobi_eigen(n, A, V, ev);
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ev[a] > ev[b]; });
+  W.assign(static_cast<size_t>(k) * k, 0.0);  // columns: eigenvectors
+  th.clear();
+  int got = 0;
+  for (int oi = 0; oi < n && got < k; ++oi) {
+    const int c = order[oi];
+    std::vector<cplx> v(k);
+    for (int a = 0; a < k; ++a) v[a] = cplx(V[static_cast<size_t>(a) * n + c], V[static_cast<size_t>(k + a) * n + c]);
+    for (int b = 0; b < got; ++b) {  // remove the directions already kept
+      cplx d = 0.0;
+      for (int a = 0; a < k; ++a) d += std::conj(W[static_cast<size_t>(a) * k + b]) * v[a];
+      for (int a = 0; a < k; ++a) v[a] -= d * W[static_cast<size_t>(a) * k + b];
+    }
+    double nn = 0.0;
+    for (int a = 0; a < k; ++a) nn += std::norm(v[a]);
+    nn = std::sqrt(nn);
+    if (nn < 0.5) continue;  // the partner of an eigenvector already kept
+    for (int a = 0; a < k; ++a) W[static_cast<size_t>(a) * k + got] = v[a] / nn;
+    th.push_back(ev[c]);
+    ++got;
+  }
+  while (static_cast<int>(th.size()) < k) th.push_back(0.0);
+}
+
+template <int KT>
+srp_status run_lr_fit(const Geometry& g, int R, int k, std::vector<cplx>& tall,
+                      std::vector<cplx>& fat, std::vector<double>& sigma, cudaStream_t s) {
+  const int J = g.J, P = g.P, K = g.K;
+  const int D = P * (K - 1);
+  const int splits = std::max(1, std::min(64, 4 * 152 / std::max(1, (D + LR_COLS - 1) / LR_COLS)));
+  const int rows_per_split = ((J + splits - 1) / splits + LR_ROWS_T - 1) / LR_ROWS_T * LR_ROWS_T;
+  const int nsplit = (J + rows_per_split - 1) / rows_per_split;
+  DevBuf d_tau, d_X, d_Y, d_Z;
+  const size_t JP = static_cast<size_t>(J) * P;
+  SRP_CUDA_TRY(cudaMalloc(&d_tau.p, JP * 8));
+  SRP_CUDA_TRY(cudaMalloc(&d_X.p, sizeof(double2) * static_cast<size_t>(D) * KT));
+  SRP_CUDA_TRY(cudaMalloc(&d_Y.p, sizeof(double2) * static_cast<size_t>(J) * KT));
+  SRP_CUDA_TRY(cudaMalloc(&d_Z.p, sizeof(double2) * static_cast<size_t>(nsplit) * D * KT));
+  auto* tau = static_cast<double*>(d_tau.p);
+  SRP_CUDA_TRY(cudaMemcpyAsync(tau, g.tau.data(), JP * 8, cudaMemcpyHostToDevice, s));
+  std::vector<cplx> Xh(static_cast<size_t>(D) * KT), Zp(static_cast<size_t>(nsplit) * D * KT);
+  auto apply_Y = [&](const std::vector<cplx>& Q, int cols) -> srp_status {  // d_Y = H Q
+    for (int d = 0; d < D; ++d)
+      for (int c = 0; c < KT; ++c) Xh[static_cast<size_t>(d) * KT + c] = c < cols ? Q[static_cast<size_t>(d) * k + c] : 0.0;
+    SRP_CUDA_TRY(cudaMemcpyAsync(d_X.p, Xh.data(), sizeof(double2) * D * KT, cudaMemcpyHostToDevice, s));
+    lr_apply_kernel<KT><<<(J + LR_ROWS - 1) / LR_ROWS, 256, 0, s>>>(tau, J, P, K, D,
+                                                                    static_cast<double2*>(d_X.p),
+                                                                    static_cast<double2*>(d_Y.p));
+    SRP_CUDA_TRY(cudaGetLastError());
+    return SRP_OK;
+  };
+  auto apply_G = [&](const std::vector<cplx>& Q, std::vector<cplx>& Zout) -> srp_status {
+    srp_status st = apply_Y(Q, k);
+    if (st != SRP_OK) return st;
+    dim3 grid((D + LR_COLS - 1) / LR_COLS, nsplit);
+    lr_t_apply_kernel<KT><<<grid, 256, 0, s>>>(tau, J, P, K, D, static_cast<double2*>(d_Y.p),
+                                               rows_per_split, static_cast<double2*>(d_Z.p));
+    SRP_CUDA_TRY(cudaGetLastError());
+    SRP_CUDA_TRY(cudaMemcpyAsync(Zp.data(), d_Z.p, sizeof(double2) * Zp.size(), cudaMemcpyDeviceToHost, s));
+    SRP_CUDA_TRY(cudaStreamSynchronize(s));
+    Zout.assign(static_cast<size_t>(D) * k, 0.0);
+    for (int sp = 0; sp < nsplit; ++sp)
+      for (int d = 0; d < D; ++d)
+        for (int c = 0; c < k; ++c) Zout[static_cast<size_t>(d) * k + c] += Zp[(static_cast<size_t>(sp) * D + d) * KT + c];
+    return SRP_OK;
+  };
+  std::mt19937_64 rng(54321);
+  std::normal_distribution<double> nd;
+  std::vector<cplx> Q(static_cast<size_t>(D) * k), Z, W, T;
+  for (auto& v : Q) v = cplx(nd(rng), nd(rng));
+  orthonormalise_c(Q, D, k);
+  std::vector<double> prev(R, 0.0), theta;
+  bool converged = false;
+  for (int it = 0; it < 300; ++it) {
+    srp_status st = apply_G(Q, Z);
+    if (st != SRP_OK) return st;
+    T.assign(static_cast<size_t>(k) * k, 0.0);  // Q^H Z, Hermitian part
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) {
+        cplx d = 0.0;
+        for (int l = 0; l < D; ++l) d += std::conj(Q[static_cast<size_t>(l) * k + a]) * Z[static_cast<size_t>(l) * k + b];
+        T[static_cast<size_t>(a) * k + b] = d;
+      }
+    for (int a = 0; a < k; ++a)
+      for (int b = a; b < k; ++b) {
+        const cplx m = 0.5 * (T[static_cast<size_t>(a) * k + b] + std::conj(T[static_cast<size_t>(b) * k + a]));
+        T[static_cast<size_t>(a) * k + b] = m;
+        T[static_cast<size_t>(b) * k + a] = std::conj(m);
+      }
+    hermitian_eigen(k, T, W, theta);  // descending
+    double change = 0.0;
+    for (int r = 0; r < R; ++r) {
+      change = std::max(change, std::fabs(theta[r] - prev[r]) / std::max(theta[r], 1e-300));
+      prev[r] = theta[r];
+    }
+    std::vector<cplx> QW(static_cast<size_t>(D) * k, 0.0), ZW(static_cast<size_t>(D) * k, 0.0);
+    for (int l = 0; l < D; ++l)
+      for (int c = 0; c < k; ++c) {
+        cplx qa = 0.0, za = 0.0;
+        for (int a = 0; a < k; ++a) {
+          const cplx w = W[static_cast<size_t>(a) * k + c];
+          qa += Q[static_cast<size_t>(l) * k + a] * w;
+          za += Z[static_cast<size_t>(l) * k + a] * w;
+        }
+        QW[static_cast<size_t>(l) * k + c] = qa;
+        ZW[static_cast<size_t>(l) * k + c] = za;
+      }
+    if (it > 2 && change < 1e-13) {
+      Q.swap(QW);
+      converged = true;
+      break;
+    }
+    orthonormalise_c(ZW, D, k);
+    Q.swap(ZW);
+  }
+  if (!converged) {
+    set_error("LR fit: subspace iteration did not converge");
+    return SRP_EUNSUPPORTED;
+  }
+  sigma.resize(k);
+  for (int c = 0; c < k; ++c) sigma[c] = std::sqrt(std::max(0.0, theta[c]));
+  // H_fat = V_R^H (R x D), H_tall = H V_R (J x R)
+  fat.assign(static_cast<size_t>(R) * D, 0.0);
+  for (int r = 0; r < R; ++r)
+    for (int d = 0; d < D; ++d) fat[static_cast<size_t>(r) * D + d] = std::conj(Q[static_cast<size_t>(d) * k + r]);
+  srp_status st = apply_Y(Q, R);
+  if (st != SRP_OK) return st;
+  std::vector<cplx> Yh(static_cast<size_t>(J) * KT);
+  SRP_CUDA_TRY(cudaMemcpyAsync(Yh.data(), d_Y.p, sizeof(double2) * Yh.size(), cudaMemcpyDeviceToHost, s));
+  SRP_CUDA_TRY(cudaStreamSynchronize(s));
+  tall.assign(static_cast<size_t>(J) * R, 0.0);
+  for (int i = 0; i < J; ++i)
+    for (int r = 0; r < R; ++r) tall[static_cast<size_t>(i) * R + r] = Yh[static_cast<size_t>(i) * KT + r];
+  return SRP_OK;
+}
+
 }  // namespace
+
+srp_status fit_lr_device(const Geometry& g, int R, std::vector<std::complex<double>>& tall,
+                         std::vector<std::complex<double>>& fat, std::vector<double>& sigma,
+                         cudaStream_t s) {
+  const int D = g.P * (g.K - 1);
+  const int k = std::min(D, R + 32);
+  if (k <= 32) return run_lr_fit<32>(g, R, k, tall, fat, sigma, s);
+  if (k <= 64) return run_lr_fit<64>(g, R, k, tall, fat, sigma, s);
+  return run_lr_fit<96>(g, R, k, tall, fat, sigma, s);
+}
 
 srp_status fit_low_rank_device(const Geometry& g, int R, std::vector<float>& tall,
                                std::vector<float>& fat, std::vector<double>& sigma,

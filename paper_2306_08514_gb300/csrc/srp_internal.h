@@ -5,6 +5,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -53,6 +54,13 @@ srp_status fit_low_rank(const Geometry& g, int R, std::vector<float>& tall,
 srp_status fit_low_rank_device(const Geometry& g, int R, std::vector<float>& tall,
                                std::vector<float>& fat, std::vector<double>& sigma,
                                cudaStream_t s);
+
+// LR-SRP: the best rank-R approximation of the complex SRP matrix H (J x P(K-1)),
+// H_tall = H V_R (J x R, row-major), H_fat = V_R^H (R x P(K-1)), by a device subspace
+// iteration on H^H H (k_fit.cu).
+srp_status fit_lr_device(const Geometry& g, int R, std::vector<std::complex<double>>& tall,
+                         std::vector<std::complex<double>>& fat, std::vector<double>& sigma,
+                         cudaStream_t s);
 
 // Symmetric eigen-decomposition (cyclic Jacobi).  A: n x n row-major, destroyed;
 // V: eigenvectors as columns; d: eigenvalues (unsorted).
@@ -187,10 +195,12 @@ struct srp_plan_s {
   int num_sms = 0;
   srp::OpType op = srp::OpType::F32;
   int Lpad = 0;       // L rounded up to a multiple of 64 (dense interpolation operands)
-  int slri_exp = 0;
+  int slri_exp = 0;   // tensor-core SLRI: u scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp;
+                      // LR: u scaled by 2^slri_exp, the tall factor by 2^-slri_exp
+  int lr_kd = 0;      // LR: contraction depth of the tall product (2R padded to 64)
   int max_Np = 0;     // largest N_p over the pairs
-  int tc_variant = -1;  // tensor-core kernel variant chosen by srp_plan_autotune (-1: heuristic)
-  bool use_front = false;  // interpolation methods: one fused front-end launch per chunk   // tensor-core SLRI: u is scaled by 2^-slri_exp, Lambda_tall by 2^slri_exp
+  int tc_variant = -1;     // tensor-core kernel variant chosen by srp_plan_autotune (-1: heuristic)
+  bool use_front = false;  // interpolation methods: one fused front-end launch per chunk
   std::vector<double> sigma;
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
   std::vector<int> h_col;
@@ -219,6 +229,9 @@ struct srp_plan_s {
   float* d_xi = nullptr;
   float* d_U = nullptr;
   unsigned long long* d_keys = nullptr;
+  unsigned long long* d_keys2 = nullptr;  // LR: keys of the fat product (not an argmax)
+  void* d_A2 = nullptr;     // LR: u as the operand of the tall product [Fmax][lr_kd]
+  void* d_A2_lo = nullptr;
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
   // staging for srp_map_host
   float* d_stage_frames = nullptr;

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(S):
     dict(window=7), dict(n_aux=-1), dict(max_frames=0), dict(method=9),
     dict(method=1, rank=0), dict(method=1, rank=65), dict(method=2, taps=0.0),
     dict(method=2, taps=1e9), dict(precision=3), dict(far_field=2), dict(far_field=1),
-    dict(method=4, n_aux=0),
+    dict(method=4, n_aux=0), dict(method=5, rank=0), dict(method=5, rank=65), dict(method=6),
 ])
 def test_invalid_desc_is_rejected_on_the_host(S, bad):
     mics = synth.mics_square()

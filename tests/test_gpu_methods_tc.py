@@ -247,3 +247,27 @@ def test_estimates_only(S, uca_small, method, kw, prec):
     plan.status()
     assert np.array_equal(am.cpu().numpy(), am2.cpu().numpy())
     assert np.array_equal(am2.cpu().numpy(), np.argmax(z.cpu().numpy(), axis=1))
+
+
+@pytest.mark.parametrize("name,F,sub,rank,prec", [
+    ("square4", None, 1, 8, "fp32"), ("square4", None, 1, 16, "fp16x3"), ("square4", None, 1, 8, "bf16"),
+    ("uca8", 70, 50, 12, "fp32"), ("uca8", 70, 50, 12, "fp16x3"),
+])
+def test_lr_srp(S, name, F, sub, rank, prec):
+    """LR-SRP (the paper's low-rank competitor, boxed Eq. z_lr): rank-R factors of the complex
+    SRP matrix from the device subspace iteration; singular values and maps vs the oracle's
+    SVD."""
+    w = R.workload(name, F, sub)
+    dt, *_ = R.geometry(name, F, sub)
+    psi = R.psi_of(w["frames"])
+    H = O.steering_matrix_H(dt, w["fs"], w["N"] // 2).reshape(dt.shape[0], -1)
+    tall, fat = O.lr_factors(H, rank)
+    s = np.linalg.svd(H, compute_uv=False)
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="lr", rank=rank,
+                  precision=prec, max_frames=64)
+    assert np.allclose(plan.slri_sigma(rank + 1), s[:rank + 1], rtol=1e-8, atol=1e-8 * s[0])
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    zo = O.srp_lr(tall, fat, psi.reshape(psi.shape[0], -1))
+    assert R.per_frame_rel(z, zo).max() <= dict(PRECS)[prec]
+    check_argmax(z, am, zo)
