@@ -236,8 +236,8 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 
 // ---------------------------------------------------------------------------------
 // Fused front end for the interpolation methods: one CTA per frame runs the STFT + PHAT
-// of every channel (the half-length Stockham FFT of stft_phat_kernel, channel groups of
-// N/4 threads) into shared memory, samples every pair by direct summation (the
+// of every channel (the half-length transform of stft_phat_kernel as a radix-4 Stockham
+// FFT, channel groups of N/8 threads) into shared memory, samples every pair by direct summation (the
 // arithmetic of gcc_direct_kernel, reading y-hat from shared memory), and writes the
 // operand the contraction needs: xi in FP32 [F][L] (FP32 SSPI gather), xi as 16-bit
 // [F][Lpad] (tensor-core SI / TD / SSPI), or u = Lambda_fat xi (SLRI) as FP32 [F][Rp] or
@@ -293,7 +293,7 @@ template <int NQ, int OT>
 __global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const FrontParams a) {
   extern __shared__ float2 sm[];
   const int N = a.N, H = N >> 1, K = H, M = a.M;
-  const int Tg = H >> 1;                // threads per channel group
+  const int Tg = H >> 2;                // threads per channel group (radix-4 FFT)
   const int groups = blockDim.x / Tg;   // channels transformed at once
   float2* tw = sm;                                   // H
   float2* yh = tw + H;                               // M*K
@@ -320,7 +320,7 @@ __global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const Fron
     }
     __syncthreads();
     // every thread of the block takes part in the FFT's barriers
-    const float2* Z = stockham_fft<false>(bufA, bufB, H, grp < groups ? j : 0, tw, 1);
+    const float2* Z = stockham_fft_r4<false>(bufA, bufB, H, grp < groups ? j : 0, tw, 1);
     if (live) {
       float2* out = yh + static_cast<size_t>(m) * K;
       for (int k = j; k < K; k += Tg) {
@@ -440,7 +440,7 @@ __global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const Fron
 int front_max_N() { return 1024; }
 
 size_t front_smem_bytes(int M, int N, int L) {
-  const int H = N / 2, Tg = H / 2;
+  const int H = N / 2, Tg = H / 4;
   const int groups = 256 / Tg;
   return sizeof(float2) * (H + static_cast<size_t>(M) * H + static_cast<size_t>(groups) * 2 * H) +
          sizeof(float) * L;
