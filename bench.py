@@ -58,6 +58,7 @@ def parse(argv=None):
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving run")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--seconds", type=float, default=10.0)
     return ap.parse_args(argv)
@@ -446,6 +447,15 @@ def run_libsrp(a):
                     ro = refs.maps(m, w["frames"][sel])
                     rep[m]["eps_z_vs_conv_db"] = float(np.median(O.eps_db(ro, rc, axis=-1)))
             out["vs_oracle"] = rep
+    if world == 1 and not a.no_serving:
+        # the serving workload's frame-to-map latency, on a reduced session mix (the full
+        # 64-session mix is `--serving`)
+        for m in methods:
+            plans[m].close()
+        res = run_serving(a, sessions=16, seconds=3.0, Ms=(4, 8))
+        res.pop("mix", None)
+        out["serving"] = dict(res, note="16 sessions (M in {4, 8}), Poisson 62.5 frames/s each, "
+                                        "3 s; full mix: bench.py --serving")
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -507,6 +517,22 @@ def session_signal(sess, seconds, fs=16000.0):
     return np.ascontiguousarray(x.astype(np.float32))
 
 
+def slowest_sessions(mix, lats, n=6):
+    """Per-session p99 frame-to-map latency, the n worst sessions with their shapes."""
+    rows = []
+    for k, ls in enumerate(lats):
+        if not ls:
+            continue
+        v = np.concatenate(ls) * 1e3
+        s = mix[k]
+        rows.append({"session": k, "M": s["M"], "J": int(s["grid"].shape[0]), "N": s["N"],
+                     "method": s["kw"]["method"], "frames": int(v.size),
+                     "p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99)),
+                     "max_ms": float(v.max())})
+    rows.sort(key=lambda r: -r["p99_ms"])
+    return rows[:n]
+
+
 def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_batch=16,
                 Ms=(4, 8, 16, 32), quiet=False):
     """Serving workload: `sessions` sessions with Poisson frame arrivals (`rate` frames/s
@@ -551,6 +577,7 @@ def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_b
     stop = threading.Event()
 
     errors = {}
+    lats = [[] for _ in mix]
 
     def poller():
         while not stop.is_set():
@@ -562,6 +589,8 @@ def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_b
                     continue
                 done["frames"] += len(idx)
                 done["cells"] += len(idx) * Js[k]
+                if len(lat):
+                    lats[k].append(lat.copy())
             time.sleep(0.0002)
 
     th = threading.Thread(target=poller, daemon=True)
@@ -603,6 +632,7 @@ def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_b
            "mean_frames_per_launch": st["frames_launched"] / max(1, st["launches"]),
            "admission_build_s": build_s, "push_retries": refused,
            "failed_sessions": {str(k): v for k, v in errors.items()},
+           "slowest_sessions": slowest_sessions(mix, lats),
            "mix": {"M": [s["M"] for s in mix], "J": Js, "N": [s["N"] for s in mix],
                    "method": [s["kw"]["method"] for s in mix]}}
     return res

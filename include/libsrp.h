@@ -329,11 +329,14 @@ srp_status srp_slri_apply_static(const float* xi, const float* fat, const float*
  *   - srp_server_push appends samples; frames of N samples are cut every `hop` samples
  *     (the last N - hop samples of each channel carry over) and queue as pending.
  *   - Continuous batching: a scheduler thread moves each session's pending frames (up to
- *     max_batch, a power of two) into a free launch slot as soon as one is free; frames
- *     arriving meanwhile join a later launch.  Sessions are spread round-robin over
- *     `streams` CUDA streams, so their launches overlap on the device.
- *   - use_graphs: each (slot, batch size) launch sequence -- H2D frames, the SRP path,
- *     D2H maps and argmax, a completion callback -- is captured once and replayed.
+ *     max_batch, a power of two) into a free launch slot as soon as the session's previous
+ *     launch has finished (one launch in flight per session); frames arriving meanwhile
+ *     join the next launch.  Sessions are spread round-robin over `streams` CUDA streams,
+ *     so the launches of different sessions overlap on the device.
+ *   - use_graphs: each (slot, power-of-two batch size) launch sequence -- H2D frames, the
+ *     SRP path, D2H maps and argmax, a completion callback -- is captured as a CUDA graph by
+ *     the builder thread at admission (after srp_plan_autotune picks the session's tile
+ *     shape for max_batch) and replayed by the scheduler.
  *   - Latency of a frame = completion of its map's D2H copy - its arrival time (the time
  *     its last sample was pushed, or the caller's t_arrival).
  * All functions are thread-safe.  The server owns its threads, streams and buffers.

@@ -8,11 +8,13 @@
 //   * Framing with overlap state: pushed samples are cut into frames of N samples with
 //     hop `hop` on the host; the last N - hop samples of every channel carry over.
 //   * Continuous batching: a scheduler thread takes each session's pending frames (up to
-//     max_batch, as a power of two) into one of its launch slots as soon as a slot is
-//     free, so frames arriving while earlier batches run join the next launch.  Sessions
-//     are spread over several CUDA streams, so their work overlaps on the device.
+//     max_batch, as a power of two) into one of its launch slots as soon as the session's
+//     previous launch has finished, so frames arriving while a batch runs join the next
+//     launch.  Sessions are spread over several CUDA streams, so their work overlaps on
+//     the device.
 //   * CUDA graphs: the launch sequence of a slot and batch size (H2D frames, the whole
-//     SRP path, D2H maps and argmax, completion callback) is captured once and replayed.
+//     SRP path, D2H maps and argmax, completion callback) is captured by the builder at
+//     admission, for every power-of-two batch size, and replayed by the scheduler.
 //   * Latency: each frame carries its arrival time (when its last sample was pushed);
 //     the completion callback stamps the time its map is in host memory.
 #include "srp_internal.h"
@@ -195,12 +197,15 @@ cudaError_t launch_slot(Server& sv, Session& ss, Slot& sl, int b) {
 void schedule_session(Server& sv, Session& ss) {
   while (ss.pend_count > 0) {
     Slot* free_sl = nullptr;
-    for (auto& sl : ss.slots)
-      if (sl->state.load() == 0) {
-        free_sl = sl.get();
-        break;
-      }
-    if (!free_sl) return;
+    bool in_flight = false;
+    for (auto& sl : ss.slots) {
+      const int st = sl->state.load();
+      in_flight = in_flight || st == 1;
+      if (st == 0 && !free_sl) free_sl = sl.get();
+    }
+    // One launch in flight per session: frames that arrive meanwhile wait and leave together
+    // in the next launch, which costs about as much as a single frame (a 128-frame tile).
+    if (!free_sl || in_flight) return;
     const int want = std::min(ss.pend_count, sv.desc.max_batch);
     const int b = 1 << floor_log2(want);
     const size_t fsz = static_cast<size_t>(ss.M) * ss.N;
@@ -306,6 +311,30 @@ void builder_loop(Server* sv) {
         }
         bytes += fb + mbytes + mb * 4;
         slots.push_back(std::move(sl));
+      }
+      // capture every (slot, power-of-two batch) launch sequence now, on the builder's own
+      // stream (a graph can be launched into any stream), so that no capture or
+      // instantiation happens on the scheduler thread while sessions are served
+      if (err.empty() && sv->desc.use_graphs) {
+        Session tmp_view;  // enqueue() reads the plan and the sizes only
+        tmp_view.plan = plan;
+        tmp_view.M = pick->M;
+        tmp_view.N = pick->N;
+        tmp_view.J = pick->J;
+        for (auto& sl : slots) {
+          for (int k = 0; (1 << k) <= sv->desc.max_batch && err.empty(); ++k) {
+            cudaGraph_t gr = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(sv->build_stream, cudaStreamCaptureModeThreadLocal);
+            cudaError_t e2 = e == cudaSuccess ? enqueue(tmp_view, *sl, 1 << k, sv->build_stream) : e;
+            if (e == cudaSuccess) e = cudaStreamEndCapture(sv->build_stream, &gr);
+            if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&sl->graphs[k], gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+              cudaGetLastError();
+              err = std::string("graph capture failed: ") + cudaGetErrorString(e2 != cudaSuccess ? e2 : e);
+            }
+          }
+        }
       }
     }
     lk.lock();
