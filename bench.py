@@ -61,6 +61,7 @@ def parse(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving run")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--seconds", type=float, default=10.0)
+    ap.add_argument("--rate", type=float, default=62.5, help="serving: frames/s per session")
     return ap.parse_args(argv)
 
 
@@ -643,11 +644,12 @@ def main():
     if a.impl == "reference":
         run_reference(a)
     elif a.serving:
-        res = run_serving(a, sessions=a.sessions, seconds=a.seconds, precision=a.precision)
+        res = run_serving(a, sessions=a.sessions, seconds=a.seconds, precision=a.precision,
+                          rate=a.rate)
         out = {"metric": "serving: map cells*frames/s and frame-to-map latency", "value": res["cells_frames_per_s"],
                "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": a.precision,
                "data": "synthetic", "config": {"workload": f"serving: {a.sessions} sessions, Poisson "
-                                               f"62.5 frames/s each, {a.seconds} s"},
+                                               f"{a.rate} frames/s each, {a.seconds} s"},
                "serving": res}
         print(json.dumps(out), flush=True)
     else:

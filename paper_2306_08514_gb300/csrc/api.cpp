@@ -119,6 +119,9 @@ constexpr int kSlriKd = 64;
 // Largest L for which the low-rank fit eigen-decomposes the L x L Gram matrix on the host.
 constexpr int kGramMaxL = 768;
 
+// Beyond this L (without the fused front end) SLRI forms u = Lambda_fat xi as a GEMM.
+constexpr int kFatGemmMinL = 1024;
+
 // One chunk of at most Fmax frames through the whole path.
 constexpr int kMaxChunkEvents = 4096;
 
@@ -260,7 +263,13 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     case SRP_SLRI: {
       SRP_LAUNCH(sample_gcc(p, p->d_yhat, F, p->d_xi, s));
       SRP_MARK(p, 2, s);
-      SRP_LAUNCH(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
+      if (p->fat_gemm) {
+        SRP_LAUNCH(launch_pack16(p->d_xi, F, g.L, p->Lpad, 1.f, p->op, p->d_A2, p->d_A2_lo, s));
+        SRP_CUDA_TRY(contract_to(p, p->d_A2, p->d_A2_lo, p->d_H, p->d_H_lo, p->Lpad, nullptr,
+                                 nullptr, F, p->d_U, Rp, p->d_keys2, s));
+      } else {
+        SRP_LAUNCH(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
+      }
       if (p->op == OpType::F32) {
         SRP_LAUNCH(launch_slri_tall(p->d_U, p->d_tall, maps, p->d_keys, F, g.J, Rp, s));
       } else {
@@ -551,9 +560,28 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
         if (split) SRP_ALLOC(p, p->d_A_lo, F * kSlriKd * eb);
         SRP_PLAN_CUDA(p, launch_pack16(p->d_tall, g.J, Rp, kSlriKd, std::ldexp(1.f, p->slri_exp),
                                        p->op, p->d_B, p->d_B_lo, s));
-        const size_t ws = tc_gemm_workspace_floats(p->Fmax, g.J, kSlriKd, split ? 3 : 1, p->num_sms);
-        if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
       }
+      size_t ws = p->op == OpType::F32
+                      ? 0
+                      : tc_gemm_workspace_floats(p->Fmax, g.J, kSlriKd, split ? 3 : 1, p->num_sms);
+      if (!p->use_front && g.L > kFatGemmMinL) {
+        // long sample vectors: u = Lambda_fat xi as a GEMM (xi operand [F][Lpad], factor
+        // [Rp][Lpad]) instead of the per-frame dot products
+        p->fat_gemm = true;
+        SRP_ALLOC(p, p->d_H, static_cast<size_t>(Rp) * p->Lpad * eb);
+        if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(Rp) * p->Lpad * eb);
+        SRP_ALLOC(p, p->d_A2, F * p->Lpad * eb);
+        if (split) SRP_ALLOC(p, p->d_A2_lo, F * p->Lpad * eb);
+        SRP_ALLOC(p, p->d_keys2, sizeof(unsigned long long) * F);
+        SRP_PLAN_CUDA(p, launch_pack16(p->d_fat, Rp, g.L, p->Lpad, 1.f, p->op, p->d_H, p->d_H_lo, s));
+        if (p->op == OpType::F32) {
+          const int nsplit = sgemm_split_count(p->Lpad);
+          if (nsplit > 1) ws = std::max(ws, static_cast<size_t>(nsplit) * F * Rp);
+        } else {
+          ws = std::max(ws, tc_gemm_workspace_floats(p->Fmax, Rp, p->Lpad, split ? 3 : 1, p->num_sms));
+        }
+      }
+      if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
       SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
     } else {
       const int Lpad = p->Lpad;

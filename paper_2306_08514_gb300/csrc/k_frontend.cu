@@ -95,7 +95,7 @@ __global__ void gcc_samples_kernel(const float2* __restrict__ yhat, int M, int P
                                    const float2* __restrict__ twiddle, float* __restrict__ xi) {
   extern __shared__ float2 smem[];
   const int K = N >> 1;
-  const int T = N >> 1;
+  const int T = N >> 2;       // threads: one radix-4 butterfly each per stage
   float2* tw = smem;          // N/2
   float2* bufA = smem + K;    // N
   float2* bufB = bufA + N;    // N
@@ -120,7 +120,7 @@ __global__ void gcc_samples_kernel(const float2* __restrict__ yhat, int M, int P
     bufA[N - k] = make_float2(a.x + b.y, b.x - a.y);      // psi_a^* + i psi_b^*
   }
   __syncthreads();
-  const float2* x = stockham_fft<true>(bufA, bufB, N, j, tw, 0);
+  const float2* x = stockham_fft_r4<true>(bufA, bufB, N, j, tw, 0);
   const int na = Np[pa];
   float* outa = xi + static_cast<size_t>(f) * L + off[pa];
   for (int t = j; t < 2 * na + 1; t += T) outa[t] = x[(t - na + N) & (N - 1)].x;
@@ -137,7 +137,7 @@ cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, c
   if (F <= 0) return cudaSuccess;
   dim3 grid((P + 1) / 2, F);
   const size_t smem = sizeof(float2) * (N / 2 + 2 * static_cast<size_t>(N));
-  gcc_samples_kernel<<<grid, N / 2, smem, s>>>(yhat, M, P, N, pairs, Np, off, L, twiddle, xi);
+  gcc_samples_kernel<<<grid, N / 4, smem, s>>>(yhat, M, P, N, pairs, Np, off, L, twiddle, xi);
   return cudaGetLastError();
 }
 
@@ -157,55 +157,79 @@ __device__ __forceinline__ float2 tw_pos(const float2* __restrict__ tw, int u, i
 }
 
 template <int NQ>
-__global__ __launch_bounds__(256) void gcc_direct_kernel(const float2* __restrict__ yhat, int M,
+__global__ __launch_bounds__(256, 2) void gcc_direct_kernel(const float2* __restrict__ yhat, int M,
                                                          int P, int K, const int2* __restrict__ pairs,
                                                          const int* __restrict__ Np,
                                                          const int* __restrict__ off, int L,
                                                          const float2* __restrict__ tw,
                                                          float* __restrict__ xi) {
+  // G pairs per warp share the rotation e^{j pi k n / K} (it depends on (k, n) only)
+  constexpr int G = NQ <= 16 ? 2 : 1;
   const int f = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float2* yf = yhat + static_cast<size_t>(f) * M * K;
   const int twoK = 2 * K;
-  for (int q = warp; q < P; q += nw) {
-    const int nq = Np[q];
-    const int2 pr = pairs[q];
-    float c[NQ + 1], sn[NQ + 1];
+  for (int q0 = warp * G; q0 < P; q0 += nw * G) {
+    int nq[G], mA[G], mB[G];
+    int nqmax = 0;
 #pragma unroll
-    for (int n = 0; n <= NQ; ++n) c[n] = sn[n] = 0.f;
+    for (int g = 0; g < G; ++g) {
+      const bool ok = q0 + g < P;
+      nq[g] = ok ? Np[q0 + g] : -1;
+      const int2 pr = ok ? pairs[q0 + g] : make_int2(0, 0);
+      mA[g] = pr.x * K;
+      mB[g] = pr.y * K;
+      nqmax = max(nqmax, nq[g]);
+    }
+    float c[G][NQ + 1], sn[G][NQ + 1];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int n = 0; n <= NQ; ++n) c[g][n] = sn[g][n] = 0.f;
     for (int k = 1 + lane; k < K; k += 32) {
-      const float2 psi = cmul_conj(__ldg(yf + pr.x * K + k), __ldg(yf + pr.y * K + k));
+      float2 psi[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        psi[g] = cmul_conj(__ldg(yf + mA[g] + k), __ldg(yf + mB[g] + k));
+        c[g][0] += psi[g].x;
+      }
       const float2 step = tw_pos(tw, k, K);
       float2 e = make_float2(1.f, 0.f);
-      c[0] += psi.x;
 #pragma unroll
       for (int n = 1; n <= NQ; ++n) {
-        if (n > nq) break;
+        if (n > nqmax) break;
         if ((n & 7) == 0) {
           e = tw_pos(tw, (k * n) & (twoK - 1), K);
         } else {
           e = cmul(e, step);
         }
-        c[n] = fmaf(psi.x, e.x, c[n]);
-        sn[n] = fmaf(psi.y, e.y, sn[n]);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          c[g][n] = fmaf(psi[g].x, e.x, c[g][n]);
+          sn[g][n] = fmaf(psi[g].y, e.y, sn[g][n]);
+        }
       }
     }
 #pragma unroll
-    for (int n = 0; n <= NQ; ++n) {
-      if (n > nq) break;
+    for (int g = 0; g < G; ++g) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        c[n] += __shfl_xor_sync(0xFFFFFFFFu, c[n], o);
-        sn[n] += __shfl_xor_sync(0xFFFFFFFFu, sn[n], o);
+      for (int n = 0; n <= NQ; ++n) {
+        if (n > nq[g]) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          c[g][n] += __shfl_xor_sync(0xFFFFFFFFu, c[g][n], o);
+          sn[g][n] += __shfl_xor_sync(0xFFFFFFFFu, sn[g][n], o);
+        }
       }
-    }
-    float* out = xi + static_cast<size_t>(f) * L + off[q] + nq;  // lag 0
+      if (nq[g] < 0) continue;
+      float* out = xi + static_cast<size_t>(f) * L + off[q0 + g] + nq[g];  // lag 0
 #pragma unroll
-    for (int n = 0; n <= NQ; ++n) {
-      if (n > nq) break;
-      if (lane == n % 32) {
-        out[n] = 2.f * (c[n] - sn[n]);
-        if (n > 0) out[-n] = 2.f * (c[n] + sn[n]);
+      for (int n = 0; n <= NQ; ++n) {
+        if (n > nq[g]) break;
+        if (lane == n % 32) {
+          out[n] = 2.f * (c[g][n] - sn[g][n]);
+          if (n > 0) out[-n] = 2.f * (c[g][n] + sn[g][n]);
+        }
       }
     }
   }

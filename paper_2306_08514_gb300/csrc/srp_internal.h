@@ -201,6 +201,7 @@ struct srp_plan_s {
   int max_Np = 0;     // largest N_p over the pairs
   int tc_variant = -1;     // tensor-core kernel variant chosen by srp_plan_autotune (-1: heuristic)
   bool use_front = false;  // interpolation methods: one fused front-end launch per chunk
+  bool fat_gemm = false;   // SLRI with long sample vectors: u = Lambda_fat xi as a GEMM
   std::vector<double> sigma;
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
   std::vector<int> h_col;
