@@ -31,7 +31,7 @@ class srp_plan_desc(C.Structure):
         ("fs", C.c_double), ("N", C.c_int), ("window", C.c_int), ("c", C.c_double),
         ("n_aux", C.c_int), ("method", C.c_int), ("rank", C.c_int),
         ("taps_per_loc_pair", C.c_double), ("precision", C.c_int), ("max_frames", C.c_int),
-        ("far_field", C.c_int),
+        ("far_field", C.c_int), ("h_on_the_fly", C.c_int),
     ]
 
 
@@ -223,7 +223,8 @@ def srp_destroy(plan) -> None:
 
 # ---- convenience wrapper ----------------------------------------------------------
 def make_desc(mic_xyz, grid_xyz, fs, N, method="conv", rank=0, taps=0.0, precision="fp32",
-              window="hann", c=340.0, n_aux=2, max_frames=256, far_field=False):
+              window="hann", c=340.0, n_aux=2, max_frames=256, far_field=False,
+              h_on_the_fly=0):
     mic = np.ascontiguousarray(mic_xyz, dtype=np.float64)
     grid = np.ascontiguousarray(grid_xyz, dtype=np.float64)
     d = srp_plan_desc()
@@ -237,6 +238,7 @@ def make_desc(mic_xyz, grid_xyz, fs, N, method="conv", rank=0, taps=0.0, precisi
     d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     d.max_frames = int(max_frames)
     d.far_field = 1 if far_field else 0
+    d.h_on_the_fly = int(h_on_the_fly)
     d._keep = (mic, grid)  # keep the arrays alive while the struct is used
     return d
 
@@ -252,9 +254,9 @@ class Plan:
 
     def __init__(self, mic_xyz, grid_xyz, fs, N, method="conv", rank=0, taps=0.0,
                  precision="fp32", window="hann", c=340.0, n_aux=2, max_frames=256,
-                 stream=None, far_field=False):
+                 stream=None, far_field=False, h_on_the_fly=0):
         self.desc = make_desc(mic_xyz, grid_xyz, fs, N, method, rank, taps, precision, window,
-                              c, n_aux, max_frames, far_field)
+                              c, n_aux, max_frames, far_field, h_on_the_fly)
         self.handle = srp_plan_create(self.desc, _stream_handle(stream))
         self.info = srp_plan_info(self.handle)
         self.M, self.J, self.N, self.L, self.P = (self.info.M, self.info.J, self.info.N,

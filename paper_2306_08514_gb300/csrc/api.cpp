@@ -41,6 +41,7 @@ srp_status validate(const srp_plan_desc* d) {
   if (d->max_frames < 1 || d->max_frames > 65536)
     return fail(SRP_EINVAL, "max_frames must be in 1..65536");
   if (d->far_field != 0 && d->far_field != 1) return fail(SRP_EINVAL, "far_field must be 0 or 1");
+  if (d->h_on_the_fly < -1 || d->h_on_the_fly > 1) return fail(SRP_EINVAL, "h_on_the_fly must be -1, 0 or 1");
   for (int i = 0; i < 3 * d->M; ++i)
     if (!std::isfinite(d->mic_xyz[i])) return fail(SRP_EINVAL, "mic_xyz has a non-finite value");
   for (long long i = 0; i < 3ll * d->J; ++i)
@@ -83,7 +84,7 @@ void free_plan(srp_plan_s* p) {
                   p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
                   p->d_hist[1], p->d_stream_frames, p->d_est_maps, p->d_A2, p->d_A2_lo,
-                  p->d_keys2};
+                  p->d_keys2, p->d_tau_hi, p->d_tau_lo};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -121,6 +122,9 @@ constexpr int kGramMaxL = 768;
 
 // Beyond this L (without the fused front end) SLRI forms u = Lambda_fat xi as a GEMM.
 constexpr int kFatGemmMinL = 1024;
+
+// A stored SRP matrix above this size is generated on the fly instead (FP32 conv).
+constexpr double kMaxStoredH = 64e9;
 
 // One chunk of at most Fmax frames through the whole path.
 constexpr int kMaxChunkEvents = 4096;
@@ -242,8 +246,15 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       SRP_LAUNCH(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
                                     p->d_A_lo, s));
       SRP_MARK(p, 2, s);
-      SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, nullptr, nullptr,
-                            F, maps, s));
+      if (p->h_generated) {
+        p->launches += sgemm_split_count(g.P * g.N) > 1 ? 2 : 1;
+        SRP_CUDA_TRY(launch_sgemm_nt_argmax(static_cast<const float*>(p->d_A), nullptr, maps,
+                                            p->d_keys, F, g.J, g.P * g.N, p->d_split, s,
+                                            p->d_tau_hi, p->d_tau_lo, g.P, g.N));
+      } else {
+        SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, nullptr, nullptr,
+                              F, maps, s));
+      }
       break;
     }
     case SRP_LR: {
@@ -376,9 +387,11 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   if (desc->method == SRP_CONV) {
     const double hbytes = static_cast<double>(g.J) * g.P * g.N * op_bytes(p->op) *
                           (p->op == OpType::F16X2 ? 2 : 1);
-    if (hbytes > 200e9) {
+    p->h_generated = desc->h_on_the_fly == 1 || (desc->h_on_the_fly == 0 && hbytes > kMaxStoredH);
+    if (p->h_generated && p->op != OpType::F32) {
       delete p;
-      return fail(SRP_EUNSUPPORTED, "SRP matrix would need more than 200 GB");
+      return fail(SRP_EUNSUPPORTED, "the SRP matrix would need " + std::to_string(hbytes / 1e9) +
+                                        " GB: generating it on the fly needs SRP_FP32");
     }
   }
 
@@ -411,7 +424,28 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   SRP_ALLOC(p, p->d_err, sizeof(int));
   SRP_PLAN_CUDA(p, cudaMemsetAsync(p->d_err, 0, sizeof(int), s));
 
-  if (desc->method == SRP_CONV) {
+  if (desc->method == SRP_CONV && p->h_generated) {
+    // the SRP matrix is generated inside the GEMM from the TDOAs split as tau_hi + tau_lo,
+    // tau_hi with 13 significant bits (so k tau_hi is exact in FP32 for k < 2^11)
+    const size_t Kd = static_cast<size_t>(g.P) * g.N;
+    std::vector<float> th(g.tau.size()), tl(g.tau.size());
+    for (size_t e = 0; e < g.tau.size(); ++e) {
+      const double t = g.tau[e];
+      int ex = 0;
+      const double m = std::frexp(t, &ex);                     // t = m 2^ex, 0.5 <= |m| < 1
+      const double hi = std::ldexp(std::trunc(std::ldexp(m, 13)), ex - 13);
+      th[e] = static_cast<float>(hi);
+      tl[e] = static_cast<float>(t - hi);
+    }
+    SRP_ALLOC(p, p->d_tau_hi, sizeof(float) * th.size());
+    SRP_ALLOC(p, p->d_tau_lo, sizeof(float) * tl.size());
+    SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau_hi, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, s));
+    SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau_lo, tl.data(), sizeof(float) * tl.size(), cudaMemcpyHostToDevice, s));
+    SRP_ALLOC(p, p->d_A, F * Kd * sizeof(float));
+    const int nsplit = sgemm_split_count(static_cast<int>(Kd));
+    if (nsplit > 1) SRP_ALLOC(p, p->d_split, sizeof(float) * nsplit * F * g.J);
+    SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
+  } else if (desc->method == SRP_CONV) {
     const size_t Kd = static_cast<size_t>(g.P) * g.N;
     const size_t eb = op_bytes(p->op);
     const bool split = p->op == OpType::F16X2;
@@ -730,10 +764,13 @@ extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t*
   const double Lpad = std::ceil(L / 64.0) * 64.0;
   double b = F * d.M * K * 8.0 + F * 8.0 + 4096.0;  // y-hat, argmax keys, small tables
   switch (d.method) {
-    case SRP_CONV:
-      b += (J + F) * P * N * eb * planes;
+    case SRP_CONV: {
+      const double hb = J * P * N * eb * planes;
+      const bool gen = d.h_on_the_fly == 1 || (d.h_on_the_fly == 0 && hb > 64e9);
+      b += (gen ? J * P * 8.0 : hb) + F * P * N * eb * planes;
       if (d.precision == SRP_FP32 && P * N > 16384) b += std::ceil(P * N / 16384.0) * F * J * 4.0;
       break;
+    }
     case SRP_SLRI: {
       const double Rp = std::ceil(d.rank / 8.0) * 8.0;
       b += F * L * 4.0 + (J + L + F) * Rp * 4.0;

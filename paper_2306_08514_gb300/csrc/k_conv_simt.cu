@@ -20,10 +20,37 @@ constexpr int BM = 128, BN = 128, BK = 8, PADS = 4;
 // (the partials are summed by split_reduce_argmax_kernel).
 // Frame tiles run fastest (blockIdx.x) so the CTAs in flight share the B (SRP matrix)
 // tiles through L2.
-template <bool SPLIT>
+//
+// GEN: B is the SRP matrix generated on the fly instead of read (for grids whose stored
+// matrix would not fit): column c = p N + r holds 2cos(theta_k) (r = k < K) or
+// -2sin(theta_k) (r = K + k), theta_k = 2 pi frac(k tau_p(i) / N), k = 0 giving 0.  tau is
+// split as tau_hi + tau_lo with tau_hi carrying 13 significant bits, so k tau_hi (k < 2^11)
+// and its fraction of N are exact in FP32 and the phase is accurate to ~1e-7.
+struct GenB {
+  const float* tau_hi;  // [J][P]
+  const float* tau_lo;  // [J][P]
+  int P, N;
+};
+
+__device__ __forceinline__ float gen_b(const GenB& g, int i, int c) {
+  const int q = c / g.N, r = c - q * g.N;
+  const int K = g.N >> 1;
+  const int k = r < K ? r : r - K;
+  if (k == 0) return 0.f;
+  const float th = __ldg(g.tau_hi + static_cast<size_t>(i) * g.P + q);
+  const float tl = __ldg(g.tau_lo + static_cast<size_t>(i) * g.P + q);
+  const float invN = 1.f / static_cast<float>(g.N);
+  const float x = static_cast<float>(k) * th * invN;  // exact
+  const float rr = (x - floorf(x)) + static_cast<float>(k) * tl * invN;
+  float sn, cs;
+  sincospif(2.f * rr, &sn, &cs);
+  return r < K ? 2.f * cs : -2.f * sn;
+}
+
+template <bool SPLIT, bool GEN>
 __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
     const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ Z,
-    unsigned long long* __restrict__ keys, int F, int J, int Kd, int kslice) {
+    unsigned long long* __restrict__ keys, int F, int J, int Kd, int kslice, const GenB gb) {
   __shared__ __align__(16) float As[2][BK][BM + PADS];
   __shared__ __align__(16) float Bs[2][BK][BN + PADS];
   const int tid = threadIdx.x;
@@ -36,10 +63,18 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
   const int kend = SPLIT ? min(Kd, kbeg + kslice) : Kd;
   if (SPLIT) Z += static_cast<size_t>(blockIdx.z) * F * J;
   const float4* Ap = reinterpret_cast<const float4*>(A + static_cast<size_t>(aok ? m0 + lr : 0) * Kd + kbeg + lk);
-  const float4* Bp = reinterpret_cast<const float4*>(B + static_cast<size_t>(bok ? n0 + lr : 0) * Kd + kbeg + lk);
+  const float4* Bp = GEN ? nullptr
+                        : reinterpret_cast<const float4*>(B + static_cast<size_t>(bok ? n0 + lr : 0) * Kd + kbeg + lk);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto load_b = [&](int kt) -> float4 {
+    if (!bok) return z4;
+    if (!GEN) return __ldg(Bp + kt * (BK / 4));
+    const int c = kbeg + kt * BK + lk;
+    return make_float4(gen_b(gb, n0 + lr, c), gen_b(gb, n0 + lr, c + 1), gen_b(gb, n0 + lr, c + 2),
+                       gen_b(gb, n0 + lr, c + 3));
+  };
   float4 ra = aok ? __ldg(Ap) : z4;
-  float4 rb = bok ? __ldg(Bp) : z4;
+  float4 rb = load_b(0);
   As[0][lk + 0][lr] = ra.x; As[0][lk + 1][lr] = ra.y; As[0][lk + 2][lr] = ra.z; As[0][lk + 3][lr] = ra.w;
   Bs[0][lk + 0][lr] = rb.x; Bs[0][lk + 1][lr] = rb.y; Bs[0][lk + 2][lr] = rb.z; Bs[0][lk + 3][lr] = rb.w;
   __syncthreads();
@@ -55,7 +90,7 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
     const int cur = kt & 1;
     if (kt + 1 < nk) {
       ra = aok ? __ldg(Ap + (kt + 1) * (BK / 4)) : z4;
-      rb = bok ? __ldg(Bp + (kt + 1) * (BK / 4)) : z4;
+      rb = load_b(kt + 1);
     }
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
@@ -143,20 +178,29 @@ int sgemm_split_count(int Kd) {
 
 cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
                                    unsigned long long* keys, int F, int J, int Kd,
-                                   float* split_ws, cudaStream_t s) {
+                                   float* split_ws, cudaStream_t s, const float* tau_hi,
+                                   const float* tau_lo, int P, int N) {
   if (F <= 0) return cudaSuccess;
   if (Kd % BK != 0) return cudaErrorInvalidValue;
+  const bool gen = tau_hi != nullptr;
+  const GenB gb{tau_hi, tau_lo, P, N};
   const int nsplit = sgemm_split_count(Kd);
   if (nsplit == 1) {
     dim3 grid((F + BM - 1) / BM, (J + BN - 1) / BN, 1);
-    sgemm_nt_argmax_kernel<false><<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd, Kd);
+    if (gen)
+      sgemm_nt_argmax_kernel<false, true><<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd, Kd, gb);
+    else
+      sgemm_nt_argmax_kernel<false, false><<<grid, 256, 0, s>>>(A, B, Z, keys, F, J, Kd, Kd, gb);
     return cudaGetLastError();
   }
   if (!split_ws) return cudaErrorInvalidValue;
   int kslice = (Kd / BK + nsplit - 1) / nsplit * BK;
   const int nz = (Kd + kslice - 1) / kslice;
   dim3 grid((F + BM - 1) / BM, (J + BN - 1) / BN, nz);
-  sgemm_nt_argmax_kernel<true><<<grid, 256, 0, s>>>(A, B, split_ws, keys, F, J, Kd, kslice);
+  if (gen)
+    sgemm_nt_argmax_kernel<true, true><<<grid, 256, 0, s>>>(A, B, split_ws, keys, F, J, Kd, kslice, gb);
+  else
+    sgemm_nt_argmax_kernel<true, false><<<grid, 256, 0, s>>>(A, B, split_ws, keys, F, J, Kd, kslice, gb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_split_reduce(split_ws, nz, Z, keys, F, J, s);

@@ -112,9 +112,12 @@ cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpTyp
 // (sgemm_split_count(Kd) > 1) the k range is split into slices of <= 16384 terms whose
 // partial maps go to split_ws [nsplit][F][J] and are summed in FP64.
 int sgemm_split_count(int Kd);
+// With tau_hi != NULL, B is not read: the SRP matrix of P pairs and frame length N is
+// generated on the fly from the split TDOA table tau_hi + tau_lo [J][P] (FP32 pairs).
 cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
                                    unsigned long long* keys, int F, int J, int Kd,
-                                   float* split_ws, cudaStream_t s);
+                                   float* split_ws, cudaStream_t s, const float* tau_hi = nullptr,
+                                   const float* tau_lo = nullptr, int P = 0, int N = 0);
 // Sums nz partial maps [nz][F][J] in FP64 into Z and merges the argmax keys.
 cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long long* keys,
                                 int F, int J, cudaStream_t s);
@@ -202,6 +205,7 @@ struct srp_plan_s {
   int tc_variant = -1;     // tensor-core kernel variant chosen by srp_plan_autotune (-1: heuristic)
   bool use_front = false;  // interpolation methods: one fused front-end launch per chunk
   bool fat_gemm = false;   // SLRI with long sample vectors: u = Lambda_fat xi as a GEMM
+  bool h_generated = false;  // conv FP32: SRP matrix generated inside the GEMM, not stored
   std::vector<double> sigma;
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
   std::vector<int> h_col;
@@ -213,6 +217,8 @@ struct srp_plan_s {
   float2* d_twiddle = nullptr;
   float* d_window = nullptr;
   void* d_H = nullptr;
+  float* d_tau_hi = nullptr;  // conv with the SRP matrix generated on the fly: split TDOAs
+  float* d_tau_lo = nullptr;
   void* d_H_lo = nullptr;
   float* d_tall = nullptr;
   float* d_fat = nullptr;

@@ -354,3 +354,19 @@ def test_stream_push_keeps_overlap(S, method, kw, hop):
     m, a = plan.stream_push(_cuda(hops[:2]))
     torch.cuda.synchronize()
     assert np.array_equal(m.cpu().numpy(), zr[:2])
+
+
+@pytest.mark.parametrize("name,F,sub", [("square4", None, 1), ("uca8", 70, 13), ("nested32", 6, 400)])
+def test_conv_srp_matrix_generated_on_the_fly(S, name, F, sub):
+    """conv. FD-SRP with the SRP matrix generated inside the FP32 GEMM (for grids whose
+    stored matrix would not fit): same maps as the FP64 oracle, N up to 2048."""
+    w = R.workload(name, F, sub)
+    dt, *_ = R.geometry(name, F, sub)
+    psi = R.psi_of(w["frames"])
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="conv", h_on_the_fly=1,
+                  max_frames=64)
+    assert plan.info.device_bytes < w["grid_xyz"].shape[0] * plan.P * w["N"] * 4  # H not stored
+    z, am = _run(plan, w["frames"])
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    check_argmax(z, am, zo)
