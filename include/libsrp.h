@@ -52,7 +52,7 @@ typedef enum {
   SRP_ENOMEM = 2,       /* a device or host allocation failed */
   SRP_ECUDA = 3,        /* a CUDA runtime call failed (message carries its text) */
   SRP_ETIMEOUT = 4,     /* a bounded wait ran out */
-  SRP_EUNSUPPORTED = 5, /* valid request this build does not implement */
+  SRP_EUNSUPPORTED = 5, /* valid request that libsrp does not implement */
   SRP_EAGAIN = 6        /* a bounded queue is full: retry after draining results */
 } srp_status;
 
@@ -152,9 +152,10 @@ typedef struct {
  * desc:   host, read only; the arrays are copied.
  * stream: stream for the uploads; the call returns after they complete.
  * out:    receives the plan handle (NULL on failure).
- * Errors: SRP_EINVAL (bad desc, including N_p >= K), SRP_EUNSUPPORTED (size beyond
- * this build: the FP32 SSPI gather with L > 1700, a device operand above 200 GB, a
- * low-rank fit that does not converge), SRP_ENOMEM, SRP_ECUDA.
+ * Errors: SRP_EINVAL (bad desc, including N_p >= K), SRP_EUNSUPPORTED (sizes libsrp does
+ * not handle: the FP32 SSPI gather with L > 1700, a device operand above 200 GB, a
+ * low-rank fit that does not converge, 16-bit LR operands out of range), SRP_ENOMEM,
+ * SRP_ECUDA.
  */
 srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out);
 
