@@ -59,6 +59,7 @@ def parse(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving run")
+    ap.add_argument("--curve", action="store_true", help="map error vs throughput over R / t")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--rate", type=float, default=62.5, help="serving: frames/s per session")
@@ -639,10 +640,81 @@ def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_b
     return res
 
 
+def run_curve(a):
+    """Map error vs throughput over the methods' complexity parameters (the paper's
+    trade-off, Sec. V): every point times srp_map on the workload's F frames (L2 flushed,
+    CUDA events) and compares sampled frames with the FP64 conv. FD-SRP oracle: eps_z in dB
+    (Sec. V-A) and the distance of the argmax location to the true source."""
+    import torch
+    import oracle as O
+    import paper_2306_08514_gb300 as S
+    import synth
+    torch.cuda.set_device(0)
+    w = synth.workload(a.workload, F=a.frames)
+    F, J, N, M = w["F"], w["grid_xyz"].shape[0], w["N"], w["mic_xyz"].shape[0]
+    P, K = M * (M - 1) // 2, N // 2
+    frames = torch.from_numpy(w["frames"]).cuda()
+    sel = np.linspace(0, F - 1, 32).astype(int)
+    dt = O.tdoa_nf(w["mic_xyz"], w["grid_xyz"])
+    zc = O.srp_conv(O.gcc_phat(O.stft(w["frames"][sel], "hann")), dt, w["fs"])
+    src = np.asarray(w["sources"][0], float)
+    Nm = O.mean_samples(O.n_p_samples(w["mic_xyz"], w["fs"]))
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    points = [("conv", {}, "fp32"), ("conv", {}, "fp16x3"), ("conv", {}, "bf16")]
+    points += [("slri", {"rank": r}, "bf16") for r in (2, 4, 8, 16, 32, 64)]
+    points += [("sspi", {"taps": t}, "bf16") for t in (0.5, 1.0, 2.0, 4.0, 8.0)]
+    points += [("lr", {"rank": r}, "bf16") for r in (4, 16, 32)]
+    points += [("si", {}, "bf16"), ("td", {}, "bf16")]
+    out = []
+    for method, kw, prec in points:
+        plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], N, method=method, precision=prec,
+                      max_frames=F, **kw)
+        plan.autotune(F)
+        maps = torch.empty((F, J), dtype=torch.float32, device="cuda")
+        am = torch.empty((F,), dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            plan.map(frames, maps, am)
+        times = []
+        for _ in range(5):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.map(frames, maps, am)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        plan.status()
+        z = maps[torch.from_numpy(sel).cuda()].double().cpu().numpy()
+        idx = am.cpu().numpy()[sel]
+        eps = O.eps_db(z, zc, axis=-1)
+        loc = np.linalg.norm(w["grid_xyz"][idx] - src[None, :], axis=1)
+        loc_c = np.linalg.norm(w["grid_xyz"][np.argmax(zc, axis=1)] - src[None, :], axis=1)
+        cx = O.complexity(J, P, K, N_mean=Nm, R=kw.get("rank"), R_H=kw.get("rank"),
+                          Q_Lambda=round(kw.get("taps", 0) * J * P) or None)
+        key = {"conv": "C", "slri": "C_slri", "sspi": "C_sspi", "lr": "C_lr", "si": "C_si",
+               "td": "C_td"}[method]
+        ms = float(np.median(times))
+        out.append({"method": method, **kw, "precision": prec, "ms": ms,
+                    "cells_frames_per_s": J * F / (ms / 1e3),
+                    "eps_z_db_median": float(np.median(eps)), "eps_z_db_max": float(np.max(eps)),
+                    "loc_err_m_median": float(np.median(loc)),
+                    "argmax_agree_conv_oracle": float(np.mean(idx == np.argmax(zc, axis=1))),
+                    "C_rel": float(cx[key] / cx["C"])})
+        plan.close()
+        del maps
+        print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+    res = {"metric": "SRP map error vs throughput (eps_z vs the FP64 conv. FD-SRP oracle)",
+           "unit": UNIT, "workload": a.workload, "F": F, "J": J,
+           "conv_oracle_loc_err_m_median": float(np.median(loc_c)), "points": out}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.curve:
+        run_curve(a)
     elif a.serving:
         res = run_serving(a, sessions=a.sessions, seconds=a.seconds, precision=a.precision,
                           rate=a.rate)
