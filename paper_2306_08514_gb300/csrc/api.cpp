@@ -79,6 +79,10 @@ cudaError_t dalloc(srp_plan_s* p, T** ptr, size_t bytes) {
 
 void free_plan(srp_plan_s* p) {
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->pipe_events)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t cs : p->copy_streams)
+    if (cs) cudaStreamDestroy(cs);
   void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
                   p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
@@ -888,18 +892,48 @@ extern "C" srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, 
     plan->d_stage_arg = static_cast<int*>(c);
     plan->device_bytes += sizeof(float) * Fm * (g.M * g.N + g.J) + sizeof(int) * Fm;
   }
+  // Pipelined: the frames go through the path in sub-batches on `stream`; the maps of each
+  // sub-batch leave on two copy streams (alternating) while the next sub-batch computes.
+  if (!plan->copy_streams[0]) {
+    for (int k = 0; k < 2; ++k)
+      SRP_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_streams[k], cudaStreamNonBlocking));
+    for (int k = 0; k < kHostPipe; ++k) SRP_CUDA_TRY(cudaEventCreateWithFlags(&plan->pipe_events[k], cudaEventDisableTiming));
+  }
+  // sub-batches of whole 128-frame tiles; conv keeps larger ones (its SRP-matrix tiles are
+  // shared by the frame tiles of a launch)
+  const int parts = plan->desc.method == SRP_CONV ? 2 : 4;
+  int sub = std::max(128, (plan->Fmax / parts + 127) / 128 * 128);
+  sub = std::min(sub, plan->Fmax);
+  int ev = 0;
   for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
     const int nf = std::min(plan->Fmax, F - c0);
     SRP_CUDA_TRY(cudaMemcpyAsync(plan->d_stage_frames, frames + static_cast<size_t>(c0) * g.M * g.N,
                                  sizeof(float) * nf * g.M * g.N, cudaMemcpyHostToDevice, s));
-    srp_status st = run_chunk(plan, plan->d_stage_frames, nf, plan->d_stage_maps,
-                              argmax ? plan->d_stage_arg : nullptr, s);
-    if (st != SRP_OK) return st;
-    SRP_CUDA_TRY(cudaMemcpyAsync(maps + static_cast<size_t>(c0) * g.J, plan->d_stage_maps,
-                                 sizeof(float) * nf * g.J, cudaMemcpyDeviceToHost, s));
-    if (argmax)
-      SRP_CUDA_TRY(cudaMemcpyAsync(argmax + c0, plan->d_stage_arg, sizeof(int) * nf,
-                                   cudaMemcpyDeviceToHost, s));
+    for (int b0 = 0; b0 < nf; b0 += sub) {
+      const int nb = std::min(sub, nf - b0);
+      srp_status st = run_chunk(plan, plan->d_stage_frames + static_cast<size_t>(b0) * g.M * g.N, nb,
+                                plan->d_stage_maps + static_cast<size_t>(b0) * g.J,
+                                argmax ? plan->d_stage_arg + b0 : nullptr, s);
+      if (st != SRP_OK) return st;
+      cudaEvent_t e = plan->pipe_events[ev % kHostPipe];
+      cudaStream_t cs = plan->copy_streams[ev % 2];
+      ++ev;
+      SRP_CUDA_TRY(cudaEventRecord(e, s));
+      SRP_CUDA_TRY(cudaStreamWaitEvent(cs, e, 0));
+      SRP_CUDA_TRY(cudaMemcpyAsync(maps + static_cast<size_t>(c0 + b0) * g.J,
+                                   plan->d_stage_maps + static_cast<size_t>(b0) * g.J,
+                                   sizeof(float) * nb * g.J, cudaMemcpyDeviceToHost, cs));
+      if (argmax)
+        SRP_CUDA_TRY(cudaMemcpyAsync(argmax + c0 + b0, plan->d_stage_arg + b0, sizeof(int) * nb,
+                                     cudaMemcpyDeviceToHost, cs));
+    }
+    // the staging buffers are reused by the next chunk: its work waits for these copies
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e = plan->pipe_events[ev % kHostPipe];
+      ++ev;
+      SRP_CUDA_TRY(cudaEventRecord(e, plan->copy_streams[k]));
+      SRP_CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
+    }
   }
   SRP_CUDA_TRY(cudaStreamSynchronize(s));
   return SRP_OK;

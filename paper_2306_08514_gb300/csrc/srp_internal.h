@@ -14,6 +14,8 @@
 
 namespace srp {
 
+constexpr int kHostPipe = 8;  // events of the srp_map_host copy pipeline
+
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
 void clear_error();
@@ -240,7 +242,10 @@ struct srp_plan_s {
   void* d_A2 = nullptr;     // LR: u as the operand of the tall product [Fmax][lr_kd]
   void* d_A2_lo = nullptr;
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
-  // staging for srp_map_host
+  // staging for srp_map_host, and its copy pipeline (two D2H streams, one event per
+  // sub-batch in flight)
+  cudaStream_t copy_streams[2] = {nullptr, nullptr};
+  cudaEvent_t pipe_events[8] = {};
   float* d_stage_frames = nullptr;
   // streaming (srp_stream_push): hop size, two history buffers [M][N - hop], frame staging
   int stream_hop = 0;
