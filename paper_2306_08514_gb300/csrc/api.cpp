@@ -85,7 +85,7 @@ void free_plan(srp_plan_s* p) {
     if (cs) cudaStreamDestroy(cs);
   void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
-                  p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps,
+                  p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps, p->d_stab,
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
                   p->d_hist[1], p->d_stream_frames, p->d_est_maps, p->d_A2, p->d_A2_lo,
                   p->d_keys2, p->d_tau_hi, p->d_tau_lo};
@@ -221,7 +221,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     const int cols = slri ? (tc ? kSlriKd : Rp) : ((method == SRP_SSPI && !tc) ? g.L : p->Lpad);
     const float scale = slri && tc ? std::ldexp(1.f, -p->slri_exp) : 1.f;
     SRP_LAUNCH(launch_front(frames, F, g.M, g.N, p->d_window, p->d_twiddle, g.P, p->d_pairs,
-                            p->d_Np, p->d_off, g.L, p->max_Np, slri ? p->d_fat : nullptr, Rp,
+                            p->d_Np, p->d_off, p->d_stab, g.L, p->max_Np, slri ? p->d_fat : nullptr, Rp,
                             cols, scale, p->op, out, p->d_A_lo, s));
     SRP_MARK(p, 1, s);
     SRP_MARK(p, 2, s);
@@ -422,6 +422,13 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_off, g.off.data(), sizeof(int) * g.P, cudaMemcpyHostToDevice, s));
   SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_twiddle, tw.data(), sizeof(float2) * g.N / 2, cudaMemcpyHostToDevice, s));
   SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_window, win.data(), sizeof(float) * g.N, cudaMemcpyHostToDevice, s));
+  std::vector<uint4> stab;
+  if (p->use_front) {
+    front_sampling_table(g.N, p->max_Np, stab);
+    SRP_ALLOC(p, p->d_stab, sizeof(uint4) * stab.size());
+    SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_stab, stab.data(), sizeof(uint4) * stab.size(),
+                                     cudaMemcpyHostToDevice, s));
+  }
   const size_t F = static_cast<size_t>(p->Fmax);
   SRP_ALLOC(p, p->d_yhat, sizeof(float2) * F * g.M * (g.N / 2));
   SRP_ALLOC(p, p->d_keys, sizeof(unsigned long long) * F);
@@ -892,34 +899,41 @@ extern "C" srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, 
     plan->d_stage_arg = static_cast<int*>(c);
     plan->device_bytes += sizeof(float) * Fm * (g.M * g.N + g.J) + sizeof(int) * Fm;
   }
-  // Pipelined: the frames go through the path in sub-batches on `stream`; the maps of each
-  // sub-batch leave on two copy streams (alternating) while the next sub-batch computes.
+  // Pipelined over sub-batches of whole 128-frame tiles: the frames of sub-batch b+1 come in
+  // on one copy stream and the maps of sub-batch b-1 leave on two others (alternating) while
+  // sub-batch b computes on `stream`. The host link (~190 GB/s each way) is the bound, the
+  // compute hides behind it.
   if (!plan->copy_streams[0]) {
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 3; ++k)
       SRP_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_streams[k], cudaStreamNonBlocking));
-    for (int k = 0; k < kHostPipe; ++k) SRP_CUDA_TRY(cudaEventCreateWithFlags(&plan->pipe_events[k], cudaEventDisableTiming));
+    for (int k = 0; k < kHostPipe; ++k)
+      SRP_CUDA_TRY(cudaEventCreateWithFlags(&plan->pipe_events[k], cudaEventDisableTiming));
   }
-  // sub-batches of whole 128-frame tiles; conv keeps larger ones (its SRP-matrix tiles are
-  // shared by the frame tiles of a launch)
-  const int parts = plan->desc.method == SRP_CONV ? 2 : 4;
+  cudaStream_t in = plan->copy_streams[2];
+  const int parts = 4;
   int sub = std::max(128, (plan->Fmax / parts + 127) / 128 * 128);
   sub = std::min(sub, plan->Fmax);
-  int ev = 0;
+  int ev = 0, out = 0;
+  auto order = [&](cudaStream_t from, cudaStream_t to) -> cudaError_t {
+    cudaEvent_t e = plan->pipe_events[ev++ % kHostPipe];
+    cudaError_t err = cudaEventRecord(e, from);
+    return err != cudaSuccess ? err : cudaStreamWaitEvent(to, e, 0);
+  };
+  const size_t frame_floats = static_cast<size_t>(g.M) * g.N;
+  SRP_CUDA_TRY(order(s, in));  // earlier work of `stream` on the staging buffers
   for (int c0 = 0; c0 < F; c0 += plan->Fmax) {
     const int nf = std::min(plan->Fmax, F - c0);
-    SRP_CUDA_TRY(cudaMemcpyAsync(plan->d_stage_frames, frames + static_cast<size_t>(c0) * g.M * g.N,
-                                 sizeof(float) * nf * g.M * g.N, cudaMemcpyHostToDevice, s));
     for (int b0 = 0; b0 < nf; b0 += sub) {
       const int nb = std::min(sub, nf - b0);
-      srp_status st = run_chunk(plan, plan->d_stage_frames + static_cast<size_t>(b0) * g.M * g.N, nb,
-                                plan->d_stage_maps + static_cast<size_t>(b0) * g.J,
+      float* d_frames = plan->d_stage_frames + b0 * frame_floats;
+      SRP_CUDA_TRY(cudaMemcpyAsync(d_frames, frames + (c0 + b0) * frame_floats,
+                                   sizeof(float) * nb * frame_floats, cudaMemcpyHostToDevice, in));
+      SRP_CUDA_TRY(order(in, s));
+      srp_status st = run_chunk(plan, d_frames, nb, plan->d_stage_maps + static_cast<size_t>(b0) * g.J,
                                 argmax ? plan->d_stage_arg + b0 : nullptr, s);
       if (st != SRP_OK) return st;
-      cudaEvent_t e = plan->pipe_events[ev % kHostPipe];
-      cudaStream_t cs = plan->copy_streams[ev % 2];
-      ++ev;
-      SRP_CUDA_TRY(cudaEventRecord(e, s));
-      SRP_CUDA_TRY(cudaStreamWaitEvent(cs, e, 0));
+      cudaStream_t cs = plan->copy_streams[out++ % 2];
+      SRP_CUDA_TRY(order(s, cs));
       SRP_CUDA_TRY(cudaMemcpyAsync(maps + static_cast<size_t>(c0 + b0) * g.J,
                                    plan->d_stage_maps + static_cast<size_t>(b0) * g.J,
                                    sizeof(float) * nb * g.J, cudaMemcpyDeviceToHost, cs));
@@ -927,13 +941,10 @@ extern "C" srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, 
         SRP_CUDA_TRY(cudaMemcpyAsync(argmax + c0 + b0, plan->d_stage_arg + b0, sizeof(int) * nb,
                                      cudaMemcpyDeviceToHost, cs));
     }
-    // the staging buffers are reused by the next chunk: its work waits for these copies
-    for (int k = 0; k < 2; ++k) {
-      cudaEvent_t e = plan->pipe_events[ev % kHostPipe];
-      ++ev;
-      SRP_CUDA_TRY(cudaEventRecord(e, plan->copy_streams[k]));
-      SRP_CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
-    }
+    // the next chunk reuses the staging buffers: its frames wait for this chunk's compute,
+    // its compute for this chunk's map copies
+    SRP_CUDA_TRY(order(s, in));
+    for (int k = 0; k < 2; ++k) SRP_CUDA_TRY(order(plan->copy_streams[k], s));
   }
   SRP_CUDA_TRY(cudaStreamSynchronize(s));
   return SRP_OK;
@@ -1082,7 +1093,7 @@ extern "C" srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int 
       plan->launches += 1;
       SRP_CUDA_TRY(launch_front(frames + static_cast<size_t>(c0) * g.M * g.N, nf, g.M, g.N,
                                 plan->d_window, plan->d_twiddle, g.P, plan->d_pairs, plan->d_Np,
-                                plan->d_off, g.L, plan->max_Np, nullptr, 0, g.L, 1.f, OpType::F32,
+                                plan->d_off, plan->d_stab, g.L, plan->max_Np, nullptr, 0, g.L, 1.f, OpType::F32,
                                 xi + static_cast<size_t>(c0) * g.L, nullptr, s));
       continue;
     }

@@ -8,6 +8,7 @@
 #include "srp_internal.h"
 
 #include <algorithm>
+#include <cmath>
 #include "srp_device.cuh"
 
 namespace srp {
@@ -305,24 +306,54 @@ struct FrontParams {
   const int2* pairs;
   const int* Np;
   const int* off;
-  const float* fat;  // SLRI: [Rp][L]; NULL: write xi
+  const uint4* stab;  // sampling operand in fragment order (front_sampling_table)
+  int nq0, NT;        // lag offset of its columns (max N_p) and its n-tiles
+  int fbuf_floats;    // FFT buffers / sampling partials (floats)
+  const float* fat;   // SLRI: [Rp][L]; NULL: write xi
   int Rp;
-  int out_cols;      // row length of the output (L, Lpad, Rp or 64)
-  float scale;       // applied to u before packing
+  int out_cols;       // row length of the output (L, Lpad, Rp or 64)
+  float scale;        // applied to u before packing
   void* out;
   void* out_lo;
 };
 
-template <int NQ, int OT>
-__global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const FrontParams a) {
+// D += A B for one m16n8k16 tile on the warp-level tensor cores (FP16 in, FP32 accumulate).
+// Fragments: a[0] = (row g, K cols 2t, 2t+1), a[1] = (row g+8, same), a[2] / a[3] = the
+// same rows at K cols + 8; b0 = (K rows 2t, 2t+1, col g), b1 = K rows + 8; d = (row g,
+// cols 2t, 2t+1), (row g+8, same); g = lane / 4, t = lane % 4.  The lower half of each
+// 32-bit register holds the element of the smaller K index.
+__device__ __forceinline__ void mma_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                          unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// v = hi + lo in FP16 pairs (x in the lower half)
+__device__ __forceinline__ void split_h2(float2 v, unsigned& hi, unsigned& lo) {
+  const __half2 h = __floats2half2_rn(v.x, v.y);
+  const float2 back = __half22float2(h);
+  const __half2 l = __floats2half2_rn(v.x - back.x, v.y - back.y);
+  hi = *reinterpret_cast<const unsigned*>(&h);
+  lo = *reinterpret_cast<const unsigned*>(&l);
+}
+
+// Rows of y-hat in shared memory are padded by 4 entries, so that the 8 rows a
+// fragment gathers at once fall into distinct bank groups.
+__host__ __device__ constexpr int front_row(int K) { return K + 4; }
+
+template <int NTM, int OT>
+__global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_kernel(const FrontParams a) {
   extern __shared__ float2 sm[];
-  const int N = a.N, H = N >> 1, K = H, M = a.M;
+  const int N = a.N, H = N >> 1, K = H, M = a.M, KS = front_row(K);
   const int Tg = H >> 2;                // threads per channel group (radix-4 FFT)
   const int groups = blockDim.x / Tg;   // channels transformed at once
   float2* tw = sm;                                   // H
-  float2* yh = tw + H;                               // M*K
-  float2* fbuf = yh + static_cast<size_t>(M) * K;    // groups * 2H
-  float* xis = reinterpret_cast<float*>(fbuf + static_cast<size_t>(groups) * 2 * H);  // L
+  float2* yh = tw + H;                               // M*KS
+  float2* fbuf = yh + static_cast<size_t>(M) * KS;   // FFT buffers / sampling partials
+  float* xis = reinterpret_cast<float*>(fbuf) + a.fbuf_floats;                       // L
   const int tid = threadIdx.x;
   const int f = blockIdx.x;
   for (int t = tid; t < H; t += blockDim.x) tw[t] = a.twiddle[t];
@@ -346,7 +377,7 @@ __global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const Fron
     // every thread of the block takes part in the FFT's barriers
     const float2* Z = stockham_fft_r4<false>(bufA, bufB, H, grp < groups ? j : 0, tw, 1);
     if (live) {
-      float2* out = yh + static_cast<size_t>(m) * K;
+      float2* out = yh + static_cast<size_t>(m) * KS;
       for (int k = j; k < K; k += Tg) {
         if (k == 0) {
           out[0] = make_float2(0.f, 0.f);
@@ -369,79 +400,74 @@ __global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const Fron
     }
   }
   __syncthreads();
-  // direct sampling: one warp per group of G pairs, lanes over bins; the rotation
-  // e^{j pi k n / K} depends on (k, n) only and is shared by the G pairs
-  constexpr int G = NQ <= 8 ? 2 : 1;
+  // Sampling (Eq. xi_p_ifft at the lags n = -N_p..N_p) as a GEMM per frame: rows = pairs,
+  // K = bins 0..K-1 with Re psi and Im psi interleaved, columns j = lags n = j - nq0, and
+  // B[2k][j] = 2 cos(pi k n / K), B[2k+1][j] = -2 sin(pi k n / K), so that
+  // xi_p(n) = 2 Re sum_k psi_p(k) exp(j pi k n / K).  psi and B in FP16 hi + lo, three
+  // products per fragment pair (hi hi, lo hi, hi lo): the dropped lo lo term is below
+  // 2^-22 of each product.  Per tile of 16 pairs, warp w sums the k-steps of its eighth of
+  // the bins into part[w]; the eight partials are then added in warp order (deterministic).
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int twoK = 2 * K;
-  for (int q0 = warp * G; q0 < a.P; q0 += nw * G) {
-    int nq[G], mA[G], mB[G];
-    int nqmax = 0;
+  {
+    const int gq = lane >> 2, tq = lane & 3;
+    const int MT = (a.P + 15) >> 4;
+    const int NT = a.NT, NC = NT * 8;
+    const int kst = (K >> 3) / nw;  // k-steps per warp
+    float* part = reinterpret_cast<float*>(fbuf);  // [nw][16][NC]
+    for (int mt = 0; mt < MT; ++mt) {
+      const int r0 = mt * 16 + gq, r1 = r0 + 8;
+      const bool v0 = r0 < a.P, v1 = r1 < a.P;
+      const int2 p0 = v0 ? __ldg(a.pairs + r0) : make_int2(0, 0);
+      const int2 p1 = v1 ? __ldg(a.pairs + r1) : make_int2(0, 0);
+      const float2* yA0 = yh + p0.x * KS;
+      const float2* yB0 = yh + p0.y * KS;
+      const float2* yA1 = yh + p1.x * KS;
+      const float2* yB1 = yh + p1.y * KS;
+      float acc[NTM][4];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const bool ok = q0 + g < a.P;
-      nq[g] = ok ? a.Np[q0 + g] : -1;
-      const int2 pr = ok ? a.pairs[q0 + g] : make_int2(0, 0);
-      mA[g] = pr.x * K;
-      mB[g] = pr.y * K;
-      nqmax = max(nqmax, nq[g]);
-    }
-    float c[G][NQ + 1], sn[G][NQ + 1];
+      for (int t = 0; t < NTM; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+      for (int s = warp * kst; s < (warp + 1) * kst; ++s) {
+        const int k0 = s * 8 + tq, k1 = k0 + 4;
+        const float2 zero = make_float2(0.f, 0.f);
+        unsigned ah[4], al[4];
+        split_h2(v0 ? cmul_conj(yA0[k0], yB0[k0]) : zero, ah[0], al[0]);
+        split_h2(v1 ? cmul_conj(yA1[k0], yB1[k0]) : zero, ah[1], al[1]);
+        split_h2(v0 ? cmul_conj(yA0[k1], yB0[k1]) : zero, ah[2], al[2]);
+        split_h2(v1 ? cmul_conj(yA1[k1], yB1[k1]) : zero, ah[3], al[3]);
+        const uint4* bt = a.stab + static_cast<size_t>(s) * NT * 32 + lane;
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-#pragma unroll
-      for (int n = 0; n <= NQ; ++n) c[g][n] = sn[g][n] = 0.f;
-    for (int k = 1 + lane; k < K; k += 32) {
-      float2 psi[G];
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        psi[g] = cmul_conj(yh[mA[g] + k], yh[mB[g] + k]);
-        c[g][0] += psi[g].x;
-      }
-      const float2 w0 = tw[k];
-      const float2 step = make_float2(w0.x, -w0.y);  // e^{+j pi k / K}
-      float2 e = make_float2(1.f, 0.f);
-#pragma unroll
-      for (int n = 1; n <= NQ; ++n) {
-        if (n > nqmax) break;
-        if ((n & 7) == 0) {
-          const int u = (k * n) & (twoK - 1);
-          const float2 wv = tw[u < K ? u : u - K];
-          e = u < K ? make_float2(wv.x, -wv.y) : make_float2(-wv.x, wv.y);
-        } else {
-          e = cmul(e, step);
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          c[g][n] = fmaf(psi[g].x, e.x, c[g][n]);
-          sn[g][n] = fmaf(psi[g].y, e.y, sn[g][n]);
+        for (int t = 0; t < NTM; ++t) {
+          if (t < NT) {
+            const uint4 b = __ldg(bt + t * 32);
+            mma_16816(acc[t], al, b.x, b.y);
+            mma_16816(acc[t], ah, b.z, b.w);
+            mma_16816(acc[t], ah, b.x, b.y);
+          }
         }
       }
-    }
+      float* pw = part + warp * 16 * NC;
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-#pragma unroll
-      for (int n = 0; n <= NQ; ++n) {
-        if (n > nq[g]) break;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          c[g][n] += __shfl_xor_sync(0xFFFFFFFFu, c[g][n], o);
-          sn[g][n] += __shfl_xor_sync(0xFFFFFFFFu, sn[g][n], o);
+      for (int t = 0; t < NTM; ++t) {
+        if (t < NT) {
+          const int c = t * 8 + 2 * tq;
+          *reinterpret_cast<float2*>(pw + gq * NC + c) = make_float2(acc[t][0], acc[t][1]);
+          *reinterpret_cast<float2*>(pw + (gq + 8) * NC + c) = make_float2(acc[t][2], acc[t][3]);
         }
       }
-      if (nq[g] < 0) continue;
-      float* xo = xis + a.off[q0 + g] + nq[g];
-#pragma unroll
-      for (int n = 0; n <= NQ; ++n) {
-        if (n > nq[g]) break;
-        if (lane == n % 32) {
-          xo[n] = 2.f * (c[g][n] - sn[g][n]);
-          if (n > 0) xo[-n] = 2.f * (c[g][n] + sn[g][n]);
-        }
+      __syncthreads();
+      for (int e = tid; e < 16 * NC; e += blockDim.x) {
+        const int rr = e / NC, c = e - rr * NC;
+        const int r = mt * 16 + rr, n = c - a.nq0;
+        if (r >= a.P) continue;
+        const int nq = __ldg(a.Np + r);
+        if (abs(n) > nq) continue;
+        float v = 0.f;
+        for (int w = 0; w < nw; ++w) v += part[w * 16 * NC + e];
+        xis[__ldg(a.off + r) + nq + n] = v;
       }
+      __syncthreads();
     }
   }
-  __syncthreads();
   const size_t row = static_cast<size_t>(f) * a.out_cols;
   if (!a.fat) {
     for (int l = tid; l < a.out_cols; l += blockDim.x)
@@ -463,35 +489,75 @@ __global__ __launch_bounds__(256, NQ <= 16 ? 4 : 2) void front_kernel(const Fron
 
 int front_max_N() { return 1024; }
 
-size_t front_smem_bytes(int M, int N, int L) {
+int front_ntiles(int max_Np) { return (2 * max_Np + 1 + 7) / 8; }
+
+void front_sampling_table(int N, int max_Np, std::vector<uint4>& tab) {
+  const int K = N / 2, KST = K / 8, NT = front_ntiles(max_Np);
+  tab.assign(static_cast<size_t>(KST) * NT * 32, make_uint4(0, 0, 0, 0));
+  // (2 cos(pi k n / K), -2 sin(pi k n / K)) as FP16 hi and lo pairs, angle reduced exactly
+  auto entry = [&](int k, int n, unsigned& hi, unsigned& lo) {
+    double c = 0.0, sn = 0.0;
+    if (k > 0) {
+      const long long u = ((static_cast<long long>(k) * n) % (2 * K) + 2 * K) % (2 * K);
+      const double th = M_PI * static_cast<double>(u) / K;
+      c = 2.0 * std::cos(th);
+      sn = -2.0 * std::sin(th);
+    }
+    const __half hc = __float2half_rn(static_cast<float>(c));
+    const __half hs = __float2half_rn(static_cast<float>(sn));
+    const __half lc = __float2half_rn(static_cast<float>(c - static_cast<double>(__half2float(hc))));
+    const __half ls = __float2half_rn(static_cast<float>(sn - static_cast<double>(__half2float(hs))));
+    const __half_raw rhc(hc), rhs(hs), rlc(lc), rls(ls);
+    hi = static_cast<unsigned>(rhc.x) | (static_cast<unsigned>(rhs.x) << 16);
+    lo = static_cast<unsigned>(rlc.x) | (static_cast<unsigned>(rls.x) << 16);
+  };
+  for (int s = 0; s < KST; ++s)
+    for (int t = 0; t < NT; ++t)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int col = t * 8 + (lane >> 2), tq = lane & 3;
+        if (col >= 2 * max_Np + 1) continue;
+        const int n = col - max_Np;
+        uint4& e = tab[(static_cast<size_t>(s) * NT + t) * 32 + lane];
+        entry(s * 8 + tq, n, e.x, e.z);
+        entry(s * 8 + tq + 4, n, e.y, e.w);
+      }
+}
+
+// twiddles, y-hat rows, FFT buffers (reused for the sampling partials of 8 warps), xi
+size_t front_smem_bytes(int M, int N, int L, int max_Np) {
   const int H = N / 2, Tg = H / 4;
   const int groups = 256 / Tg;
-  return sizeof(float2) * (H + static_cast<size_t>(M) * H + static_cast<size_t>(groups) * 2 * H) +
-         sizeof(float) * L;
+  const size_t fbuf = std::max(sizeof(float2) * groups * 2 * H,
+                               sizeof(float) * 8 * 16 * 8 * front_ntiles(max_Np));
+  return sizeof(float2) * (H + static_cast<size_t>(M) * front_row(H)) + fbuf + sizeof(float) * L;
 }
 
 bool front_supported(int M, int N, int L, int max_Np) {
   return N >= 256 && N <= front_max_N() && max_Np <= gcc_direct_max_lag() &&
-         front_smem_bytes(M, N, L) <= 200 * 1024;
+         front_smem_bytes(M, N, L, max_Np) <= 200 * 1024;
 }
 
 cudaError_t launch_front(const float* frames, int F, int M, int N, const float* window,
                          const float2* twiddle, int P, const int2* pairs, const int* Np,
-                         const int* off, int L, int max_Np, const float* fat, int Rp,
-                         int out_cols, float scale, OpType t, void* out, void* out_lo,
+                         const int* off, const uint4* stab, int L, int max_Np, const float* fat,
+                         int Rp, int out_cols, float scale, OpType t, void* out, void* out_lo,
                          cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
   if (!front_supported(M, N, L, max_Np)) return cudaErrorNotSupported;
-  FrontParams a{frames, M, N, P, L, window, twiddle, pairs, Np, off, fat, Rp, out_cols, scale, out, out_lo};
-  const size_t smem = front_smem_bytes(M, N, L);
-  const int NQ = max_Np <= 8 ? 8 : max_Np <= 16 ? 16 : 32;
+  const int NT = front_ntiles(max_Np);
+  const int H = N / 2, groups = 256 / (H / 4);
+  const int fbuf_floats = std::max(4 * groups * H, 8 * 16 * 8 * NT);
+  FrontParams a{frames, M, N, P, L, window, twiddle, pairs, Np, off, stab, max_Np, NT,
+                fbuf_floats, fat, Rp, out_cols, scale, out, out_lo};
+  const size_t smem = front_smem_bytes(M, N, L, max_Np);
+  const int NTM = NT <= 2 ? 2 : NT <= 4 ? 4 : 9;
   const int OT = t == OpType::F32 ? 0 : t == OpType::F16 ? 1 : t == OpType::BF16 ? 2 : 3;
-  // one dispatch table entry per (NQ, operand type)
+  // one dispatch table entry per (n-tile bucket, operand type)
   void (*kern)(const FrontParams) = nullptr;
-#define SRP_FRONT(NQV, OTV) if (NQ == NQV && OT == OTV) kern = front_kernel<NQV, OTV>;
-  SRP_FRONT(8, 0) SRP_FRONT(8, 1) SRP_FRONT(8, 2) SRP_FRONT(8, 3)
-  SRP_FRONT(16, 0) SRP_FRONT(16, 1) SRP_FRONT(16, 2) SRP_FRONT(16, 3)
-  SRP_FRONT(32, 0) SRP_FRONT(32, 1) SRP_FRONT(32, 2) SRP_FRONT(32, 3)
+#define SRP_FRONT(NTV, OTV) if (NTM == NTV && OT == OTV) kern = front_kernel<NTV, OTV>;
+  SRP_FRONT(2, 0) SRP_FRONT(2, 1) SRP_FRONT(2, 2) SRP_FRONT(2, 3)
+  SRP_FRONT(4, 0) SRP_FRONT(4, 1) SRP_FRONT(4, 2) SRP_FRONT(4, 3)
+  SRP_FRONT(9, 0) SRP_FRONT(9, 1) SRP_FRONT(9, 2) SRP_FRONT(9, 3)
 #undef SRP_FRONT
   if (!kern) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

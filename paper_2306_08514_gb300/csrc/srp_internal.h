@@ -14,7 +14,7 @@
 
 namespace srp {
 
-constexpr int kHostPipe = 8;  // events of the srp_map_host copy pipeline
+constexpr int kHostPipe = 16;  // events of the srp_map_host copy pipeline
 
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
@@ -94,15 +94,19 @@ cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N
 // Cross-spectra packed as the conv GEMM operand A [F][P*N]:
 // A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
 enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3 /* hi + lo planes */ };
-// Fused STFT + PHAT + direct sampling (+ Lambda_fat) per frame: writes xi (fat == NULL)
+// Fused STFT + PHAT + sampling (+ Lambda_fat) per frame: writes xi (fat == NULL)
 // or u = fat xi * scale, rows of out_cols entries (zero padded) in operand type t.
+// The sampling is a per-frame GEMM on the warp-level tensor cores against stab, the
+// table front_sampling_table(N, max_Np) builds (exp(j pi k n / K) for n = -max_Np..max_Np
+// in FP16 hi + lo, fragment order).
 // Returns cudaErrorNotSupported where front_supported() is false (the caller then runs
 // the separate kernels).
 bool front_supported(int M, int N, int L, int max_Np);
+void front_sampling_table(int N, int max_Np, std::vector<uint4>& tab);
 cudaError_t launch_front(const float* frames, int F, int M, int N, const float* window,
                          const float2* twiddle, int P, const int2* pairs, const int* Np,
-                         const int* off, int L, int max_Np, const float* fat, int Rp,
-                         int out_cols, float scale, OpType t, void* out, void* out_lo,
+                         const int* off, const uint4* stab, int L, int max_Np, const float* fat,
+                         int Rp, int out_cols, float scale, OpType t, void* out, void* out_lo,
                          cudaStream_t s);
 
 cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
@@ -242,10 +246,11 @@ struct srp_plan_s {
   void* d_A2 = nullptr;     // LR: u as the operand of the tall product [Fmax][lr_kd]
   void* d_A2_lo = nullptr;
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
-  // staging for srp_map_host, and its copy pipeline (two D2H streams, one event per
-  // sub-batch in flight)
-  cudaStream_t copy_streams[2] = {nullptr, nullptr};
-  cudaEvent_t pipe_events[8] = {};
+  uint4* d_stab = nullptr;  // fused front end: the sampling operand (front_sampling_table)
+  // staging for srp_map_host, and its copy pipeline (two D2H streams and one H2D stream;
+  // events recycled round-robin to order them against the compute stream)
+  cudaStream_t copy_streams[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t pipe_events[srp::kHostPipe] = {};
   float* d_stage_frames = nullptr;
   // streaming (srp_stream_push): hop size, two history buffers [M][N - hop], frame staging
   int stream_hop = 0;

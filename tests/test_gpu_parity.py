@@ -255,6 +255,28 @@ def test_host_entry_matches_device_entry_and_is_deterministic(S):
         assert np.array_equal(zh, z1) and np.array_equal(ah, a1)
 
 
+@pytest.mark.parametrize("kw", [dict(method="conv", precision="bf16"),
+                                dict(method="slri", rank=8),
+                                dict(method="sspi", taps=2.0, precision="bf16")],
+                         ids=["conv-bf16", "slri-fp32", "sspi-bf16"])
+def test_host_entry_pipelined_sub_batches(S, kw):
+    """srp_map_host splits a chunk into sub-batches whose frames come in and whose maps leave
+    on copy streams while the next computes; 1000 frames through 600-frame chunks give
+    several sub-batches per chunk and a ragged last one.  Maps agree with the device entry
+    (FP32 sums may be ordered differently), argmax is the host map's own."""
+    w = R.workload("square4", 1000)
+    fr = np.ascontiguousarray(w["frames"])
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], max_frames=600, **kw)
+    z1, a1 = _run(plan, fr)
+    zh, ah = plan.map_host(fr)
+    plan.status()
+    assert R.per_frame_rel(zh, z1).max() <= 1e-6
+    assert np.array_equal(ah, np.argmax(zh, axis=1))
+    gap = np.sort(z1, axis=1)[:, -1] - np.sort(z1, axis=1)[:, -2]
+    clear = gap > 1e-5 * np.abs(z1).max(axis=1)
+    assert np.array_equal(ah[clear], a1[clear])
+
+
 def test_largest_fft_and_most_mics_conv(S):
     """N = 2048 and M = 32 (nested arrays) on a reduced grid."""
     w = R.workload("nested32", 6, 400)
