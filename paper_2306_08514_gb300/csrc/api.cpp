@@ -85,7 +85,7 @@ void free_plan(srp_plan_s* p) {
     if (cs) cudaStreamDestroy(cs);
   void* ptrs[] = {p->d_pairs, p->d_Np, p->d_off, p->d_twiddle, p->d_window, p->d_H, p->d_H_lo,
                   p->d_tall, p->d_fat, p->d_row_ptr, p->d_taps, p->d_yhat, p->d_A, p->d_A_lo,
-                  p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps, p->d_stab,
+                  p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps, p->d_stab, p->d_ftab,
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
                   p->d_hist[1], p->d_stream_frames, p->d_est_maps, p->d_A2, p->d_A2_lo,
                   p->d_keys2, p->d_tau_hi, p->d_tau_lo};
@@ -221,7 +221,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     const int cols = slri ? (tc ? kSlriKd : Rp) : ((method == SRP_SSPI && !tc) ? g.L : p->Lpad);
     const float scale = slri && tc ? std::ldexp(1.f, -p->slri_exp) : 1.f;
     SRP_LAUNCH(launch_front(frames, F, g.M, g.N, p->d_window, p->d_twiddle, g.P, p->d_pairs,
-                            p->d_Np, p->d_off, p->d_stab, g.L, p->max_Np, slri ? p->d_fat : nullptr, Rp,
+                            p->d_Np, p->d_off, p->d_stab, g.L, p->max_Np, slri ? p->d_ftab : nullptr, Rp,
                             cols, scale, p->op, out, p->d_A_lo, s));
     SRP_MARK(p, 1, s);
     SRP_MARK(p, 2, s);
@@ -594,6 +594,13 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       SRP_ALLOC(p, p->d_U, sizeof(float) * F * Rp);
       SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tall, tall.data(), sizeof(float) * tall.size(), cudaMemcpyHostToDevice, s));
       SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_fat, fat.data(), sizeof(float) * fat.size(), cudaMemcpyHostToDevice, s));
+      std::vector<uint4> ftab;
+      if (p->use_front) {
+        front_fat_table(fat.data(), Rp, g.L, ftab);
+        SRP_ALLOC(p, p->d_ftab, sizeof(uint4) * ftab.size());
+        SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_ftab, ftab.data(), sizeof(uint4) * ftab.size(),
+                                         cudaMemcpyHostToDevice, s));
+      }
       if (p->op != OpType::F32) {
         // u = Lambda_fat xi has |u_r| <= ||xi||_2 <= 2K sqrt(P) (Parseval over the 2K lags of
         // each pair, |psi| <= 1): scale u by 2^-e into the FP16 range and Lambda_tall by 2^e.

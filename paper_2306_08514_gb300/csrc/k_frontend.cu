@@ -298,9 +298,19 @@ __device__ __forceinline__ void put_op(void* hi, void* lo, size_t idx, float v) 
   }
 }
 
+// out[idx] = v in the operand type ot chosen at run time (0 FP32, 1 FP16, 2 BF16, 3 FP16 hi + lo)
+__device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx, float v) {
+  switch (ot) {
+    case 0: put_op<0>(hi, lo, idx, v); break;
+    case 1: put_op<1>(hi, lo, idx, v); break;
+    case 2: put_op<2>(hi, lo, idx, v); break;
+    default: put_op<3>(hi, lo, idx, v); break;
+  }
+}
+
 struct FrontParams {
   const float* frames;
-  int M, N, P, L;
+  int M, P, L;
   const float* window;
   const float2* twiddle;
   const int2* pairs;
@@ -309,10 +319,11 @@ struct FrontParams {
   const uint4* stab;  // sampling operand in fragment order (front_sampling_table)
   int nq0, NT;        // lag offset of its columns (max N_p) and its n-tiles
   int fbuf_floats;    // FFT buffers / sampling partials (floats)
-  const float* fat;   // SLRI: [Rp][L]; NULL: write xi
+  const uint4* ftab;  // SLRI: Lambda_fat in fragment order (front_fat_table); NULL: write xi
   int Rp;
   int out_cols;       // row length of the output (L, Lpad, Rp or 64)
   float scale;        // applied to u before packing
+  int ot;             // operand type of the output
   void* out;
   void* out_lo;
 };
@@ -344,54 +355,64 @@ __device__ __forceinline__ void split_h2(float2 v, unsigned& hi, unsigned& lo) {
 // fragment gathers at once fall into distinct bank groups.
 __host__ __device__ constexpr int front_row(int K) { return K + 4; }
 
-template <int NTM, int OT>
+// One CTA of 256 threads per frame; H = N/2 is the complex FFT length (= K), NTM bounds
+// the n-tiles of the sampling GEMM.
+template <int H, int NTM>
 __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_kernel(const FrontParams a) {
   extern __shared__ float2 sm[];
-  const int N = a.N, H = N >> 1, K = H, M = a.M, KS = front_row(K);
-  const int Tg = H >> 2;                // threads per channel group (radix-4 FFT)
-  const int groups = blockDim.x / Tg;   // channels transformed at once
+  constexpr int N = 2 * H, K = H, KS = front_row(K);
+  constexpr int Tg = H / 4;              // threads per channel group (radix-4 FFT)
+  constexpr int groups = 256 / Tg;       // channels transformed at once
+  constexpr int NW = 8;                  // warps
+  const int M = a.M;
   float2* tw = sm;                                   // H
   float2* yh = tw + H;                               // M*KS
-  float2* fbuf = yh + static_cast<size_t>(M) * KS;   // FFT buffers / sampling partials
-  float* xis = reinterpret_cast<float*>(fbuf) + a.fbuf_floats;                       // L
+  float2* fbuf = yh + static_cast<size_t>(M) * KS;   // FFT buffers / GEMM partials
+  float* xis = reinterpret_cast<float*>(fbuf) + a.fbuf_floats;  // L
   const int tid = threadIdx.x;
   const int f = blockIdx.x;
-  for (int t = tid; t < H; t += blockDim.x) tw[t] = a.twiddle[t];
+  for (int t = tid; t < H; t += 256) tw[t] = a.twiddle[t];
+  // each thread owns the complex samples j + i Tg (i = 0..3) of its group's channel,
+  // loaded one round ahead
   const int grp = tid / Tg, j = tid - grp * Tg;
   float2* bufA = fbuf + grp * 2 * H;
   float2* bufB = bufA + H;
   const float2* w2 = reinterpret_cast<const float2*>(a.window);
+  float2 xv[4], wv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) wv[i] = __ldg(w2 + j + i * Tg);
+  auto load_round = [&](int m0) {
+    const int m = m0 + grp;
+    const float2* x2 = reinterpret_cast<const float2*>(a.frames + (static_cast<size_t>(f) * M + (m < M ? m : 0)) * N);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xv[i] = m < M ? __ldg(x2 + j + i * Tg) : make_float2(0.f, 0.f);
+  };
+  load_round(0);
   for (int m0 = 0; m0 < M; m0 += groups) {
     const int m = m0 + grp;
-    const bool live = grp < groups && m < M;
     __syncthreads();  // twiddles ready / previous round's buffers consumed
-    if (grp < groups) {
-      const float2* x2 = reinterpret_cast<const float2*>(a.frames + (static_cast<size_t>(f) * M + (live ? m : 0)) * N);
-      for (int jj = j; jj < H; jj += Tg) {
-        const float2 v = live ? __ldg(x2 + jj) : make_float2(0.f, 0.f);
-        const float2 ww = __ldg(w2 + jj);
-        bufA[jj] = make_float2(v.x * ww.x, v.y * ww.y);
-      }
-    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      bufA[j + i * Tg] = make_float2(xv[i].x * wv[i].x, xv[i].y * wv[i].y);
+    if (m0 + groups < M) load_round(m0 + groups);  // in flight during this round's FFT
     __syncthreads();
     // every thread of the block takes part in the FFT's barriers
-    const float2* Z = stockham_fft_r4<false>(bufA, bufB, H, grp < groups ? j : 0, tw, 1);
-    if (live) {
+    const float2* Z = stockham_fft_r4_fixed<H, 1, false>(bufA, bufB, j, tw);
+    if (m < M) {
+      // real spectrum from the packed transform, then PHAT
       float2* out = yh + static_cast<size_t>(m) * KS;
-      for (int k = j; k < K; k += Tg) {
-        if (k == 0) {
-          out[0] = make_float2(0.f, 0.f);
-          continue;
-        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = j + i * Tg;
         const float2 zk = Z[k];
-        const float2 zc = make_float2(Z[H - k].x, -Z[H - k].y);
+        const float2 zc = make_float2(Z[(H - k) & (H - 1)].x, -Z[(H - k) & (H - 1)].y);
         const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
         const float2 O = make_float2(0.5f * (zk.y - zc.y), -0.5f * (zk.x - zc.x));
         const float2 WO = cmul(tw[k], O);
         const float2 Y = make_float2(E.x + WO.x, E.y + WO.y);
         const float p = Y.x * Y.x + Y.y * Y.y;
         float2 r = make_float2(0.f, 0.f);
-        if (p >= 1e-30f) {
+        if (k > 0 && p >= 1e-30f) {
           const float sc = __frsqrt_rn(p);
           r = make_float2(Y.x * sc, Y.y * sc);
         }
@@ -407,89 +428,152 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
   // products per fragment pair (hi hi, lo hi, hi lo): the dropped lo lo term is below
   // 2^-22 of each product.  Per tile of 16 pairs, warp w sums the k-steps of its eighth of
   // the bins into part[w]; the eight partials are then added in warp order (deterministic).
-  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
   {
-    const int gq = lane >> 2, tq = lane & 3;
+    constexpr int NCM = NTM * 8;        // partial row stride
+    constexpr int kst = (K / 8) / NW;   // k-steps per warp
     const int MT = (a.P + 15) >> 4;
-    const int NT = a.NT, NC = NT * 8;
-    const int kst = (K >> 3) / nw;  // k-steps per warp
-    float* part = reinterpret_cast<float*>(fbuf);  // [nw][16][NC]
+    const int NT = a.NT;
+    float* part = reinterpret_cast<float*>(fbuf);  // [NW][16][NCM]
     for (int mt = 0; mt < MT; ++mt) {
       const int r0 = mt * 16 + gq, r1 = r0 + 8;
       const bool v0 = r0 < a.P, v1 = r1 < a.P;
       const int2 p0 = v0 ? __ldg(a.pairs + r0) : make_int2(0, 0);
       const int2 p1 = v1 ? __ldg(a.pairs + r1) : make_int2(0, 0);
-      const float2* yA0 = yh + p0.x * KS;
-      const float2* yB0 = yh + p0.y * KS;
-      const float2* yA1 = yh + p1.x * KS;
-      const float2* yB1 = yh + p1.y * KS;
-      float acc[NTM][4];
+      const int sb = warp * kst;
+      const float2* yA0 = yh + p0.x * KS + sb * 8 + tq;
+      const float2* yB0 = yh + p0.y * KS + sb * 8 + tq;
+      const float2* yA1 = yh + p1.x * KS + sb * 8 + tq;
+      const float2* yB1 = yh + p1.y * KS + sb * 8 + tq;
+      const uint4* bt = a.stab + static_cast<size_t>(sb) * NT * 32 + lane;
+      // hi x hi and the two lo products in separate accumulators (independent chains),
+      // except for many n-tiles (register budget)
+      constexpr bool SA = NTM <= 4;
+      float acc[NTM][4], accl[SA ? NTM : 1][4];
 #pragma unroll
-      for (int t = 0; t < NTM; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-      for (int s = warp * kst; s < (warp + 1) * kst; ++s) {
-        const int k0 = s * 8 + tq, k1 = k0 + 4;
+      for (int t = 0; t < NTM; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[t][e] = accl[SA ? t : 0][e] = 0.f;
+      // small n-tile counts: the B fragments of the next k-step are loaded one step ahead
+      constexpr bool PF = false;
+      uint4 bn[PF ? NTM : 1];
+      if constexpr (PF) {
+#pragma unroll
+        for (int t = 0; t < NTM; ++t)
+          if (t < NT) bn[t] = __ldg(bt + t * 32);
+      }
+#pragma unroll(kst <= 4 ? kst : 1)
+      for (int s = 0; s < kst; ++s) {
         const float2 zero = make_float2(0.f, 0.f);
         unsigned ah[4], al[4];
-        split_h2(v0 ? cmul_conj(yA0[k0], yB0[k0]) : zero, ah[0], al[0]);
-        split_h2(v1 ? cmul_conj(yA1[k0], yB1[k0]) : zero, ah[1], al[1]);
-        split_h2(v0 ? cmul_conj(yA0[k1], yB0[k1]) : zero, ah[2], al[2]);
-        split_h2(v1 ? cmul_conj(yA1[k1], yB1[k1]) : zero, ah[3], al[3]);
-        const uint4* bt = a.stab + static_cast<size_t>(s) * NT * 32 + lane;
+        split_h2(v0 ? cmul_conj(yA0[8 * s], yB0[8 * s]) : zero, ah[0], al[0]);
+        split_h2(v1 ? cmul_conj(yA1[8 * s], yB1[8 * s]) : zero, ah[1], al[1]);
+        split_h2(v0 ? cmul_conj(yA0[8 * s + 4], yB0[8 * s + 4]) : zero, ah[2], al[2]);
+        split_h2(v1 ? cmul_conj(yA1[8 * s + 4], yB1[8 * s + 4]) : zero, ah[3], al[3]);
+        uint4 bc[PF ? NTM : 1];
+        if constexpr (PF) {
+#pragma unroll
+          for (int t = 0; t < NTM; ++t) {
+            bc[t] = bn[t];
+            if (t < NT && s + 1 < kst) bn[t] = __ldg(bt + (s + 1) * NT * 32 + t * 32);
+          }
+        }
 #pragma unroll
         for (int t = 0; t < NTM; ++t) {
           if (t < NT) {
-            const uint4 b = __ldg(bt + t * 32);
-            mma_16816(acc[t], al, b.x, b.y);
-            mma_16816(acc[t], ah, b.z, b.w);
+            const uint4 b = PF ? bc[PF ? t : 0] : __ldg(bt + s * NT * 32 + t * 32);
+            float(&dl)[4] = SA ? accl[SA ? t : 0] : acc[t];
+            mma_16816(dl, al, b.x, b.y);
+            mma_16816(dl, ah, b.z, b.w);
             mma_16816(acc[t], ah, b.x, b.y);
           }
         }
       }
-      float* pw = part + warp * 16 * NC;
+      if constexpr (SA) {
+#pragma unroll
+        for (int t = 0; t < NTM; ++t)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[t][e] += accl[SA ? t : 0][e];
+      }
+      float* pw = part + warp * 16 * NCM;
 #pragma unroll
       for (int t = 0; t < NTM; ++t) {
         if (t < NT) {
           const int c = t * 8 + 2 * tq;
-          *reinterpret_cast<float2*>(pw + gq * NC + c) = make_float2(acc[t][0], acc[t][1]);
-          *reinterpret_cast<float2*>(pw + (gq + 8) * NC + c) = make_float2(acc[t][2], acc[t][3]);
+          *reinterpret_cast<float2*>(pw + gq * NCM + c) = make_float2(acc[t][0], acc[t][1]);
+          *reinterpret_cast<float2*>(pw + (gq + 8) * NCM + c) = make_float2(acc[t][2], acc[t][3]);
         }
       }
       __syncthreads();
-      for (int e = tid; e < 16 * NC; e += blockDim.x) {
-        const int rr = e / NC, c = e - rr * NC;
+      for (int e = tid; e < 16 * NCM; e += 256) {
+        const int rr = e / NCM, c = e - rr * NCM;
         const int r = mt * 16 + rr, n = c - a.nq0;
-        if (r >= a.P) continue;
+        if (r >= a.P || c >= NT * 8) continue;
         const int nq = __ldg(a.Np + r);
         if (abs(n) > nq) continue;
         float v = 0.f;
-        for (int w = 0; w < nw; ++w) v += part[w * 16 * NC + e];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v += part[w * 16 * NCM + e];
         xis[__ldg(a.off + r) + nq + n] = v;
       }
       __syncthreads();
     }
   }
   const size_t row = static_cast<size_t>(f) * a.out_cols;
-  if (!a.fat) {
-    for (int l = tid; l < a.out_cols; l += blockDim.x)
-      put_op<OT>(a.out, a.out_lo, row + l, l < a.L ? xis[l] : 0.f);
+  if (!a.ftab) {
+    for (int l = tid; l < a.out_cols; l += 256)
+      put_op_rt(a.ot, a.out, a.out_lo, row + l, l < a.L ? xis[l] : 0.f);
     return;
   }
-  // u_r = sum_l fat[r][l] xi[l], one warp per r
-  for (int r = warp; r < a.out_cols; r += nw) {
-    float acc = 0.f;
-    if (r < a.Rp) {
-      const float* fr = a.fat + static_cast<size_t>(r) * a.L;
-      for (int l = lane; l < a.L; l += 32) acc = fmaf(__ldg(fr + l), xis[l], acc);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  // u = Lambda_fat xi on the warp-level tensor cores: A = Lambda_fat tiles of 16 rows x 16
+  // samples (fragment table, FP16 hi + lo), B = xi as column 0 (FP16 hi + lo, columns 1..7
+  // zero); warp w takes the k-steps w, w + 8, ...; partials added in warp order.
+  {
+    const int MTf = (a.Rp + 15) >> 4, KSf = (a.L + 15) >> 4;
+    float* part = reinterpret_cast<float*>(fbuf);  // [NW][MTf * 16]
+    for (int mt = 0; mt < MTf; ++mt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int s = warp; s < KSf; s += NW) {
+        const uint4* fa = a.ftab + ((static_cast<size_t>(mt) * KSf + s) * 32 + lane) * 2;
+        const uint4 h = __ldg(fa), l = __ldg(fa + 1);
+        unsigned bh0 = 0u, bl0 = 0u, bh1 = 0u, bl1 = 0u;
+        if (gq == 0) {
+          const int l0 = s * 16 + 2 * tq;
+          split_h2(make_float2(l0 < a.L ? xis[l0] : 0.f, l0 + 1 < a.L ? xis[l0 + 1] : 0.f), bh0, bl0);
+          split_h2(make_float2(l0 + 8 < a.L ? xis[l0 + 8] : 0.f, l0 + 9 < a.L ? xis[l0 + 9] : 0.f), bh1, bl1);
+        }
+        const unsigned ah[4] = {h.x, h.y, h.z, h.w}, al[4] = {l.x, l.y, l.z, l.w};
+        mma_16816(dl, al, bh0, bh1);
+        mma_16816(dl, ah, bl0, bl1);
+        mma_16816(d, ah, bh0, bh1);
+      }
+      if (tq == 0) {
+        part[warp * MTf * 16 + mt * 16 + gq] = d[0] + dl[0];
+        part[warp * MTf * 16 + mt * 16 + gq + 8] = d[2] + dl[2];
+      }
     }
-    if (lane == 0) put_op<OT>(a.out, a.out_lo, row + r, acc * a.scale);
+    __syncthreads();
+    for (int r = tid; r < a.out_cols; r += 256) {
+      float u = 0.f;
+      if (r < a.Rp) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) u += part[w * MTf * 16 + r];
+      }
+      put_op_rt(a.ot, a.out, a.out_lo, row + r, u * a.scale);
+    }
   }
 }
 
 int front_max_N() { return 1024; }
 
 int front_ntiles(int max_Np) { return (2 * max_Np + 1 + 7) / 8; }
+
+// n-tile bucket of the kernel instantiation (its partial rows hold 8 NTM floats)
+int front_ntm(int max_Np) {
+  const int NT = front_ntiles(max_Np);
+  return NT <= 2 ? 2 : NT <= 4 ? 4 : 9;
+}
 
 void front_sampling_table(int N, int max_Np, std::vector<uint4>& tab) {
   const int K = N / 2, KST = K / 8, NT = front_ntiles(max_Np);
@@ -524,11 +608,35 @@ void front_sampling_table(int N, int max_Np, std::vector<uint4>& tab) {
 }
 
 // twiddles, y-hat rows, FFT buffers (reused for the sampling partials of 8 warps), xi
+void front_fat_table(const float* fat, int Rp, int L, std::vector<uint4>& tab) {
+  const int MTf = (Rp + 15) / 16, KSf = (L + 15) / 16;
+  tab.assign(static_cast<size_t>(MTf) * KSf * 32 * 2, make_uint4(0, 0, 0, 0));
+  auto val = [&](int r, int l) { return r < Rp && l < L ? fat[static_cast<size_t>(r) * L + l] : 0.f; };
+  auto pack = [](float x, float y, unsigned& hi, unsigned& lo) {
+    const __half hx = __float2half_rn(x), hy = __float2half_rn(y);
+    const __half lx = __float2half_rn(x - __half2float(hx)), ly = __float2half_rn(y - __half2float(hy));
+    const __half_raw rhx(hx), rhy(hy), rlx(lx), rly(ly);
+    hi = static_cast<unsigned>(rhx.x) | (static_cast<unsigned>(rhy.x) << 16);
+    lo = static_cast<unsigned>(rlx.x) | (static_cast<unsigned>(rly.x) << 16);
+  };
+  for (int mt = 0; mt < MTf; ++mt)
+    for (int s = 0; s < KSf; ++s)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int r0 = mt * 16 + (lane >> 2), r1 = r0 + 8;
+        const int c0 = s * 16 + 2 * (lane & 3), c1 = c0 + 8;
+        uint4* e = &tab[((static_cast<size_t>(mt) * KSf + s) * 32 + lane) * 2];
+        pack(val(r0, c0), val(r0, c0 + 1), e[0].x, e[1].x);
+        pack(val(r1, c0), val(r1, c0 + 1), e[0].y, e[1].y);
+        pack(val(r0, c1), val(r0, c1 + 1), e[0].z, e[1].z);
+        pack(val(r1, c1), val(r1, c1 + 1), e[0].w, e[1].w);
+      }
+}
+
 size_t front_smem_bytes(int M, int N, int L, int max_Np) {
   const int H = N / 2, Tg = H / 4;
   const int groups = 256 / Tg;
   const size_t fbuf = std::max(sizeof(float2) * groups * 2 * H,
-                               sizeof(float) * 8 * 16 * 8 * front_ntiles(max_Np));
+                               sizeof(float) * 8 * 16 * 8 * front_ntm(max_Np));
   return sizeof(float2) * (H + static_cast<size_t>(M) * front_row(H)) + fbuf + sizeof(float) * L;
 }
 
@@ -539,25 +647,25 @@ bool front_supported(int M, int N, int L, int max_Np) {
 
 cudaError_t launch_front(const float* frames, int F, int M, int N, const float* window,
                          const float2* twiddle, int P, const int2* pairs, const int* Np,
-                         const int* off, const uint4* stab, int L, int max_Np, const float* fat,
+                         const int* off, const uint4* stab, int L, int max_Np, const uint4* ftab,
                          int Rp, int out_cols, float scale, OpType t, void* out, void* out_lo,
                          cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
   if (!front_supported(M, N, L, max_Np)) return cudaErrorNotSupported;
   const int NT = front_ntiles(max_Np);
   const int H = N / 2, groups = 256 / (H / 4);
-  const int fbuf_floats = std::max(4 * groups * H, 8 * 16 * 8 * NT);
-  FrontParams a{frames, M, N, P, L, window, twiddle, pairs, Np, off, stab, max_Np, NT,
-                fbuf_floats, fat, Rp, out_cols, scale, out, out_lo};
+  const int NTM = front_ntm(max_Np);
+  const int fbuf_floats = std::max(4 * groups * H, 8 * 16 * 8 * NTM);
+  const int ot = t == OpType::F32 ? 0 : t == OpType::F16 ? 1 : t == OpType::BF16 ? 2 : 3;
+  FrontParams a{frames, M, P, L, window, twiddle, pairs, Np, off, stab, max_Np, NT,
+                fbuf_floats, ftab, Rp, out_cols, scale, ot, out, out_lo};
   const size_t smem = front_smem_bytes(M, N, L, max_Np);
-  const int NTM = NT <= 2 ? 2 : NT <= 4 ? 4 : 9;
-  const int OT = t == OpType::F32 ? 0 : t == OpType::F16 ? 1 : t == OpType::BF16 ? 2 : 3;
-  // one dispatch table entry per (n-tile bucket, operand type)
+  // one dispatch table entry per (FFT length, n-tile bucket)
   void (*kern)(const FrontParams) = nullptr;
-#define SRP_FRONT(NTV, OTV) if (NTM == NTV && OT == OTV) kern = front_kernel<NTV, OTV>;
-  SRP_FRONT(2, 0) SRP_FRONT(2, 1) SRP_FRONT(2, 2) SRP_FRONT(2, 3)
-  SRP_FRONT(4, 0) SRP_FRONT(4, 1) SRP_FRONT(4, 2) SRP_FRONT(4, 3)
-  SRP_FRONT(9, 0) SRP_FRONT(9, 1) SRP_FRONT(9, 2) SRP_FRONT(9, 3)
+#define SRP_FRONT(HV, NTV) if (H == HV && NTM == NTV) kern = front_kernel<HV, NTV>;
+  SRP_FRONT(128, 2) SRP_FRONT(128, 4) SRP_FRONT(128, 9)
+  SRP_FRONT(256, 2) SRP_FRONT(256, 4) SRP_FRONT(256, 9)
+  SRP_FRONT(512, 2) SRP_FRONT(512, 4) SRP_FRONT(512, 9)
 #undef SRP_FRONT
   if (!kern) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -94,18 +94,20 @@ cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N
 // Cross-spectra packed as the conv GEMM operand A [F][P*N]:
 // A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
 enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3 /* hi + lo planes */ };
-// Fused STFT + PHAT + sampling (+ Lambda_fat) per frame: writes xi (fat == NULL)
-// or u = fat xi * scale, rows of out_cols entries (zero padded) in operand type t.
-// The sampling is a per-frame GEMM on the warp-level tensor cores against stab, the
-// table front_sampling_table(N, max_Np) builds (exp(j pi k n / K) for n = -max_Np..max_Np
-// in FP16 hi + lo, fragment order).
+// Fused STFT + PHAT + sampling (+ Lambda_fat) per frame: writes xi (ftab == NULL)
+// or u = Lambda_fat xi * scale, rows of out_cols entries (zero padded) in operand type t.
+// The sampling and the Lambda_fat product are per-frame GEMMs on the warp-level tensor
+// cores against two tables in fragment order, FP16 hi + lo: stab from
+// front_sampling_table(N, max_Np) (exp(j pi k n / K) for n = -max_Np..max_Np) and ftab
+// from front_fat_table(fat [Rp][L], Rp, L).
 // Returns cudaErrorNotSupported where front_supported() is false (the caller then runs
 // the separate kernels).
 bool front_supported(int M, int N, int L, int max_Np);
 void front_sampling_table(int N, int max_Np, std::vector<uint4>& tab);
+void front_fat_table(const float* fat, int Rp, int L, std::vector<uint4>& tab);
 cudaError_t launch_front(const float* frames, int F, int M, int N, const float* window,
                          const float2* twiddle, int P, const int2* pairs, const int* Np,
-                         const int* off, const uint4* stab, int L, int max_Np, const float* fat,
+                         const int* off, const uint4* stab, int L, int max_Np, const uint4* ftab,
                          int Rp, int out_cols, float scale, OpType t, void* out, void* out_lo,
                          cudaStream_t s);
 
@@ -247,6 +249,7 @@ struct srp_plan_s {
   void* d_A2_lo = nullptr;
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
   uint4* d_stab = nullptr;  // fused front end: the sampling operand (front_sampling_table)
+  uint4* d_ftab = nullptr;  // fused front end, SLRI: Lambda_fat (front_fat_table)
   // staging for srp_map_host, and its copy pipeline (two D2H streams and one H2D stream;
   // events recycled round-robin to order them against the compute stream)
   cudaStream_t copy_streams[3] = {nullptr, nullptr, nullptr};
