@@ -355,6 +355,85 @@ __device__ __forceinline__ void split_h2(float2 v, unsigned& hi, unsigned& lo) {
 // fragment gathers at once fall into distinct bank groups.
 __host__ __device__ constexpr int front_row(int K) { return K + 4; }
 
+// FFT buffers of the front kernel hold element i at i + i/16: the strided stores of the
+// first radix-4 stages then spread over all banks.
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int fpad_len(int H) { return H + H / 16; }
+
+// Radix-4 Stockham FFT of compile-time length H (as stockham_fft_r4_fixed with TWS = 1) on
+// padded buffers, with the thread's twiddles of the stages Ns > 1 in registers (tw4[s] =
+// w^k, w^2k, w^3k of the s-th such stage; front_fft_twiddles).  Called by H/4 threads per
+// channel; every thread of the block takes part in the barriers.
+template <int H>
+struct FrontFft {
+  static constexpr bool odd = (__builtin_ctz(H) & 1) != 0;
+  static constexpr int NTW = __builtin_ctz(H) / 2 - (odd ? 0 : 1);  // stages with twiddles
+};
+
+template <int H>
+__device__ __forceinline__ void front_fft_twiddles(const float2* __restrict__ twg, int j,
+                                                   float2 (&tw4)[FrontFft<H>::NTW][3]) {
+  constexpr int S = H;  // table entries exp(-2 pi i t / 2H), t < H
+  int Ns = FrontFft<H>::odd ? 2 : 4;
+#pragma unroll
+  for (int st = 0; st < FrontFft<H>::NTW; ++st, Ns <<= 2) {
+    const int k = j & (Ns - 1);
+    const int t1 = (k * (H / (4 * Ns))) << 1;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int u = (m + 1) * t1;
+      const float2 w = __ldg(twg + (u < S ? u : u - S));
+      tw4[st][m] = u < S ? w : make_float2(-w.x, -w.y);
+    }
+  }
+}
+
+template <int H>
+__device__ __forceinline__ float2* front_fft(float2* a, float2* b, int j,
+                                             const float2 (&tw4)[FrontFft<H>::NTW][3]) {
+  constexpr int q = H >> 2;
+  constexpr bool odd = FrontFft<H>::odd;
+  if constexpr (odd) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int jj = j + i * q;
+      const float2 v0 = a[fpad(jj)], v1 = a[fpad(jj + 2 * q)];
+      b[fpad(2 * jj)] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      b[fpad(2 * jj + 1)] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  int st = 0;
+#pragma unroll
+  for (int Ns = odd ? 2 : 1; Ns < H; Ns <<= 2) {
+    const int k = j & (Ns - 1);
+    const float2 a0 = a[fpad(j)];
+    float2 a1 = a[fpad(j + q)], a2 = a[fpad(j + 2 * q)], a3 = a[fpad(j + 3 * q)];
+    if (Ns > 1) {
+      a1 = cmul(a1, tw4[st][0]);
+      a2 = cmul(a2, tw4[st][1]);
+      a3 = cmul(a3, tw4[st][2]);
+      ++st;
+    }
+    const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y), d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
+    const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y), d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
+    const float2 r13 = make_float2(d13.y, -d13.x);  // -i d13
+    const int d = ((j - k) << 2) + k;
+    b[fpad(d)] = make_float2(s02.x + s13.x, s02.y + s13.y);
+    b[fpad(d + Ns)] = make_float2(d02.x + r13.x, d02.y + r13.y);
+    b[fpad(d + 2 * Ns)] = make_float2(s02.x - s13.x, s02.y - s13.y);
+    b[fpad(d + 3 * Ns)] = make_float2(d02.x - r13.x, d02.y - r13.y);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
 // One CTA of 256 threads per frame; H = N/2 is the complex FFT length (= K), NTM bounds
 // the n-tiles of the sampling GEMM.
 template <int H, int NTM>
@@ -375,8 +454,10 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
   // each thread owns the complex samples j + i Tg (i = 0..3) of its group's channel,
   // loaded one round ahead
   const int grp = tid / Tg, j = tid - grp * Tg;
-  float2* bufA = fbuf + grp * 2 * H;
-  float2* bufB = bufA + H;
+  float2* bufA = fbuf + grp * 2 * fpad_len(H);
+  float2* bufB = bufA + fpad_len(H);
+  float2 tw4[FrontFft<H>::NTW][3];
+  front_fft_twiddles<H>(a.twiddle, j, tw4);
   const float2* w2 = reinterpret_cast<const float2*>(a.window);
   float2 xv[4], wv[4];
 #pragma unroll
@@ -393,19 +474,20 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
     __syncthreads();  // twiddles ready / previous round's buffers consumed
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      bufA[j + i * Tg] = make_float2(xv[i].x * wv[i].x, xv[i].y * wv[i].y);
+      bufA[fpad(j + i * Tg)] = make_float2(xv[i].x * wv[i].x, xv[i].y * wv[i].y);
     if (m0 + groups < M) load_round(m0 + groups);  // in flight during this round's FFT
     __syncthreads();
     // every thread of the block takes part in the FFT's barriers
-    const float2* Z = stockham_fft_r4_fixed<H, 1, false>(bufA, bufB, j, tw);
+    const float2* Z = front_fft<H>(bufA, bufB, j, tw4);
     if (m < M) {
       // real spectrum from the packed transform, then PHAT
       float2* out = yh + static_cast<size_t>(m) * KS;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int k = j + i * Tg;
-        const float2 zk = Z[k];
-        const float2 zc = make_float2(Z[(H - k) & (H - 1)].x, -Z[(H - k) & (H - 1)].y);
+        const float2 zk = Z[fpad(k)];
+        const float2 zr = Z[fpad((H - k) & (H - 1))];
+        const float2 zc = make_float2(zr.x, -zr.y);
         const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
         const float2 O = make_float2(0.5f * (zk.y - zc.y), -0.5f * (zk.x - zc.x));
         const float2 WO = cmul(tw[k], O);
@@ -635,7 +717,7 @@ void front_fat_table(const float* fat, int Rp, int L, std::vector<uint4>& tab) {
 size_t front_smem_bytes(int M, int N, int L, int max_Np) {
   const int H = N / 2, Tg = H / 4;
   const int groups = 256 / Tg;
-  const size_t fbuf = std::max(sizeof(float2) * groups * 2 * H,
+  const size_t fbuf = std::max(sizeof(float2) * groups * 2 * fpad_len(H),
                                sizeof(float) * 8 * 16 * 8 * front_ntm(max_Np));
   return sizeof(float2) * (H + static_cast<size_t>(M) * front_row(H)) + fbuf + sizeof(float) * L;
 }
@@ -655,7 +737,7 @@ cudaError_t launch_front(const float* frames, int F, int M, int N, const float* 
   const int NT = front_ntiles(max_Np);
   const int H = N / 2, groups = 256 / (H / 4);
   const int NTM = front_ntm(max_Np);
-  const int fbuf_floats = std::max(4 * groups * H, 8 * 16 * 8 * NTM);
+  const int fbuf_floats = std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * NTM);
   const int ot = t == OpType::F32 ? 0 : t == OpType::F16 ? 1 : t == OpType::BF16 ? 2 : 3;
   FrontParams a{frames, M, P, L, window, twiddle, pairs, Np, off, stab, max_Np, NT,
                 fbuf_floats, ftab, Rp, out_cols, scale, ot, out, out_lo};
