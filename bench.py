@@ -48,7 +48,8 @@ def parse(argv=None):
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--rank", type=int, default=16, help="SLRI rank R")
     ap.add_argument("--taps", type=float, default=4.0, help="SSPI taps per location and pair")
-    ap.add_argument("--precision", default="bf16", help="fp32 | bf16 | fp16 | fp16x3")
+    ap.add_argument("--precision", default="bf16",
+                    help="fp32 | bf16 | fp16 | tf32 | bf16x3 | fp16x3 | tf32x3")
     ap.add_argument("--conv-precision", default=None)
     ap.add_argument("--slri-precision", default=None)
     ap.add_argument("--sspi-precision", default=None)
@@ -251,7 +252,7 @@ def contraction_work(m, prec, info, F, R):
     """(kind, amount per launch) of the dominant kernel of method m: algorithmic FLOPs of
     the contraction (a split-precision FP16 hi+lo run executes three products) or bytes."""
     J, P, K, L = info.J, info.P, info.K, info.L
-    x3 = 3.0 if prec == "fp16x3" else 1.0
+    x3 = 3.0 if prec.endswith("x3") else 1.0
     if m == "conv":
         return "flop", x3 * 4.0 * J * P * (K - 1) * F  # 2JP(K-1) real MACs per frame
     if m == "slri":
@@ -386,6 +387,11 @@ def run_libsrp(a):
             peak = FFMA_LANES * 2 * smmax * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": work / t_launch / 1e12, "peak": peak, "unit": "TFLOP/s",
                     "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
+        elif prec[dom].startswith("tf32"):
+            # TF32 has no measured peak: the measured BF16 one x the nominal ratio 1.1 / 2.25
+            roof = {"bound": "tensor", "achieved": work / t_launch / 1e12, "peak": bf16s * 1.1 / 2.25,
+                    "unit": "TFLOP/s",
+                    "peak_source": f"{src} bf16 sustained x 1.1/2.25 (nominal TF32 / BF16 dense rates)"}
         else:
             roof = {"bound": "tensor", "achieved": work / t_launch / 1e12, "peak": bf16s,
                     "unit": "TFLOP/s", "peak_source": f"{src} bf16 sustained (FP16 runs at the BF16 rate)"}

@@ -65,17 +65,24 @@ typedef enum {
   SRP_LR = 5     /* LR-SRP, Sec. III-A, boxed Eq. z_lr (rank-R factors of H) */
 } srp_method;
 
-/* Arithmetic of the map contraction (the front end -- DFT, PHAT, iFFT sampling -- is FP32
- * in every case).  The tensor-core precisions run every method on tcgen05 GEMMs:
- * conv over the SRP matrix; SI, TD and SSPI over a dense [J][L] interpolation operand
- * (SSPI and TD skip the all-zero 64-column blocks of each 256-cell tile); SLRI's
- * Lambda_tall product (Lambda_fat xi stays FP32). */
+/* Arithmetic of the map contraction.  The front end (DFT, PHAT, sampling, Lambda_fat xi) is
+ * FP32-class in every case: FP32 FFTs, and the sampling and Lambda_fat products on the
+ * warp-level tensor cores with FP16 hi+lo operands.  The tensor-core precisions run every
+ * method's contraction on tcgen05 GEMMs: conv over the SRP matrix; SI, TD and SSPI over a
+ * dense [J][L] interpolation operand (SSPI and TD skip the all-zero 64-column blocks of
+ * each 256-cell tile); SLRI's Lambda_tall product; LR-SRP's two factor products.  "x3":
+ * operands split into hi + lo planes (hi = rnd(x), lo = rnd(x - hi)) and three products
+ * hi*hi + hi*lo + lo*hi accumulated in FP32. */
 typedef enum {
   SRP_FP32 = 0,    /* FP32 operands, FP32 FFMA on CUDA cores */
-  SRP_BF16 = 1,    /* BF16 tensor-core GEMM, FP32 accumulate */
-  SRP_FP16 = 2,    /* FP16 tensor-core GEMM, FP32 accumulate */
-  SRP_FP16X3 = 4   /* FP16 hi+lo split operands, 3 tensor-core products
-                      (hi*hi + hi*lo + lo*hi), FP32 accumulate: FP32-class maps */
+  SRP_BF16 = 1,    /* BF16 tensor-core GEMM (kind::f16), FP32 accumulate */
+  SRP_FP16 = 2,    /* FP16 tensor-core GEMM (kind::f16), FP32 accumulate */
+  SRP_BF16X3 = 3,  /* BF16 hi+lo, 3 products: 16 significant bits per operand */
+  SRP_FP16X3 = 4,  /* FP16 hi+lo, 3 products: 22 significant bits, FP32-class maps */
+  SRP_TF32X3 = 5,  /* TF32 hi+lo, 3 products: 22 significant bits with the FP32 exponent
+                      range, FP32-class maps at half the kind::f16 rate */
+  SRP_TF32 = 6     /* TF32 tensor-core GEMM (kind::tf32, FP32 operands rounded to 10
+                      mantissa bits), FP32 accumulate */
 } srp_precision;
 
 typedef enum {

@@ -13,4 +13,5 @@ from ._abi import (  # noqa: F401
     make_desc, lib, SIGNATURES, LIB_PATH,
     SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_ETIMEOUT, SRP_EUNSUPPORTED, SRP_EAGAIN,
     SRP_CONV, SRP_SLRI, SRP_SSPI, SRP_SI, SRP_TD, SRP_LR, SRP_FP32, SRP_BF16, SRP_FP16, SRP_FP16X3,
+    SRP_BF16X3, SRP_TF32X3, SRP_TF32, PRECISIONS,
 )

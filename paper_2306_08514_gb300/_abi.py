@@ -15,12 +15,13 @@ LIB_PATH = os.path.join(_PKG, "libsrp.so")
 
 SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_ETIMEOUT, SRP_EUNSUPPORTED, SRP_EAGAIN = 0, 1, 2, 3, 4, 5, 6
 SRP_CONV, SRP_SLRI, SRP_SSPI, SRP_SI, SRP_TD, SRP_LR = 0, 1, 2, 3, 4, 5
-SRP_FP32, SRP_BF16, SRP_FP16, SRP_FP16X3 = 0, 1, 2, 4
+SRP_FP32, SRP_BF16, SRP_FP16, SRP_BF16X3, SRP_FP16X3, SRP_TF32X3, SRP_TF32 = 0, 1, 2, 3, 4, 5, 6
 SRP_WIN_HANN, SRP_WIN_SQRT_HANN, SRP_WIN_RECT = 0, 1, 2
 
 METHODS = {"conv": SRP_CONV, "slri": SRP_SLRI, "sspi": SRP_SSPI, "si": SRP_SI, "td": SRP_TD,
            "lr": SRP_LR}
-PRECISIONS = {"fp32": SRP_FP32, "bf16": SRP_BF16, "fp16": SRP_FP16, "fp16x3": SRP_FP16X3}
+PRECISIONS = {"fp32": SRP_FP32, "bf16": SRP_BF16, "fp16": SRP_FP16, "bf16x3": SRP_BF16X3,
+              "fp16x3": SRP_FP16X3, "tf32x3": SRP_TF32X3, "tf32": SRP_TF32}
 WINDOWS = {"hann": SRP_WIN_HANN, "sqrt-hann": SRP_WIN_SQRT_HANN, "rect": SRP_WIN_RECT}
 
 

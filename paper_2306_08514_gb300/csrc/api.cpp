@@ -53,8 +53,7 @@ srp_status validate(const srp_plan_desc* d) {
         return fail(SRP_EINVAL, "far-field grid rows must be unit vectors");
     }
   if (d->method < SRP_CONV || d->method > SRP_LR) return fail(SRP_EINVAL, "unknown method");
-  if (d->precision != SRP_FP32 && d->precision != SRP_BF16 && d->precision != SRP_FP16 &&
-      d->precision != SRP_FP16X3)
+  if (d->precision < SRP_FP32 || d->precision > SRP_TF32)
     return fail(SRP_EINVAL, "unknown precision");
   if (d->method == SRP_TD && d->n_aux < 1)
     return fail(SRP_EINVAL, "conv. TD-SRP needs n_aux >= 1 (the rounded lag must be sampled)");
@@ -115,7 +114,17 @@ void free_plan(srp_plan_s* p) {
     }                                                                                      \
   } while (0)
 
-size_t op_bytes(OpType t) { return t == OpType::F32 ? 4 : 2; }
+OpType op_of(int precision) {
+  switch (precision) {
+    case SRP_BF16: return OpType::BF16;
+    case SRP_FP16: return OpType::F16;
+    case SRP_BF16X3: return OpType::BF16X2;
+    case SRP_FP16X3: return OpType::F16X2;
+    case SRP_TF32: return OpType::TF32;
+    case SRP_TF32X3: return OpType::TF32X2;
+    default: return OpType::F32;
+  }
+}
 
 // Contraction depth of the tensor-core SLRI product (R <= 64 padded to one k-block); also
 // the multiple that pads L for the dense interpolation operands.
@@ -160,8 +169,7 @@ cudaError_t contract_to(srp_plan_s* p, const void* A, const void* A_lo, const vo
     return launch_sgemm_nt_argmax(static_cast<const float*>(A), static_cast<const float*>(B), out,
                                   keys, F, Jout, Kd, p->d_split, s);
   }
-  const int nseg = p->op == OpType::F16X2 ? 3 : 1;
-  p->launches += (!kb_ptr && tc_gemm_slices(F, Jout, Kd, nseg, p->num_sms) > 1) ? 2 : 1;
+  p->launches += (!kb_ptr && tc_gemm_slices(F, Jout, Kd, p->op, p->num_sms) > 1) ? 2 : 1;
   TcGemm tg;
   tg.A = A;
   tg.A_lo = A_lo;
@@ -371,10 +379,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     }
     p->nnz = static_cast<long long>(nz);
   }
-  p->op = desc->precision == SRP_FP32 ? OpType::F32
-          : desc->precision == SRP_BF16 ? OpType::BF16
-          : desc->precision == SRP_FP16 ? OpType::F16
-                                        : OpType::F16X2;
+  p->op = op_of(desc->precision);
   p->Lpad = (g.L + kSlriKd - 1) / kSlriKd * kSlriKd;
   p->max_Np = *std::max_element(g.Np.begin(), g.Np.end());
   p->use_front = desc->method != SRP_CONV && desc->method != SRP_LR &&
@@ -382,7 +387,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   if (desc->method == SRP_SI || desc->method == SRP_TD ||
       (desc->method == SRP_SSPI && p->op != OpType::F32)) {
     const double bbytes = static_cast<double>(g.J) * p->Lpad * op_bytes(p->op) *
-                          (p->op == OpType::F16X2 ? 2 : 1);
+                          (op_split(p->op) ? 2 : 1);
     if (bbytes > 200e9) {
       delete p;
       return fail(SRP_EUNSUPPORTED, "dense interpolation operand would need more than 200 GB");
@@ -390,7 +395,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   }
   if (desc->method == SRP_CONV) {
     const double hbytes = static_cast<double>(g.J) * g.P * g.N * op_bytes(p->op) *
-                          (p->op == OpType::F16X2 ? 2 : 1);
+                          (op_split(p->op) ? 2 : 1);
     p->h_generated = desc->h_on_the_fly == 1 || (desc->h_on_the_fly == 0 && hbytes > kMaxStoredH);
     if (p->h_generated && p->op != OpType::F32) {
       delete p;
@@ -459,7 +464,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   } else if (desc->method == SRP_CONV) {
     const size_t Kd = static_cast<size_t>(g.P) * g.N;
     const size_t eb = op_bytes(p->op);
-    const bool split = p->op == OpType::F16X2;
+    const bool split = op_split(p->op);
     SRP_ALLOC(p, p->d_H, static_cast<size_t>(g.J) * Kd * eb);
     if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(g.J) * Kd * eb);
     SRP_ALLOC(p, p->d_A, F * Kd * eb);
@@ -469,8 +474,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       const int nsplit = sgemm_split_count(static_cast<int>(Kd));
       if (nsplit > 1) ws_floats = static_cast<size_t>(nsplit) * F * g.J;
     } else {
-      ws_floats = tc_gemm_workspace_floats(p->Fmax, g.J, static_cast<int>(Kd), split ? 3 : 1,
-                                           p->num_sms);
+      ws_floats = tc_gemm_workspace_floats(p->Fmax, g.J, static_cast<int>(Kd), p->op, p->num_sms);
     }
     if (ws_floats > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws_floats);
     double* d_tau = nullptr;
@@ -498,7 +502,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     const int R = p->R, D = g.P * (g.K - 1);
     const size_t Kd = static_cast<size_t>(g.P) * g.N;
     const size_t eb = op_bytes(p->op);
-    const bool split = p->op == OpType::F16X2;
+    const bool split = op_split(p->op);
     std::vector<std::complex<double>> ht, hf;
     srp_status fst = fit_lr_device(g, R, ht, hf, p->sigma, s);
     if (fst != SRP_OK) {
@@ -510,7 +514,8 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       // |u| <= ||psi||_2 <= sqrt(D) (rows of H_fat are orthonormal, |psi| <= 1); the tall
       // entries are at most 2 sigma_1: scale them by 2^-e into the FP16 range
       p->slri_exp = std::max(0, static_cast<int>(std::ceil(std::log2(2.0 * p->sigma[0] / 16384.0))));
-      if (std::sqrt(static_cast<double>(D)) * std::ldexp(1.0, p->slri_exp) > 16384.0) {
+      const bool fp16 = p->op == OpType::F16 || p->op == OpType::F16X2;
+      if (fp16 && std::sqrt(static_cast<double>(D)) * std::ldexp(1.0, p->slri_exp) > 16384.0) {
         free_plan(p);
         return fail(SRP_EUNSUPPORTED, "LR-SRP operands exceed the FP16 range (use SRP_FP32)");
       }
@@ -570,14 +575,14 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       const int nsplit = sgemm_split_count(static_cast<int>(Kd));
       if (nsplit > 1) ws = static_cast<size_t>(nsplit) * F * 2 * R;
     } else {
-      ws = std::max(tc_gemm_workspace_floats(p->Fmax, 2 * R, static_cast<int>(Kd), split ? 3 : 1, p->num_sms),
-                    tc_gemm_workspace_floats(p->Fmax, g.J, p->lr_kd, split ? 3 : 1, p->num_sms));
+      ws = std::max(tc_gemm_workspace_floats(p->Fmax, 2 * R, static_cast<int>(Kd), p->op, p->num_sms),
+                    tc_gemm_workspace_floats(p->Fmax, g.J, p->lr_kd, p->op, p->num_sms));
     }
     if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
   } else {
     SRP_ALLOC(p, p->d_xi, sizeof(float) * F * g.L);
     const size_t eb = op_bytes(p->op);
-    const bool split = p->op == OpType::F16X2;
+    const bool split = op_split(p->op);
     if (desc->method == SRP_SLRI) {
       std::vector<float> tall, fat;
       // exact Gram eigen-decomposition for short sample vectors, device subspace
@@ -615,7 +620,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       }
       size_t ws = p->op == OpType::F32
                       ? 0
-                      : tc_gemm_workspace_floats(p->Fmax, g.J, kSlriKd, split ? 3 : 1, p->num_sms);
+                      : tc_gemm_workspace_floats(p->Fmax, g.J, kSlriKd, p->op, p->num_sms);
       if (!p->use_front && g.L > kFatGemmMinL) {
         // long sample vectors: u = Lambda_fat xi as a GEMM (xi operand [F][Lpad], factor
         // [Rp][Lpad]) instead of the per-frame dot products
@@ -630,7 +635,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
           const int nsplit = sgemm_split_count(p->Lpad);
           if (nsplit > 1) ws = std::max(ws, static_cast<size_t>(nsplit) * F * Rp);
         } else {
-          ws = std::max(ws, tc_gemm_workspace_floats(p->Fmax, Rp, p->Lpad, split ? 3 : 1, p->num_sms));
+          ws = std::max(ws, tc_gemm_workspace_floats(p->Fmax, Rp, p->Lpad, p->op, p->num_sms));
         }
       }
       if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
@@ -741,7 +746,7 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
           const int nsplit = sgemm_split_count(Lpad);
           if (nsplit > 1) ws = static_cast<size_t>(nsplit) * F * g.J;
         } else if (kb_ptr.empty()) {
-          ws = tc_gemm_workspace_floats(p->Fmax, g.J, Lpad, split ? 3 : 1, p->num_sms);
+          ws = tc_gemm_workspace_floats(p->Fmax, g.J, Lpad, p->op, p->num_sms);
         }
         if (ws > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws);
       }
@@ -777,8 +782,8 @@ extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t*
     }
   if (maxNp >= d.N / 2) return fail(SRP_EINVAL, "N_p >= K: the sample window is wider than the frame");
   const double J = d.J, P = d.M * (d.M - 1) / 2.0, N = d.N, K = d.N / 2.0, F = d.max_frames;
-  const double eb = d.precision == SRP_FP32 ? 4.0 : 2.0;
-  const double planes = d.precision == SRP_FP16X3 ? 2.0 : 1.0;
+  const double eb = static_cast<double>(op_bytes(op_of(d.precision)));
+  const double planes = op_split(op_of(d.precision)) ? 2.0 : 1.0;
   const double Lpad = std::ceil(L / 64.0) * 64.0;
   double b = F * d.M * K * 8.0 + F * 8.0 + 4096.0;  // y-hat, argmax keys, small tables
   switch (d.method) {

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include "srp_device.cuh"
+#include "srp_ops.cuh"
 
 namespace srp {
 
@@ -269,42 +270,16 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 // 16-bit [F][64] scaled by `scale`.  Saves the y-hat round trip through global memory and
 // the separate packing and Lambda_fat launches.
 // ---------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T f2op(float v);
-template <>
-__device__ __forceinline__ __half f2op<__half>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 f2op<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-template <typename T>
-__device__ __forceinline__ float op2f(T v);
-template <>
-__device__ __forceinline__ float op2f<__half>(__half v) { return __half2float(v); }
-template <>
-__device__ __forceinline__ float op2f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// out[idx] = v as FP32, 16-bit, or 16-bit hi + lo
-template <int OT>
-__device__ __forceinline__ void put_op(void* hi, void* lo, size_t idx, float v) {
-  if constexpr (OT == 0) {
-    static_cast<float*>(hi)[idx] = v;
-  } else if constexpr (OT == 1) {
-    static_cast<__half*>(hi)[idx] = f2op<__half>(v);
-  } else if constexpr (OT == 2) {
-    static_cast<__nv_bfloat16*>(hi)[idx] = f2op<__nv_bfloat16>(v);
-  } else {
-    const __half h = f2op<__half>(v);
-    static_cast<__half*>(hi)[idx] = h;
-    static_cast<__half*>(lo)[idx] = f2op<__half>(v - op2f<__half>(h));
-  }
-}
-
-// out[idx] = v in the operand type ot chosen at run time (0 FP32, 1 FP16, 2 BF16, 3 FP16 hi + lo)
+// out[idx] = v in the operand type ot (an OpType value) chosen at run time
 __device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx, float v) {
-  switch (ot) {
-    case 0: put_op<0>(hi, lo, idx, v); break;
-    case 1: put_op<1>(hi, lo, idx, v); break;
-    case 2: put_op<2>(hi, lo, idx, v); break;
-    default: put_op<3>(hi, lo, idx, v); break;
+  switch (static_cast<OpType>(ot)) {
+    case OpType::F32: op_store<float, false>(hi, lo, idx, v); break;
+    case OpType::F16: op_store<__half, false>(hi, lo, idx, v); break;
+    case OpType::BF16: op_store<__nv_bfloat16, false>(hi, lo, idx, v); break;
+    case OpType::F16X2: op_store<__half, true>(hi, lo, idx, v); break;
+    case OpType::BF16X2: op_store<__nv_bfloat16, true>(hi, lo, idx, v); break;
+    case OpType::TF32: op_store<tf32_t, false>(hi, lo, idx, v); break;
+    case OpType::TF32X2: op_store<tf32_t, true>(hi, lo, idx, v); break;
   }
 }
 
@@ -738,7 +713,7 @@ cudaError_t launch_front(const float* frames, int F, int M, int N, const float* 
   const int H = N / 2, groups = 256 / (H / 4);
   const int NTM = front_ntm(max_Np);
   const int fbuf_floats = std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * NTM);
-  const int ot = t == OpType::F32 ? 0 : t == OpType::F16 ? 1 : t == OpType::BF16 ? 2 : 3;
+  const int ot = static_cast<int>(t);
   FrontParams a{frames, M, P, L, window, twiddle, pairs, Np, off, stab, max_Np, NT,
                 fbuf_floats, ftab, Rp, out_cols, scale, ot, out, out_lo};
   const size_t smem = front_smem_bytes(M, N, L, max_Np);
@@ -816,21 +791,10 @@ cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N
 // Im psi_p(k) at p*N + K + k (k = 0..K-1, psi(0) = 0).  With B[i] = [2cos, -2sin]
 // (launch_conv_matrix) the dot product is 2 Re[H_p psi_p] summed over pairs.
 // ---------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T to_op(float v);
-template <>
-__device__ __forceinline__ float to_op<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ __half to_op<__half>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(float v) {
-  return __float2bfloat16_rn(v);
-}
-
 template <typename T, bool SPLIT>
 __global__ void conv_pack_kernel(const float2* __restrict__ yhat, int F, int M, int P, int N,
-                                 const int2* __restrict__ pairs, T* __restrict__ A,
-                                 T* __restrict__ A_lo) {
+                                 const int2* __restrict__ pairs, void* __restrict__ A,
+                                 void* __restrict__ A_lo) {
   const int K = N >> 1;
   const size_t total = static_cast<size_t>(F) * P * K;
   for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < total;
@@ -843,14 +807,8 @@ __global__ void conv_pack_kernel(const float2* __restrict__ yhat, int F, int M, 
     const float2* yf = yhat + static_cast<size_t>(f) * M * K;
     const float2 v = cmul_conj(yf[q.x * K + k], yf[q.y * K + k]);
     const size_t base = (static_cast<size_t>(f) * P + p) * N + k;
-    const T re = to_op<T>(v.x);
-    const T im = to_op<T>(v.y);
-    A[base] = re;
-    A[base + K] = im;
-    if (SPLIT) {
-      A_lo[base] = to_op<T>(v.x - static_cast<float>(re));
-      A_lo[base + K] = to_op<T>(v.y - static_cast<float>(im));
-    }
+    op_store<T, SPLIT>(A, A_lo, base, v.x);
+    op_store<T, SPLIT>(A, A_lo, base + K, v.y);
   }
 }
 
@@ -866,25 +824,10 @@ cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, con
   if (F <= 0) return cudaSuccess;
   const size_t total = static_cast<size_t>(F) * P * (N / 2);
   const int g = grid_for(total, 256);
-  switch (t) {
-    case OpType::F32:
-      conv_pack_kernel<float, false><<<g, 256, 0, s>>>(yhat, F, M, P, N, pairs,
-                                                       static_cast<float*>(A), nullptr);
-      break;
-    case OpType::F16:
-      conv_pack_kernel<__half, false><<<g, 256, 0, s>>>(yhat, F, M, P, N, pairs,
-                                                        static_cast<__half*>(A), nullptr);
-      break;
-    case OpType::BF16:
-      conv_pack_kernel<__nv_bfloat16, false><<<g, 256, 0, s>>>(
-          yhat, F, M, P, N, pairs, static_cast<__nv_bfloat16*>(A), nullptr);
-      break;
-    case OpType::F16X2:
-      conv_pack_kernel<__half, true><<<g, 256, 0, s>>>(yhat, F, M, P, N, pairs,
-                                                       static_cast<__half*>(A),
-                                                       static_cast<__half*>(A_lo));
-      break;
-  }
+  op_dispatch(t, [&](auto tag) {
+    using Tag = decltype(tag);
+    conv_pack_kernel<typename Tag::type, Tag::split><<<g, 256, 0, s>>>(yhat, F, M, P, N, pairs, A, A_lo);
+  });
   return cudaGetLastError();
 }
 
@@ -895,7 +838,7 @@ cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, con
 // ---------------------------------------------------------------------------------
 template <typename T, bool SPLIT>
 __global__ void conv_matrix_kernel(const double* __restrict__ tau, int J, int P, int N,
-                                   T* __restrict__ B, T* __restrict__ B_lo) {
+                                   void* __restrict__ B, void* __restrict__ B_lo) {
   const int K = N >> 1;
   const size_t total = static_cast<size_t>(J) * P * K;
   for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < total;
@@ -911,18 +854,8 @@ __global__ void conv_matrix_kernel(const double* __restrict__ tau, int J, int P,
       sn *= -2.0;
     }
     const size_t base = ip * N + k;
-    if constexpr (SPLIT) {
-      const __half hc = __float2half_rn(static_cast<float>(c));
-      const __half hs = __float2half_rn(static_cast<float>(sn));
-      B[base] = hc;
-      B[base + K] = hs;
-      B_lo[base] = __float2half_rn(static_cast<float>(c - static_cast<double>(__half2float(hc))));
-      B_lo[base + K] =
-          __float2half_rn(static_cast<float>(sn - static_cast<double>(__half2float(hs))));
-    } else {
-      B[base] = to_op<T>(static_cast<float>(c));
-      B[base + K] = to_op<T>(static_cast<float>(sn));
-    }
+    op_store_d<T, SPLIT>(B, B_lo, base, c);
+    op_store_d<T, SPLIT>(B, B_lo, base + K, sn);
   }
 }
 
@@ -930,24 +863,10 @@ cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpTyp
                                void* B_lo, cudaStream_t s) {
   const size_t total = static_cast<size_t>(J) * P * (N / 2);
   const int g = grid_for(total, 256);
-  switch (t) {
-    case OpType::F32:
-      conv_matrix_kernel<float, false><<<g, 256, 0, s>>>(tau_dev, J, P, N, static_cast<float*>(B),
-                                                         nullptr);
-      break;
-    case OpType::F16:
-      conv_matrix_kernel<__half, false><<<g, 256, 0, s>>>(tau_dev, J, P, N,
-                                                          static_cast<__half*>(B), nullptr);
-      break;
-    case OpType::BF16:
-      conv_matrix_kernel<__nv_bfloat16, false><<<g, 256, 0, s>>>(
-          tau_dev, J, P, N, static_cast<__nv_bfloat16*>(B), nullptr);
-      break;
-    case OpType::F16X2:
-      conv_matrix_kernel<__half, true><<<g, 256, 0, s>>>(tau_dev, J, P, N, static_cast<__half*>(B),
-                                                         static_cast<__half*>(B_lo));
-      break;
-  }
+  op_dispatch(t, [&](auto tag) {
+    using Tag = decltype(tag);
+    conv_matrix_kernel<typename Tag::type, Tag::split><<<g, 256, 0, s>>>(tau_dev, J, P, N, B, B_lo);
+  });
   return cudaGetLastError();
 }
 

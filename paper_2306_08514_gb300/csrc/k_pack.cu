@@ -1,47 +1,17 @@
 // Operand preparation for the tensor-core contractions (k_tc_gemm.cu):
-//   * pack16:       FP32 rows -> 16-bit rows padded to a multiple of 64 columns, optionally
-//                   split into hi + lo planes (hi = fp16(x), lo = fp16(x - hi));
+//   * pack16:       FP32 rows -> operand rows (FP16, BF16 or TF32) padded to a multiple of
+//                   64 columns, optionally split into hi + lo planes (srp_ops.cuh);
 //   * csr_to_dense: the kept entries of Lambda_sp (Eq. min_Lambda_sp) scattered into a
 //                   zeroed dense [J][Lpad] operand;
 //   * interp_dense: Lambda of SI-SRP, [Lambda_p]_{i,n} = sinc(Delta t_p(i)/T - n)
 //                   (Eq. Lambda_p), or its conv. TD-SRP counterpart, 1 where
 //                   n = round(Delta t_p(i)/T) (Eq. TD_SRP), evaluated in FP64 per entry.
 #include "srp_internal.h"
+#include "srp_ops.cuh"
 
 namespace srp {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ T cvt16(float v);
-template <>
-__device__ __forceinline__ __half cvt16<__half>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 cvt16<__nv_bfloat16>(float v) {
-  return __float2bfloat16_rn(v);
-}
-template <typename T>
-__device__ __forceinline__ float back32(T v);
-template <>
-__device__ __forceinline__ float back32<__half>(__half v) { return __half2float(v); }
-template <>
-__device__ __forceinline__ float back32<__nv_bfloat16>(__nv_bfloat16 v) {
-  return __bfloat162float(v);
-}
-
-// Writes v (FP64 or FP32 value) at out[idx] in the operand type: FP32, 16-bit, or 16-bit
-// hi + lo with the lo plane holding the rounding remainder of hi.
-template <typename T, bool SPLIT>
-__device__ __forceinline__ void put(void* hi, void* lo, size_t idx, double v) {
-  if constexpr (sizeof(T) == 4) {
-    static_cast<float*>(hi)[idx] = static_cast<float>(v);
-  } else {
-    const T h = cvt16<T>(static_cast<float>(v));
-    static_cast<T*>(hi)[idx] = h;
-    if constexpr (SPLIT)
-      static_cast<T*>(lo)[idx] = cvt16<T>(static_cast<float>(v - static_cast<double>(back32<T>(h))));
-  }
-}
 
 int grid_for(size_t total, int block) {
   size_t g = (total + block - 1) / block;
@@ -59,7 +29,7 @@ __global__ void pack16_kernel(const float* __restrict__ X, int rows, int C, int 
     const int c = static_cast<int>(e % Cpad);
     const size_t r = e / Cpad;
     const float v = c < C ? X[r * C + c] * scale : 0.f;
-    put<T, SPLIT>(hi, lo, e, static_cast<double>(v));
+    op_store<T, SPLIT>(hi, lo, e, v);
   }
 }
 
@@ -73,8 +43,7 @@ __global__ void csr_to_dense_kernel(const long long* __restrict__ row_ptr,
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < J; i += warps) {
     for (long long t = row_ptr[i] + lane; t < row_ptr[i + 1]; t += 32) {
       const int2 tp = taps[t];
-      put<T, SPLIT>(hi, lo, static_cast<size_t>(i) * Cpad + tp.x,
-                    static_cast<double>(__int_as_float(tp.y)));
+      op_store<T, SPLIT>(hi, lo, static_cast<size_t>(i) * Cpad + tp.x, __int_as_float(tp.y));
     }
   }
 }
@@ -102,27 +71,17 @@ __global__ void interp_dense_kernel(const double* __restrict__ tau, int J, int P
         v = x == 0.0 ? 1.0 : sinpi(x) / (M_PI * x);
       }
     }
-    put<T, SPLIT>(hi, lo, e, v);
+    op_store_d<T, SPLIT>(hi, lo, e, v);
   }
 }
 
 }  // namespace
 
-#define SRP_DISPATCH_OP(t, KERNEL, ...)                                                    \
-  switch (t) {                                                                             \
-    case OpType::F32:                                                                      \
-      KERNEL<float, false><<<g, 256, 0, s>>>(__VA_ARGS__);                                 \
-      break;                                                                               \
-    case OpType::F16:                                                                      \
-      KERNEL<__half, false><<<g, 256, 0, s>>>(__VA_ARGS__);                                \
-      break;                                                                               \
-    case OpType::BF16:                                                                     \
-      KERNEL<__nv_bfloat16, false><<<g, 256, 0, s>>>(__VA_ARGS__);                         \
-      break;                                                                               \
-    case OpType::F16X2:                                                                    \
-      KERNEL<__half, true><<<g, 256, 0, s>>>(__VA_ARGS__);                                 \
-      break;                                                                               \
-  }
+#define SRP_DISPATCH_OP(t, KERNEL, ...)                                            \
+  op_dispatch(t, [&](auto tag) {                                                   \
+    using Tag = decltype(tag);                                                     \
+    KERNEL<typename Tag::type, Tag::split><<<g, 256, 0, s>>>(__VA_ARGS__);         \
+  });
 
 cudaError_t launch_pack16(const float* X, int rows, int C, int Cpad, float scale, OpType t,
                           void* hi, void* lo, cudaStream_t s) {
@@ -135,9 +94,9 @@ cudaError_t launch_pack16(const float* X, int rows, int C, int Cpad, float scale
 
 cudaError_t launch_csr_to_dense(const long long* row_ptr, const int2* taps, int J, int Cpad,
                                 OpType t, void* hi, void* lo, cudaStream_t s) {
-  const size_t eb = t == OpType::F32 ? 4 : 2;
+  const size_t eb = op_bytes(t);
   cudaError_t e = cudaMemsetAsync(hi, 0, static_cast<size_t>(J) * Cpad * eb, s);
-  if (e == cudaSuccess && t == OpType::F16X2)
+  if (e == cudaSuccess && op_split(t))
     e = cudaMemsetAsync(lo, 0, static_cast<size_t>(J) * Cpad * eb, s);
   if (e != cudaSuccess) return e;
   const int g = grid_for(static_cast<size_t>(J) * 32, 256);

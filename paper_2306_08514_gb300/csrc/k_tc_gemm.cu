@@ -74,7 +74,9 @@ constexpr int MIN_KB_PER_SLICE = 32;
 
 struct TcParams {
   int F, J;
-  int kb_per_seg, nseg;  // dense k-blocks of 64 per operand segment, number of segments
+  int kb_per_seg, nseg;  // dense k-steps per operand segment, number of segments
+  int sub_shift;         // log2 of the k-steps per 64 operand columns (1 for TF32, else 0)
+  int tf32;              // kind::tf32 instead of kind::f16
   const int* kb_ptr;     // block-sparse: k-block list of cell tile n is
   const int* kb_idx;     //   kb_idx[kb_ptr[n] .. kb_ptr[n+1]); NULL = dense
   int nM, nN, nslices, kb_per_slice;
@@ -98,7 +100,8 @@ __device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
   w.n = rem / p.nM;
   w.m = rem - w.n * p.nM;
   w.list = p.kb_ptr ? (w.n * p.tn) / LIST_TILE : 0;
-  w.m_len = p.kb_ptr ? __ldg(p.kb_ptr + w.list + 1) - __ldg(p.kb_ptr + w.list) : p.kb_per_seg;
+  w.m_len = p.kb_ptr ? (__ldg(p.kb_ptr + w.list + 1) - __ldg(p.kb_ptr + w.list)) << p.sub_shift
+                     : p.kb_per_seg;
   const int nsteps = w.m_len * p.nseg;
   w.s0 = min(nsteps, w.slice * p.kb_per_slice);
   w.s1 = min(nsteps, w.s0 + p.kb_per_slice);
@@ -173,7 +176,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int s = w.s0; s < w.s1; ++s) {
           const int seg = s / w.m_len;
           const int loc = s - seg * w.m_len;
-          const int kx = (list ? __ldg(list + loc) : loc) * TK;  // load overlaps the wait
+          // 64-column block of the k-step (from the list when block-sparse) and, for TF32,
+          // which 32-column half; the load overlaps the wait
+          const int b64 = list ? __ldg(list + (loc >> p.sub_shift)) : loc >> p.sub_shift;
+          const int kx = b64 * TK + ((loc & ((1 << p.sub_shift) - 1)) << (6 - p.sub_shift));
           if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, 1, WAIT_NS)) {
             ok = false;
             break;
@@ -226,11 +232,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_after();
             const uint64_t ad = sdesc_k128(sA + stage * A_BYTES);
             const uint64_t bd = sdesc_k128(sB + stage * B_BYTES);
+            // four MMAs per 128-byte k-step (K = 16 of 16-bit or K = 8 of TF32 each)
+            if (p.tf32) {
 #pragma unroll
-            for (int k = 0; k < TK / 16; ++k)
-              mma_f16(d, ad + static_cast<uint64_t>((k * 32) >> 4),
-                      bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
-                      (s > c0 || k > 0) ? 1u : 0u);
+              for (int k = 0; k < 4; ++k)
+                mma_tf32(d, ad + static_cast<uint64_t>((k * 32) >> 4),
+                         bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
+                         (s > c0 || k > 0) ? 1u : 0u);
+            } else {
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                mma_f16(d, ad + static_cast<uint64_t>((k * 32) >> 4),
+                        bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
+                        (s > c0 || k > 0) ? 1u : 0u);
+            }
             mma_commit(empty_bar(stage));
             if (++stage == STAGES) {
               stage = 0;
@@ -365,11 +380,13 @@ cudaError_t get_encode() {
 
 // 2-D K-major operand map: inner dimension Kd (contiguous), outer `rows`, box 64 x box_rows,
 // 128-byte swizzle; out-of-range rows read as zero.
+// 2-D operand map over [rows][Kd] elements of ebytes (2 or 4), box of one 128-byte k-step
+// (64 or 32 elements) x box_rows, 128-byte swizzle.
 cudaError_t make_operand_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, uint64_t Kd,
-                             uint64_t rows, uint32_t box_rows) {
+                             uint64_t rows, uint32_t box_rows, uint32_t ebytes) {
   cuuint64_t dims[2] = {Kd, rows};
-  cuuint64_t strides[1] = {Kd * 2};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(TK), box_rows};
+  cuuint64_t strides[1] = {Kd * ebytes};
+  cuuint32_t box[2] = {128u / ebytes, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -392,24 +409,27 @@ cudaError_t make_output_map(CUtensorMap* m, float* base, uint64_t J, uint64_t F,
 
 // Reduction slices for F frames (dense operands): 1 while the output tiles fill the GPU;
 // otherwise enough slices (of at least MIN_KB_PER_SLICE k-blocks) to give every SM a tile.
-static int slices_for(int F, int J, int Kd, int nseg, int num_sms, int tn) {
+// k-steps of a dense reduction over Kd columns in operand type t, all segments
+static int ksteps_of(int Kd, OpType t) { return Kd / TK * op_kb_per64(t) * (op_split(t) ? 3 : 1); }
+
+static int slices_for(int F, int J, int Kd, OpType t, int num_sms, int tn) {
   if (F <= 0) return 1;
   const long long tiles = static_cast<long long>((F + TM - 1) / TM) * ((J + tn - 1) / tn);
   if (tiles >= num_sms) return 1;
-  const int kb_total = Kd / TK * nseg;
+  const int kb_total = ksteps_of(Kd, t);
   const long long want = (num_sms + tiles - 1) / tiles;
   const int cap = kb_total / MIN_KB_PER_SLICE > 1 ? kb_total / MIN_KB_PER_SLICE : 1;
   return static_cast<int>(want < cap ? want : cap);
 }
 
-int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms) {
-  return slices_for(F, J, Kd, nseg, num_sms, 256);
+int tc_gemm_slices(int F, int J, int Kd, OpType t, int num_sms) {
+  return slices_for(F, J, Kd, t, num_sms, 256);
 }
 
-size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms) {
+size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, OpType t, int num_sms) {
   size_t need = 0;  // the 256-cell variants need the most slices
   for (int F = 1; F <= F_max; ++F) {
-    const int ns = slices_for(F, J, Kd, nseg, num_sms, 256);
+    const int ns = slices_for(F, J, Kd, t, num_sms, 256);
     if (ns > 1) need = std::max(need, static_cast<size_t>(ns) * F * static_cast<size_t>(J));
   }
   return need;
@@ -436,7 +456,7 @@ int tc_gemm_cell_tile() { return LIST_TILE; }
 int tc_gemm_k_block() { return TK; }
 
 int tc_gemm_default_variant(int Kd, OpType t) {
-  const int steps = Kd / TK * (t == OpType::F16X2 ? 3 : 1);
+  const int steps = ksteps_of(Kd, t);
   return steps <= SHORT_MAX_STEPS ? TC_SHORT_256 : TC_LONG_256;
 }
 
@@ -448,15 +468,20 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   const int variant = g.variant >= 0 ? g.variant : tc_gemm_default_variant(g.Kd, g.t);
   if (variant < 0 || variant >= TC_NVARIANTS) return cudaErrorInvalidValue;
   const int tn = variant == TC_LONG_128 ? 128 : 256;
-  const bool split3 = g.t == OpType::F16X2;
-  const CUtensorMapDataType dt = g.t == OpType::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  if (g.t == OpType::F32) return cudaErrorInvalidValue;
+  const bool split3 = op_split(g.t);
+  const bool tf32 = op_tf32(g.t);
+  const bool bf16 = g.t == OpType::BF16 || g.t == OpType::BF16X2;
+  const CUtensorMapDataType dt = tf32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const uint32_t eb = tf32 ? 4u : 2u;
   CUtensorMap mA0, mA1, mB0, mB1, mZ;
-  if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, TM)) != cudaSuccess) return e;
-  if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, tn)) != cudaSuccess) return e;
+  if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
+  if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, tn, eb)) != cudaSuccess) return e;
   if (split3) {
-    if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, TM)) != cudaSuccess) return e;
-    if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, tn)) != cudaSuccess) return e;
+    if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
+    if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, tn, eb)) != cudaSuccess) return e;
   } else {
     mA1 = mA0;
     mB1 = mB0;
@@ -465,13 +490,15 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.F = g.F;
   p.J = g.J;
   p.tn = tn;
-  p.kb_per_seg = g.Kd / TK;
+  p.sub_shift = tf32 ? 1 : 0;
+  p.tf32 = tf32 ? 1 : 0;
+  p.kb_per_seg = (g.Kd / TK) << p.sub_shift;
   p.nseg = split3 ? 3 : 1;
   p.kb_ptr = g.kb_ptr;
   p.kb_idx = g.kb_idx;
   p.nM = (g.F + TM - 1) / TM;
   p.nN = (g.J + tn - 1) / tn;
-  p.nslices = g.kb_ptr ? 1 : slices_for(g.F, g.J, g.Kd, p.nseg, num_sms, tn);
+  p.nslices = g.kb_ptr ? 1 : slices_for(g.F, g.J, g.Kd, g.t, num_sms, tn);
   const int kb_total = p.kb_per_seg * p.nseg;
   if (p.nslices > 1) {
     p.kb_per_slice = (kb_total + p.nslices - 1) / p.nslices;
@@ -494,7 +521,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   } else {
     mZ = mA0;  // unused
   }
-  const uint32_t idesc = tc::idesc_f16(g.t == OpType::BF16 ? 1u : 0u, TM, tn);
+  const uint32_t idesc = tc::idesc_f16(tf32 ? 2u : bf16 ? 1u : 0u, TM, tn);
   const int total = p.nM * p.nN * p.nslices;
   int grid = total < num_sms ? total : num_sms;
   if (g.max_ctas > 0 && grid > g.max_ctas) grid = g.max_ctas;

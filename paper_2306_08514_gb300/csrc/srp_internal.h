@@ -93,7 +93,17 @@ cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N
                                  cudaStream_t s);
 // Cross-spectra packed as the conv GEMM operand A [F][P*N]:
 // A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
-enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3 /* hi + lo planes */ };
+// Operand type of a contraction: FP32 (CUDA cores), or one or two (hi + lo) planes of
+// FP16, BF16 or TF32 for the tensor cores.  The values double as the front kernel's output
+// codes.
+enum class OpType { F32 = 0, F16 = 1, BF16 = 2, F16X2 = 3, BF16X2 = 4, TF32 = 5, TF32X2 = 6 };
+inline bool op_split(OpType t) {
+  return t == OpType::F16X2 || t == OpType::BF16X2 || t == OpType::TF32X2;
+}
+inline bool op_tf32(OpType t) { return t == OpType::TF32 || t == OpType::TF32X2; }
+inline size_t op_bytes(OpType t) { return t == OpType::F32 || op_tf32(t) ? 4 : 2; }
+// tensor-core k-blocks (128-byte rows) per 64 operand columns
+inline int op_kb_per64(OpType t) { return op_tf32(t) ? 2 : 1; }
 // Fused STFT + PHAT + sampling (+ Lambda_fat) per frame: writes xi (ftab == NULL)
 // or u = Lambda_fat xi * scale, rows of out_cols entries (zero padded) in operand type t.
 // The sampling and the Lambda_fat product are per-frame GEMMs on the warp-level tensor
@@ -129,9 +139,10 @@ cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
 // Sums nz partial maps [nz][F][J] in FP64 into Z and merges the argmax keys.
 cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long long* keys,
                                 int F, int J, cudaStream_t s);
-// Tensor-core contraction (tcgen05, k_tc_gemm.cu): Z[F][J] = A B^T with 16-bit K-major
-// operands A [F][Kd], B [J][Kd] (Kd a multiple of tc_gemm_k_block()), FP32 accumulation,
-// fused argmax keys.  t = F16X2 runs three products over hi and lo planes.  With kb_ptr
+// Tensor-core contraction (tcgen05, k_tc_gemm.cu): Z[F][J] = A B^T with K-major operands
+// A [F][Kd], B [J][Kd] of type t (FP16, BF16 or TF32; Kd a multiple of tc_gemm_k_block()),
+// FP32 accumulation, fused argmax keys.  The split types (op_split) run three products over
+// hi and lo planes.  With kb_ptr
 // (device, [ceil(J / tc_gemm_cell_tile()) + 1]) and kb_idx, the cells of list tile n only
 // visit the k-blocks kb_idx[kb_ptr[n] .. kb_ptr[n+1]) (block-sparse B).  Dense reductions whose
 // output tiles do not fill the GPU are split into tc_gemm_slices(...) slices written to
@@ -160,8 +171,8 @@ enum { TC_LONG_256 = 0,   // 128x256 tiles, 4 operand stages, 1 output box per e
        TC_NVARIANTS = 3 };
 int tc_gemm_default_variant(int Kd, OpType t);
 cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s);
-int tc_gemm_slices(int F, int J, int Kd, int nseg, int num_sms);
-size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, int nseg, int num_sms);
+int tc_gemm_slices(int F, int J, int Kd, OpType t, int num_sms);
+size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, OpType t, int num_sms);
 int tc_gemm_cell_tile();
 // Resolves the tensor-map encoder and sets the kernel's shared-memory attribute on the
 // current device (done at plan creation, so that later launches can be graph-captured).

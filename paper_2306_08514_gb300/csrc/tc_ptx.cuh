@@ -133,6 +133,17 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
       : "memory");
 }
 
+// As mma_f16 for kind::tf32 (TF32 inputs stored as 32-bit words, F32 accumulate); one
+// instruction reduces K = 8, the same 32 bytes of each operand row as kind::f16's K = 16.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrive on an mbarrier once all previously issued tcgen05 ops of this thread complete.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -181,8 +192,8 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A and B of the same 16-bit type
-// (0 = F16, 1 = BF16), both K-major, shape M x N.
+// Instruction descriptor of kind::f16 and kind::tf32: D = F32, A and B of the same type
+// (0 = F16, 1 = BF16 with kind::f16; 2 = TF32 with kind::tf32), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt, int M, int N) {
   return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(S):
     dict(M=1), dict(N=500), dict(N=128), dict(N=4096), dict(fs=0.0), dict(c=-1.0),
     dict(window=7), dict(n_aux=-1), dict(max_frames=0), dict(method=9),
     dict(method=1, rank=0), dict(method=1, rank=65), dict(method=2, taps=0.0),
-    dict(method=2, taps=1e9), dict(precision=3), dict(far_field=2), dict(far_field=1),
+    dict(method=2, taps=1e9), dict(precision=7), dict(precision=-1), dict(far_field=2), dict(far_field=1),
     dict(method=4, n_aux=0), dict(method=5, rank=0), dict(method=5, rank=65), dict(method=6),
 ])
 def test_invalid_desc_is_rejected_on_the_host(S, bad):
@@ -92,3 +92,9 @@ def test_plan_estimate_needs_no_gpu(S):
     assert abs(conv32 - 2 * conv16) < 0.02 * conv32
     assert J * P * N * 4 <= conv32 <= 1.1 * J * P * N * 4
     assert slri < conv16 / 50
+    # TF32 operands are 4 bytes, the x3 precisions hold hi and lo planes
+    est = {p: S.srp_plan_estimate_bytes(S.make_desc(mics, grid, 16000.0, 512, precision=p, max_frames=64))
+           for p in ("tf32", "bf16x3", "fp16x3", "tf32x3")}
+    assert abs(est["tf32"] - conv32) < 0.02 * conv32
+    assert abs(est["bf16x3"] - 2 * conv16) < 0.02 * conv32 and est["bf16x3"] == est["fp16x3"]
+    assert abs(est["tf32x3"] - 2 * conv32) < 0.02 * conv32

@@ -18,7 +18,8 @@ from tests.test_gpu_parity import S, _run, check_argmax, _check_taps, sq, uca_sm
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-PRECS = [("fp32", TOL), ("fp16x3", TOL), ("fp16", 2e-3), ("bf16", 1.5e-2)]
+PRECS = [("fp32", TOL), ("fp16x3", TOL), ("tf32x3", TOL), ("bf16x3", 1e-4), ("fp16", 2e-3),
+         ("tf32", 2e-3), ("bf16", 1.5e-2)]
 TC_PRECS = PRECS[1:]
 
 

@@ -89,10 +89,13 @@ def test_conv_fp32_square4(S, sq):
     assert check_argmax(z, am, zo) >= 0.99
 
 
-# Tensor-core conv bounds: FP16 hi+lo meets the FP32 bar; single FP16 / BF16 operands
-# carry a relative rounding of 2^-11 / 2^-8 per operand, i.e. about sqrt(2/3) u of map
-# error for sums of many terms: stated bounds 2e-3 (FP16) and 1.5e-2 (BF16).
-TC_CASES = [("fp16x3", TOL), ("fp16", 2e-3), ("bf16", 1.5e-2)]
+# Tensor-core conv bounds: FP16 hi+lo and TF32 hi+lo (22 significant bits) meet the FP32
+# bar; single FP16 / TF32 / BF16 operands carry a relative rounding of 2^-11 / 2^-11 / 2^-8
+# per operand, i.e. about sqrt(2/3) u of map error for sums of many terms: stated bounds
+# 2e-3 (FP16, TF32) and 1.5e-2 (BF16); BF16 hi+lo keeps 16 significant bits (the dropped
+# lo*lo and the rounding of lo are ~2^-16 per product): stated bound 1e-4.
+TC_CASES = [("fp16x3", TOL), ("tf32x3", TOL), ("bf16x3", 1e-4), ("fp16", 2e-3), ("tf32", 2e-3),
+            ("bf16", 1.5e-2)]
 
 
 @pytest.mark.parametrize("prec,tol", TC_CASES)
