@@ -251,12 +251,20 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     if (p->profiling && p->chunks_recorded < kMaxChunkEvents) ++p->chunks_recorded;
     return SRP_OK;
   }
-  SRP_LAUNCH(launch_stft_phat(frames, F, g.M, g.N, p->d_window, p->d_twiddle, p->d_yhat, s));
-  SRP_MARK(p, 1, s);
+  if (p->use_front_conv) {
+    // conv / LR operand straight from the frames (one fused launch)
+    SRP_LAUNCH(launch_front_conv(frames, F, g.M, g.N, p->d_window, p->d_twiddle, g.P, p->d_pairs,
+                                 p->op, p->d_A, p->d_A_lo, s));
+    SRP_MARK(p, 1, s);
+  } else {
+    SRP_LAUNCH(launch_stft_phat(frames, F, g.M, g.N, p->d_window, p->d_twiddle, p->d_yhat, s));
+    SRP_MARK(p, 1, s);
+    if (method == SRP_CONV || method == SRP_LR)
+      SRP_LAUNCH(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
+                                  p->d_A_lo, s));
+  }
   switch (method) {
     case SRP_CONV: {
-      SRP_LAUNCH(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
-                                    p->d_A_lo, s));
       SRP_MARK(p, 2, s);
       if (p->h_generated) {
         p->launches += sgemm_split_count(g.P * g.N) > 1 ? 2 : 1;
@@ -272,8 +280,6 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     case SRP_LR: {
       // u = H_fat psi as a real product over the conv operand (rows u_re, u_im), then
       // z = 2 Re[H_tall u] = [2 Re H_tall | -2 Im H_tall] [u_re; u_im] (boxed Eq. z_lr)
-      SRP_LAUNCH(launch_conv_pack(p->d_yhat, F, g.M, g.P, g.N, p->d_pairs, p->op, p->d_A,
-                                  p->d_A_lo, s));
       SRP_MARK(p, 2, s);
       SRP_CUDA_TRY(contract_to(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, nullptr, nullptr,
                                F, p->d_U, 2 * p->R, p->d_keys2, s));
@@ -384,6 +390,8 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   p->max_Np = *std::max_element(g.Np.begin(), g.Np.end());
   p->use_front = desc->method != SRP_CONV && desc->method != SRP_LR &&
                  front_supported(g.M, g.N, g.L, p->max_Np);
+  p->use_front_conv = (desc->method == SRP_CONV || desc->method == SRP_LR) &&
+                      front_conv_supported(g.M, g.N);
   if (desc->method == SRP_SI || desc->method == SRP_TD ||
       (desc->method == SRP_SSPI && p->op != OpType::F32)) {
     const double bbytes = static_cast<double>(g.J) * p->Lpad * op_bytes(p->op) *

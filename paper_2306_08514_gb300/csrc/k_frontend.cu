@@ -301,6 +301,7 @@ struct FrontParams {
   int ot;             // operand type of the output
   void* out;
   void* out_lo;
+  int conv_out;       // 1: write the conv operand row [P*N] of psi instead of sampling
 };
 
 // D += A B for one m16n8k16 tile on the warp-level tensor cores (FP16 in, FP32 accumulate).
@@ -478,6 +479,19 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
     }
   }
   __syncthreads();
+  if (a.conv_out) {
+    // conv. FD-SRP operand (layout of conv_pack_kernel): per pair, Re psi_p(k) at p N + k and
+    // Im psi_p(k) at p N + K + k, k = 0..K-1 (psi(0) = 0: y-hat(0) is zero)
+    const size_t row = static_cast<size_t>(f) * a.P * N;
+    for (int e = tid; e < a.P * K; e += 256) {
+      const int p = e / K, k = e - p * K;
+      const int2 pr = __ldg(a.pairs + p);
+      const float2 v = cmul_conj(yh[pr.x * KS + k], yh[pr.y * KS + k]);
+      put_op_rt(a.ot, a.out, a.out_lo, row + static_cast<size_t>(p) * N + k, v.x);
+      put_op_rt(a.ot, a.out, a.out_lo, row + static_cast<size_t>(p) * N + K + k, v.y);
+    }
+    return;
+  }
   // Sampling (Eq. xi_p_ifft at the lags n = -N_p..N_p) as a GEMM per frame: rows = pairs,
   // K = bins 0..K-1 with Re psi and Im psi interleaved, columns j = lags n = j - nq0, and
   // B[2k][j] = 2 cos(pi k n / K), B[2k+1][j] = -2 sin(pi k n / K), so that
@@ -702,6 +716,9 @@ bool front_supported(int M, int N, int L, int max_Np) {
          front_smem_bytes(M, N, L, max_Np) <= 200 * 1024;
 }
 
+static cudaError_t front_launch(const FrontParams& a, int F, int N, int NTM, size_t smem,
+                                cudaStream_t s);
+
 cudaError_t launch_front(const float* frames, int F, int M, int N, const float* window,
                          const float2* twiddle, int P, const int2* pairs, const int* Np,
                          const int* off, const uint4* stab, int L, int max_Np, const uint4* ftab,
@@ -715,8 +732,27 @@ cudaError_t launch_front(const float* frames, int F, int M, int N, const float* 
   const int fbuf_floats = std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * NTM);
   const int ot = static_cast<int>(t);
   FrontParams a{frames, M, P, L, window, twiddle, pairs, Np, off, stab, max_Np, NT,
-                fbuf_floats, ftab, Rp, out_cols, scale, ot, out, out_lo};
-  const size_t smem = front_smem_bytes(M, N, L, max_Np);
+                fbuf_floats, ftab, Rp, out_cols, scale, ot, out, out_lo, 0};
+  return front_launch(a, F, N, front_ntm(max_Np), front_smem_bytes(M, N, L, max_Np), s);
+}
+
+bool front_conv_supported(int M, int N) { return front_supported(M, N, 0, 0); }
+
+cudaError_t launch_front_conv(const float* frames, int F, int M, int N, const float* window,
+                              const float2* twiddle, int P, const int2* pairs, OpType t, void* A,
+                              void* A_lo, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  if (!front_conv_supported(M, N)) return cudaErrorNotSupported;
+  const int H = N / 2, groups = 256 / (H / 4);
+  FrontParams a{frames, M, P, 0, window, twiddle, pairs, nullptr, nullptr, nullptr, 0, 1,
+                std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * 2), nullptr, 0, 0, 1.f,
+                static_cast<int>(t), A, A_lo, 1};
+  return front_launch(a, F, N, 2, front_smem_bytes(M, N, 0, 0), s);
+}
+
+static cudaError_t front_launch(const FrontParams& a, int F, int N, int NTM, size_t smem,
+                                cudaStream_t s) {
+  const int H = N / 2;
   // one dispatch table entry per (FFT length, n-tile bucket)
   void (*kern)(const FrontParams) = nullptr;
 #define SRP_FRONT(HV, NTV) if (H == HV && NTM == NTV) kern = front_kernel<HV, NTV>;

@@ -123,6 +123,12 @@ cudaError_t launch_front(const float* frames, int F, int M, int N, const float* 
 
 cudaError_t launch_conv_pack(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
                              OpType t, void* A, void* A_lo, cudaStream_t s);
+// The same operand straight from the frames: the front kernel's STFT + PHAT in shared
+// memory, then the cross-spectra packed (no y-hat round trip through memory).
+bool front_conv_supported(int M, int N);
+cudaError_t launch_front_conv(const float* frames, int F, int M, int N, const float* window,
+                              const float2* twiddle, int P, const int2* pairs, OpType t, void* A,
+                              void* A_lo, cudaStream_t s);
 // SRP matrix in GEMM layout B [J][P*N]: 2cos(theta), -2sin(theta), theta = 2 pi k tau / N.
 cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpType t, void* B,
                                void* B_lo, cudaStream_t s);
@@ -259,6 +265,7 @@ struct srp_plan_s {
   void* d_A2 = nullptr;     // LR: u as the operand of the tall product [Fmax][lr_kd]
   void* d_A2_lo = nullptr;
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
+  bool use_front_conv = false;  // conv / LR operand from the fused front kernel
   uint4* d_stab = nullptr;  // fused front end: the sampling operand (front_sampling_table)
   uint4* d_ftab = nullptr;  // fused front end, SLRI: Lambda_fat (front_fat_table)
   // staging for srp_map_host, and its copy pipeline (two D2H streams and one H2D stream;
