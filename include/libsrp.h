@@ -305,6 +305,26 @@ srp_status srp_plan_stage_ms(srp_plan_t plan, float* ms, int* calls);
 srp_status srp_plan_status(srp_plan_t plan, void* stream);
 
 /*
+ * Failure-detection test hooks.  They make a failure on the host side of a call, never a
+ * device fault, trap or unbounded wait.
+ *
+ * srp_debug_fail_allocations -- the next `n` device allocations libsrp makes for plans
+ * and serving slots fail as if the device were out of memory, after `after` further
+ * allocations have succeeded (process-wide; n = 0 clears).  Plan creation then returns
+ * SRP_ENOMEM having released what it had allocated; the server refuses the session.
+ * Errors: SRP_EINVAL (after or n negative).  Needs no GPU.
+ *
+ * srp_debug_stall_next_contraction -- the plan's next tensor-core contraction issues no
+ * operand loads: its MMA and epilogue warps wait on barriers that nothing completes until
+ * their bounded waits (0.2 s for this launch) run out; the kernel releases its tensor
+ * memory and returns.  srp_plan_status then reports SRP_ETIMEOUT and the plan stays
+ * usable for the next call.  Errors: SRP_EINVAL (NULL plan), SRP_EUNSUPPORTED (the plan
+ * has no tensor-core contraction: SRP_FP32).
+ */
+srp_status srp_debug_fail_allocations(int after, int n);
+srp_status srp_debug_stall_next_contraction(srp_plan_t plan);
+
+/*
  * srp_slri_apply_static -- the SLRI interpolation of one batch, u = Lambda_fat xi then
  * z = Lambda_tall u and the argmax per frame, without allocating any memory.  The paper
  * has no counterpart: this entry point exists for callers that cannot allocate device

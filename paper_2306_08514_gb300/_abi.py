@@ -84,6 +84,8 @@ SIGNATURES = {
     "srp_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "srp_plan_stage_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
     "srp_plan_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "srp_debug_fail_allocations": (C.c_int, [C.c_int, C.c_int]),
+    "srp_debug_stall_next_contraction": (C.c_int, [C.c_void_p]),
     "srp_slri_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                         C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "srp_stream_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
@@ -209,6 +211,12 @@ def srp_plan_stage_ms(plan) -> dict:
 def srp_plan_status(plan, stream=None) -> None:
     """Raise SrpError(SRP_ETIMEOUT) if a bounded wait in one of the plan's kernels ran out."""
     _check(lib().srp_plan_status(plan, stream))
+
+
+def srp_debug_fail_allocations(after, n) -> None:
+    """Failure-detection test hook: the next n device allocations of libsrp fail (as out of
+    memory) after `after` more succeed; n = 0 clears."""
+    _check(lib().srp_debug_fail_allocations(int(after), int(n)))
 
 
 def srp_slri_apply_static(xi_ptr, fat_ptr, tall_ptr, F, L, R, J, maps_ptr, argmax_ptr,
@@ -343,6 +351,11 @@ class Plan:
 
     def status(self, stream=None):
         srp_plan_status(self.handle, _stream_handle(stream))
+
+    def debug_stall_next_contraction(self):
+        """Failure-detection test hook: the next tensor-core contraction's bounded waits run
+        out (SRP_ETIMEOUT from status(); the plan stays usable)."""
+        _check(lib().srp_debug_stall_next_contraction(self.handle))
 
     def lags(self):
         return srp_plan_lags(self.handle, self.P)

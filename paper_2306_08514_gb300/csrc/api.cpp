@@ -2,6 +2,8 @@
 // per-call launch sequence of the SRP path.
 #include "srp_internal.h"
 
+#include <mutex>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -71,7 +73,7 @@ void window_table(int N, int kind, std::vector<float>& w) {
 template <typename T>
 cudaError_t dalloc(srp_plan_s* p, T** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  cudaError_t e = device_alloc(reinterpret_cast<void**>(ptr), bytes);
   if (e == cudaSuccess) p->device_bytes += bytes;
   return e;
 }
@@ -186,6 +188,8 @@ cudaError_t contract_to(srp_plan_s* p, const void* A, const void* A_lo, const vo
   tg.split_ws = p->d_split;
   tg.err = p->d_err;
   tg.variant = p->tc_variant;
+  tg.stall = p->stall_next;
+  p->stall_next = false;
   return launch_tc_gemm(tg, p->num_sms, s);
 }
 
@@ -1182,6 +1186,44 @@ extern "C" srp_status srp_plan_status(srp_plan_t plan, void* stream) {
     return fail(SRP_ETIMEOUT, "a bounded wait inside a kernel ran out (code " + std::to_string(code) +
                                   "); its maps are invalid");
   }
+  return SRP_OK;
+}
+
+namespace srp {
+namespace {
+std::mutex g_alloc_mu;
+int g_alloc_skip = 0, g_alloc_fail = 0;  // allocations to let through, then to fail
+}
+cudaError_t device_alloc(void** ptr, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    if (g_alloc_skip > 0) {
+      --g_alloc_skip;
+    } else if (g_alloc_fail > 0) {
+      --g_alloc_fail;
+      *ptr = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(ptr, bytes);
+}
+}  // namespace srp
+
+extern "C" srp_status srp_debug_fail_allocations(int after, int n) {
+  clear_error();
+  if (after < 0 || n < 0) return fail(SRP_EINVAL, "after and n must be >= 0");
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc_skip = n > 0 ? after : 0;
+  g_alloc_fail = n;
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_debug_stall_next_contraction(srp_plan_t plan) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (plan->op == OpType::F32 || plan->h_generated)
+    return fail(SRP_EUNSUPPORTED, "the plan runs no tensor-core contraction");
+  plan->stall_next = true;
   return SRP_OK;
 }
 

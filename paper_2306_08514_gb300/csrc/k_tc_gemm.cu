@@ -68,7 +68,8 @@ static_assert(smem_bytes<4, 1, 256>() <= 232448 && smem_bytes<2, 4, 256>() <= 23
 // k-steps per tile up to which the heuristic picks 2 stages + 4 boxes (measured on uca8:
 // SLRI's one k-block per tile 0.112 -> 0.085 ms; SSPI's five k-blocks run faster with 4)
 constexpr int SHORT_MAX_STEPS = 3;
-constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr uint64_t WAIT_NS = 2000000000ull;        // limit of every mbarrier wait
+constexpr uint64_t STALL_WAIT_NS = 200000000ull;   // ... in a failure-detection test launch
 constexpr int MIN_KB_PER_SLICE = 32;
 }  // namespace
 
@@ -77,6 +78,8 @@ struct TcParams {
   int kb_per_seg, nseg;  // dense k-steps per operand segment, number of segments
   int sub_shift;         // log2 of the k-steps per 64 operand columns (1 for TF32, else 0)
   int tf32;              // kind::tf32 instead of kind::f16
+  int stall;             // failure-detection test: the producer issues no loads
+  unsigned long long wait_ns;  // limit of every mbarrier wait
   const int* kb_ptr;     // block-sparse: k-block list of cell tile n is
   const int* kb_idx;     //   kb_idx[kb_ptr[n] .. kb_ptr[n+1]); NULL = dense
   int nM, nN, nslices, kb_per_slice;
@@ -170,7 +173,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t phase = 0;
       uint32_t filled = 0, filled_par = 0;  // per stage: loaded at least once, its parity
       bool ok = true;
-      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      // p.stall (failure-detection test): no load is issued, so the MMA issuer's and the
+      // epilogue's bounded waits run out and the CTA records the timeout
+      for (int t = blockIdx.x; t < total && ok && !p.stall; t += gridDim.x) {
         const TileWork w = tile_work(p, t);
         const int* list = p.kb_ptr ? p.kb_idx + __ldg(p.kb_ptr + w.list) : nullptr;
         for (int s = w.s0; s < w.s1; ++s) {
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           // which 32-column half; the load overlaps the wait
           const int b64 = list ? __ldg(list + (loc >> p.sub_shift)) : loc >> p.sub_shift;
           const int kx = b64 * TK + ((loc & ((1 << p.sub_shift) - 1)) << (6 - p.sub_shift));
-          if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, 1, WAIT_NS)) {
+          if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, 1, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         volatile int dummy = 0;
         for (int s = 0; s < STAGES; ++s)
           if ((filled >> s) & 1u)
-            mbar_wait_bounded(full_bar(s), (filled_par >> s) & 1u, &dummy, 1, WAIT_NS / 10);
+            mbar_wait_bounded(full_bar(s), (filled_par >> s) & 1u, &dummy, 1, p.wait_ns / 10);
       }
     }
     __syncwarp();
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int c0 = w.s0; c0 < w.s1 && ok; c0 += KB_PER_CHUNK, ++gc) {
           const int acc = gc & 1;
           const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
-          if (!mbar_wait_bounded(tempty_bar(acc), aph ^ 1u, abort_flag, 3, WAIT_NS)) {
+          if (!mbar_wait_bounded(tempty_bar(acc), aph ^ 1u, abort_flag, 3, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t d = tmem_base + static_cast<uint32_t>(acc * TN);
           const int c1 = min(w.s1, c0 + KB_PER_CHUNK);
           for (int s = c0; s < c1; ++s) {
-            if (!mbar_wait_bounded(full_bar(stage), phase, abort_flag, 2, WAIT_NS)) {
+            if (!mbar_wait_bounded(full_bar(stage), phase, abort_flag, 2, p.wait_ns)) {
               ok = false;
               break;
             }
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // all MMAs this thread issued must finish before TMEM is released
       mma_commit(drain_bar);
       volatile int dummy = 0;
-      mbar_wait_bounded(drain_bar, 0u, &dummy, 1, WAIT_NS);
+      mbar_wait_bounded(drain_bar, 0u, &dummy, 1, p.wait_ns);
     }
     __syncwarp();
   } else {
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int c0 = w.s0; c0 < w.s1; c0 += KB_PER_CHUNK, ++gc) {
         const int acc = gc & 1;
         const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
-        const bool got = mbar_wait_bounded(tfull_bar(acc), aph, abort_flag, 4, WAIT_NS);
+        const bool got = mbar_wait_bounded(tfull_bar(acc), aph, abort_flag, 4, p.wait_ns);
         if (!__all_sync(0xFFFFFFFFu, got)) {
           ok = false;
           break;
@@ -492,6 +497,8 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.tn = tn;
   p.sub_shift = tf32 ? 1 : 0;
   p.tf32 = tf32 ? 1 : 0;
+  p.stall = g.stall ? 1 : 0;
+  p.wait_ns = g.stall ? STALL_WAIT_NS : WAIT_NS;
   p.kb_per_seg = (g.Kd / TK) << p.sub_shift;
   p.nseg = split3 ? 3 : 1;
   p.kb_ptr = g.kb_ptr;

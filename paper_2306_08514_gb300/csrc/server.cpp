@@ -303,9 +303,9 @@ void builder_loop(Server* sv) {
         if (cudaMallocHost(&sl->h_frames, fb) != cudaSuccess ||
             cudaMallocHost(&sl->h_maps, mbytes) != cudaSuccess ||
             cudaMallocHost(&sl->h_arg, mb * 4) != cudaSuccess ||
-            cudaMalloc(&sl->d_frames, fb) != cudaSuccess ||
-            cudaMalloc(&sl->d_maps, mbytes) != cudaSuccess ||
-            cudaMalloc(&sl->d_arg, mb * 4) != cudaSuccess) {
+            device_alloc(reinterpret_cast<void**>(&sl->d_frames), fb) != cudaSuccess ||
+            device_alloc(reinterpret_cast<void**>(&sl->d_maps), mbytes) != cudaSuccess ||
+            device_alloc(reinterpret_cast<void**>(&sl->d_arg), mb * 4) != cudaSuccess) {
           cudaGetLastError();
           err = "slot allocation failed";
         }

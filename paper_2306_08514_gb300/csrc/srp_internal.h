@@ -16,6 +16,11 @@ namespace srp {
 
 constexpr int kHostPipe = 16;  // events of the srp_map_host copy pipeline
 
+// ------------------------------------------------------------------ device memory
+// cudaMalloc, except that the next n calls fail as if the device were out of memory after
+// srp_debug_fail_allocations(n) (failure-detection tests).
+cudaError_t device_alloc(void** ptr, size_t bytes);
+
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
 void clear_error();
@@ -169,6 +174,8 @@ struct TcGemm {
   int* err = nullptr;
   int variant = -1;   // TC_* kernel variant, -1: the heuristic's choice
   int max_ctas = 0;   // cap on the persistent grid (0: one CTA per SM)
+  bool stall = false; // failure-detection test: no operand load is issued, the bounded
+                      // waits (0.2 s) run out and *err records the timeout
 };
 // Kernel variants (tile width and shared-memory split) the autotuner chooses from.
 enum { TC_LONG_256 = 0,   // 128x256 tiles, 4 operand stages, 1 output box per epilogue warp
@@ -266,6 +273,7 @@ struct srp_plan_s {
   void* d_A2_lo = nullptr;
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
   bool use_front_conv = false;  // conv / LR operand from the fused front kernel
+  bool stall_next = false;  // srp_debug_stall_next_contraction
   uint4* d_stab = nullptr;  // fused front end: the sampling operand (front_sampling_table)
   uint4* d_ftab = nullptr;  // fused front end, SLRI: Lambda_fat (front_fat_table)
   // staging for srp_map_host, and its copy pipeline (two D2H streams and one H2D stream;

@@ -98,3 +98,14 @@ def test_plan_estimate_needs_no_gpu(S):
     assert abs(est["tf32"] - conv32) < 0.02 * conv32
     assert abs(est["bf16x3"] - 2 * conv16) < 0.02 * conv32 and est["bf16x3"] == est["fp16x3"]
     assert abs(est["tf32x3"] - 2 * conv32) < 0.02 * conv32
+
+
+def test_allocation_failure_hook_checks_its_arguments(S):
+    """srp_debug_fail_allocations is host bookkeeping (no GPU): negative counts are refused,
+    and n = 0 clears the injection."""
+    for after, n in ((-1, 1), (0, -1)):
+        with pytest.raises(S.SrpError) as e:
+            S.srp_debug_fail_allocations(after, n)
+        assert e.value.status == S.SRP_EINVAL
+    S.srp_debug_fail_allocations(3, 2)
+    S.srp_debug_fail_allocations(0, 0)
