@@ -305,6 +305,24 @@ srp_status srp_plan_stage_ms(srp_plan_t plan, float* ms, int* calls);
 srp_status srp_plan_status(srp_plan_t plan, void* stream);
 
 /*
+ * srp_plan_save / srp_plan_create_from_file -- checkpoint and resume a plan's offline fit
+ * (the paper computes the interpolation factors "upfront", Sec. IV; with long sample
+ * vectors the FP64 fit dominates plan creation).  srp_plan_save writes the method's fit to
+ * `path`: SLRI sigma, Lambda_tall [J][Rp] and Lambda_fat [Rp][L] (FP32, as the plan uses
+ * them), the SSPI taps (CSR), or LR-SRP's sigma and complex FP64 factors; other methods
+ * have no fit and write the header only.  The file carries a hash of the inputs the fit
+ * depends on (microphones, grid, fs, N, c, n_aux, method, rank or taps, far_field) and a
+ * checksum.  srp_plan_create_from_file is srp_plan_create with the fit read from `path`
+ * instead of computed; the precision, window and max_frames may differ from the saved
+ * plan's.  Errors: SRP_EINVAL (NULL arguments, unreadable or damaged file, a file made for
+ * other inputs or another method), then as srp_plan_create.  The file format is
+ * little-endian and versioned.
+ */
+srp_status srp_plan_save(srp_plan_t plan, const char* path);
+srp_status srp_plan_create_from_file(const srp_plan_desc* desc, const char* path, void* stream,
+                                     srp_plan_t* out);
+
+/*
  * Failure-detection test hooks.  They make a failure on the host side of a call, never a
  * device fault, trap or unbounded wait.
  *

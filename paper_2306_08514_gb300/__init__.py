@@ -10,6 +10,7 @@ from ._abi import (  # noqa: F401
     srp_map_host, srp_gcc_samples, srp_plan_sspi_taps, srp_plan_slri_sigma,
     srp_plan_set_profiling, srp_plan_stage_ms, srp_plan_status, srp_slri_apply_static,
     srp_plan_estimate_bytes, srp_server_now, srp_destroy, srp_last_error, srp_debug_fail_allocations,
+    srp_plan_save, srp_plan_create_from_file,
     make_desc, lib, SIGNATURES, LIB_PATH,
     SRP_OK, SRP_EINVAL, SRP_ENOMEM, SRP_ECUDA, SRP_ETIMEOUT, SRP_EUNSUPPORTED, SRP_EAGAIN,
     SRP_CONV, SRP_SLRI, SRP_SSPI, SRP_SI, SRP_TD, SRP_LR, SRP_FP32, SRP_BF16, SRP_FP16, SRP_FP16X3,

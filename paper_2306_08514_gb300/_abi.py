@@ -85,6 +85,9 @@ SIGNATURES = {
     "srp_plan_stage_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
     "srp_plan_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "srp_debug_fail_allocations": (C.c_int, [C.c_int, C.c_int]),
+    "srp_plan_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "srp_plan_create_from_file": (C.c_int, [C.POINTER(srp_plan_desc), C.c_char_p, C.c_void_p,
+                                            C.POINTER(C.c_void_p)]),
     "srp_debug_stall_next_contraction": (C.c_int, [C.c_void_p]),
     "srp_slri_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                         C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -148,6 +151,17 @@ def srp_plan_create(desc: srp_plan_desc, stream=None) -> C.c_void_p:
     h = C.c_void_p()
     _check(lib().srp_plan_create(C.byref(desc), stream, C.byref(h)))
     return h
+
+
+def srp_plan_create_from_file(desc: srp_plan_desc, path, stream=None) -> C.c_void_p:
+    """srp_plan_create with the method's fit read from a file written by srp_plan_save."""
+    h = C.c_void_p()
+    _check(lib().srp_plan_create_from_file(C.byref(desc), os.fsencode(path), stream, C.byref(h)))
+    return h
+
+
+def srp_plan_save(plan, path) -> None:
+    _check(lib().srp_plan_save(plan, os.fsencode(path)))
 
 
 def srp_plan_info(plan) -> srp_plan_info_t:
@@ -263,10 +277,14 @@ class Plan:
 
     def __init__(self, mic_xyz, grid_xyz, fs, N, method="conv", rank=0, taps=0.0,
                  precision="fp32", window="hann", c=340.0, n_aux=2, max_frames=256,
-                 stream=None, far_field=False, h_on_the_fly=0):
+                 stream=None, far_field=False, h_on_the_fly=0, plan_file=None):
+        """plan_file: create from a file written by save() (the fit is read, not computed)."""
         self.desc = make_desc(mic_xyz, grid_xyz, fs, N, method, rank, taps, precision, window,
                               c, n_aux, max_frames, far_field, h_on_the_fly)
-        self.handle = srp_plan_create(self.desc, _stream_handle(stream))
+        if plan_file is None:
+            self.handle = srp_plan_create(self.desc, _stream_handle(stream))
+        else:
+            self.handle = srp_plan_create_from_file(self.desc, plan_file, _stream_handle(stream))
         self.info = srp_plan_info(self.handle)
         self.M, self.J, self.N, self.L, self.P = (self.info.M, self.info.J, self.info.N,
                                                   self.info.L, self.info.P)
@@ -351,6 +369,10 @@ class Plan:
 
     def status(self, stream=None):
         srp_plan_status(self.handle, _stream_handle(stream))
+
+    def save(self, path):
+        """srp_plan_save: write the plan's fit (checkpoint) to path."""
+        srp_plan_save(self.handle, path)
 
     def debug_stall_next_contraction(self):
         """Failure-detection test hook: the next tensor-core contraction's bounded waits run

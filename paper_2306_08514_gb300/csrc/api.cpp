@@ -343,7 +343,9 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
 
 using namespace srp;
 
-extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out) {
+// Plan creation; `fit` (from a saved plan) replaces the method's FP64 fit when given.
+static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_t* out,
+                              const FitData* fit) {
   clear_error();
   if (!out) return fail(SRP_EINVAL, "out is NULL");
   *out = nullptr;
@@ -516,7 +518,14 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
     const size_t eb = op_bytes(p->op);
     const bool split = op_split(p->op);
     std::vector<std::complex<double>> ht, hf;
-    srp_status fst = fit_lr_device(g, R, ht, hf, p->sigma, s);
+    srp_status fst = SRP_OK;
+    if (fit) {
+      ht = fit->ht;
+      hf = fit->hf;
+      p->sigma = fit->sigma;
+    } else {
+      fst = fit_lr_device(g, R, ht, hf, p->sigma, s);
+    }
     if (fst != SRP_OK) {
       free_plan(p);
       return fst;
@@ -576,6 +585,8 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       free_plan(p);
       return SRP_ECUDA;
     }
+    p->lr_tall = std::move(ht);  // kept for srp_plan_save
+    p->lr_fat = std::move(hf);
     SRP_ALLOC(p, p->d_A, F * Kd * eb);
     if (split) SRP_ALLOC(p, p->d_A_lo, F * Kd * eb);
     SRP_ALLOC(p, p->d_U, sizeof(float) * F * 2 * R);
@@ -599,8 +610,15 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
       std::vector<float> tall, fat;
       // exact Gram eigen-decomposition for short sample vectors, device subspace
       // iteration beyond (the L x L Jacobi solve grows as L^3)
-      srp_status fst = g.L <= kGramMaxL ? fit_low_rank(g, p->R, tall, fat, p->sigma)
-                                        : fit_low_rank_device(g, p->R, tall, fat, p->sigma, s);
+      srp_status fst = SRP_OK;
+      if (fit) {
+        tall = fit->tall;
+        fat = fit->fat;
+        p->sigma = fit->sigma;
+      } else {
+        fst = g.L <= kGramMaxL ? fit_low_rank(g, p->R, tall, fat, p->sigma)
+                               : fit_low_rank_device(g, p->R, tall, fat, p->sigma, s);
+      }
       if (fst != SRP_OK) {
         free_plan(p);
         return fst;
@@ -670,7 +688,16 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
         }
       };
       if (desc->method == SRP_SSPI) {
-        srp_status fst = fit_sparse(g, p->nnz, p->h_row_ptr, p->h_col, p->h_val, p->tied);
+        srp_status fst = SRP_OK;
+        if (fit) {
+          p->nnz = fit->nnz;
+          p->tied = fit->tied;
+          p->h_row_ptr = fit->row_ptr;
+          p->h_col = fit->col;
+          p->h_val = fit->val;
+        } else {
+          fst = fit_sparse(g, p->nnz, p->h_row_ptr, p->h_col, p->h_val, p->tied);
+        }
         if (fst != SRP_OK) {
           free_plan(p);
           return fst;
@@ -771,6 +798,212 @@ extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, s
   p->fit_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
   return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_create(const srp_plan_desc* desc, void* stream, srp_plan_t* out) {
+  return create_plan(desc, stream, out, nullptr);
+}
+
+// ------------------------------------------------------------------ plan files
+// Little-endian binary: magic, version, method, the hash of the inputs the fit depends on,
+// sizes, the fit (SLRI: sigma, Lambda_tall [J][Rp], Lambda_fat [Rp][L] in FP32; SSPI: the
+// CSR taps; LR-SRP: sigma and the complex FP64 factors), and an FNV-1a checksum of the
+// preceding bytes.
+namespace {
+constexpr char kPlanMagic[8] = {'S', 'R', 'P', 'P', 'L', 'A', 'N', '\0'};
+constexpr uint32_t kPlanVersion = 1;
+
+struct Fnv {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* d, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(d);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  }
+  template <typename T>
+  void val(const T& v) { add(&v, sizeof(T)); }
+};
+
+// hash of everything the method's fit depends on (not the precision, window or batch size)
+uint64_t fit_inputs_hash(const srp_plan_desc& d) {
+  Fnv f;
+  f.val(d.M);
+  f.add(d.mic_xyz, sizeof(double) * 3 * d.M);
+  f.val(d.J);
+  f.add(d.grid_xyz, sizeof(double) * 3 * static_cast<size_t>(d.J));
+  f.val(d.fs);
+  f.val(d.N);
+  f.val(d.c);
+  f.val(d.n_aux);
+  f.val(static_cast<int>(d.method));
+  f.val(d.method == SRP_SLRI || d.method == SRP_LR ? d.rank : 0);
+  f.val(d.method == SRP_SSPI ? d.taps_per_loc_pair : 0.0);
+  f.val(d.far_field);
+  return f.h;
+}
+
+struct Writer {
+  std::FILE* fp;
+  Fnv sum;
+  bool ok = true;
+  void add(const void* d, size_t n) {
+    if (n == 0) return;
+    ok = ok && std::fwrite(d, 1, n, fp) == n;
+    sum.add(d, n);
+  }
+  template <typename T>
+  void val(const T& v) { add(&v, sizeof(T)); }
+  template <typename T>
+  void vec(const std::vector<T>& v) {
+    const uint64_t n = v.size();
+    val(n);
+    add(v.data(), sizeof(T) * v.size());
+  }
+};
+
+struct Reader {
+  std::vector<unsigned char> buf;
+  size_t pos = 0;
+  bool ok = true;
+  void get(void* d, size_t n) {
+    if (!ok || buf.size() - pos < n) {
+      ok = false;
+      return;
+    }
+    std::memcpy(d, buf.data() + pos, n);
+    pos += n;
+  }
+  template <typename T>
+  T val() {
+    T v{};
+    get(&v, sizeof(T));
+    return v;
+  }
+  template <typename T>
+  void vec(std::vector<T>& v, uint64_t expect) {
+    const uint64_t n = val<uint64_t>();
+    if (!ok || n != expect || n > (buf.size() - pos) / sizeof(T)) {
+      ok = false;
+      return;
+    }
+    v.resize(n);
+    get(v.data(), sizeof(T) * n);
+  }
+};
+}  // namespace
+
+extern "C" srp_status srp_plan_save(srp_plan_t plan, const char* path) {
+  clear_error();
+  if (!plan || !path) return fail(SRP_EINVAL, "plan or path is NULL");
+  const Geometry& g = plan->g;
+  const int method = plan->desc.method;
+  FitData fit;
+  if (method == SRP_SLRI) {
+    const int Rp = (plan->R + 7) / 8 * 8;
+    fit.tall.resize(static_cast<size_t>(g.J) * Rp);
+    fit.fat.resize(static_cast<size_t>(Rp) * g.L);
+    SRP_CUDA_TRY(cudaMemcpy(fit.tall.data(), plan->d_tall, sizeof(float) * fit.tall.size(),
+                            cudaMemcpyDeviceToHost));
+    SRP_CUDA_TRY(cudaMemcpy(fit.fat.data(), plan->d_fat, sizeof(float) * fit.fat.size(),
+                            cudaMemcpyDeviceToHost));
+  }
+  std::FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(SRP_EINVAL, std::string("cannot open ") + path + " for writing");
+  Writer w{fp};
+  w.add(kPlanMagic, sizeof(kPlanMagic));
+  w.val(kPlanVersion);
+  w.val(static_cast<int32_t>(method));
+  w.val(fit_inputs_hash(plan->desc));
+  w.val(static_cast<int32_t>(g.J));
+  w.val(static_cast<int32_t>(g.P));
+  w.val(static_cast<int32_t>(g.L));
+  w.val(static_cast<int32_t>(plan->R));
+  if (method == SRP_SLRI || method == SRP_LR) w.vec(plan->sigma);
+  if (method == SRP_SLRI) {
+    w.vec(fit.tall);
+    w.vec(fit.fat);
+  } else if (method == SRP_SSPI) {
+    w.val(static_cast<int64_t>(plan->nnz));
+    w.val(static_cast<int64_t>(plan->tied));
+    w.vec(plan->h_row_ptr);
+    w.vec(plan->h_col);
+    w.vec(plan->h_val);
+  } else if (method == SRP_LR) {
+    w.vec(plan->lr_tall);
+    w.vec(plan->lr_fat);
+  }
+  const uint64_t sum = w.sum.h;
+  w.val(sum);
+  const bool ok = w.ok && std::fclose(fp) == 0;
+  if (!ok) return fail(SRP_EINVAL, std::string("writing ") + path + " failed");
+  return SRP_OK;
+}
+
+extern "C" srp_status srp_plan_create_from_file(const srp_plan_desc* desc, const char* path,
+                                                void* stream, srp_plan_t* out) {
+  clear_error();
+  if (!out) return fail(SRP_EINVAL, "out is NULL");
+  *out = nullptr;
+  srp_status st = validate(desc);
+  if (st != SRP_OK) return st;
+  if (!path) return fail(SRP_EINVAL, "path is NULL");
+  Reader r;
+  {
+    std::FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(SRP_EINVAL, std::string("cannot open ") + path);
+    unsigned char chunk[1 << 16];
+    size_t n;
+    while ((n = std::fread(chunk, 1, sizeof(chunk), fp)) > 0) r.buf.insert(r.buf.end(), chunk, chunk + n);
+    std::fclose(fp);
+  }
+  if (r.buf.size() < sizeof(kPlanMagic) + 8 || std::memcmp(r.buf.data(), kPlanMagic, sizeof(kPlanMagic)) != 0)
+    return fail(SRP_EINVAL, std::string(path) + " is not a libsrp plan file");
+  {
+    Fnv f;
+    f.add(r.buf.data(), r.buf.size() - 8);
+    uint64_t stored;
+    std::memcpy(&stored, r.buf.data() + r.buf.size() - 8, 8);
+    if (stored != f.h) return fail(SRP_EINVAL, std::string(path) + ": checksum mismatch (damaged file)");
+    r.buf.resize(r.buf.size() - 8);
+  }
+  r.pos = sizeof(kPlanMagic);
+  if (r.val<uint32_t>() != kPlanVersion) return fail(SRP_EINVAL, "unsupported plan file version");
+  const int method = r.val<int32_t>();
+  if (method != desc->method) return fail(SRP_EINVAL, "the plan file holds another method");
+  if (r.val<uint64_t>() != fit_inputs_hash(*desc))
+    return fail(SRP_EINVAL, "the plan file was made for other inputs (geometry, fs, N, c, "
+                            "n_aux, rank, taps or far field differ)");
+  Geometry g;
+  st = build_geometry(*desc, g);
+  if (st != SRP_OK) return st;
+  const int J = r.val<int32_t>(), P = r.val<int32_t>(), L = r.val<int32_t>(), R = r.val<int32_t>();
+  if (!r.ok || J != g.J || P != g.P || L != g.L) return fail(SRP_EINVAL, "plan file sizes do not match");
+  FitData fit;
+  const int Rp = (R + 7) / 8 * 8;
+  if (method == SRP_SLRI || method == SRP_LR) {
+    const uint64_t ns = r.val<uint64_t>();
+    r.pos -= sizeof(uint64_t);
+    r.vec(fit.sigma, ns);
+  }
+  if (method == SRP_SLRI) {
+    r.vec(fit.tall, static_cast<uint64_t>(J) * Rp);
+    r.vec(fit.fat, static_cast<uint64_t>(Rp) * L);
+  } else if (method == SRP_SSPI) {
+    fit.nnz = r.val<int64_t>();
+    fit.tied = r.val<int64_t>();
+    r.vec(fit.row_ptr, static_cast<uint64_t>(J) + 1);
+    r.vec(fit.col, static_cast<uint64_t>(fit.nnz));
+    r.vec(fit.val, static_cast<uint64_t>(fit.nnz));
+    if (r.ok && (fit.row_ptr.front() != 0 || fit.row_ptr.back() != fit.nnz)) r.ok = false;
+  } else if (method == SRP_LR) {
+    const int D = P * (g.K - 1);
+    r.vec(fit.ht, static_cast<uint64_t>(J) * R);
+    r.vec(fit.hf, static_cast<uint64_t>(R) * D);
+  }
+  if (!r.ok || r.pos != r.buf.size()) return fail(SRP_EINVAL, "plan file contents do not match its header");
+  return create_plan(desc, stream, out, &fit);
 }
 
 extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t* bytes) {

@@ -16,6 +16,17 @@ namespace srp {
 
 constexpr int kHostPipe = 16;  // events of the srp_map_host copy pipeline
 
+// A method's fit as a saved plan holds it (srp_plan_save / srp_plan_create_from_file).
+struct FitData {
+  std::vector<double> sigma;                             // SLRI, LR-SRP
+  std::vector<float> tall, fat;                          // SLRI: [J][Rp], [Rp][L]
+  long long nnz = 0, tied = 0;                           // SSPI
+  std::vector<long long> row_ptr;
+  std::vector<int> col;
+  std::vector<float> val;
+  std::vector<std::complex<double>> ht, hf;              // LR-SRP: [J][R], [R][P(K-1)]
+};
+
 // ------------------------------------------------------------------ device memory
 // cudaMalloc, except that the next n calls fail as if the device were out of memory after
 // srp_debug_fail_allocations(n) (failure-detection tests).
@@ -239,6 +250,7 @@ struct srp_plan_s {
   bool fat_gemm = false;   // SLRI with long sample vectors: u = Lambda_fat xi as a GEMM
   bool h_generated = false;  // conv FP32: SRP matrix generated inside the GEMM, not stored
   std::vector<double> sigma;
+  std::vector<std::complex<double>> lr_tall, lr_fat;  // LR-SRP factors kept for srp_plan_save
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
   std::vector<int> h_col;
   std::vector<float> h_val;

@@ -109,3 +109,37 @@ def test_allocation_failure_hook_checks_its_arguments(S):
         assert e.value.status == S.SRP_EINVAL
     S.srp_debug_fail_allocations(3, 2)
     S.srp_debug_fail_allocations(0, 0)
+
+
+def _fnv1a64(b):
+    h = 1469598103934665603
+    for x in b:
+        h = ((h ^ x) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_plan_file_is_checked_before_any_gpu_work(S, tmp_path):
+    """srp_plan_create_from_file refuses a missing file, a foreign file, a damaged file and a
+    well-formed file made for other inputs, on the host (no GPU is touched)."""
+    import struct
+    mics = synth.mics_square()
+    grid = synth.grid_plane((0, 0), (4, 4), (10, 10))
+    desc = S.make_desc(mics, grid, 16000.0, 512, method="slri", rank=4)
+
+    def refused(path, what):
+        with pytest.raises(S.SrpError) as e:
+            S.srp_plan_create_from_file(desc, path)
+        assert e.value.status == S.SRP_EINVAL and what in str(e.value), str(e.value)
+
+    refused(tmp_path / "missing.plan", "cannot open")
+    foreign = tmp_path / "foreign.plan"
+    foreign.write_bytes(b"not a plan file at all")
+    refused(foreign, "not a libsrp plan file")
+    body = b"SRPPLAN\0" + struct.pack("<Iiq", 1, 1, 12345) + struct.pack("<iiii", 100, 6, 0, 4)
+    good_sum = body + struct.pack("<Q", _fnv1a64(body))
+    other = tmp_path / "other.plan"
+    other.write_bytes(good_sum)
+    refused(other, "other inputs")
+    damaged = tmp_path / "damaged.plan"
+    damaged.write_bytes(good_sum[:-1] + bytes([good_sum[-1] ^ 1]))
+    refused(damaged, "checksum")
