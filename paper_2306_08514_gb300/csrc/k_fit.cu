@@ -135,19 +135,27 @@ __global__ void sin_pi_kernel(const double* __restrict__ tau, size_t n, double* 
 
 // Modified Gram-Schmidt, twice, on the columns of A (rows x cols, row-major).
 void orthonormalise(std::vector<double>& A, int rows, int cols) {
+  // on the transpose, so that every dot product and update runs over contiguous memory
+  std::vector<double> T(A.size());
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) T[static_cast<size_t>(c) * rows + r] = A[static_cast<size_t>(r) * cols + c];
   for (int pass = 0; pass < 2; ++pass)
     for (int c = 0; c < cols; ++c) {
+      double* tc = T.data() + static_cast<size_t>(c) * rows;
       for (int b = 0; b < c; ++b) {
+        const double* tb = T.data() + static_cast<size_t>(b) * rows;
         double d = 0.0;
-        for (int r = 0; r < rows; ++r) d += A[static_cast<size_t>(r) * cols + b] * A[static_cast<size_t>(r) * cols + c];
-        for (int r = 0; r < rows; ++r) A[static_cast<size_t>(r) * cols + c] -= d * A[static_cast<size_t>(r) * cols + b];
+        for (int r = 0; r < rows; ++r) d += tb[r] * tc[r];
+        for (int r = 0; r < rows; ++r) tc[r] -= d * tb[r];
       }
       double nn = 0.0;
-      for (int r = 0; r < rows; ++r) nn += A[static_cast<size_t>(r) * cols + c] * A[static_cast<size_t>(r) * cols + c];
+      for (int r = 0; r < rows; ++r) nn += tc[r] * tc[r];
       nn = std::sqrt(nn);
       const double inv = nn > 0 ? 1.0 / nn : 0.0;
-      for (int r = 0; r < rows; ++r) A[static_cast<size_t>(r) * cols + c] *= inv;
+      for (int r = 0; r < rows; ++r) tc[r] *= inv;
     }
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) A[static_cast<size_t>(r) * cols + c] = T[static_cast<size_t>(c) * rows + r];
 }
 
 struct DevBuf {
@@ -224,13 +232,16 @@ srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
   for (int it = 0; it < 300; ++it) {
     srp_status st = apply_G(Q, Z);
     if (st != SRP_OK) return st;
-    Tm.assign(static_cast<size_t>(k) * k, 0.0);  // T = Q^T Z, symmetrised
-    for (int a = 0; a < k; ++a)
-      for (int b = 0; b < k; ++b) {
-        double d = 0.0;
-        for (int l = 0; l < L; ++l) d += Q[static_cast<size_t>(l) * k + a] * Z[static_cast<size_t>(l) * k + b];
-        Tm[static_cast<size_t>(a) * k + b] = d;
+    Tm.assign(static_cast<size_t>(k) * k, 0.0);  // T = Q^T Z (summed row by row), symmetrised
+    for (int l = 0; l < L; ++l) {
+      const double* ql = Q.data() + static_cast<size_t>(l) * k;
+      const double* zl = Z.data() + static_cast<size_t>(l) * k;
+      for (int a = 0; a < k; ++a) {
+        const double qa = ql[a];
+        double* ta = Tm.data() + static_cast<size_t>(a) * k;
+        for (int b = 0; b < k; ++b) ta[b] += qa * zl[b];
       }
+    }
     for (int a = 0; a < k; ++a)
       for (int b = a + 1; b < k; ++b) {
         const double m = 0.5 * (Tm[static_cast<size_t>(a) * k + b] + Tm[static_cast<size_t>(b) * k + a]);
@@ -408,19 +419,26 @@ using cplx = std::complex<double>;
 
 // Modified Gram-Schmidt, twice, on the columns of a complex rows x cols matrix.
 void orthonormalise_c(std::vector<cplx>& A, int rows, int cols) {
+  std::vector<cplx> T(A.size());  // on the transpose (contiguous columns)
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) T[static_cast<size_t>(c) * rows + r] = A[static_cast<size_t>(r) * cols + c];
   for (int pass = 0; pass < 2; ++pass)
     for (int c = 0; c < cols; ++c) {
+      cplx* tc = T.data() + static_cast<size_t>(c) * rows;
       for (int b = 0; b < c; ++b) {
+        const cplx* tb = T.data() + static_cast<size_t>(b) * rows;
         cplx d = 0.0;
-        for (int r = 0; r < rows; ++r) d += std::conj(A[static_cast<size_t>(r) * cols + b]) * A[static_cast<size_t>(r) * cols + c];
-        for (int r = 0; r < rows; ++r) A[static_cast<size_t>(r) * cols + c] -= d * A[static_cast<size_t>(r) * cols + b];
+        for (int r = 0; r < rows; ++r) d += std::conj(tb[r]) * tc[r];
+        for (int r = 0; r < rows; ++r) tc[r] -= d * tb[r];
       }
       double nn = 0.0;
-      for (int r = 0; r < rows; ++r) nn += std::norm(A[static_cast<size_t>(r) * cols + c]);
+      for (int r = 0; r < rows; ++r) nn += std::norm(tc[r]);
       nn = std::sqrt(nn);
       const double inv = nn > 0 ? 1.0 / nn : 0.0;
-      for (int r = 0; r < rows; ++r) A[static_cast<size_t>(r) * cols + c] *= inv;
+      for (int r = 0; r < rows; ++r) tc[r] *= inv;
     }
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) A[static_cast<size_t>(r) * cols + c] = T[static_cast<size_t>(c) * rows + r];
 }
 
 // Eigen-decomposition of a k x k Hermitian T through the real symmetric 2k x 2k matrix
@@ -516,13 +534,16 @@ srp_status run_lr_fit(const Geometry& g, int R, int k, std::vector<cplx>& tall,
   for (int it = 0; it < 300; ++it) {
     srp_status st = apply_G(Q, Z);
     if (st != SRP_OK) return st;
-    T.assign(static_cast<size_t>(k) * k, 0.0);  // Q^H Z, Hermitian part
-    for (int a = 0; a < k; ++a)
-      for (int b = 0; b < k; ++b) {
-        cplx d = 0.0;
-        for (int l = 0; l < D; ++l) d += std::conj(Q[static_cast<size_t>(l) * k + a]) * Z[static_cast<size_t>(l) * k + b];
-        T[static_cast<size_t>(a) * k + b] = d;
+    T.assign(static_cast<size_t>(k) * k, 0.0);  // Q^H Z (summed row by row), Hermitian part
+    for (int l = 0; l < D; ++l) {
+      const cplx* ql = Q.data() + static_cast<size_t>(l) * k;
+      const cplx* zl = Z.data() + static_cast<size_t>(l) * k;
+      for (int a = 0; a < k; ++a) {
+        const cplx qa = std::conj(ql[a]);
+        cplx* ta = T.data() + static_cast<size_t>(a) * k;
+        for (int b = 0; b < k; ++b) ta[b] += qa * zl[b];
       }
+    }
     for (int a = 0; a < k; ++a)
       for (int b = a; b < k; ++b) {
         const cplx m = 0.5 * (T[static_cast<size_t>(a) * k + b] + std::conj(T[static_cast<size_t>(b) * k + a]));
@@ -582,19 +603,21 @@ srp_status fit_lr_device(const Geometry& g, int R, std::vector<std::complex<doub
                          std::vector<std::complex<double>>& fat, std::vector<double>& sigma,
                          cudaStream_t s) {
   const int D = g.P * (g.K - 1);
-  const int k = std::min(D, R + 32);
-  if (k <= 32) return run_lr_fit<32>(g, R, k, tall, fat, sigma, s);
-  if (k <= 64) return run_lr_fit<64>(g, R, k, tall, fat, sigma, s);
-  return run_lr_fit<96>(g, R, k, tall, fat, sigma, s);
+  const int want = R + 32;  // as fit_low_rank_device: the whole column bucket is used
+  if (want <= 32) return run_lr_fit<32>(g, R, std::min(D, 32), tall, fat, sigma, s);
+  if (want <= 64) return run_lr_fit<64>(g, R, std::min(D, 64), tall, fat, sigma, s);
+  return run_lr_fit<96>(g, R, std::min(D, 96), tall, fat, sigma, s);
 }
 
 srp_status fit_low_rank_device(const Geometry& g, int R, std::vector<float>& tall,
                                std::vector<float>& fat, std::vector<double>& sigma,
                                cudaStream_t s) {
-  const int k = std::min(g.L, R + 32);
-  if (k <= 32) return run_fit<32>(g, R, k, tall, fat, sigma, s);
-  if (k <= 64) return run_fit<64>(g, R, k, tall, fat, sigma, s);
-  return run_fit<96>(g, R, k, tall, fat, sigma, s);
+  // at least 32 guard columns, and every column of the kernel's bucket used (the padding
+  // would cost the same and the extra columns speed the convergence up)
+  const int want = R + 32;
+  if (want <= 32) return run_fit<32>(g, R, std::min(g.L, 32), tall, fat, sigma, s);
+  if (want <= 64) return run_fit<64>(g, R, std::min(g.L, 64), tall, fat, sigma, s);
+  return run_fit<96>(g, R, std::min(g.L, 96), tall, fat, sigma, s);
 }
 
 }  // namespace srp
