@@ -12,6 +12,8 @@
 // eigenproblem run on the host in FP64.
 #include "srp_internal.h"
 
+#include <mutex>
+
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -31,41 +33,56 @@ __device__ __forceinline__ double lam_entry(double tau, double s, int n) {
   return ((n & 1) ? -s : s) / (M_PI * x);
 }
 
+// The entry in the product's type: FP64 as above, or FP32 from the FP64 difference tau - n
+// (the early iterations of the subspace iteration run in FP32, see run_fit).
+template <typename T>
+__device__ __forceinline__ T lam_entry_t(double tau, double s, int n);
+template <>
+__device__ __forceinline__ double lam_entry_t<double>(double tau, double s, int n) {
+  return lam_entry(tau, s, n);
+}
+template <>
+__device__ __forceinline__ float lam_entry_t<float>(double tau, double s, int n) {
+  const double x = tau - static_cast<double>(n);
+  if (x == 0.0) return 1.f;
+  return static_cast<float>((n & 1) ? -s : s) / (3.14159265358979323846f * static_cast<float>(x));
+}
+
 // Y[i][c] = sum_l Lambda[i][l] X[l][c], rows i of this block, c < KT.
-template <int KT>
+template <typename T, int KT>
 __global__ __launch_bounds__(256) void lam_apply_kernel(const double* __restrict__ tau,
                                                         const double* __restrict__ stau, int J,
                                                         int P, const int* __restrict__ col_pair,
                                                         const int* __restrict__ col_lag, int L,
-                                                        const double* __restrict__ X,
-                                                        double* __restrict__ Y) {
-  __shared__ double lam[ROWS][COLS + 1];
-  __shared__ double xs[COLS][KT];
+                                                        const T* __restrict__ X,
+                                                        T* __restrict__ Y) {
+  __shared__ T lam[ROWS][COLS + 1];
+  __shared__ T xs[COLS][KT];
   const int t = threadIdx.x;
   const int i0 = blockIdx.x * ROWS;
   const int r = t >> 2, cq = t & 3;
-  double acc[KT / 4];
+  T acc[KT / 4];
 #pragma unroll
-  for (int j = 0; j < KT / 4; ++j) acc[j] = 0.0;
+  for (int j = 0; j < KT / 4; ++j) acc[j] = T(0);
   for (int l0 = 0; l0 < L; l0 += COLS) {
     for (int e = t; e < ROWS * COLS; e += 256) {
       const int rr = e / COLS, ll = e % COLS;
       const int i = i0 + rr, l = l0 + ll;
-      double v = 0.0;
+      T v = T(0);
       if (i < J && l < L) {
         const size_t ip = static_cast<size_t>(i) * P + col_pair[l];
-        v = lam_entry(tau[ip], stau[ip], col_lag[l]);
+        v = lam_entry_t<T>(tau[ip], stau[ip], col_lag[l]);
       }
       lam[rr][ll] = v;
     }
     for (int e = t; e < COLS * KT; e += 256) {
       const int ll = e / KT, c = e % KT;
-      xs[ll][c] = (l0 + ll < L) ? X[static_cast<size_t>(l0 + ll) * KT + c] : 0.0;
+      xs[ll][c] = (l0 + ll < L) ? X[static_cast<size_t>(l0 + ll) * KT + c] : T(0);
     }
     __syncthreads();
 #pragma unroll 4
     for (int ll = 0; ll < COLS; ++ll) {
-      const double a = lam[r][ll];
+      const T a = lam[r][ll];
 #pragma unroll
       for (int j = 0; j < KT / 4; ++j) acc[j] = fma(a, xs[ll][cq + 4 * j], acc[j]);
     }
@@ -78,43 +95,43 @@ __global__ __launch_bounds__(256) void lam_apply_kernel(const double* __restrict
 }
 
 // Zpart[s][l][c] = sum_{i in split s} Lambda[i][l] Y[i][c], columns l of this block.
-template <int KT>
+template <typename T, int KT>
 __global__ __launch_bounds__(256) void lam_t_apply_kernel(const double* __restrict__ tau,
                                                           const double* __restrict__ stau, int J,
                                                           int P, const int* __restrict__ col_pair,
                                                           const int* __restrict__ col_lag, int L,
-                                                          const double* __restrict__ Y,
+                                                          const T* __restrict__ Y,
                                                           int rows_per_split,
-                                                          double* __restrict__ Zpart) {
-  __shared__ double lam[ROWS_T][COLS + 1];
-  __shared__ double ys[ROWS_T][KT];
+                                                          T* __restrict__ Zpart) {
+  __shared__ T lam[ROWS_T][COLS + 1];
+  __shared__ T ys[ROWS_T][KT];
   const int t = threadIdx.x;
   const int l0 = blockIdx.x * COLS;
   const int ib = blockIdx.y * rows_per_split;
   const int ie = min(J, ib + rows_per_split);
   const int lc = t >> 3, cq = t & 7;
-  double acc[KT / 8];
+  T acc[KT / 8];
 #pragma unroll
-  for (int j = 0; j < KT / 8; ++j) acc[j] = 0.0;
+  for (int j = 0; j < KT / 8; ++j) acc[j] = T(0);
   for (int i0 = ib; i0 < ie; i0 += ROWS_T) {
     for (int e = t; e < ROWS_T * COLS; e += 256) {
       const int rr = e / COLS, ll = e % COLS;
       const int i = i0 + rr, l = l0 + ll;
-      double v = 0.0;
+      T v = T(0);
       if (i < ie && l < L) {
         const size_t ip = static_cast<size_t>(i) * P + col_pair[l];
-        v = lam_entry(tau[ip], stau[ip], col_lag[l]);
+        v = lam_entry_t<T>(tau[ip], stau[ip], col_lag[l]);
       }
       lam[rr][ll] = v;
     }
     for (int e = t; e < ROWS_T * KT; e += 256) {
       const int rr = e / KT, c = e % KT;
-      ys[rr][c] = (i0 + rr < ie) ? Y[static_cast<size_t>(i0 + rr) * KT + c] : 0.0;
+      ys[rr][c] = (i0 + rr < ie) ? Y[static_cast<size_t>(i0 + rr) * KT + c] : T(0);
     }
     __syncthreads();
 #pragma unroll 4
     for (int rr = 0; rr < ROWS_T; ++rr) {
-      const double a = lam[rr][lc];
+      const T a = lam[rr][lc];
 #pragma unroll
       for (int j = 0; j < KT / 8; ++j) acc[j] = fma(a, ys[rr][cq + 8 * j], acc[j]);
     }
@@ -195,29 +212,52 @@ srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
   sin_pi_kernel<<<1024, 256, 0, s>>>(tau, JP, stau);
   SRP_CUDA_TRY(cudaGetLastError());
 
-  // Y = Lambda X (host X [L][k] -> host Y [J][KT]) and Z = Lambda^T Y
-  std::vector<double> Xh(static_cast<size_t>(L) * KT), Zh(static_cast<size_t>(L) * KT);
+  // Z = Lambda^T Lambda Q on the device: Y = Lambda X, then Z = Lambda^T Y in row splits
+  // summed on the host in FP64.  fp32: the products in FP32 (entries, operands and sums).
   std::vector<double> Zp(static_cast<size_t>(nsplit) * L * KT);
-  auto apply_G = [&](const std::vector<double>& Q, std::vector<double>& Zout) -> srp_status {
-    for (int l = 0; l < L; ++l)
-      for (int c = 0; c < KT; ++c) Xh[static_cast<size_t>(l) * KT + c] = c < k ? Q[static_cast<size_t>(l) * k + c] : 0.0;
-    SRP_CUDA_TRY(cudaMemcpyAsync(d_X.p, Xh.data(), sizeof(double) * L * KT, cudaMemcpyHostToDevice, s));
-    lam_apply_kernel<KT><<<(J + ROWS - 1) / ROWS, 256, 0, s>>>(tau, stau, J, P, cols, cols + L, L,
-                                                               static_cast<double*>(d_X.p),
-                                                               static_cast<double*>(d_Y.p));
-    SRP_CUDA_TRY(cudaGetLastError());
-    dim3 grid((L + COLS - 1) / COLS, nsplit);
-    lam_t_apply_kernel<KT><<<grid, 256, 0, s>>>(tau, stau, J, P, cols, cols + L, L,
-                                                static_cast<double*>(d_Y.p), rows_per_split,
-                                                static_cast<double*>(d_Z.p));
-    SRP_CUDA_TRY(cudaGetLastError());
-    SRP_CUDA_TRY(cudaMemcpyAsync(Zp.data(), d_Z.p, sizeof(double) * Zp.size(), cudaMemcpyDeviceToHost, s));
-    SRP_CUDA_TRY(cudaStreamSynchronize(s));
-    Zout.assign(static_cast<size_t>(L) * k, 0.0);
-    for (int sp = 0; sp < nsplit; ++sp)
+  std::vector<float> Zpf;
+  auto apply_G = [&](const std::vector<double>& Q, std::vector<double>& Zout, bool fp32) -> srp_status {
+    const size_t n = static_cast<size_t>(L) * KT;
+    if (fp32) {
+      std::vector<float> Xf(n, 0.f);
       for (int l = 0; l < L; ++l)
-        for (int c = 0; c < k; ++c)
-          Zout[static_cast<size_t>(l) * k + c] += Zp[(static_cast<size_t>(sp) * L + l) * KT + c];
+        for (int c = 0; c < k; ++c) Xf[static_cast<size_t>(l) * KT + c] = static_cast<float>(Q[static_cast<size_t>(l) * k + c]);
+      SRP_CUDA_TRY(cudaMemcpyAsync(d_X.p, Xf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+      lam_apply_kernel<float, KT><<<(J + ROWS - 1) / ROWS, 256, 0, s>>>(
+          tau, stau, J, P, cols, cols + L, L, static_cast<float*>(d_X.p), static_cast<float*>(d_Y.p));
+      SRP_CUDA_TRY(cudaGetLastError());
+      dim3 grid((L + COLS - 1) / COLS, nsplit);
+      lam_t_apply_kernel<float, KT><<<grid, 256, 0, s>>>(tau, stau, J, P, cols, cols + L, L,
+                                                         static_cast<float*>(d_Y.p), rows_per_split,
+                                                         static_cast<float*>(d_Z.p));
+      SRP_CUDA_TRY(cudaGetLastError());
+      Zpf.resize(Zp.size());
+      SRP_CUDA_TRY(cudaMemcpyAsync(Zpf.data(), d_Z.p, sizeof(float) * Zpf.size(), cudaMemcpyDeviceToHost, s));
+      SRP_CUDA_TRY(cudaStreamSynchronize(s));
+      for (size_t e = 0; e < Zp.size(); ++e) Zp[e] = Zpf[e];
+    } else {
+      std::vector<double> Xh(n, 0.0);
+      for (int l = 0; l < L; ++l)
+        for (int c = 0; c < k; ++c) Xh[static_cast<size_t>(l) * KT + c] = Q[static_cast<size_t>(l) * k + c];
+      SRP_CUDA_TRY(cudaMemcpyAsync(d_X.p, Xh.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      lam_apply_kernel<double, KT><<<(J + ROWS - 1) / ROWS, 256, 0, s>>>(
+          tau, stau, J, P, cols, cols + L, L, static_cast<double*>(d_X.p), static_cast<double*>(d_Y.p));
+      SRP_CUDA_TRY(cudaGetLastError());
+      dim3 grid((L + COLS - 1) / COLS, nsplit);
+      lam_t_apply_kernel<double, KT><<<grid, 256, 0, s>>>(tau, stau, J, P, cols, cols + L, L,
+                                                          static_cast<double*>(d_Y.p), rows_per_split,
+                                                          static_cast<double*>(d_Z.p));
+      SRP_CUDA_TRY(cudaGetLastError());
+      SRP_CUDA_TRY(cudaMemcpyAsync(Zp.data(), d_Z.p, sizeof(double) * Zp.size(), cudaMemcpyDeviceToHost, s));
+      SRP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    Zout.assign(static_cast<size_t>(L) * k, 0.0);
+    parallel_for(L, [&](long long b, long long e) {
+      for (int sp = 0; sp < nsplit; ++sp)
+        for (long long l = b; l < e; ++l)
+          for (int c = 0; c < k; ++c)
+            Zout[static_cast<size_t>(l) * k + c] += Zp[(static_cast<size_t>(sp) * L + l) * KT + c];
+    });
     return SRP_OK;
   };
 
@@ -229,18 +269,40 @@ srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
   std::vector<double> prev(R, 0.0);
   std::vector<int> order(k);
   bool converged = false;
-  for (int it = 0; it < 300; ++it) {
-    srp_status st = apply_G(Q, Z);
+  // Two phases: FP32 products until the Ritz values settle at FP32 accuracy (their relative
+  // change below 1e-6, or no longer shrinking), then FP64 products until they change by
+  // less than 1e-13.  The iteration corrects the earlier phase's rounding itself, so the
+  // result is that of the FP64 iteration; the FP32 products run ~60x faster on GB300.
+  bool fp32 = true;
+  int fp64_its = 0;
+  double best32 = 1e300;
+  int stale32 = 0;
+  for (int it = 0; it < 400; ++it) {
+    srp_status st = apply_G(Q, Z, fp32);
     if (st != SRP_OK) return st;
-    Tm.assign(static_cast<size_t>(k) * k, 0.0);  // T = Q^T Z (summed row by row), symmetrised
-    for (int l = 0; l < L; ++l) {
-      const double* ql = Q.data() + static_cast<size_t>(l) * k;
-      const double* zl = Z.data() + static_cast<size_t>(l) * k;
-      for (int a = 0; a < k; ++a) {
-        const double qa = ql[a];
-        double* ta = Tm.data() + static_cast<size_t>(a) * k;
-        for (int b = 0; b < k; ++b) ta[b] += qa * zl[b];
-      }
+    // T = Q^T Z, summed row by row in fixed chunks (deterministic), then symmetrised
+    Tm.assign(static_cast<size_t>(k) * k, 0.0);
+    {
+      std::mutex mu;
+      std::vector<std::pair<long long, std::vector<double>>> parts;
+      parallel_for(L, [&](long long b, long long e) {
+        std::vector<double> t(static_cast<size_t>(k) * k, 0.0);
+        for (long long l = b; l < e; ++l) {
+          const double* ql = Q.data() + static_cast<size_t>(l) * k;
+          const double* zl = Z.data() + static_cast<size_t>(l) * k;
+          for (int a = 0; a < k; ++a) {
+            const double qa = ql[a];
+            double* ta = t.data() + static_cast<size_t>(a) * k;
+            for (int c = 0; c < k; ++c) ta[c] += qa * zl[c];
+          }
+        }
+        std::lock_guard<std::mutex> lock(mu);
+        parts.emplace_back(b, std::move(t));
+      });
+      std::sort(parts.begin(), parts.end(),
+                [](const auto& x, const auto& y) { return x.first < y.first; });
+      for (const auto& pt : parts)
+        for (size_t e = 0; e < Tm.size(); ++e) Tm[e] += pt.second[e];
     }
     for (int a = 0; a < k; ++a)
       for (int b = a + 1; b < k; ++b) {
@@ -258,19 +320,29 @@ srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
     }
     // Ritz vectors of this Q and the next basis orth(Z W) (W sorted)
     std::vector<double> QW(static_cast<size_t>(L) * k, 0.0), ZW(static_cast<size_t>(L) * k, 0.0);
-    for (int l = 0; l < L; ++l)
-      for (int c = 0; c < k; ++c) {
-        double qa = 0.0, za = 0.0;
-        const int wc = order[c];
-        for (int a = 0; a < k; ++a) {
-          const double w = W[static_cast<size_t>(a) * k + wc];
-          qa += Q[static_cast<size_t>(l) * k + a] * w;
-          za += Z[static_cast<size_t>(l) * k + a] * w;
+    parallel_for(L, [&](long long b, long long e) {
+      for (long long l = b; l < e; ++l)
+        for (int c = 0; c < k; ++c) {
+          double qa = 0.0, za = 0.0;
+          const int wc = order[c];
+          for (int a = 0; a < k; ++a) {
+            const double w = W[static_cast<size_t>(a) * k + wc];
+            qa += Q[static_cast<size_t>(l) * k + a] * w;
+            za += Z[static_cast<size_t>(l) * k + a] * w;
+          }
+          QW[static_cast<size_t>(l) * k + c] = qa;
+          ZW[static_cast<size_t>(l) * k + c] = za;
         }
-        QW[static_cast<size_t>(l) * k + c] = qa;
-        ZW[static_cast<size_t>(l) * k + c] = za;
+    });
+    if (fp32) {
+      if (change < best32 * 0.5) {
+        best32 = change;
+        stale32 = 0;
+      } else {
+        ++stale32;
       }
-    if (it > 2 && change < 1e-13) {
+      if (it > 2 && (change < 1e-6 || stale32 >= 4)) fp32 = false;
+    } else if (++fp64_its > 2 && change < 1e-13) {
       Q.swap(QW);
       converged = true;
       break;
@@ -289,12 +361,13 @@ srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
   fat.assign(static_cast<size_t>(Rp) * L, 0.f);
   for (int r = 0; r < R; ++r)
     for (int l = 0; l < L; ++l) fat[static_cast<size_t>(r) * L + l] = static_cast<float>(Q[static_cast<size_t>(l) * k + r]);
+  std::vector<double> Xh(static_cast<size_t>(L) * KT, 0.0);
   for (int l = 0; l < L; ++l)
-    for (int c = 0; c < KT; ++c) Xh[static_cast<size_t>(l) * KT + c] = c < R ? Q[static_cast<size_t>(l) * k + c] : 0.0;
+    for (int c = 0; c < R; ++c) Xh[static_cast<size_t>(l) * KT + c] = Q[static_cast<size_t>(l) * k + c];
   SRP_CUDA_TRY(cudaMemcpyAsync(d_X.p, Xh.data(), sizeof(double) * L * KT, cudaMemcpyHostToDevice, s));
-  lam_apply_kernel<KT><<<(J + ROWS - 1) / ROWS, 256, 0, s>>>(tau, stau, J, P, cols, cols + L, L,
-                                                             static_cast<double*>(d_X.p),
-                                                             static_cast<double*>(d_Y.p));
+  lam_apply_kernel<double, KT><<<(J + ROWS - 1) / ROWS, 256, 0, s>>>(tau, stau, J, P, cols, cols + L, L,
+                                                                     static_cast<double*>(d_X.p),
+                                                                     static_cast<double*>(d_Y.p));
   SRP_CUDA_TRY(cudaGetLastError());
   std::vector<double> Yh(static_cast<size_t>(J) * KT);
   SRP_CUDA_TRY(cudaMemcpyAsync(Yh.data(), d_Y.p, sizeof(double) * Yh.size(), cudaMemcpyDeviceToHost, s));

@@ -18,7 +18,7 @@ unsigned host_threads() {
 }
 
 // Runs fn(begin, end) over [0, n) split into contiguous chunks, one per thread.
-static void parallel_for(long long n, const std::function<void(long long, long long)>& fn) {
+void parallel_for(long long n, const std::function<void(long long, long long)>& fn) {
   const unsigned T = host_threads();
   if (n <= 0) return;
   if (T <= 1 || n < 64) {

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include <complex>
+#include <functional>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -15,6 +16,10 @@
 namespace srp {
 
 constexpr int kHostPipe = 16;  // events of the srp_map_host copy pipeline
+
+// Runs fn(begin, end) over [0, n) in contiguous chunks on the host's threads (the chunks
+// depend only on n and the thread count).
+void parallel_for(long long n, const std::function<void(long long, long long)>& fn);
 
 // A method's fit as a saved plan holds it (srp_plan_save / srp_plan_create_from_file).
 struct FitData {
