@@ -123,57 +123,4 @@ __device__ __forceinline__ float2* stockham_fft_r4(float2* a, float2* b, int H, 
   return a;
 }
 
-// stockham_fft_r4 for a compile-time length H and table shift TWS: the stages unroll and
-// their index arithmetic folds to constants.
-template <int H, int TWS, bool INV>
-__device__ __forceinline__ float2* stockham_fft_r4_fixed(float2* a, float2* b, int j,
-                                                         const float2* tw) {
-  static_assert(H >= 4 && (H & (H - 1)) == 0, "power-of-two length");
-  constexpr int q = H >> 2;
-  constexpr int S = (H << TWS) >> 1;  // table entries
-  constexpr bool odd = (__builtin_ctz(H) & 1) != 0;
-  if constexpr (odd) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int jj = j + i * q;
-      const float2 v0 = a[jj], v1 = a[jj + 2 * q];
-      b[2 * jj] = make_float2(v0.x + v1.x, v0.y + v1.y);
-      b[2 * jj + 1] = make_float2(v0.x - v1.x, v0.y - v1.y);
-    }
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
-  }
-#pragma unroll
-  for (int Ns = odd ? 2 : 1; Ns < H; Ns <<= 2) {
-    const int k = j & (Ns - 1);
-    const float2 a0 = a[j];
-    float2 a1 = a[j + q], a2 = a[j + 2 * q], a3 = a[j + 3 * q];
-    const int t1 = (k * (H / (4 * Ns))) << TWS;
-    float2 w1 = tw_lookup(tw, t1, S), w2 = tw_lookup(tw, 2 * t1, S), w3 = tw_lookup(tw, 3 * t1, S);
-    if (INV) {
-      w1.y = -w1.y;
-      w2.y = -w2.y;
-      w3.y = -w3.y;
-    }
-    a1 = cmul(a1, w1);
-    a2 = cmul(a2, w2);
-    a3 = cmul(a3, w3);
-    const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y), d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
-    const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y), d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
-    const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-    const int d = ((j - k) << 2) + k;
-    b[d] = make_float2(s02.x + s13.x, s02.y + s13.y);
-    b[d + Ns] = make_float2(d02.x + r13.x, d02.y + r13.y);
-    b[d + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
-    b[d + 3 * Ns] = make_float2(d02.x - r13.x, d02.y - r13.y);
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
-  }
-  return a;
-}
-
 }  // namespace srp
