@@ -1,9 +1,10 @@
-// Front end of the SRP path: STFT + PHAT, cross-spectra, iFFT sampling, and the
+// Front end of the SRP path: STFT + PHAT, cross-spectra, sampling of the TD GCCs, and the
 // operands of the conventional SRP-matrix product.
 //
 //   y-hat_m(omega_k) = y_m / |y_m|                   PHAT, Eq. corrmatrix
 //   psi_p(omega_k)  = y-hat_m y-hat_m'^*            k = 1..K-1 (Eq. psi_p_single)
-//   xi_p(nT)        = iFFT_2K[psi-bar_p](n)          Eq. xi_p_ifft, n_prime
+//   xi_p(nT)        = iFFT_2K[psi-bar_p](n)          Eq. xi_p_ifft, n_prime (or its matrix
+//                                                    form S-bar_p psi-bar_p, Eq. xi_computed)
 //   H_p[i,k]        = exp(j omega_k Delta t_p(i))    Eq. H_p_single
 #include "srp_internal.h"
 
@@ -261,14 +262,15 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 }
 
 // ---------------------------------------------------------------------------------
-// Fused front end for the interpolation methods: one CTA per frame runs the STFT + PHAT
-// of every channel (the half-length transform of stft_phat_kernel as a radix-4 Stockham
-// FFT, channel groups of N/8 threads) into shared memory, samples every pair by direct summation (the
-// arithmetic of gcc_direct_kernel, reading y-hat from shared memory), and writes the
-// operand the contraction needs: xi in FP32 [F][L] (FP32 SSPI gather), xi as 16-bit
-// [F][Lpad] (tensor-core SI / TD / SSPI), or u = Lambda_fat xi (SLRI) as FP32 [F][Rp] or
-// 16-bit [F][64] scaled by `scale`.  Saves the y-hat round trip through global memory and
-// the separate packing and Lambda_fat launches.
+// Fused front end: one CTA per frame runs the STFT + PHAT of every channel (the
+// half-length transform of stft_phat_kernel as a radix-4 Stockham FFT, channel groups of
+// N/8 threads) into shared memory, then either samples every pair (the matrix form of
+// Eq. xi_p_ifft as a per-frame GEMM on the warp-level tensor cores) and writes the operand
+// the interpolation contraction needs -- xi in FP32 [F][L] (FP32 SSPI gather), xi in the
+// operand type [F][Lpad] (tensor-core SI / TD / SSPI), or u = Lambda_fat xi (SLRI, a second
+// small GEMM) as [F][Rp] or [F][64] scaled by `scale` -- or writes the packed cross-spectra
+// of the conv. FD-SRP / LR-SRP operand.  Saves the y-hat round trip through global memory
+// and the separate sampling, packing and Lambda_fat launches.
 // ---------------------------------------------------------------------------------
 // out[idx] = v in the operand type ot (an OpType value) chosen at run time
 __device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx, float v) {
