@@ -181,6 +181,24 @@ def _fft_len(n: int) -> int:
     return 1 << int(np.ceil(np.log2(max(2, n))))
 
 
+_CHUNK = 4096
+
+
+def _ramps(shifts: np.ndarray, L: int) -> tuple:
+    """Factors of the linear-phase ramps exp(-2 pi i k s / L), k = 0..L/2, for the shifts s:
+    with k = k0 + j (k0 a multiple of _CHUNK, j < _CHUNK) the ramp is A[k0 / _CHUNK, s] *
+    B[s, j].  Each factor is one FP64 exponential, so a ramp entry is exact to rounding.
+    Returns (A [chunks][S], B [S][_CHUNK], number of bins)."""
+    nb = L // 2 + 1
+    nch = -(-nb // _CHUNK)
+    k0 = np.arange(nch, dtype=np.float64) * _CHUNK
+    j = np.arange(_CHUNK, dtype=np.float64)
+    s = np.asarray(shifts, dtype=np.float64)
+    A = np.exp((-2j * np.pi / L) * np.outer(k0, s))
+    B = np.exp((-2j * np.pi / L) * np.outer(s, j))
+    return A, B, nb
+
+
 def propagate(sources, fs: float, mic_xyz: np.ndarray, n_out: int, c: float = C_SOUND,
               images=None) -> np.ndarray:
     """Free-field (or image-source) propagation with exact band-limited fractional delays.
@@ -199,12 +217,14 @@ def propagate(sources, fs: float, mic_xyz: np.ndarray, n_out: int, c: float = C_
         dmax = max(np.linalg.norm(mic_xyz - p[0], axis=1).max() for p in paths)
         L = _fft_len(max(len(sig), n_out) + int(np.ceil(dmax / c * fs)) + 64)
         S = np.fft.rfft(sig, L)
-        f = np.arange(L // 2 + 1) / L  # cycles per sample
+        ppos = np.array([p[0] for p in paths])
+        pgain = np.array([p[1] for p in paths], dtype=np.float64)
         for m in range(M):
-            acc = np.zeros(L // 2 + 1, dtype=np.complex128)
-            for (ppos, gain) in paths:
-                d = float(np.linalg.norm(mic_xyz[m] - ppos))
-                acc += (gain / d) * np.exp(-2j * np.pi * f * (d / c * fs))
+            d = np.linalg.norm(ppos - mic_xyz[m], axis=1)
+            # sum over paths of (gain / d) exp(-2 pi i f d fs / c), f = k / L, as one
+            # product of the ramp factors
+            A, B, nb = _ramps(d / c * fs, L)
+            acc = (A @ ((pgain / d)[:, None] * B)).ravel()[:nb]
             out[m] += np.fft.irfft(S * acc, L)[:n_out]
     return out
 
@@ -249,13 +269,18 @@ def diffuse_noise(g: np.random.Generator, fs: float, mic_xyz: np.ndarray, n_out:
     ctr = mic_xyz.mean(axis=0)
     rel = mic_xyz - ctr
     L = _fft_len(n_out + 64)
-    f = np.arange(L // 2 + 1) / L
-    acc = np.zeros((M, L // 2 + 1), dtype=np.complex128)
+    nb = L // 2 + 1
+    nch = -(-nb // _CHUNK)
+    acc = np.zeros((M, nch * _CHUNK), dtype=np.complex128)
     for w in range(n_waves):
-        S = np.fft.rfft(g.standard_normal(n_out), L)
+        S = np.zeros(nch * _CHUNK, dtype=np.complex128)
+        S[:nb] = np.fft.rfft(g.standard_normal(n_out), L)
+        S = S.reshape(nch, _CHUNK)
         adv = rel @ v[w] / c * fs  # arrival advance in samples for direction v
-        acc += S[None, :] * np.exp(2j * np.pi * f[None, :] * adv[:, None])
-    return np.fft.irfft(acc, L, axis=1)[:, :n_out] / np.sqrt(n_waves)
+        A, B, _ = _ramps(-adv, L)  # exp(+2 pi i f adv) as factors
+        for m in range(M):
+            acc[m] += (S * np.outer(A[:, m], B[m])).ravel()
+    return np.fft.irfft(acc[:, :nb], L, axis=1)[:, :n_out] / np.sqrt(n_waves)
 
 
 def add_noise_snr(x: np.ndarray, noise: np.ndarray, snr_db: float) -> np.ndarray:
