@@ -199,15 +199,25 @@ cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void*
   return contract_to(p, A, A_lo, B, B_lo, Kd, kb_ptr, kb_idx, F, maps, p->g.J, p->d_keys, s);
 }
 
-// Sampling stage (Eq. xi_p_ifft / xi_computed): direct summation for short lag windows,
-// the two-pairs-per-iFFT kernel otherwise.
-cudaError_t sample_gcc(srp_plan_s* p, const float2* yhat, int F, float* xi, cudaStream_t s) {
+// Samples of the TD GCCs (Eq. xi_p_ifft / xi_computed) into out [F][cols] in operand type t
+// (zero padded beyond L).  The two-pairs-per-iFFT kernel writes them directly; for short lag
+// windows the direct sums write FP32 xi, packed into the operand when t or cols differ.
+cudaError_t sample_to(srp_plan_s* p, const float2* yhat, int F, void* out, void* out_lo, int cols,
+                      OpType t, cudaStream_t s) {
   const Geometry& g = p->g;
-  if (p->max_Np <= gcc_direct_max_lag())
-    return launch_gcc_direct(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L,
-                             p->max_Np, p->d_twiddle, xi, s);
+  if (p->max_Np <= gcc_direct_max_lag()) {
+    const bool as_is = t == OpType::F32 && cols == g.L;
+    float* xi = as_is ? static_cast<float*>(out) : p->d_xi;
+    ++p->launches;
+    cudaError_t e = launch_gcc_direct(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L,
+                                      p->max_Np, p->d_twiddle, xi, s);
+    if (e != cudaSuccess || as_is) return e;
+    ++p->launches;
+    return launch_pack16(p->d_xi, F, g.L, cols, 1.f, t, out, out_lo, s);
+  }
+  ++p->launches;
   return launch_gcc_samples(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L,
-                            p->d_twiddle, xi, s);
+                            p->d_twiddle, t, out, out_lo, cols, s);
 }
 
 // A counted kernel launch of the per-call path.
@@ -294,13 +304,14 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       break;
     }
     case SRP_SLRI: {
-      SRP_LAUNCH(sample_gcc(p, p->d_yhat, F, p->d_xi, s));
-      SRP_MARK(p, 2, s);
       if (p->fat_gemm) {
-        SRP_LAUNCH(launch_pack16(p->d_xi, F, g.L, p->Lpad, 1.f, p->op, p->d_A2, p->d_A2_lo, s));
+        SRP_CUDA_TRY(sample_to(p, p->d_yhat, F, p->d_A2, p->d_A2_lo, p->Lpad, p->op, s));
+        SRP_MARK(p, 2, s);
         SRP_CUDA_TRY(contract_to(p, p->d_A2, p->d_A2_lo, p->d_H, p->d_H_lo, p->Lpad, nullptr,
                                  nullptr, F, p->d_U, Rp, p->d_keys2, s));
       } else {
+        SRP_CUDA_TRY(sample_to(p, p->d_yhat, F, p->d_xi, nullptr, g.L, OpType::F32, s));
+        SRP_MARK(p, 2, s);
         SRP_LAUNCH(launch_slri_fat(p->d_xi, p->d_fat, p->d_U, F, g.L, Rp, s));
       }
       if (p->op == OpType::F32) {
@@ -316,13 +327,14 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
     case SRP_SSPI:
     case SRP_SI:
     case SRP_TD: {
-      SRP_LAUNCH(sample_gcc(p, p->d_yhat, F, p->d_xi, s));
-      SRP_MARK(p, 2, s);
       if (method == SRP_SSPI && p->op == OpType::F32) {
+        SRP_CUDA_TRY(sample_to(p, p->d_yhat, F, p->d_xi, nullptr, g.L, OpType::F32, s));
+        SRP_MARK(p, 2, s);
         SRP_LAUNCH(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
                                  p->num_sms, s));
       } else {
-        SRP_LAUNCH(launch_pack16(p->d_xi, F, g.L, p->Lpad, 1.f, p->op, p->d_A, p->d_A_lo, s));
+        SRP_CUDA_TRY(sample_to(p, p->d_yhat, F, p->d_A, p->d_A_lo, p->Lpad, p->op, s));
+        SRP_MARK(p, 2, s);
         SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, p->Lpad, p->d_kb_ptr,
                               p->d_kb_idx, F, maps, s));
       }
@@ -1354,10 +1366,11 @@ extern "C" srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int 
                                 xi + static_cast<size_t>(c0) * g.L, nullptr, s));
       continue;
     }
-    plan->launches += 2;
+    plan->launches += 1;
     SRP_CUDA_TRY(launch_stft_phat(frames + static_cast<size_t>(c0) * g.M * g.N, nf, g.M, g.N,
                                   plan->d_window, plan->d_twiddle, plan->d_yhat, s));
-    SRP_CUDA_TRY(sample_gcc(plan, plan->d_yhat, nf, xi + static_cast<size_t>(c0) * g.L, s));
+    SRP_CUDA_TRY(sample_to(plan, plan->d_yhat, nf, xi + static_cast<size_t>(c0) * g.L, nullptr, g.L,
+                           OpType::F32, s));
   }
   return SRP_OK;
 }

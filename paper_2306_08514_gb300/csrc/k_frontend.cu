@@ -86,61 +86,180 @@ cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const flo
   return cudaGetLastError();
 }
 
+// out[idx] = v in the operand type ot (an OpType value) chosen at run time
+__device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx, float v) {
+  switch (static_cast<OpType>(ot)) {
+    case OpType::F32: op_store<float, false>(hi, lo, idx, v); break;
+    case OpType::F16: op_store<__half, false>(hi, lo, idx, v); break;
+    case OpType::BF16: op_store<__nv_bfloat16, false>(hi, lo, idx, v); break;
+    case OpType::F16X2: op_store<__half, true>(hi, lo, idx, v); break;
+    case OpType::BF16X2: op_store<__nv_bfloat16, true>(hi, lo, idx, v); break;
+    case OpType::TF32: op_store<tf32_t, false>(hi, lo, idx, v); break;
+    case OpType::TF32X2: op_store<tf32_t, true>(hi, lo, idx, v); break;
+  }
+}
+
+// Padded FFT buffers hold element i at i + i/16: the strided stores of the first radix-4
+// stages then spread over all banks.
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int fpad_len(int H) { return H + H / 16; }
+
+// Radix-4 Stockham FFT of compile-time length H (natural order in and out, unnormalised;
+// one radix-2 stage first when log2 H is odd) on padded buffers, with the thread's
+// twiddles of the stages Ns > 1 in registers: tw4[s] = w^k, w^2k, w^3k of the s-th such
+// stage (pfft_twiddles), w = exp(-2 pi i / 4Ns) (exp(+...) when INV).  The global table
+// holds exp(-2 pi i t / Nt) for t < Nt/2, Nt = H << TWS.  Called by H/4 threads per
+// transform (j = 0..H/4-1); every thread of the block takes part in the barriers.
+template <int H>
+struct PFft {
+  static constexpr bool odd = (__builtin_ctz(H) & 1) != 0;
+  static constexpr int NTW = __builtin_ctz(H) / 2 - (odd ? 0 : 1);  // stages with twiddles
+};
+
+template <int H, int TWS, bool INV>
+__device__ __forceinline__ void pfft_twiddles(const float2* __restrict__ twg, int j,
+                                              float2 (&tw4)[PFft<H>::NTW][3]) {
+  constexpr int S = (H << TWS) >> 1;  // table entries
+  int Ns = PFft<H>::odd ? 2 : 4;
+#pragma unroll
+  for (int st = 0; st < PFft<H>::NTW; ++st, Ns <<= 2) {
+    const int k = j & (Ns - 1);
+    const int t1 = (k * (H / (4 * Ns))) << TWS;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int u = (m + 1) * t1;
+      const float2 w = __ldg(twg + (u < S ? u : u - S));
+      const float2 v = u < S ? w : make_float2(-w.x, -w.y);
+      tw4[st][m] = INV ? make_float2(v.x, -v.y) : v;
+    }
+  }
+}
+
+template <int H, bool INV>
+__device__ __forceinline__ float2* pfft(float2* a, float2* b, int j,
+                                        const float2 (&tw4)[PFft<H>::NTW][3]) {
+  constexpr int q = H >> 2;
+  constexpr bool odd = PFft<H>::odd;
+  if constexpr (odd) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int jj = j + i * q;
+      const float2 v0 = a[fpad(jj)], v1 = a[fpad(jj + 2 * q)];
+      b[fpad(2 * jj)] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      b[fpad(2 * jj + 1)] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  int st = 0;
+#pragma unroll
+  for (int Ns = odd ? 2 : 1; Ns < H; Ns <<= 2) {
+    const int k = j & (Ns - 1);
+    const float2 a0 = a[fpad(j)];
+    float2 a1 = a[fpad(j + q)], a2 = a[fpad(j + 2 * q)], a3 = a[fpad(j + 3 * q)];
+    if (Ns > 1) {
+      a1 = cmul(a1, tw4[st][0]);
+      a2 = cmul(a2, tw4[st][1]);
+      a3 = cmul(a3, tw4[st][2]);
+      ++st;
+    }
+    const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y), d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
+    const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y), d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
+    // -i d13 (forward) or +i d13 (inverse)
+    const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+    const int d = ((j - k) << 2) + k;
+    b[fpad(d)] = make_float2(s02.x + s13.x, s02.y + s13.y);
+    b[fpad(d + Ns)] = make_float2(d02.x + r13.x, d02.y + r13.y);
+    b[fpad(d + 2 * Ns)] = make_float2(s02.x - s13.x, s02.y - s13.y);
+    b[fpad(d + 3 * Ns)] = make_float2(d02.x - r13.x, d02.y - r13.y);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
 // ---------------------------------------------------------------------------------
 // Sampling.  Two pairs share one N-point complex iFFT: the input is
 // psi-bar_a + i psi-bar_b, both two-sided (Appendix, Eq. psi_p_two) and Hermitian, so
 // the (unnormalised) inverse transform is xi-bar_a + i xi-bar_b.  The lags
 // n = -N_p..N_p are read at index mod(n, N) (Eq. n_prime) and stored ascending.
 // ---------------------------------------------------------------------------------
-__global__ void gcc_samples_kernel(const float2* __restrict__ yhat, int M, int P, int N,
-                                   const int2* __restrict__ pairs, const int* __restrict__ Np,
-                                   const int* __restrict__ off, int L,
-                                   const float2* __restrict__ twiddle, float* __restrict__ xi) {
-  extern __shared__ float2 smem[];
-  const int K = N >> 1;
-  const int T = N >> 2;       // threads: one radix-4 butterfly each per stage
-  float2* tw = smem;          // N/2
-  float2* bufA = smem + K;    // N
-  float2* bufB = bufA + N;    // N
+template <int N>
+__global__ __launch_bounds__(N / 4) void gcc_samples_kernel(
+    const float2* __restrict__ yhat, int M, int P, const int2* __restrict__ pairs,
+    const int* __restrict__ Np, const int* __restrict__ off, int L,
+    const float2* __restrict__ twiddle, int ot, void* out, void* out_lo, int out_cols) {
+  __shared__ float2 buf[2 * fpad_len(N)];
+  constexpr int K = N >> 1;
+  constexpr int T = N >> 2;  // threads: one radix-4 butterfly each per stage
+  float2* bufA = buf;
+  float2* bufB = buf + fpad_len(N);
   const int j = threadIdx.x;
-  for (int t = j; t < K; t += T) tw[t] = twiddle[t];
+  float2 tw4[PFft<N>::NTW][3];
+  pfft_twiddles<N, 0, true>(twiddle, j, tw4);
   const int f = blockIdx.y;
   const int pa = 2 * blockIdx.x;
   const int pb = pa + 1;
   const bool hasb = pb < P;
-  const int2 qa = pairs[pa];
-  const int2 qb = hasb ? pairs[pb] : make_int2(0, 0);
+  const int2 qa = __ldg(pairs + pa);
+  const int2 qb = hasb ? __ldg(pairs + pb) : make_int2(0, 0);
   const float2* yf = yhat + static_cast<size_t>(f) * M * K;
-  for (int k = j; k < K; k += T) {
+#pragma unroll
+  for (int i = 0; i < K / T; ++i) {
+    const int k = j + i * T;
     if (k == 0) {
-      bufA[0] = make_float2(0.f, 0.f);
-      bufA[K] = make_float2(0.f, 0.f);
+      bufA[fpad(0)] = make_float2(0.f, 0.f);
+      bufA[fpad(K)] = make_float2(0.f, 0.f);
       continue;
     }
-    const float2 a = cmul_conj(yf[qa.x * K + k], yf[qa.y * K + k]);
-    const float2 b = hasb ? cmul_conj(yf[qb.x * K + k], yf[qb.y * K + k]) : make_float2(0.f, 0.f);
-    bufA[k] = make_float2(a.x - b.y, a.y + b.x);          // psi_a + i psi_b
-    bufA[N - k] = make_float2(a.x + b.y, b.x - a.y);      // psi_a^* + i psi_b^*
+    const float2 a = cmul_conj(__ldg(yf + qa.x * K + k), __ldg(yf + qa.y * K + k));
+    const float2 b = hasb ? cmul_conj(__ldg(yf + qb.x * K + k), __ldg(yf + qb.y * K + k))
+                          : make_float2(0.f, 0.f);
+    bufA[fpad(k)] = make_float2(a.x - b.y, a.y + b.x);      // psi_a + i psi_b
+    bufA[fpad(N - k)] = make_float2(a.x + b.y, b.x - a.y);  // psi_a^* + i psi_b^*
   }
   __syncthreads();
-  const float2* x = stockham_fft_r4<true>(bufA, bufB, N, j, tw, 0);
-  const int na = Np[pa];
-  float* outa = xi + static_cast<size_t>(f) * L + off[pa];
-  for (int t = j; t < 2 * na + 1; t += T) outa[t] = x[(t - na + N) & (N - 1)].x;
+  const float2* x = pfft<N, true>(bufA, bufB, j, tw4);
+  const size_t row = static_cast<size_t>(f) * out_cols;
+  const int na = __ldg(Np + pa);
+  const size_t oa = row + __ldg(off + pa);
+  for (int t = j; t < 2 * na + 1; t += T) put_op_rt(ot, out, out_lo, oa + t, x[fpad((t - na + N) & (N - 1))].x);
   if (hasb) {
-    const int nb = Np[pb];
-    float* outb = xi + static_cast<size_t>(f) * L + off[pb];
-    for (int t = j; t < 2 * nb + 1; t += T) outb[t] = x[(t - nb + N) & (N - 1)].y;
+    const int nb = __ldg(Np + pb);
+    const size_t ob = row + __ldg(off + pb);
+    for (int t = j; t < 2 * nb + 1; t += T) put_op_rt(ot, out, out_lo, ob + t, x[fpad((t - nb + N) & (N - 1))].y);
   }
+  if (blockIdx.x == 0)  // the operand's zero padding beyond L
+    for (int c = L + j; c < out_cols; c += T) put_op_rt(ot, out, out_lo, row + c, 0.f);
 }
 
 cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
                                const int* Np, const int* off, int L, const float2* twiddle,
-                               float* xi, cudaStream_t s) {
+                               OpType t, void* out, void* out_lo, int out_cols, cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
+  if (out_cols < L) return cudaErrorInvalidValue;
   dim3 grid((P + 1) / 2, F);
-  const size_t smem = sizeof(float2) * (N / 2 + 2 * static_cast<size_t>(N));
-  gcc_samples_kernel<<<grid, N / 4, smem, s>>>(yhat, M, P, N, pairs, Np, off, L, twiddle, xi);
+  const int ot = static_cast<int>(t);
+  switch (N) {
+    case 256:
+      gcc_samples_kernel<256><<<grid, 64, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      break;
+    case 512:
+      gcc_samples_kernel<512><<<grid, 128, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      break;
+    case 1024:
+      gcc_samples_kernel<1024><<<grid, 256, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      break;
+    case 2048:
+      gcc_samples_kernel<2048><<<grid, 512, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -272,19 +391,6 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 // of the conv. FD-SRP / LR-SRP operand.  Saves the y-hat round trip through global memory
 // and the separate sampling, packing and Lambda_fat launches.
 // ---------------------------------------------------------------------------------
-// out[idx] = v in the operand type ot (an OpType value) chosen at run time
-__device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx, float v) {
-  switch (static_cast<OpType>(ot)) {
-    case OpType::F32: op_store<float, false>(hi, lo, idx, v); break;
-    case OpType::F16: op_store<__half, false>(hi, lo, idx, v); break;
-    case OpType::BF16: op_store<__nv_bfloat16, false>(hi, lo, idx, v); break;
-    case OpType::F16X2: op_store<__half, true>(hi, lo, idx, v); break;
-    case OpType::BF16X2: op_store<__nv_bfloat16, true>(hi, lo, idx, v); break;
-    case OpType::TF32: op_store<tf32_t, false>(hi, lo, idx, v); break;
-    case OpType::TF32X2: op_store<tf32_t, true>(hi, lo, idx, v); break;
-  }
-}
-
 struct FrontParams {
   const float* frames;
   int M, P, L;
@@ -333,85 +439,6 @@ __device__ __forceinline__ void split_h2(float2 v, unsigned& hi, unsigned& lo) {
 // fragment gathers at once fall into distinct bank groups.
 __host__ __device__ constexpr int front_row(int K) { return K + 4; }
 
-// FFT buffers of the front kernel hold element i at i + i/16: the strided stores of the
-// first radix-4 stages then spread over all banks.
-__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int fpad_len(int H) { return H + H / 16; }
-
-// Radix-4 Stockham FFT of compile-time length H (as stockham_fft_r4_fixed with TWS = 1) on
-// padded buffers, with the thread's twiddles of the stages Ns > 1 in registers (tw4[s] =
-// w^k, w^2k, w^3k of the s-th such stage; front_fft_twiddles).  Called by H/4 threads per
-// channel; every thread of the block takes part in the barriers.
-template <int H>
-struct FrontFft {
-  static constexpr bool odd = (__builtin_ctz(H) & 1) != 0;
-  static constexpr int NTW = __builtin_ctz(H) / 2 - (odd ? 0 : 1);  // stages with twiddles
-};
-
-template <int H>
-__device__ __forceinline__ void front_fft_twiddles(const float2* __restrict__ twg, int j,
-                                                   float2 (&tw4)[FrontFft<H>::NTW][3]) {
-  constexpr int S = H;  // table entries exp(-2 pi i t / 2H), t < H
-  int Ns = FrontFft<H>::odd ? 2 : 4;
-#pragma unroll
-  for (int st = 0; st < FrontFft<H>::NTW; ++st, Ns <<= 2) {
-    const int k = j & (Ns - 1);
-    const int t1 = (k * (H / (4 * Ns))) << 1;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const int u = (m + 1) * t1;
-      const float2 w = __ldg(twg + (u < S ? u : u - S));
-      tw4[st][m] = u < S ? w : make_float2(-w.x, -w.y);
-    }
-  }
-}
-
-template <int H>
-__device__ __forceinline__ float2* front_fft(float2* a, float2* b, int j,
-                                             const float2 (&tw4)[FrontFft<H>::NTW][3]) {
-  constexpr int q = H >> 2;
-  constexpr bool odd = FrontFft<H>::odd;
-  if constexpr (odd) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int jj = j + i * q;
-      const float2 v0 = a[fpad(jj)], v1 = a[fpad(jj + 2 * q)];
-      b[fpad(2 * jj)] = make_float2(v0.x + v1.x, v0.y + v1.y);
-      b[fpad(2 * jj + 1)] = make_float2(v0.x - v1.x, v0.y - v1.y);
-    }
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
-  }
-  int st = 0;
-#pragma unroll
-  for (int Ns = odd ? 2 : 1; Ns < H; Ns <<= 2) {
-    const int k = j & (Ns - 1);
-    const float2 a0 = a[fpad(j)];
-    float2 a1 = a[fpad(j + q)], a2 = a[fpad(j + 2 * q)], a3 = a[fpad(j + 3 * q)];
-    if (Ns > 1) {
-      a1 = cmul(a1, tw4[st][0]);
-      a2 = cmul(a2, tw4[st][1]);
-      a3 = cmul(a3, tw4[st][2]);
-      ++st;
-    }
-    const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y), d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
-    const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y), d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
-    const float2 r13 = make_float2(d13.y, -d13.x);  // -i d13
-    const int d = ((j - k) << 2) + k;
-    b[fpad(d)] = make_float2(s02.x + s13.x, s02.y + s13.y);
-    b[fpad(d + Ns)] = make_float2(d02.x + r13.x, d02.y + r13.y);
-    b[fpad(d + 2 * Ns)] = make_float2(s02.x - s13.x, s02.y - s13.y);
-    b[fpad(d + 3 * Ns)] = make_float2(d02.x - r13.x, d02.y - r13.y);
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
-  }
-  return a;
-}
-
 // One CTA of 256 threads per frame; H = N/2 is the complex FFT length (= K), NTM bounds
 // the n-tiles of the sampling GEMM.
 template <int H, int NTM>
@@ -434,8 +461,8 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
   const int grp = tid / Tg, j = tid - grp * Tg;
   float2* bufA = fbuf + grp * 2 * fpad_len(H);
   float2* bufB = bufA + fpad_len(H);
-  float2 tw4[FrontFft<H>::NTW][3];
-  front_fft_twiddles<H>(a.twiddle, j, tw4);
+  float2 tw4[PFft<H>::NTW][3];
+  pfft_twiddles<H, 1, false>(a.twiddle, j, tw4);
   const float2* w2 = reinterpret_cast<const float2*>(a.window);
   float2 xv[4], wv[4];
 #pragma unroll
@@ -456,7 +483,7 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
     if (m0 + groups < M) load_round(m0 + groups);  // in flight during this round's FFT
     __syncthreads();
     // every thread of the block takes part in the FFT's barriers
-    const float2* Z = front_fft<H>(bufA, bufB, j, tw4);
+    const float2* Z = pfft<H, false>(bufA, bufB, j, tw4);
     if (m < M) {
       // real spectrum from the packed transform, then PHAT
       float2* out = yh + static_cast<size_t>(m) * KS;

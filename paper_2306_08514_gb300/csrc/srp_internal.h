@@ -96,24 +96,6 @@ srp_status fit_sparse(const Geometry& g, long long nnz, std::vector<long long>& 
 unsigned host_threads();
 
 // ------------------------------------------------------------------ kernels
-// Front end: window + real DFT of length N + PHAT, y-hat [F][M][K] (bin 0 zeroed).
-cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const float* window,
-                             const float2* twiddle, float2* yhat, cudaStream_t s);
-// Cross-spectra, two-sided iFFT of length N, lag selection -> xi [F][L].
-cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N,
-                               const int2* pairs, const int* Np, const int* off, int L,
-                               const float2* twiddle, float* xi, cudaStream_t s);
-// The same samples by direct summation over the bins (N_p <= gcc_direct_max_lag()).
-int gcc_direct_max_lag();
-cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
-                              const int* Np, const int* off, int L, int max_Np,
-                              const float2* twiddle, float* xi, cudaStream_t s);
-// Frames from consecutive hops [B][M][hop] and the history [M][N - hop] (streaming front).
-cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N,
-                                 const float* hist_in, float* frames, float* hist_out,
-                                 cudaStream_t s);
-// Cross-spectra packed as the conv GEMM operand A [F][P*N]:
-// A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
 // Operand type of a contraction: FP32 (CUDA cores), or one or two (hi + lo) planes of
 // FP16, BF16 or TF32 for the tensor cores.  The values double as the front kernel's output
 // codes.
@@ -125,6 +107,26 @@ inline bool op_tf32(OpType t) { return t == OpType::TF32 || t == OpType::TF32X2;
 inline size_t op_bytes(OpType t) { return t == OpType::F32 || op_tf32(t) ? 4 : 2; }
 // tensor-core k-blocks (128-byte rows) per 64 operand columns
 inline int op_kb_per64(OpType t) { return op_tf32(t) ? 2 : 1; }
+// Front end: window + real DFT of length N + PHAT, y-hat [F][M][K] (bin 0 zeroed).
+cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const float* window,
+                             const float2* twiddle, float2* yhat, cudaStream_t s);
+// Cross-spectra, two-sided iFFT of length N, lag selection -> out [F][out_cols] in operand
+// type t (xi in columns 0..L-1, zeros beyond; FP32 xi: t = F32, out_cols = L).
+cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N,
+                               const int2* pairs, const int* Np, const int* off, int L,
+                               const float2* twiddle, OpType t, void* out, void* out_lo,
+                               int out_cols, cudaStream_t s);
+// The same samples by direct summation over the bins (N_p <= gcc_direct_max_lag()).
+int gcc_direct_max_lag();
+cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                              const int* Np, const int* off, int L, int max_Np,
+                              const float2* twiddle, float* xi, cudaStream_t s);
+// Frames from consecutive hops [B][M][hop] and the history [M][N - hop] (streaming front).
+cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N,
+                                 const float* hist_in, float* frames, float* hist_out,
+                                 cudaStream_t s);
+// Cross-spectra packed as the conv GEMM operand A [F][P*N]:
+// A[f][p*N + k] = Re psi_p(k), A[f][p*N + K + k] = Im psi_p(k), k = 0..K-1, psi(0) = 0.
 // Fused STFT + PHAT + sampling (+ Lambda_fat) per frame: writes xi (ftab == NULL)
 // or u = Lambda_fat xi * scale, rows of out_cols entries (zero padded) in operand type t.
 // The sampling and the Lambda_fat product are per-frame GEMMs on the warp-level tensor
