@@ -104,80 +104,136 @@ __device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int fpad_len(int H) { return H + H / 16; }
 
-// Radix-4 Stockham FFT of compile-time length H (natural order in and out, unnormalised;
-// one radix-2 stage first when log2 H is odd) on padded buffers, with the thread's
-// twiddles of the stages Ns > 1 in registers: tw4[s] = w^k, w^2k, w^3k of the s-th such
-// stage (pfft_twiddles), w = exp(-2 pi i / 4Ns) (exp(+...) when INV).  The global table
-// holds exp(-2 pi i t / Nt) for t < Nt/2, Nt = H << TWS.  Called by H/4 threads per
-// transform (j = 0..H/4-1); every thread of the block takes part in the barriers.
+// Mixed-radix Stockham FFT of compile-time length H (natural order in and out,
+// unnormalised) on padded buffers: a first stage of radix R0 = 2, 4 or 8 with Ns = 1 (no
+// twiddles), then radix-8 stages.  Stage with sub-transform length Ns and radix R:
+// butterfly b (< H/R) takes a[b + m H/R], m < R, multiplies input m by w^(m k) (w =
+// exp(-2 pi i / (R Ns)), exp(+...) when INV; k = b mod Ns), transforms, and writes output r
+// to ((b - k) R + k) + r Ns.  Called by H/8 threads per transform (t = 0..H/8-1), each
+// owning one radix-8 butterfly per stage; the thread's twiddles w^k, w^2k, w^4k of each
+// radix-8 stage are in registers (p8_twiddles).  Every thread of the block takes part in
+// the barriers.
 template <int H>
-struct PFft {
-  static constexpr bool odd = (__builtin_ctz(H) & 1) != 0;
-  static constexpr int NTW = __builtin_ctz(H) / 2 - (odd ? 0 : 1);  // stages with twiddles
+struct P8 {
+  static constexpr int LOG = __builtin_ctz(H);
+  static constexpr int R0 = LOG % 3 == 0 ? 8 : (LOG % 3 == 1 ? 2 : 4);
+  static constexpr int LOG0 = R0 == 8 ? 3 : (R0 == 4 ? 2 : 1);
+  static constexpr int NTW = (LOG - LOG0) / 3;  // radix-8 stages after the first
 };
 
 template <int H, int TWS, bool INV>
-__device__ __forceinline__ void pfft_twiddles(const float2* __restrict__ twg, int j,
-                                              float2 (&tw4)[PFft<H>::NTW][3]) {
-  constexpr int S = (H << TWS) >> 1;  // table entries
-  int Ns = PFft<H>::odd ? 2 : 4;
+__device__ __forceinline__ void p8_twiddles(const float2* __restrict__ twg, int t,
+                                            float2 (&tw3)[P8<H>::NTW > 0 ? P8<H>::NTW : 1][3]) {
+  int Ns = P8<H>::R0;
 #pragma unroll
-  for (int st = 0; st < PFft<H>::NTW; ++st, Ns <<= 2) {
-    const int k = j & (Ns - 1);
-    const int t1 = (k * (H / (4 * Ns))) << TWS;
+  for (int st = 0; st < P8<H>::NTW; ++st, Ns <<= 3) {
+    const int k = t & (Ns - 1);
+    const int u = (k * (H / (8 * Ns))) << TWS;  // w^k = table[u]; 4u < table size
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      const int u = (m + 1) * t1;
-      const float2 w = __ldg(twg + (u < S ? u : u - S));
-      const float2 v = u < S ? w : make_float2(-w.x, -w.y);
-      tw4[st][m] = INV ? make_float2(v.x, -v.y) : v;
+      const float2 w = __ldg(twg + (u << m));
+      tw3[st][m] = INV ? make_float2(w.x, -w.y) : w;
     }
   }
 }
 
-template <int H, bool INV>
-__device__ __forceinline__ float2* pfft(float2* a, float2* b, int j,
-                                        const float2 (&tw4)[PFft<H>::NTW][3]) {
-  constexpr int q = H >> 2;
-  constexpr bool odd = PFft<H>::odd;
-  if constexpr (odd) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int jj = j + i * q;
-      const float2 v0 = a[fpad(jj)], v1 = a[fpad(jj + 2 * q)];
-      b[fpad(2 * jj)] = make_float2(v0.x + v1.x, v0.y + v1.y);
-      b[fpad(2 * jj + 1)] = make_float2(v0.x - v1.x, v0.y - v1.y);
-    }
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// 4-point DFT in place (forward: exp(-...), inverse: exp(+...))
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& c0, float2& c1, float2& c2, float2& c3) {
+  const float2 s02 = cadd(c0, c2), d02 = csub(c0, c2), s13 = cadd(c1, c3), d13 = csub(c1, c3);
+  const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);  // +-i d13
+  c0 = cadd(s02, s13);
+  c1 = cadd(d02, r13);
+  c2 = csub(s02, s13);
+  c3 = csub(d02, r13);
+}
+
+// 8-point DFT in place: a_m = x_m + x_{m+4} give the even outputs (4-point DFT), b_m =
+// (x_m - x_{m+4}) W8^m the odd ones
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&x)[8]) {
+  constexpr float h = 0.70710678118654752440f;
+  float2 a0 = cadd(x[0], x[4]), a1 = cadd(x[1], x[5]), a2 = cadd(x[2], x[6]), a3 = cadd(x[3], x[7]);
+  float2 b0 = csub(x[0], x[4]), b1 = csub(x[1], x[5]), b2 = csub(x[2], x[6]), b3 = csub(x[3], x[7]);
+  if (INV) {  // W8 = (1 + i)/sqrt2, W8^2 = i, W8^3 = (-1 + i)/sqrt2
+    b1 = make_float2(h * (b1.x - b1.y), h * (b1.x + b1.y));
+    b2 = make_float2(-b2.y, b2.x);
+    b3 = make_float2(-h * (b3.x + b3.y), h * (b3.x - b3.y));
+  } else {    // W8 = (1 - i)/sqrt2, W8^2 = -i, W8^3 = (-1 - i)/sqrt2
+    b1 = make_float2(h * (b1.x + b1.y), h * (b1.y - b1.x));
+    b2 = make_float2(b2.y, -b2.x);
+    b3 = make_float2(h * (b3.y - b3.x), -h * (b3.x + b3.y));
   }
-  int st = 0;
+  dft4<INV>(a0, a1, a2, a3);
+  dft4<INV>(b0, b1, b2, b3);
+  x[0] = a0; x[2] = a1; x[4] = a2; x[6] = a3;
+  x[1] = b0; x[3] = b1; x[5] = b2; x[7] = b3;
+}
+
+template <int H, bool INV>
+__device__ __forceinline__ float2* p8fft(float2* a, float2* b, int t,
+                                         const float2 (&tw3)[P8<H>::NTW > 0 ? P8<H>::NTW : 1][3]) {
+  constexpr int R0 = P8<H>::R0;
+  constexpr int T = H / 8;
+  // first stage, Ns = 1: 8 / R0 butterflies of radix R0 per thread
+  {
+    constexpr int S = H / R0;
 #pragma unroll
-  for (int Ns = odd ? 2 : 1; Ns < H; Ns <<= 2) {
-    const int k = j & (Ns - 1);
-    const float2 a0 = a[fpad(j)];
-    float2 a1 = a[fpad(j + q)], a2 = a[fpad(j + 2 * q)], a3 = a[fpad(j + 3 * q)];
-    if (Ns > 1) {
-      a1 = cmul(a1, tw4[st][0]);
-      a2 = cmul(a2, tw4[st][1]);
-      a3 = cmul(a3, tw4[st][2]);
-      ++st;
+    for (int i = 0; i < 8 / R0; ++i) {
+      const int bi = t + i * T;
+      if constexpr (R0 == 8) {
+        float2 x[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) x[m] = a[fpad(bi + m * S)];
+        dft8<INV>(x);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) b[fpad(bi * 8 + r)] = x[r];
+      } else if constexpr (R0 == 4) {
+        float2 c0 = a[fpad(bi)], c1 = a[fpad(bi + S)], c2 = a[fpad(bi + 2 * S)], c3 = a[fpad(bi + 3 * S)];
+        dft4<INV>(c0, c1, c2, c3);
+        b[fpad(bi * 4)] = c0;
+        b[fpad(bi * 4 + 1)] = c1;
+        b[fpad(bi * 4 + 2)] = c2;
+        b[fpad(bi * 4 + 3)] = c3;
+      } else {
+        const float2 v0 = a[fpad(bi)], v1 = a[fpad(bi + S)];
+        b[fpad(bi * 2)] = cadd(v0, v1);
+        b[fpad(bi * 2 + 1)] = csub(v0, v1);
+      }
     }
-    const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y), d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
-    const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y), d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
-    // -i d13 (forward) or +i d13 (inverse)
-    const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-    const int d = ((j - k) << 2) + k;
-    b[fpad(d)] = make_float2(s02.x + s13.x, s02.y + s13.y);
-    b[fpad(d + Ns)] = make_float2(d02.x + r13.x, d02.y + r13.y);
-    b[fpad(d + 2 * Ns)] = make_float2(s02.x - s13.x, s02.y - s13.y);
-    b[fpad(d + 3 * Ns)] = make_float2(d02.x - r13.x, d02.y - r13.y);
     __syncthreads();
-    float2* t = a;
+    float2* tmp = a;
     a = b;
-    b = t;
+    b = tmp;
+  }
+  // radix-8 stages, one butterfly per thread
+  int Ns = R0;
+#pragma unroll
+  for (int st = 0; st < P8<H>::NTW; ++st, Ns <<= 3) {
+    const int k = t & (Ns - 1);
+    float2 x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = a[fpad(t + m * T)];
+    const float2 w1 = tw3[st][0], w2 = tw3[st][1], w4 = tw3[st][2];
+    const float2 w3 = cmul(w2, w1), w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w6, w1);
+    x[1] = cmul(x[1], w1);
+    x[2] = cmul(x[2], w2);
+    x[3] = cmul(x[3], w3);
+    x[4] = cmul(x[4], w4);
+    x[5] = cmul(x[5], w5);
+    x[6] = cmul(x[6], w6);
+    x[7] = cmul(x[7], w7);
+    dft8<INV>(x);
+    const int d = ((t - k) << 3) + k;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) b[fpad(d + r * Ns)] = x[r];
+    __syncthreads();
+    float2* tmp = a;
+    a = b;
+    b = tmp;
   }
   return a;
 }
@@ -189,18 +245,18 @@ __device__ __forceinline__ float2* pfft(float2* a, float2* b, int j,
 // n = -N_p..N_p are read at index mod(n, N) (Eq. n_prime) and stored ascending.
 // ---------------------------------------------------------------------------------
 template <int N>
-__global__ __launch_bounds__(N / 4) void gcc_samples_kernel(
+__global__ __launch_bounds__(N / 8) void gcc_samples_kernel(
     const float2* __restrict__ yhat, int M, int P, const int2* __restrict__ pairs,
     const int* __restrict__ Np, const int* __restrict__ off, int L,
     const float2* __restrict__ twiddle, int ot, void* out, void* out_lo, int out_cols) {
   __shared__ float2 buf[2 * fpad_len(N)];
   constexpr int K = N >> 1;
-  constexpr int T = N >> 2;  // threads: one radix-4 butterfly each per stage
+  constexpr int T = N >> 3;  // threads: one radix-8 butterfly each per stage
   float2* bufA = buf;
   float2* bufB = buf + fpad_len(N);
   const int j = threadIdx.x;
-  float2 tw4[PFft<N>::NTW][3];
-  pfft_twiddles<N, 0, true>(twiddle, j, tw4);
+  float2 tw3[P8<N>::NTW > 0 ? P8<N>::NTW : 1][3];
+  p8_twiddles<N, 0, true>(twiddle, j, tw3);
   const int f = blockIdx.y;
   const int pa = 2 * blockIdx.x;
   const int pb = pa + 1;
@@ -223,7 +279,7 @@ __global__ __launch_bounds__(N / 4) void gcc_samples_kernel(
     bufA[fpad(N - k)] = make_float2(a.x + b.y, b.x - a.y);  // psi_a^* + i psi_b^*
   }
   __syncthreads();
-  const float2* x = pfft<N, true>(bufA, bufB, j, tw4);
+  const float2* x = p8fft<N, true>(bufA, bufB, j, tw3);
   const size_t row = static_cast<size_t>(f) * out_cols;
   const int na = __ldg(Np + pa);
   const size_t oa = row + __ldg(off + pa);
@@ -246,16 +302,16 @@ cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, c
   const int ot = static_cast<int>(t);
   switch (N) {
     case 256:
-      gcc_samples_kernel<256><<<grid, 64, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      gcc_samples_kernel<256><<<grid, 32, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
       break;
     case 512:
-      gcc_samples_kernel<512><<<grid, 128, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      gcc_samples_kernel<512><<<grid, 64, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
       break;
     case 1024:
-      gcc_samples_kernel<1024><<<grid, 256, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      gcc_samples_kernel<1024><<<grid, 128, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
       break;
     case 2048:
-      gcc_samples_kernel<2048><<<grid, 512, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
+      gcc_samples_kernel<2048><<<grid, 256, 0, s>>>(yhat, M, P, pairs, Np, off, L, twiddle, ot, out, out_lo, out_cols);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -445,7 +501,7 @@ template <int H, int NTM>
 __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_kernel(const FrontParams a) {
   extern __shared__ float2 sm[];
   constexpr int N = 2 * H, K = H, KS = front_row(K);
-  constexpr int Tg = H / 4;              // threads per channel group (radix-4 FFT)
+  constexpr int Tg = H / 8;              // threads per channel group (radix-8 FFT)
   constexpr int groups = 256 / Tg;       // channels transformed at once
   constexpr int NW = 8;                  // warps
   const int M = a.M;
@@ -456,39 +512,33 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
   const int tid = threadIdx.x;
   const int f = blockIdx.x;
   for (int t = tid; t < H; t += 256) tw[t] = a.twiddle[t];
-  // each thread owns the complex samples j + i Tg (i = 0..3) of its group's channel,
-  // loaded one round ahead
+  // each thread owns the complex samples j + i Tg (i = 0..7) of its group's channel
   const int grp = tid / Tg, j = tid - grp * Tg;
   float2* bufA = fbuf + grp * 2 * fpad_len(H);
   float2* bufB = bufA + fpad_len(H);
-  float2 tw4[PFft<H>::NTW][3];
-  pfft_twiddles<H, 1, false>(a.twiddle, j, tw4);
+  float2 tw3[P8<H>::NTW > 0 ? P8<H>::NTW : 1][3];
+  p8_twiddles<H, 1, false>(a.twiddle, j, tw3);
   const float2* w2 = reinterpret_cast<const float2*>(a.window);
-  float2 xv[4], wv[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) wv[i] = __ldg(w2 + j + i * Tg);
-  auto load_round = [&](int m0) {
-    const int m = m0 + grp;
-    const float2* x2 = reinterpret_cast<const float2*>(a.frames + (static_cast<size_t>(f) * M + (m < M ? m : 0)) * N);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) xv[i] = m < M ? __ldg(x2 + j + i * Tg) : make_float2(0.f, 0.f);
-  };
-  load_round(0);
   for (int m0 = 0; m0 < M; m0 += groups) {
     const int m = m0 + grp;
+    const float2* x2 = reinterpret_cast<const float2*>(a.frames + (static_cast<size_t>(f) * M + (m < M ? m : 0)) * N);
+    float2 xv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xv[i] = m < M ? __ldg(x2 + j + i * Tg) : make_float2(0.f, 0.f);
     __syncthreads();  // twiddles ready / previous round's buffers consumed
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      bufA[fpad(j + i * Tg)] = make_float2(xv[i].x * wv[i].x, xv[i].y * wv[i].y);
-    if (m0 + groups < M) load_round(m0 + groups);  // in flight during this round's FFT
+    for (int i = 0; i < 8; ++i) {
+      const float2 ww = __ldg(w2 + j + i * Tg);
+      bufA[fpad(j + i * Tg)] = make_float2(xv[i].x * ww.x, xv[i].y * ww.y);
+    }
     __syncthreads();
     // every thread of the block takes part in the FFT's barriers
-    const float2* Z = pfft<H, false>(bufA, bufB, j, tw4);
+    const float2* Z = p8fft<H, false>(bufA, bufB, j, tw3);
     if (m < M) {
       // real spectrum from the packed transform, then PHAT
       float2* out = yh + static_cast<size_t>(m) * KS;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < 8; ++i) {
         const int k = j + i * Tg;
         const float2 zk = Z[fpad(k)];
         const float2 zr = Z[fpad((H - k) & (H - 1))];
@@ -733,7 +783,7 @@ void front_fat_table(const float* fat, int Rp, int L, std::vector<uint4>& tab) {
 }
 
 size_t front_smem_bytes(int M, int N, int L, int max_Np) {
-  const int H = N / 2, Tg = H / 4;
+  const int H = N / 2, Tg = H / 8;
   const int groups = 256 / Tg;
   const size_t fbuf = std::max(sizeof(float2) * groups * 2 * fpad_len(H),
                                sizeof(float) * 8 * 16 * 8 * front_ntm(max_Np));
@@ -756,7 +806,7 @@ cudaError_t launch_front(const float* frames, int F, int M, int N, const float* 
   if (F <= 0) return cudaSuccess;
   if (!front_supported(M, N, L, max_Np)) return cudaErrorNotSupported;
   const int NT = front_ntiles(max_Np);
-  const int H = N / 2, groups = 256 / (H / 4);
+  const int H = N / 2, groups = 256 / (H / 8);
   const int NTM = front_ntm(max_Np);
   const int fbuf_floats = std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * NTM);
   const int ot = static_cast<int>(t);
@@ -772,7 +822,7 @@ cudaError_t launch_front_conv(const float* frames, int F, int M, int N, const fl
                               void* A_lo, cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
   if (!front_conv_supported(M, N)) return cudaErrorNotSupported;
-  const int H = N / 2, groups = 256 / (H / 4);
+  const int H = N / 2, groups = 256 / (H / 8);
   FrontParams a{frames, M, P, 0, window, twiddle, pairs, nullptr, nullptr, nullptr, 0, 1,
                 std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * 2), nullptr, 0, 0, 1.f,
                 static_cast<int>(t), A, A_lo, 1};
