@@ -16,76 +16,13 @@
 namespace srp {
 
 // ---------------------------------------------------------------------------------
-// STFT + PHAT.  One group of N/4 threads per (frame, microphone).  The N real
-// samples are packed as N/2 complex numbers z[j] = x[2j] + i x[2j+1], transformed by
-// an N/2-point FFT, and the N-point spectrum is recovered for k = 1..K-1 as
-// X[k] = E[k] + W^k O[k] with E = (Z[k] + Z[N/2-k]^*)/2, O = (Z[k] - Z[N/2-k]^*)/(2i).
-// An all-zero channel gives exactly X = 0, hence y-hat = 0 (|y|^2 < 1e-30 -> 0).
+// STFT + PHAT.  One group of N/16 threads per (frame, microphone), 256 threads per
+// block.  The N real samples are packed as H = N/2 complex numbers z[j] = x[2j] + i x[2j+1],
+// transformed by the H-point mixed-radix FFT (p8fft), and the N-point spectrum is recovered
+// for k = 1..K-1 as X[k] = E[k] + W^k O[k] with E = (Z[k] + Z[H-k]^*)/2,
+// O = (Z[k] - Z[H-k]^*)/(2i).  An all-zero channel gives exactly X = 0, hence y-hat = 0
+// (|y|^2 < 1e-30 -> 0).
 // ---------------------------------------------------------------------------------
-__global__ void stft_phat_kernel(const float* __restrict__ frames, int M, int N,
-                                 const float* __restrict__ window,
-                                 const float2* __restrict__ twiddle,
-                                 float2* __restrict__ yhat) {
-  extern __shared__ float2 smem[];
-  const int H = N >> 1;       // complex FFT length
-  const int T = H >> 1;       // threads per channel group
-  float2* tw = smem;          // N/2 entries
-  float2* bufA = smem + H + threadIdx.y * 2 * H;
-  float2* bufB = bufA + H;
-  const int tid = threadIdx.y * T + threadIdx.x;
-  const int nthreads = T * blockDim.y;
-  for (int t = tid; t < H; t += nthreads) tw[t] = twiddle[t];
-
-  const int f = blockIdx.y;
-  const int m = blockIdx.x * blockDim.y + threadIdx.y;
-  const bool live = m < M;
-  const float2* x2 =
-      reinterpret_cast<const float2*>(frames + (static_cast<size_t>(f) * M + (live ? m : 0)) * N);
-  const float2* w2 = reinterpret_cast<const float2*>(window);
-  for (int j = threadIdx.x; j < H; j += T) {
-    float2 v = live ? x2[j] : make_float2(0.f, 0.f);
-    float2 w = w2[j];
-    bufA[j] = make_float2(v.x * w.x, v.y * w.y);
-  }
-  __syncthreads();
-  float2* Z = stockham_fft<false>(bufA, bufB, H, threadIdx.x, tw, 1);
-  if (!live) return;  // no barrier follows
-  const int K = H;
-  float2* out = yhat + (static_cast<size_t>(f) * M + m) * K;
-  for (int k = threadIdx.x; k < K; k += T) {
-    if (k == 0) {
-      out[0] = make_float2(0.f, 0.f);  // DC is not used (Sec. II-D)
-      continue;
-    }
-    const float2 zk = Z[k];
-    const float2 zc = make_float2(Z[H - k].x, -Z[H - k].y);
-    const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
-    const float2 O = make_float2(0.5f * (zk.y - zc.y), -0.5f * (zk.x - zc.x));
-    const float2 X = make_float2(E.x, E.y);
-    const float2 WO = cmul(tw[k], O);
-    const float2 Y = make_float2(X.x + WO.x, X.y + WO.y);
-    const float p = Y.x * Y.x + Y.y * Y.y;
-    float2 r = make_float2(0.f, 0.f);
-    if (p >= 1e-30f) {
-      const float s = __frsqrt_rn(p);
-      r = make_float2(Y.x * s, Y.y * s);
-    }
-    out[k] = r;
-  }
-}
-
-cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const float* window,
-                             const float2* twiddle, float2* yhat, cudaStream_t s) {
-  if (F <= 0) return cudaSuccess;
-  const int T = N / 4;
-  const int cpb = T >= 256 ? 1 : 256 / T;  // channels per block
-  dim3 block(T, cpb);
-  dim3 grid((M + cpb - 1) / cpb, F);
-  const size_t smem = sizeof(float2) * (N / 2 + static_cast<size_t>(cpb) * N);
-  stft_phat_kernel<<<grid, block, smem, s>>>(frames, M, N, window, twiddle, yhat);
-  return cudaGetLastError();
-}
-
 // out[idx] = v in the operand type ot (an OpType value) chosen at run time
 __device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx, float v) {
   switch (static_cast<OpType>(ot)) {
@@ -236,6 +173,76 @@ __device__ __forceinline__ float2* p8fft(float2* a, float2* b, int t,
     b = tmp;
   }
   return a;
+}
+
+template <int H>
+__global__ __launch_bounds__(256) void stft_phat_kernel(const float* __restrict__ frames, int M,
+                                                        const float* __restrict__ window,
+                                                        const float2* __restrict__ twiddle,
+                                                        float2* __restrict__ yhat) {
+  extern __shared__ float2 smem[];
+  constexpr int N = 2 * H, K = H;
+  constexpr int Tg = H / 8;  // threads per channel group
+  float2* tw = smem;         // H entries
+  float2* bufA = smem + H + threadIdx.y * 2 * fpad_len(H);
+  float2* bufB = bufA + fpad_len(H);
+  const int tid = threadIdx.y * Tg + threadIdx.x;
+  for (int t = tid; t < H; t += Tg * blockDim.y) tw[t] = twiddle[t];
+  float2 tw3[P8<H>::NTW > 0 ? P8<H>::NTW : 1][3];
+  p8_twiddles<H, 1, false>(twiddle, threadIdx.x, tw3);
+  const int f = blockIdx.y;
+  const int m = blockIdx.x * blockDim.y + threadIdx.y;
+  const bool live = m < M;
+  const float2* x2 =
+      reinterpret_cast<const float2*>(frames + (static_cast<size_t>(f) * M + (live ? m : 0)) * N);
+  const float2* w2 = reinterpret_cast<const float2*>(window);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int j = threadIdx.x + i * Tg;
+    const float2 v = live ? __ldg(x2 + j) : make_float2(0.f, 0.f);
+    const float2 w = __ldg(w2 + j);
+    bufA[fpad(j)] = make_float2(v.x * w.x, v.y * w.y);
+  }
+  __syncthreads();
+  const float2* Z = p8fft<H, false>(bufA, bufB, threadIdx.x, tw3);
+  if (!live) return;  // no barrier follows
+  float2* out = yhat + (static_cast<size_t>(f) * M + m) * K;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = threadIdx.x + i * Tg;
+    const float2 zk = Z[fpad(k)];
+    const float2 zr = Z[fpad((H - k) & (H - 1))];
+    const float2 zc = make_float2(zr.x, -zr.y);
+    const float2 E = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+    const float2 O = make_float2(0.5f * (zk.y - zc.y), -0.5f * (zk.x - zc.x));
+    const float2 WO = cmul(tw[k], O);
+    const float2 Y = make_float2(E.x + WO.x, E.y + WO.y);
+    const float p = Y.x * Y.x + Y.y * Y.y;
+    float2 r = make_float2(0.f, 0.f);
+    if (k > 0 && p >= 1e-30f) {  // DC is not used (Sec. II-D)
+      const float sc = __frsqrt_rn(p);
+      r = make_float2(Y.x * sc, Y.y * sc);
+    }
+    out[k] = r;
+  }
+}
+
+cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const float* window,
+                             const float2* twiddle, float2* yhat, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  const int H = N / 2, Tg = H / 8;
+  const int cpb = 256 / Tg;  // channels per block
+  dim3 block(Tg, cpb);
+  dim3 grid((M + cpb - 1) / cpb, F);
+  const size_t smem = sizeof(float2) * (H + static_cast<size_t>(cpb) * 2 * fpad_len(H));
+  switch (H) {
+    case 128: stft_phat_kernel<128><<<grid, block, smem, s>>>(frames, M, window, twiddle, yhat); break;
+    case 256: stft_phat_kernel<256><<<grid, block, smem, s>>>(frames, M, window, twiddle, yhat); break;
+    case 512: stft_phat_kernel<512><<<grid, block, smem, s>>>(frames, M, window, twiddle, yhat); break;
+    case 1024: stft_phat_kernel<1024><<<grid, block, smem, s>>>(frames, M, window, twiddle, yhat); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------
