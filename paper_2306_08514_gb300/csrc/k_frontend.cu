@@ -36,8 +36,8 @@ __device__ __forceinline__ void put_op_rt(int ot, void* hi, void* lo, size_t idx
   }
 }
 
-// Padded FFT buffers hold element i at i + i/16: the strided stores of the first radix-4
-// stages then spread over all banks.
+// Padded FFT buffers hold element i at i + i/16: the strided stores of the early stages
+// then spread over the banks.
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int fpad_len(int H) { return H + H / 16; }
 
@@ -445,8 +445,8 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 
 // ---------------------------------------------------------------------------------
 // Fused front end: one CTA per frame runs the STFT + PHAT of every channel (the
-// half-length transform of stft_phat_kernel as a radix-4 Stockham FFT, channel groups of
-// N/8 threads) into shared memory, then either samples every pair (the matrix form of
+// half-length transform of stft_phat_kernel on the mixed-radix FFT, channel groups of
+// N/16 threads) into shared memory, then either samples every pair (the matrix form of
 // Eq. xi_p_ifft as a per-frame GEMM on the warp-level tensor cores) and writes the operand
 // the interpolation contraction needs -- xi in FP32 [F][L] (FP32 SSPI gather), xi in the
 // operand type [F][Lpad] (tensor-core SI / TD / SSPI), or u = Lambda_fat xi (SLRI, a second
