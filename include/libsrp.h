@@ -143,7 +143,8 @@ typedef struct {
  *   SRP_SLRI: Lambda (Eq. Lambda_p) -> its best rank-R approximation (Eq.
  *             min_Lambda_lr) from the eigen-decomposition of Lambda^T Lambda in FP64
  *             (L <= 768: Jacobi on the Gram matrix; longer: subspace iteration with
- *             Rayleigh-Ritz whose products Lambda X, Lambda^T Y run on the device in FP64),
+ *             Rayleigh-Ritz whose products Lambda X, Lambda^T Y run on the device, in FP32
+ *             until the Ritz values settle and then in FP64 to 1e-13 relative),
  *             Lambda_fat = V_R^T, Lambda_tall = Lambda V_R, stored FP32;
  *   SRP_SSPI: the Q_Lambda largest-magnitude entries of Lambda (Eq. min_Lambda_sp),
  *             magnitudes quantised to multiples of 2^-40 and ties broken by ascending
@@ -202,10 +203,15 @@ srp_status srp_map(srp_plan_t plan, const float* frames, int F, float* maps, int
 
 /*
  * srp_map_host -- srp_map on host buffers: copies frames host->device into plan-owned
- * staging, runs srp_map, copies maps (and argmax) device->host, and synchronises
+ * staging, runs the path, copies maps (and argmax) device->host, and synchronises
  * `stream` before returning.  frames: host float [F][M][N]; maps: host float [F][J];
- * argmax: host int32 [F] or NULL.  The staging buffers (max_frames frames and maps)
- * are allocated on the first call and kept by the plan.
+ * argmax: host int32 [F] or NULL (page-locked host memory gives the full link rate).  Each
+ * chunk of max_frames frames is processed in sub-batches of whole 128-frame tiles: the
+ * frames of one sub-batch come in on a plan-owned copy stream and the maps of the
+ * previous ones leave on two others while `stream` computes, ordered with events.  The
+ * staging buffers (max_frames frames and maps), the three copy streams and their events
+ * are created on the first call and kept by the plan; calls on one plan must not overlap.
+ * Errors: as srp_map.
  */
 srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, float* maps, int* argmax,
                         void* stream);
