@@ -1008,12 +1008,20 @@ extern "C" srp_status srp_plan_create_from_file(const srp_plan_desc* desc, const
     r.vec(fit.row_ptr, static_cast<uint64_t>(J) + 1);
     r.vec(fit.col, static_cast<uint64_t>(fit.nnz));
     r.vec(fit.val, static_cast<uint64_t>(fit.nnz));
-    if (r.ok && (fit.row_ptr.front() != 0 || fit.row_ptr.back() != fit.nnz)) r.ok = false;
+    // the taps index device buffers: rows must be well formed and columns inside [0, L)
+    if (r.ok && (fit.nnz < 0 || fit.row_ptr.front() != 0 || fit.row_ptr.back() != fit.nnz))
+      r.ok = false;
+    for (size_t i = 1; r.ok && i < fit.row_ptr.size(); ++i)
+      if (fit.row_ptr[i] < fit.row_ptr[i - 1]) r.ok = false;
+    for (size_t t = 0; r.ok && t < fit.col.size(); ++t)
+      if (fit.col[t] < 0 || fit.col[t] >= L) r.ok = false;
   } else if (method == SRP_LR) {
     const int D = P * (g.K - 1);
     r.vec(fit.ht, static_cast<uint64_t>(J) * R);
     r.vec(fit.hf, static_cast<uint64_t>(R) * D);
   }
+  if (r.ok && (method == SRP_SLRI || method == SRP_LR) && (R != desc->rank || fit.sigma.empty()))
+    r.ok = false;
   if (!r.ok || r.pos != r.buf.size()) return fail(SRP_EINVAL, "plan file contents do not match its header");
   return create_plan(desc, stream, out, &fit);
 }
