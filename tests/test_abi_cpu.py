@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import synth
+from paper_2306_08514_gb300._abi import METHODS as M_
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -143,3 +144,67 @@ def test_plan_file_is_checked_before_any_gpu_work(S, tmp_path):
     damaged = tmp_path / "damaged.plan"
     damaged.write_bytes(good_sum[:-1] + bytes([good_sum[-1] ^ 1]))
     refused(damaged, "checksum")
+
+
+def _fit_inputs_hash(S, desc, mics, grid):
+    """The hash srp_plan_save stores: FNV-1a 64 over the fields the fit depends on, in the
+    order and widths of srp_plan_desc (int32 / float64, little-endian)."""
+    import struct
+    sspi = desc.method == M_["sspi"]
+    lowrank = desc.method in (M_["slri"], M_["lr"])
+    b = struct.pack("<i", desc.M) + np.ascontiguousarray(mics, "<f8").tobytes()
+    b += struct.pack("<i", desc.J) + np.ascontiguousarray(grid, "<f8").tobytes()
+    b += struct.pack("<did", desc.fs, desc.N, desc.c)
+    b += struct.pack("<iii", desc.n_aux, desc.method, desc.rank if lowrank else 0)
+    b += struct.pack("<di", desc.taps_per_loc_pair if sspi else 0.0, desc.far_field)
+    return _fnv1a64(b)
+
+
+def test_plan_file_with_bad_sspi_taps_is_refused_before_any_gpu_work(S, tmp_path):
+    """An SSPI plan file whose header, input hash and checksum are all right but whose taps
+    would index outside the device buffers (a column outside [0, L), row pointers out of
+    order, a row range that does not cover the taps) is refused on the host."""
+    import struct
+    mics = synth.mics_square()
+    grid = synth.grid_plane((0, 0), (4, 4), (10, 10))
+    desc = S.make_desc(mics, grid, 16000.0, 512, method="sspi", taps=1.0)
+    J, M = grid.shape[0], mics.shape[0]
+    pairs = [(m, mp) for mp in range(M - 1) for m in range(mp + 1, M)]
+    Np = [int(np.floor(np.sqrt(((mics[m] - mics[mp]) ** 2).sum()) / desc.c * desc.fs)) + desc.n_aux
+          for m, mp in pairs]
+    P, L = len(pairs), sum(2 * n + 1 for n in Np)
+    h = _fit_inputs_hash(S, desc, mics, grid)
+
+    def plan_file(name, row_ptr, col, nnz=None, tail=b""):
+        row_ptr = np.asarray(row_ptr, "<i8")
+        col = np.asarray(col, "<i4")
+        nnz = len(col) if nnz is None else nnz
+        body = b"SRPPLAN\0" + struct.pack("<IiQ", 1, M_["sspi"], h)
+        body += struct.pack("<iiii", J, P, L, 0) + struct.pack("<qq", nnz, 0)
+        for a in (row_ptr, col, np.ones(len(col), "<f4")):
+            body += struct.pack("<Q", a.size) + a.tobytes()
+        body += tail
+        path = tmp_path / name
+        path.write_bytes(body + struct.pack("<Q", _fnv1a64(body)))
+        return path
+
+    rows = np.arange(J + 1)  # one tap per location
+    cols = np.arange(J) % L
+    # control: the unflawed file passes every file check (without a GPU the plan then fails
+    # at its first CUDA call; with one it is created)
+    try:
+        S.srp_destroy(S.srp_plan_create_from_file(desc, plan_file("ok.plan", rows, cols)))
+    except S.SrpError as e:
+        assert e.status != S.SRP_EINVAL and "plan file" not in str(e), str(e)
+    for name, args in [
+        ("col_high", (rows, np.where(np.arange(J) == 7, L, cols))),
+        ("col_negative", (rows, np.where(np.arange(J) == 0, -1, cols))),
+        ("rows_unordered", (np.where(np.arange(J + 1) == 5, 9, rows), cols)),
+        ("rows_start", (rows + 1, cols)),
+        ("rows_short", (np.minimum(rows, J - 1), cols)),
+        ("trailing", (rows, cols, None, b"\0\0\0\0")),
+    ]:
+        with pytest.raises(S.SrpError) as e:
+            S.srp_plan_create_from_file(desc, plan_file(name + ".plan", *args))
+        assert e.value.status == S.SRP_EINVAL
+        assert "contents do not match its header" in str(e.value), (name, str(e.value))
