@@ -208,3 +208,23 @@ def test_plan_file_with_bad_sspi_taps_is_refused_before_any_gpu_work(S, tmp_path
             S.srp_plan_create_from_file(desc, plan_file(name + ".plan", *args))
         assert e.value.status == S.SRP_EINVAL
         assert "contents do not match its header" in str(e.value), (name, str(e.value))
+
+
+def test_header_serves_a_plain_c_program(S, tmp_path):
+    """include/libsrp.h compiles as strict C99 and C11 (no C++ in the interface), and a C
+    program linked against libsrp.so alone sizes a plan and gets the documented host-side
+    argument checks (tests/abi_consumer.c; no call needs a GPU)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = os.path.join(ROOT, "tests", "abi_consumer.c")
+    lib_dir = os.path.dirname(S.LIB_PATH)
+    for std in ("c99", "c11"):
+        exe = str(tmp_path / f"consumer_{std}")
+        subprocess.run([gcc, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), src, "-o", exe, S.LIB_PATH,
+                        f"-Wl,-rpath,{lib_dir}"], check=True, capture_output=True)
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+        assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
