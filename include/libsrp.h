@@ -95,7 +95,8 @@ typedef enum {
 typedef struct {
   int M;                    /* number of microphones, 2..64 */
   const double* mic_xyz;    /* [M][3] microphone positions r_m in metres */
-  int J;                    /* number of candidate locations, >= 1 */
+  int J;                    /* number of candidate locations, 1..67107840 (SRP_FP32:
+                               1..8388480) */
   const double* grid_xyz;   /* [J][3] candidate locations q_i in metres (near field,
                                Eq. Deltat_i first case), or unit vectors (far_field) */
   double fs;                /* sampling rate 1/T in Hz, > 0 */

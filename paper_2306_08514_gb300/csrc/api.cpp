@@ -32,7 +32,11 @@ srp_status validate(const srp_plan_desc* d) {
   if (!d) return fail(SRP_EINVAL, "desc is NULL");
   if (d->M < 2 || d->M > 64) return fail(SRP_EINVAL, "M must be in 2..64");
   if (!d->mic_xyz) return fail(SRP_EINVAL, "mic_xyz is NULL");
-  if (d->J < 1) return fail(SRP_EINVAL, "J must be >= 1");
+  // the split-K reduction covers 1024 cells per block row and the FP32 FFMA GEMM 128, with
+  // at most 65535 block rows (checked before grid_xyz is read)
+  if (d->J < 1 || d->J > 65535 * 1024) return fail(SRP_EINVAL, "J must be in 1..67107840");
+  if (d->precision == SRP_FP32 && d->J > 65535 * 128)
+    return fail(SRP_EINVAL, "SRP_FP32 plans take J <= 8388480 (use a tensor-core precision)");
   if (!d->grid_xyz) return fail(SRP_EINVAL, "grid_xyz is NULL");
   if (!(d->fs > 0) || !std::isfinite(d->fs)) return fail(SRP_EINVAL, "fs must be > 0");
   if (!is_pow2(d->N) || d->N < 256 || d->N > 2048)

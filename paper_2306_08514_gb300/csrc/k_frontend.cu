@@ -227,9 +227,20 @@ __global__ __launch_bounds__(256) void stft_phat_kernel(const float* __restrict_
   }
 }
 
+// Launches that index frames by blockIdx.y take at most kMaxGridY frames each; longer
+// batches are issued as consecutive launches on offset base pointers.
+constexpr int kMaxGridY = 65535;
+
 cudaError_t launch_stft_phat(const float* frames, int F, int M, int N, const float* window,
                              const float2* twiddle, float2* yhat, cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
+  if (F > kMaxGridY) {
+    const cudaError_t e = launch_stft_phat(frames, kMaxGridY, M, N, window, twiddle, yhat, s);
+    if (e != cudaSuccess) return e;
+    const size_t f0 = kMaxGridY;
+    return launch_stft_phat(frames + f0 * M * N, F - kMaxGridY, M, N, window, twiddle,
+                            yhat + f0 * M * (N / 2), s);
+  }
   const int H = N / 2, Tg = H / 8;
   const int cpb = 256 / Tg;  // channels per block
   dim3 block(Tg, cpb);
@@ -305,6 +316,16 @@ cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, c
                                OpType t, void* out, void* out_lo, int out_cols, cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
   if (out_cols < L) return cudaErrorInvalidValue;
+  if (F > kMaxGridY) {
+    cudaError_t e = launch_gcc_samples(yhat, kMaxGridY, M, P, N, pairs, Np, off, L, twiddle, t,
+                                       out, out_lo, out_cols, s);
+    if (e != cudaSuccess) return e;
+    const size_t f0 = kMaxGridY, rows = f0 * out_cols * op_bytes(t);
+    char* hi = static_cast<char*>(out) + rows;
+    char* lo = out_lo ? static_cast<char*>(out_lo) + rows : nullptr;
+    return launch_gcc_samples(yhat + f0 * M * (N / 2), F - kMaxGridY, M, P, N, pairs, Np, off,
+                              L, twiddle, t, hi, lo, out_cols, s);
+  }
   dim3 grid((P + 1) / 2, F);
   const int ot = static_cast<int>(t);
   switch (N) {

@@ -64,6 +64,20 @@ def test_invalid_desc_is_rejected_on_the_host(S, bad):
     assert S.srp_last_error()
 
 
+@pytest.mark.parametrize("J,precision", [(65535 * 1024 + 1, "bf16"), (65535 * 128 + 1, "fp32")])
+def test_grid_larger_than_the_launch_grids_is_rejected(S, J, precision):
+    """J beyond what the map kernels' grids cover (65535 block rows of 1024 cells, or 128 for
+    the FP32 FFMA GEMM) is refused before grid_xyz is read, so a small array serves here."""
+    mics = synth.mics_square()
+    grid = synth.grid_plane((0, 0), (4, 4), (5, 5))
+    d = S.make_desc(mics, grid, 16000.0, 512, precision=precision)
+    d.J = J
+    for call in (lambda: S.srp_plan_create(d, None), lambda: S.srp_plan_estimate_bytes(d)):
+        with pytest.raises(S.SrpError) as e:
+            call()
+        assert e.value.status == S.SRP_EINVAL and "J" in str(e.value)
+
+
 def test_window_wider_than_frame_is_rejected(S):
     mics = synth.mics_square() * 40.0
     grid = synth.grid_plane((0, 0), (4, 4), (5, 5))
