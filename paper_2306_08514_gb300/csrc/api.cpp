@@ -508,7 +508,7 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
     }
     if (ws_floats > 0) SRP_ALLOC(p, p->d_split, sizeof(float) * ws_floats);
     double* d_tau = nullptr;
-    if (cudaMalloc(&d_tau, sizeof(double) * g.tau.size()) != cudaSuccess) {
+    if (device_alloc(reinterpret_cast<void**>(&d_tau), sizeof(double) * g.tau.size()) != cudaSuccess) {
       cudaGetLastError();
       set_error("cudaMalloc for the TDOA table failed");
       free_plan(p);
@@ -577,7 +577,7 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
       }
     float* d_tmp = nullptr;
     const size_t tmp_n = std::max(b1.size(), b2.size());
-    if (cudaMalloc(&d_tmp, sizeof(float) * tmp_n) != cudaSuccess) {
+    if (device_alloc(reinterpret_cast<void**>(&d_tmp), sizeof(float) * tmp_n) != cudaSuccess) {
       cudaGetLastError();
       free_plan(p);
       return fail(SRP_ENOMEM, "LR factor staging");
@@ -756,8 +756,8 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
         if (split) SRP_ALLOC(p, p->d_B_lo, static_cast<size_t>(g.J) * Lpad * eb);
         double* d_tau = nullptr;
         int* d_cols = nullptr;
-        cudaError_t e = cudaMalloc(&d_tau, sizeof(double) * g.tau.size());
-        if (e == cudaSuccess) e = cudaMalloc(&d_cols, sizeof(int) * 2 * g.L);
+        cudaError_t e = device_alloc(reinterpret_cast<void**>(&d_tau), sizeof(double) * g.tau.size());
+        if (e == cudaSuccess) e = device_alloc(reinterpret_cast<void**>(&d_cols), sizeof(int) * 2 * g.L);
         if (e == cudaSuccess)
           e = cudaMemcpyAsync(d_tau, g.tau.data(), sizeof(double) * g.tau.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
@@ -774,7 +774,7 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
           cudaGetLastError();
           set_error(std::string("interpolation operand: ") + cudaGetErrorString(e));
           free_plan(p);
-          return SRP_ECUDA;
+          return e == cudaErrorMemoryAllocation ? SRP_ENOMEM : SRP_ECUDA;
         }
         if (desc->method == SRP_TD && p->op != OpType::F32) {
           add_lists([&](int i, std::vector<char>& used) {
@@ -1135,7 +1135,8 @@ extern "C" srp_status srp_map(srp_plan_t plan, const float* frames, int F, float
   float* sink = nullptr;  // estimates only on the FP32 kernels: maps go to plan scratch
   if (!maps && plan->op == OpType::F32) {
     if (!plan->d_est_maps) {
-      if (cudaMalloc(&plan->d_est_maps, sizeof(float) * plan->Fmax * static_cast<size_t>(g.J)) != cudaSuccess) {
+      if (device_alloc(reinterpret_cast<void**>(&plan->d_est_maps),
+                       sizeof(float) * plan->Fmax * static_cast<size_t>(g.J)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SRP_ENOMEM, "estimate-only scratch allocation failed");
       }
@@ -1167,9 +1168,9 @@ extern "C" srp_status srp_map_host(srp_plan_t plan, const float* frames, int F, 
     void* a = nullptr;
     void* b = nullptr;
     void* c = nullptr;
-    if (cudaMalloc(&a, sizeof(float) * Fm * g.M * g.N) != cudaSuccess ||
-        cudaMalloc(&b, sizeof(float) * Fm * g.J) != cudaSuccess ||
-        cudaMalloc(&c, sizeof(int) * Fm) != cudaSuccess) {
+    if (device_alloc(&a, sizeof(float) * Fm * g.M * g.N) != cudaSuccess ||
+        device_alloc(&b, sizeof(float) * Fm * g.J) != cudaSuccess ||
+        device_alloc(&c, sizeof(int) * Fm) != cudaSuccess) {
       cudaGetLastError();
       if (a) cudaFree(a);
       if (b) cudaFree(b);
@@ -1248,13 +1249,15 @@ extern "C" srp_status srp_stream_push(srp_plan_t plan, const float* hops, int B,
     for (int k = 0; k < 2; ++k) {
       if (plan->d_hist[k]) cudaFree(plan->d_hist[k]);
       plan->d_hist[k] = nullptr;
-      if (cudaMalloc(&plan->d_hist[k], sizeof(float) * std::max<size_t>(1, g.M * Hn)) != cudaSuccess) {
+      if (device_alloc(reinterpret_cast<void**>(&plan->d_hist[k]),
+                       sizeof(float) * std::max<size_t>(1, g.M * Hn)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SRP_ENOMEM, "stream history allocation failed");
       }
     }
     if (!plan->d_stream_frames &&
-        cudaMalloc(&plan->d_stream_frames, sizeof(float) * plan->Fmax * g.M * g.N) != cudaSuccess) {
+        device_alloc(reinterpret_cast<void**>(&plan->d_stream_frames),
+                     sizeof(float) * plan->Fmax * g.M * g.N) != cudaSuccess) {
       cudaGetLastError();
       return fail(SRP_ENOMEM, "stream frame staging allocation failed");
     }
@@ -1306,8 +1309,8 @@ extern "C" srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream,
   plan->profiling = false;
   const int saved = plan->tc_variant;
   const long long launches = plan->launches;
-  if (cudaMalloc(&d_frames, sizeof(float) * F * g.M * g.N) != cudaSuccess ||
-      cudaMalloc(&d_maps, sizeof(float) * F * static_cast<size_t>(g.J)) != cudaSuccess) {
+  if (device_alloc(reinterpret_cast<void**>(&d_frames), sizeof(float) * F * g.M * g.N) != cudaSuccess ||
+      device_alloc(reinterpret_cast<void**>(&d_maps), sizeof(float) * F * static_cast<size_t>(g.J)) != cudaSuccess) {
     cudaGetLastError();
     st = fail(SRP_ENOMEM, "autotune buffers");
   }

@@ -182,6 +182,17 @@ struct DevBuf {
   }
 };
 
+// Fit scratch comes from device_alloc like every plan buffer (so the allocation-failure
+// hook reaches it); a failed allocation is SRP_ENOMEM.
+#define SRP_FIT_ALLOC(buf, bytes)                                                 \
+  do {                                                                            \
+    if (device_alloc(&(buf).p, (bytes)) != cudaSuccess) {                         \
+      cudaGetLastError();                                                         \
+      ::srp::set_error("fit scratch allocation of " + std::to_string(bytes) + " bytes failed"); \
+      return SRP_ENOMEM;                                                          \
+    }                                                                             \
+  } while (0)
+
 template <int KT>
 srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
                    std::vector<float>& fat, std::vector<double>& sigma, cudaStream_t s) {
@@ -197,12 +208,12 @@ srp_status run_fit(const Geometry& g, int R, int k, std::vector<float>& tall,
   const int nsplit = (J + rows_per_split - 1) / rows_per_split;
   DevBuf d_tau, d_s, d_cols, d_X, d_Y, d_Z;
   const size_t JP = static_cast<size_t>(J) * P;
-  SRP_CUDA_TRY(cudaMalloc(&d_tau.p, JP * 8));
-  SRP_CUDA_TRY(cudaMalloc(&d_s.p, JP * 8));
-  SRP_CUDA_TRY(cudaMalloc(&d_cols.p, sizeof(int) * 2 * L));
-  SRP_CUDA_TRY(cudaMalloc(&d_X.p, sizeof(double) * L * KT));
-  SRP_CUDA_TRY(cudaMalloc(&d_Y.p, sizeof(double) * static_cast<size_t>(J) * KT));
-  SRP_CUDA_TRY(cudaMalloc(&d_Z.p, sizeof(double) * static_cast<size_t>(nsplit) * L * KT));
+  SRP_FIT_ALLOC(d_tau, JP * 8);
+  SRP_FIT_ALLOC(d_s, JP * 8);
+  SRP_FIT_ALLOC(d_cols, sizeof(int) * 2 * L);
+  SRP_FIT_ALLOC(d_X, sizeof(double) * L * KT);
+  SRP_FIT_ALLOC(d_Y, sizeof(double) * static_cast<size_t>(J) * KT);
+  SRP_FIT_ALLOC(d_Z, sizeof(double) * static_cast<size_t>(nsplit) * L * KT);
   auto* tau = static_cast<double*>(d_tau.p);
   auto* stau = static_cast<double*>(d_s.p);
   auto* cols = static_cast<int*>(d_cols.p);
@@ -565,10 +576,10 @@ srp_status run_lr_fit(const Geometry& g, int R, int k, std::vector<cplx>& tall,
   const int nsplit = (J + rows_per_split - 1) / rows_per_split;
   DevBuf d_tau, d_X, d_Y, d_Z;
   const size_t JP = static_cast<size_t>(J) * P;
-  SRP_CUDA_TRY(cudaMalloc(&d_tau.p, JP * 8));
-  SRP_CUDA_TRY(cudaMalloc(&d_X.p, sizeof(double2) * static_cast<size_t>(D) * KT));
-  SRP_CUDA_TRY(cudaMalloc(&d_Y.p, sizeof(double2) * static_cast<size_t>(J) * KT));
-  SRP_CUDA_TRY(cudaMalloc(&d_Z.p, sizeof(double2) * static_cast<size_t>(nsplit) * D * KT));
+  SRP_FIT_ALLOC(d_tau, JP * 8);
+  SRP_FIT_ALLOC(d_X, sizeof(double2) * static_cast<size_t>(D) * KT);
+  SRP_FIT_ALLOC(d_Y, sizeof(double2) * static_cast<size_t>(J) * KT);
+  SRP_FIT_ALLOC(d_Z, sizeof(double2) * static_cast<size_t>(nsplit) * D * KT);
   auto* tau = static_cast<double*>(d_tau.p);
   SRP_CUDA_TRY(cudaMemcpyAsync(tau, g.tau.data(), JP * 8, cudaMemcpyHostToDevice, s));
   std::vector<cplx> Xh(static_cast<size_t>(D) * KT), Zp(static_cast<size_t>(nsplit) * D * KT);
