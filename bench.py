@@ -164,32 +164,34 @@ class OracleRefs:
         self.tall, self.fat, _ = O.slri_factors(self.Lam, R)
         self.Lsp = O.sspi_matrix(self.Lam, self.lags, int(round(t * self.Lam.shape[0] * len(self.lags))))
 
-    def maps(self, method, frames):
-        """The oracle's maps of `method` for `frames`, or None where the oracle's factors are
-        out of reach at this size (LR-SRP needs the SVD of the whole SRP matrix)."""
+    def maps(self, method, frames, cells=slice(None)):
+        """The oracle's maps of `method` for `frames` on the grid cells `cells` (all by
+        default), or None where the oracle's factors are out of reach at this size (LR-SRP
+        needs the SVD of the whole SRP matrix)."""
         O = self.O
         psi = O.gcc_phat(O.stft(frames, "hann"))
         if method == "conv":
-            return O.srp_conv(psi, self.dt, self.fs)
+            return O.srp_conv(psi, self.dt[cells], self.fs)
         if method == "lr":
             return None
         xi, _ = O.gcc_samples_ifft(psi, self.lags, self.K)
         if method == "slri":
-            return O.srp_slri(self.tall, self.fat, xi)
+            return O.srp_slri(self.tall[cells], self.fat, xi)
         if method == "si":
-            return O.srp_si(self.Lam, xi)
+            return O.srp_si(self.Lam[cells], xi)
         if method == "td":
-            return xi @ O.td_matrix(self.dt, self.fs, self.lags).T
-        return O.srp_sspi(self.Lsp, xi)
+            return xi @ O.td_matrix(self.dt[cells], self.fs, self.lags).T
+        return O.srp_sspi(self.Lsp[cells], xi)
 
 
-def cpu_baseline(refs, frames):
+def cpu_baseline(refs, frames, stride=1):
     """The FP64 oracle as it stands: per-frame work of all three methods on a bounded
-    sample (every grid cell); plan-time fits are excluded like the GPU's."""
+    sample (every `stride`-th grid cell); plan-time fits are excluded like the GPU's."""
+    cells = slice(None, None, stride)
     t0 = time.perf_counter()
-    out = {m: refs.maps(m, frames) for m in ("conv", "slri", "sspi")}
+    out = {m: refs.maps(m, frames, cells) for m in ("conv", "slri", "sspi")}
     el = time.perf_counter() - t0
-    J = refs.w["grid_xyz"].shape[0]
+    J = len(range(refs.w["grid_xyz"].shape[0])[cells])
     try:
         import threadpoolctl
         cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
@@ -197,9 +199,30 @@ def cpu_baseline(refs, frames):
         cores = os.cpu_count()
     n = frames.shape[0]
     return out, {"value": 3 * J * n / el, "unit": UNIT, "cores": int(cores), "kind": "oracle",
-                 "sample": f"{n} frame(s) x {J} cells x 3 methods (FP64 conv H, SLRI, SSPI "
-                           f"from the oracle's factors); plan-time SVD/selection excluded",
+                 "sample": f"{n} frame(s) x {J} cells"
+                           + (f" (1 in {stride} of the grid)" if stride > 1 else "")
+                           + " x 3 methods (FP64 conv H, SLRI, SSPI from the oracle's factors);"
+                             " plan-time SVD/selection excluded",
                  "seconds": el}
+
+
+REF_FULL_STEPS = 12
+
+
+def arm_methods(a):
+    methods = [m for m in a.methods.split(",") if m]
+    return methods, {m: getattr(a, f"{m}_precision", None) or a.precision for m in methods}
+
+
+def workload_config(a, M, J, N, F, methods, prec):
+    """The benchmark's `config`, shared by both arms (the reference arm times the same
+    workload on a bounded sample of it)."""
+    return {"workload": f"{a.workload}: M={M}, J={J}, N={N} Hann, F={F} frames/step/rank; "
+                        + ", ".join(f"{m} {prec[m]}" for m in methods)
+                        + f" (SLRI R={a.rank}, SSPI t={a.taps})",
+            "maps_per_frame": len(methods),
+            "l2": "flushed before every step (512 MB write, outside the timed events)"
+            if not a.no_flush else "not flushed"}
 
 
 def run_reference(a):
@@ -207,13 +230,20 @@ def run_reference(a):
     if rank != 0:
         return
     import synth
-    w = synth.workload(a.workload, F=max(4, a.warmup + a.steps))
+    w = synth.workload(a.workload, F=a.frames)  # the libsrp arm's workload (rank 0)
+    methods, prec = arm_methods(a)
+    config = workload_config(a, w["mic_xyz"].shape[0], w["grid_xyz"].shape[0], w["N"], w["F"],
+                             methods, prec)
     refs = OracleRefs(w, a.rank, a.taps)
-    J = w["grid_xyz"].shape[0]
+    # a bounded run: beyond REF_FULL_STEPS steps, each step takes every stride-th cell, so
+    # the whole run does about REF_FULL_STEPS full frames of work (about 2 min on 8 cores)
+    stride = max(1, -(-(a.warmup + a.steps) // REF_FULL_STEPS))
+    J = len(range(w["grid_xyz"].shape[0])[::stride])
     times = []
     r = None
     for s in range(a.warmup + a.steps):
-        _, r = cpu_baseline(refs, w["frames"][s:s + 1])
+        f = s % w["F"]
+        _, r = cpu_baseline(refs, w["frames"][f:f + 1], stride)
         if s >= a.warmup:
             times.append(r["seconds"])
     ms = 1e3 * float(np.mean(times))
@@ -221,9 +251,9 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{a.workload}: 1 frame per step, all 3 methods, FP64 oracle on host"},
+           "config": config,
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                            "sample": r["sample"]},
+                            "sample": "per step: " + r["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -286,8 +316,7 @@ def run_libsrp(a):
     w = synth.workload(a.workload, F=a.frames, seed=None if rank == 0 else shard_seed(1002, rank))
     F, J, N, M = w["F"], w["grid_xyz"].shape[0], w["N"], w["mic_xyz"].shape[0]
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], N)
-    methods = [m for m in a.methods.split(",") if m]
-    prec = {m: getattr(a, f"{m}_precision", None) or a.precision for m in methods}
+    methods, prec = arm_methods(a)
     kw = {"conv": dict(method="conv"), "slri": dict(method="slri", rank=a.rank),
           "sspi": dict(method="sspi", taps=a.taps), "si": dict(method="si"),
           "td": dict(method="td"), "lr": dict(method="lr", rank=a.rank)}
@@ -419,12 +448,7 @@ def run_libsrp(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "/".join(sorted(set(prec.values()))), "data": "synthetic",
-        "config": {"workload": f"{a.workload}: M={M}, J={J}, N={N} Hann, F={F} frames/step/rank; "
-                               + ", ".join(f"{m} {prec[m]}" for m in methods)
-                               + f" (SLRI R={a.rank}, SSPI t={a.taps})",
-                   "maps_per_frame": len(methods),
-                   "l2": "flushed before every step (512 MB write, outside the timed events)"
-                   if not a.no_flush else "not flushed"},
+        "config": workload_config(a, M, J, N, F, methods, prec),
         "wall_ms_per_step": 1e3 * wall / a.steps,
         "methods": per,
         "autotune": tuned,
