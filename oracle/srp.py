@@ -6,7 +6,7 @@ m > m', J candidate locations, DFT length 2K, one-sided bins k = 1..K-1, samplin
 period T = 1/fs.  Arrays are 0-based; the paper's 1-based "mod[.]+1" indices become
 plain "mod[.]".
 
-Readings of points where the paper is silent (each is listed in the design doc):
+Readings of points where the paper is silent (both this oracle and the CUDA library take them):
 * sinc(x) = sin(pi x)/(pi x), sinc(0) = 1 (Whittaker-Shannon, Eq. SRPinterp).
 * The iFFT is the unnormalised inverse DFT, i.e. 2K * numpy.fft.ifft (Eq. xi_p_ifft,
   which must equal S-bar times psi-bar, Appendix).
