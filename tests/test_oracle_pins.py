@@ -85,6 +85,26 @@ def test_stft_shift_theorem():
         assert np.max(np.abs(got - expect)) < 1e-10
 
 
+def test_hann_window_closed_form():
+    """Reading 4 (periodic Hann): the N-point DFT of 0.5 - 0.5 cos(2 pi n / N) is N/2 at
+    k = 0, -N/4 at k = +-1 and zero elsewhere, so the windowed DFT is the three-tap
+    modulation 0.5 X[k] - 0.25 X[k-1] - 0.25 X[k+1] of the plain DFT X (numpy's full FFT,
+    a library routine).  The square-root Hann window squares to the Hann window."""
+    for N in (256, 512, 1024):
+        Wk = np.fft.fft(O.analysis_window(N, "hann"))
+        expect = np.zeros(N, dtype=np.complex128)
+        expect[0], expect[1], expect[-1] = N / 2, -N / 4, -N / 4
+        assert np.max(np.abs(Wk - expect)) <= 1e-10 * N
+        sq = O.analysis_window(N, "sqrt-hann")
+        assert np.all(sq >= 0) and np.allclose(sq ** 2, O.analysis_window(N, "hann"), atol=1e-15)
+    x = synth.rng(17).standard_normal((2, 3, 512))
+    X = np.fft.fft(x, axis=-1)
+    Y = O.stft(x, "hann")
+    k = np.arange(257)
+    mod = 0.5 * X[..., k] - 0.25 * X[..., (k - 1) % 512] - 0.25 * X[..., (k + 1) % 512]
+    assert np.max(np.abs(Y - mod)) <= 1e-12 * np.max(np.abs(X))
+
+
 # ---------------------------------------------------------------- P1: DSB identity
 @pytest.mark.parametrize("case", ["sq", "uca"])
 def test_P1_conv_equals_delay_and_sum_power(case, request):
@@ -171,6 +191,9 @@ def test_P3_integer_lag_equals_conv_pair_term(sq):
         off = sum(len(l) for l in lags[:p])
         col = [off + list(lags[p]).index(n) for n in n_int]
         assert np.allclose(zc, xi[:, col], rtol=0, atol=1e-10 * np.max(np.abs(xi)))
+        blk = slice(off, off + len(lags[p]))  # SI-SRP of this pair alone picks the same sample
+        assert np.allclose(O.srp_si(Lam[:, blk], xi[:, blk]), zc, rtol=0,
+                           atol=1e-10 * np.max(np.abs(xi)))
 
 
 def test_P4_hermitian_symmetry(uca):
@@ -395,6 +418,26 @@ def test_P9_paper_worked_numbers():
     for key, val in (("C_samp_ifft", "C_rel_samp"), ("C_td", "C_rel_td"), ("C_lr", "C_rel_lr"),
                      ("C_si", "C_rel_si"), ("C_slri", "C_rel_slri"), ("C_sspi", "C_rel_sspi")):
         assert math.isclose(c[key] / C, tf[val], rel_tol=1e-12), key
+
+
+# ---------------------------------------------------------------- estimate and measures
+def test_argmax_takes_the_lowest_index_on_ties():
+    """Reading of Eq. (imax) for tied maxima: the lowest location index."""
+    z = np.array([[0.0, 3.0, 1.0, 3.0], [5.0, 5.0, 5.0, 5.0], [-2.0, -1.0, -1.0, -3.0]])
+    assert list(O.argmax_map(z)) == [1, 0, 1]
+
+
+def test_error_measures_closed_forms():
+    """Sec. V-A measures on maps with a known error: a map scaled by (1 + e) is
+    10 log10(e^2) dB and e relative away from the original; orthogonal errors add."""
+    z = synth.rng(23).standard_normal((4, 300))
+    for e in (1e-1, 1e-3, 1e-6):
+        assert math.isclose(O.eps_db((1 + e) * z, z), 20.0 * math.log10(e), abs_tol=1e-6)
+        assert np.allclose(O.rel_err((1 + e) * z, z), e, rtol=1e-6)
+    a = np.zeros((1, 4))
+    ref = np.array([[3.0, 0.0, 0.0, 0.0]])
+    a[0, 0], a[0, 1] = 3.0, 4.0  # error (0, 4): ||e|| / ||ref|| = 4 / 3
+    assert math.isclose(O.rel_err(a, ref)[0], 4.0 / 3.0, rel_tol=1e-15)
 
 
 # ---------------------------------------------------------------- P10: truncation
