@@ -84,7 +84,8 @@ class Clocks:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
         self.proc = None
         self.index = index
 
@@ -99,6 +100,10 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            if getattr(self, "f", None):
+                self.f.close()
+            if os.path.exists(self.path):
+                os.unlink(self.path)
             return None
         self.proc.terminate()
         try:
