@@ -214,6 +214,13 @@ def cpu_baseline(refs, frames, stride=1):
 REF_FULL_STEPS = 12
 
 
+def reference_stride(warmup: int, steps: int) -> int:
+    """Grid-cell stride of the reference arm: up to REF_FULL_STEPS warm-up plus timed steps
+    take every cell; longer runs take one cell in ceil((W + K) / REF_FULL_STEPS) per step,
+    so the whole run does about REF_FULL_STEPS frames of full work."""
+    return max(1, -(-(warmup + steps) // REF_FULL_STEPS))
+
+
 def arm_methods(a):
     methods = [m for m in a.methods.split(",") if m]
     return methods, {m: getattr(a, f"{m}_precision", None) or a.precision for m in methods}
@@ -242,7 +249,7 @@ def run_reference(a):
     refs = OracleRefs(w, a.rank, a.taps)
     # a bounded run: beyond REF_FULL_STEPS steps, each step takes every stride-th cell, so
     # the whole run does about REF_FULL_STEPS full frames of work (about 2 min on 8 cores)
-    stride = max(1, -(-(a.warmup + a.steps) // REF_FULL_STEPS))
+    stride = reference_stride(a.warmup, a.steps)
     J = len(range(w["grid_xyz"].shape[0])[::stride])
     times = []
     r = None
