@@ -58,6 +58,8 @@ PIN_CALLS = {
     "argmax": lambda fx: PINS.test_argmax_takes_the_lowest_index_on_ties(),
     "measures": lambda fx: PINS.test_error_measures_closed_forms(),
     "P10": lambda fx: PINS.test_P10_si_error_shrinks_with_aux_samples(fx.getfixturevalue("sq")),
+    "ff": lambda fx: PINS.test_tdoa_ff_is_nf_limit(),
+    "lr_rank": lambda fx: PINS.test_lr_rank_R_is_the_best_approximation(fx.getfixturevalue("sq")),
 }
 
 
@@ -198,6 +200,32 @@ def _two_sided_no_conj(psi_p, K):
     return out
 
 
+def _tdoa_ff_sign(mic_xyz, dirs, c=340.0):
+    return -O.srp.__dict__["_orig_tdoa_ff"](mic_xyz, dirs, c)
+
+
+def _mean_samples_no_one(Np):
+    return 2.0 * float(np.sum(Np)) / len(Np)
+
+
+def _samples_direct_half(psi, lags, K):
+    return 0.5 * O.srp.__dict__["_orig_gcc_samples_direct"](psi, lags, K)
+
+
+def _srp_td_floor(dt, fs, xi_fn):
+    out = None
+    for p in range(dt.shape[1]):
+        v = xi_fn(p, np.floor(dt[:, p] * fs).astype(np.int64))
+        out = v if out is None else out + v
+    return out
+
+
+def _lr_smallest(H2d, R_H):
+    import scipy.linalg
+    U, s, Vh = scipy.linalg.svd(H2d, full_matrices=False)
+    return U[:, -R_H:] * s[-R_H:], Vh[-R_H:]
+
+
 # (oracle function, mistake, pins that must fail)
 MUTANTS = {
     "pairs_m_below_mprime": ("mic_pairs", _pairs_reversed, ["pairs"]),
@@ -226,6 +254,11 @@ MUTANTS = {
     "complexity_table_convention": ("complexity", _complexity_table_convention, ["P9"]),
     "argmax_last_of_ties": ("argmax_map", _argmax_last, ["argmax"]),
     "rel_err_not_square_rooted": ("rel_err", _rel_err_squared, ["measures"]),
+    "tdoa_ff_sign_flipped": ("tdoa_ff", _tdoa_ff_sign, ["ff"]),
+    "mean_samples_without_centre": ("mean_samples", _mean_samples_no_one, ["P9"]),
+    "samples_direct_factor_two": ("gcc_samples_direct", _samples_direct_half, ["P3_ifft"]),
+    "td_lookup_floor_not_round": ("srp_td", _srp_td_floor, ["td"]),
+    "lr_smallest_triplets": ("lr_factors", _lr_smallest, ["lr_rank"]),
 }
 
 

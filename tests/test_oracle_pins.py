@@ -293,6 +293,27 @@ def test_lr_full_rank_equals_conv(sq):
     assert np.max(np.abs(z - zc)) <= 1e-10 * np.max(np.abs(zc))
 
 
+def test_lr_rank_R_is_the_best_approximation(sq):
+    """Eq. (min_lr): H_tall H_fat is the best rank-R_H approximation of the complex SRP
+    matrix: it equals H W_R W_R^H with W_R the top eigenvectors of H^H H (numpy.linalg.eigh,
+    another routine than the SVD the oracle calls), and its residual is the sum of the
+    dropped squared singular values (Eckart-Young)."""
+    w, Y, psi, dt = sq
+    K = w["N"] // 2
+    H = O.steering_matrix_H(dt[::5], w["fs"], K).reshape(dt[::5].shape[0], -1)
+    ev, W = np.linalg.eigh(H.conj().T @ H)
+    s = np.sqrt(np.clip(ev[::-1], 0, None))
+    for R in (2, 7, 20):
+        if s[R - 1] - s[R] < 1e-6 * s[0]:
+            continue  # degenerate cut: the rank-R optimum is not unique
+        tall, fat = O.lr_factors(H, R)
+        WR = W[:, ::-1][:, :R]
+        ref = H @ WR @ WR.conj().T
+        assert np.max(np.abs(tall @ fat - ref)) <= 1e-8 * np.max(np.abs(H))
+        res = np.linalg.norm(H - tall @ fat) ** 2
+        assert abs(res - np.sum(s[R:] ** 2)) <= 1e-9 * np.sum(s ** 2)
+
+
 # ---------------------------------------------------------------- P6: low rank
 def test_P6_rank_R_matches_gram_eigenprojector(uca):
     """Eq. (min_Lambda_lr): Lambda_lr = Lambda V_R V_R^T with V_R the top eigenvectors of
