@@ -108,3 +108,16 @@ def test_shards_draw_distinct_seeded_frames():
     assert (w1["frames"] == w1b["frames"]).all()
     assert not (w1["frames"] == w2["frames"]).all()
     assert w1["frames"].shape == w2["frames"].shape
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    """Under torchrun (N > 1) the reference arm's other ranks exit without work or output."""
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    a = bench.parse(["--impl", "reference", "--gpus", "2", "--workload", "square4",
+                     "--frames", "4", "--steps", "2", "--warmup", "1"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(a)
+    assert buf.getvalue() == ""
