@@ -46,6 +46,7 @@ PIN_CALLS = {
     "P1_sq": lambda fx: PINS.test_P1_conv_equals_delay_and_sum_power("sq", fx),
     "P1_uca": lambda fx: PINS.test_P1_conv_equals_delay_and_sum_power("uca", fx),
     "P2": lambda fx: PINS.test_P2_source_on_grid_point_is_the_exact_peak(),
+    "P2_win": lambda fx: PINS.test_P2_windowed_free_field_source_on_a_grid_point_is_the_argmax("hann"),
     "P3_ifft": lambda fx: PINS.test_P3_samples_direct_equal_ifft_selection(fx.getfixturevalue("sq")),
     "P3_int": lambda fx: PINS.test_P3_integer_lag_equals_conv_pair_term(fx.getfixturevalue("sq")),
     "nmod": lambda fx: PINS.test_lag_order_is_nmod(),
@@ -229,11 +230,11 @@ def _lr_smallest(H2d, R_H):
 # (oracle function, mistake, pins that must fail)
 MUTANTS = {
     "pairs_m_below_mprime": ("mic_pairs", _pairs_reversed, ["pairs"]),
-    "tdoa_sign_flipped": ("tdoa_nf", _tdoa_sign, ["P1_sq", "P2", "tdoa_range"]),
-    "tdoa_speed_343": ("tdoa_nf", _tdoa_c343, ["P2"]),
+    "tdoa_sign_flipped": ("tdoa_nf", _tdoa_sign, ["P1_sq", "P2", "P2_win", "tdoa_range"]),
+    "tdoa_speed_343": ("tdoa_nf", _tdoa_c343, ["P2", "P2_win"]),
     "window_symmetric_hann": ("analysis_window", _window_symmetric, ["hann"]),
-    "stft_plus_exponent": ("stft", _stft_plus_sign, ["shift", "P2"]),
-    "phat_conjugate_swapped": ("gcc_phat", _phat_conj_swapped, ["P1_sq", "P2"]),
+    "stft_plus_exponent": ("stft", _stft_plus_sign, ["shift", "P2", "P2_win"]),
+    "phat_conjugate_swapped": ("gcc_phat", _phat_conj_swapped, ["P1_sq", "P2", "P2_win"]),
     "phat_weight_dropped": ("gcc_phat", _phat_unweighted, ["P1_sq", "P2"]),
     "phat_bins_off_by_one": ("gcc_phat", _phat_with_dc, ["P1_sq", "P2"]),
     "omega_off_by_one": ("_omega", _omega_off_by_one, ["P2"]),

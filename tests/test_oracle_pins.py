@@ -159,6 +159,39 @@ def test_P2_source_on_grid_point_is_the_exact_peak():
     assert np.all(O.argmax_map(z) == s)
 
 
+@pytest.mark.parametrize("window", ["hann", "sqrt-hann"])
+def test_P2_windowed_free_field_source_on_a_grid_point_is_the_argmax(window):
+    """Time-domain variant of P2: a white source exactly on a grid point, propagated in free
+    field (band-limited fractional delays, 1/r gain, no noise), framed with a Hann or
+    square-root Hann window.  The PHAT maps of conv. FD-SRP, SI-SRP and full-rank SLRI-SRP
+    all peak at that grid point in every frame (Sec. II-B: the true location maximises the
+    delay-and-sum power)."""
+    mics = synth.mics_square()
+    grid = synth.grid_plane((1.0, 1.0), (3.0, 3.0), (9, 9))
+    s = 58
+    fs, N, hop, F = 16000.0, 512, 256, 6
+    sig = synth.white(synth.rng(31), (F - 1) * hop + N + 64)
+    x = synth.propagate([(sig, grid[s])], fs, mics, (F - 1) * hop + N)
+    frames = synth.cut_frames(x, N, hop, F).astype(np.float64)
+    psi = O.gcc_phat(O.stft(frames, window))
+    dt = O.tdoa_nf(mics, grid)
+    K = N // 2
+    z = O.srp_conv(psi, dt, fs)
+    lags = O.pair_lags(O.n_p_samples(mics, fs))
+    xi = O.gcc_samples_direct(psi, lags, K)
+    Lam = O.interp_matrix(dt, fs, lags)
+    tall, fat, _ = O.slri_factors(Lam, min(Lam.shape))
+    for zz in (z, O.srp_si(Lam, xi), O.srp_slri(tall, fat, xi)):
+        assert np.all(O.argmax_map(zz) == s)
+    # under PHAT z <= 2P(K-1) everywhere; the true point comes close to it (the delays are
+    # exact and there is no noise), and it beats the runner-up (a neighbouring cell)
+    P = len(O.mic_pairs(len(mics)))
+    assert np.all(z <= 2 * P * (K - 1) * (1 + 1e-12))
+    assert np.all(z[:, s] >= 0.98 * 2 * P * (K - 1))
+    top2 = np.sort(z, axis=1)[:, -2:]
+    assert np.all(top2[:, 1] - top2[:, 0] > 0.005 * top2[:, 1])
+
+
 # ---------------------------------------------------------------- P3/P4: sampling
 def test_P3_samples_direct_equal_ifft_selection(sq):
     """Eq. (xi_computed) = Eq. (xi_p_ifft)-(n_prime): 2 Re[S_p psi_p] equals the
