@@ -200,8 +200,9 @@ def cpu_baseline(refs, frames, stride=1):
     try:
         import threadpoolctl
         cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
-    except Exception:
-        cores = os.cpu_count()
+    except Exception:  # no threadpoolctl: the BLAS thread setting, else the usable CPUs
+        env = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or ""
+        cores = int(env) if env.isdigit() and int(env) > 0 else len(os.sched_getaffinity(0))
     n = frames.shape[0]
     return out, {"value": 3 * J * n / el, "unit": UNIT, "cores": int(cores), "kind": "oracle",
                  "sample": f"{n} frame(s) x {J} cells"
