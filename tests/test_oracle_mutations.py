@@ -61,6 +61,7 @@ PIN_CALLS = {
     "P10": lambda fx: PINS.test_P10_si_error_shrinks_with_aux_samples(fx.getfixturevalue("sq")),
     "ff": lambda fx: PINS.test_tdoa_ff_is_nf_limit(),
     "lr_rank": lambda fx: PINS.test_lr_rank_R_is_the_best_approximation(fx.getfixturevalue("sq")),
+    "dirichlet": lambda fx: PINS.test_dirichlet_kernel_closed_form_and_exact_interpolation(),
 }
 
 
@@ -227,6 +228,12 @@ def _lr_smallest(H2d, R_H):
     return U[:, -R_H:] * s[-R_H:], Vh[-R_H:]
 
 
+def _dirichlet_with_nyquist(x, K):
+    k = np.arange(-K + 1, K + 1)  # one term too many: the Nyquist bin
+    x = np.asarray(x, float)
+    return np.real(np.exp(1j * np.pi * x[..., None] * k / K).sum(axis=-1)) / (2 * K)
+
+
 # (oracle function, mistake, pins that must fail)
 MUTANTS = {
     "pairs_m_below_mprime": ("mic_pairs", _pairs_reversed, ["pairs"]),
@@ -260,6 +267,7 @@ MUTANTS = {
     "samples_direct_factor_two": ("gcc_samples_direct", _samples_direct_half, ["P3_ifft"]),
     "td_lookup_floor_not_round": ("srp_td", _srp_td_floor, ["td"]),
     "lr_smallest_triplets": ("lr_factors", _lr_smallest, ["lr_rank"]),
+    "dirichlet_with_nyquist_term": ("dirichlet", _dirichlet_with_nyquist, ["dirichlet"]),
 }
 
 

@@ -298,6 +298,29 @@ def test_P5_exact_kernel_si_equals_conv(sq):
     assert np.max(np.abs(O.srp_slri(tall, fat, xi) - z)) <= 1e-10 * np.max(np.abs(z))
 
 
+def test_dirichlet_kernel_closed_form_and_exact_interpolation():
+    """The test-only 2K-periodic kernel: its sum equals the closed form
+    sin(pi (2K-1) x / 2K) / (2K sin(pi x / 2K)) (the Dirichlet kernel), and it interpolates a
+    trigonometric polynomial of degree K-1 with no DC or Nyquist term (the TD GCC of
+    Eq. xi_p_discreteFreq with psi(0) = psi(omega_b) = 0) exactly from its 2K integer
+    samples n = -K+1..K, at any real x."""
+    for K in (4, 8, 16):
+        x = np.linspace(-2.3 * K, 2.3 * K, 997)
+        x = x[np.abs(np.sin(np.pi * x / (2 * K))) > 1e-3]  # the closed form is 0/0 at 2K m
+        closed = np.sin(np.pi * (2 * K - 1) * x / (2 * K)) / (2 * K * np.sin(np.pi * x / (2 * K)))
+        assert np.max(np.abs(O.dirichlet(x, K) - closed)) <= 1e-12
+        g = synth.rng(K)
+        psi = g.standard_normal(K - 1) + 1j * g.standard_normal(K - 1)
+        k = np.arange(1, K)
+
+        def xi(t):
+            return 2.0 * np.real(np.exp(1j * np.pi * np.outer(t, k) / K) @ psi)
+
+        n = np.arange(-K + 1, K + 1)
+        interp = O.dirichlet(x[:, None] - n[None, :], K) @ xi(n)
+        assert np.max(np.abs(interp - xi(x))) <= 1e-10 * np.max(np.abs(xi(n)))
+
+
 def test_td_is_one_hot_interpolation(sq):
     """Sec. III-B.2: conv. TD-SRP = SI with the one-hot Lambda at the rounded lag."""
     w, Y, psi, dt = sq
