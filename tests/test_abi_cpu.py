@@ -242,3 +242,36 @@ def test_header_serves_a_plain_c_program(S, tmp_path):
                         f"-Wl,-rpath,{lib_dir}"], check=True, capture_output=True)
         r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
         assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
+
+
+def test_binding_structs_match_the_header_layout(S, tmp_path):
+    """The ctypes structures of the Python binding have the size and field offsets that a C
+    compiler gives the header's structures (a drift between include/libsrp.h and the binding
+    would pass garbage across the ABI)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2306_08514_gb300 import _abi as A
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"srp_plan_desc": A.srp_plan_desc, "srp_plan_info_t": A.srp_plan_info_t,
+               "srp_server_desc": A.srp_server_desc, "srp_server_stats_t": A.srp_server_stats_t,
+               "srp_tune_report_t": A.srp_tune_report_t}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", "#include \"libsrp.h\"", "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:-1]): int(l.split()[-1]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
