@@ -275,3 +275,43 @@ def test_binding_structs_match_the_header_layout(S, tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def _header_declarations():
+    """(name, return type, [parameter declarations]) of every function the header declares."""
+    text = open(os.path.join(ROOT, "include", "libsrp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"#.*", "", text)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(srp_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text):
+        ret = " ".join(m.group(1).split()[-3:])
+        params = [p.strip() for p in m.group(3).split(",")]
+        if params == ["void"]:
+            params = []
+        out.append((m.group(2), ret, params))
+    return out
+
+
+def test_binding_signatures_match_the_header(S):
+    """Every entry point's ctypes signature has the header's parameter count, pointers where
+    the header has pointers (or handle typedefs), and scalars of the header's width."""
+    import ctypes
+    decls = _header_declarations()
+    assert {d[0] for d in decls} == set(S.SIGNATURES)
+    scalars = {"int": ctypes.c_int, "double": ctypes.c_double, "size_t": ctypes.c_size_t,
+               "float": ctypes.c_float, "long long": ctypes.c_longlong}
+    handles = ("srp_plan_t", "srp_server_t")
+    for name, ret, params in decls:
+        restype, argtypes = S.SIGNATURES[name]
+        assert len(argtypes) == len(params), name
+        for p, t in zip(params, argtypes):
+            ptype = re.sub(r"\b(const|restrict)\b", "", p).strip()
+            if "*" in ptype or ptype.split()[0] in handles:
+                assert t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer), (name, p)
+            else:
+                base = " ".join(ptype.split()[:-1])
+                want = scalars.get(base, ctypes.c_int)  # enums pass as int
+                assert ctypes.sizeof(t) == ctypes.sizeof(want) and t != ctypes.c_void_p, (name, p)
+        want_ret = {"srp_status": ctypes.c_int, "double": ctypes.c_double,
+                    "const char*": ctypes.c_char_p, "void": None}[ret.split()[-1] if ret != "const char*" else ret]
+        assert restype == want_ret, (name, ret, restype)
