@@ -41,3 +41,37 @@ def test_presets_are_seeded_and_sized(name, M, J, N):
     assert np.array_equal(a["frames"], b["frames"])
     assert a["frames"].shape == (12, M, N) and a["frames"].dtype == np.float32
     assert a["grid_xyz"].shape == (J, 3) and a["mic_xyz"].shape == (M, 3)
+
+
+def test_image_sources_count_gains_and_first_order_mirrors():
+    """Shoebox image method with total reflection order <= 3: per axis one image with no
+    reflection and two with r >= 1 reflections, so 1 + 6 + 18 + 38 = 63 images; gains
+    beta^order; the six first-order images are the mirrors in the six walls; no duplicates."""
+    room = (6.0, 4.0, 3.0)
+    src = np.array([1.3, 2.9, 0.7])
+    imgs = synth.image_sources(src, room, 3, 0.7)
+    assert len(imgs) == 63
+    pos = np.array([p for p, _ in imgs])
+    assert len(np.unique(np.round(pos, 9), axis=0)) == 63
+    gains = sorted(round(g, 12) for _, g in imgs)
+    want = [1.0] + [0.7] * 6 + [round(0.7 ** 2, 12)] * 18 + [round(0.7 ** 3, 12)] * 38
+    assert gains == sorted(want)
+    first = {tuple(np.round(p, 9)) for p, g in imgs if abs(g - 0.7) < 1e-12}
+    mirrors = set()
+    for ax in range(3):
+        for wall in (0.0, room[ax]):
+            m = src.copy()
+            m[ax] = 2 * wall - src[ax]
+            mirrors.add(tuple(np.round(m, 9)))
+    assert first == mirrors
+    assert any(np.allclose(p, src) and g == 1.0 for p, g in imgs)
+
+
+def test_noise_is_added_at_the_requested_snr():
+    g = synth.rng(9)
+    x = g.standard_normal((4, 5000)) * np.array([[1.0], [0.5], [2.0], [1.5]])
+    n = g.standard_normal((4, 5000))
+    for snr in (10.0, 15.0, 20.0):
+        y = synth.add_noise_snr(x, n, snr)
+        got = 10 * np.log10(np.mean(x ** 2) / np.mean((y - x) ** 2))
+        assert abs(got - snr) < 1e-9
