@@ -7,10 +7,10 @@ with on/off envelope and 10 dB diffuse noise (synthetic, seeded).  One step comp
 for the whole batch, the maps of conv. FD-SRP, SLRI-SRP (R=16) and SSPI-SRP (t=4 taps
 per location and pair), each through the full path (STFT + PHAT, cross-spectra / iFFT
 sampling, contraction, argmax).  ``value`` counts every map cell produced: 3 * J * F per
-step and rank.  The default precision is BF16 on the tensor cores for every method: the
-conv. point is then the fastest conv. FD-SRP whose map error (vs the FP64 oracle) stays
-far below the approximation error of SLRI/SSPI, i.e. the matched-error comparison;
-``--precision fp16x3`` gives FP32-class maps (<= 1e-5 of the oracle).
+step and rank.  The default precision is FP32-class for every method: FP16 hi+lo on the
+tensor cores (three products, FP32 accumulation), whose maps stay within 1e-5 of the FP64
+oracle.  A BF16 point of the same step is measured after the timed region and reported
+as an extra key (``bf16_point``); ``--precision`` picks another headline precision.
 
 Timing: every step is bracketed by CUDA events on the launching stream, with an L2 flush
 (a 512 MB write) before each step outside the events.  Prints one JSON line (rank 0).
@@ -48,7 +48,7 @@ def parse(argv=None):
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--rank", type=int, default=16, help="SLRI rank R")
     ap.add_argument("--taps", type=float, default=4.0, help="SSPI taps per location and pair")
-    ap.add_argument("--precision", default="bf16",
+    ap.add_argument("--precision", default="fp16x3",
                     help="fp32 | bf16 | fp16 | tf32 | bf16x3 | fp16x3 | tf32x3")
     ap.add_argument("--conv-precision", default=None)
     ap.add_argument("--slri-precision", default=None)
@@ -56,6 +56,10 @@ def parse(argv=None):
     ap.add_argument("--methods", default="conv,slri,sspi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-bf16-point", action="store_true",
+                    help="skip the extra BF16 measurement of the same step")
+    ap.add_argument("--argmax-frames", type=int, default=1024,
+                    help="frames whose argmax is compared with the FP64 oracle's")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
@@ -191,7 +195,8 @@ class OracleRefs:
 
 def cpu_baseline(refs, frames, stride=1):
     """The FP64 oracle as it stands: per-frame work of all three methods on a bounded
-    sample (every `stride`-th grid cell); plan-time fits are excluded like the GPU's."""
+    sample (every `stride`-th grid cell).  The SLRI / SSPI fits are made beforehand, like
+    the GPU plans'; the oracle's conv. FD-SRP builds its SRP matrix inside every call."""
     cells = slice(None, None, stride)
     t0 = time.perf_counter()
     out = {m: refs.maps(m, frames, cells) for m in ("conv", "slri", "sspi")}
@@ -207,8 +212,9 @@ def cpu_baseline(refs, frames, stride=1):
     return out, {"value": 3 * J * n / el, "unit": UNIT, "cores": int(cores), "kind": "oracle",
                  "sample": f"{n} frame(s) x {J} cells"
                            + (f" (1 in {stride} of the grid)" if stride > 1 else "")
-                           + " x 3 methods (FP64 conv H, SLRI, SSPI from the oracle's factors);"
-                             " plan-time SVD/selection excluded",
+                           + " x 3 methods: conv. FD-SRP with its SRP matrix H built inside the"
+                             " call (the oracle generates H per call), SLRI and SSPI from factors"
+                             " fitted beforehand (the SVD and the top-Q selection are not timed)",
                  "seconds": el}
 
 
@@ -300,12 +306,12 @@ def measured_traffic(workload, F, method, prec):
 
 
 def contraction_work(m, prec, info, F, R):
-    """(kind, amount per launch) of the dominant kernel of method m: algorithmic FLOPs of
-    the contraction (a split-precision FP16 hi+lo run executes three products) or bytes."""
+    """(kind, amount per launch) of the dominant kernel of method m: the algorithm's FLOPs
+    of the contraction, 2JP(K-1) real MACs per frame for conv. FD-SRP (Eq. SRPomp) whatever
+    the precision, or the bytes of the map write that bounds SLRI / SSPI."""
     J, P, K, L = info.J, info.P, info.K, info.L
-    x3 = 3.0 if prec.endswith("x3") else 1.0
     if m == "conv":
-        return "flop", x3 * 4.0 * J * P * (K - 1) * F  # 2JP(K-1) real MACs per frame
+        return "flop", 4.0 * J * P * (K - 1) * F
     if m == "slri":
         return "byte", 4.0 * J * F  # the map write; 2R(J+L) flop per frame is far below
     if m == "sspi":
@@ -313,6 +319,186 @@ def contraction_work(m, prec, info, F, R):
             return "flop", 2.0 * info.nnz * F
         return "byte", 4.0 * J * F
     return "byte", 4.0 * J * F
+
+
+def contraction_peak(prec, kind, peaks_):
+    """(peak, unit, bound, source) the dominant kernel is measured against.  A hi+lo split
+    runs three products per algorithmic MAC, so its peak in algorithmic FLOP/s is the
+    operand type's tensor rate / 3.  Kernels timed per step (a few ms, L2 flushed between
+    steps) take the burst figure."""
+    hbm, bf16, _bf16s, smmax, src = peaks_
+    if kind == "byte":
+        return hbm, "GB/s", "hbm", f"{src} copy"
+    if prec == "fp32":
+        return (FFMA_LANES * 2 * smmax * 1e6 / 1e12, "TFLOP/s", "alu",
+                "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock")
+    split = 3.0 if prec.endswith("x3") else 1.0
+    if prec.startswith("tf32"):
+        # no TF32 peak is measured: the measured BF16 burst x the nominal ratio 1.1 / 2.25
+        base, what = bf16 * 1.1 / 2.25, f"{src} bf16 burst x 1.1/2.25 (nominal TF32 / BF16 dense rates)"
+    else:
+        base, what = bf16, f"{src} bf16 burst (FP16 runs at the BF16 rate)"
+    if split > 1:
+        what += " / 3 (hi+lo: three products per algorithmic MAC)"
+    return base / split, "TFLOP/s", "tensor", what
+
+
+def roofline_of(dom, prec, info, F, R, t_launch, peaks_):
+    """The roofline object of the dominant kernel: algorithmic work per launch over the
+    launch's CUDA-event duration, against the matching peak."""
+    kind, work = contraction_work(dom, prec, info, F, R)
+    peak, unit, bound, what = contraction_peak(prec, kind, peaks_)
+    achieved = work / t_launch / (1e12 if kind == "flop" else 1e9)
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "peak_source": what, "frac": achieved / peak,
+            "work_per_launch": {"kind": kind, "amount": work}}
+
+
+def grid_pitch(grid_xyz):
+    """Per-axis spacing of a regular grid of cell centres (inf on an axis with one value)."""
+    h = []
+    for ax in range(3):
+        u = np.unique(np.round(np.asarray(grid_xyz)[:, ax], 9))
+        h.append(float(np.min(np.diff(u))) if len(u) > 1 else np.inf)
+    return np.array(h)
+
+
+def argmax_report(idx, ref, grid_xyz):
+    """Agreement of per-frame estimates `idx` with the maxima of the FP64 maps `ref`
+    [frames][J] (Eq. imax): exact index, within one grid cell on every axis, distance in
+    metres, and the map value lost at the pick relative to the peak's height above the
+    map's median (0 when the pick is a maximum of the oracle's map)."""
+    idx = np.asarray(idx, np.int64)
+    io = np.argmax(ref, axis=1)
+    d = np.asarray(grid_xyz)[idx] - np.asarray(grid_xyz)[io]
+    cells = np.max(np.abs(d) / grid_pitch(grid_xyz)[None, :], axis=1)
+    metres = np.linalg.norm(d, axis=1)
+    r = np.arange(len(idx))
+    top = ref[r, io]
+    gap = (top - ref[r, idx]) / np.maximum(top - np.median(ref, axis=1), 1e-300)
+    return {"frames": int(len(idx)), "exact": float(np.mean(idx == io)),
+            "within_one_cell": float(np.mean(cells <= 1.0 + 1e-6)),
+            "dist_m_median": float(np.median(metres)),
+            "dist_m_p99": float(np.percentile(metres, 99)), "dist_m_max": float(metres.max()),
+            "peak_gap_median": float(np.median(gap)), "peak_gap_max": float(gap.max())}
+
+
+PLAN_KW = {"conv": lambda a: dict(method="conv"), "slri": lambda a: dict(method="slri", rank=a.rank),
+           "sspi": lambda a: dict(method="sspi", taps=a.taps), "si": lambda a: dict(method="si"),
+           "td": lambda a: dict(method="td"), "lr": lambda a: dict(method="lr", rank=a.rank)}
+
+
+def make_plans(S, a, w, methods, prec, F):
+    """One plan per method at its precision, each tuned (tile shape) for batches of F."""
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    plans = {m: S.Plan(*args, max_frames=F, precision=prec[m], **PLAN_KW[m](a)) for m in methods}
+    tuned = {m: plans[m].autotune(F) for m in methods} if not a.no_autotune else {}
+    return plans, tuned
+
+
+def per_method(plans, methods, prec, steps, J, F):
+    """Per-method stage times (CUDA events on the launching stream, averaged per step)."""
+    per = {}
+    for m in methods:
+        st = plans[m].stage_ms()
+        ms_m = sum(st[k] for k in ("frontend", "spectra", "contract", "argmax")) / steps
+        per[m] = {"precision": prec[m], "ms_per_step": ms_m, "cells_frames_per_s": J * F / (ms_m / 1e3),
+                  "stage_ms": {k: st[k] / steps for k in ("frontend", "spectra", "contract", "argmax")}}
+    return per
+
+
+def dominant(per, methods):
+    return max(methods, key=lambda m: per[m]["stage_ms"]["contract"])
+
+
+def kernel_name(dom, p):
+    tc = p != "fp32"
+    return {"conv": "tc_gemm_kernel (conv SRP matrix)" if tc else "sgemm_nt_argmax_kernel",
+            "slri": "SLRI fat + pack + tc_gemm_kernel" if tc else "SLRI fat + tall",
+            "sspi": "SSPI pack + tc_gemm_kernel" if tc else "sspi_kernel",
+            }.get(dom, f"{dom} contraction ({'tc_gemm_kernel' if tc else 'sgemm_nt_argmax_kernel'})")
+
+
+def speedups(per):
+    out = {}
+    for m in ("slri", "sspi", "si", "td", "lr"):
+        if "conv" in per and m in per:
+            out[f"speedup_{m}_vs_conv"] = per[m]["cells_frames_per_s"] / per["conv"]["cells_frames_per_s"]
+    return out
+
+
+def extra_point(S, a, w, methods, precision, frames, stream, flush, peaks_, steps=8, warmup=3):
+    """The same step at another precision, measured after the timed region (L2 flushed
+    before every step, CUDA events): its throughput, per-method times and roofline.
+    Returns (summary, maps, argmax) with the maps kept for the error report."""
+    import torch
+    F, J = w["F"], w["grid_xyz"].shape[0]
+    prec = {m: precision for m in methods}
+    plans, tuned = make_plans(S, a, w, methods, prec, F)
+    maps = {m: torch.empty((F, J), dtype=torch.float32, device=frames.device) for m in methods}
+    am = {m: torch.empty((F,), dtype=torch.int32, device=frames.device) for m in methods}
+    for _ in range(warmup):
+        for m in methods:
+            plans[m].map(frames, maps[m], am[m], stream=stream)
+    torch.cuda.synchronize()
+    for m in methods:
+        plans[m].status()
+        plans[m].set_profiling(True)
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for m in methods:
+            plans[m].map(frames, maps[m], am[m], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    per = per_method(plans, methods, prec, steps, J, F)
+    ms = tot / steps
+    dom = dominant(per, methods)
+    roof = roofline_of(dom, precision, plans[dom].info, F, a.rank,
+                       per[dom]["stage_ms"]["contract"] / 1e3, peaks_)
+    roof["kernel"] = kernel_name(dom, precision)
+    for m in methods:
+        plans[m].set_profiling(False)
+        plans[m].status()
+        plans[m].close()
+    out = {"precision": precision, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+           "value": len(methods) * J * F / (ms / 1e3), "methods": per, "autotune": tuned,
+           "roofline": roof, **speedups(per)}
+    return out, maps, am
+
+
+def oracle_report(a, w, methods, variants):
+    """Each variant's maps against the FP64 oracle of the same method: the relative map
+    error over 32 frames spread over the batch, and the argmax agreement (exact, within
+    one grid cell, distance in metres) over `a.argmax_frames` frames.  `variants` maps a
+    name to (precision per method, host maps accessor, host argmax per method)."""
+    import oracle as O
+    F = w["F"]
+    sel_arg = np.unique(np.linspace(0, F - 1, min(F, a.argmax_frames)).astype(int))
+    sel_err = sel_arg[np.unique(np.linspace(0, len(sel_arg) - 1, min(32, len(sel_arg))).astype(int))]
+    pos_err = np.searchsorted(sel_arg, sel_err)
+    refs = OracleRefs(w, a.rank, a.taps)
+    rep = {v: {} for v in variants}
+    rc = None
+    for m in methods:
+        ref = refs.maps(m, w["frames"][sel_arg])
+        if m == "conv":
+            rc = ref
+        for v, (prec, get_maps, idx) in variants.items():
+            if ref is None:
+                rep[v][m] = {"frames_checked": 0, "note": "no FP64 oracle factors at this size"}
+                continue
+            z = get_maps(m, sel_err).astype(np.float64)
+            rel = O.rel_err(z, ref[pos_err], axis=-1)
+            rep[v][m] = {"precision": prec[m], "frames_checked": int(len(sel_err)),
+                         "rel_err_max": float(rel.max()), "rel_err_median": float(np.median(rel)),
+                         "argmax": argmax_report(idx[m][sel_arg], ref, w["grid_xyz"])}
+            if m != "conv" and rc is not None:
+                rep[v][m]["eps_z_vs_conv_db"] = float(np.median(O.eps_db(ref[pos_err], rc[pos_err], axis=-1)))
+    return refs, rep
 
 
 def run_libsrp(a):
@@ -328,13 +514,8 @@ def run_libsrp(a):
 
     w = synth.workload(a.workload, F=a.frames, seed=None if rank == 0 else shard_seed(1002, rank))
     F, J, N, M = w["F"], w["grid_xyz"].shape[0], w["N"], w["mic_xyz"].shape[0]
-    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], N)
     methods, prec = arm_methods(a)
-    kw = {"conv": dict(method="conv"), "slri": dict(method="slri", rank=a.rank),
-          "sspi": dict(method="sspi", taps=a.taps), "si": dict(method="si"),
-          "td": dict(method="td"), "lr": dict(method="lr", rank=a.rank)}
-    plans = {m: S.Plan(*args, max_frames=F, precision=prec[m], **kw[m]) for m in methods}
-    tuned = {m: plans[m].autotune(F) for m in methods} if not a.no_autotune else {}
+    plans, tuned = make_plans(S, a, w, methods, prec, F)
     frames = torch.from_numpy(w["frames"]).to(dev)
     maps = {m: torch.empty((F, J), dtype=torch.float32, device=dev) for m in methods}
     am = {m: torch.empty((F,), dtype=torch.int32, device=dev) for m in methods}
@@ -374,18 +555,11 @@ def run_libsrp(a):
     ck = clocks.stop() if rank == 0 else None
     dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps
     launches = sum(plans[m].info_now().launches - launches0[m] for m in methods)
-    stages = {m: plans[m].stage_ms() for m in methods}
+    per = per_method(plans, methods, prec, a.steps, J, F)
     for m in methods:
         plans[m].set_profiling(False)
         plans[m].status()
     dev_ms, wall = reduce_max([dev_ms, wall], world, dev)
-
-    per = {}
-    for m in methods:
-        st = stages[m]
-        ms_m = sum(st[k] for k in ("frontend", "spectra", "contract", "argmax")) / a.steps
-        per[m] = {"precision": prec[m], "ms_per_step": ms_m, "cells_frames_per_s": J * F / (ms_m / 1e3),
-                  "stage_ms": {k: st[k] / a.steps for k in ("frontend", "spectra", "contract", "argmax")}}
 
     # estimates only (srp_map with maps = NULL: argmax per frame, no map written)
     for m in methods:
@@ -425,37 +599,15 @@ def run_libsrp(a):
         return
     cells = len(methods) * J * F * world
     value = cells / (dev_ms / 1e3)
-    hbm, bf16, bf16s, smmax, src = peaks()
+    pk = peaks()
 
     # dominant kernel: the contraction with the largest time (its CUDA-event duration on the
     # launching stream, per launch; one launch per method and step)
-    dom = max(methods, key=lambda m: per[m]["stage_ms"]["contract"])
-    t_launch = per[dom]["stage_ms"]["contract"] / 1e3
-    info = plans[dom].info
-    kind, work = contraction_work(dom, prec[dom], info, F, a.rank)
-    if kind == "flop":
-        if prec[dom] == "fp32":
-            peak = FFMA_LANES * 2 * smmax * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": work / t_launch / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
-        elif prec[dom].startswith("tf32"):
-            # TF32 has no measured peak: the measured BF16 one x the nominal ratio 1.1 / 2.25
-            roof = {"bound": "tensor", "achieved": work / t_launch / 1e12, "peak": bf16s * 1.1 / 2.25,
-                    "unit": "TFLOP/s",
-                    "peak_source": f"{src} bf16 sustained x 1.1/2.25 (nominal TF32 / BF16 dense rates)"}
-        else:
-            roof = {"bound": "tensor", "achieved": work / t_launch / 1e12, "peak": bf16s,
-                    "unit": "TFLOP/s", "peak_source": f"{src} bf16 sustained (FP16 runs at the BF16 rate)"}
-    else:
-        roof = {"bound": "hbm", "achieved": work / t_launch / 1e9, "peak": hbm, "unit": "GB/s",
-                "peak_source": f"{src} copy"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    dom = dominant(per, methods)
+    roof = roofline_of(dom, prec[dom], plans[dom].info, F, a.rank,
+                       per[dom]["stage_ms"]["contract"] / 1e3, pk)
     roof["traffic"] = measured_traffic(a.workload, F, dom, prec[dom])
-    roof["kernel"] = {"conv": "tc_gemm_kernel (conv SRP matrix)" if prec[dom] != "fp32" else "sgemm_nt_argmax_kernel",
-                      "slri": "SLRI fat + pack + tc_gemm_kernel" if prec[dom] != "fp32" else "SLRI fat + tall",
-                      "sspi": "SSPI pack + tc_gemm_kernel" if prec[dom] != "fp32" else "sspi_kernel",
-                      }.get(dom, f"{dom} contraction ({'tc_gemm_kernel' if prec[dom] != 'fp32' else 'sgemm_nt_argmax_kernel'})")
-    roof["work_per_launch"] = {"kind": kind, "amount": work}
+    roof["kernel"] = kernel_name(dom, prec[dom])
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -471,45 +623,38 @@ def run_libsrp(a):
                 "d2h_bytes_per_step": len(methods) * F * (J * 4 + 4)},
         "gpu_launches": launches // a.steps * a.steps,
         "clocks": ck,
+        **speedups(per),
     }
-    for m in ("slri", "sspi", "si", "td", "lr"):
-        if "conv" in per and m in per:
-            out[f"speedup_{m}_vs_conv"] = per[m]["cells_frames_per_s"] / per["conv"]["cells_frames_per_s"]
+    for m in methods:  # the e2e staging buffers are no longer needed
+        plans[m].close()
+    del hmaps, ham
+
+    bmaps = bam = None
+    variants = {"headline": (prec, lambda m, s: maps[m][torch.from_numpy(s).to(dev)].cpu().numpy(),
+                             {m: am[m].cpu().numpy() for m in methods})}
+    if world == 1 and not a.no_bf16_point and any(p != "bf16" for p in prec.values()):
+        bp, bmaps, bam = extra_point(S, a, w, methods, "bf16", frames, stream, flush, pk)
+        out["bf16_point"] = bp
+        variants["bf16_point"] = ({m: "bf16" for m in methods},
+                                  lambda m, s: bmaps[m][torch.from_numpy(s).to(dev)].cpu().numpy(),
+                                  {m: bam[m].cpu().numpy() for m in methods})
 
     if world == 1 and not (a.no_oracle_check and a.no_cpu_baseline):
-        import oracle as O
-        refs = OracleRefs(w, a.rank, a.taps)
-        z = {m: maps[m].cpu().numpy() for m in methods}
-        idx = {m: am[m].cpu().numpy() for m in methods}
-        sel = np.array([0, F // 2])
-        zo, cb = cpu_baseline(refs, w["frames"][sel[:1]])
-        if not a.no_cpu_baseline:
-            out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
+        refs = None
         if not a.no_oracle_check:
-            rep = {}
-            rc = refs.maps("conv", w["frames"][sel]) if "conv" in methods else None
-            for m in methods:
-                fsel = sel if m == "conv" else np.arange(0, F, max(1, F // 200))
-                ref = rc if m == "conv" else refs.maps(m, w["frames"][fsel])
-                if ref is None:
-                    rep[m] = {"frames_checked": 0, "note": "no FP64 oracle factors at this size"}
-                    continue
-                rel = O.rel_err(z[m][fsel].astype(np.float64), ref, axis=-1)
-                err = np.max(np.abs(z[m][fsel].astype(np.float64) - ref), axis=1)
-                picked = ref[np.arange(len(fsel)), idx[m][fsel]]
-                rep[m] = {"frames_checked": int(len(fsel)), "rel_err_max": float(rel.max()),
-                          "rel_err_median": float(np.median(rel)),
-                          "argmax_exact": float(np.mean(idx[m][fsel] == np.argmax(ref, axis=1))),
-                          "argmax_within_error": float(np.mean(picked >= ref.max(axis=1) - 2 * err - 1e-9))}
-                if m != "conv" and rc is not None:
-                    ro = refs.maps(m, w["frames"][sel])
-                    rep[m]["eps_z_vs_conv_db"] = float(np.median(O.eps_db(ro, rc, axis=-1)))
-            out["vs_oracle"] = rep
+            refs, rep = oracle_report(a, w, methods, variants)
+            out["vs_oracle"] = rep["headline"]
+            if "bf16_point" in rep:
+                out["bf16_point"]["vs_oracle"] = rep["bf16_point"]
+        if not a.no_cpu_baseline:
+            refs = refs or OracleRefs(w, a.rank, a.taps)
+            _, cb = cpu_baseline(refs, w["frames"][:1])
+            out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
     if world == 1 and not a.no_serving:
         # the serving workload's frame-to-map latency, on a reduced session mix (the full
         # 64-session mix is `--serving`)
-        for m in methods:
-            plans[m].close()
+        del maps, variants, bmaps, bam
+        torch.cuda.empty_cache()
         res = run_serving(a, sessions=16, seconds=3.0, Ms=(4, 8))
         res.pop("mix", None)
         out["serving"] = dict(res, note="16 sessions (M in {4, 8}), Poisson 62.5 frames/s each, "

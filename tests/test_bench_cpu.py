@@ -53,16 +53,59 @@ class _Info:
 
 @pytest.mark.parametrize("method,prec,kind,amount", [
     ("conv", "bf16", "flop", 4.0 * 60000 * 28 * 255 * 2000),
-    ("conv", "fp16x3", "flop", 3 * 4.0 * 60000 * 28 * 255 * 2000),
+    ("conv", "fp16x3", "flop", 4.0 * 60000 * 28 * 255 * 2000),
     ("slri", "bf16", "byte", 4.0 * 60000 * 2000),
     ("sspi", "bf16", "byte", 4.0 * 60000 * 2000),
     ("sspi", "fp32", "flop", 2.0 * 6720000 * 2000),
 ])
 def test_contraction_work_per_launch(method, prec, kind, amount):
-    """conv: 2JP(K-1) real MACs per frame (Eq. SRPomp) = 4JP(K-1) flop, three products for
-    the hi+lo precisions; SLRI/SSPI on the tensor cores: the 4-byte map write per cell."""
+    """conv: 2JP(K-1) real MACs per frame (Eq. SRPomp) = 4JP(K-1) flop at every precision
+    (the algorithm's work); SLRI/SSPI on the tensor cores: the 4-byte map write per cell."""
     k, w = bench.contraction_work(method, prec, _Info, 2000, 16)
     assert k == kind and math.isclose(w, amount, rel_tol=1e-15)
+
+
+@pytest.mark.parametrize("prec,peak,bound", [
+    ("bf16", 1895.8, "tensor"), ("fp16", 1895.8, "tensor"),
+    ("fp16x3", 1895.8 / 3, "tensor"), ("bf16x3", 1895.8 / 3, "tensor"),
+    ("tf32", 1895.8 * 1.1 / 2.25, "tensor"), ("tf32x3", 1895.8 * 1.1 / 2.25 / 3, "tensor"),
+    ("fp32", 152 * 128 * 2 * 2070e6 / 1e12, "alu"),
+])
+def test_contraction_peak_matches_the_operand_type_and_split(prec, peak, bound):
+    """The burst BF16 figure for kernels timed per step; TF32 at the nominal 1.1 / 2.25
+    ratio; a hi+lo split runs three products per algorithmic MAC (peak / 3); FP32 FFMA
+    from unit counts and the maximum SM clock."""
+    pk = (6781.8, 1895.8, 1714.1, 2070.0, "measured")
+    got, unit, b, _ = bench.contraction_peak(prec, "flop", pk)
+    assert math.isclose(got, peak, rel_tol=1e-12) and unit == "TFLOP/s" and b == bound
+    assert bench.contraction_peak(prec, "byte", pk)[:3] == (6781.8, "GB/s", "hbm")
+    r = bench.roofline_of("conv", prec, _Info, 2000, 16, 6.26e-3, pk)
+    assert math.isclose(r["achieved"], 4.0 * 60000 * 28 * 255 * 2000 / 6.26e-3 / 1e12, rel_tol=1e-12)
+    assert math.isclose(r["frac"], r["achieved"] / peak, rel_tol=1e-12)
+
+
+def test_argmax_report_counts_exact_neighbour_and_distant_picks():
+    """A pick on the oracle's maximum, one on the next cell, one three cells away: exact
+    1/3, within one cell 2/3; distances 0, h and 3h; the peak gap is 0 at the maximum."""
+    g = synth.grid_box((0, 0, 0), (1.0, 1.0, 1.0), 0.1)
+    J = g.shape[0]
+    h = bench.grid_pitch(g)
+    assert np.allclose(h, 0.1)
+    ref = np.zeros((3, J))
+    top = 555
+    ref[:, top] = 1.0
+    nb = int(np.argmin(np.linalg.norm(g - (g[top] + [0.1, 0, 0]), axis=1)))
+    far = int(np.argmin(np.linalg.norm(g - (g[top] + [0, 0.3, 0]), axis=1)))
+    rep = bench.argmax_report([top, nb, far], ref, g)
+    assert rep["frames"] == 3 and math.isclose(rep["exact"], 1 / 3)
+    assert math.isclose(rep["within_one_cell"], 2 / 3)
+    assert math.isclose(rep["dist_m_median"], 0.1, rel_tol=1e-9)
+    assert math.isclose(rep["dist_m_max"], 0.3, rel_tol=1e-9)
+    assert rep["peak_gap_median"] == 1.0 and rep["peak_gap_max"] == 1.0
+    assert bench.argmax_report([top], ref[:1], g)["peak_gap_max"] == 0.0
+    # a plane grid: the axis with a single value does not count
+    gp = synth.grid_plane((0.0, 0.0), (4.0, 4.0), (50, 50))
+    assert np.isinf(bench.grid_pitch(gp)[2]) and np.allclose(bench.grid_pitch(gp)[:2], 0.08)
 
 
 def test_measured_traffic_goes_stale_with_the_kernel_source(tmp_path, monkeypatch):
