@@ -370,8 +370,10 @@ srp_status srp_debug_stall_next_contraction(srp_plan_t plan);
  * calls whose execution overlaps on the GPU (different streams, or different host
  * threads without ordering) race and give wrong results: serialise them.
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  Errors: SRP_EINVAL, SRP_ECUDA, SRP_EUNSUPPORTED (device index > 63).
+ * (cudaGetSymbolAddress) with that device current and caches it per CUDA context (under
+ * the context's process-unique ID), so the first call after a device reset or in a new
+ * context repeats the lookup; make the first call on a device before any stream capture.
+ * Errors: SRP_EINVAL (sizes, NULL or misaligned pointers), SRP_ECUDA.
  */
 srp_status srp_slri_apply_static(const float* xi, const float* fat, const float* tall, int F,
                                  int L, int R, int J, float* maps, int* argmax, void* stream);

@@ -6,6 +6,8 @@
 #include "srp_internal.h"
 #include "srp_device.cuh"
 
+#include <cuda.h>
+
 #include <cstdint>
 #include <mutex>
 
@@ -316,8 +318,10 @@ cudaError_t launch_argmax_finalize(const unsigned long long* keys, int* argmax, 
 // The intermediate u = Lambda_fat xi and the argmax keys live in one file-scope device
 // array instead of plan scratch: u at offset 0 (kStaticUFloats floats), keys after it.
 // Host code must not pass the array's name to a kernel (on the host it is only a
-// stand-in): the device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, and cached.
+// stand-in): the device address is looked up with cudaGetSymbolAddress, with the device
+// current, once per CUDA context, and cached under the context's process-unique ID
+// (cuCtxGetId), so that a device reset or a new primary context gets a fresh lookup
+// instead of an address that belonged to a context that no longer exists.
 // ---------------------------------------------------------------------------------
 namespace srp {
 namespace {
@@ -325,32 +329,84 @@ constexpr size_t kStaticUFloats = size_t(1) << 20;  // F * R <= 1,048,576 (4 MiB
 constexpr int kStaticMaxFrames = 65536;             // argmax keys (512 KiB)
 constexpr size_t kStaticBytes =
     kStaticUFloats * sizeof(float) + kStaticMaxFrames * sizeof(unsigned long long);
-constexpr int kMaxDevices = 64;
+constexpr int kStaticCache = 64;  // contexts remembered (oldest replaced)
+struct StaticAddr {
+  unsigned long long ctx_id;  // 0: empty
+  void* addr;
+};
 std::mutex g_static_mu;
-void* g_static_addr[kMaxDevices] = {};
+StaticAddr g_static_addr[kStaticCache] = {};
+int g_static_next = 0;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_slri_static_scratch[kStaticBytes];
 
+// The process-unique ID of the context current on this thread, 0 if none is bound yet.
+static srp_status current_context_id(unsigned long long* id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || !f1 ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f2) {
+      set_error("srp_slri_apply_static: the driver has no cuCtxGetCurrent / cuCtxGetId");
+      return SRP_ECUDA;
+    }
+    g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext c = nullptr;
+  if (g_ctx_current(&c) != CUDA_SUCCESS) {
+    set_error("srp_slri_apply_static: cuCtxGetCurrent failed");
+    return SRP_ECUDA;
+  }
+  *id = 0;
+  if (c && g_ctx_id(c, id) != CUDA_SUCCESS) {
+    set_error("srp_slri_apply_static: cuCtxGetId failed");
+    return SRP_ECUDA;
+  }
+  return SRP_OK;
+}
+
 static srp_status static_scratch(void** out) {
   int dev = 0;
   SRP_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("srp_slri_apply_static: device index beyond 63");
-    return SRP_EUNSUPPORTED;
-  }
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_slri_static_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("srp_slri_apply_static: cudaGetSymbolAddress failed: ") +
-                cudaGetErrorString(e));
-      return SRP_ECUDA;
-    }
-    g_static_addr[dev] = p;
+  unsigned long long id = 0;
+  srp_status st = current_context_id(&id);
+  if (st != SRP_OK) return st;
+  if (id != 0) {
+    for (const StaticAddr& e : g_static_addr)
+      if (e.ctx_id == id) {
+        *out = e.addr;
+        return SRP_OK;
+      }
   }
-  *out = g_static_addr[dev];
+  // first call in this context: the lookup binds the device's primary context if this
+  // thread has none yet
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_slri_static_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("srp_slri_apply_static: cudaGetSymbolAddress failed: ") +
+              cudaGetErrorString(e));
+    return SRP_ECUDA;
+  }
+  st = current_context_id(&id);
+  if (st != SRP_OK) return st;
+  if (id != 0) {
+    g_static_addr[g_static_next] = {id, p};
+    g_static_next = (g_static_next + 1) % kStaticCache;
+  }
+  *out = p;
   return SRP_OK;
 }
 

@@ -115,7 +115,7 @@ def grid_ff_halfsphere(step_deg: float = 2.0) -> np.ndarray:
 
     Elevation rings at 0, step, ..., 90-step deg each carry 360/step azimuths, plus
     the zenith as a single point: for a 2 deg pitch J = 45*180 + 1 = 8101, the
-    far-field grid size of the paper's Table I.
+    far-field grid size of the paper's Table II.
     """
     n_az = int(round(360.0 / step_deg))
     n_el = int(round(90.0 / step_deg))

@@ -86,7 +86,9 @@ def test_contraction_peak_matches_the_operand_type_and_split(prec, peak, bound):
 
 def test_argmax_report_counts_exact_neighbour_and_distant_picks():
     """A pick on the oracle's maximum, one on the next cell, one three cells away: exact
-    1/3, within one cell 2/3; distances 0, h and 3h; the peak gap is 0 at the maximum."""
+    1/3, within one cell 2/3; distances 0, h and 3h; the peak gap is 0 at the maximum.
+    With a mirror-image twin of the maximum (an exact tie), a pick on the twin agrees up
+    to ties and is at distance 0 from the nearest maximum."""
     g = synth.grid_box((0, 0, 0), (1.0, 1.0, 1.0), 0.1)
     J = g.shape[0]
     h = bench.grid_pitch(g)
@@ -97,12 +99,19 @@ def test_argmax_report_counts_exact_neighbour_and_distant_picks():
     nb = int(np.argmin(np.linalg.norm(g - (g[top] + [0.1, 0, 0]), axis=1)))
     far = int(np.argmin(np.linalg.norm(g - (g[top] + [0, 0.3, 0]), axis=1)))
     rep = bench.argmax_report([top, nb, far], ref, g)
-    assert rep["frames"] == 3 and math.isclose(rep["exact"], 1 / 3)
+    assert rep["frames"] == 3 and math.isclose(rep["exact_index"], 1 / 3)
+    assert math.isclose(rep["agree_up_to_ties"], 1 / 3)
     assert math.isclose(rep["within_one_cell"], 2 / 3)
     assert math.isclose(rep["dist_m_median"], 0.1, rel_tol=1e-9)
     assert math.isclose(rep["dist_m_max"], 0.3, rel_tol=1e-9)
     assert rep["peak_gap_median"] == 1.0 and rep["peak_gap_max"] == 1.0
     assert bench.argmax_report([top], ref[:1], g)["peak_gap_max"] == 0.0
+    # an exact twin (rounding noise far below the tie tolerance) three cells away
+    twin = ref[:1].copy()
+    twin[0, far] = 1.0 - 1e-15
+    rep = bench.argmax_report([far], twin, g)
+    assert rep["exact_index"] == 0.0 and rep["agree_up_to_ties"] == 1.0
+    assert rep["within_one_cell"] == 1.0 and rep["dist_m_max"] == 0.0
     # a plane grid: the axis with a single value does not count
     gp = synth.grid_plane((0.0, 0.0), (4.0, 4.0), (50, 50))
     assert np.isinf(bench.grid_pitch(gp)[2]) and np.allclose(bench.grid_pitch(gp)[:2], 0.08)

@@ -5,14 +5,15 @@ N = 2048, F = 1024).  The FP64 oracle cannot evaluate these whole (the SVD of wa
 
 * conv: the oracle's map on 256 sampled cells of two sampled frames;
 * SLRI: the plan's own factors (read back from its checkpoint file) applied in FP64 to the
-  oracle's GCC samples, and the fit itself on the sampled rows (Lambda_tall = Lambda V,
-  V orthonormal);
+  oracle's GCC samples, the fit on the sampled rows (Lambda_tall = Lambda V, V
+  orthonormal), and that V spans the top-R singular subspace of the whole Lambda: the
+  Ritz residual of Lambda^T Lambda V and a deflated subspace iteration that finds no
+  direction outside span(V) above sigma_R^2, with Lambda streamed from the oracle in row
+  blocks (FP64);
 * SSPI: the plan's taps applied in FP64 to the oracle's samples, the tap count, and the
   global top-Q_Lambda property on the sampled rows (every entry above the smallest kept
   magnitude is kept, every entry below it dropped).
 """
-import struct
-
 import numpy as np
 import pytest
 
@@ -25,32 +26,6 @@ pytestmark = pytest.mark.gpu
 BF16_TOL = 1.5e-2
 
 
-def read_slri_plan(path):
-    """Lambda_tall [J][Rp] and Lambda_fat [Rp][L] from a saved SLRI plan (the little-endian
-    format srp_plan_save documents)."""
-    b = open(path, "rb").read()
-    assert b[:8] == b"SRPPLAN\0"
-    pos = 8
-    version, method, _h = struct.unpack_from("<Iiq", b, pos)
-    pos += 16
-    J, P, L, R = struct.unpack_from("<iiii", b, pos)
-    pos += 16
-
-    def vec(dtype):
-        nonlocal pos
-        (n,) = struct.unpack_from("<Q", b, pos)
-        pos += 8
-        a = np.frombuffer(b, dtype=dtype, count=n, offset=pos)
-        pos += n * np.dtype(dtype).itemsize
-        return a
-
-    sigma = vec(np.float64)
-    tall = vec(np.float32)
-    fat = vec(np.float32)
-    Rp = tall.size // J
-    return tall.reshape(J, Rp), fat.reshape(Rp, L), sigma, R
-
-
 def _setup(name):
     w = R.workload(name)
     dt, Np, lags, perm = R.geometry(name)
@@ -61,23 +36,33 @@ def _setup(name):
     psi = R.psi_of(w["frames"][fsel])
     xi = R.xi_ascending(psi, lags, perm, w["N"] // 2)  # the GPU's sample order
     lam_cells = O.interp_matrix(dt[cells], w["fs"], lags)[:, perm]
-    return w, dt, fsel, cells, psi, xi, lam_cells
+    return w, dt, lags, perm, fsel, cells, psi, xi, lam_cells
 
 
-def _check_slri(S, w, fsel, cells, xi, lam_cells, rank, tmp_path):
+def _check_slri(S, w, dt, lags, perm, fsel, cells, xi, lam_cells, rank, tmp_path):
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
     plan = S.Plan(*args, method="slri", rank=rank, precision="bf16", max_frames=w["F"])
     z, am = _run(plan, w["frames"])
     plan.status()
     assert np.array_equal(am, np.argmax(z, axis=1))
     plan.save(tmp_path / "slri.plan")
-    tall, fat, sigma, Rr = read_slri_plan(tmp_path / "slri.plan")
+    tall, fat, sigma, Rr = R.read_slri_plan(tmp_path / "slri.plan")
     V = fat[:rank].astype(np.float64).T  # [L][R]
     # the fit: orthonormal V, Lambda_tall = Lambda V on the sampled rows
     assert np.abs(V.T @ V - np.eye(rank)).max() < 1e-5
     want = lam_cells @ V
     got = tall[cells, :rank].astype(np.float64)
     assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+    # V spans the top-R right singular subspace of the whole Lambda (Eckart-Young, Eq.
+    # min_Lambda_lr).  V is stored in FP32 (2^-24 per entry), so its Ritz residual is
+    # bounded by about sigma_1^2 * 2^-24 * sqrt(R); 1e-6 leaves margin for that and nothing
+    # for a stalled iteration.  The plan's sigma are the square roots of the Ritz values.
+    ritz, resid, mu = R.top_subspace_certificate(
+        lambda Y: R.gram_apply(dt, w["fs"], lags, perm, Y), V)
+    sig = plan.slri_sigma(rank)
+    assert resid <= 1e-6, resid
+    assert np.allclose(np.sqrt(ritz), sig, rtol=1e-6, atol=0), (np.sqrt(ritz), sig)
+    assert mu < ritz[-1] * (1 - 1e-6), (mu, ritz[-1])
     # the run-time path: z = Lambda_tall (Lambda_fat xi) with the plan's factors, in FP64
     zo = (xi @ V) @ tall[cells, :rank].astype(np.float64).T
     assert R.per_frame_rel(z[fsel][:, cells], zo).max() <= BF16_TOL
@@ -108,7 +93,7 @@ def _check_sspi(S, w, fsel, cells, xi, lam_cells, t):
 
 
 def test_walls16_full_size_sampled(S, tmp_path):
-    w, dt, fsel, cells, psi, xi, lam_cells = _setup("walls16")
+    w, dt, lags, perm, fsel, cells, psi, xi, lam_cells = _setup("walls16")
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
     plan = S.Plan(*args, method="conv", precision="bf16", max_frames=w["F"])
     z, am = _run(plan, w["frames"])
@@ -117,11 +102,11 @@ def test_walls16_full_size_sampled(S, tmp_path):
     zo = R.conv_cells(psi, dt, w["fs"], cells)
     assert R.per_frame_rel(z[fsel][:, cells], zo).max() <= BF16_TOL
     del plan, z
-    _check_slri(S, w, fsel, cells, xi, lam_cells, 16, tmp_path)
+    _check_slri(S, w, dt, lags, perm, fsel, cells, xi, lam_cells, 16, tmp_path)
     _check_sspi(S, w, fsel, cells, xi, lam_cells, 4.0)
 
 
 def test_nested32_full_size_sampled(S, tmp_path):
-    w, dt, fsel, cells, psi, xi, lam_cells = _setup("nested32")
-    _check_slri(S, w, fsel, cells, xi, lam_cells, 16, tmp_path)
+    w, dt, lags, perm, fsel, cells, psi, xi, lam_cells = _setup("nested32")
+    _check_slri(S, w, dt, lags, perm, fsel, cells, xi, lam_cells, 16, tmp_path)
     _check_sspi(S, w, fsel, cells, xi, lam_cells, 8.0)
