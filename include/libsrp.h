@@ -203,6 +203,30 @@ srp_status srp_map(srp_plan_t plan, const float* frames, int F, float* maps, int
                    void* stream);
 
 /*
+ * srp_map_peaks -- several source estimates per frame: the peak picking of Eq. (qshat)-
+ * (imax) extended to several sources.  For each frame Eq. (imax) is taken K times, each
+ * time over the candidate locations not yet excluded; a pick excludes itself and every
+ * location closer than d_min metres to it.  The lowest index wins a tie.  The distance
+ * test is made in FP32 on the grid coordinates rounded to FP32: d^2 = ((dx*dx + dy*dy) +
+ * dz*dz) with every operation rounded to FP32, excluded when d^2 < d_min^2 (the FP64
+ * square rounded to FP32); on a far-field plan the coordinates are the unit directions.
+ *   frames: device float [F][M][N].
+ *   maps:   device float [F][J], written (as srp_map), or NULL: estimates only.  The maps
+ *           then go through plan-owned scratch in chunks of at most 32 MB (allocated on
+ *           the first such call and kept), small enough to stay in L2 between the
+ *           contraction that writes them and the passes that read them.
+ *   K:      picks per frame, 1..16;  d_min: metres, finite, >= 0 (0: the K largest cells).
+ *   peaks:  device int32 [F][K], written; -1 where no location is left.
+ *   values: device float [F][K] (the map values at the picks, NaN where -1) or NULL.
+ * Pick 0 is the argmax srp_map returns.  The first call also copies the grid coordinates
+ * to the device (J x 16 bytes, kept by the plan).  Asynchronous on `stream`.
+ * Errors: SRP_EINVAL (NULL plan, frames or peaks; F < 0; K or d_min out of range),
+ * SRP_ENOMEM, SRP_ECUDA.
+ */
+srp_status srp_map_peaks(srp_plan_t plan, const float* frames, int F, float* maps, int K,
+                         double d_min, int* peaks, float* values, void* stream);
+
+/*
  * srp_map_host -- srp_map on host buffers: copies frames host->device into plan-owned
  * staging, runs the path, copies maps (and argmax) device->host, and synchronises
  * `stream` before returning.  frames: host float [F][M][N]; maps: host float [F][J];

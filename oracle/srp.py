@@ -30,7 +30,7 @@ __all__ = [
     "pair_lags", "sampling_matrix_S", "two_sided", "gcc_samples_direct",
     "gcc_samples_ifft", "sinc", "dirichlet", "interp_matrix", "srp_si", "slri_factors",
     "srp_slri", "sspi_select", "sspi_matrix", "srp_sspi", "td_matrix", "srp_td",
-    "lr_factors", "srp_lr", "argmax_map", "eps_db", "rel_err",
+    "lr_factors", "srp_lr", "argmax_map", "srp_peaks", "eps_db", "rel_err",
     "complexity", "lags_to_ascending", "SPARSE_KEY_SCALE",
 ]
 
@@ -380,6 +380,38 @@ def srp_lr(H_tall, H_fat, psi_flat):
 def argmax_map(z):
     """Eq. (imax): i_max = argmax_i z(i); the lowest index wins a tie."""
     return np.argmax(z, axis=-1)
+
+
+def srp_peaks(z, grid_xyz, K, d_min):
+    """Several source estimates from one map: Eq. (imax) taken K times, each time over the
+    candidate locations not yet excluded, where a pick excludes itself and every location
+    closer than d_min metres to it (the peak picking behind Eq. (qshat), extended to
+    several sources).  The lowest index wins a tie.  The exclusion test takes the
+    distance in FP32, as the GPU does: with the coordinates rounded to FP32, the squared
+    distance is ((dx*dx + dy*dy) + dz*dz), every operation rounded to FP32, and a location
+    is excluded when that is below d_min^2 rounded to FP32.  z: [F][J] (or [J]).
+    Returns (indices int64 [F][K], values [F][K]); -1 and NaN where no location is left."""
+    z = np.atleast_2d(np.asarray(z))
+    F, J = z.shape
+    q = np.asarray(grid_xyz, float).astype(np.float32)
+    t = np.float32(float(d_min) * float(d_min))
+    idx = np.full((F, K), -1, dtype=np.int64)
+    val = np.full((F, K), np.nan)
+    for f in range(F):
+        allowed = np.ones(J, bool)
+        for k in range(K):
+            if not allowed.any():
+                break
+            i = int(np.argmax(np.where(allowed, z[f], -np.inf)))
+            if not allowed[i]:  # every allowed value is -inf
+                i = int(np.flatnonzero(allowed)[0])
+            idx[f, k] = i
+            val[f, k] = z[f, i]
+            d = q - q[i]
+            d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+            allowed &= d2 >= t
+            allowed[i] = False
+    return idx, val
 
 
 def eps_db(approx, ref, axis=None):

@@ -77,6 +77,8 @@ SIGNATURES = {
     "srp_plan_lags": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "srp_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "srp_map_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "srp_map_peaks": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double,
+                                C.c_void_p, C.c_void_p, C.c_void_p]),
     "srp_gcc_samples": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "srp_plan_sspi_taps": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                                      C.POINTER(C.c_float)]),
@@ -178,6 +180,11 @@ def srp_plan_lags(plan, P: int) -> np.ndarray:
 
 def srp_map(plan, frames_ptr, F, maps_ptr, argmax_ptr, stream) -> None:
     _check(lib().srp_map(plan, frames_ptr, F, maps_ptr, argmax_ptr, stream))
+
+
+def srp_map_peaks(plan, frames_ptr, F, maps_ptr, K, d_min, peaks_ptr, values_ptr, stream) -> None:
+    _check(lib().srp_map_peaks(plan, frames_ptr, F, maps_ptr, int(K), float(d_min), peaks_ptr,
+                               values_ptr, stream))
 
 
 def srp_map_host(plan, frames_ptr, F, maps_ptr, argmax_ptr, stream) -> None:
@@ -304,6 +311,22 @@ class Plan:
                 C.c_void_p(argmax.data_ptr()) if argmax is not None else None,
                 _stream_handle(stream))
         return maps, argmax
+
+    def peaks(self, frames, K, d_min, maps=None, want_maps=True, stream=None):
+        """Several estimates per frame (srp_map_peaks): returns (peaks [F][K] int32, values
+        [F][K] float32, maps [F][J] or None).  want_maps=False: estimates only."""
+        import torch
+        assert frames.is_cuda and frames.dtype == torch.float32 and frames.is_contiguous()
+        F = frames.shape[0]
+        if maps is None and want_maps:
+            maps = torch.empty((F, self.J), dtype=torch.float32, device=frames.device)
+        peaks = torch.empty((F, K), dtype=torch.int32, device=frames.device)
+        values = torch.empty((F, K), dtype=torch.float32, device=frames.device)
+        srp_map_peaks(self.handle, C.c_void_p(frames.data_ptr()), F,
+                      C.c_void_p(maps.data_ptr()) if maps is not None else None, K, d_min,
+                      C.c_void_p(peaks.data_ptr()), C.c_void_p(values.data_ptr()),
+                      _stream_handle(stream))
+        return peaks, values, maps
 
     def map_host(self, frames, maps=None, argmax=None, stream=None):
         """frames, maps, argmax: host arrays (numpy or pinned CPU tensors)."""

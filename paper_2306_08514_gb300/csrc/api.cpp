@@ -93,7 +93,8 @@ void free_plan(srp_plan_s* p) {
                   p->d_split, p->d_xi, p->d_U, p->d_keys, p->d_err, p->d_stage_frames, p->d_stage_maps, p->d_stab, p->d_ftab,
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
                   p->d_hist[1], p->d_stream_frames, p->d_est_maps, p->d_A2, p->d_A2_lo,
-                  p->d_keys2, p->d_tau_hi, p->d_tau_lo};
+                  p->d_keys2, p->d_tau_hi, p->d_tau_lo, p->d_grid4, p->d_peak_maps,
+                  p->d_blk_ptr, p->d_blk_cols};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -224,6 +225,17 @@ cudaError_t sample_to(srp_plan_s* p, const float2* yhat, int F, void* out, void*
                             p->d_twiddle, t, out, out_lo, cols, s);
 }
 
+// FP32 SSPI gather of p->d_xi into maps: the whole-L kernel, or the per-block column lists
+// for long sample vectors.
+cudaError_t sspi_gather(srp_plan_s* p, float* maps, int F, cudaStream_t s) {
+  const Geometry& g = p->g;
+  if (p->sspi_umax > 0)
+    return launch_sspi_band(p->d_xi, p->d_row_ptr, p->d_taps, p->d_blk_ptr, p->d_blk_cols,
+                            p->sspi_umax, p->sspi_fb, maps, p->d_keys, F, g.J, g.L, s);
+  return launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
+                     p->num_sms, s);
+}
+
 // A counted kernel launch of the per-call path.
 #define SRP_LAUNCH(expr)  \
   do {                    \
@@ -257,8 +269,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, kSlriKd, nullptr, nullptr,
                             F, maps, s));
     } else if (method == SRP_SSPI && !tc) {
-      SRP_LAUNCH(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
-                             p->num_sms, s));
+      SRP_LAUNCH(sspi_gather(p, maps, F, s));
     } else {
       SRP_CUDA_TRY(contract(p, p->d_A, p->d_A_lo, p->d_B, p->d_B_lo, p->Lpad, p->d_kb_ptr,
                             p->d_kb_idx, F, maps, s));
@@ -334,8 +345,7 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
       if (method == SRP_SSPI && p->op == OpType::F32) {
         SRP_CUDA_TRY(sample_to(p, p->d_yhat, F, p->d_xi, nullptr, g.L, OpType::F32, s));
         SRP_MARK(p, 2, s);
-        SRP_LAUNCH(launch_sspi(p->d_xi, p->d_row_ptr, p->d_taps, maps, p->d_keys, F, g.J, g.L,
-                                 p->num_sms, s));
+        SRP_LAUNCH(sspi_gather(p, maps, F, s));
       } else {
         SRP_CUDA_TRY(sample_to(p, p->d_yhat, F, p->d_A, p->d_A_lo, p->Lpad, p->op, s));
         SRP_MARK(p, 2, s);
@@ -377,6 +387,12 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
     return st;
   }
   const Geometry& g = p->g;
+  p->h_grid4.resize(4 * static_cast<size_t>(g.J));
+  for (int i = 0; i < g.J; ++i) {
+    for (int a = 0; a < 3; ++a)
+      p->h_grid4[4 * static_cast<size_t>(i) + a] = static_cast<float>(desc->grid_xyz[3 * static_cast<size_t>(i) + a]);
+    p->h_grid4[4 * static_cast<size_t>(i) + 3] = 0.f;
+  }
   // method-specific host-side checks (still no GPU needed)
   if (desc->method == SRP_SLRI) {
     if (desc->rank < 1 || desc->rank > 64 || desc->rank > std::min(g.J, g.L)) {
@@ -399,11 +415,6 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
     if (!(t > 0) || !(nz >= 1) || nz > static_cast<double>(g.J) * g.L) {
       delete p;
       return fail(SRP_EINVAL, "taps_per_loc_pair gives Q_Lambda outside 1..J*L");
-    }
-    if (desc->precision == SRP_FP32 && g.L * 33 * 4 > 220 * 1024) {
-      delete p;
-      return fail(SRP_EUNSUPPORTED,
-                  "the FP32 SSPI gather supports L <= 1700 (use a tensor-core precision)");
     }
     p->nnz = static_cast<long long>(nz);
   }
@@ -723,6 +734,48 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
           int vb;
           std::memcpy(&vb, &p->h_val[t], 4);
           taps[t] = make_int2(p->h_col[t], vb);
+        }
+        if (p->op == OpType::F32 && !sspi_full_fits(g.L)) {
+          // long sample vectors: per 64-cell block, the sorted columns its taps use; the
+          // taps then index that list (the host keeps the global columns for export)
+          const int nrb = (g.J + 63) / 64;
+          std::vector<long long> bptr(nrb + 1, 0);
+          std::vector<int> bcols, mark(g.L, -1), loc(g.L, 0);
+          int umax = 0;
+          for (int b = 0; b < nrb; ++b) {
+            const int i0 = b * 64, i1 = std::min(g.J, i0 + 64);
+            std::vector<int> cols;
+            for (long long t = p->h_row_ptr[i0]; t < p->h_row_ptr[i1]; ++t) {
+              const int c = p->h_col[t];
+              if (mark[c] != b) {
+                mark[c] = b;
+                cols.push_back(c);
+              }
+            }
+            std::sort(cols.begin(), cols.end());
+            for (size_t u = 0; u < cols.size(); ++u) loc[cols[u]] = static_cast<int>(u);
+            for (long long t = p->h_row_ptr[i0]; t < p->h_row_ptr[i1]; ++t) taps[t].x = loc[p->h_col[t]];
+            bcols.insert(bcols.end(), cols.begin(), cols.end());
+            bptr[b + 1] = static_cast<long long>(bcols.size());
+            umax = std::max(umax, static_cast<int>(cols.size()));
+          }
+          int fb = 32;
+          while (fb > 1 && sspi_band_smem(umax, fb) > 220 * 1024) fb >>= 1;
+          if (sspi_band_smem(umax, fb) > 220 * 1024) {
+            free_plan(p);
+            return fail(SRP_EUNSUPPORTED, "the FP32 SSPI gather needs the taps of 64 cells to span at most " +
+                                              std::to_string((220 * 1024 / 4 - 65) / 2) +
+                                              " columns (" + std::to_string(umax) +
+                                              " here; use a tensor-core precision)");
+          }
+          p->sspi_umax = umax;
+          p->sspi_fb = fb;
+          SRP_ALLOC(p, p->d_blk_ptr, sizeof(long long) * bptr.size());
+          SRP_ALLOC(p, p->d_blk_cols, sizeof(int) * std::max<size_t>(1, bcols.size()));
+          SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_blk_ptr, bptr.data(), sizeof(long long) * bptr.size(), cudaMemcpyHostToDevice, s));
+          if (!bcols.empty())
+            SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_blk_cols, bcols.data(), sizeof(int) * bcols.size(), cudaMemcpyHostToDevice, s));
+          SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));  // the host vectors go out of scope
         }
         SRP_ALLOC(p, p->d_row_ptr, sizeof(long long) * (g.J + 1));
         SRP_ALLOC(p, p->d_taps, sizeof(int2) * taps.size());
@@ -1150,6 +1203,61 @@ extern "C" srp_status srp_map(srp_plan_t plan, const float* frames, int F, float
     srp_status st = run_chunk(plan, frames + static_cast<size_t>(c0) * g.M * g.N, nf, out,
                               argmax ? argmax + c0 : nullptr, s);
     if (st != SRP_OK) return st;
+  }
+  return SRP_OK;
+}
+
+// Map scratch of srp_map_peaks without maps: chunks of frames whose maps stay within this
+// many bytes, a fraction of the 126 MB L2, so that the exclusion passes read them from L2.
+constexpr size_t kPeakScratchBytes = size_t(32) << 20;
+
+extern "C" srp_status srp_map_peaks(srp_plan_t plan, const float* frames, int F, float* maps,
+                                    int K, double d_min, int* peaks, float* values,
+                                    void* stream) {
+  clear_error();
+  if (!plan) return fail(SRP_EINVAL, "plan is NULL");
+  if (F < 0) return fail(SRP_EINVAL, "F < 0");
+  if (K < 1 || K > kPeaksMax) return fail(SRP_EINVAL, "K must be in 1..16");
+  if (!(d_min >= 0) || !std::isfinite(d_min)) return fail(SRP_EINVAL, "d_min must be finite and >= 0");
+  if (F == 0) return SRP_OK;
+  if (!frames || !peaks) return fail(SRP_EINVAL, "frames or peaks is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Geometry& g = plan->g;
+  if (!plan->d_grid4) {
+    const size_t bytes = sizeof(float4) * static_cast<size_t>(g.J);
+    if (dalloc(plan, &plan->d_grid4, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      plan->d_grid4 = nullptr;
+      return fail(SRP_ENOMEM, "grid coordinate table allocation failed");
+    }
+    SRP_CUDA_TRY(cudaMemcpyAsync(plan->d_grid4, plan->h_grid4.data(), bytes, cudaMemcpyHostToDevice, s));
+  }
+  int chunk = plan->Fmax;
+  float* sink = nullptr;
+  if (!maps) {
+    if (!plan->d_peak_maps) {
+      const size_t per = sizeof(float) * static_cast<size_t>(g.J);
+      int fc = static_cast<int>(std::min<size_t>(plan->Fmax, std::max<size_t>(1, kPeakScratchBytes / per)));
+      if (dalloc(plan, &plan->d_peak_maps, per * fc) != cudaSuccess) {
+        cudaGetLastError();
+        plan->d_peak_maps = nullptr;
+        return fail(SRP_ENOMEM, "peak map scratch allocation failed");
+      }
+      plan->peak_chunk = fc;
+    }
+    sink = plan->d_peak_maps;
+    chunk = plan->peak_chunk;
+  }
+  const float t = static_cast<float>(d_min * d_min);
+  for (int c0 = 0; c0 < F; c0 += chunk) {
+    const int nf = std::min(chunk, F - c0);
+    float* out = maps ? maps + static_cast<size_t>(c0) * g.J : sink;
+    srp_status st = run_chunk(plan, frames + static_cast<size_t>(c0) * g.M * g.N, nf, out, nullptr, s);
+    if (st != SRP_OK) return st;
+    plan->launches += peaks_launches(nf, K);
+    SRP_CUDA_TRY(launch_peaks(out, nf, g.J, plan->d_grid4, plan->d_keys, K, t,
+                              peaks + static_cast<size_t>(c0) * K,
+                              values ? values + static_cast<size_t>(c0) * K : nullptr, s));
   }
   return SRP_OK;
 }

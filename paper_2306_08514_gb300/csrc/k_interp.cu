@@ -296,6 +296,141 @@ cudaError_t launch_sspi(const float* xi, const long long* row_ptr, const int2* t
 }
 
 // ---------------------------------------------------------------------------------
+// SSPI gather for long sample vectors.  Row block b (64 consecutive cells) stages only
+// the columns its taps use (blk_cols[blk_ptr[b]..blk_ptr[b+1]), sorted; taps carry the
+// column's position in that list) for FB frames, transposed in shared memory
+// ([U][FB+1]).  One warp per row: lanes take the row's taps 32 at a time with FB
+// accumulators each, then a halving reduction leaves lane l with the row's value for
+// frame l >> (5 - log2 FB).  Results go through a shared-memory tile as in sspi_kernel.
+// ---------------------------------------------------------------------------------
+template <int FB>
+__device__ __forceinline__ void halving_reduce(float (&acc)[FB], int lane) {
+  int n = FB;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    if (n > 1) {
+      n >>= 1;
+      const bool upper = (lane & off) != 0;
+#pragma unroll
+      for (int j = 0; j < FB / 2; ++j) {
+        if (j < n) {
+          const float send = upper ? acc[j] : acc[j + n];
+          const float keep = upper ? acc[j + n] : acc[j];
+          acc[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, off);
+        }
+      }
+    } else {
+      acc[0] += __shfl_xor_sync(0xFFFFFFFFu, acc[0], off);
+    }
+  }
+}
+
+template <>
+__device__ __forceinline__ void halving_reduce<1>(float (&acc)[1], int) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) acc[0] += __shfl_xor_sync(0xFFFFFFFFu, acc[0], off);
+}
+
+template <int FB>
+__global__ __launch_bounds__(256) void sspi_band_kernel(
+    const float* __restrict__ xi, const long long* __restrict__ row_ptr,
+    const int2* __restrict__ taps, const long long* __restrict__ blk_ptr,
+    const int* __restrict__ blk_cols, float* __restrict__ Z, unsigned long long* __restrict__ keys,
+    int F, int J, int L) {
+  constexpr int RB = 64, XS = FB + 1, OS = RB + 1;
+  constexpr int LOG = FB == 32 ? 5 : FB == 16 ? 4 : FB == 8 ? 3 : FB == 4 ? 2 : FB == 2 ? 1 : 0;
+  extern __shared__ float sm[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.y;
+  const long long c0 = blk_ptr[b];
+  const int U = static_cast<int>(blk_ptr[b + 1] - c0);
+  float* xs = sm;                                 // [U][XS]
+  float* os = sm + static_cast<size_t>(U) * XS;   // [FB][OS]
+  const int f0 = blockIdx.x * FB;
+  const int nf = min(FB, F - f0);
+  for (int e = tid; e < U * FB; e += 256) {
+    const int fb = e / U, u = e - fb * U;
+    xs[u * XS + fb] = fb < nf ? xi[static_cast<size_t>(f0 + fb) * L + blk_cols[c0 + u]] : 0.f;
+  }
+  __syncthreads();
+  const int i0 = b * RB;
+  for (int rr = warp; rr < RB; rr += 8) {
+    const int i = i0 + rr;
+    float acc[FB];
+#pragma unroll
+    for (int q = 0; q < FB; ++q) acc[q] = 0.f;
+    if (i < J) {
+      const long long e = row_ptr[i + 1];
+      for (long long t = row_ptr[i] + lane; t < e; t += 32) {
+        const int2 tp = __ldg(taps + t);
+        const float v = __int_as_float(tp.y);
+        const float* xr = xs + tp.x * XS;
+#pragma unroll
+        for (int q = 0; q < FB; ++q) acc[q] = fmaf(v, xr[q], acc[q]);
+      }
+    }
+    halving_reduce<FB>(acc, lane);
+    if ((lane & ((32 >> LOG) - 1)) == 0) os[(lane >> (5 - LOG)) * OS + rr] = acc[0];
+  }
+  __syncthreads();
+  for (int fb = warp; fb < nf; fb += 8) {
+    unsigned long long best = 0ull;
+    float* zr = Z + static_cast<size_t>(f0 + fb) * J;
+    for (int rr = lane; rr < RB; rr += 32) {
+      const int i = i0 + rr;
+      if (i < J) {
+        const float v = os[fb * OS + rr];
+        zr[i] = v;
+        const unsigned long long k = argmax_key(v, i);
+        best = k > best ? k : best;
+      }
+    }
+    best = warp_max_u64(best);
+    if (lane == 0 && best) atomicMax(keys + f0 + fb, best);
+  }
+}
+
+size_t sspi_band_smem(int U, int FB) {
+  return sizeof(float) * (static_cast<size_t>(U) * (FB + 1) + static_cast<size_t>(FB) * 65);
+}
+
+bool sspi_full_fits(int L) { return sspi_smem<1>(L) <= 220 * 1024; }
+
+cudaError_t launch_sspi_band(const float* xi, const long long* row_ptr, const int2* taps,
+                             const long long* blk_ptr, const int* blk_cols, int umax, int FB,
+                             float* Z, unsigned long long* keys, int F, int J, int L,
+                             cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  const int nrb = (J + 63) / 64;
+  if (nrb > 65535) return cudaErrorInvalidValue;
+  const size_t smem = sspi_band_smem(umax, FB);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  const dim3 grid((F + FB - 1) / FB, nrb);
+#define SRP_BAND(FBV)                                                                        \
+  case FBV: {                                                                                \
+    cudaError_t e = cudaFuncSetAttribute(sspi_band_kernel<FBV>,                              \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                         static_cast<int>(smem));                            \
+    if (e != cudaSuccess) return e;                                                          \
+    sspi_band_kernel<FBV><<<grid, 256, smem, s>>>(xi, row_ptr, taps, blk_ptr, blk_cols, Z,   \
+                                                  keys, F, J, L);                            \
+    break;                                                                                   \
+  }
+  switch (FB) {
+    SRP_BAND(32)
+    SRP_BAND(16)
+    SRP_BAND(8)
+    SRP_BAND(4)
+    SRP_BAND(2)
+    SRP_BAND(1)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SRP_BAND
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
 __global__ void argmax_finalize_kernel(const unsigned long long* __restrict__ keys,
                                        int* __restrict__ out, int F) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;

@@ -231,9 +231,26 @@ cudaError_t launch_slri_tall(const float* U, const float* tall, float* Z,
 cudaError_t launch_sspi(const float* xi, const long long* row_ptr, const int2* taps, float* Z,
                         unsigned long long* keys, int F, int J, int L, int num_sms,
                         cudaStream_t s);
+// SSPI for long sample vectors: per 64-cell row block only the columns its taps use are
+// staged (blk_ptr [J/64 + 1], blk_cols; taps carry positions in the block's list), FB
+// frames per block (32, 16, .., 1) chosen so that sspi_band_smem(umax, FB) fits.
+bool sspi_full_fits(int L);
+size_t sspi_band_smem(int U, int FB);
+cudaError_t launch_sspi_band(const float* xi, const long long* row_ptr, const int2* taps,
+                             const long long* blk_ptr, const int* blk_cols, int umax, int FB,
+                             float* Z, unsigned long long* keys, int F, int J, int L,
+                             cudaStream_t s);
 // keys -> argmax (lowest index among equal maxima).
 cudaError_t launch_argmax_finalize(const unsigned long long* keys, int* argmax, int F,
                                    cudaStream_t s);
+// Several estimates per frame (k_peaks.cu): pick 0 from the argmax keys of the maps Z
+// [F][J], then K - 1 exclusion passes; picks [F][K] (-1: none left), values [F][K] or NULL.
+// keys are left cleared.  grid: the cells' FP32 coordinates (x, y, z, 0).
+constexpr int kPeaksMax = 16;
+cudaError_t launch_peaks(const float* Z, int F, int J, const float4* grid,
+                         unsigned long long* keys, int K, float t, int* picks, float* values,
+                         cudaStream_t s);
+int peaks_launches(int F, int K);
 
 }  // namespace srp
 
@@ -275,6 +292,10 @@ struct srp_plan_s {
   float* d_fat = nullptr;
   long long* d_row_ptr = nullptr;
   int2* d_taps = nullptr;
+  long long* d_blk_ptr = nullptr;  // FP32 SSPI, long sample vectors: per-block column lists
+  int* d_blk_cols = nullptr;
+  int sspi_umax = 0;               //   (0: the whole-L gather), the longest list
+  int sspi_fb = 0;                 //   frames per thread block
   void* d_B = nullptr;     // dense interpolation operand [J][Lpad] (SI, TD, tensor-core SSPI)
   void* d_B_lo = nullptr;  //   or Lambda_tall as [J][64] (tensor-core SLRI); lo plane for FP16X2
   int* d_kb_ptr = nullptr;  // block-sparse k-block lists per cell tile of d_B
@@ -306,6 +327,10 @@ struct srp_plan_s {
   float* d_hist[2] = {nullptr, nullptr};
   float* d_stream_frames = nullptr;
   float* d_est_maps = nullptr;  // estimates-only calls of FP32 plans: map scratch [Fmax][J]
+  std::vector<float> h_grid4;    // the cells' coordinates rounded to FP32, (x, y, z, 0)
+  float4* d_grid4 = nullptr;     // the same on the device (srp_map_peaks, made on first use)
+  float* d_peak_maps = nullptr;  // srp_map_peaks without maps: L2-sized map scratch
+  int peak_chunk = 0;            //   frames per chunk of that scratch
   float* d_stage_maps = nullptr;
   int* d_stage_arg = nullptr;
   size_t device_bytes = 0;

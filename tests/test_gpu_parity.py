@@ -399,3 +399,25 @@ def test_conv_srp_matrix_generated_on_the_fly(S, name, F, sub):
     zo = O.srp_conv(psi, dt, w["fs"])
     assert R.per_frame_rel(z, zo).max() <= TOL
     check_argmax(z, am, zo)
+
+
+@pytest.mark.parametrize("name,F,sub,t", [("walls16", 70, 37, 4.0), ("nested32", 37, 101, 8.0),
+                                          ("walls16", 9, 300, 0.5)])
+def test_sspi_fp32_long_sample_vectors(S, name, F, sub, t):
+    """The FP32 SSPI gather beyond the whole-vector kernel's reach (walls16 L = 43326,
+    nested32 L = 7408): each 64-cell block stages only the columns its taps use.  Against
+    the oracle masked by the plan's validated taps, FP32 bound; ragged frame and cell
+    blocks."""
+    w = R.workload(name, F, sub)
+    dt, Np, lags, perm = R.geometry(name, F, sub)
+    psi = R.psi_of(w["frames"])
+    xi_o, _ = O.gcc_samples_ifft(psi, lags, w["N"] // 2)
+    mask, tied, taken, nnz = R.sspi(name, t, F, sub)
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="sspi", taps=t,
+                  max_frames=64)
+    Lam = R.lam(name, F, sub)
+    mask_g = _check_taps(plan, mask, perm, Lam)
+    z, am = _run(plan, w["frames"])
+    zo = O.srp_sspi(np.where(mask_g, Lam, 0.0), xi_o)
+    assert R.per_frame_rel(z, zo).max() <= TOL
+    check_argmax(z, am, zo)

@@ -62,10 +62,65 @@ PIN_CALLS = {
     "ff": lambda fx: PINS.test_tdoa_ff_is_nf_limit(),
     "lr_rank": lambda fx: PINS.test_lr_rank_R_is_the_best_approximation(fx.getfixturevalue("sq")),
     "dirichlet": lambda fx: PINS.test_dirichlet_kernel_closed_form_and_exact_interpolation(),
+    "peaks_line": lambda fx: PINS.test_peaks_worked_example_on_a_line(),
+    "peaks_sort": lambda fx: PINS.test_peaks_without_separation_are_the_sorted_map(),
+    "peaks_far": lambda fx: PINS.test_peaks_beyond_the_grid_diameter_leave_the_argmax_only(),
+    "peaks_box": lambda fx: PINS.test_peaks_are_separated_and_greedy_on_a_box_grid(),
+    "peaks_two": lambda fx: PINS.test_peaks_of_two_sources_on_grid_points_are_the_sources(),
 }
 
 
 # ---------------------------------------------------------------- the planted mistakes
+def _peaks_generic(z, grid_xyz, K, d_min, tie_last=False, strict=False, last_only=False,
+                   keep_self=False):
+    """srp_peaks with one planted mistake switched on."""
+    z = np.atleast_2d(np.asarray(z))
+    F, J = z.shape
+    q = np.asarray(grid_xyz, float).astype(np.float32)
+    t = np.float32(float(d_min) * float(d_min))
+    idx = np.full((F, K), -1, dtype=np.int64)
+    val = np.full((F, K), np.nan)
+    for f in range(F):
+        allowed = np.ones(J, bool)
+        picked = np.zeros(J, bool)
+        for k in range(K):
+            if not allowed.any():
+                break
+            v = np.where(allowed, z[f], -np.inf)
+            i = int(J - 1 - np.argmax(v[::-1])) if tie_last else int(np.argmax(v))
+            idx[f, k], val[f, k] = i, z[f, i]
+            picked[i] = True
+            d = q - q[i]
+            d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+            ok = d2 > t if strict else d2 >= t
+            allowed = (ok & ~picked) if last_only else (allowed & ok)
+            if not keep_self:
+                allowed[i] = False
+            elif d_min == 0:
+                allowed[i] = True
+    return idx, val
+
+
+def _peaks_tie_last(z, g, K, d):
+    return _peaks_generic(z, g, K, d, tie_last=True)
+
+
+def _peaks_strict(z, g, K, d):
+    return _peaks_generic(z, g, K, d, strict=True)
+
+
+def _peaks_last_only(z, g, K, d):
+    return _peaks_generic(z, g, K, d, last_only=True)
+
+
+def _peaks_keep_self(z, g, K, d):
+    return _peaks_generic(z, g, K, d, keep_self=True)
+
+
+def _peaks_radius_not_squared(z, g, K, d):
+    return _peaks_generic(z, g, K, math.sqrt(d) if d > 0 else d)
+
+
 def _pairs_reversed(M):
     return [(mp, m) for mp in range(M - 1) for m in range(mp + 1, M)]
 
@@ -268,6 +323,11 @@ MUTANTS = {
     "td_lookup_floor_not_round": ("srp_td", _srp_td_floor, ["td"]),
     "lr_smallest_triplets": ("lr_factors", _lr_smallest, ["lr_rank"]),
     "dirichlet_with_nyquist_term": ("dirichlet", _dirichlet_with_nyquist, ["dirichlet"]),
+    "peaks_last_of_ties": ("srp_peaks", _peaks_tie_last, ["peaks_line", "peaks_sort"]),
+    "peaks_boundary_excluded": ("srp_peaks", _peaks_strict, ["peaks_line"]),
+    "peaks_exclude_around_last_pick_only": ("srp_peaks", _peaks_last_only, ["peaks_line"]),
+    "peaks_pick_not_excluded": ("srp_peaks", _peaks_keep_self, ["peaks_sort"]),
+    "peaks_radius_compared_unsquared": ("srp_peaks", _peaks_radius_not_squared, ["peaks_box"]),
 }
 
 

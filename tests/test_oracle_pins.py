@@ -504,6 +504,95 @@ def test_argmax_takes_the_lowest_index_on_ties():
     assert list(O.argmax_map(z)) == [1, 0, 1]
 
 
+def _line(J, h=1.0):
+    return np.stack([np.arange(J) * h, np.zeros(J), np.zeros(J)], axis=1)
+
+
+def test_peaks_worked_example_on_a_line():
+    """Eq. (imax) repeated with exclusion, worked by hand on a line of unit spacing with
+    d_min = 2: 9 at cell 1 (the lower index of the tie 1 / 3) excludes cells 0..2 (cell 3,
+    exactly 2 away, stays); 9 at cell 3 excludes 2..4; 8 at cell 6 excludes 5..7; nothing
+    is left for a fourth pick."""
+    z = np.array([[4.0, 9.0, 1.0, 9.0, 7.0, 3.0, 8.0, 0.0]])
+    idx, val = O.srp_peaks(z, _line(8), 4, 2.0)
+    assert idx.tolist() == [[1, 3, 6, -1]]
+    assert val[0, :3].tolist() == [9.0, 9.0, 8.0] and np.isnan(val[0, 3])
+    # d_min = 1: neighbours exactly 1 away stay, so 7 at cell 4 is the fourth pick
+    idx, _ = O.srp_peaks(z, _line(8), 4, 1.0)
+    assert idx.tolist() == [[1, 3, 6, 4]]
+
+
+def test_peaks_without_separation_are_the_sorted_map():
+    """d_min = 0 excludes only the picks themselves: the K largest values in descending
+    order, ties in ascending index -- a full sort (numpy lexsort)."""
+    g = synth.rng(31)
+    z = np.round(g.standard_normal((5, 400)), 1)  # many ties
+    grid = g.uniform(0, 4, (400, 3))
+    idx, val = O.srp_peaks(z, grid, 12, 0.0)
+    for f in range(5):
+        order = np.lexsort((np.arange(400), -z[f]))
+        assert idx[f].tolist() == order[:12].tolist()
+        assert np.array_equal(val[f], z[f, order[:12]])
+
+
+def test_peaks_beyond_the_grid_diameter_leave_the_argmax_only():
+    g = synth.rng(32)
+    z = g.standard_normal((3, 200))
+    grid = g.uniform(0, 2, (200, 3))
+    idx, _ = O.srp_peaks(z, grid, 3, 10.0)
+    assert idx[:, 0].tolist() == O.argmax_map(z).tolist()
+    assert np.all(idx[:, 1:] == -1)
+
+
+def test_peaks_are_separated_and_greedy_on_a_box_grid():
+    """Invariants on a 3-D grid: picks are pairwise at least d_min apart, and each is the
+    largest value among the cells at least d_min from every earlier pick (checked with a
+    margin of 1e-6 m on both sides, away from the FP32 exclusion boundary)."""
+    grid = synth.grid_box((0, 0, 0), (1.0, 0.8, 0.6), 0.1)
+    g = synth.rng(33)
+    z = g.standard_normal((4, grid.shape[0]))
+    d_min = 0.25
+    idx, val = O.srp_peaks(z, grid, 5, d_min)
+    for f in range(4):
+        picks = [i for i in idx[f] if i >= 0]
+        assert len(picks) == 5
+        for k, i in enumerate(picks):
+            d_prev = [np.linalg.norm(grid - grid[j], axis=1) for j in picks[:k]]
+            far = np.all([d >= d_min + 1e-6 for d in d_prev], axis=0) if k else np.ones(len(z[f]), bool)
+            near = np.any([d < d_min - 1e-6 for d in d_prev], axis=0) if k else np.zeros(len(z[f]), bool)
+            assert not near[i]
+            assert z[f, i] >= z[f, far].max()
+            assert val[f, k] == z[f, i]
+
+
+def test_peaks_of_two_sources_on_grid_points_are_the_sources():
+    """Closed form: with psi the mean of two exactly delayed single-source spectra, the map
+    is the mean of two single-source maps, each 2P(K-1) at its source (Eq. SRPomp with
+    psi_p(w_k) = exp(-j w_k dt_p(s))).  With d_min = 0.5 m the two picks are the two source
+    cells, each with z >= P(K-1) - max|cross term|.  The array is not planar, so no mirror
+    image of a source is an exact tie."""
+    mics = synth.rng(41).uniform((1.0, 1.0, 0.4), (3.0, 3.0, 1.6), (8, 3))
+    grid = synth.grid_box((0.5, 0.5, 0.5), (3.5, 3.5, 1.5), 0.25)
+    fs, N = 16000.0, 256
+    s1, s2 = 20, 500
+    assert np.linalg.norm(grid[s1] - grid[s2]) > 1.5
+    psis = []
+    for s in (s1, s2):
+        tau = np.linalg.norm(mics - grid[s], axis=1) / 340.0 * fs
+        _, f64 = synth.circular_delay_frames(synth.rng(40 + s), tau, N, 2)
+        psis.append(O.gcc_phat(O.stft(f64, "rect")))
+    dt = O.tdoa_nf(mics, grid)
+    z1, z2 = (O.srp_conv(p, dt, fs) for p in psis)
+    z = O.srp_conv(0.5 * (psis[0] + psis[1]), dt, fs)
+    assert np.allclose(z, 0.5 * (z1 + z2), rtol=0, atol=1e-9 * np.abs(z).max())
+    P, K = 28, N // 2
+    idx, val = O.srp_peaks(z, grid, 2, 0.5)
+    for f in range(2):
+        assert set(idx[f].tolist()) == {s1, s2}
+        cross = max(abs(z2[f, s1]), abs(z1[f, s2])) / 2
+        assert np.all(val[f] >= P * (K - 1) - cross - 1e-9)
+
+
 def test_error_measures_closed_forms():
     """Sec. V-A measures on maps with a known error: a map scaled by (1 + e) is
     10 log10(e^2) dB and e relative away from the original; orthogonal errors add."""
