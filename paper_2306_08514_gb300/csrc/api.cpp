@@ -699,18 +699,29 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
       SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
     } else {
       const int Lpad = p->Lpad;
-      const int kb_n = Lpad / kSlriKd;
       const int tile = tc_gemm_cell_tile();
       const int ntiles = (g.J + tile - 1) / tile;
-      std::vector<int> kb_ptr, kb_idx;  // non-zero k-blocks of each cell tile (block-sparse B)
+      // block-sparse B: per cell tile, the first columns of disjoint 64-column windows that
+      // cover every column a cell of the tile uses.  Windows start at multiples of 8 (the
+      // TMA x-coordinate rule for 16-bit operands) and are laid greedily: each starts at the
+      // first uncovered used column rounded down to 8, which never reaches back into the
+      // previous window since that ends on a multiple of 8.  Columns beyond Lpad read zeros.
+      std::vector<int> kb_ptr, kb_idx;
       auto add_lists = [&](const std::function<void(int, std::vector<char>&)>& mark_cells) {
         kb_ptr.assign(1, 0);
-        std::vector<char> used(kb_n);
+        std::vector<char> used(Lpad);
         for (int n = 0; n < ntiles; ++n) {
           std::fill(used.begin(), used.end(), 0);
           for (int i = n * tile; i < std::min(g.J, (n + 1) * tile); ++i) mark_cells(i, used);
-          for (int k = 0; k < kb_n; ++k)
-            if (used[k]) kb_idx.push_back(k);
+          for (int c = 0; c < Lpad;) {
+            if (!used[c]) {
+              ++c;
+              continue;
+            }
+            const int start = c & ~7;
+            kb_idx.push_back(start);
+            c = start + kSlriKd;
+          }
           kb_ptr.push_back(static_cast<int>(kb_idx.size()));
         }
       };
@@ -788,7 +799,7 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
                                                p->d_B_lo, s));
           add_lists([&](int i, std::vector<char>& used) {
             for (long long t = p->h_row_ptr[i]; t < p->h_row_ptr[i + 1]; ++t)
-              used[p->h_col[t] / kSlriKd] = 1;
+              used[p->h_col[t]] = 1;
           });
           SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
           cudaFree(p->d_row_ptr);  // the dense operand replaces the tap list on the device
@@ -834,7 +845,7 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
             for (int q = 0; q < g.P; ++q) {
               const double t = g.tau[static_cast<size_t>(i) * g.P + q];
               const double r = t < 0.0 ? -std::floor(-t + 0.5) : std::floor(t + 0.5);
-              used[(g.off[q] + static_cast<int>(r) + g.Np[q]) / kSlriKd] = 1;
+              used[g.off[q] + static_cast<int>(r) + g.Np[q]] = 1;
             }
           });
         }

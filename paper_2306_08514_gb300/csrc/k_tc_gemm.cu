@@ -80,8 +80,8 @@ struct TcParams {
   int tf32;              // kind::tf32 instead of kind::f16
   int stall;             // failure-detection test: the producer issues no loads
   unsigned long long wait_ns;  // limit of every mbarrier wait
-  const int* kb_ptr;     // block-sparse: k-block list of cell tile n is
-  const int* kb_idx;     //   kb_idx[kb_ptr[n] .. kb_ptr[n+1]); NULL = dense
+  const int* kb_ptr;     // block-sparse: the 64-column windows of cell tile n start at the
+  const int* kb_idx;     //   columns kb_idx[kb_ptr[n] .. kb_ptr[n+1]); NULL = dense
   int nM, nN, nslices, kb_per_slice;
   int tma_out;           // 1: results leave by TMA store through tmZ; 0: plain stores
   int tn;                // cell width of a tile
@@ -181,10 +181,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int s = w.s0; s < w.s1; ++s) {
           const int seg = s / w.m_len;
           const int loc = s - seg * w.m_len;
-          // 64-column block of the k-step (from the list when block-sparse) and, for TF32,
-          // which 32-column half; the load overlaps the wait
-          const int b64 = list ? __ldg(list + (loc >> p.sub_shift)) : loc >> p.sub_shift;
-          const int kx = b64 * TK + ((loc & ((1 << p.sub_shift) - 1)) << (6 - p.sub_shift));
+          // first column of the k-step's 64-column window (from the list when block-sparse:
+          // any multiple of 8, windows disjoint) and, for TF32, which 32-column half; the
+          // load overlaps the wait
+          const int c64 = list ? __ldg(list + (loc >> p.sub_shift)) : (loc >> p.sub_shift) * TK;
+          const int kx = c64 + ((loc & ((1 << p.sub_shift) - 1)) << (6 - p.sub_shift));
           if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, abort_flag, 1, p.wait_ns)) {
             ok = false;
             break;

@@ -173,7 +173,8 @@ cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long
 // FP32 accumulation, fused argmax keys.  The split types (op_split) run three products over
 // hi and lo planes.  With kb_ptr
 // (device, [ceil(J / tc_gemm_cell_tile()) + 1]) and kb_idx, the cells of list tile n only
-// visit the k-blocks kb_idx[kb_ptr[n] .. kb_ptr[n+1]) (block-sparse B).  Dense reductions whose
+// visit the 64-column windows starting at the columns kb_idx[kb_ptr[n] .. kb_ptr[n+1])
+// (block-sparse B; multiples of 8, windows disjoint, columns past Kd read as zero).  Dense reductions whose
 // output tiles do not fill the GPU are split into tc_gemm_slices(...) slices written to
 // split_ws (tc_gemm_workspace_floats(...) floats suffice for any F <= F_max) and summed
 // in FP64.  A bounded wait that runs out stores a non-zero code in *err.
@@ -298,7 +299,7 @@ struct srp_plan_s {
   int sspi_fb = 0;                 //   frames per thread block
   void* d_B = nullptr;     // dense interpolation operand [J][Lpad] (SI, TD, tensor-core SSPI)
   void* d_B_lo = nullptr;  //   or Lambda_tall as [J][64] (tensor-core SLRI); lo plane for FP16X2
-  int* d_kb_ptr = nullptr;  // block-sparse k-block lists per cell tile of d_B
+  int* d_kb_ptr = nullptr;  // block-sparse window lists per cell tile of d_B (first columns)
   int* d_kb_idx = nullptr;
   // scratch
   float2* d_yhat = nullptr;

