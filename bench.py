@@ -63,11 +63,16 @@ def parse(argv=None):
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
-    ap.add_argument("--no-serving", action="store_true", help="skip the short serving run")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the walls16 / nested32 points")
     ap.add_argument("--curve", action="store_true", help="map error vs throughput over R / t")
     ap.add_argument("--sessions", type=int, default=64)
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--rate", type=float, default=62.5, help="serving: frames/s per session")
+    ap.add_argument("--serving-precision", default="auto",
+                    help="serving: a precision for every session, or auto (FP32 for M <= 8, "
+                         "BF16 otherwise)")
     return ap.parse_args(argv)
 
 
@@ -485,6 +490,79 @@ def extra_point(S, a, w, methods, precision, frames, stream, flush, peaks_, step
     return out, maps, am
 
 
+# The other workloads, measured after the headline (the default run includes them): each
+# point is (method, precision, plan keywords, frames timed), on the workload's frames.
+OTHER_WORKLOADS = [
+    ("walls16", 1024, [("conv", "bf16", {}, None), ("conv", "fp16x3", {}, None),
+                       ("slri", "bf16", {"rank": 16}, None), ("slri", "fp16x3", {"rank": 16}, None),
+                       ("sspi", "bf16", {"taps": 4.0}, None)]),
+    ("nested32", 1024, [("conv", "fp32", {}, 64), ("slri", "bf16", {"rank": 16}, None),
+                        ("slri", "bf16", {"rank": 64}, None), ("sspi", "bf16", {"taps": 8.0}, None)]),
+]
+
+
+def other_workloads(a, S, stream, flush, pk, steps=3):
+    """The large workloads (16 wall microphones, N = 1024, J = 72000; 32 microphones on two
+    nested circles, N = 2048, J = 240000) at a batch of 1024 frames: per point the plan is
+    built (fit included, not timed), tuned, warmed once, and `steps` steps are timed with
+    CUDA events (L2 flushed before each).  Conv. FD-SRP in FP32 on the 32-microphone grid
+    (its SRP matrix generated inside the GEMM) is timed on the first 64 frames."""
+    import torch
+    import synth
+    out = {}
+    for name, F, points in OTHER_WORKLOADS:
+        t0 = time.perf_counter()
+        w = synth.workload(name, F=F)
+        J = w["grid_xyz"].shape[0]
+        frames_all = torch.from_numpy(w["frames"]).cuda()
+        rows = []
+        for method, prec, kw, nf in points:
+            n = nf or F
+            frames = frames_all[:n].contiguous()
+            tb = time.perf_counter()
+            plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method=method,
+                          precision=prec, max_frames=n, **kw)
+            build_s = time.perf_counter() - tb
+            plan.autotune(n)
+            maps = torch.empty((n, J), dtype=torch.float32, device="cuda")
+            am = torch.empty((n,), dtype=torch.int32, device="cuda")
+            plan.map(frames, maps, am, stream=stream)
+            torch.cuda.synchronize()
+            plan.status()
+            plan.set_profiling(True)
+            tot = 0.0
+            for _ in range(steps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.map(frames, maps, am, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            st = plan.stage_ms()
+            plan.set_profiling(False)
+            plan.status()
+            ms = tot / steps
+            stage = {k: st[k] / steps for k in ("frontend", "spectra", "contract", "argmax")}
+            roof = roofline_of(method, prec, plan.info, n, kw.get("rank", 0),
+                               stage["contract"] / 1e3, pk)
+            rows.append({"method": method, "precision": prec, **kw, "frames": n,
+                         "ms_per_step": ms, "cells_frames_per_s": J * n / (ms / 1e3),
+                         "stage_ms": stage, "plan_build_s": build_s, "roofline": roof})
+            plan.close()
+            del maps, am
+        conv = {r["precision"]: r["cells_frames_per_s"] for r in rows if r["method"] == "conv"}
+        for r in rows:
+            if r["method"] != "conv" and conv:
+                ref = conv.get(r["precision"]) or max(conv.values())
+                r["speedup_vs_conv"] = r["cells_frames_per_s"] / ref
+        out[name] = {"F": F, "J": J, "M": int(w["mic_xyz"].shape[0]), "N": int(w["N"]),
+                     "points": rows, "seconds": time.perf_counter() - t0}
+        del frames_all
+        torch.cuda.empty_cache()
+    return out
+
+
 def oracle_report(a, w, methods, variants):
     """Each variant's maps against the FP64 oracle of the same method: the relative map
     error over 32 frames spread over the batch, and the argmax agreement (exact, within
@@ -665,15 +743,16 @@ def run_libsrp(a):
             refs = refs or OracleRefs(w, a.rank, a.taps)
             _, cb = cpu_baseline(refs, w["frames"][:1])
             out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
+    del maps, variants, bmaps, bam
+    torch.cuda.empty_cache()
+    if world == 1 and not a.no_other_workloads:
+        out["other_workloads"] = other_workloads(a, S, stream, flush, pk)
     if world == 1 and not a.no_serving:
-        # the serving workload's frame-to-map latency, on a reduced session mix (the full
-        # 64-session mix is `--serving`)
-        del maps, variants, bmaps, bam
-        torch.cuda.empty_cache()
-        res = run_serving(a, sessions=16, seconds=3.0, Ms=(4, 8))
+        # the serving workload: the full mix of 64 sessions, Poisson arrivals, 5 s
+        res = run_serving(a, sessions=64, seconds=5.0)
         res.pop("mix", None)
-        out["serving"] = dict(res, note="16 sessions (M in {4, 8}), Poisson 62.5 frames/s each, "
-                                        "3 s; full mix: bench.py --serving")
+        out["serving"] = dict(res, note="64 sessions (M in {4, 8, 16, 32}), Poisson 62.5 frames/s "
+                                        "each, 5 s")
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -751,7 +830,16 @@ def slowest_sessions(mix, lats, n=6):
     return rows[:n]
 
 
-def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_batch=16,
+def session_precision(sess, precision):
+    """precision "auto": FP32 on the CUDA cores for the 4- and 8-microphone arrays, whose
+    plans use the fused front end and share grouped launches; BF16 on the tensor cores for
+    the 16- and 32-microphone arrays (long sample vectors or many pairs)."""
+    if precision != "auto":
+        return precision
+    return "fp32" if sess["M"] <= 8 else "bf16"
+
+
+def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="auto", max_batch=16,
                 Ms=(4, 8, 16, 32), quiet=False):
     """Serving workload: `sessions` sessions with Poisson frame arrivals (`rate` frames/s
     each) pushed in real time by a feeder thread, results drained (argmax and latency) by a
@@ -767,8 +855,8 @@ def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_b
     srv = S.Server(hbm_budget=int(0.6 * free), max_sessions=sessions, max_batch=max_batch,
                    streams=8, slots_per_session=3, pending_frames=16 * max_batch)
     t_build = time.perf_counter()
-    sids = [srv.open(s["mics"], s["grid"], 16000.0, s["N"], s["hop"], precision=precision, **s["kw"])
-            for s in mix]
+    sids = [srv.open(s["mics"], s["grid"], 16000.0, s["N"], s["hop"],
+                     precision=session_precision(s, precision), **s["kw"]) for s in mix]
     while True:
         infos = [srv.session_info(x)["state"] for x in sids]
         if all(st == "active" for st in infos):
@@ -848,6 +936,10 @@ def run_serving(a, sessions=64, seconds=10.0, rate=62.5, precision="bf16", max_b
            "latency_max_ms": 1e3 * st["latency_max_s"], "launches": st["launches"],
            "graph_launches": st["graph_launches"],
            "mean_frames_per_launch": st["frames_launched"] / max(1, st["launches"]),
+           "group_launches": st["group_launches"], "group_frames": st["group_frames"],
+           "mean_sessions_per_group_launch": st["group_sessions"] / max(1, st["group_launches"]),
+           "mean_frames_per_group_launch": st["group_frames"] / max(1, st["group_launches"]),
+           "precision_by_M": {str(M): session_precision({"M": M}, precision) for M in Ms},
            "admission_build_s": build_s, "push_retries": refused,
            "failed_sessions": {str(k): v for k, v in errors.items()},
            "slowest_sessions": slowest_sessions(mix, lats),
@@ -932,10 +1024,10 @@ def main():
     elif a.curve:
         run_curve(a)
     elif a.serving:
-        res = run_serving(a, sessions=a.sessions, seconds=a.seconds, precision=a.precision,
-                          rate=a.rate)
+        res = run_serving(a, sessions=a.sessions, seconds=a.seconds,
+                          precision=a.serving_precision, rate=a.rate)
         out = {"metric": "serving: map cells*frames/s and frame-to-map latency", "value": res["cells_frames_per_s"],
-               "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": a.precision,
+               "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": a.serving_precision,
                "data": "synthetic", "config": {"workload": f"serving: {a.sessions} sessions, Poisson "
                                                f"{a.rate} frames/s each, {a.seconds} s"},
                "serving": res}

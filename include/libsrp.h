@@ -421,6 +421,16 @@ srp_status srp_slri_apply_static(const float* xi, const float* fat, const float*
  *     SRP path, D2H maps and argmax, a completion callback -- is captured as a CUDA graph by
  *     the builder thread at admission (after srp_plan_autotune picks the session's tile
  *     shape for max_batch) and replayed by the scheduler.
+ *   - Grouped launches (group_launches = 1): sessions whose plan is FP32 (CUDA cores),
+ *     uses the fused front end (N <= 1024, N_p <= 32) and is SLRI or SSPI with the
+ *     whole-vector gather (L <= 1643) are bucketed by (method, N, sampling tiles, padded
+ *     rank or gather width).  The scheduler takes the pending frames of every such session
+ *     of a bucket that has no launch in flight into one grouped launch: one host-to-device
+ *     copy of all their frames and of a work list, one front-end kernel over the list of
+ *     (session, frame) items, one interpolation kernel over (session, cell block, frame
+ *     block) items, one argmax pass, one device-to-host copy of all their maps.  Each
+ *     session still has at most one launch in flight, and its maps equal srp_map's on its
+ *     plan bit for bit.  Other sessions launch on their own.
  *   - Latency of a frame = completion of its map's D2H copy - its arrival time (the time
  *     its last sample was pushed, or the caller's t_arrival).
  * All functions are thread-safe.  The server owns its threads, streams and buffers.
@@ -435,6 +445,7 @@ typedef struct {
   int slots_per_session;  /* launches a session may have in flight or awaiting poll, 1..16 */
   int pending_frames;     /* pending-frame queue per session (>= max_batch) */
   int use_graphs;         /* 1: replay captured CUDA graphs; 0: issue launches directly */
+  int group_launches;     /* 1: sessions that qualify share launches (see below); 0: never */
 } srp_server_desc;
 
 typedef struct {
@@ -445,6 +456,9 @@ typedef struct {
   size_t device_bytes;        /* device memory held (or reserved) by admitted sessions */
   int sessions_active, sessions_queued;
   double latency_p50_s, latency_p99_s, latency_max_s;  /* over frames polled since reset */
+  long long group_launches;   /* of `launches`: grouped launches shared by several sessions */
+  long long group_frames;     /* frames they carried */
+  long long group_sessions;   /* session batches they carried (sum over the launches) */
 } srp_server_stats_t;
 
 enum { SRP_SESSION_QUEUED = 0, SRP_SESSION_ACTIVE = 1, SRP_SESSION_CLOSING = 2,

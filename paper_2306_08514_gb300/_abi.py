@@ -48,7 +48,7 @@ class srp_server_desc(C.Structure):
     _fields_ = [
         ("hbm_budget", C.c_size_t), ("max_sessions", C.c_int), ("max_batch", C.c_int),
         ("streams", C.c_int), ("slots_per_session", C.c_int), ("pending_frames", C.c_int),
-        ("use_graphs", C.c_int),
+        ("use_graphs", C.c_int), ("group_launches", C.c_int),
     ]
 
 
@@ -58,6 +58,8 @@ class srp_server_stats_t(C.Structure):
         ("launches", C.c_longlong), ("graph_launches", C.c_longlong),
         ("device_bytes", C.c_size_t), ("sessions_active", C.c_int), ("sessions_queued", C.c_int),
         ("latency_p50_s", C.c_double), ("latency_p99_s", C.c_double), ("latency_max_s", C.c_double),
+        ("group_launches", C.c_longlong), ("group_frames", C.c_longlong),
+        ("group_sessions", C.c_longlong),
     ]
 
 
@@ -440,12 +442,13 @@ class Server:
     streams, CUDA-graph replay.  Host numpy in, host numpy out."""
 
     def __init__(self, hbm_budget=8 << 30, max_sessions=64, max_batch=16, streams=8,
-                 slots_per_session=2, pending_frames=None, use_graphs=True):
+                 slots_per_session=2, pending_frames=None, use_graphs=True, group_launches=True):
         d = srp_server_desc()
         d.hbm_budget, d.max_sessions, d.max_batch = int(hbm_budget), int(max_sessions), int(max_batch)
         d.streams, d.slots_per_session = int(streams), int(slots_per_session)
         d.pending_frames = int(pending_frames or 8 * max_batch)
         d.use_graphs = 1 if use_graphs else 0
+        d.group_launches = 1 if group_launches else 0
         self.desc = d
         self.handle = C.c_void_p()
         _check(lib().srp_server_create(C.byref(d), C.byref(self.handle)))

@@ -311,11 +311,156 @@ __global__ __launch_bounds__(N / 8) void gcc_samples_kernel(
     for (int c = L + j; c < out_cols; c += T) put_op_rt(ot, out, out_lo, row + c, 0.f);
 }
 
+// ---------------------------------------------------------------------------------
+// Sampling for N = 1024 with the frame's y-hat held in shared memory.  One block per
+// frame loads y-hat [M][K] once; each warp takes pairs of pairs (2t, 2t+1) in turn and
+// forms psi-bar_a + i psi-bar_b (two-sided, Eq. psi_p_two) straight from it.  The
+// 1024-point inverse DFT runs as 32 x 32 Cooley-Tukey: with n = 32 n1 + n2 and
+// k = k1 + 32 k2, lane n2 takes the 32-point DFT over n1 in registers, multiplies output k1
+// by W^(n2 k1) (W = exp(+2 pi i / 1024)), one warp-local transpose through shared memory
+// hands lane k1 the values of every n2, and a second 32-point DFT over n2 gives
+// X[k1 + 32 k2] in lane k1.  The samples of lags -N_p..N_p (index mod(n, N), Eq. n_prime)
+// leave coalesced, ascending.
+// ---------------------------------------------------------------------------------
+// cos(j pi / 16), j = 0..8
+__device__ __forceinline__ constexpr float cos_pi16(int j) {
+  return j == 0 ? 1.0f
+       : j == 1 ? 0.98078528040323044913f
+       : j == 2 ? 0.92387953251128675613f
+       : j == 3 ? 0.83146961230254523708f
+       : j == 4 ? 0.70710678118654752440f
+       : j == 5 ? 0.55557023301960222474f
+       : j == 6 ? 0.38268343236508977173f
+       : j == 7 ? 0.19509032201612826785f
+                : 0.0f;
+}
+
+__device__ __forceinline__ constexpr int bitrev5(int i) {
+  return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
+}
+
+// 32-point DFT in place (natural order in and out; exp(-2 pi i kn/32), exp(+...) when INV):
+// bit reversal, then five radix-2 stages with the twiddles as constants.
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&x)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int r = bitrev5(i);
+    if (i < r) {
+      const float2 t = x[i];
+      x[i] = x[r];
+      x[r] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < 32; half <<= 1) {
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const int e = j * (16 / half);  // twiddle exp(-+2 pi i e / 32), e = 0..15
+      const float c = e <= 8 ? cos_pi16(e) : -cos_pi16(16 - e);
+      const float sn = e <= 8 ? cos_pi16(8 - e) : cos_pi16(e - 8);
+#pragma unroll
+      for (int k = j; k < 32; k += 2 * half) {
+        float2 t = x[k + half];
+        if (e == 8) {
+          t = INV ? make_float2(-t.y, t.x) : make_float2(t.y, -t.x);
+        } else if (e != 0) {
+          t = cmul(INV ? make_float2(c, sn) : make_float2(c, -sn), t);
+        }
+        x[k + half] = csub(x[k], t);
+        x[k] = cadd(x[k], t);
+      }
+    }
+  }
+}
+
+constexpr int kS32Warps = 4;
+
+__global__ __launch_bounds__(32 * kS32Warps, 1) void gcc_samples32_kernel(
+    const float2* __restrict__ yhat, int M, int P, const int2* __restrict__ pairs,
+    const int* __restrict__ Np, const int* __restrict__ off, int L,
+    const float2* __restrict__ twiddle, int ot, void* out, void* out_lo, int out_cols) {
+  constexpr int N = 1024, K = 512;
+  extern __shared__ float4 sm4[];
+  float2* ys = reinterpret_cast<float2*>(sm4);  // [M][K]
+  float2* tr = ys + static_cast<size_t>(M) * K; // [warps][32][33]
+  const int f = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const float4* src = reinterpret_cast<const float4*>(yhat + static_cast<size_t>(f) * M * K);
+    for (int e = threadIdx.x; e < M * K / 2; e += blockDim.x) sm4[e] = __ldg(src + e);
+  }
+  __syncthreads();
+  float2* T = tr + warp * 32 * 33;
+  const size_t row = static_cast<size_t>(f) * out_cols;
+  for (int tp = warp; 2 * tp < P; tp += kS32Warps) {
+    const int pa = 2 * tp, pb = pa + 1;
+    const bool hasb = pb < P;
+    const int2 qa = __ldg(pairs + pa);
+    const int2 qb = hasb ? __ldg(pairs + pb) : make_int2(0, 0);
+    float2 x[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) {
+      const int k = 32 * n1 + lane;
+      float2 v = make_float2(0.f, 0.f);
+      if (k != 0 && k != K) {
+        const int kk = n1 < 16 ? k : N - k;
+        const float2 a = cmul_conj(ys[qa.x * K + kk], ys[qa.y * K + kk]);
+        const float2 b = hasb ? cmul_conj(ys[qb.x * K + kk], ys[qb.y * K + kk]) : make_float2(0.f, 0.f);
+        v = n1 < 16 ? make_float2(a.x - b.y, a.y + b.x)   // psi_a + i psi_b
+                    : make_float2(a.x + b.y, b.x - a.y);  // psi_a^* + i psi_b^* (mirror)
+      }
+      x[n1] = v;
+    }
+    dft32<true>(x);
+#pragma unroll
+    for (int k1 = 1; k1 < 32; ++k1) {
+      const int e = lane * k1;  // < N; the table holds exp(-2 pi i e / N) for e < N/2
+      const float2 w = __ldg(twiddle + (e & (K - 1)));
+      const float sg = e < K ? 1.f : -1.f;
+      x[k1] = cmul(x[k1], make_float2(sg * w.x, -sg * w.y));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) T[k1 * 33 + lane] = x[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) x[n2] = T[lane * 33 + n2];
+    __syncwarp();
+    dft32<true>(x);  // lane k1 now holds X[k1 + 32 k2] in x[k2]
+    const int na = __ldg(Np + pa);
+    const size_t oa = row + __ldg(off + pa);
+    const int nb = hasb ? __ldg(Np + pb) : 0;
+    const size_t ob = hasb ? row + __ldg(off + pb) : 0;
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+      const int idx = lane + 32 * k2;
+      const int n = idx < K ? idx : idx - N;  // the lag of this output
+      if (n >= -na && n <= na) put_op_rt(ot, out, out_lo, oa + n + na, x[k2].x);
+      if (hasb && n >= -nb && n <= nb) put_op_rt(ot, out, out_lo, ob + n + nb, x[k2].y);
+    }
+  }
+  if (warp == 0)  // the operand's zero padding beyond L
+    for (int c = L + lane; c < out_cols; c += 32) put_op_rt(ot, out, out_lo, row + c, 0.f);
+}
+
+size_t gcc_samples32_smem(int M) {
+  return sizeof(float2) * (static_cast<size_t>(M) * 512 + kS32Warps * 32 * 33);
+}
+
 cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
                                const int* Np, const int* off, int L, const float2* twiddle,
                                OpType t, void* out, void* out_lo, int out_cols, cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
   if (out_cols < L) return cudaErrorInvalidValue;
+  if (N == 1024 && gcc_samples32_smem(M) <= 200 * 1024) {
+    const size_t smem = gcc_samples32_smem(M);
+    cudaError_t e = cudaFuncSetAttribute(gcc_samples32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    gcc_samples32_kernel<<<F, 32 * kS32Warps, smem, s>>>(yhat, M, P, pairs, Np, off, L, twiddle,
+                                                         static_cast<int>(t), out, out_lo, out_cols);
+    return cudaGetLastError();
+  }
   if (F > kMaxGridY) {
     cudaError_t e = launch_gcc_samples(yhat, kMaxGridY, M, P, N, pairs, Np, off, L, twiddle, t,
                                        out, out_lo, out_cols, s);
@@ -475,26 +620,7 @@ cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, co
 // of the conv. FD-SRP / LR-SRP operand.  Saves the y-hat round trip through global memory
 // and the separate sampling, packing and Lambda_fat launches.
 // ---------------------------------------------------------------------------------
-struct FrontParams {
-  const float* frames;
-  int M, P, L;
-  const float* window;
-  const float2* twiddle;
-  const int2* pairs;
-  const int* Np;
-  const int* off;
-  const uint4* stab;  // sampling operand in fragment order (front_sampling_table)
-  int nq0, NT;        // lag offset of its columns (max N_p) and its n-tiles
-  int fbuf_floats;    // FFT buffers / sampling partials (floats)
-  const uint4* ftab;  // SLRI: Lambda_fat in fragment order (front_fat_table); NULL: write xi
-  int Rp;
-  int out_cols;       // row length of the output (L, Lpad, Rp or 64)
-  float scale;        // applied to u before packing
-  int ot;             // operand type of the output
-  void* out;
-  void* out_lo;
-  int conv_out;       // 1: write the conv operand row [P*N] of psi instead of sampling
-};
+// FrontParams (srp_internal.h): the per-batch arguments of the fused front kernel.
 
 // D += A B for one m16n8k16 tile on the warp-level tensor cores (FP16 in, FP32 accumulate).
 // Fragments: a[0] = (row g, K cols 2t, 2t+1), a[1] = (row g+8, same), a[2] / a[3] = the
@@ -526,7 +652,7 @@ __host__ __device__ constexpr int front_row(int K) { return K + 4; }
 // One CTA of 256 threads per frame; H = N/2 is the complex FFT length (= K), NTM bounds
 // the n-tiles of the sampling GEMM.
 template <int H, int NTM>
-__global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_kernel(const FrontParams a) {
+__device__ __forceinline__ void front_body(const FrontParams& a, const int f) {
   extern __shared__ float2 sm[];
   constexpr int N = 2 * H, K = H, KS = front_row(K);
   constexpr int Tg = H / 8;              // threads per channel group (radix-8 FFT)
@@ -538,7 +664,6 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
   float2* fbuf = yh + static_cast<size_t>(M) * KS;   // FFT buffers / GEMM partials
   float* xis = reinterpret_cast<float*>(fbuf) + a.fbuf_floats;  // L
   const int tid = threadIdx.x;
-  const int f = blockIdx.x;
   for (int t = tid; t < H; t += 256) tw[t] = a.twiddle[t];
   // each thread owns the complex samples j + i Tg (i = 0..7) of its group's channel
   const int grp = tid / Tg, j = tid - grp * Tg;
@@ -741,6 +866,58 @@ __global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_ke
       put_op_rt(a.ot, a.out, a.out_lo, row + r, u * a.scale);
     }
   }
+}
+
+template <int H, int NTM>
+__global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_kernel(const FrontParams a) {
+  front_body<H, NTM>(a, blockIdx.x);
+}
+
+// Grouped front end (serving): items[i] = (index into params, frame within that list
+// entry's batch); blocks walk the items the host counted (*count), so one launch serves the
+// frames of many sessions.  Every session in a launch shares H and NTM; the dynamic shared
+// memory covers the largest of them.
+template <int H, int NTM>
+__global__ __launch_bounds__(256, NTM <= 2 ? 4 : NTM <= 4 ? 3 : 2) void front_group_kernel(
+    const FrontParams* __restrict__ params, const int2* __restrict__ items,
+    const int* __restrict__ count) {
+  const int n = *count;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int2 it = items[i];
+    const FrontParams a = params[it.x];
+    front_body<H, NTM>(a, it.y);
+    __syncthreads();  // the next item reuses the shared memory
+  }
+}
+
+cudaError_t launch_front_group(const FrontParams* params, const int2* items, const int* count,
+                               int grid, int N, int NTM, size_t smem, cudaStream_t s) {
+  const int H = N / 2;
+  void (*kern)(const FrontParams*, const int2*, const int*) = nullptr;
+#define SRP_FRONT_G(HV, NTV) if (H == HV && NTM == NTV) kern = front_group_kernel<HV, NTV>;
+  SRP_FRONT_G(128, 2) SRP_FRONT_G(128, 4) SRP_FRONT_G(128, 9)
+  SRP_FRONT_G(256, 2) SRP_FRONT_G(256, 4) SRP_FRONT_G(256, 9)
+  SRP_FRONT_G(512, 2) SRP_FRONT_G(512, 4) SRP_FRONT_G(512, 9)
+#undef SRP_FRONT_G
+  if (!kern || grid < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, smem, s>>>(params, items, count);
+  return cudaGetLastError();
+}
+
+// The parameters launch_front would pass (the caller fills frames and out per batch).
+FrontParams front_params(int M, int N, const float* window, const float2* twiddle, int P,
+                         const int2* pairs, const int* Np, const int* off, const uint4* stab,
+                         int L, int max_Np, const uint4* ftab, int Rp, int out_cols, float scale,
+                         OpType t) {
+  const int H = N / 2, groups = 256 / (H / 8);
+  const int NTM = front_ntm(max_Np);
+  const int fbuf_floats = std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * NTM);
+  return FrontParams{nullptr, M, P, L, window, twiddle, pairs, Np, off, stab, max_Np,
+                     front_ntiles(max_Np), fbuf_floats, ftab, Rp, out_cols, scale,
+                     static_cast<int>(t), nullptr, nullptr, 0};
 }
 
 int front_max_N() { return 1024; }

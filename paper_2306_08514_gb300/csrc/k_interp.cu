@@ -88,17 +88,17 @@ cudaError_t launch_slri_fat(const float* xi, const float* fat, float* U, int F, 
 // frame is reduced per warp, then per block, then merged with one atomicMax.
 // ---------------------------------------------------------------------------------
 template <int R, int CPT>
-__global__ __launch_bounds__(256) void slri_tall_kernel(const float* __restrict__ U,
-                                                        const float* __restrict__ tall,
-                                                        float* __restrict__ Z,
-                                                        unsigned long long* __restrict__ keys,
-                                                        int F, int J, int FB) {
+__device__ __forceinline__ void slri_tall_body(const float* __restrict__ U,
+                                               const float* __restrict__ tall,
+                                               float* __restrict__ Z,
+                                               unsigned long long* __restrict__ keys, int F,
+                                               int J, int FB, int bx, int by) {
   extern __shared__ float4 sm4[];
   float* Us = reinterpret_cast<float*>(sm4);                                  // [FB][R]
   unsigned long long* red = reinterpret_cast<unsigned long long*>(Us + FB * R);  // [8][FB]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ibase = blockIdx.x * (256 * CPT);
-  const int f0 = blockIdx.y * FB;
+  const int ibase = bx * (256 * CPT);
+  const int f0 = by * FB;
   const int nf = min(FB, F - f0);
   for (int e = tid; e < nf * R; e += 256) Us[e] = U[static_cast<size_t>(f0) * R + e];
   float t[CPT][R];
@@ -159,6 +159,61 @@ __global__ __launch_bounds__(256) void slri_tall_kernel(const float* __restrict_
 }
 
 template <int R, int CPT>
+__global__ __launch_bounds__(256) void slri_tall_kernel(const float* __restrict__ U,
+                                                        const float* __restrict__ tall,
+                                                        float* __restrict__ Z,
+                                                        unsigned long long* __restrict__ keys,
+                                                        int F, int J, int FB) {
+  slri_tall_body<R, CPT>(U, tall, Z, keys, F, J, FB, blockIdx.x, blockIdx.y);
+}
+
+// Grouped (serving): items (session, cell block, frame block of 64), walked by the CTAs.
+template <int R, int CPT>
+__global__ __launch_bounds__(256) void slri_tall_group_kernel(const GroupInterp* __restrict__ g,
+                                                              const int4* __restrict__ items,
+                                                              const int* __restrict__ count) {
+  const int n = *count;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int4 it = items[i];
+    const GroupInterp e = g[it.x];
+    slri_tall_body<R, CPT>(e.in, e.tall, e.Z, e.keys, e.F, e.J, 64, it.y, it.z);
+    __syncthreads();  // the next item reuses the shared memory
+  }
+}
+
+template <int R, int CPT>
+static cudaError_t run_tall_group(const GroupInterp* g, const int4* items, const int* count,
+                                  int grid, cudaStream_t s) {
+  const size_t smem = sizeof(float) * 64 * R + sizeof(unsigned long long) * 8 * 64;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(slri_tall_group_kernel<R, CPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  slri_tall_group_kernel<R, CPT><<<grid, 256, smem, s>>>(g, items, count);
+  return cudaGetLastError();
+}
+
+int slri_tall_cells_per_block(int Rp) { return 256 * (Rp <= 16 ? 4 : Rp <= 32 ? 2 : 1); }
+
+cudaError_t launch_slri_tall_group(const GroupInterp* g, const int4* items, const int* count,
+                                   int grid, int Rp, cudaStream_t s) {
+  if (grid < 1) return cudaErrorInvalidValue;
+  switch (Rp) {  // the cells per thread of launch_slri_tall
+    case 8: return run_tall_group<8, 4>(g, items, count, grid, s);
+    case 16: return run_tall_group<16, 4>(g, items, count, grid, s);
+    case 24: return run_tall_group<24, 2>(g, items, count, grid, s);
+    case 32: return run_tall_group<32, 2>(g, items, count, grid, s);
+    case 40: return run_tall_group<40, 1>(g, items, count, grid, s);
+    case 48: return run_tall_group<48, 1>(g, items, count, grid, s);
+    case 56: return run_tall_group<56, 1>(g, items, count, grid, s);
+    case 64: return run_tall_group<64, 1>(g, items, count, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int R, int CPT>
 static cudaError_t run_tall(const float* U, const float* tall, float* Z, unsigned long long* keys,
                             int F, int J, cudaStream_t s) {
   const int FB = 64;
@@ -198,25 +253,24 @@ cudaError_t launch_slri_tall(const float* U, const float* tall, float* Z,
 // written coalesced and the argmax is reduced per frame.
 // ---------------------------------------------------------------------------------
 template <int FPL>
-__global__ __launch_bounds__(256) void sspi_kernel(const float* __restrict__ xi,
-                                                   const long long* __restrict__ row_ptr,
-                                                   const int2* __restrict__ taps,
-                                                   float* __restrict__ Z,
-                                                   unsigned long long* __restrict__ keys, int F,
-                                                   int J, int L, int nrb) {
+__device__ __forceinline__ void sspi_body(const float* __restrict__ xi,
+                                          const long long* __restrict__ row_ptr,
+                                          const int2* __restrict__ taps, float* __restrict__ Z,
+                                          unsigned long long* __restrict__ keys, int F, int J,
+                                          int L, int fx, int rb_begin, int rb_end, int rb_step) {
   constexpr int FB = 32 * FPL, RB = 64, XS = FB + 1, OS = RB + 1;
   extern __shared__ float sm[];
   float* xs = sm;            // [L][XS]
   float* os = sm + L * XS;   // [FB][OS]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int f0 = blockIdx.x * FB;
+  const int f0 = fx * FB;
   const int nf = min(FB, F - f0);
   for (int e = tid; e < FB * L; e += 256) {
     const int fb = e / L, l = e - fb * L;
     xs[l * XS + fb] = fb < nf ? xi[static_cast<size_t>(f0 + fb) * L + l] : 0.f;
   }
   __syncthreads();
-  for (int rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
+  for (int rb = rb_begin; rb < rb_end; rb += rb_step) {
     const int i0 = rb * RB;
     for (int rr = warp; rr < RB; rr += 8) {
       const int i = i0 + rr;
@@ -257,6 +311,30 @@ __global__ __launch_bounds__(256) void sspi_kernel(const float* __restrict__ xi,
       if (lane == 0 && best) atomicMax(keys + f0 + fb, best);
     }
     __syncthreads();
+  }
+}
+
+template <int FPL>
+__global__ __launch_bounds__(256) void sspi_kernel(const float* __restrict__ xi,
+                                                   const long long* __restrict__ row_ptr,
+                                                   const int2* __restrict__ taps,
+                                                   float* __restrict__ Z,
+                                                   unsigned long long* __restrict__ keys, int F,
+                                                   int J, int L, int nrb) {
+  sspi_body<FPL>(xi, row_ptr, taps, Z, keys, F, J, L, blockIdx.x, blockIdx.y, nrb, gridDim.y);
+}
+
+// Grouped (serving): items (session, frame group, first row block, end row block).
+template <int FPL>
+__global__ __launch_bounds__(256) void sspi_group_kernel(const GroupInterp* __restrict__ g,
+                                                         const int4* __restrict__ items,
+                                                         const int* __restrict__ count) {
+  const int n = *count;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int4 it = items[i];
+    const GroupInterp e = g[it.x];
+    sspi_body<FPL>(e.in, e.row_ptr, e.taps, e.Z, e.keys, e.F, e.J, e.L, it.y, it.z, it.w, 1);
+    __syncthreads();  // the next item restages the shared memory
   }
 }
 
@@ -395,6 +473,27 @@ size_t sspi_band_smem(int U, int FB) {
 }
 
 bool sspi_full_fits(int L) { return sspi_smem<1>(L) <= 220 * 1024; }
+
+int sspi_group_frames(int Lmax) { return sspi_smem<2>(Lmax) <= 110 * 1024 ? 64 : 32; }
+
+cudaError_t launch_sspi_group(const GroupInterp* g, const int4* items, const int* count, int grid,
+                              int Lmax, cudaStream_t s) {
+  if (grid < 1 || !sspi_full_fits(Lmax)) return cudaErrorInvalidValue;
+  if (sspi_group_frames(Lmax) == 64) {
+    const size_t smem = sspi_smem<2>(Lmax);
+    cudaError_t e = cudaFuncSetAttribute(sspi_group_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    sspi_group_kernel<2><<<grid, 256, smem, s>>>(g, items, count);
+  } else {
+    const size_t smem = sspi_smem<1>(Lmax);
+    cudaError_t e = cudaFuncSetAttribute(sspi_group_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    sspi_group_kernel<1><<<grid, 256, smem, s>>>(g, items, count);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sspi_band(const float* xi, const long long* row_ptr, const int2* taps,
                              const long long* blk_ptr, const int* blk_cols, int umax, int FB,

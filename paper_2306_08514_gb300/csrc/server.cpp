@@ -15,6 +15,12 @@
 //   * CUDA graphs: the launch sequence of a slot and batch size (H2D frames, the whole
 //     SRP path, D2H maps and argmax, completion callback) is captured by the builder at
 //     admission, for every power-of-two batch size, and replayed by the scheduler.
+//   * Grouped launches: sessions with FP32 plans on the fused front end (SLRI, or SSPI with
+//     the whole-vector gather) are bucketed by (method, N, sampling tiles, padded rank or
+//     gather width); the pending frames of every such session of a bucket that has no
+//     launch in flight leave together: one copy of all their frames and of a work list in,
+//     one front-end kernel over (session, frame) items, one interpolation kernel over
+//     (session, cell block, frame block) items, one argmax pass, one copy of all maps out.
 //   * Latency: each frame carries its arrival time (when its last sample was pushed);
 //     the completion callback stamps the time its map is in host memory.
 #include "srp_internal.h"
@@ -48,6 +54,7 @@ int floor_log2(int v) {
 
 struct Server;
 struct Session;
+struct GroupSlot;
 
 // One launch slot: pinned host and device buffers for up to max_batch frames.
 struct Slot {
@@ -66,6 +73,7 @@ struct Slot {
   std::vector<long long> idx;
   std::vector<double> t_arr;
   std::vector<cudaGraphExec_t> graphs;  // per log2(batch)
+  GroupSlot* group = nullptr;  // grouped launch carrying this batch (h_maps / h_arg point into it)
 };
 
 enum {
@@ -94,6 +102,35 @@ struct Session {
   std::vector<std::unique_ptr<Slot>> slots;
   long long launch_seq = 0;
   long long frames_done = 0;
+  // grouped launches (FP32 plans on the fused front end, SLRI or whole-vector SSPI)
+  bool grouped = false;
+  long long gkey = 0;        // bucket
+  FrontParams fp{};          // front-end arguments (frames and out filled per launch)
+  int cols = 0;              // front-end output row: Rp (SLRI) or L (SSPI)
+  size_t front_smem = 0;
+  int Rp = 0, L = 0, nrb = 0;
+};
+
+// One grouped launch in flight or awaiting polls: pinned host and device buffers shared by
+// the sessions it carries.
+struct GroupSlot {
+  cudaStream_t stream = nullptr;
+  int cap_frames = 0, cap_items = 0;
+  size_t cap_in = 0, cap_out = 0, cap_scr = 0, cap_desc = 0;  // floats / bytes
+  float* h_in = nullptr;   // pinned frames
+  float* d_in = nullptr;
+  float* h_out = nullptr;  // pinned maps
+  float* d_out = nullptr;
+  int* h_arg = nullptr;
+  int* d_arg = nullptr;
+  float* d_scr = nullptr;  // front-end outputs (u or xi)
+  unsigned long long* d_keys = nullptr;
+  char* h_desc = nullptr;  // work list: counts, front arguments, interpolation arguments, items
+  char* d_desc = nullptr;
+  std::atomic<int> state{0};  // 0 free, 1 in flight, 2 done (members await polls)
+  int refs = 0;               // member batches not yet polled
+  std::vector<Slot*> members;
+  Server* server = nullptr;
 };
 
 struct Server {
@@ -111,8 +148,11 @@ struct Server {
   bool stop = false;
   bool building = false;
   std::thread sched, builder;
+  std::vector<std::unique_ptr<GroupSlot>> gslots;  // grouped launches (made on first use)
+  int num_sms = 0;
   // stats
   long long frames_done = 0, launches = 0, graph_launches = 0, frames_launched = 0;
+  long long group_launches = 0, group_frames = 0, group_sessions = 0;
   std::vector<float> latencies;
   std::atomic<int> completions{0};
 };
@@ -130,6 +170,11 @@ void CUDART_CB done_cb(void* u) {
 }
 
 void free_slot(Slot* sl) {
+  if (sl->group) {  // maps and argmax lived in the grouped launch's buffers
+    sl->h_maps = nullptr;
+    sl->h_arg = nullptr;
+    sl->group = nullptr;
+  }
   for (cudaGraphExec_t g : sl->graphs)
     if (g) cudaGraphExecDestroy(g);
   sl->graphs.clear();
@@ -143,8 +188,22 @@ void free_slot(Slot* sl) {
   sl->h_arg = sl->d_arg = nullptr;
 }
 
+// A batch of a grouped launch is consumed (polled, or dropped with its session).  The
+// launch's buffers are free again once it is done and every batch it carried is consumed
+// (the scheduler checks; the completion callback may still be running until it marks the
+// launch done, so nothing else touches the member list).  Called with the server lock held.
+void group_batch_done(Slot* sl) {
+  GroupSlot* g = sl->group;
+  sl->h_maps = nullptr;
+  sl->h_arg = nullptr;
+  sl->group = nullptr;
+  if (g) --g->refs;
+}
+
 void release_session(Server& sv, Session& ss) {
   if (ss.stream) cudaStreamSynchronize(ss.stream);
+  for (auto& sl : ss.slots)
+    if (sl->group && sl->state.load() == 2) group_batch_done(sl.get());
   for (auto& sl : ss.slots) free_slot(sl.get());
   ss.slots.clear();
   if (ss.plan) srp_destroy(ss.plan);
@@ -234,13 +293,285 @@ void schedule_session(Server& sv, Session& ss) {
   }
 }
 
+// ------------------------------------------------------------------ grouped launches
+constexpr int kGroupSlots = 4;
+constexpr size_t kGroupInFloats = size_t(8) << 20;    // 32 MB of frames per launch
+constexpr size_t kGroupOutFloats = size_t(16) << 20;  // 64 MB of maps per launch
+constexpr int kGroupMaxCols = 1664;                   // front-end output row (Rp or L <= 1643)
+constexpr int kGroupItems = 1 << 16;                  // interpolation work items per launch
+constexpr int kSspiRowChunk = 8;                      // row blocks of 64 cells per SSPI item
+
+size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+long long group_key(const srp_plan_s* P) {
+  const int method = P->desc.method == SRP_SLRI ? 1 : 2;
+  const int w = P->desc.method == SRP_SLRI ? (P->R + 7) / 8 * 8 : sspi_group_frames(P->g.L);
+  return (static_cast<long long>(method) << 40) | (static_cast<long long>(P->g.N) << 24) |
+         (static_cast<long long>(front_ntm(P->max_Np)) << 16) | w;
+}
+
+bool group_eligible(const srp_plan_s* P) {
+  return P->op == OpType::F32 && P->use_front &&
+         (P->desc.method == SRP_SLRI || (P->desc.method == SRP_SSPI && P->sspi_umax == 0)) &&
+         ((P->R + 7) / 8 * 8 <= kGroupMaxCols) && P->g.L <= kGroupMaxCols;
+}
+
+void free_group(GroupSlot* g) {
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->h_in) cudaFreeHost(g->h_in);
+  if (g->h_out) cudaFreeHost(g->h_out);
+  if (g->h_arg) cudaFreeHost(g->h_arg);
+  if (g->h_desc) cudaFreeHost(g->h_desc);
+  void* d[] = {g->d_in, g->d_out, g->d_arg, g->d_scr, g->d_keys, g->d_desc};
+  for (void* q : d)
+    if (q) cudaFree(q);
+  if (g->stream) cudaStreamDestroy(g->stream);
+}
+
+// The grouped launches' buffers, made once by the builder thread (outside the server lock)
+// when the first session that qualifies is admitted.  Returns false if they cannot be
+// allocated (the session then launches on its own).
+bool make_groups(const Server& sv, std::vector<std::unique_ptr<GroupSlot>>& out) {
+  const int cap_frames = std::min(4096, sv.desc.max_batch * sv.desc.max_sessions);
+  std::vector<std::unique_ptr<GroupSlot>> gs;
+  bool ok = true;
+  for (int i = 0; i < kGroupSlots && ok; ++i) {
+    auto g = std::make_unique<GroupSlot>();
+    g->server = const_cast<Server*>(&sv);
+    g->cap_frames = cap_frames;
+    g->cap_items = kGroupItems;
+    g->cap_in = kGroupInFloats;
+    g->cap_out = kGroupOutFloats;
+    g->cap_scr = static_cast<size_t>(cap_frames) * kGroupMaxCols;
+    g->cap_desc = align16(16) + align16(sizeof(FrontParams) * cap_frames) +
+                  align16(sizeof(GroupInterp) * cap_frames) + align16(sizeof(int2) * cap_frames) +
+                  align16(sizeof(int4) * g->cap_items);
+    ok = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaMallocHost(&g->h_in, 4 * g->cap_in) == cudaSuccess &&
+         cudaMallocHost(&g->h_out, 4 * g->cap_out) == cudaSuccess &&
+         cudaMallocHost(&g->h_arg, 4 * static_cast<size_t>(cap_frames)) == cudaSuccess &&
+         cudaMallocHost(&g->h_desc, g->cap_desc) == cudaSuccess &&
+         device_alloc(reinterpret_cast<void**>(&g->d_in), 4 * g->cap_in) == cudaSuccess &&
+         device_alloc(reinterpret_cast<void**>(&g->d_out), 4 * g->cap_out) == cudaSuccess &&
+         device_alloc(reinterpret_cast<void**>(&g->d_arg), 4 * static_cast<size_t>(cap_frames)) == cudaSuccess &&
+         device_alloc(reinterpret_cast<void**>(&g->d_scr), 4 * g->cap_scr) == cudaSuccess &&
+         device_alloc(reinterpret_cast<void**>(&g->d_keys), 8 * static_cast<size_t>(cap_frames)) == cudaSuccess &&
+         device_alloc(reinterpret_cast<void**>(&g->d_desc), g->cap_desc) == cudaSuccess;
+    gs.push_back(std::move(g));
+  }
+  if (!ok) {
+    cudaGetLastError();
+    for (auto& g : gs) free_group(g.get());
+    return false;
+  }
+  out = std::move(gs);
+  return true;
+}
+
+void CUDART_CB group_done_cb(void* u);
+
+// One grouped launch of bucket `key` carrying the pending frames of `list` (sessions with no
+// launch in flight and a free slot), as many as the launch's buffers hold.  Called with the
+// server lock held.
+void issue_group(Server& sv, GroupSlot& g, long long key, const std::vector<Session*>& list) {
+  const bool slri = (key >> 40) == 1;
+  const int N = static_cast<int>((key >> 24) & 0xFFFF);
+  const int NTM = static_cast<int>((key >> 16) & 0xFF);
+  const int width = static_cast<int>(key & 0xFFFF);  // SLRI: Rp; SSPI: frames per item
+  struct Entry {
+    Session* ss;
+    Slot* sl;
+    int b, f_off, n_items;
+    size_t in_off, out_off, scr_off;
+  };
+  std::vector<Entry> es;
+  size_t in = 0, out = 0, scr = 0;
+  int frames = 0, items = 0, Lmax = 0;
+  size_t smem = 0;
+  for (Session* ss : list) {
+    Slot* sl = nullptr;
+    for (auto& x : ss->slots)
+      if (x->state.load() == 0) {
+        sl = x.get();
+        break;
+      }
+    if (!sl) continue;
+    const size_t fsz = static_cast<size_t>(ss->M) * ss->N;
+    const int cpb = slri ? slri_tall_cells_per_block(ss->Rp) : 0;
+    auto n_items = [&](int b) {
+      return slri ? ((ss->J + cpb - 1) / cpb) * ((b + 63) / 64)
+                  : ((b + width - 1) / width) * ((ss->nrb + kSspiRowChunk - 1) / kSspiRowChunk);
+    };
+    int b = std::min(ss->pend_count, sv.desc.max_batch);
+    while (b > 0 && (frames + b > g.cap_frames || in + b * fsz > g.cap_in ||
+                     out + static_cast<size_t>(b) * ss->J > g.cap_out ||
+                     scr + static_cast<size_t>(b) * ss->cols > g.cap_scr ||
+                     items + n_items(b) > g.cap_items))
+      --b;
+    if (b == 0) break;  // the launch is full; the rest leave with the next one
+    es.push_back({ss, sl, b, frames, n_items(b), in, out, scr});
+    in += (b * fsz + 3) & ~size_t(3);
+    out += (static_cast<size_t>(b) * ss->J + 3) & ~size_t(3);
+    scr += (static_cast<size_t>(b) * ss->cols + 3) & ~size_t(3);
+    frames += b;
+    items += n_items(b);
+    Lmax = std::max(Lmax, ss->L);
+    smem = std::max(smem, ss->front_smem);
+  }
+  if (es.empty()) return;
+  const int E = static_cast<int>(es.size());
+  // work list in pinned memory: counts | front arguments | interpolation arguments | items
+  char* h = g.h_desc;
+  const size_t o_fp = 16, o_gi = o_fp + align16(sizeof(FrontParams) * E),
+               o_fi = o_gi + align16(sizeof(GroupInterp) * E), o_ci = o_fi + align16(sizeof(int2) * frames),
+               desc_bytes = o_ci + align16(sizeof(int4) * items);
+  int* counts = reinterpret_cast<int*>(h);
+  FrontParams* fp = reinterpret_cast<FrontParams*>(h + o_fp);
+  GroupInterp* gi = reinterpret_cast<GroupInterp*>(h + o_gi);
+  int2* fi = reinterpret_cast<int2*>(h + o_fi);
+  int4* ci = reinterpret_cast<int4*>(h + o_ci);
+  int nfi = 0, nci = 0;
+  g.members.clear();
+  for (int e = 0; e < E; ++e) {
+    Entry& x = es[e];
+    Session& ss = *x.ss;
+    Slot& sl = *x.sl;
+    const size_t fsz = static_cast<size_t>(ss.M) * ss.N;
+    sl.idx.resize(x.b);
+    sl.t_arr.resize(x.b);
+    for (int j = 0; j < x.b; ++j) {
+      const int slot_i = (ss.pend_head + j) % ss.pend_cap;
+      std::memcpy(g.h_in + x.in_off + j * fsz, ss.pend.data() + slot_i * fsz, fsz * 4);
+      sl.idx[j] = ss.pend_idx[slot_i];
+      sl.t_arr[j] = ss.pend_t[slot_i];
+    }
+    ss.pend_head = (ss.pend_head + x.b) % ss.pend_cap;
+    ss.pend_count -= x.b;
+    sl.b = x.b;
+    sl.seq = ss.launch_seq++;
+    sl.group = &g;
+    sl.h_maps = g.h_out + x.out_off;
+    sl.h_arg = g.h_arg + x.f_off;
+    sl.state.store(1);
+    g.members.push_back(&sl);
+    const srp_plan_s* P = ss.plan;
+    FrontParams a = ss.fp;
+    a.frames = g.d_in + x.in_off;
+    a.out = g.d_scr + x.scr_off;
+    a.out_lo = nullptr;
+    fp[e] = a;
+    gi[e] = GroupInterp{g.d_scr + x.scr_off, P->d_tall, P->d_row_ptr, P->d_taps, g.d_out + x.out_off,
+                        g.d_keys + x.f_off, x.b, ss.J, ss.L};
+    for (int j = 0; j < x.b; ++j) fi[nfi++] = make_int2(e, j);
+    if (slri) {
+      const int cpb = slri_tall_cells_per_block(ss.Rp);
+      for (int by = 0; by < (x.b + 63) / 64; ++by)
+        for (int bx = 0; bx < (ss.J + cpb - 1) / cpb; ++bx) ci[nci++] = make_int4(e, bx, by, 0);
+    } else {
+      for (int fx = 0; fx < (x.b + width - 1) / width; ++fx)
+        for (int rb = 0; rb < ss.nrb; rb += kSspiRowChunk)
+          ci[nci++] = make_int4(e, fx, rb, std::min(rb + kSspiRowChunk, ss.nrb));
+    }
+  }
+  counts[0] = nfi;
+  counts[1] = nci;
+  g.refs = E;
+  g.state.store(1);
+  cudaStream_t s = g.stream;
+  const int* d_counts = reinterpret_cast<const int*>(g.d_desc);
+  const int cap_grid = 4 * std::max(1, sv.num_sms);
+  cudaError_t e = cudaMemcpyAsync(g.d_desc, g.h_desc, desc_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g.d_in, g.h_in, 4 * in, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.d_keys, 0, 8 * static_cast<size_t>(frames), s);
+  if (e == cudaSuccess)
+    e = launch_front_group(reinterpret_cast<const FrontParams*>(g.d_desc + o_fp),
+                           reinterpret_cast<const int2*>(g.d_desc + o_fi), d_counts,
+                           std::min(nfi, cap_grid), N, NTM, smem, s);
+  const GroupInterp* d_gi = reinterpret_cast<const GroupInterp*>(g.d_desc + o_gi);
+  const int4* d_ci = reinterpret_cast<const int4*>(g.d_desc + o_ci);
+  if (e == cudaSuccess)
+    e = slri ? launch_slri_tall_group(d_gi, d_ci, d_counts + 1, std::min(nci, cap_grid), width, s)
+             : launch_sspi_group(d_gi, d_ci, d_counts + 1, std::min(nci, cap_grid), Lmax, s);
+  if (e == cudaSuccess) e = launch_argmax_finalize(g.d_keys, g.d_arg, frames, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_out, g.d_out, 4 * out, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g.h_arg, g.d_arg, 4 * static_cast<size_t>(frames), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(s, group_done_cb, &g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    for (Entry& x : es) {
+      x.ss->error = std::string("grouped launch failed: ") + cudaGetErrorString(e);
+      x.ss->state = ST_FAILED;
+      x.sl->group = nullptr;
+      x.sl->h_maps = nullptr;
+      x.sl->h_arg = nullptr;
+      x.sl->state.store(0);
+    }
+    g.members.clear();
+    g.refs = 0;
+    g.state.store(0);
+    return;
+  }
+  ++sv.launches;
+  ++sv.group_launches;
+  sv.frames_launched += frames;
+  sv.group_frames += frames;
+  sv.group_sessions += E;
+}
+
+// Grouped launches for every bucket with work, one per free launch buffer set.  Called with
+// the server lock held.
+void schedule_groups(Server& sv) {
+  if (sv.gslots.empty()) return;
+  std::map<long long, std::vector<Session*>> buckets;
+  for (auto& kv : sv.sessions) {
+    Session& ss = *kv.second;
+    if (ss.state != ST_ACTIVE || !ss.grouped || ss.pend_count == 0) continue;
+    bool in_flight = false, has_free = false;
+    for (auto& sl : ss.slots) {
+      const int st = sl->state.load();
+      in_flight = in_flight || st == 1;
+      has_free = has_free || st == 0;
+    }
+    if (has_free && !in_flight) buckets[ss.gkey].push_back(&ss);
+  }
+  for (auto& kb : buckets) {
+    GroupSlot* g = nullptr;
+    for (auto& gs : sv.gslots) {
+      const int st = gs->state.load();
+      if (st == 0 || (st == 2 && gs->refs == 0)) {
+        g = gs.get();
+        break;
+      }
+    }
+    if (!g) return;
+    g->members.clear();
+    g->state.store(0);
+    issue_group(sv, *g, kb.first, kb.second);
+  }
+}
+
+void CUDART_CB group_done_cb(void* u) {
+  GroupSlot* g = static_cast<GroupSlot*>(u);
+  const double t = now_s();
+  for (Slot* sl : g->members) {
+    sl->done_t = t;
+    sl->state.store(2);
+  }
+  g->state.store(2);  // last: after this the callback no longer reads the member list
+  g->server->completions.fetch_add(1);
+  g->server->cv.notify_all();
+}
+
 void scheduler_loop(Server* sv) {
   cudaSetDevice(sv->device);
   std::unique_lock<std::mutex> lk(sv->mu);
   while (!sv->stop) {
+    schedule_groups(*sv);
     for (auto& kv : sv->sessions) {
       Session& ss = *kv.second;
-      if (ss.state == ST_ACTIVE) schedule_session(*sv, ss);
+      if (ss.state == ST_ACTIVE && !ss.grouped) schedule_session(*sv, ss);
       if (ss.state == ST_CLOSING || ss.state == ST_FAILED) {
         bool busy = false;
         for (auto& sl : ss.slots) busy = busy || sl->state.load() == 1;
@@ -257,6 +588,7 @@ void scheduler_loop(Server* sv) {
 
 void builder_loop(Server* sv) {
   cudaSetDevice(sv->device);
+  bool groups_made = false;  // the grouped launches' buffers (made by this thread only)
   std::unique_lock<std::mutex> lk(sv->mu);
   while (!sv->stop) {
     Session* pick = nullptr;
@@ -286,8 +618,26 @@ void builder_loop(Server* sv) {
     if (st == SRP_OK) st = srp_plan_autotune(plan, sv->desc.max_batch, sv->build_stream, nullptr);
     std::vector<std::unique_ptr<Slot>> slots;
     size_t bytes = 0;
+    // grouped launches: the session's batches travel in shared launch buffers, so its
+    // slots are bookkeeping only (no buffers, no graphs of their own)
+    bool grouped = false;
+    std::vector<std::unique_ptr<GroupSlot>> new_groups;
+    if (st == SRP_OK && sv->desc.group_launches && group_eligible(plan)) {
+      grouped = groups_made || make_groups(*sv, new_groups);
+      groups_made = groups_made || grouped;
+    }
     if (st != SRP_OK) {
       err = srp_last_error();
+    } else if (grouped) {
+      srp_plan_info_t info;
+      srp_plan_info(plan, &info);
+      bytes = info.device_bytes;
+      for (int i = 0; i < sv->desc.slots_per_session; ++i) {
+        auto sl = std::make_unique<Slot>();
+        sl->server = sv;
+        sl->owner = pick;
+        slots.push_back(std::move(sl));
+      }
     } else {
       srp_plan_info_t info;
       srp_plan_info(plan, &info);
@@ -338,6 +688,7 @@ void builder_loop(Server* sv) {
       }
     }
     lk.lock();
+    if (!new_groups.empty()) sv->gslots = std::move(new_groups);
     sv->used_bytes -= std::min(sv->used_bytes, pick->est_bytes);
     if (!err.empty()) {
       for (auto& sl : slots) free_slot(sl.get());
@@ -347,6 +698,21 @@ void builder_loop(Server* sv) {
       --sv->active;
     } else {
       pick->plan = plan;
+      if (grouped) {
+        const srp_plan_s* P = plan;
+        const Geometry& g = P->g;
+        const bool slri = P->desc.method == SRP_SLRI;
+        pick->grouped = true;
+        pick->gkey = group_key(P);
+        pick->Rp = (P->R + 7) / 8 * 8;
+        pick->L = g.L;
+        pick->nrb = (g.J + 63) / 64;
+        pick->cols = slri ? pick->Rp : g.L;
+        pick->front_smem = front_smem_bytes(g.M, g.N, g.L, P->max_Np);
+        pick->fp = front_params(g.M, g.N, P->d_window, P->d_twiddle, g.P, P->d_pairs, P->d_Np,
+                                P->d_off, P->d_stab, g.L, P->max_Np, slri ? P->d_ftab : nullptr,
+                                pick->Rp, pick->cols, 1.f, OpType::F32);
+      }
       pick->slots = std::move(slots);
       pick->bytes = bytes;
       sv->used_bytes += bytes;
@@ -387,6 +753,7 @@ extern "C" srp_status srp_server_create(const srp_server_desc* desc, srp_server_
   auto sv = std::make_unique<Server>();
   sv->desc = *desc;
   SRP_CUDA_TRY(cudaGetDevice(&sv->device));
+  SRP_CUDA_TRY(cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->device));
   for (int i = 0; i < desc->streams; ++i) {
     cudaStream_t s;
     SRP_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -509,6 +876,7 @@ extern "C" srp_status srp_server_poll(srp_server_t server, int session, int max_
     n += next->b;
     ss.frames_done += next->b;
     sv->frames_done += next->b;
+    if (next->group) group_batch_done(next);
     next->state.store(0);
   }
   *n_out = n;
@@ -574,6 +942,9 @@ extern "C" srp_status srp_server_stats(srp_server_t server, srp_server_stats_t* 
   st->frames_launched = sv->frames_launched;
   st->launches = sv->launches;
   st->graph_launches = sv->graph_launches;
+  st->group_launches = sv->group_launches;
+  st->group_frames = sv->group_frames;
+  st->group_sessions = sv->group_sessions;
   st->device_bytes = sv->used_bytes;
   for (auto& kv : sv->sessions) {
     const int s = kv.second->state;
@@ -601,6 +972,7 @@ extern "C" srp_status srp_server_reset_stats(srp_server_t server) {
   std::lock_guard<std::mutex> lk(sv->mu);
   sv->latencies.clear();
   sv->frames_done = sv->frames_launched = sv->launches = sv->graph_launches = 0;
+  sv->group_launches = sv->group_frames = sv->group_sessions = 0;
   return SRP_OK;
 }
 
@@ -618,10 +990,14 @@ extern "C" void srp_server_destroy(srp_server_t server) {
   if (sv->sched.joinable()) sv->sched.join();
   if (sv->builder.joinable()) sv->builder.join();
   for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
+  for (auto& g : sv->gslots)
+    if (g->stream) cudaStreamSynchronize(g->stream);
   for (auto& kv : sv->sessions) {
     Session& ss = *kv.second;
     release_session(*sv, ss);
   }
+  for (auto& g : sv->gslots) free_group(g.get());
+  sv->gslots.clear();
   for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
   if (sv->build_stream) cudaStreamDestroy(sv->build_stream);
   delete sv;

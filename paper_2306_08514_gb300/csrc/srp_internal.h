@@ -232,6 +232,61 @@ cudaError_t launch_slri_tall(const float* U, const float* tall, float* Z,
 cudaError_t launch_sspi(const float* xi, const long long* row_ptr, const int2* taps, float* Z,
                         unsigned long long* keys, int F, int J, int L, int num_sms,
                         cudaStream_t s);
+// Fused front end (k_frontend.cu): STFT + PHAT + sampling (+ Lambda_fat xi), one CTA per
+// frame.  These are its per-batch arguments.
+struct FrontParams {
+  const float* frames;
+  int M, P, L;
+  const float* window;
+  const float2* twiddle;
+  const int2* pairs;
+  const int* Np;
+  const int* off;
+  const uint4* stab;  // sampling operand in fragment order (front_sampling_table)
+  int nq0, NT;        // lag offset of its columns (max N_p) and its n-tiles
+  int fbuf_floats;    // FFT buffers / sampling partials (floats)
+  const uint4* ftab;  // SLRI: Lambda_fat in fragment order (front_fat_table); NULL: write xi
+  int Rp;
+  int out_cols;       // row length of the output (L, Lpad, Rp or 64)
+  float scale;        // applied to u before packing
+  int ot;             // operand type of the output
+  void* out;
+  void* out_lo;
+  int conv_out;       // 1: write the conv operand row [P*N] of psi instead of sampling
+};
+// front_params: the arguments launch_front would build (frames and out left NULL).
+FrontParams front_params(int M, int N, const float* window, const float2* twiddle, int P,
+                         const int2* pairs, const int* Np, const int* off, const uint4* stab,
+                         int L, int max_Np, const uint4* ftab, int Rp, int out_cols, float scale,
+                         OpType t);
+size_t front_smem_bytes(int M, int N, int L, int max_Np);
+int front_ntm(int max_Np);
+int front_ntiles(int max_Np);
+// Grouped front end: items [(params index, frame)], *count of them, on `grid` CTAs that
+// walk the list; every entry shares N and front_ntm(max_Np); smem = the largest
+// front_smem_bytes of the entries.
+cudaError_t launch_front_group(const FrontParams* params, const int2* items, const int* count,
+                               int grid, int N, int NTM, size_t smem, cudaStream_t s);
+// Grouped interpolation (serving, FP32): one entry per session in a launch.
+struct GroupInterp {
+  const float* in;            // SLRI: u [F][Rp];  SSPI: xi [F][L]
+  const float* tall;          // SLRI: Lambda_tall [J][Rp]
+  const long long* row_ptr;   // SSPI: taps as CSR rows
+  const int2* taps;
+  float* Z;                   // maps [F][J]
+  unsigned long long* keys;   // argmax keys [F]
+  int F, J, L;
+};
+// SLRI: items (entry, cell block of slri_tall_cells_per_block(Rp) cells, frame block of 64);
+// every entry has the padded rank Rp.
+int slri_tall_cells_per_block(int Rp);
+cudaError_t launch_slri_tall_group(const GroupInterp* g, const int4* items, const int* count,
+                                   int grid, int Rp, cudaStream_t s);
+// SSPI (whole-vector gather, sspi_full_fits(L) for every entry): items (entry, frame group of
+// sspi_group_frames(Lmax) frames, first and end 64-cell row block).
+int sspi_group_frames(int Lmax);
+cudaError_t launch_sspi_group(const GroupInterp* g, const int4* items, const int* count, int grid,
+                              int Lmax, cudaStream_t s);
 // SSPI for long sample vectors: per 64-cell row block only the columns its taps use are
 // staged (blk_ptr [J/64 + 1], blk_cols; taps carry positions in the block's list), FB
 // frames per block (32, 16, .., 1) chosen so that sspi_band_smem(umax, FB) fits.

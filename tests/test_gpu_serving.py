@@ -179,18 +179,75 @@ def test_back_pressure_and_failed_session(S):
             refused = True
             break
     assert refused
-    # a plan that cannot be built (the FP32 SSPI gather with L > 1700) fails its session only
-    big = synth.mics_square(half=1.5)
-    bad = srv.open(big, w["grid_xyz"], w["fs"], 2048, 1024, method="sspi", taps=1.0,
-                   precision="fp32")
-    t0 = time.time()
-    while True:
-        try:
-            st = srv.session_info(bad)["state"]
-        except S.SrpError:
-            break
-        assert st in ("queued", "active") and time.time() - t0 < 30
-        time.sleep(0.01)
+    # a plan that cannot be built (every device allocation fails while it is built, through
+    # the allocation-failure test hook) fails its session only
+    S.srp_debug_fail_allocations(0, 1 << 30)
+    try:
+        bad = _open(srv, "square4-sspi32")
+        t0 = time.time()
+        while True:
+            try:
+                st = srv.session_info(bad)["state"]
+            except S.SrpError:
+                break
+            assert st in ("queued", "active") and time.time() - t0 < 30
+            time.sleep(0.01)
+    finally:
+        S.srp_debug_fail_allocations(0, 0)
     srv.close_session(bad)
     assert srv.session_info(sid)["state"] == "active"
     srv.close()
+
+
+GROUPED = {
+    # sessions whose FP32 plans qualify for grouped launches: two buckets (SLRI R = 16 on
+    # the uca8 array, whole-vector SSPI), different grids in each
+    "g-slri-13": ("uca8", 37, 13, 256, dict(method="slri", rank=16, precision="fp32")),
+    "g-slri-17": ("uca8", 31, 17, 256, dict(method="slri", rank=16, precision="fp32")),
+    "g-slri-23": ("uca8", 26, 23, 256, dict(method="slri", rank=14, precision="fp32")),
+    "g-sspi-13": ("uca8", 29, 13, 256, dict(method="sspi", taps=4.0, precision="fp32")),
+    "g-sspi-19": ("uca8", 35, 19, 256, dict(method="sspi", taps=2.0, precision="fp32")),
+}
+
+
+def test_grouped_launches_share_kernels_and_match_srp_map(S):
+    """FP32 sessions on the fused front end share launches: one front-end kernel, one
+    interpolation kernel and one argmax pass carry the frames of several sessions.  Every
+    session's maps and estimates equal srp_map's on its own plan bit for bit (the grouped
+    kernels run the same per-frame arithmetic), and launches carry more than one session
+    on average."""
+    import torch
+    refs, inputs = {}, {}
+    for n, (wl, F, sub, hop, kw) in GROUPED.items():
+        w = R.workload(wl, F, sub)
+        inputs[n] = (w, hop, kw)
+        plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], max_frames=64, **kw)
+        maps, am = plan.map(torch.from_numpy(w["frames"]).cuda())
+        torch.cuda.synchronize()
+        refs[n] = (maps.cpu().numpy(), am.cpu().numpy())
+        plan.close()
+    srv = S.Server(hbm_budget=8 << 30, max_batch=8, streams=2, slots_per_session=3,
+                   pending_frames=64, group_launches=True)
+    sids = {n: srv.open(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], hop, **kw)
+            for n, (w, hop, kw) in inputs.items()}
+    t0 = time.time()
+    while any(srv.session_info(s)["state"] != "active" for s in sids.values()):
+        assert time.time() - t0 < 120, "sessions not admitted"
+        time.sleep(0.01)
+    srv.reset_stats()
+    plan_of = {sids[n]: (stream_of(w["frames"], hop), hop) for n, (w, hop, kw) in inputs.items()}
+    _feed(srv, plan_of, np.random.default_rng(5), np.random.default_rng(6))
+    got = _drain(srv, list(sids.values()), {sids[n]: inputs[n][0]["F"] for n in inputs})
+    st = srv.stats()
+    srv.close()
+    for n, sid in sids.items():
+        zr, ar = refs[n]
+        F = inputs[n][0]["F"]
+        assert sorted(got[sid]) == list(range(F))
+        z = np.stack([got[sid][f][0] for f in range(F)])
+        a = np.array([got[sid][f][1] for f in range(F)])
+        assert np.array_equal(z, zr), n
+        assert np.array_equal(a, ar), n
+    assert st["group_launches"] > 0 and st["group_launches"] == st["launches"], st
+    assert st["group_sessions"] > st["group_launches"], st  # launches shared by sessions
+    assert st["group_frames"] == sum(inputs[n][0]["F"] for n in inputs), st
