@@ -496,7 +496,8 @@ OTHER_WORKLOADS = [
     ("walls16", 1024, [("conv", "bf16", {}, None), ("conv", "fp16x3", {}, None),
                        ("slri", "bf16", {"rank": 16}, None), ("slri", "fp16x3", {"rank": 16}, None),
                        ("sspi", "bf16", {"taps": 4.0}, None)]),
-    ("nested32", 1024, [("conv", "fp32", {}, 64), ("slri", "bf16", {"rank": 16}, None),
+    ("nested32", 1024, [("conv", "fp32", {}, 64), ("conv", "fp16x3", {}, None),
+                        ("conv", "bf16", {}, None), ("slri", "bf16", {"rank": 16}, None),
                         ("slri", "bf16", {"rank": 64}, None), ("sspi", "bf16", {"taps": 8.0}, None)]),
 ]
 
@@ -505,8 +506,9 @@ def other_workloads(a, S, stream, flush, pk, steps=3):
     """The large workloads (16 wall microphones, N = 1024, J = 72000; 32 microphones on two
     nested circles, N = 2048, J = 240000) at a batch of 1024 frames: per point the plan is
     built (fit included, not timed), tuned, warmed once, and `steps` steps are timed with
-    CUDA events (L2 flushed before each).  Conv. FD-SRP in FP32 on the 32-microphone grid
-    (its SRP matrix generated inside the GEMM) is timed on the first 64 frames."""
+    CUDA events (L2 flushed before each).  On the 32-microphone grid the SRP matrix is not
+    stored: conv. FD-SRP in FP32 generates it inside the GEMM (timed on the first 64
+    frames), on the tensor cores it is generated in chunks of cells."""
     import torch
     import synth
     out = {}

@@ -115,9 +115,11 @@ typedef struct {
   int far_field;            /* 0: grid_xyz are locations q_i (near field); 1: grid_xyz are
                                unit incident directions (far field, Eq. Deltat_i second
                                case: Delta t_p(i) = (r_m - r_m')^T q_i / c) */
-  int h_on_the_fly;         /* conv: 1 = generate the SRP matrix inside the GEMM instead of
-                               storing it (SRP_FP32 only); 0 = only when the stored matrix
-                               would exceed 64 GB; -1 = never */
+  int h_on_the_fly;         /* conv: 1 = do not store the whole SRP matrix: SRP_FP32
+                               generates it inside the GEMM, the tensor-core precisions
+                               generate the rows of one chunk of cells (at most 48 GB, about
+                               two waves of output tiles) before each chunk's GEMM; 0 = only
+                               when the stored matrix would exceed 64 GB; -1 = never */
 } srp_plan_desc;
 
 /* Sizes of a created plan (filled by srp_plan_info). */
@@ -140,7 +142,9 @@ typedef struct {
  *   SRP_CONV: the SRP matrix H of Eq. H_p_single/H_single, stored as the real
  *             matrix [2cos(w_k dt_p(i)) | -2sin(w_k dt_p(i))] in the precision asked, or
  *             (h_on_the_fly, FP32) generated inside the GEMM from the TDOAs split as two
- *             FP32 numbers (phases accurate to ~1e-7) when it would not fit;
+ *             FP32 numbers (phases accurate to ~1e-7) when it would not fit, or on the
+ *             tensor cores generated in chunks of cells from the FP64 TDOAs, one chunk's
+ *             rows before that chunk's GEMM;
  *   SRP_SLRI: Lambda (Eq. Lambda_p) -> its best rank-R approximation (Eq.
  *             min_Lambda_lr) from the eigen-decomposition of Lambda^T Lambda in FP64
  *             (L <= 768: Jacobi on the Gram matrix; longer: subspace iteration with

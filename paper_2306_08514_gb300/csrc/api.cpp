@@ -94,7 +94,7 @@ void free_plan(srp_plan_s* p) {
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
                   p->d_hist[1], p->d_stream_frames, p->d_est_maps, p->d_A2, p->d_A2_lo,
                   p->d_keys2, p->d_tau_hi, p->d_tau_lo, p->d_grid4, p->d_peak_maps,
-                  p->d_blk_ptr, p->d_blk_cols};
+                  p->d_blk_ptr, p->d_blk_cols, p->d_tau};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -143,8 +143,10 @@ constexpr int kGramMaxL = 768;
 // Beyond this L (without the fused front end) SLRI forms u = Lambda_fat xi as a GEMM.
 constexpr int kFatGemmMinL = 1024;
 
-// A stored SRP matrix above this size is generated on the fly instead (FP32 conv).
+// A stored SRP matrix above this size is generated on the fly instead (FP32 conv) or in
+// chunks of cells before each chunk's GEMM (tensor cores, chunks of at most kMaxChunkH).
 constexpr double kMaxStoredH = 64e9;
+constexpr double kMaxChunkH = 48e9;
 
 // One chunk of at most Fmax frames through the whole path.
 constexpr int kMaxChunkEvents = 4096;
@@ -191,6 +193,33 @@ cudaError_t contract_to(srp_plan_s* p, const void* A, const void* A_lo, const vo
   tg.Z = out;
   tg.keys = keys;
   tg.split_ws = p->d_split;
+  tg.err = p->d_err;
+  tg.variant = p->tc_variant;
+  tg.stall = p->stall_next;
+  p->stall_next = false;
+  return launch_tc_gemm(tg, p->num_sms, s);
+}
+
+// A block of jn map columns starting at column c0 (rows J apart): Z[:, c0 + j] = A B_j^T
+// for the jn rows of B, argmax keys over the whole map; never split into slices.
+cudaError_t contract_cols(srp_plan_s* p, const void* A, const void* A_lo, const void* B,
+                          const void* B_lo, int Kd, int F, float* out, int c0, int jn,
+                          cudaStream_t s) {
+  ++p->launches;
+  TcGemm tg;
+  tg.A = A;
+  tg.A_lo = A_lo;
+  tg.B = B;
+  tg.B_lo = B_lo;
+  tg.t = p->op;
+  tg.F = F;
+  tg.J = jn;
+  tg.Kd = Kd;
+  tg.Z = out;
+  tg.ldz = p->g.J;
+  tg.col0 = c0;
+  tg.no_split = true;
+  tg.keys = p->d_keys;
   tg.err = p->d_err;
   tg.variant = p->tc_variant;
   tg.stall = p->stall_next;
@@ -295,7 +324,16 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
   switch (method) {
     case SRP_CONV: {
       SRP_MARK(p, 2, s);
-      if (p->h_generated) {
+      if (p->h_chunk > 0) {
+        // chunks of cells: generate their SRP-matrix rows, then their block of map columns
+        for (int c0 = 0; c0 < g.J; c0 += p->h_chunk) {
+          const int jn = std::min(p->h_chunk, g.J - c0);
+          SRP_LAUNCH(launch_conv_matrix(p->d_tau + static_cast<size_t>(c0) * g.P, jn, g.P, g.N,
+                                        p->op, p->d_H, p->d_H_lo, s));
+          SRP_CUDA_TRY(contract_cols(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, F,
+                                     maps ? maps + c0 : nullptr, c0, jn, s));
+        }
+      } else if (p->h_generated) {
         p->launches += sgemm_split_count(g.P * g.N) > 1 ? 2 : 1;
         SRP_CUDA_TRY(launch_sgemm_nt_argmax(static_cast<const float*>(p->d_A), nullptr, maps,
                                             p->d_keys, F, g.J, g.P * g.N, p->d_split, s,
@@ -439,9 +477,24 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
                           (op_split(p->op) ? 2 : 1);
     p->h_generated = desc->h_on_the_fly == 1 || (desc->h_on_the_fly == 0 && hbytes > kMaxStoredH);
     if (p->h_generated && p->op != OpType::F32) {
-      delete p;
-      return fail(SRP_EUNSUPPORTED, "the SRP matrix would need " + std::to_string(hbytes / 1e9) +
-                                        " GB: generating it on the fly needs SRP_FP32");
+      // tensor cores: the rows of a chunk of cells are generated before each GEMM of the
+      // chunk; the chunk gives about two waves of tiles with the largest batch (whole
+      // 256-cell tiles, at most kMaxChunkH bytes)
+      p->h_generated = false;
+      const double per_cell = hbytes / g.J;
+      int ncell_tiles = 1;
+      {
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+          cudaGetLastError();
+          sms = 152;
+        }
+        const int frame_tiles = (p->Fmax + 127) / 128;
+        ncell_tiles = std::max(1, (2 * sms + frame_tiles - 1) / frame_tiles);
+      }
+      const int by_budget = std::max(1, static_cast<int>(kMaxChunkH / (per_cell * 256)));
+      p->h_chunk = std::min(g.J, 256 * std::min(ncell_tiles, by_budget));
     }
   }
 
@@ -501,6 +554,19 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
     SRP_ALLOC(p, p->d_A, F * Kd * sizeof(float));
     const int nsplit = sgemm_split_count(static_cast<int>(Kd));
     if (nsplit > 1) SRP_ALLOC(p, p->d_split, sizeof(float) * nsplit * F * g.J);
+    SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
+  } else if (desc->method == SRP_CONV && p->h_chunk > 0) {
+    // tensor cores, SRP matrix generated per chunk of cells before each chunk's GEMM: the
+    // FP64 TDOA table stays on the device, d_H holds one chunk's rows
+    const size_t Kd = static_cast<size_t>(g.P) * g.N;
+    const size_t eb = op_bytes(p->op);
+    const bool split = op_split(p->op);
+    SRP_ALLOC(p, p->d_H, static_cast<size_t>(p->h_chunk) * Kd * eb);
+    if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(p->h_chunk) * Kd * eb);
+    SRP_ALLOC(p, p->d_A, F * Kd * eb);
+    if (split) SRP_ALLOC(p, p->d_A_lo, F * Kd * eb);
+    SRP_ALLOC(p, p->d_tau, sizeof(double) * g.tau.size());
+    SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau, g.tau.data(), sizeof(double) * g.tau.size(), cudaMemcpyHostToDevice, s));
     SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
   } else if (desc->method == SRP_CONV) {
     const size_t Kd = static_cast<size_t>(g.P) * g.N;
@@ -1123,7 +1189,10 @@ extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t*
     case SRP_CONV: {
       const double hb = J * P * N * eb * planes;
       const bool gen = d.h_on_the_fly == 1 || (d.h_on_the_fly == 0 && hb > 64e9);
-      b += (gen ? J * P * 8.0 : hb) + F * P * N * eb * planes;
+      // generated in the FP32 GEMM (the split TDOAs), or per chunk of at most kMaxChunkH
+      // bytes for the tensor cores (plus the FP64 TDOA table)
+      const double hgen = d.precision == SRP_FP32 ? J * P * 8.0 : std::min(hb, kMaxChunkH) + J * P * 8.0;
+      b += (gen ? hgen : hb) + F * P * N * eb * planes;
       if (d.precision == SRP_FP32 && P * N > 16384) b += std::ceil(P * N / 16384.0) * F * J * 4.0;
       break;
     }

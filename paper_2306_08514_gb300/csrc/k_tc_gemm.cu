@@ -85,7 +85,8 @@ struct TcParams {
   int nM, nN, nslices, kb_per_slice;
   int tma_out;           // 1: results leave by TMA store through tmZ; 0: plain stores
   int tn;                // cell width of a tile
-  float* Z;              // maps [F][J] (nslices == 1) or partial maps [nslices][F][J]
+  int ldz, col0;         // row stride of Z; map index of its column 0 (argmax keys)
+  float* Z;              // maps [F][ldz] (nslices == 1) or partial maps [nslices][F][J]
   unsigned long long* keys;
   int* err;
 };
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             bv = sum[j];
             bi = n0 + j;
           }
-        if (f < p.F && bi >= 0) atomicMax(p.keys + f, argmax_key(bv, bi));
+        if (f < p.F && bi >= 0) atomicMax(p.keys + f, argmax_key(bv, p.col0 + bi));
       }
       if (!p.Z) continue;  // estimates only: the argmax is all that leaves
       if (p.tma_out) {
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       } else if (f < p.F) {
-        float* zrow = p.Z + (static_cast<size_t>(w.slice) * p.F + f) * p.J + n0;
+        float* zrow = p.Z + (static_cast<size_t>(w.slice) * p.F + f) * p.ldz + n0;
 #pragma unroll
         for (int j = 0; j < EPI_COLS; ++j)
           if (n0 + j < p.J) zrow[j] = sum[j];
@@ -400,10 +401,12 @@ cudaError_t make_operand_map(CUtensorMap* m, const void* base, CUtensorMapDataTy
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// 3-D FP32 output map over [slices][F][J], box 32 x 32 x 1, 128-byte swizzle.
-cudaError_t make_output_map(CUtensorMap* m, float* base, uint64_t J, uint64_t F, uint64_t slices) {
+// 3-D FP32 output map over [slices][F][J] with rows ld floats apart, box 32 x 32 x 1,
+// 128-byte swizzle.
+cudaError_t make_output_map(CUtensorMap* m, float* base, uint64_t J, uint64_t F, uint64_t slices,
+                            uint64_t ld) {
   cuuint64_t dims[3] = {J, F, slices};
-  cuuint64_t strides[2] = {J * 4, J * F * 4};
+  cuuint64_t strides[2] = {ld * 4, ld * F * 4};
   cuuint32_t box[3] = {32, 32, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
@@ -506,7 +509,8 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.kb_idx = g.kb_idx;
   p.nM = (g.F + TM - 1) / TM;
   p.nN = (g.J + tn - 1) / tn;
-  p.nslices = g.kb_ptr ? 1 : slices_for(g.F, g.J, g.Kd, g.t, num_sms, tn);
+  p.nslices = (g.kb_ptr || g.no_split) ? 1 : slices_for(g.F, g.J, g.Kd, g.t, num_sms, tn);
+  p.col0 = g.col0;
   const int kb_total = p.kb_per_seg * p.nseg;
   if (p.nslices > 1) {
     p.kb_per_slice = (kb_total + p.nslices - 1) / p.nslices;
@@ -517,15 +521,17 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.keys = g.keys;
   p.err = g.err;
   if (p.nslices > 1) {
-    if (!g.split_ws) return cudaErrorInvalidValue;
+    if (!g.split_ws || (g.ldz && g.ldz != g.J)) return cudaErrorInvalidValue;
     p.Z = g.split_ws;
+    p.ldz = g.J;
   } else {
     p.Z = g.Z;
+    p.ldz = g.ldz ? g.ldz : g.J;
   }
   // TMA output needs 16-byte row strides and a 16-byte aligned base.
-  p.tma_out = p.Z && (g.J % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Z) % 16 == 0);
+  p.tma_out = p.Z && (p.ldz % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Z) % 16 == 0);
   if (p.tma_out) {
-    if ((e = make_output_map(&mZ, p.Z, g.J, g.F, p.nslices)) != cudaSuccess) return e;
+    if ((e = make_output_map(&mZ, p.Z, g.J, g.F, p.nslices, p.ldz)) != cudaSuccess) return e;
   } else {
     mZ = mA0;  // unused
   }

@@ -188,6 +188,9 @@ struct TcGemm {
   const int* kb_ptr = nullptr;
   const int* kb_idx = nullptr;
   float* Z = nullptr;
+  int ldz = 0;        // row stride of Z in floats (0: J); with col0 a column block of a wider map
+  int col0 = 0;       // index of Z's first column in the map (argmax keys carry col0 + column)
+  bool no_split = false;  // never split the reduction into slices (column blocks of a map)
   unsigned long long* keys = nullptr;
   float* split_ws = nullptr;
   int* err = nullptr;
@@ -329,6 +332,9 @@ struct srp_plan_s {
   bool use_front = false;  // interpolation methods: one fused front-end launch per chunk
   bool fat_gemm = false;   // SLRI with long sample vectors: u = Lambda_fat xi as a GEMM
   bool h_generated = false;  // conv FP32: SRP matrix generated inside the GEMM, not stored
+  int h_chunk = 0;           // conv on the tensor cores, SRP matrix too large to store: cells
+                             // per chunk whose rows are generated into d_H before each GEMM
+  double* d_tau = nullptr;   //   the TDOA table [J][P] kept for that
   std::vector<double> sigma;
   std::vector<std::complex<double>> lr_tall, lr_fat;  // LR-SRP factors kept for srp_plan_save
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export

@@ -3,7 +3,8 @@
 N = 2048, F = 1024).  The FP64 oracle cannot evaluate these whole (the SVD of walls16's
 72000 x 43326 Lambda, nested32's 952 M SSPI taps), so sampled outputs are checked:
 
-* conv: the oracle's map on 256 sampled cells of two sampled frames;
+* conv: the oracle's map on 256 sampled cells of two sampled frames (walls16 in BF16;
+  nested32 in FP16 hi+lo with its SRP matrix generated in chunks of cells);
 * SLRI: the plan's own factors (read back from its checkpoint file) applied in FP64 to the
   oracle's GCC samples, the fit on the sampled rows (Lambda_tall = Lambda V, V
   orthonormal), and that V spans the top-R singular subspace of the whole Lambda: the
@@ -108,5 +109,15 @@ def test_walls16_full_size_sampled(S, tmp_path):
 
 def test_nested32_full_size_sampled(S, tmp_path):
     w, dt, lags, perm, fsel, cells, psi, xi, lam_cells = _setup("nested32")
+    # conv. FD-SRP on the tensor cores in FP16 hi+lo: the SRP matrix (975 GB as hi + lo
+    # planes) is generated in chunks of cells before each chunk's GEMM
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    plan = S.Plan(*args, method="conv", precision="fp16x3", max_frames=w["F"])
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    assert np.array_equal(am, np.argmax(z, axis=1))
+    zo = R.conv_cells(psi, dt, w["fs"], cells)
+    assert R.per_frame_rel(z[fsel][:, cells], zo).max() <= 1e-5
+    del plan, z
     _check_slri(S, w, dt, lags, perm, fsel, cells, xi, lam_cells, 16, tmp_path)
     _check_sspi(S, w, fsel, cells, xi, lam_cells, 8.0)

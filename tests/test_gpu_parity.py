@@ -421,3 +421,23 @@ def test_sspi_fp32_long_sample_vectors(S, name, F, sub, t):
     zo = O.srp_sspi(np.where(mask_g, Lam, 0.0), xi_o)
     assert R.per_frame_rel(z, zo).max() <= TOL
     check_argmax(z, am, zo)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16x3", TOL), ("bf16", 1.5e-2), ("tf32x3", TOL)])
+def test_conv_tensor_cores_with_srp_matrix_in_chunks(S, uca_small, prec, tol):
+    """Conv. FD-SRP on the tensor cores without the whole SRP matrix stored: the rows of one
+    chunk of cells are generated before that chunk's GEMM (h_on_the_fly).  A batch size of
+    32768 frames makes the chunks 512 cells (about two waves of tiles), so the 4616 cells
+    take ten chunks, the last of 8 cells; maps and estimates-only calls against the oracle."""
+    import torch
+    name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
+    plan = S.Plan(w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"], method="conv", precision=prec,
+                  max_frames=32768, h_on_the_fly=1)
+    z, am = _run(plan, w["frames"])
+    plan.status()
+    zo = O.srp_conv(psi, dt, w["fs"])
+    assert R.per_frame_rel(z, zo).max() <= tol
+    check_argmax(z, am, zo)
+    _, am2 = plan.map(_cuda(w["frames"]), want_maps=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(am2.cpu().numpy(), am)
