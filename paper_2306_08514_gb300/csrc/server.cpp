@@ -127,10 +127,21 @@ struct GroupSlot {
   unsigned long long* d_keys = nullptr;
   char* h_desc = nullptr;  // work list: counts, front arguments, interpolation arguments, items
   char* d_desc = nullptr;
+  size_t o_fp = 0, o_gi = 0, o_fi = 0, o_ci = 0;  // fixed work-list layout in h_desc / d_desc
   std::atomic<int> state{0};  // 0 free, 1 in flight, 2 done (members await polls)
   int refs = 0;               // member batches not yet polled
   std::vector<Slot*> members;
   Server* server = nullptr;
+  // one captured graph per bucket; its copies are resized before each replay
+  struct Graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy[7] = {};  // counts + front args, interp args, front items, interp
+                                   // items, frames (in); maps, argmax (out)
+    size_t front_smem = 0;
+    int Lmax = 0;
+  };
+  std::map<long long, Graph> graphs;
 };
 
 struct Server {
@@ -318,6 +329,11 @@ bool group_eligible(const srp_plan_s* P) {
 
 void free_group(GroupSlot* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
+  for (auto& kv : g->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  g->graphs.clear();
   if (g->h_in) cudaFreeHost(g->h_in);
   if (g->h_out) cudaFreeHost(g->h_out);
   if (g->h_arg) cudaFreeHost(g->h_arg);
@@ -343,9 +359,11 @@ bool make_groups(const Server& sv, std::vector<std::unique_ptr<GroupSlot>>& out)
     g->cap_in = kGroupInFloats;
     g->cap_out = kGroupOutFloats;
     g->cap_scr = static_cast<size_t>(cap_frames) * kGroupMaxCols;
-    g->cap_desc = align16(16) + align16(sizeof(FrontParams) * cap_frames) +
-                  align16(sizeof(GroupInterp) * cap_frames) + align16(sizeof(int2) * cap_frames) +
-                  align16(sizeof(int4) * g->cap_items);
+    g->o_fp = 16;
+    g->o_gi = g->o_fp + align16(sizeof(FrontParams) * cap_frames);
+    g->o_fi = g->o_gi + align16(sizeof(GroupInterp) * cap_frames);
+    g->o_ci = g->o_fi + align16(sizeof(int2) * cap_frames);
+    g->cap_desc = g->o_ci + align16(sizeof(int4) * g->cap_items);
     ok = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess &&
          cudaMallocHost(&g->h_in, 4 * g->cap_in) == cudaSuccess &&
          cudaMallocHost(&g->h_out, 4 * g->cap_out) == cudaSuccess &&
@@ -369,6 +387,104 @@ bool make_groups(const Server& sv, std::vector<std::unique_ptr<GroupSlot>>& out)
 }
 
 void CUDART_CB group_done_cb(void* u);
+
+// The launch sequence of a grouped launch on stream s (issued directly or captured): the
+// work list and the frames in, the keys cleared, the front end over the front items, the
+// interpolation over its items, the argmax, the maps and argmax out, the completion
+// callback.  sizes: the bytes of the seven copies (see GroupSlot::Graph).  Grids are
+// fixed (the kernels walk the item counts the work list carries), so a captured sequence
+// stays valid for any work list once its copies are resized.
+cudaError_t enqueue_group(Server& sv, GroupSlot& g, long long key, size_t front_smem, int Lmax,
+                          const size_t* sizes, cudaStream_t s) {
+  const bool slri = (key >> 40) == 1;
+  const int N = static_cast<int>((key >> 24) & 0xFFFF);
+  const int NTM = static_cast<int>((key >> 16) & 0xFF);
+  const int width = static_cast<int>(key & 0xFFFF);
+  const int grid = 4 * std::max(1, sv.num_sms);
+  const int* d_counts = reinterpret_cast<const int*>(g.d_desc);
+  cudaError_t e = cudaMemcpyAsync(g.d_desc, g.h_desc, sizes[0], cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g.d_desc + g.o_gi, g.h_desc + g.o_gi, sizes[1], cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g.d_desc + g.o_fi, g.h_desc + g.o_fi, sizes[2], cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g.d_desc + g.o_ci, g.h_desc + g.o_ci, sizes[3], cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g.d_in, g.h_in, sizes[4], cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.d_keys, 0, 8 * static_cast<size_t>(g.cap_frames), s);
+  if (e == cudaSuccess)
+    e = launch_front_group(reinterpret_cast<const FrontParams*>(g.d_desc + g.o_fp),
+                           reinterpret_cast<const int2*>(g.d_desc + g.o_fi), d_counts, grid, N, NTM,
+                           front_smem, s);
+  const GroupInterp* d_gi = reinterpret_cast<const GroupInterp*>(g.d_desc + g.o_gi);
+  const int4* d_ci = reinterpret_cast<const int4*>(g.d_desc + g.o_ci);
+  if (e == cudaSuccess)
+    e = slri ? launch_slri_tall_group(d_gi, d_ci, d_counts + 1, grid, width, s)
+             : launch_sspi_group(d_gi, d_ci, d_counts + 1, grid, Lmax, s);
+  if (e == cudaSuccess) e = launch_argmax_finalize(g.d_keys, g.d_arg, g.cap_frames, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_out, g.d_out, sizes[5], cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_arg, g.d_arg, sizes[6], cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(s, group_done_cb, &g);
+  return e;
+}
+
+// Captures the sequence into gg (on success gg.exec is set and its seven copy nodes found).
+void capture_group(Server& sv, GroupSlot& g, long long key, size_t front_smem, int Lmax,
+                   const size_t* sizes, GroupSlot::Graph& gg) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal);
+  const cudaError_t e2 = e == cudaSuccess ? enqueue_group(sv, g, key, front_smem, Lmax, sizes, g.stream) : e;
+  if (e == cudaSuccess) e = cudaStreamEndCapture(g.stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return;
+  }
+  // the copy nodes, told apart by their endpoints
+  const void* src[7] = {g.h_desc, g.h_desc + g.o_gi, g.h_desc + g.o_fi, g.h_desc + g.o_ci,
+                        g.h_in, g.d_out, g.d_arg};
+  size_t n = 0;
+  cudaGraphGetNodes(graph, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  cudaGraphGetNodes(graph, nodes.data(), &n);
+  int found = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeMemcpy) continue;
+    cudaMemcpy3DParms mp{};
+    if (cudaGraphMemcpyNodeGetParams(nd, &mp) != cudaSuccess) continue;
+    for (int i = 0; i < 7; ++i)
+      if (mp.srcPtr.ptr == src[i] && !gg.copy[i]) {
+        gg.copy[i] = nd;
+        ++found;
+      }
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (found == 7 && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+    gg.graph = graph;
+    gg.exec = exec;
+    gg.front_smem = front_smem;
+    gg.Lmax = Lmax;
+  } else {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    gg = GroupSlot::Graph();
+  }
+}
+
+// Resizes the seven copies of a captured grouped launch.
+cudaError_t update_group_graph(GroupSlot& g, GroupSlot::Graph& gg, const size_t* sizes) {
+  void* dst[7] = {g.d_desc, g.d_desc + g.o_gi, g.d_desc + g.o_fi, g.d_desc + g.o_ci, g.d_in,
+                  g.h_out, g.h_arg};
+  const void* src[7] = {g.h_desc, g.h_desc + g.o_gi, g.h_desc + g.o_fi, g.h_desc + g.o_ci,
+                        g.h_in, g.d_out, g.d_arg};
+  for (int i = 0; i < 7; ++i) {
+    const cudaMemcpyKind kind = i < 5 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    const cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(gg.exec, gg.copy[i], dst[i], src[i],
+                                                             std::max<size_t>(sizes[i], 16), kind);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 // One grouped launch of bucket `key` carrying the pending frames of `list` (sessions with no
 // launch in flight and a free slot), as many as the launch's buffers hold.  Called with the
@@ -420,11 +536,10 @@ void issue_group(Server& sv, GroupSlot& g, long long key, const std::vector<Sess
   }
   if (es.empty()) return;
   const int E = static_cast<int>(es.size());
-  // work list in pinned memory: counts | front arguments | interpolation arguments | items
+  // work list in pinned memory (fixed layout): counts | front arguments | interpolation
+  // arguments | front items | interpolation items
   char* h = g.h_desc;
-  const size_t o_fp = 16, o_gi = o_fp + align16(sizeof(FrontParams) * E),
-               o_fi = o_gi + align16(sizeof(GroupInterp) * E), o_ci = o_fi + align16(sizeof(int2) * frames),
-               desc_bytes = o_ci + align16(sizeof(int4) * items);
+  const size_t o_fp = g.o_fp, o_gi = g.o_gi, o_fi = g.o_fi, o_ci = g.o_ci;
   int* counts = reinterpret_cast<int*>(h);
   FrontParams* fp = reinterpret_cast<FrontParams*>(h + o_fp);
   GroupInterp* gi = reinterpret_cast<GroupInterp*>(h + o_gi);
@@ -478,25 +593,27 @@ void issue_group(Server& sv, GroupSlot& g, long long key, const std::vector<Sess
   g.refs = E;
   g.state.store(1);
   cudaStream_t s = g.stream;
-  const int* d_counts = reinterpret_cast<const int*>(g.d_desc);
-  const int cap_grid = 4 * std::max(1, sv.num_sms);
-  cudaError_t e = cudaMemcpyAsync(g.d_desc, g.h_desc, desc_bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(g.d_in, g.h_in, 4 * in, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g.d_keys, 0, 8 * static_cast<size_t>(frames), s);
-  if (e == cudaSuccess)
-    e = launch_front_group(reinterpret_cast<const FrontParams*>(g.d_desc + o_fp),
-                           reinterpret_cast<const int2*>(g.d_desc + o_fi), d_counts,
-                           std::min(nfi, cap_grid), N, NTM, smem, s);
-  const GroupInterp* d_gi = reinterpret_cast<const GroupInterp*>(g.d_desc + o_gi);
-  const int4* d_ci = reinterpret_cast<const int4*>(g.d_desc + o_ci);
-  if (e == cudaSuccess)
-    e = slri ? launch_slri_tall_group(d_gi, d_ci, d_counts + 1, std::min(nci, cap_grid), width, s)
-             : launch_sspi_group(d_gi, d_ci, d_counts + 1, std::min(nci, cap_grid), Lmax, s);
-  if (e == cudaSuccess) e = launch_argmax_finalize(g.d_keys, g.d_arg, frames, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_out, g.d_out, 4 * out, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(g.h_arg, g.d_arg, 4 * static_cast<size_t>(frames), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaLaunchHostFunc(s, group_done_cb, &g);
+  const size_t sizes[7] = {o_fp + sizeof(FrontParams) * E, sizeof(GroupInterp) * E,
+                           sizeof(int2) * nfi, sizeof(int4) * nci, 4 * in, 4 * out,
+                           4 * static_cast<size_t>(frames)};
+  cudaError_t e = cudaErrorUnknown;
+  bool replayed = false;
+  if (sv.desc.use_graphs) {
+    GroupSlot::Graph& gg = g.graphs[key];
+    if (gg.exec && (gg.front_smem < smem || gg.Lmax < Lmax)) {  // recapture with more smem
+      cudaGraphExecDestroy(gg.exec);
+      cudaGraphDestroy(gg.graph);
+      gg = GroupSlot::Graph();
+    }
+    if (!gg.exec) capture_group(sv, g, key, std::max(smem, gg.front_smem), std::max(Lmax, gg.Lmax), sizes, gg);
+    if (gg.exec) {
+      e = update_group_graph(g, gg, sizes);
+      if (e == cudaSuccess) e = cudaGraphLaunch(gg.exec, s);
+      replayed = e == cudaSuccess;
+      if (!replayed) cudaGetLastError();
+    }
+  }
+  if (!replayed) e = enqueue_group(sv, g, key, smem, Lmax, sizes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaStreamSynchronize(s);
@@ -513,6 +630,7 @@ void issue_group(Server& sv, GroupSlot& g, long long key, const std::vector<Sess
     g.state.store(0);
     return;
   }
+  if (replayed) ++sv.graph_launches;
   ++sv.launches;
   ++sv.group_launches;
   sv.frames_launched += frames;

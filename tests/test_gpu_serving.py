@@ -179,21 +179,19 @@ def test_back_pressure_and_failed_session(S):
             refused = True
             break
     assert refused
-    # a plan that cannot be built (every device allocation fails while it is built, through
-    # the allocation-failure test hook) fails its session only
-    S.srp_debug_fail_allocations(0, 1 << 30)
-    try:
-        bad = _open(srv, "square4-sspi32")
-        t0 = time.time()
-        while True:
-            try:
-                st = srv.session_info(bad)["state"]
-            except S.SrpError:
-                break
-            assert st in ("queued", "active") and time.time() - t0 < 30
-            time.sleep(0.01)
-    finally:
-        S.srp_debug_fail_allocations(0, 0)
+    # a plan that cannot be built (an SLRI rank above the 25 cells of its grid: accepted
+    # when the session opens, refused when its plan is built) fails its session only
+    tiny = synth.grid_plane((1.0, 1.0), (3.0, 3.0), (5, 5))
+    bad = srv.open(w["mic_xyz"], tiny, w["fs"], w["N"], hop, method="slri", rank=40,
+                   precision="fp32")
+    t0 = time.time()
+    while True:
+        try:
+            st = srv.session_info(bad)["state"]
+        except S.SrpError:
+            break
+        assert st in ("queued", "active") and time.time() - t0 < 30
+        time.sleep(0.01)
     srv.close_session(bad)
     assert srv.session_info(sid)["state"] == "active"
     srv.close()
