@@ -94,7 +94,7 @@ void free_plan(srp_plan_s* p) {
                   p->d_stage_arg, p->d_B, p->d_B_lo, p->d_kb_ptr, p->d_kb_idx, p->d_hist[0],
                   p->d_hist[1], p->d_stream_frames, p->d_est_maps, p->d_A2, p->d_A2_lo,
                   p->d_keys2, p->d_tau_hi, p->d_tau_lo, p->d_grid4, p->d_peak_maps,
-                  p->d_blk_ptr, p->d_blk_cols, p->d_tau};
+                  p->d_blk_ptr, p->d_blk_cols};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -328,8 +328,9 @@ srp_status run_chunk(srp_plan_s* p, const float* frames, int F, float* maps, int
         // chunks of cells: generate their SRP-matrix rows, then their block of map columns
         for (int c0 = 0; c0 < g.J; c0 += p->h_chunk) {
           const int jn = std::min(p->h_chunk, g.J - c0);
-          SRP_LAUNCH(launch_conv_matrix(p->d_tau + static_cast<size_t>(c0) * g.P, jn, g.P, g.N,
-                                        p->op, p->d_H, p->d_H_lo, s));
+          const size_t o = static_cast<size_t>(c0) * g.P;
+          SRP_LAUNCH(launch_conv_matrix_split(p->d_tau_hi + o, p->d_tau_lo + o, jn, g.P, g.N,
+                                              p->op, p->d_H, p->d_H_lo, s));
           SRP_CUDA_TRY(contract_cols(p, p->d_A, p->d_A_lo, p->d_H, p->d_H_lo, g.P * g.N, F,
                                      maps ? maps + c0 : nullptr, c0, jn, s));
         }
@@ -565,8 +566,20 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
     if (split) SRP_ALLOC(p, p->d_H_lo, static_cast<size_t>(p->h_chunk) * Kd * eb);
     SRP_ALLOC(p, p->d_A, F * Kd * eb);
     if (split) SRP_ALLOC(p, p->d_A_lo, F * Kd * eb);
-    SRP_ALLOC(p, p->d_tau, sizeof(double) * g.tau.size());
-    SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau, g.tau.data(), sizeof(double) * g.tau.size(), cudaMemcpyHostToDevice, s));
+    // the TDOAs split as tau_hi (13 significant bits) + tau_lo for the FP32 generation
+    std::vector<float> th(g.tau.size()), tl(g.tau.size());
+    for (size_t e = 0; e < g.tau.size(); ++e) {
+      const double t = g.tau[e];
+      int ex = 0;
+      const double m = std::frexp(t, &ex);
+      const double hi = std::ldexp(std::trunc(std::ldexp(m, 13)), ex - 13);
+      th[e] = static_cast<float>(hi);
+      tl[e] = static_cast<float>(t - hi);
+    }
+    SRP_ALLOC(p, p->d_tau_hi, sizeof(float) * th.size());
+    SRP_ALLOC(p, p->d_tau_lo, sizeof(float) * tl.size());
+    SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau_hi, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, s));
+    SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau_lo, tl.data(), sizeof(float) * tl.size(), cudaMemcpyHostToDevice, s));
     SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
   } else if (desc->method == SRP_CONV) {
     const size_t Kd = static_cast<size_t>(g.P) * g.N;
@@ -1191,7 +1204,7 @@ extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t*
       const bool gen = d.h_on_the_fly == 1 || (d.h_on_the_fly == 0 && hb > 64e9);
       // generated in the FP32 GEMM (the split TDOAs), or per chunk of at most kMaxChunkH
       // bytes for the tensor cores (plus the FP64 TDOA table)
-      const double hgen = d.precision == SRP_FP32 ? J * P * 8.0 : std::min(hb, kMaxChunkH) + J * P * 8.0;
+      const double hgen = d.precision == SRP_FP32 ? J * P * 8.0 : std::min(hb, kMaxChunkH) + J * P * 8.0;  // split TDOAs
       b += (gen ? hgen : hb) + F * P * N * eb * planes;
       if (d.precision == SRP_FP32 && P * N > 16384) b += std::ceil(P * N / 16384.0) * F * J * 4.0;
       break;

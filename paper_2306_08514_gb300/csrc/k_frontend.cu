@@ -911,9 +911,9 @@ cudaError_t launch_front_group(const FrontParams* params, const int2* items, con
 FrontParams front_params(int M, int N, const float* window, const float2* twiddle, int P,
                          const int2* pairs, const int* Np, const int* off, const uint4* stab,
                          int L, int max_Np, const uint4* ftab, int Rp, int out_cols, float scale,
-                         OpType t) {
+                         OpType t, int NTM) {
   const int H = N / 2, groups = 256 / (H / 8);
-  const int NTM = front_ntm(max_Np);
+  if (NTM < front_ntm(max_Np)) NTM = front_ntm(max_Np);
   const int fbuf_floats = std::max(4 * groups * fpad_len(H), 8 * 16 * 8 * NTM);
   return FrontParams{nullptr, M, P, L, window, twiddle, pairs, Np, off, stab, max_Np,
                      front_ntiles(max_Np), fbuf_floats, ftab, Rp, out_cols, scale,
@@ -987,12 +987,16 @@ void front_fat_table(const float* fat, int Rp, int L, std::vector<uint4>& tab) {
       }
 }
 
-size_t front_smem_bytes(int M, int N, int L, int max_Np) {
+size_t front_smem_bytes_ntm(int M, int N, int L, int NTM) {
   const int H = N / 2, Tg = H / 8;
   const int groups = 256 / Tg;
   const size_t fbuf = std::max(sizeof(float2) * groups * 2 * fpad_len(H),
-                               sizeof(float) * 8 * 16 * 8 * front_ntm(max_Np));
+                               sizeof(float) * 8 * 16 * 8 * NTM);
   return sizeof(float2) * (H + static_cast<size_t>(M) * front_row(H)) + fbuf + sizeof(float) * L;
+}
+
+size_t front_smem_bytes(int M, int N, int L, int max_Np) {
+  return front_smem_bytes_ntm(M, N, L, front_ntm(max_Np));
 }
 
 bool front_supported(int M, int N, int L, int max_Np) {
@@ -1177,6 +1181,50 @@ __global__ void conv_matrix_kernel(const double* __restrict__ tau, int J, int P,
     op_store_d<T, SPLIT>(B, B_lo, base, c);
     op_store_d<T, SPLIT>(B, B_lo, base + K, sn);
   }
+}
+
+// The same rows from the TDOAs split as tau_hi + tau_lo (tau_hi with 13 significant bits,
+// so k tau_hi / N and its fraction are exact in FP32 for k < 2^11), with FP32 sincospif:
+// phases within ~4e-7 rad, the accuracy of the FP16 / TF32 hi + lo planes, at FP32 rates
+// (the FP64 reduction and sincospi above run at the FP64 rate, 1/64 of FP32 on GB300).
+// Used per call where the matrix is generated in chunks of cells.  One block per row
+// (cell, pair), threads over the bins.
+template <typename T, bool SPLIT>
+__global__ __launch_bounds__(128) void conv_matrix_split_kernel(const float* __restrict__ tau_hi,
+                                                                const float* __restrict__ tau_lo,
+                                                                size_t rows, int N,
+                                                                void* __restrict__ B,
+                                                                void* __restrict__ B_lo) {
+  const int K = N >> 1;
+  const float invN = 1.f / static_cast<float>(N);
+  for (size_t ip = blockIdx.x; ip < rows; ip += gridDim.x) {
+    const float th = __ldg(tau_hi + ip), tl = __ldg(tau_lo + ip);
+    const size_t base = ip * N;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      float c = 0.f, sn = 0.f;
+      if (k != 0) {
+        const float x = static_cast<float>(k) * th * invN;  // exact
+        const float rr = (x - floorf(x)) + static_cast<float>(k) * tl * invN;
+        sincospif(2.f * rr, &sn, &c);
+        c *= 2.f;
+        sn *= -2.f;
+      }
+      op_store<T, SPLIT>(B, B_lo, base + k, c);
+      op_store<T, SPLIT>(B, B_lo, base + K + k, sn);
+    }
+  }
+}
+
+cudaError_t launch_conv_matrix_split(const float* tau_hi, const float* tau_lo, int J, int P, int N,
+                                     OpType t, void* B, void* B_lo, cudaStream_t s) {
+  const size_t rows = static_cast<size_t>(J) * P;
+  if (rows == 0) return cudaSuccess;
+  const int g = static_cast<int>(std::min<size_t>(rows, 152 * 64));
+  op_dispatch(t, [&](auto tag) {
+    using Tag = decltype(tag);
+    conv_matrix_split_kernel<typename Tag::type, Tag::split><<<g, 128, 0, s>>>(tau_hi, tau_lo, rows, N, B, B_lo);
+  });
+  return cudaGetLastError();
 }
 
 cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpType t, void* B,

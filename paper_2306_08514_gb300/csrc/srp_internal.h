@@ -155,6 +155,10 @@ cudaError_t launch_front_conv(const float* frames, int F, int M, int N, const fl
 // SRP matrix in GEMM layout B [J][P*N]: 2cos(theta), -2sin(theta), theta = 2 pi k tau / N.
 cudaError_t launch_conv_matrix(const double* tau_dev, int J, int P, int N, OpType t, void* B,
                                void* B_lo, cudaStream_t s);
+// The same rows from the TDOAs split as tau_hi + tau_lo (FP32 phases, ~4e-7 rad): per-call
+// generation of chunks of cells.
+cudaError_t launch_conv_matrix_split(const float* tau_hi, const float* tau_lo, int J, int P, int N,
+                                     OpType t, void* B, void* B_lo, cudaStream_t s);
 // Z[F][J] = A B^T in FP32 FFMA, fused per-frame argmax keys.  For long reductions
 // (sgemm_split_count(Kd) > 1) the k range is split into slices of <= 16384 terms whose
 // partial maps go to split_ws [nsplit][F][J] and are summed in FP64.
@@ -257,12 +261,15 @@ struct FrontParams {
   void* out_lo;
   int conv_out;       // 1: write the conv operand row [P*N] of psi instead of sampling
 };
-// front_params: the arguments launch_front would build (frames and out left NULL).
+// front_params: the arguments launch_front would build (frames and out left NULL), for a
+// kernel instantiated with NTM n-tiles (at least front_ntm(max_Np): a wider instantiation
+// serves narrower plans, whose partial buffers are then sized for it).
 FrontParams front_params(int M, int N, const float* window, const float2* twiddle, int P,
                          const int2* pairs, const int* Np, const int* off, const uint4* stab,
                          int L, int max_Np, const uint4* ftab, int Rp, int out_cols, float scale,
-                         OpType t);
+                         OpType t, int NTM);
 size_t front_smem_bytes(int M, int N, int L, int max_Np);
+size_t front_smem_bytes_ntm(int M, int N, int L, int NTM);
 int front_ntm(int max_Np);
 int front_ntiles(int max_Np);
 // Grouped front end: items [(params index, frame)], *count of them, on `grid` CTAs that
@@ -334,7 +341,7 @@ struct srp_plan_s {
   bool h_generated = false;  // conv FP32: SRP matrix generated inside the GEMM, not stored
   int h_chunk = 0;           // conv on the tensor cores, SRP matrix too large to store: cells
                              // per chunk whose rows are generated into d_H before each GEMM
-  double* d_tau = nullptr;   //   the TDOA table [J][P] kept for that
+                             // (from d_tau_hi / d_tau_lo)
   std::vector<double> sigma;
   std::vector<std::complex<double>> lr_tall, lr_fat;  // LR-SRP factors kept for srp_plan_save
   std::vector<long long> h_row_ptr;  // SSPI taps kept on the host for export
