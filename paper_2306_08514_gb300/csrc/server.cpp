@@ -314,20 +314,18 @@ constexpr int kSspiRowChunk = 8;                      // row blocks of 64 cells 
 
 size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-// Every grouped session runs the front end's widest sampling instantiation (n-tiles up to
-// 9, i.e. N_p <= 32), so buckets differ only by method, N and padded rank / gather width.
-constexpr int kGroupNTM = 9;
-
+// A grouped session runs the front end's own sampling instantiation (its n-tile count:
+// the wider ones accumulate in another order), so that its maps equal srp_map's bit for bit.
 long long group_key(const srp_plan_s* P) {
   const int method = P->desc.method == SRP_SLRI ? 1 : 2;
   const int w = P->desc.method == SRP_SLRI ? (P->R + 7) / 8 * 8 : sspi_group_frames(P->g.L);
   return (static_cast<long long>(method) << 40) | (static_cast<long long>(P->g.N) << 24) |
-         (static_cast<long long>(kGroupNTM) << 16) | w;
+         (static_cast<long long>(front_ntm(P->max_Np)) << 16) | w;
 }
 
 bool group_eligible(const srp_plan_s* P) {
   return P->op == OpType::F32 && P->use_front &&
-         front_smem_bytes_ntm(P->g.M, P->g.N, P->g.L, kGroupNTM) <= 200 * 1024 &&
+         front_smem_bytes(P->g.M, P->g.N, P->g.L, P->max_Np) <= 200 * 1024 &&
          (P->desc.method == SRP_SLRI || (P->desc.method == SRP_SSPI && P->sspi_umax == 0)) &&
          ((P->R + 7) / 8 * 8 <= kGroupMaxCols) && P->g.L <= kGroupMaxCols;
 }
@@ -831,10 +829,10 @@ void builder_loop(Server* sv) {
         pick->L = g.L;
         pick->nrb = (g.J + 63) / 64;
         pick->cols = slri ? pick->Rp : g.L;
-        pick->front_smem = front_smem_bytes_ntm(g.M, g.N, g.L, kGroupNTM);
+        pick->front_smem = front_smem_bytes(g.M, g.N, g.L, P->max_Np);
         pick->fp = front_params(g.M, g.N, P->d_window, P->d_twiddle, g.P, P->d_pairs, P->d_Np,
                                 P->d_off, P->d_stab, g.L, P->max_Np, slri ? P->d_ftab : nullptr,
-                                pick->Rp, pick->cols, 1.f, OpType::F32, kGroupNTM);
+                                pick->Rp, pick->cols, 1.f, OpType::F32, 0);
       }
       pick->slots = std::move(slots);
       pick->bytes = bytes;
