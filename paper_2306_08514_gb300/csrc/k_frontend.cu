@@ -311,156 +311,11 @@ __global__ __launch_bounds__(N / 8) void gcc_samples_kernel(
     for (int c = L + j; c < out_cols; c += T) put_op_rt(ot, out, out_lo, row + c, 0.f);
 }
 
-// ---------------------------------------------------------------------------------
-// Sampling for N = 1024 with the frame's y-hat held in shared memory.  One block per
-// frame loads y-hat [M][K] once; each warp takes pairs of pairs (2t, 2t+1) in turn and
-// forms psi-bar_a + i psi-bar_b (two-sided, Eq. psi_p_two) straight from it.  The
-// 1024-point inverse DFT runs as 32 x 32 Cooley-Tukey: with n = 32 n1 + n2 and
-// k = k1 + 32 k2, lane n2 takes the 32-point DFT over n1 in registers, multiplies output k1
-// by W^(n2 k1) (W = exp(+2 pi i / 1024)), one warp-local transpose through shared memory
-// hands lane k1 the values of every n2, and a second 32-point DFT over n2 gives
-// X[k1 + 32 k2] in lane k1.  The samples of lags -N_p..N_p (index mod(n, N), Eq. n_prime)
-// leave coalesced, ascending.
-// ---------------------------------------------------------------------------------
-// cos(j pi / 16), j = 0..8
-__device__ __forceinline__ constexpr float cos_pi16(int j) {
-  return j == 0 ? 1.0f
-       : j == 1 ? 0.98078528040323044913f
-       : j == 2 ? 0.92387953251128675613f
-       : j == 3 ? 0.83146961230254523708f
-       : j == 4 ? 0.70710678118654752440f
-       : j == 5 ? 0.55557023301960222474f
-       : j == 6 ? 0.38268343236508977173f
-       : j == 7 ? 0.19509032201612826785f
-                : 0.0f;
-}
-
-__device__ __forceinline__ constexpr int bitrev5(int i) {
-  return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
-}
-
-// 32-point DFT in place (natural order in and out; exp(-2 pi i kn/32), exp(+...) when INV):
-// bit reversal, then five radix-2 stages with the twiddles as constants.
-template <bool INV>
-__device__ __forceinline__ void dft32(float2 (&x)[32]) {
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int r = bitrev5(i);
-    if (i < r) {
-      const float2 t = x[i];
-      x[i] = x[r];
-      x[r] = t;
-    }
-  }
-#pragma unroll
-  for (int half = 1; half < 32; half <<= 1) {
-#pragma unroll
-    for (int j = 0; j < half; ++j) {
-      const int e = j * (16 / half);  // twiddle exp(-+2 pi i e / 32), e = 0..15
-      const float c = e <= 8 ? cos_pi16(e) : -cos_pi16(16 - e);
-      const float sn = e <= 8 ? cos_pi16(8 - e) : cos_pi16(e - 8);
-#pragma unroll
-      for (int k = j; k < 32; k += 2 * half) {
-        float2 t = x[k + half];
-        if (e == 8) {
-          t = INV ? make_float2(-t.y, t.x) : make_float2(t.y, -t.x);
-        } else if (e != 0) {
-          t = cmul(INV ? make_float2(c, sn) : make_float2(c, -sn), t);
-        }
-        x[k + half] = csub(x[k], t);
-        x[k] = cadd(x[k], t);
-      }
-    }
-  }
-}
-
-constexpr int kS32Warps = 4;
-
-__global__ __launch_bounds__(32 * kS32Warps, 1) void gcc_samples32_kernel(
-    const float2* __restrict__ yhat, int M, int P, const int2* __restrict__ pairs,
-    const int* __restrict__ Np, const int* __restrict__ off, int L,
-    const float2* __restrict__ twiddle, int ot, void* out, void* out_lo, int out_cols) {
-  constexpr int N = 1024, K = 512;
-  extern __shared__ float4 sm4[];
-  float2* ys = reinterpret_cast<float2*>(sm4);  // [M][K]
-  float2* tr = ys + static_cast<size_t>(M) * K; // [warps][32][33]
-  const int f = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  {
-    const float4* src = reinterpret_cast<const float4*>(yhat + static_cast<size_t>(f) * M * K);
-    for (int e = threadIdx.x; e < M * K / 2; e += blockDim.x) sm4[e] = __ldg(src + e);
-  }
-  __syncthreads();
-  float2* T = tr + warp * 32 * 33;
-  const size_t row = static_cast<size_t>(f) * out_cols;
-  for (int tp = warp; 2 * tp < P; tp += kS32Warps) {
-    const int pa = 2 * tp, pb = pa + 1;
-    const bool hasb = pb < P;
-    const int2 qa = __ldg(pairs + pa);
-    const int2 qb = hasb ? __ldg(pairs + pb) : make_int2(0, 0);
-    float2 x[32];
-#pragma unroll
-    for (int n1 = 0; n1 < 32; ++n1) {
-      const int k = 32 * n1 + lane;
-      float2 v = make_float2(0.f, 0.f);
-      if (k != 0 && k != K) {
-        const int kk = n1 < 16 ? k : N - k;
-        const float2 a = cmul_conj(ys[qa.x * K + kk], ys[qa.y * K + kk]);
-        const float2 b = hasb ? cmul_conj(ys[qb.x * K + kk], ys[qb.y * K + kk]) : make_float2(0.f, 0.f);
-        v = n1 < 16 ? make_float2(a.x - b.y, a.y + b.x)   // psi_a + i psi_b
-                    : make_float2(a.x + b.y, b.x - a.y);  // psi_a^* + i psi_b^* (mirror)
-      }
-      x[n1] = v;
-    }
-    dft32<true>(x);
-#pragma unroll
-    for (int k1 = 1; k1 < 32; ++k1) {
-      const int e = lane * k1;  // < N; the table holds exp(-2 pi i e / N) for e < N/2
-      const float2 w = __ldg(twiddle + (e & (K - 1)));
-      const float sg = e < K ? 1.f : -1.f;
-      x[k1] = cmul(x[k1], make_float2(sg * w.x, -sg * w.y));
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) T[k1 * 33 + lane] = x[k1];
-    __syncwarp();
-#pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) x[n2] = T[lane * 33 + n2];
-    __syncwarp();
-    dft32<true>(x);  // lane k1 now holds X[k1 + 32 k2] in x[k2]
-    const int na = __ldg(Np + pa);
-    const size_t oa = row + __ldg(off + pa);
-    const int nb = hasb ? __ldg(Np + pb) : 0;
-    const size_t ob = hasb ? row + __ldg(off + pb) : 0;
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) {
-      const int idx = lane + 32 * k2;
-      const int n = idx < K ? idx : idx - N;  // the lag of this output
-      if (n >= -na && n <= na) put_op_rt(ot, out, out_lo, oa + n + na, x[k2].x);
-      if (hasb && n >= -nb && n <= nb) put_op_rt(ot, out, out_lo, ob + n + nb, x[k2].y);
-    }
-  }
-  if (warp == 0)  // the operand's zero padding beyond L
-    for (int c = L + lane; c < out_cols; c += 32) put_op_rt(ot, out, out_lo, row + c, 0.f);
-}
-
-size_t gcc_samples32_smem(int M) {
-  return sizeof(float2) * (static_cast<size_t>(M) * 512 + kS32Warps * 32 * 33);
-}
-
 cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
                                const int* Np, const int* off, int L, const float2* twiddle,
                                OpType t, void* out, void* out_lo, int out_cols, cudaStream_t s) {
   if (F <= 0) return cudaSuccess;
   if (out_cols < L) return cudaErrorInvalidValue;
-  if (N == 1024 && gcc_samples32_smem(M) <= 200 * 1024) {
-    const size_t smem = gcc_samples32_smem(M);
-    cudaError_t e = cudaFuncSetAttribute(gcc_samples32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    gcc_samples32_kernel<<<F, 32 * kS32Warps, smem, s>>>(yhat, M, P, pairs, Np, off, L, twiddle,
-                                                         static_cast<int>(t), out, out_lo, out_cols);
-    return cudaGetLastError();
-  }
   if (F > kMaxGridY) {
     cudaError_t e = launch_gcc_samples(yhat, kMaxGridY, M, P, N, pairs, Np, off, L, twiddle, t,
                                        out, out_lo, out_cols, s);
