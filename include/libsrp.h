@@ -216,9 +216,10 @@ srp_status srp_map(srp_plan_t plan, const float* frames, int F, float* maps, int
  * square rounded to FP32); on a far-field plan the coordinates are the unit directions.
  *   frames: device float [F][M][N].
  *   maps:   device float [F][J], written (as srp_map), or NULL: estimates only.  The maps
- *           then go through plan-owned scratch in chunks of at most 32 MB (allocated on
- *           the first such call and kept), small enough to stay in L2 between the
- *           contraction that writes them and the passes that read them.
+ *           then go through plan-owned scratch in chunks of at most 32 MB (whole
+ *           128-frame tiles where that allows; allocated on the first such call and kept),
+ *           small enough to stay in L2 between the contraction that writes them and the
+ *           passes that read them.
  *   K:      picks per frame, 1..16;  d_min: metres, finite, >= 0 (0: the K largest cells).
  *   peaks:  device int32 [F][K], written; -1 where no location is left.
  *   values: device float [F][K] (the map values at the picks, NaN where -1) or NULL.
@@ -275,8 +276,11 @@ srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int F, float* x
 /*
  * srp_plan_autotune -- pick the tensor-core kernel variant of this plan by timing them on
  * the device: 128x256-cell tiles with 4 operand stages (long reductions), 128x256 with 2
- * stages and 4 output boxes per epilogue warp (short reductions, map-write bound), and
- * 128x128 tiles (twice the tiles for small grids or batches).  Each variant runs the whole
+ * stages and 4 output boxes per epilogue warp (short reductions, map-write bound),
+ * 128x128 tiles (twice the tiles for small grids or batches), and for the hi + lo
+ * precisions 128x256 tiles with 2 stages that each hold the hi and lo planes of both
+ * operands for one k-block and issue its three products in turn (each operand tile loaded
+ * once instead of twice; variant 3).  Each variant runs the whole
  * srp_map path 2 + 5 times on F frames of a synthetic input (plan-owned temporary
  * buffers); the fastest is kept by the plan for later calls.  Until a plan is tuned a
  * heuristic picks by reduction length.  FP32 plans have nothing to tune (variant -1).
@@ -292,8 +296,9 @@ typedef struct {
 } srp_tune_report_t;
 srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream, srp_tune_report_t* report);
 
-/* srp_plan_set_variant -- pin the tensor-core variant (0..2 as in srp_plan_autotune) or
- * return to the heuristic (-1).  Errors: SRP_EINVAL (out of range, or an FP32 plan). */
+/* srp_plan_set_variant -- pin the tensor-core variant (0..3 as in srp_plan_autotune) or
+ * return to the heuristic (-1).  Errors: SRP_EINVAL (out of range, an FP32 plan, or
+ * variant 3 without a hi + lo precision). */
 srp_status srp_plan_set_variant(srp_plan_t plan, int variant);
 
 /*

@@ -1330,7 +1330,10 @@ extern "C" srp_status srp_map_peaks(srp_plan_t plan, const float* frames, int F,
   if (!maps) {
     if (!plan->d_peak_maps) {
       const size_t per = sizeof(float) * static_cast<size_t>(g.J);
-      int fc = static_cast<int>(std::min<size_t>(plan->Fmax, std::max<size_t>(1, kPeakScratchBytes / per)));
+      // whole 128-frame tiles of the contraction where the budget allows
+      size_t fit = std::max<size_t>(1, kPeakScratchBytes / per);
+      if (fit >= 128) fit = fit / 128 * 128;
+      int fc = static_cast<int>(std::min<size_t>(plan->Fmax, fit));
       if (dalloc(plan, &plan->d_peak_maps, per * fc) != cudaSuccess) {
         cudaGetLastError();
         plan->d_peak_maps = nullptr;
@@ -1521,6 +1524,7 @@ extern "C" srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream,
     st = fail(SRP_ECUDA, "autotune set-up");
   float best = 0.f;
   for (int v = 0; v < TC_NVARIANTS && st == SRP_OK; ++v) {
+    if (!tc_gemm_variant_valid(v, plan->op)) continue;
     plan->tc_variant = v;
     for (int it = 0; it < 2 && st == SRP_OK; ++it)  // warm-up
       st = run_chunk(plan, d_frames, F, d_maps, nullptr, s);
@@ -1554,9 +1558,11 @@ extern "C" srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream,
 extern "C" srp_status srp_plan_set_variant(srp_plan_t plan, int variant) {
   clear_error();
   if (!plan) return fail(SRP_EINVAL, "plan is NULL");
-  if (variant < -1 || variant >= TC_NVARIANTS) return fail(SRP_EINVAL, "variant must be in -1..2");
+  if (variant < -1 || variant >= TC_NVARIANTS) return fail(SRP_EINVAL, "variant must be in -1..3");
   if (plan->op == OpType::F32 && variant != -1)
     return fail(SRP_EINVAL, "FP32 plans have no tensor-core variant");
+  if (variant >= 0 && !tc_gemm_variant_valid(variant, plan->op))
+    return fail(SRP_EINVAL, "variant 3 (hi and lo planes per stage) needs a hi + lo precision");
   plan->tc_variant = variant;
   return SRP_OK;
 }

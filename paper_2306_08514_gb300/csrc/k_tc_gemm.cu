@@ -58,13 +58,17 @@ constexpr int stage_bytes() { return A_BYTES + TN * TK * 2; }
 // epilogue warp.  Long reductions keep 4 stages and one box; short ones (bound by the map
 // write) keep 2 stages and 4 boxes, so a warp's boxes of a tile leave without waiting for
 // one another.  TN is the cell width of a tile (256, or 128 for small grids).
-template <int STAGES, int BOXES, int TN>
+// FUSED (hi + lo precisions): a stage holds A_hi, A_lo, B_hi and B_lo of one k-block and
+// feeds all three products, so each operand tile is loaded once instead of twice.
+template <int STAGES, int BOXES, int TN, bool FUSED = false>
 constexpr int smem_bytes() {
-  return STAGES * stage_bytes<TN>() + NEPI * BOXES * OUT_BOX + BAR_BYTES + 1024;
+  return STAGES * stage_bytes<TN>() * (FUSED ? 2 : 1) + NEPI * BOXES * OUT_BOX + BAR_BYTES + 1024;
 }
 static_assert(smem_bytes<4, 1, 256>() <= 232448 && smem_bytes<2, 4, 256>() <= 232448 &&
-                  smem_bytes<4, 2, 128>() <= 232448,
+                  smem_bytes<4, 2, 128>() <= 232448 && smem_bytes<2, 1, 256, true>() <= 232448,
               "shared memory budget");
+// k-blocks per accumulator chunk of the FUSED kernel: 3 x 12 = 36 K=16 steps
+constexpr int KB_PER_CHUNK_FUSED = 3;
 // k-steps per tile up to which the heuristic picks 2 stages + 4 boxes (measured on uca8:
 // SLRI's one k-block per tile 0.112 -> 0.085 ms; SSPI's five k-blocks run faster with 4)
 constexpr int SHORT_MAX_STEPS = 3;
@@ -112,20 +116,23 @@ __device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
   return w;
 }
 
-template <int STAGES, int BOXES, int TN>
+template <int STAGES, int BOXES, int TN, bool FUSED = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
                    const __grid_constant__ CUtensorMap tmZ, const TcParams p, const uint32_t idesc) {
   using namespace tc;
   constexpr int B_BYTES = TN * TK * 2;
-  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int NPL = FUSED ? 2 : 1;         // operand planes per stage (hi, lo)
+  constexpr int STAGE_BYTES = NPL * (A_BYTES + B_BYTES);
+  constexpr int CHUNK = FUSED ? KB_PER_CHUNK_FUSED : KB_PER_CHUNK;
   constexpr int EPI_COLS = TN / 2;           // columns per epilogue thread
   constexpr uint32_t TMEM_COLS = 2 * TN;     // two accumulators
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // stage s: A planes at sA + s * NPL * A_BYTES, B planes at sB + s * NPL * B_BYTES
   const uint32_t sA = smem_u32(smem);
-  const uint32_t sB = sA + STAGES * A_BYTES;
+  const uint32_t sB = sA + STAGES * NPL * A_BYTES;
   uint8_t* out_smem = smem + STAGES * STAGE_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(out_smem + NEPI * BOXES * OUT_BOX);
   const uint32_t bar0 = smem_u32(bars);
@@ -191,11 +198,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = false;
             break;
           }
-          const CUtensorMap* ta = seg == 2 ? &tmA1 : &tmA0;
-          const CUtensorMap* tb = seg == 1 ? &tmB1 : &tmB0;
           mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
-          tma_load_2d(sA + stage * A_BYTES, ta, kx, w.m * TM, full_bar(stage));
-          tma_load_2d(sB + stage * B_BYTES, tb, kx, w.n * TN, full_bar(stage));
+          if constexpr (FUSED) {
+            const uint32_t a = sA + stage * 2 * A_BYTES, b = sB + stage * 2 * B_BYTES;
+            tma_load_2d(a, &tmA0, kx, w.m * TM, full_bar(stage));
+            tma_load_2d(a + A_BYTES, &tmA1, kx, w.m * TM, full_bar(stage));
+            tma_load_2d(b, &tmB0, kx, w.n * TN, full_bar(stage));
+            tma_load_2d(b + B_BYTES, &tmB1, kx, w.n * TN, full_bar(stage));
+          } else {
+            const CUtensorMap* ta = seg == 2 ? &tmA1 : &tmA0;
+            const CUtensorMap* tb = seg == 1 ? &tmB1 : &tmB0;
+            tma_load_2d(sA + stage * A_BYTES, ta, kx, w.m * TM, full_bar(stage));
+            tma_load_2d(sB + stage * B_BYTES, tb, kx, w.n * TN, full_bar(stage));
+          }
           filled |= 1u << stage;
           filled_par = (filled_par & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -221,7 +236,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int gc = 0;  // chunks issued by this CTA (selects the accumulator and its phase)
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         const TileWork w = tile_work(p, t);
-        for (int c0 = w.s0; c0 < w.s1 && ok; c0 += KB_PER_CHUNK, ++gc) {
+        for (int c0 = w.s0; c0 < w.s1 && ok; c0 += CHUNK, ++gc) {
           const int acc = gc & 1;
           const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
           if (!mbar_wait_bounded(tempty_bar(acc), aph ^ 1u, abort_flag, 3, p.wait_ns)) {
@@ -230,28 +245,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem_base + static_cast<uint32_t>(acc * TN);
-          const int c1 = min(w.s1, c0 + KB_PER_CHUNK);
+          const int c1 = min(w.s1, c0 + CHUNK);
           for (int s = c0; s < c1; ++s) {
             if (!mbar_wait_bounded(full_bar(stage), phase, abort_flag, 2, p.wait_ns)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint64_t ad = sdesc_k128(sA + stage * A_BYTES);
-            const uint64_t bd = sdesc_k128(sB + stage * B_BYTES);
-            // four MMAs per 128-byte k-step (K = 16 of 16-bit or K = 8 of TF32 each)
-            if (p.tf32) {
+            // FUSED: the products A_hi B_hi, A_hi B_lo, A_lo B_hi of this k-block in turn;
+            // otherwise the stage's one pair
 #pragma unroll
-              for (int k = 0; k < 4; ++k)
-                mma_tf32(d, ad + static_cast<uint64_t>((k * 32) >> 4),
-                         bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
-                         (s > c0 || k > 0) ? 1u : 0u);
-            } else {
+            for (int pr = 0; pr < (FUSED ? 3 : 1); ++pr) {
+              const uint32_t a_off = (FUSED && pr == 2) ? A_BYTES : 0u;
+              const uint32_t b_off = (FUSED && pr == 1) ? B_BYTES : 0u;
+              const uint64_t ad = sdesc_k128(sA + stage * NPL * A_BYTES + a_off);
+              const uint64_t bd = sdesc_k128(sB + stage * NPL * B_BYTES + b_off);
+              // four MMAs per 128-byte k-step (K = 16 of 16-bit or K = 8 of TF32 each)
+              if (p.tf32) {
 #pragma unroll
-              for (int k = 0; k < 4; ++k)
-                mma_f16(d, ad + static_cast<uint64_t>((k * 32) >> 4),
-                        bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
-                        (s > c0 || k > 0) ? 1u : 0u);
+                for (int k = 0; k < 4; ++k)
+                  mma_tf32(d, ad + static_cast<uint64_t>((k * 32) >> 4),
+                           bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
+                           (s > c0 || pr > 0 || k > 0) ? 1u : 0u);
+              } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  mma_f16(d, ad + static_cast<uint64_t>((k * 32) >> 4),
+                          bd + static_cast<uint64_t>((k * 32) >> 4), idesc,
+                          (s > c0 || pr > 0 || k > 0) ? 1u : 0u);
+              }
             }
             mma_commit(empty_bar(stage));
             if (++stage == STAGES) {
@@ -282,7 +304,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       float sum[EPI_COLS];
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) sum[j] = 0.f;
-      for (int c0 = w.s0; c0 < w.s1; c0 += KB_PER_CHUNK, ++gc) {
+      for (int c0 = w.s0; c0 < w.s1; c0 += CHUNK, ++gc) {
         const int acc = gc & 1;
         const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
         const bool got = mbar_wait_bounded(tfull_bar(acc), aph, abort_flag, 4, p.wait_ns);
@@ -445,11 +467,11 @@ size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, OpType t, int num_sms)
 }
 
 namespace {
-template <int STAGES, int BOXES, int TN>
+template <int STAGES, int BOXES, int TN, bool FUSED = false>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(tc_gemm_kernel<STAGES, BOXES, TN>,
+  return cudaFuncSetAttribute(tc_gemm_kernel<STAGES, BOXES, TN, FUSED>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem_bytes<STAGES, BOXES, TN>());
+                              smem_bytes<STAGES, BOXES, TN, FUSED>());
 }
 }  // namespace
 
@@ -458,7 +480,12 @@ cudaError_t tc_gemm_prepare() {
   if (e != cudaSuccess) return e;
   if ((e = set_smem_attr<4, 1, 256>()) != cudaSuccess) return e;
   if ((e = set_smem_attr<2, 4, 256>()) != cudaSuccess) return e;
+  if ((e = set_smem_attr<2, 1, 256, true>()) != cudaSuccess) return e;
   return set_smem_attr<4, 2, 128>();
+}
+
+bool tc_gemm_variant_valid(int variant, OpType t) {
+  return variant >= 0 && variant < TC_NVARIANTS && (variant != TC_FUSED3_256 || op_split(t));
 }
 
 int tc_gemm_cell_tile() { return LIST_TILE; }
@@ -475,7 +502,8 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
   const int variant = g.variant >= 0 ? g.variant : tc_gemm_default_variant(g.Kd, g.t);
-  if (variant < 0 || variant >= TC_NVARIANTS) return cudaErrorInvalidValue;
+  if (!tc_gemm_variant_valid(variant, g.t)) return cudaErrorInvalidValue;
+  const bool fused = variant == TC_FUSED3_256;
   const int tn = variant == TC_LONG_128 ? 128 : 256;
   if (g.t == OpType::F32) return cudaErrorInvalidValue;
   const bool split3 = op_split(g.t);
@@ -504,7 +532,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.stall = g.stall ? 1 : 0;
   p.wait_ns = g.stall ? STALL_WAIT_NS : WAIT_NS;
   p.kb_per_seg = (g.Kd / TK) << p.sub_shift;
-  p.nseg = split3 ? 3 : 1;
+  p.nseg = (split3 && !fused) ? 3 : 1;  // FUSED: one pass, the three products per k-block
   p.kb_ptr = g.kb_ptr;
   p.kb_idx = g.kb_idx;
   p.nM = (g.F + TM - 1) / TM;
@@ -547,6 +575,10 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
     case TC_LONG_128:
       if ((e = set_smem_attr<4, 2, 128>()) != cudaSuccess) return e;
       tc_gemm_kernel<4, 2, 128><<<grid, NTHREADS, smem_bytes<4, 2, 128>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+      break;
+    case TC_FUSED3_256:
+      if ((e = set_smem_attr<2, 1, 256, true>()) != cudaSuccess) return e;
+      tc_gemm_kernel<2, 1, 256, true><<<grid, NTHREADS, smem_bytes<2, 1, 256, true>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
       break;
     default:
       if ((e = set_smem_attr<4, 1, 256>()) != cudaSuccess) return e;

@@ -207,7 +207,10 @@ struct TcGemm {
 enum { TC_LONG_256 = 0,   // 128x256 tiles, 4 operand stages, 1 output box per epilogue warp
        TC_SHORT_256 = 1,  // 128x256 tiles, 2 stages, 4 boxes (short reductions)
        TC_LONG_128 = 2,   // 128x128 tiles, 4 stages, 2 boxes (small grids: twice the tiles)
-       TC_NVARIANTS = 3 };
+       TC_FUSED3_256 = 3, // hi + lo precisions: 128x256 tiles, 2 stages each holding the hi and
+                          // lo planes of A and B for one k-block (the three products in turn)
+       TC_NVARIANTS = 4 };
+bool tc_gemm_variant_valid(int variant, OpType t);
 int tc_gemm_default_variant(int Kd, OpType t);
 cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s);
 int tc_gemm_slices(int F, int J, int Kd, OpType t, int num_sms);

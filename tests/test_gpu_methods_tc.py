@@ -156,8 +156,10 @@ def test_slri_long_sample_vectors(S, name, F, sub, rank, prec):
 @pytest.mark.parametrize("method,kw", [("conv", {}), ("slri", dict(rank=16)), ("sspi", dict(taps=4.0)),
                                        ("td", {})])
 def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
-    """The three tcgen05 variants (128x256 4-stage, 128x256 2-stage 4-box, 128x128) give the
-    oracle's maps on ragged tiles; srp_plan_autotune times them and keeps one."""
+    """The four tcgen05 variants (128x256 4-stage, 128x256 2-stage 4-box, 128x128, and for
+    the hi + lo precisions 128x256 with the hi and lo planes of one k-block per stage) give
+    the oracle's maps on ragged tiles; srp_plan_autotune times them and keeps one; a BF16
+    plan refuses the hi + lo variant."""
     name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
     Lam = R.lam(name, F, sub)
@@ -174,16 +176,20 @@ def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
     plan = S.Plan(*args, method=method, precision="fp16x3", max_frames=64, **kw)
     if method == "sspi":  # Lambda masked by the plan's own (valid) selection
         zo = O.srp_sspi(np.where(_check_taps(plan, mask, perm, Lam), Lam, 0.0), xi_o)
-    for v in (0, 1, 2, -1):
+    for v in (0, 1, 2, 3, -1):
         plan.set_variant(v)
         z, am = _run(plan, w["frames"])
         plan.status()
         assert R.per_frame_rel(z, zo).max() <= TOL, v
         check_argmax(z, am, zo)
     rep = plan.autotune(F=64)
-    assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 3
+    assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 4
     z, am = _run(plan, w["frames"])
     assert R.per_frame_rel(z, zo).max() <= TOL
+    single = S.Plan(*args, method=method, precision="bf16", max_frames=64, **kw)
+    with pytest.raises(S.SrpError):
+        single.set_variant(3)
+    assert len(single.autotune(F=64)["ms"]) == 3
 
 
 @pytest.mark.parametrize("method,kw,prec,tol", [
