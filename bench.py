@@ -63,6 +63,8 @@ def parse(argv=None):
                     help="frames whose argmax is compared with the FP64 oracle's")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="pin the tensor-core kernel variant of every plan (0..3, as srp_plan_autotune)")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
     ap.add_argument("--no-other-workloads", action="store_true",
@@ -413,6 +415,10 @@ def make_plans(S, a, w, methods, prec, F):
     """One plan per method at its precision, each tuned (tile shape) for batches of F."""
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
     plans = {m: S.Plan(*args, max_frames=F, precision=prec[m], **PLAN_KW[m](a)) for m in methods}
+    if a.variant is not None:
+        for m in methods:
+            plans[m].set_variant(a.variant)
+        return plans, {m: {"variant": a.variant, "pinned": True} for m in methods}
     tuned = {m: plans[m].autotune(F) for m in methods} if not a.no_autotune else {}
     return plans, tuned
 

@@ -4,10 +4,10 @@
 // than d_min to it.  The lowest index wins a tie (the order of argmax_key).
 //
 // Pick 0 is the contraction's argmax (its keys are already merged per frame).  Every later
-// pick is one pass over the frame's map row: blocks of 2048 cells test each cell against
-// the earlier picks, reduce the largest key and merge it into keys[f] with atomicMax; a
-// per-frame take kernel decodes the key, writes the pick and clears the key for the next
-// pass.  The exclusion test is made in FP32 with a fixed operation order (no contraction
+// pick is one pass over the frames' map rows: blocks of 2048 cells and 8 frames test each
+// cell against the frame's earlier picks, reduce the largest key per frame and merge it into
+// keys[f] with atomicMax; a per-frame take kernel decodes the key, writes the pick and
+// clears the key for the next pass.  The exclusion test is made in FP32 with a fixed operation order (no contraction
 // into FMA), so that the decision is reproducible on the host:
 //   d^2 = ((dx*dx + dy*dy) + dz*dz), d = q_i - q_pick, every operation rounded to FP32,
 //   excluded when d^2 < t, t = d_min^2 rounded to FP32.
@@ -19,7 +19,7 @@ namespace srp {
 namespace {
 constexpr int kPeakCellsPerThread = 8;
 constexpr int kPeakThreads = 256;
-constexpr int kPeakMaxFramesPerLaunch = 65535;  // frames index grid y
+constexpr int kPeakMaxBlocksY = 65535;  // frame blocks index grid y
 }  // namespace
 
 __device__ __forceinline__ float peak_dist2(float4 a, float4 b) {
@@ -29,53 +29,68 @@ __device__ __forceinline__ float peak_dist2(float4 a, float4 b) {
   return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-// Pass for pick k >= 1 of frame f = f0 + blockIdx.y.
+// Pass for pick k >= 1 of the frames f0 + blockIdx.y * FPB .. + FPB - 1: each thread keeps
+// the coordinates of its cells in registers and tests them for every frame of the block.
+constexpr int kPeakFramesPerBlock = 8;
+
 __global__ __launch_bounds__(kPeakThreads) void peaks_pass_kernel(
-    const float* __restrict__ Z, int J, const float4* __restrict__ grid,
+    const float* __restrict__ Z, int F, int J, const float4* __restrict__ grid,
     const int* __restrict__ picks, int K, int k, float t, unsigned long long* __restrict__ keys,
     int f0) {
-  __shared__ float4 pc[kPeaksMax];
-  __shared__ int pi[kPeaksMax];
-  __shared__ int ended;
-  __shared__ unsigned long long red[kPeakThreads / 32];
-  const int f = f0 + blockIdx.y;
+  constexpr int FPB = kPeakFramesPerBlock;
+  __shared__ float4 pc[FPB][kPeaksMax];
+  __shared__ int pi[FPB][kPeaksMax];
+  __shared__ int ended[FPB];
+  __shared__ unsigned long long red[kPeakThreads / 32][FPB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) ended = 0;
+  const int fb0 = f0 + blockIdx.y * FPB;
+  const int nf = min(FPB, F - fb0);
+  if (tid < FPB) ended[tid] = tid < nf ? 0 : 1;
   __syncthreads();
-  if (tid < k) {
-    const int i = picks[static_cast<size_t>(f) * K + tid];
-    pi[tid] = i;
+  for (int e = tid; e < nf * k; e += kPeakThreads) {
+    const int fl = e / k, j = e - fl * k;
+    const int i = picks[static_cast<size_t>(fb0 + fl) * K + j];
+    pi[fl][j] = i;
     if (i < 0) {
-      ended = 1;
+      ended[fl] = 1;
     } else {
-      pc[tid] = __ldg(grid + i);
+      pc[fl][j] = __ldg(grid + i);
     }
   }
   __syncthreads();
-  if (ended) return;  // an earlier pick found no location left (uniform over the block)
-  const float* zr = Z + static_cast<size_t>(f) * J;
-  unsigned long long best = 0ull;
   const int base = blockIdx.x * (kPeakThreads * kPeakCellsPerThread);
+  float4 q[kPeakCellsPerThread];
 #pragma unroll
   for (int c = 0; c < kPeakCellsPerThread; ++c) {
     const int i = base + c * kPeakThreads + tid;
-    if (i < J) {
-      const float4 q = __ldg(grid + i);
-      bool ok = true;
-      for (int j = 0; j < k; ++j) ok = ok && i != pi[j] && !(peak_dist2(q, pc[j]) < t);
-      if (ok) {
-        const unsigned long long key = argmax_key(zr[i], i);
-        best = key > best ? key : best;
+    q[c] = i < J ? __ldg(grid + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int fl = 0; fl < nf; ++fl) {
+    unsigned long long best = 0ull;
+    if (!ended[fl]) {  // uniform over the block
+      const float* zr = Z + static_cast<size_t>(fb0 + fl) * J;
+#pragma unroll
+      for (int c = 0; c < kPeakCellsPerThread; ++c) {
+        const int i = base + c * kPeakThreads + tid;
+        if (i < J) {
+          bool ok = true;
+          for (int j = 0; j < k; ++j) ok = ok && i != pi[fl][j] && !(peak_dist2(q[c], pc[fl][j]) < t);
+          if (ok) {
+            const unsigned long long key = argmax_key(zr[i], i);
+            best = key > best ? key : best;
+          }
+        }
       }
     }
-  }
-  best = warp_max_u64(best);
-  if (lane == 0) red[warp] = best;
-  __syncthreads();
-  if (warp == 0) {
-    best = lane < kPeakThreads / 32 ? red[lane] : 0ull;
     best = warp_max_u64(best);
-    if (lane == 0 && best) atomicMax(keys + f, best);
+    if (lane == 0) red[warp][fl] = best;
+  }
+  __syncthreads();
+  if (tid < nf) {
+    unsigned long long b = 0ull;
+#pragma unroll
+    for (int w = 0; w < kPeakThreads / 32; ++w) b = red[w][tid] > b ? red[w][tid] : b;
+    if (b) atomicMax(keys + fb0 + tid, b);
   }
 }
 
@@ -108,10 +123,13 @@ cudaError_t launch_peaks(const float* Z, int F, int J, const float4* grid,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int gx = (J + kPeakThreads * kPeakCellsPerThread - 1) / (kPeakThreads * kPeakCellsPerThread);
+  constexpr int span = kPeakMaxBlocksY * kPeakFramesPerBlock;  // frames per launch
   for (int k = 1; k < K; ++k) {
-    for (int f0 = 0; f0 < F; f0 += kPeakMaxFramesPerLaunch) {
-      const int nf = F - f0 < kPeakMaxFramesPerLaunch ? F - f0 : kPeakMaxFramesPerLaunch;
-      peaks_pass_kernel<<<dim3(gx, nf), kPeakThreads, 0, s>>>(Z, J, grid, picks, K, k, t, keys, f0);
+    for (int f0 = 0; f0 < F; f0 += span) {
+      const int nf = F - f0 < span ? F - f0 : span;
+      const int gy = (nf + kPeakFramesPerBlock - 1) / kPeakFramesPerBlock;
+      peaks_pass_kernel<<<dim3(gx, gy), kPeakThreads, 0, s>>>(Z, f0 + nf, J, grid, picks, K, k, t,
+                                                               keys, f0);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -123,7 +141,8 @@ cudaError_t launch_peaks(const float* Z, int F, int J, const float4* grid,
 }
 
 int peaks_launches(int F, int K) {
-  const int slices = (F + kPeakMaxFramesPerLaunch - 1) / kPeakMaxFramesPerLaunch;
+  const int span = kPeakMaxBlocksY * kPeakFramesPerBlock;
+  const int slices = (F + span - 1) / span;
   return 1 + (K - 1) * (slices + 1);
 }
 
