@@ -147,6 +147,8 @@ constexpr int kFatGemmMinL = 1024;
 // chunks of cells before each chunk's GEMM (tensor cores, chunks of at most kMaxChunkH).
 constexpr double kMaxStoredH = 64e9;
 constexpr double kMaxChunkH = 48e9;
+constexpr int kChunkSliceSteps = 512;  // k-steps per reduction slice of a chunk's GEMM
+constexpr int kChunkMaxSlices = 64;
 
 // One chunk of at most Fmax frames through the whole path.
 constexpr int kMaxChunkEvents = 4096;
@@ -201,11 +203,12 @@ cudaError_t contract_to(srp_plan_s* p, const void* A, const void* A_lo, const vo
 }
 
 // A block of jn map columns starting at column c0 (rows J apart): Z[:, c0 + j] = A B_j^T
-// for the jn rows of B, argmax keys over the whole map; never split into slices.
+// for the jn rows of B, argmax keys over the whole map; the reduction in the plan's
+// h_slices slices (summed in FP64).
 cudaError_t contract_cols(srp_plan_s* p, const void* A, const void* A_lo, const void* B,
                           const void* B_lo, int Kd, int F, float* out, int c0, int jn,
                           cudaStream_t s) {
-  ++p->launches;
+  p->launches += p->h_slices > 1 ? 2 : 1;
   TcGemm tg;
   tg.A = A;
   tg.A_lo = A_lo;
@@ -218,7 +221,9 @@ cudaError_t contract_cols(srp_plan_s* p, const void* A, const void* A_lo, const 
   tg.Z = out;
   tg.ldz = p->g.J;
   tg.col0 = c0;
-  tg.no_split = true;
+  tg.force_slices = p->h_slices;
+  tg.no_split = p->h_slices <= 1;
+  tg.split_ws = p->d_split;
   tg.keys = p->d_keys;
   tg.err = p->d_err;
   tg.variant = p->tc_variant;
@@ -580,6 +585,14 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
     SRP_ALLOC(p, p->d_tau_lo, sizeof(float) * tl.size());
     SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau_hi, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, s));
     SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_tau_lo, tl.data(), sizeof(float) * tl.size(), cudaMemcpyHostToDevice, s));
+    // a chunk's reduction (P N columns: about 1e6 on the 32-microphone grid) in slices of
+    // about kChunkSliceSteps k-steps: the CTAs sharing a cell tile's rows of H then walk
+    // short, equal reductions and stay together, so those rows come from L2 once instead of
+    // from DRAM for every frame tile; the partial maps are summed in FP64
+    const int ksteps = static_cast<int>(Kd / 64) * op_kb_per64(p->op);
+    p->h_slices = std::max(1, std::min(kChunkMaxSlices, ksteps / kChunkSliceSteps));
+    if (p->h_slices > 1)
+      SRP_ALLOC(p, p->d_split, sizeof(float) * static_cast<size_t>(p->h_slices) * F * p->h_chunk);
     SRP_PLAN_CUDA(p, cudaStreamSynchronize(s));
   } else if (desc->method == SRP_CONV) {
     const size_t Kd = static_cast<size_t>(g.P) * g.N;
@@ -1204,7 +1217,13 @@ extern "C" srp_status srp_plan_estimate_bytes(const srp_plan_desc* desc, size_t*
       const bool gen = d.h_on_the_fly == 1 || (d.h_on_the_fly == 0 && hb > 64e9);
       // generated in the FP32 GEMM (the split TDOAs), or per chunk of at most kMaxChunkH
       // bytes for the tensor cores (plus the FP64 TDOA table)
-      const double hgen = d.precision == SRP_FP32 ? J * P * 8.0 : std::min(hb, kMaxChunkH) + J * P * 8.0;  // split TDOAs
+      // the TC chunk path also holds its reduction slices' partial maps (at most 64 x F x the
+      // chunk's cells; the chunk bounded here by the whole grid)
+      const double hgen = d.precision == SRP_FP32
+                              ? J * P * 8.0
+                              : std::min(hb, kMaxChunkH) + J * P * 8.0 +
+                                    std::min(64.0, std::floor(P * N / 64.0 / kChunkSliceSteps)) * F *
+                                        std::min(J, kMaxChunkH / (hb / J)) * 4.0;
       b += (gen ? hgen : hb) + F * P * N * eb * planes;
       if (d.precision == SRP_FP32 && P * N > 16384) b += std::ceil(P * N / 16384.0) * F * J * 4.0;
       break;

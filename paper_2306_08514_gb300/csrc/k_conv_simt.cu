@@ -143,11 +143,13 @@ __global__ __launch_bounds__(256, 2) void sgemm_nt_argmax_kernel(
   }
 }
 
-// Z[f][i] = sum over the nsplit partial maps (summed in FP64), plus the argmax keys.
+// Z[f][i] = sum over the nsplit partial maps [nsplit][F][J] (summed in FP64), plus the
+// argmax keys.  Z's rows are ldz floats apart and its column 0 is cell col0 of the map (a
+// column block of a wider map); the keys carry col0 + i.
 __global__ __launch_bounds__(256) void split_reduce_argmax_kernel(const float* __restrict__ part,
                                                                   int nsplit, float* __restrict__ Z,
                                                                   unsigned long long* __restrict__ keys,
-                                                                  int F, int J) {
+                                                                  int F, int J, int ldz, int col0) {
   __shared__ unsigned long long red[8];
   const int f = blockIdx.x;
   const size_t FJ = static_cast<size_t>(F) * J;
@@ -157,8 +159,8 @@ __global__ __launch_bounds__(256) void split_reduce_argmax_kernel(const float* _
     double acc = 0.0;
     for (int z = 0; z < nsplit; ++z) acc += static_cast<double>(part[z * FJ + idx]);
     const float v = static_cast<float>(acc);
-    if (Z) Z[idx] = v;  // Z == NULL: estimates only
-    const unsigned long long k = argmax_key(v, i);
+    if (Z) Z[static_cast<size_t>(f) * ldz + i] = v;  // Z == NULL: estimates only
+    const unsigned long long k = argmax_key(v, col0 + i);
     best = k > best ? k : best;
   }
   best = warp_max_u64(best);
@@ -207,9 +209,9 @@ cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
 }
 
 cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long long* keys,
-                                int F, int J, cudaStream_t s) {
+                                int F, int J, cudaStream_t s, int ldz, int col0) {
   dim3 g2(F, (J + 1023) / 1024);
-  split_reduce_argmax_kernel<<<g2, 256, 0, s>>>(ws, nz, Z, keys, F, J);
+  split_reduce_argmax_kernel<<<g2, 256, 0, s>>>(ws, nz, Z, keys, F, J, ldz > 0 ? ldz : J, col0);
   return cudaGetLastError();
 }
 

@@ -65,10 +65,23 @@ __global__ __launch_bounds__(kPeakThreads) void peaks_pass_kernel(
     const int i = base + c * kPeakThreads + tid;
     q[c] = i < J ? __ldg(grid + i) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  for (int fl = 0; fl < nf; ++fl) {
+  // every map value of the block's frames and cells is loaded before any is tested, so the
+  // loads are in flight together
+  float v[FPB][kPeakCellsPerThread];
+#pragma unroll
+  for (int fl = 0; fl < FPB; ++fl) {
+    const float* zr = Z + static_cast<size_t>(fb0 + (fl < nf ? fl : 0)) * J;
+#pragma unroll
+    for (int c = 0; c < kPeakCellsPerThread; ++c) {
+      const int i = base + c * kPeakThreads + tid;
+      v[fl][c] = (fl < nf && i < J) ? zr[i] : 0.f;
+    }
+  }
+#pragma unroll
+  for (int fl = 0; fl < FPB; ++fl) {
+    if (fl >= nf) break;  // uniform over the block
     unsigned long long best = 0ull;
     if (!ended[fl]) {  // uniform over the block
-      const float* zr = Z + static_cast<size_t>(fb0 + fl) * J;
 #pragma unroll
       for (int c = 0; c < kPeakCellsPerThread; ++c) {
         const int i = base + c * kPeakThreads + tid;
@@ -76,7 +89,7 @@ __global__ __launch_bounds__(kPeakThreads) void peaks_pass_kernel(
           bool ok = true;
           for (int j = 0; j < k; ++j) ok = ok && i != pi[fl][j] && !(peak_dist2(q[c], pc[fl][j]) < t);
           if (ok) {
-            const unsigned long long key = argmax_key(zr[i], i);
+            const unsigned long long key = argmax_key(v[fl][c], i);
             best = key > best ? key : best;
           }
         }

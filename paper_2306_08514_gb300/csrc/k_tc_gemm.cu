@@ -537,7 +537,9 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.kb_idx = g.kb_idx;
   p.nM = (g.F + TM - 1) / TM;
   p.nN = (g.J + tn - 1) / tn;
-  p.nslices = (g.kb_ptr || g.no_split) ? 1 : slices_for(g.F, g.J, g.Kd, g.t, num_sms, tn);
+  p.nslices = (g.kb_ptr || g.no_split) ? 1
+              : g.force_slices > 0 ? g.force_slices
+                                   : slices_for(g.F, g.J, g.Kd, g.t, num_sms, tn);
   p.col0 = g.col0;
   const int kb_total = p.kb_per_seg * p.nseg;
   if (p.nslices > 1) {
@@ -548,8 +550,8 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   }
   p.keys = g.keys;
   p.err = g.err;
-  if (p.nslices > 1) {
-    if (!g.split_ws || (g.ldz && g.ldz != g.J)) return cudaErrorInvalidValue;
+  if (p.nslices > 1) {  // partial maps [nslices][F][J] in the workspace, summed afterwards
+    if (!g.split_ws) return cudaErrorInvalidValue;
     p.Z = g.split_ws;
     p.ldz = g.J;
   } else {
@@ -587,7 +589,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || p.nslices == 1) return e;
-  return launch_split_reduce(g.split_ws, p.nslices, g.Z, g.keys, g.F, g.J, s);
+  return launch_split_reduce(g.split_ws, p.nslices, g.Z, g.keys, g.F, g.J, s, g.ldz, g.col0);
 }
 
 }  // namespace srp

@@ -169,9 +169,10 @@ cudaError_t launch_sgemm_nt_argmax(const float* A, const float* B, float* Z,
                                    unsigned long long* keys, int F, int J, int Kd,
                                    float* split_ws, cudaStream_t s, const float* tau_hi = nullptr,
                                    const float* tau_lo = nullptr, int P = 0, int N = 0);
-// Sums nz partial maps [nz][F][J] in FP64 into Z and merges the argmax keys.
+// Sums nz partial maps [nz][F][J] in FP64 into Z (rows ldz floats apart, 0: J) and merges
+// the argmax keys (cell indices offset by col0).
 cudaError_t launch_split_reduce(const float* ws, int nz, float* Z, unsigned long long* keys,
-                                int F, int J, cudaStream_t s);
+                                int F, int J, cudaStream_t s, int ldz = 0, int col0 = 0);
 // Tensor-core contraction (tcgen05, k_tc_gemm.cu): Z[F][J] = A B^T with K-major operands
 // A [F][Kd], B [J][Kd] of type t (FP16, BF16 or TF32; Kd a multiple of tc_gemm_k_block()),
 // FP32 accumulation, fused argmax keys.  The split types (op_split) run three products over
@@ -194,7 +195,8 @@ struct TcGemm {
   float* Z = nullptr;
   int ldz = 0;        // row stride of Z in floats (0: J); with col0 a column block of a wider map
   int col0 = 0;       // index of Z's first column in the map (argmax keys carry col0 + column)
-  bool no_split = false;  // never split the reduction into slices (column blocks of a map)
+  bool no_split = false;  // never split the reduction into slices
+  int force_slices = 0;   // > 0: split the (dense) reduction into this many slices
   unsigned long long* keys = nullptr;
   float* split_ws = nullptr;
   int* err = nullptr;
@@ -342,6 +344,7 @@ struct srp_plan_s {
   bool use_front = false;  // interpolation methods: one fused front-end launch per chunk
   bool fat_gemm = false;   // SLRI with long sample vectors: u = Lambda_fat xi as a GEMM
   bool h_generated = false;  // conv FP32: SRP matrix generated inside the GEMM, not stored
+  int h_slices = 0;          //   slices of each chunk's reduction (d_split holds the partials)
   int h_chunk = 0;           // conv on the tensor cores, SRP matrix too large to store: cells
                              // per chunk whose rows are generated into d_H before each GEMM
                              // (from d_tau_hi / d_tau_lo)
