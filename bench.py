@@ -47,6 +47,8 @@ def parse(argv=None):
     ap.add_argument("--impl", default="libsrp", choices=["libsrp", "reference"])
     ap.add_argument("--workload", default="uca8")
     ap.add_argument("--frames", type=int, default=None)
+    ap.add_argument("--cells", type=int, default=None,
+                    help="keep the first CELLS grid cells (small profiling captures of a kernel)")
     ap.add_argument("--rank", type=int, default=16, help="SLRI rank R")
     ap.add_argument("--taps", type=float, default=4.0, help="SSPI taps per location and pair")
     ap.add_argument("--precision", default="fp16x3",
@@ -627,6 +629,8 @@ def run_libsrp(a):
     import synth
 
     w = synth.workload(a.workload, F=a.frames, seed=None if rank == 0 else shard_seed(1002, rank))
+    if a.cells:
+        w["grid_xyz"] = w["grid_xyz"][:a.cells]
     F, J, N, M = w["F"], w["grid_xyz"].shape[0], w["N"], w["mic_xyz"].shape[0]
     methods, prec = arm_methods(a)
     plans, tuned = make_plans(S, a, w, methods, prec, F)

@@ -14,9 +14,11 @@
 // Persistent, warp-specialised kernel, one CTA per SM:
 //   warp 0      TMA producer: 128x64 tile of A and 256x64 tile of B per k-block into a
 //               4-stage (2-stage for <= 3 k-blocks per tile) 128-byte-swizzled
-//               shared-memory ring;
+//               shared-memory ring (the FUSED hi + lo kernel: 2 stages, each with the hi
+//               and lo planes of both operands);
 //   warp 1      TMEM owner and single-thread MMA issuer: 4 x tcgen05.mma (M128 N256 K16)
-//               per k-block into one of two 128x256 FP32 accumulators (512 TMEM columns);
+//               per k-block and product into one of two 128x256 FP32 accumulators (512 TMEM
+//               columns);
 //   warps 2-9   epilogue: two warps per TMEM lane quarter, each owning 128 of the 256
 //               columns of 32 frame rows; results leave through swizzled shared-memory
 //               boxes (1 per warp, or 4 with the 2-stage ring) and TMA tensor stores
@@ -26,9 +28,16 @@
 // chunks of KB_PER_CHUNK k-blocks: each chunk starts a fresh TMEM accumulator (the two
 // accumulators alternate, so the MMAs of chunk c+1 overlap the drain of chunk c), and the
 // epilogue adds every finished chunk into FP32 registers (round to nearest).
-// Tiles run m-fastest so the CTAs in flight share the tiles of B.  When the output
-// tiles are too few to fill the GPU the (dense) reduction is also split into slices
-// written to a workspace and summed in FP64 (split_reduce in k_conv_simt.cu).  Every
+// Tiles run m-fastest so the CTAs in flight share the tiles of B.  Cluster variants
+// (CS = 2 CTAs per cluster) go further: the two frame tiles of one cell tile run
+// together, CTA r of the cluster loads rows [r TN/2, (r+1) TN/2) of each B tile and
+// multicasts them into the same stage of both CTAs, and each CTA's MMA issuer frees a
+// stage in both (a stage is refilled once both CTAs have consumed it), so each B tile
+// crosses L2 once per pair of frame tiles.  A frame tile past F (odd tile counts)
+// computes on zero rows and writes nothing.  (Clusters of 4 measured slower: with one
+// CTA per SM fewer of the GPCs' SMs can host whole clusters.)  When the output tiles are
+// too few to fill the GPU the (dense) reduction is also split into slices written to a
+// workspace and summed in FP64 (split_reduce in k_conv_simt.cu).  Every
 // mbarrier wait is bounded (2 s); on a timeout the CTA records an error code, drains its
 // own copies and MMAs, frees its TMEM and returns.
 #include "srp_internal.h"
@@ -46,23 +55,23 @@ namespace srp {
 namespace {
 constexpr int TM = 128, TK = 64;
 constexpr int LIST_TILE = 256;                // cells per block-sparse k-block list
-constexpr int A_BYTES = TM * TK * 2;
 constexpr int NEPI = 8;                       // epilogue warps
 constexpr int NTHREADS = 64 + 32 * NEPI;
 constexpr int OUT_BOX = 32 * 32 * 4;          // one 32x32 FP32 output box
 constexpr int KB_PER_CHUNK = 8;               // 32 K=16 steps per accumulator chunk
 constexpr int BAR_BYTES = 256;
-template <int TN>
-constexpr int stage_bytes() { return A_BYTES + TN * TK * 2; }
+template <int TN, bool FUSED = false>
+constexpr int stage_bytes() { return (FUSED ? 2 : 1) * (TM + TN) * TK * 2; }
 // Shared-memory splits (variants): STAGES operand stages and BOXES output boxes per
 // epilogue warp.  Long reductions keep 4 stages and one box; short ones (bound by the map
 // write) keep 2 stages and 4 boxes, so a warp's boxes of a tile leave without waiting for
 // one another.  TN is the cell width of a tile (256, or 128 for small grids).
 // FUSED (hi + lo precisions): a stage holds A_hi, A_lo, B_hi and B_lo of one k-block and
-// feeds all three products, so each operand tile is loaded once instead of twice.
+// feeds all three products, so each operand tile is loaded once instead of twice.  (Half
+// k-blocks of 64-byte rows, 64-byte swizzle, in 4 stages measured 4-7 % slower.)
 template <int STAGES, int BOXES, int TN, bool FUSED = false>
 constexpr int smem_bytes() {
-  return STAGES * stage_bytes<TN>() * (FUSED ? 2 : 1) + NEPI * BOXES * OUT_BOX + BAR_BYTES + 1024;
+  return STAGES * stage_bytes<TN, FUSED>() + NEPI * BOXES * OUT_BOX + BAR_BYTES + 1024;
 }
 static_assert(smem_bytes<4, 1, 256>() <= 232448 && smem_bytes<2, 4, 256>() <= 232448 &&
                   smem_bytes<4, 2, 128>() <= 232448 && smem_bytes<2, 1, 256, true>() <= 232448,
@@ -100,13 +109,22 @@ struct TileWork {
   int slice, m, n, s0, s1, m_len, list;
 };
 
-__device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
+// Tile t of a cluster of CS CTAs (t counts groups of CS frame tiles), as seen by the CTA
+// of cluster rank crank; CS = 1 is the plain m-fastest walk.
+template <int CS>
+__device__ __forceinline__ int tile_groups(const TcParams& p) {
+  return (p.nM + CS - 1) / CS * p.nN * p.nslices;
+}
+
+template <int CS>
+__device__ __forceinline__ TileWork tile_work(const TcParams& p, int t, int crank) {
   TileWork w;
-  const int per_slice = p.nM * p.nN;
+  const int nMg = (p.nM + CS - 1) / CS;
+  const int per_slice = nMg * p.nN;
   w.slice = t / per_slice;
   const int rem = t - w.slice * per_slice;
-  w.n = rem / p.nM;
-  w.m = rem - w.n * p.nM;
+  w.n = rem / nMg;
+  w.m = (rem - w.n * nMg) * CS + crank;
   w.list = p.kb_ptr ? (w.n * p.tn) / LIST_TILE : 0;
   w.m_len = p.kb_ptr ? (__ldg(p.kb_ptr + w.list + 1) - __ldg(p.kb_ptr + w.list)) << p.sub_shift
                      : p.kb_per_seg;
@@ -116,18 +134,24 @@ __device__ __forceinline__ TileWork tile_work(const TcParams& p, int t) {
   return w;
 }
 
-template <int STAGES, int BOXES, int TN, bool FUSED = false>
+template <int STAGES, int BOXES, int TN, bool FUSED = false, int CS = 1>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
                    const __grid_constant__ CUtensorMap tmZ, const TcParams p, const uint32_t idesc) {
   using namespace tc;
+  constexpr int A_BYTES = TM * TK * 2;
   constexpr int B_BYTES = TN * TK * 2;
   constexpr int NPL = FUSED ? 2 : 1;         // operand planes per stage (hi, lo)
   constexpr int STAGE_BYTES = NPL * (A_BYTES + B_BYTES);
   constexpr int CHUNK = FUSED ? KB_PER_CHUNK_FUSED : KB_PER_CHUNK;
   constexpr int EPI_COLS = TN / 2;           // columns per epilogue thread
   constexpr uint32_t TMEM_COLS = 2 * TN;     // two accumulators
+  constexpr int B_SLICE_ROWS = TN / CS;      // rows of a B tile this CTA loads (and multicasts)
+  constexpr uint32_t B_SLICE_BYTES = B_SLICE_ROWS * TK * 2;
+  constexpr uint16_t CMASK = static_cast<uint16_t>((1u << CS) - 1u);
+  static_assert(CS == 1 || CS == 2, "cluster size");
+  static_assert(B_SLICE_BYTES % 1024 == 0, "B slices must keep the 1024-byte swizzle atom");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // stage s: A planes at sA + s * NPL * A_BYTES, B planes at sB + s * NPL * B_BYTES
@@ -148,7 +172,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
+      mbar_init(empty_bar(s), CS);  // freed by the MMA issuer of every CTA of the cluster
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
@@ -164,9 +188,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // the peers' multicast loads and MMA commits may target this CTA's barriers only once
+  // they are initialised
+  if constexpr (CS > 1) cluster_sync();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int total = p.nM * p.nN * p.nslices;
+  const int total = tile_groups<CS>(p);
+  const int crank = CS > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+  const int tile0 = CS > 1 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+  const int tstep = CS > 1 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -183,8 +213,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       // p.stall (failure-detection test): no load is issued, so the MMA issuer's and the
       // epilogue's bounded waits run out and the CTA records the timeout
-      for (int t = blockIdx.x; t < total && ok && !p.stall; t += gridDim.x) {
-        const TileWork w = tile_work(p, t);
+      for (int t = tile0; t < total && ok && !p.stall; t += tstep) {
+        const TileWork w = tile_work<CS>(p, t, crank);
         const int* list = p.kb_ptr ? p.kb_idx + __ldg(p.kb_ptr + w.list) : nullptr;
         for (int s = w.s0; s < w.s1; ++s) {
           const int seg = s / w.m_len;
@@ -203,13 +233,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t a = sA + stage * 2 * A_BYTES, b = sB + stage * 2 * B_BYTES;
             tma_load_2d(a, &tmA0, kx, w.m * TM, full_bar(stage));
             tma_load_2d(a + A_BYTES, &tmA1, kx, w.m * TM, full_bar(stage));
-            tma_load_2d(b, &tmB0, kx, w.n * TN, full_bar(stage));
-            tma_load_2d(b + B_BYTES, &tmB1, kx, w.n * TN, full_bar(stage));
+            if constexpr (CS > 1) {
+              const uint32_t bs = b + crank * B_SLICE_BYTES;
+              const int y = w.n * TN + crank * B_SLICE_ROWS;
+              tma_load_2d_mc(bs, &tmB0, kx, y, full_bar(stage), CMASK);
+              tma_load_2d_mc(bs + B_BYTES, &tmB1, kx, y, full_bar(stage), CMASK);
+            } else {
+              tma_load_2d(b, &tmB0, kx, w.n * TN, full_bar(stage));
+              tma_load_2d(b + B_BYTES, &tmB1, kx, w.n * TN, full_bar(stage));
+            }
           } else {
             const CUtensorMap* ta = seg == 2 ? &tmA1 : &tmA0;
             const CUtensorMap* tb = seg == 1 ? &tmB1 : &tmB0;
             tma_load_2d(sA + stage * A_BYTES, ta, kx, w.m * TM, full_bar(stage));
-            tma_load_2d(sB + stage * B_BYTES, tb, kx, w.n * TN, full_bar(stage));
+            if constexpr (CS > 1)
+              tma_load_2d_mc(sB + stage * B_BYTES + crank * B_SLICE_BYTES, tb, kx,
+                             w.n * TN + crank * B_SLICE_ROWS, full_bar(stage), CMASK);
+            else
+              tma_load_2d(sB + stage * B_BYTES, tb, kx, w.n * TN, full_bar(stage));
           }
           filled |= 1u << stage;
           filled_par = (filled_par & ~(1u << stage)) | (phase << stage);
@@ -234,8 +275,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t phase = 0;
       bool ok = true;
       int gc = 0;  // chunks issued by this CTA (selects the accumulator and its phase)
-      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        const TileWork w = tile_work(p, t);
+      for (int t = tile0; t < total && ok; t += tstep) {
+        const TileWork w = tile_work<CS>(p, t, crank);
         for (int c0 = w.s0; c0 < w.s1 && ok; c0 += CHUNK, ++gc) {
           const int acc = gc & 1;
           const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
@@ -275,7 +316,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                           (s > c0 || pr > 0 || k > 0) ? 1u : 0u);
               }
             }
-            mma_commit(empty_bar(stage));
+            if constexpr (CS > 1)
+              mma_commit_mc(empty_bar(stage), CMASK);  // the stage is free in this CTA once
+            else                                       // every CTA of the cluster consumed it
+              mma_commit(empty_bar(stage));
             if (++stage == STAGES) {
               stage = 0;
               phase ^= 1u;
@@ -299,8 +343,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint8_t* boxes = out_smem + (warp - 2) * BOXES * OUT_BOX;
     int gc = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const TileWork w = tile_work(p, t);
+    for (int t = tile0; t < total && ok; t += tstep) {
+      const TileWork w = tile_work<CS>(p, t, crank);
       float sum[EPI_COLS];
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) sum[j] = 0.f;
@@ -383,6 +427,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  // no CTA leaves while a peer may still multicast into its shared memory or arrive on its
+  // barriers: every CTA gets here after its MMAs (and with them its commits) completed
+  if constexpr (CS > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, TMEM_COLS);
@@ -407,10 +454,8 @@ cudaError_t get_encode() {
   return cudaSuccess;
 }
 
-// 2-D K-major operand map: inner dimension Kd (contiguous), outer `rows`, box 64 x box_rows,
-// 128-byte swizzle; out-of-range rows read as zero.
-// 2-D operand map over [rows][Kd] elements of ebytes (2 or 4), box of one 128-byte k-step
-// (64 or 32 elements) x box_rows, 128-byte swizzle.
+// 2-D K-major operand map over [rows][Kd] elements of ebytes (2 or 4), box of one 128-byte
+// k-step (64 or 32 elements) x box_rows, 128-byte swizzle; out-of-range rows read as zero.
 cudaError_t make_operand_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, uint64_t Kd,
                              uint64_t rows, uint32_t box_rows, uint32_t ebytes) {
   cuuint64_t dims[2] = {Kd, rows};
@@ -467,25 +512,127 @@ size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, OpType t, int num_sms)
 }
 
 namespace {
-template <int STAGES, int BOXES, int TN, bool FUSED = false>
+template <int STAGES, int BOXES, int TN, bool FUSED = false, int CS = 1>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(tc_gemm_kernel<STAGES, BOXES, TN, FUSED>,
+  return cudaFuncSetAttribute(tc_gemm_kernel<STAGES, BOXES, TN, FUSED, CS>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               smem_bytes<STAGES, BOXES, TN, FUSED>());
 }
+
+// Clusters of the variant that can be resident at once on the current device (queried at
+// plan creation and cached per device, so that a captured launch needs no query).
+constexpr int kMaxDevices = 64;
+std::mutex g_cl_mu;
+int g_max_clusters[kMaxDevices][TC_NVARIANTS] = {};
+
+template <int STAGES, int BOXES, int TN, bool FUSED, int CS>
+cudaError_t query_clusters(int variant) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if ((e = set_smem_attr<STAGES, BOXES, TN, FUSED, CS>()) != cudaSuccess) return e;
+  if (CS == 1) return cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lock(g_cl_mu);
+    if (g_max_clusters[dev][variant] > 0) return cudaSuccess;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CS);
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem_bytes<STAGES, BOXES, TN, FUSED>();
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  e = cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<STAGES, BOXES, TN, FUSED, CS>, &cfg);
+  if (e != cudaSuccess) return e;
+  if (n < 1) return cudaErrorInvalidConfiguration;
+  std::lock_guard<std::mutex> lock(g_cl_mu);
+  g_max_clusters[dev][variant] = n;
+  return cudaSuccess;
+}
+
+int max_clusters(int variant) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  std::lock_guard<std::mutex> lock(g_cl_mu);
+  return g_max_clusters[dev][variant];
+}
+
+// Launches one variant: a plain persistent grid of `ctas` CTAs, or (CS > 1) `ctas` CTAs in
+// clusters of CS.
+template <int STAGES, int BOXES, int TN, bool FUSED, int CS>
+cudaError_t launch_variant(int ctas, const CUtensorMap& mA0, const CUtensorMap& mA1,
+                           const CUtensorMap& mB0, const CUtensorMap& mB1, const CUtensorMap& mZ,
+                           const TcParams& p, uint32_t idesc, cudaStream_t s) {
+  cudaError_t e = set_smem_attr<STAGES, BOXES, TN, FUSED, CS>();
+  if (e != cudaSuccess) return e;
+  constexpr int smem = smem_bytes<STAGES, BOXES, TN, FUSED>();
+  if constexpr (CS == 1) {
+    tc_gemm_kernel<STAGES, BOXES, TN, FUSED, 1><<<ctas, NTHREADS, smem, s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
+    return cudaGetLastError();
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<STAGES, BOXES, TN, FUSED, CS>, mA0, mA1, mB0,
+                              mB1, mZ, p, idesc);
+  }
+}
+
+template <int CS>
+cudaError_t prepare_cs() {
+  constexpr int c = CS == 1 ? 0 : 1;
+  cudaError_t e;
+  if ((e = query_clusters<4, 1, 256, false, CS>(TC_LONG_256 + TC_NBASE * c)) != cudaSuccess) return e;
+  if ((e = query_clusters<2, 4, 256, false, CS>(TC_SHORT_256 + TC_NBASE * c)) != cudaSuccess) return e;
+  if ((e = query_clusters<2, 1, 256, true, CS>(TC_FUSED3_256 + TC_NBASE * c)) != cudaSuccess) return e;
+  return query_clusters<4, 2, 128, false, CS>(TC_LONG_128 + TC_NBASE * c);
+}
+
+template <int CS>
+cudaError_t launch_base(int base, int ctas, const CUtensorMap& mA0, const CUtensorMap& mA1,
+                        const CUtensorMap& mB0, const CUtensorMap& mB1, const CUtensorMap& mZ,
+                        const TcParams& p, uint32_t idesc, cudaStream_t s) {
+  switch (base) {
+    case TC_SHORT_256:
+      return launch_variant<2, 4, 256, false, CS>(ctas, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
+    case TC_LONG_128:
+      return launch_variant<4, 2, 128, false, CS>(ctas, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
+    case TC_FUSED3_256:
+      return launch_variant<2, 1, 256, true, CS>(ctas, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
+    default:
+      return launch_variant<4, 1, 256, false, CS>(ctas, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
+  }
+}
 }  // namespace
+
+int tc_gemm_cluster_size(int variant) { return variant >= TC_NBASE ? 2 : 1; }
 
 cudaError_t tc_gemm_prepare() {
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
-  if ((e = set_smem_attr<4, 1, 256>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<2, 4, 256>()) != cudaSuccess) return e;
-  if ((e = set_smem_attr<2, 1, 256, true>()) != cudaSuccess) return e;
-  return set_smem_attr<4, 2, 128>();
+  if ((e = prepare_cs<1>()) != cudaSuccess) return e;
+  return prepare_cs<2>();
 }
 
 bool tc_gemm_variant_valid(int variant, OpType t) {
-  return variant >= 0 && variant < TC_NVARIANTS && (variant != TC_FUSED3_256 || op_split(t));
+  return variant >= 0 && variant < TC_NVARIANTS &&
+         (variant % TC_NBASE != TC_FUSED3_256 || op_split(t));
 }
 
 int tc_gemm_cell_tile() { return LIST_TILE; }
@@ -503,8 +650,9 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int variant = g.variant >= 0 ? g.variant : tc_gemm_default_variant(g.Kd, g.t);
   if (!tc_gemm_variant_valid(variant, g.t)) return cudaErrorInvalidValue;
-  const bool fused = variant == TC_FUSED3_256;
-  const int tn = variant == TC_LONG_128 ? 128 : 256;
+  const int base = variant % TC_NBASE;
+  const bool fused = base == TC_FUSED3_256;
+  const int tn = base == TC_LONG_128 ? 128 : 256;
   if (g.t == OpType::F32) return cudaErrorInvalidValue;
   const bool split3 = op_split(g.t);
   const bool tf32 = op_tf32(g.t);
@@ -513,16 +661,6 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
                                  : bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   const uint32_t eb = tf32 ? 4u : 2u;
-  CUtensorMap mA0, mA1, mB0, mB1, mZ;
-  if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
-  if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, tn, eb)) != cudaSuccess) return e;
-  if (split3) {
-    if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
-    if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, tn, eb)) != cudaSuccess) return e;
-  } else {
-    mA1 = mA0;
-    mB1 = mB0;
-  }
   TcParams p;
   p.F = g.F;
   p.J = g.J;
@@ -540,6 +678,22 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.nslices = (g.kb_ptr || g.no_split) ? 1
               : g.force_slices > 0 ? g.force_slices
                                    : slices_for(g.F, g.J, g.Kd, g.t, num_sms, tn);
+  // clusters share the B tiles of the frame tiles of one cell tile; a split reduction (too
+  // few output tiles to fill the GPU) runs unclustered
+  int cs = p.nslices > 1 ? 1 : tc_gemm_cluster_size(variant);
+  const int max_cl = cs > 1 ? max_clusters(base + TC_NBASE) : 0;
+  if (cs > 1 && max_cl < 1) return cudaErrorNotReady;  // tc_gemm_prepare() did not run here
+  CUtensorMap mA0, mA1, mB0, mB1, mZ;
+  const uint32_t b_rows = static_cast<uint32_t>(tn / cs);  // each CTA loads its slice of B
+  if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
+  if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, b_rows, eb)) != cudaSuccess) return e;
+  if (split3) {
+    if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
+    if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, b_rows, eb)) != cudaSuccess) return e;
+  } else {
+    mA1 = mA0;
+    mB1 = mB0;
+  }
   p.col0 = g.col0;
   const int kb_total = p.kb_per_seg * p.nseg;
   if (p.nslices > 1) {
@@ -566,28 +720,18 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
     mZ = mA0;  // unused
   }
   const uint32_t idesc = tc::idesc_f16(tf32 ? 2u : bf16 ? 1u : 0u, TM, tn);
-  const int total = p.nM * p.nN * p.nslices;
-  int grid = total < num_sms ? total : num_sms;
-  if (g.max_ctas > 0 && grid > g.max_ctas) grid = g.max_ctas;
-  switch (variant) {
-    case TC_SHORT_256:
-      if ((e = set_smem_attr<2, 4, 256>()) != cudaSuccess) return e;
-      tc_gemm_kernel<2, 4, 256><<<grid, NTHREADS, smem_bytes<2, 4, 256>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
-      break;
-    case TC_LONG_128:
-      if ((e = set_smem_attr<4, 2, 128>()) != cudaSuccess) return e;
-      tc_gemm_kernel<4, 2, 128><<<grid, NTHREADS, smem_bytes<4, 2, 128>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
-      break;
-    case TC_FUSED3_256:
-      if ((e = set_smem_attr<2, 1, 256, true>()) != cudaSuccess) return e;
-      tc_gemm_kernel<2, 1, 256, true><<<grid, NTHREADS, smem_bytes<2, 1, 256, true>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
-      break;
-    default:
-      if ((e = set_smem_attr<4, 1, 256>()) != cudaSuccess) return e;
-      tc_gemm_kernel<4, 1, 256><<<grid, NTHREADS, smem_bytes<4, 1, 256>(), s>>>(mA0, mA1, mB0, mB1, mZ, p, idesc);
-      break;
+  if (cs == 1) {
+    const int total = p.nM * p.nN * p.nslices;
+    int grid = total < num_sms ? total : num_sms;
+    if (g.max_ctas > 0 && grid > g.max_ctas) grid = g.max_ctas;
+    e = launch_base<1>(base, grid, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
+  } else {
+    // persistent clusters: no more than can be resident at once, nor than tile groups
+    const int groups = (p.nM + cs - 1) / cs * p.nN;
+    int ncl = groups < max_cl ? groups : max_cl;
+    if (g.max_ctas > 0 && ncl > g.max_ctas / cs) ncl = g.max_ctas / cs > 0 ? g.max_ctas / cs : 1;
+    e = launch_base<2>(base, ncl * cs, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
   }
-  e = cudaGetLastError();
   if (e != cudaSuccess || p.nslices == 1) return e;
   return launch_split_reduce(g.split_ws, p.nslices, g.Z, g.keys, g.F, g.J, s, g.ldz, g.col0);
 }

@@ -211,7 +211,11 @@ enum { TC_LONG_256 = 0,   // 128x256 tiles, 4 operand stages, 1 output box per e
        TC_LONG_128 = 2,   // 128x128 tiles, 4 stages, 2 boxes (small grids: twice the tiles)
        TC_FUSED3_256 = 3, // hi + lo precisions: 128x256 tiles, 2 stages each holding the hi and
                           // lo planes of A and B for one k-block (the three products in turn)
-       TC_NVARIANTS = 4 };
+       TC_NBASE = 4,      // variant v + 4: variant v in clusters of 2 CTAs that share each
+                          // B tile by TMA multicast
+       TC_NVARIANTS = 8 };
+// CTAs per cluster of a variant (1 or 2).
+int tc_gemm_cluster_size(int variant);
 bool tc_gemm_variant_valid(int variant, OpType t);
 int tc_gemm_default_variant(int Kd, OpType t);
 cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s);

@@ -96,11 +96,16 @@ def test_server_refuses_a_session_whose_allocations_fail(S):
 
 @pytest.mark.parametrize("method,kw", [("slri", dict(rank=8)), ("sspi", dict(taps=2.0)),
                                        ("conv", {})])
-def test_bounded_waits_run_out_and_the_plan_stays_usable(S, method, kw):
+@pytest.mark.parametrize("variant", [-1, 4])
+def test_bounded_waits_run_out_and_the_plan_stays_usable(S, method, kw, variant):
+    """The stall hook on the heuristic's kernel and on its cluster variant (two CTAs sharing
+    the B tiles; SLRI and SSPI run it clustered, conv's split reduction unclustered): both
+    CTAs of a cluster time out, meet at the cluster's closing barrier and return."""
     import torch
     w, args = _square4(S)
     fr = torch.from_numpy(np.ascontiguousarray(w["frames"][:32])).cuda()
     plan = S.Plan(*args, method=method, precision="bf16", max_frames=32, **kw)
+    plan.set_variant(variant)
     z0, a0 = _maps(plan, fr)
     plan.status()
     plan.debug_stall_next_contraction()

@@ -128,6 +128,15 @@ def test_uca8_full_size_tensor_cores_sampled(S):
     zo = O.srp_sspi(np.where(mask_g, R.lam("uca8"), 0.0), xi_o)
     assert R.per_frame_rel(z[fsel], zo).max() <= TOL
     check_argmax(z[fsel], am[fsel], zo)
+    # each kernel alone and in clusters of 2 CTAs that share the B tiles by multicast (16
+    # frame tiles per cell tile): the same maps bit for bit
+    for base in (0, 1, 3):
+        plan.set_variant(base)
+        zb, amb = _run(plan, frames)
+        plan.set_variant(base + 4)
+        zc, amc = _run(plan, frames)
+        plan.status()
+        assert np.array_equal(zc, zb) and np.array_equal(amc, amb), base
 
 
 @pytest.mark.parametrize("name,F,sub,rank,prec", [
@@ -157,9 +166,11 @@ def test_slri_long_sample_vectors(S, name, F, sub, rank, prec):
                                        ("td", {})])
 def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
     """The four tcgen05 variants (128x256 4-stage, 128x256 2-stage 4-box, 128x128, and for
-    the hi + lo precisions 128x256 with the hi and lo planes of one k-block per stage) give
-    the oracle's maps on ragged tiles; srp_plan_autotune times them and keeps one; a BF16
-    plan refuses the hi + lo variant."""
+    the hi + lo precisions 128x256 with the hi and lo planes of one k-block per stage), each
+    also in clusters of 2 CTAs sharing the B tiles by multicast, give the oracle's maps on
+    ragged tiles (70 frames: one frame tile, so the clusters also run a frame tile past F)
+    and the clustered maps equal the unclustered ones bit for bit; srp_plan_autotune times
+    them and keeps one; a BF16 plan refuses the hi + lo variants."""
     name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
     Lam = R.lam(name, F, sub)
@@ -176,20 +187,26 @@ def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
     plan = S.Plan(*args, method=method, precision="fp16x3", max_frames=64, **kw)
     if method == "sspi":  # Lambda masked by the plan's own (valid) selection
         zo = O.srp_sspi(np.where(_check_taps(plan, mask, perm, Lam), Lam, 0.0), xi_o)
-    for v in (0, 1, 2, 3, -1):
+    base = {}
+    for v in list(range(8)) + [-1]:
         plan.set_variant(v)
         z, am = _run(plan, w["frames"])
         plan.status()
         assert R.per_frame_rel(z, zo).max() <= TOL, v
         check_argmax(z, am, zo)
+        if 0 <= v < 4:
+            base[v] = (z, am)
+        elif v >= 4:  # the same kernel with shared B tiles: the same maps bit for bit
+            assert np.array_equal(z, base[v % 4][0]) and np.array_equal(am, base[v % 4][1]), v
     rep = plan.autotune(F=64)
-    assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 4
+    assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 8
     z, am = _run(plan, w["frames"])
     assert R.per_frame_rel(z, zo).max() <= TOL
     single = S.Plan(*args, method=method, precision="bf16", max_frames=64, **kw)
-    with pytest.raises(S.SrpError):
-        single.set_variant(3)
-    assert len(single.autotune(F=64)["ms"]) == 3
+    for v in (3, 7):
+        with pytest.raises(S.SrpError):
+            single.set_variant(v)
+    assert len(single.autotune(F=64)["ms"]) == 6
 
 
 @pytest.mark.parametrize("method,kw,prec,tol", [

@@ -108,6 +108,13 @@ def test_conv_tensor_core_square4(S, sq, prec, tol):
     zo = O.srp_conv(psi, dt, w["fs"])
     assert R.per_frame_rel(z, zo).max() <= tol
     check_argmax(z, am, zo)
+    if prec.endswith("x3"):  # the hi + lo per stage kernel (64-byte k-steps), alone and paired
+        for v in (3, 7):
+            plan.set_variant(v)
+            z, am = _run(plan, w["frames"])
+            plan.status()
+            assert R.per_frame_rel(z, zo).max() <= tol, v
+            check_argmax(z, am, zo)
 
 
 @pytest.mark.parametrize("rank", [8, 16])
@@ -333,6 +340,16 @@ def test_uca8_full_size_sampled(S, uca_full):
     plan.status()
     assert R.per_frame_rel(z[fsel], zo).max() <= TOL
     check_argmax(z[fsel], am[fsel], zo)
+    # the hi + lo per stage kernel alone and in clusters of 2 CTAs sharing the SRP matrix's
+    # tiles by multicast (16 frame tiles per cell tile): the same maps bit for bit
+    plan.set_variant(3)
+    z3, am3 = _run(plan, frames)
+    assert R.per_frame_rel(z3[fsel], zo).max() <= TOL
+    plan.set_variant(7)
+    zc, amc = _run(plan, frames)
+    plan.status()
+    assert np.array_equal(zc, z3) and np.array_equal(amc, am3)
+    del z3, zc
     # SLRI, R = 16
     tall, fat, s = R.slri("uca8", 16)
     z, am = _run(S.Plan(*args, method="slri", rank=16, max_frames=F), frames)
