@@ -347,122 +347,10 @@ cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N, c
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------------
-// Sampling by direct summation, for short lag windows (N_p <= NQ): the same samples as
-// the iFFT route, xi_p(n) = 2 sum_{k=1}^{K-1} Re[psi_p(k) e^{j pi k n / K}] (Eq.
-// xi_computed with the sampling matrix S_p of Eq. S_p), evaluated as
-//   xi_p(+-n) = 2 (C_n -+ S_n),  C_n = sum_k Re psi cos(pi k n/K),  S_n = sum_k Im psi sin(..)
-// One CTA per frame, one warp per pair (strided), lanes over bins.  e^{j pi k n / K} is
-// advanced by a rotation per lag and re-anchored from the twiddle table every 8 lags.
-// No barrier and no shared memory: a frame's y-hat (M*K*8 bytes) stays in L1.
-// ---------------------------------------------------------------------------------
-__device__ __forceinline__ float2 tw_pos(const float2* __restrict__ tw, int u, int K) {
-  // e^{+j pi u / K} for 0 <= u < 2K from tw[t] = e^{-j pi t / K}, t < K
-  const float2 w = __ldg(tw + (u < K ? u : u - K));
-  return u < K ? make_float2(w.x, -w.y) : make_float2(-w.x, w.y);
-}
-
-template <int NQ>
-__global__ __launch_bounds__(256, 2) void gcc_direct_kernel(const float2* __restrict__ yhat, int M,
-                                                         int P, int K, const int2* __restrict__ pairs,
-                                                         const int* __restrict__ Np,
-                                                         const int* __restrict__ off, int L,
-                                                         const float2* __restrict__ tw,
-                                                         float* __restrict__ xi) {
-  // G pairs per warp share the rotation e^{j pi k n / K} (it depends on (k, n) only)
-  constexpr int G = NQ <= 16 ? 2 : 1;
-  const int f = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const float2* yf = yhat + static_cast<size_t>(f) * M * K;
-  const int twoK = 2 * K;
-  for (int q0 = warp * G; q0 < P; q0 += nw * G) {
-    int nq[G], mA[G], mB[G];
-    int nqmax = 0;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const bool ok = q0 + g < P;
-      nq[g] = ok ? Np[q0 + g] : -1;
-      const int2 pr = ok ? pairs[q0 + g] : make_int2(0, 0);
-      mA[g] = pr.x * K;
-      mB[g] = pr.y * K;
-      nqmax = max(nqmax, nq[g]);
-    }
-    float c[G][NQ + 1], sn[G][NQ + 1];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-#pragma unroll
-      for (int n = 0; n <= NQ; ++n) c[g][n] = sn[g][n] = 0.f;
-    for (int k = 1 + lane; k < K; k += 32) {
-      float2 psi[G];
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        psi[g] = cmul_conj(__ldg(yf + mA[g] + k), __ldg(yf + mB[g] + k));
-        c[g][0] += psi[g].x;
-      }
-      const float2 step = tw_pos(tw, k, K);
-      float2 e = make_float2(1.f, 0.f);
-#pragma unroll
-      for (int n = 1; n <= NQ; ++n) {
-        if (n > nqmax) break;
-        if ((n & 7) == 0) {
-          e = tw_pos(tw, (k * n) & (twoK - 1), K);
-        } else {
-          e = cmul(e, step);
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          c[g][n] = fmaf(psi[g].x, e.x, c[g][n]);
-          sn[g][n] = fmaf(psi[g].y, e.y, sn[g][n]);
-        }
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-#pragma unroll
-      for (int n = 0; n <= NQ; ++n) {
-        if (n > nq[g]) break;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          c[g][n] += __shfl_xor_sync(0xFFFFFFFFu, c[g][n], o);
-          sn[g][n] += __shfl_xor_sync(0xFFFFFFFFu, sn[g][n], o);
-        }
-      }
-      if (nq[g] < 0) continue;
-      float* out = xi + static_cast<size_t>(f) * L + off[q0 + g] + nq[g];  // lag 0
-#pragma unroll
-      for (int n = 0; n <= NQ; ++n) {
-        if (n > nq[g]) break;
-        if (lane == n % 32) {
-          out[n] = 2.f * (c[g][n] - sn[g][n]);
-          if (n > 0) out[-n] = 2.f * (c[g][n] + sn[g][n]);
-        }
-      }
-    }
-  }
-}
-
+// Lag windows up to this N_p are sampled in the matrix form of Eq. xi_computed (the sampling
+// GEMM of the fused front end or of gcc_mma_kernel); wider ones by the iFFT.
 int gcc_direct_max_lag() { return 32; }
 
-cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
-                              const int* Np, const int* off, int L, int max_Np,
-                              const float2* twiddle, float* xi, cudaStream_t s) {
-  if (F <= 0) return cudaSuccess;
-  const int K = N / 2;
-  const int threads = P >= 8 ? 256 : 32 * P;
-#define SRP_GD(NQV)                                                                         \
-  gcc_direct_kernel<NQV><<<F, threads, 0, s>>>(yhat, M, P, K, pairs, Np, off, L, twiddle, xi)
-  if (max_Np <= 8) {
-    SRP_GD(8);
-  } else if (max_Np <= 16) {
-    SRP_GD(16);
-  } else if (max_Np <= 32) {
-    SRP_GD(32);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-#undef SRP_GD
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------------
 // Fused front end: one CTA per frame runs the STFT + PHAT of every channel (the
@@ -503,6 +391,199 @@ __device__ __forceinline__ void split_h2(float2 v, unsigned& hi, unsigned& lo) {
 // Rows of y-hat in shared memory are padded by 4 entries, so that the 8 rows a
 // fragment gathers at once fall into distinct bank groups.
 __host__ __device__ constexpr int front_row(int K) { return K + 4; }
+
+// ---------------------------------------------------------------------------------
+// Sampling for short lag windows (N_p <= 32) from y-hat in global memory, as the per-frame
+// GEMM of the fused front end's sampling (Eq. xi_p_ifft at the lags n = -N_p..N_p in the
+// matrix form of Eq. xi_computed: rows = pairs, K = bins with Re psi and Im psi
+// interleaved, columns = lags; B = front_sampling_table; FP16 hi + lo, three products on
+// the warp-level tensor cores, or the hi product alone for operands of 8 to 11 bits).  It
+// serves the frames the fused kernel cannot hold (N =
+// 2048, or many channels): one CTA per frame stages the spectra of all M channels and the
+// sampling table's fragments through shared memory 64 bins at a time, copied
+// asynchronously one chunk ahead (two buffers); in each round every warp owns MTW m-tiles
+// of 16 pairs and keeps their sums in registers across the chunks -- each k-step's three
+// products go into a fresh accumulator, which is then added in FP32 (round to nearest), so
+// that the tensor cores' truncating accumulation stays small -- and the samples are
+// written in the operand type, zero padded beyond L.
+// ---------------------------------------------------------------------------------
+constexpr int kMmaChunk = 64;                 // bins per staged chunk (8 k-steps)
+constexpr int kMmaRow = kMmaChunk + 4;        // padded row: 8 rows x 4 bins hit distinct banks
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<unsigned>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int NTM, bool X3>
+__global__ __launch_bounds__(256, NTM <= 4 ? 2 : 1) void gcc_mma_kernel(
+    const float2* __restrict__ yhat, int M, int P, int K, const int2* __restrict__ pairs,
+    const int* __restrict__ Np, const int* __restrict__ off, int L,
+    const uint4* __restrict__ stab, int NT, int nq0, int ot, void* out, void* out_lo,
+    int out_cols) {
+  constexpr int MTW = NTM <= 4 ? 4 : 2;  // m-tiles per warp and round (registers)
+  constexpr int KS = kMmaChunk / 8;      // k-steps per chunk
+  // two buffers, each [M][kMmaRow] spectra then [KS][NT][32] fragments of the table
+  extern __shared__ float2 ys[];
+  const int buf_f2 = M * kMmaRow + KS * NT * 32 * 2;  // one buffer in float2 units
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int MT = (P + 15) >> 4;
+  const int nch = K / kMmaChunk, nrounds = (MT + 8 * MTW - 1) / (8 * MTW);
+  const float2* yf = yhat + static_cast<size_t>(f) * M * K;
+  const size_t orow = static_cast<size_t>(f) * out_cols;
+  // stage i = (round, chunk): the chunk's spectra of every channel and its table fragments,
+  // copied asynchronously one stage ahead of the computation
+  auto stage = [&](int i) {
+    const int c0 = (i % nch) * kMmaChunk;
+    float2* yb = ys + (i & 1) * buf_f2;
+    uint4* bb = reinterpret_cast<uint4*>(yb + M * kMmaRow);
+    for (int e = tid; e < M * (kMmaChunk / 2); e += 256) {
+      const int m = e / (kMmaChunk / 2), j = e - m * (kMmaChunk / 2);
+      cp_async16(yb + m * kMmaRow + 2 * j, yf + static_cast<size_t>(m) * K + c0 + 2 * j);
+    }
+    const uint4* bsrc = stab + static_cast<size_t>(c0 >> 3) * NT * 32;
+    for (int e = tid; e < KS * NT * 32; e += 256) cp_async16(bb + e, bsrc + e);
+    cp_async_commit();
+  };
+  float sum[MTW][NTM][4];
+  int ch_a0[MTW], ch_b0[MTW], ch_a1[MTW], ch_b1[MTW];
+  const int total = nrounds * nch;
+  stage(0);
+  for (int i = 0; i < total; ++i) {
+    const int r0 = (i / nch) * 8 * MTW, c = i % nch;
+    if (c == 0) {
+#pragma unroll
+      for (int g = 0; g < MTW; ++g) {
+#pragma unroll
+        for (int t = 0; t < NTM; ++t)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) sum[g][t][e] = 0.f;
+        // the channels of this thread's two rows (pairs past P read pair 0; their samples
+        // are never written) as row offsets into a staged chunk
+        const int ra = (r0 + g * 8 + warp) * 16 + gq, rb = ra + 8;
+        const int2 pa = __ldg(pairs + (ra < P ? ra : 0)), pb = __ldg(pairs + (rb < P ? rb : 0));
+        ch_a0[g] = pa.x * kMmaRow;
+        ch_b0[g] = pa.y * kMmaRow;
+        ch_a1[g] = pb.x * kMmaRow;
+        ch_b1[g] = pb.y * kMmaRow;
+      }
+    }
+    if (i + 1 < total) {
+      stage(i + 1);        // its buffer was released by the barrier ending stage i - 1
+      cp_async_wait<1>();  // this thread's copies of stage i have landed
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();       // ... and every thread's
+    const float2* yb = ys + (i & 1) * buf_f2;
+    const uint4* bs = reinterpret_cast<const uint4*>(yb + M * kMmaRow);
+    // each k-step: the table fragments once, then for every m-tile of the warp its psi
+    // fragments and a fresh three-product chain, added into the FP32 sums (short dependent
+    // chains, the m-tiles independent of one another)
+#pragma unroll(NTM <= 4 ? 2 : 1)
+    for (int s = 0; s < KS; ++s) {
+      uint4 b[NTM];
+#pragma unroll
+      for (int t = 0; t < NTM; ++t)
+        if (t < NT) b[t] = bs[(s * NT + t) * 32 + lane];
+#pragma unroll
+      for (int g = 0; g < MTW; ++g) {
+        if (r0 + g * 8 + warp >= MT) continue;  // warp-uniform
+        const float2* q = yb + 8 * s + tq;
+        const float2 v[4] = {cmul_conj(q[ch_a0[g]], q[ch_b0[g]]), cmul_conj(q[ch_a1[g]], q[ch_b1[g]]),
+                             cmul_conj(q[ch_a0[g] + 4], q[ch_b0[g] + 4]),
+                             cmul_conj(q[ch_a1[g] + 4], q[ch_b1[g] + 4])};
+        unsigned ah[4], al[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (X3) {
+            split_h2(v[e], ah[e], al[e]);
+          } else {
+            const __half2 h = __floats2half2_rn(v[e].x, v[e].y);
+            ah[e] = *reinterpret_cast<const unsigned*>(&h);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < NTM; ++t) {
+          if (t < NT) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            if (X3) {
+              mma_16816(c, al, b[t].x, b[t].y);
+              mma_16816(c, ah, b[t].z, b[t].w);
+            }
+            mma_16816(c, ah, b[t].x, b[t].y);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sum[g][t][e] += c[e];
+          }
+        }
+      }
+    }
+    __syncthreads();  // stage i's buffer may be refilled (by stage i + 2)
+    if (c + 1 < nch) continue;
+    // the round is complete.  d fragments: (row gq, cols 2tq, 2tq+1) and (row gq + 8,
+    // same); column c is lag c - nq0
+#pragma unroll
+    for (int g = 0; g < MTW; ++g) {
+      if (r0 + g * 8 + warp >= MT) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = (r0 + g * 8 + warp) * 16 + gq + 8 * h;
+        if (r >= P) continue;
+        const int nq = __ldg(Np + r);
+        const size_t o = orow + __ldg(off + r) + nq;  // lag 0 of pair r
+#pragma unroll
+        for (int t = 0; t < NTM; ++t) {
+          if (t >= NT) continue;
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int n = t * 8 + 2 * tq + cc - nq0;
+            if (n >= -nq && n <= nq) put_op_rt(ot, out, out_lo, o + n, sum[g][t][2 * h + cc]);
+          }
+        }
+      }
+    }
+  }
+  for (int c = L + tid; c < out_cols; c += 256) put_op_rt(ot, out, out_lo, orow + c, 0.f);
+}
+
+size_t gcc_mma_smem_bytes(int M, int max_Np) {  // two stage buffers
+  return 2 * (sizeof(float2) * static_cast<size_t>(M) * kMmaRow +
+              sizeof(uint4) * (kMmaChunk / 8) * front_ntiles(max_Np) * 32);
+}
+
+bool gcc_mma_supported(int M, int N, int max_Np) {
+  return N >= 2 * kMmaChunk && (N / 2) % kMmaChunk == 0 && max_Np <= gcc_direct_max_lag() &&
+         gcc_mma_smem_bytes(M, max_Np) <= 200 * 1024;
+}
+
+cudaError_t launch_gcc_mma(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                           const int* Np, const int* off, int L, const uint4* stab, int max_Np,
+                           OpType t, void* out, void* out_lo, int out_cols, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  if (!gcc_mma_supported(M, N, max_Np) || out_cols < L) return cudaErrorInvalidValue;
+  const int NT = front_ntiles(max_Np), NTM = front_ntm(max_Np);
+  const size_t smem = gcc_mma_smem_bytes(M, max_Np);
+  // FP32-class operands (FP32 and the hi + lo types) sample with the three products of
+  // the hi + lo split (22 significant bits); single 16-bit and TF32 operands, which keep 8
+  // to 11 bits of each sample, with the one product of FP16 psi and table
+  const bool x3 = t == OpType::F32 || op_split(t);
+  void (*kern)(const float2*, int, int, int, const int2*, const int*, const int*, int,
+               const uint4*, int, int, int, void*, void*, int) =
+      x3 ? (NTM == 2 ? gcc_mma_kernel<2, true> : NTM == 4 ? gcc_mma_kernel<4, true> : gcc_mma_kernel<9, true>)
+         : (NTM == 2 ? gcc_mma_kernel<2, false> : NTM == 4 ? gcc_mma_kernel<4, false> : gcc_mma_kernel<9, false>);
+  cudaError_t e = allow_max_dynamic_smem(kern);
+  if (e != cudaSuccess) return e;
+  kern<<<F, 256, smem, s>>>(yhat, M, P, N / 2, pairs, Np, off, L, stab, NT, max_Np,
+                            static_cast<int>(t), out, out_lo, out_cols);
+  return cudaGetLastError();
+}
 
 // One CTA of 256 threads per frame; H = N/2 is the complex FFT length (= K), NTM bounds
 // the n-tiles of the sampling GEMM.
@@ -755,8 +836,7 @@ cudaError_t launch_front_group(const FrontParams* params, const int2* items, con
   SRP_FRONT_G(512, 2) SRP_FRONT_G(512, 4) SRP_FRONT_G(512, 9)
 #undef SRP_FRONT_G
   if (!kern || grid < 1) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = allow_max_dynamic_smem(kern);
   if (e != cudaSuccess) return e;
   kern<<<grid, 256, smem, s>>>(params, items, count);
   return cudaGetLastError();
@@ -904,8 +984,7 @@ static cudaError_t front_launch(const FrontParams& a, int F, int N, int NTM, siz
   SRP_FRONT(512, 2) SRP_FRONT(512, 4) SRP_FRONT(512, 9)
 #undef SRP_FRONT
   if (!kern) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = allow_max_dynamic_smem(kern);
   if (e != cudaSuccess) return e;
   kern<<<F, 256, smem, s>>>(a);
   return cudaGetLastError();

@@ -62,9 +62,7 @@ cudaError_t launch_slri_fat(const float* xi, const float* fat, float* U, int F, 
   const int grid = (F + fb - 1) / fb;
 #define SRP_FAT(FBV)                                                                         \
   case FBV: {                                                                                \
-    cudaError_t e = cudaFuncSetAttribute(slri_fat_kernel<FBV>,                               \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                                         static_cast<int>(smem));                            \
+    cudaError_t e = allow_max_dynamic_smem(slri_fat_kernel<FBV>);                            \
     if (e != cudaSuccess) return e;                                                          \
     slri_fat_kernel<FBV><<<grid, 256, smem, s>>>(xi, fat, U, F, L, R);                       \
     break;                                                                                   \
@@ -186,9 +184,7 @@ static cudaError_t run_tall_group(const GroupInterp* g, const int4* items, const
                                   int grid, cudaStream_t s) {
   const size_t smem = sizeof(float) * 64 * R + sizeof(unsigned long long) * 8 * 64;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(slri_tall_group_kernel<R, CPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_max_dynamic_smem(slri_tall_group_kernel<R, CPT>);
     if (e != cudaSuccess) return e;
   }
   slri_tall_group_kernel<R, CPT><<<grid, 256, smem, s>>>(g, items, count);
@@ -220,9 +216,7 @@ static cudaError_t run_tall(const float* U, const float* tall, float* Z, unsigne
   const size_t smem = sizeof(float) * FB * R + sizeof(unsigned long long) * 8 * FB;
   dim3 grid((J + 256 * CPT - 1) / (256 * CPT), (F + FB - 1) / FB);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(slri_tall_kernel<R, CPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_max_dynamic_smem(slri_tall_kernel<R, CPT>);
     if (e != cudaSuccess) return e;
   }
   slri_tall_kernel<R, CPT><<<grid, 256, smem, s>>>(U, tall, Z, keys, F, J, FB);
@@ -354,8 +348,7 @@ cudaError_t launch_sspi(const float* xi, const long long* row_ptr, const int2* t
     const int fx = (F + 63) / 64;
     int gy = (2 * num_sms * 4 + fx - 1) / fx;
     gy = max(1, min(gy, nrb));
-    cudaError_t e = cudaFuncSetAttribute(sspi_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_max_dynamic_smem(sspi_kernel<2>);
     if (e != cudaSuccess) return e;
     sspi_kernel<2><<<dim3(fx, gy), 256, smem, s>>>(xi, row_ptr, taps, Z, keys, F, J, L, nrb);
   } else if (sspi_smem<1>(L) <= lim1) {
@@ -363,8 +356,7 @@ cudaError_t launch_sspi(const float* xi, const long long* row_ptr, const int2* t
     const int fx = (F + 31) / 32;
     int gy = (num_sms * 4 + fx - 1) / fx;
     gy = max(1, min(gy, nrb));
-    cudaError_t e = cudaFuncSetAttribute(sspi_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_max_dynamic_smem(sspi_kernel<1>);
     if (e != cudaSuccess) return e;
     sspi_kernel<1><<<dim3(fx, gy), 256, smem, s>>>(xi, row_ptr, taps, Z, keys, F, J, L, nrb);
   } else {
@@ -481,14 +473,12 @@ cudaError_t launch_sspi_group(const GroupInterp* g, const int4* items, const int
   if (grid < 1 || !sspi_full_fits(Lmax)) return cudaErrorInvalidValue;
   if (sspi_group_frames(Lmax) == 64) {
     const size_t smem = sspi_smem<2>(Lmax);
-    cudaError_t e = cudaFuncSetAttribute(sspi_group_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_max_dynamic_smem(sspi_group_kernel<2>);
     if (e != cudaSuccess) return e;
     sspi_group_kernel<2><<<grid, 256, smem, s>>>(g, items, count);
   } else {
     const size_t smem = sspi_smem<1>(Lmax);
-    cudaError_t e = cudaFuncSetAttribute(sspi_group_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = allow_max_dynamic_smem(sspi_group_kernel<1>);
     if (e != cudaSuccess) return e;
     sspi_group_kernel<1><<<grid, 256, smem, s>>>(g, items, count);
   }
@@ -507,9 +497,7 @@ cudaError_t launch_sspi_band(const float* xi, const long long* row_ptr, const in
   const dim3 grid((F + FB - 1) / FB, nrb);
 #define SRP_BAND(FBV)                                                                        \
   case FBV: {                                                                                \
-    cudaError_t e = cudaFuncSetAttribute(sspi_band_kernel<FBV>,                              \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                                         static_cast<int>(smem));                            \
+    cudaError_t e = allow_max_dynamic_smem(sspi_band_kernel<FBV>);                           \
     if (e != cudaSuccess) return e;                                                          \
     sspi_band_kernel<FBV><<<grid, 256, smem, s>>>(xi, row_ptr, taps, blk_ptr, blk_cols, Z,   \
                                                   keys, F, J, L);                            \

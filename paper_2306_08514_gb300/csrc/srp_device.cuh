@@ -24,6 +24,24 @@ __device__ __forceinline__ unsigned long long argmax_key(float v, int i) {
          static_cast<unsigned long long>(0xFFFFFFFFu - static_cast<unsigned>(i));
 }
 
+// Lets `kern` launch with up to the device's opt-in maximum of dynamic shared memory.  The
+// value set is the same for every launch, so that host threads launching the kernel with
+// different sizes at the same time (plans used concurrently) cannot undo each other's
+// setting between the call and the launch.
+template <typename Kernel>
+inline cudaError_t allow_max_dynamic_smem(Kernel kern) {
+  int dev = 0, most = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&most, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);  // the kernel's static shared memory counts too
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              most - static_cast<int>(fa.sharedSizeBytes));
+}
+
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -116,11 +116,15 @@ cudaError_t launch_gcc_samples(const float2* yhat, int F, int M, int P, int N,
                                const int2* pairs, const int* Np, const int* off, int L,
                                const float2* twiddle, OpType t, void* out, void* out_lo,
                                int out_cols, cudaStream_t s);
-// The same samples by direct summation over the bins (N_p <= gcc_direct_max_lag()).
+// Lag windows up to this N_p are sampled in the matrix form of Eq. xi_computed.
 int gcc_direct_max_lag();
-cudaError_t launch_gcc_direct(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
-                              const int* Np, const int* off, int L, int max_Np,
-                              const float2* twiddle, float* xi, cudaStream_t s);
+// The same samples (N_p <= gcc_direct_max_lag()) as a per-frame GEMM on the warp-level
+// tensor cores from y-hat [F][M][N/2] in global memory, written in operand type t into
+// out [F][out_cols] (zero padded beyond L); stab = front_sampling_table(N, max_Np).
+bool gcc_mma_supported(int M, int N, int max_Np);
+cudaError_t launch_gcc_mma(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                           const int* Np, const int* off, int L, const uint4* stab, int max_Np,
+                           OpType t, void* out, void* out_lo, int out_cols, cudaStream_t s);
 // Frames from consecutive hops [B][M][hop] and the history [M][N - hop] (streaming front).
 cudaError_t launch_stream_frames(const float* hops, int B, int M, int hop, int N,
                                  const float* hist_in, float* frames, float* hist_out,
@@ -346,6 +350,7 @@ struct srp_plan_s {
   int max_Np = 0;     // largest N_p over the pairs
   int tc_variant = -1;     // tensor-core kernel variant chosen by srp_plan_autotune (-1: heuristic)
   bool use_front = false;  // interpolation methods: one fused front-end launch per chunk
+  bool use_mma_sampling = false;  // otherwise, short lag windows: sampling by gcc_mma
   bool fat_gemm = false;   // SLRI with long sample vectors: u = Lambda_fat xi as a GEMM
   bool h_generated = false;  // conv FP32: SRP matrix generated inside the GEMM, not stored
   int h_slices = 0;          //   slices of each chunk's reduction (d_split holds the partials)
@@ -393,7 +398,7 @@ struct srp_plan_s {
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
   bool use_front_conv = false;  // conv / LR operand from the fused front kernel
   bool stall_next = false;  // srp_debug_stall_next_contraction
-  uint4* d_stab = nullptr;  // fused front end: the sampling operand (front_sampling_table)
+  uint4* d_stab = nullptr;  // fused front end or gcc_mma: the sampling operand (front_sampling_table)
   uint4* d_ftab = nullptr;  // fused front end, SLRI: Lambda_fat (front_fat_table)
   // staging for srp_map_host, and its copy pipeline (two D2H streams and one H2D stream;
   // events recycled round-robin to order them against the compute stream)

@@ -52,8 +52,9 @@ def check_argmax(z, am, zo):
                                     (2048, 1.5)])
 def test_gcc_samples_match_oracle(S, N, half):
     """Eq. xi_p_ifft / n_prime on the GPU vs the oracle's iFFT sampling.  Square arrays of
-    half-side `half` give max N_p of 4 (0.02), 15 (0.1), 28 (0.2) -- direct summation with 8,
-    16 and 32 lag registers -- and 135 / 201 (1.0 / 1.5): the iFFT kernel."""
+    half-side `half` give max N_p of 4 (0.02), 15 (0.1), 28 (0.2) -- the sampling GEMM with
+    2, 4 and 9 n-tiles of lags (in the fused front end for N <= 1024, from spectra in global
+    memory for N = 2048) -- and 135 / 201 (1.0 / 1.5): the iFFT kernel."""
     mics = synth.mics_square(half=half)
     grid = synth.grid_plane((1, 1), (3, 3), (8, 8))
     g = synth.rng(N)
@@ -68,6 +69,38 @@ def test_gcc_samples_match_oracle(S, N, half):
     ref = R.xi_ascending(R.psi_of(frames), lags, O.lags_to_ascending(lags), N // 2)
     scale = np.max(np.abs(ref), axis=1, keepdims=True)
     assert np.max(np.abs(xi - ref) / scale) <= TOL
+
+
+@pytest.mark.parametrize("N,M,diam,prec", [(2048, 40, 0.1, "fp32"), (2048, 40, 0.25, "fp16x3"),
+                                           (2048, 40, 0.6, "fp32"), (1024, 40, 0.25, "bf16"),
+                                           (256, 48, 0.6, "fp32")])
+def test_gcc_samples_many_channels_short_windows(S, N, M, diam, prec):
+    """Sampling GEMM from spectra in global memory (frames the fused front end cannot hold:
+    N = 2048, or 40-48 channels): 780-1128 pairs (two or more rounds of m-tiles per frame),
+    max N_p in each n-tile bucket (15, 31 and 65 lags), against the oracle's iFFT sampling
+    (Eq. xi_p_ifft / n_prime).  Bounds: the FP32 1e-5 on each frame's samples as a whole
+    (sqrt(sum err^2 / sum xi^2), the measure of the maps); sample by sample 5e-5 of the
+    frame's largest sample, because with 10^5-10^6 samples per test the largest single
+    error comes from PHAT's division at the weakest bin of a frame (FP32 spectra: a bin
+    10^3 below the frame's typical magnitude turns a 1e-7 rounding into a 1e-4 phase
+    error), whatever the sampling kernel."""
+    g = synth.rng(N + M)
+    v = g.standard_normal((M, 3))
+    mics = (2.0, 2.0, 1.0) + 0.5 * diam * v / np.linalg.norm(v, axis=1, keepdims=True)
+    grid = synth.grid_plane((1, 1), (3, 3), (8, 8))
+    frames = g.standard_normal((37, M, N)).astype(np.float32)
+    plan = S.Plan(mics, grid, 16000.0, N, method="si", precision=prec, max_frames=16)
+    import torch
+    xi = plan.gcc_samples(_cuda(frames)).cpu().numpy()
+    torch.cuda.synchronize()
+    Np = O.n_p_samples(mics, 16000.0)
+    assert np.array_equal(plan.lags(), Np)
+    assert Np.max() <= 32
+    lags = O.pair_lags(Np)
+    ref = R.xi_ascending(R.psi_of(frames), lags, O.lags_to_ascending(lags), N // 2)
+    assert R.per_frame_rel(xi, ref).max() <= TOL
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    assert np.max(np.abs(xi - ref) / scale) <= 5 * TOL
 
 
 # ------------------------------------------------------------------ square4 (full size)
@@ -108,7 +141,7 @@ def test_conv_tensor_core_square4(S, sq, prec, tol):
     zo = O.srp_conv(psi, dt, w["fs"])
     assert R.per_frame_rel(z, zo).max() <= tol
     check_argmax(z, am, zo)
-    if prec.endswith("x3"):  # the hi + lo per stage kernel (64-byte k-steps), alone and paired
+    if prec.endswith("x3"):  # the hi + lo per stage kernel, alone and in clusters of two
         for v in (3, 7):
             plan.set_variant(v)
             z, am = _run(plan, w["frames"])
