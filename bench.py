@@ -64,6 +64,8 @@ def parse(argv=None):
     ap.add_argument("--argmax-frames", type=int, default=1024,
                     help="frames whose argmax is compared with the FP64 oracle's")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--clock-ms", type=int, default=20,
+                    help="nvidia-smi sampling interval during the timed region (0: no sampling)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the tensor-core kernel variant of every plan (0..3, as srp_plan_autotune)")
@@ -97,21 +99,25 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, interval_ms=20):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         self.proc = None
         self.index = index
+        self.interval_ms = interval_ms
 
     def start(self):
-        """Starts the sampler (every 20 ms) and returns once it has written its first sample
+        """Starts the sampler (every interval_ms) and returns once it has written its first sample
         (nvidia-smi takes a while to start), so that the timed region that follows is
         sampled from its beginning; mark() then sets where the timed region's samples begin."""
         self.n0 = 0
+        if self.interval_ms <= 0:
+            return
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                          "--format=csv,noheader,nounits", "-lms",
+                                          str(self.interval_ms)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -672,7 +678,7 @@ def run_libsrp(a):
         plans[m].status()
         plans[m].set_profiling(True)
     launches0 = {m: plans[m].info_now().launches for m in methods}
-    clocks = Clocks(local)
+    clocks = Clocks(local, a.clock_ms)
     if rank == 0:
         clocks.start()
     if world > 1:

@@ -282,26 +282,29 @@ srp_status srp_gcc_samples(srp_plan_t plan, const float* frames, int F, float* x
  * operands for one k-block and issue its three products in turn (each operand tile loaded
  * once instead of twice; variant 3); variants 4..7 are variants 0..3 run in clusters of
  * 2 CTAs that take two frame tiles of one cell tile together and share each tile of the
- * SRP / interpolation operand by TMA multicast (each CTA loads half of it; the maps are
- * the same bit for bit).  Each variant runs the whole
+ * SRP / interpolation operand by TMA multicast (each CTA loads half of it), and variants
+ * 8..11 in clusters of 2 x 2 that also share each tile of the frame operand between two
+ * cell tiles (dense reductions; block-sparse ones run as 4..7); the maps are the same bit
+ * for bit.  Each variant runs the whole
  * srp_map path 2 + 5 times on F frames of a synthetic input (plan-owned temporary
  * buffers); the fastest is kept by the plan for later calls.  Until a plan is tuned a
- * heuristic picks by reduction length.  FP32 plans have nothing to tune (variant -1).
+ * heuristic picks by reduction length (and clusters of two from two frame tiles on).
+ * FP32 plans have nothing to tune (variant -1).
  * F: 1..max_frames, the batch size the plan will serve.  Synchronises `stream`.
  * report: host, written (or NULL): the chosen variant and the mean milliseconds per
  * srp_map call of every variant (-1 where not run).  Errors: SRP_EINVAL, SRP_ENOMEM,
  * SRP_ECUDA.
  */
-enum { SRP_TUNE_MAX = 8 };
+enum { SRP_TUNE_MAX = 12 };
 typedef struct {
   int variant;
   float ms[SRP_TUNE_MAX];
 } srp_tune_report_t;
 srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream, srp_tune_report_t* report);
 
-/* srp_plan_set_variant -- pin the tensor-core variant (0..7 as in srp_plan_autotune) or
+/* srp_plan_set_variant -- pin the tensor-core variant (0..11 as in srp_plan_autotune) or
  * return to the heuristic (-1).  Errors: SRP_EINVAL (out of range, an FP32 plan, or
- * variant 3 or 7 without a hi + lo precision). */
+ * variant 3, 7 or 11 without a hi + lo precision). */
 srp_status srp_plan_set_variant(srp_plan_t plan, int variant);
 
 /*

@@ -67,13 +67,15 @@ SESSION_STATES = {0: "queued", 1: "active", 2: "closing", 3: "closed", 4: "faile
 
 
 class srp_tune_report_t(C.Structure):
-    _fields_ = [("variant", C.c_int), ("ms", C.c_float * 8)]
+    _fields_ = [("variant", C.c_int), ("ms", C.c_float * 12)]
 
 
 _TUNE_BASE = {0: "128x256 4-stage", 1: "128x256 2-stage 4-box", 2: "128x128 4-stage",
               3: "128x256 hi+lo per stage"}
-# variants 4..7: variants 0..3 in clusters of 2 CTAs sharing the B tiles
-TUNE_VARIANTS = {-1: "fp32", **_TUNE_BASE, **{v + 4: name + " cluster 2" for v, name in _TUNE_BASE.items()}}
+# variants 4..7 / 8..11: variants 0..3 in clusters of 2 CTAs sharing the B tiles / of 2 x 2
+# sharing the B and the A tiles
+TUNE_VARIANTS = {-1: "fp32", **_TUNE_BASE, **{v + 4: name + " cluster 2" for v, name in _TUNE_BASE.items()},
+                 **{v + 8: name + " cluster 2x2" for v, name in _TUNE_BASE.items()}}
 
 # every symbol include/libsrp.h declares, with (restype, argtypes)
 SIGNATURES = {
@@ -354,7 +356,7 @@ class Plan:
         F = int(F or self.desc.max_frames)
         _check(lib().srp_plan_autotune(self.handle, F, _stream_handle(stream), C.byref(rep)))
         return {"variant": TUNE_VARIANTS.get(rep.variant, rep.variant),
-                "ms": {TUNE_VARIANTS[v]: rep.ms[v] for v in range(8) if rep.ms[v] >= 0}}
+                "ms": {TUNE_VARIANTS[v]: rep.ms[v] for v in range(12) if rep.ms[v] >= 0}}
 
     def set_variant(self, variant):
         _check(lib().srp_plan_set_variant(self.handle, int(variant)))

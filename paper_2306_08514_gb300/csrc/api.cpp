@@ -1575,11 +1575,11 @@ extern "C" srp_status srp_plan_autotune(srp_plan_t plan, int F, void* stream,
 extern "C" srp_status srp_plan_set_variant(srp_plan_t plan, int variant) {
   clear_error();
   if (!plan) return fail(SRP_EINVAL, "plan is NULL");
-  if (variant < -1 || variant >= TC_NVARIANTS) return fail(SRP_EINVAL, "variant must be in -1..7");
+  if (variant < -1 || variant >= TC_NVARIANTS) return fail(SRP_EINVAL, "variant must be in -1..11");
   if (plan->op == OpType::F32 && variant != -1)
     return fail(SRP_EINVAL, "FP32 plans have no tensor-core variant");
   if (variant >= 0 && !tc_gemm_variant_valid(variant, plan->op))
-    return fail(SRP_EINVAL, "variants 3 and 7 (hi and lo planes per stage) need a hi + lo precision");
+    return fail(SRP_EINVAL, "variants 3, 7 and 11 (hi and lo planes per stage) need a hi + lo precision");
   plan->tc_variant = variant;
   return SRP_OK;
 }

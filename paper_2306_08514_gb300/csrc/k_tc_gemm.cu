@@ -33,11 +33,14 @@
 // together, CTA r of the cluster loads rows [r TN/2, (r+1) TN/2) of each B tile and
 // multicasts them into the same stage of both CTAs, and each CTA's MMA issuer frees a
 // stage in both (a stage is refilled once both CTAs have consumed it), so each B tile
-// crosses L2 once per pair of frame tiles.  A frame tile past F (odd tile counts)
-// computes on zero rows and writes nothing.  (Clusters of 4 measured slower: with one
-// CTA per SM fewer of the GPCs' SMs can host whole clusters.)  When the output tiles are
-// too few to fill the GPU the (dense) reduction is also split into slices written to a
-// workspace and summed in FP64 (split_reduce in k_conv_simt.cu).  Every
+// crosses L2 once per pair of frame tiles.  Clusters of 2 x 2 (dense reductions) add the
+// other direction: the two cell tiles of a cluster share each A tile the same way, so that
+// both operands cross L2 once per two tiles (long reductions over operands far larger
+// than L2, where the CTAs sharing a tile would otherwise drift apart and re-read it from
+// DRAM).  A tile past F or J computes on zero rows and writes nothing; a single frame tile
+// runs unclustered.  When the output tiles are too few to
+// fill the GPU, or the reduction is long, the (dense) reduction is also split into slices
+// written to a workspace and summed in FP64 (split_reduce in k_conv_simt.cu).  Every
 // mbarrier wait is bounded (2 s); on a timeout the CTA records an error code, drains its
 // own copies and MMAs, frees its TMEM and returns.
 #include "srp_internal.h"
@@ -109,22 +112,33 @@ struct TileWork {
   int slice, m, n, s0, s1, m_len, list;
 };
 
-// Tile t of a cluster of CS CTAs (t counts groups of CS frame tiles), as seen by the CTA
-// of cluster rank crank; CS = 1 is the plain m-fastest walk.
+// Clusters of CS CTAs: CM frame tiles x CN cell tiles (CS = 1: 1 x 1, 2: 2 x 1, 4: 2 x 2);
+// cluster rank r is (rm, rn) = (r mod CM, r / CM).
+template <int CS>
+struct ClusterShape {
+  static constexpr int CM = CS == 1 ? 1 : 2;
+  static constexpr int CN = CS == 4 ? 2 : 1;
+};
+
+// Tile t of a cluster (t counts groups of CM x CN tiles), as seen by the CTA (rm, rn); CS = 1
+// is the plain m-fastest walk.
 template <int CS>
 __device__ __forceinline__ int tile_groups(const TcParams& p) {
-  return (p.nM + CS - 1) / CS * p.nN * p.nslices;
+  constexpr int CM = ClusterShape<CS>::CM, CN = ClusterShape<CS>::CN;
+  return (p.nM + CM - 1) / CM * ((p.nN + CN - 1) / CN) * p.nslices;
 }
 
 template <int CS>
-__device__ __forceinline__ TileWork tile_work(const TcParams& p, int t, int crank) {
+__device__ __forceinline__ TileWork tile_work(const TcParams& p, int t, int rm, int rn) {
+  constexpr int CM = ClusterShape<CS>::CM, CN = ClusterShape<CS>::CN;
   TileWork w;
-  const int nMg = (p.nM + CS - 1) / CS;
-  const int per_slice = nMg * p.nN;
+  const int nMg = (p.nM + CM - 1) / CM;
+  const int per_slice = nMg * ((p.nN + CN - 1) / CN);
   w.slice = t / per_slice;
   const int rem = t - w.slice * per_slice;
-  w.n = rem / nMg;
-  w.m = (rem - w.n * nMg) * CS + crank;
+  const int ng = rem / nMg;
+  w.n = ng * CN + rn;
+  w.m = (rem - ng * nMg) * CM + rm;
   w.list = p.kb_ptr ? (w.n * p.tn) / LIST_TILE : 0;
   w.m_len = p.kb_ptr ? (__ldg(p.kb_ptr + w.list + 1) - __ldg(p.kb_ptr + w.list)) << p.sub_shift
                      : p.kb_per_seg;
@@ -147,11 +161,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int CHUNK = FUSED ? KB_PER_CHUNK_FUSED : KB_PER_CHUNK;
   constexpr int EPI_COLS = TN / 2;           // columns per epilogue thread
   constexpr uint32_t TMEM_COLS = 2 * TN;     // two accumulators
-  constexpr int B_SLICE_ROWS = TN / CS;      // rows of a B tile this CTA loads (and multicasts)
+  // clusters: CTA (rm, rn) loads rows [rm TN/CM, (rm+1) TN/CM) of its B tile for the CM
+  // CTAs of its cell tile and rows [rn TM/CN, (rn+1) TM/CN) of its A tile for the CN CTAs
+  // of its frame tile, each multicast into the same stage of those CTAs
+  constexpr int CM = ClusterShape<CS>::CM, CN = ClusterShape<CS>::CN;
+  constexpr int B_SLICE_ROWS = TN / CM;
   constexpr uint32_t B_SLICE_BYTES = B_SLICE_ROWS * TK * 2;
+  constexpr int A_SLICE_ROWS = TM / CN;
+  constexpr uint32_t A_SLICE_BYTES = A_SLICE_ROWS * TK * 2;
   constexpr uint16_t CMASK = static_cast<uint16_t>((1u << CS) - 1u);
-  static_assert(CS == 1 || CS == 2, "cluster size");
-  static_assert(B_SLICE_BYTES % 1024 == 0, "B slices must keep the 1024-byte swizzle atom");
+  static_assert(CS == 1 || CS == 2 || CS == 4, "cluster size");
+  static_assert(B_SLICE_BYTES % 1024 == 0 && A_SLICE_BYTES % 1024 == 0,
+                "slices must keep the 1024-byte swizzle atom");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // stage s: A planes at sA + s * NPL * A_BYTES, B planes at sB + s * NPL * B_BYTES
@@ -195,6 +216,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
   const int total = tile_groups<CS>(p);
   const int crank = CS > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+  const int rm = crank % CM, rn = crank / CM;
+  // the CTAs sharing this CTA's B tile (same rn) and A tile (same rm)
+  const uint16_t mask_b = static_cast<uint16_t>(((1u << CM) - 1u) << (rn * CM));
+  uint16_t mask_a = 0;
+#pragma unroll
+  for (int j = 0; j < CN; ++j) mask_a |= static_cast<uint16_t>(1u << (rm + CM * j));
   const int tile0 = CS > 1 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
   const int tstep = CS > 1 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
 
@@ -214,7 +241,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // p.stall (failure-detection test): no load is issued, so the MMA issuer's and the
       // epilogue's bounded waits run out and the CTA records the timeout
       for (int t = tile0; t < total && ok && !p.stall; t += tstep) {
-        const TileWork w = tile_work<CS>(p, t, crank);
+        const TileWork w = tile_work<CS>(p, t, rm, rn);
         const int* list = p.kb_ptr ? p.kb_idx + __ldg(p.kb_ptr + w.list) : nullptr;
         for (int s = w.s0; s < w.s1; ++s) {
           const int seg = s / w.m_len;
@@ -231,13 +258,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mbar_arrive_expect_tx(full_bar(stage), STAGE_BYTES);
           if constexpr (FUSED) {
             const uint32_t a = sA + stage * 2 * A_BYTES, b = sB + stage * 2 * B_BYTES;
-            tma_load_2d(a, &tmA0, kx, w.m * TM, full_bar(stage));
-            tma_load_2d(a + A_BYTES, &tmA1, kx, w.m * TM, full_bar(stage));
-            if constexpr (CS > 1) {
-              const uint32_t bs = b + crank * B_SLICE_BYTES;
-              const int y = w.n * TN + crank * B_SLICE_ROWS;
-              tma_load_2d_mc(bs, &tmB0, kx, y, full_bar(stage), CMASK);
-              tma_load_2d_mc(bs + B_BYTES, &tmB1, kx, y, full_bar(stage), CMASK);
+            if constexpr (CN > 1) {
+              const uint32_t as = a + rn * A_SLICE_BYTES;
+              const int y = w.m * TM + rn * A_SLICE_ROWS;
+              tma_load_2d_mc(as, &tmA0, kx, y, full_bar(stage), mask_a);
+              tma_load_2d_mc(as + A_BYTES, &tmA1, kx, y, full_bar(stage), mask_a);
+            } else {
+              tma_load_2d(a, &tmA0, kx, w.m * TM, full_bar(stage));
+              tma_load_2d(a + A_BYTES, &tmA1, kx, w.m * TM, full_bar(stage));
+            }
+            if constexpr (CM > 1) {
+              const uint32_t bs = b + rm * B_SLICE_BYTES;
+              const int y = w.n * TN + rm * B_SLICE_ROWS;
+              tma_load_2d_mc(bs, &tmB0, kx, y, full_bar(stage), mask_b);
+              tma_load_2d_mc(bs + B_BYTES, &tmB1, kx, y, full_bar(stage), mask_b);
             } else {
               tma_load_2d(b, &tmB0, kx, w.n * TN, full_bar(stage));
               tma_load_2d(b + B_BYTES, &tmB1, kx, w.n * TN, full_bar(stage));
@@ -245,10 +279,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           } else {
             const CUtensorMap* ta = seg == 2 ? &tmA1 : &tmA0;
             const CUtensorMap* tb = seg == 1 ? &tmB1 : &tmB0;
-            tma_load_2d(sA + stage * A_BYTES, ta, kx, w.m * TM, full_bar(stage));
-            if constexpr (CS > 1)
-              tma_load_2d_mc(sB + stage * B_BYTES + crank * B_SLICE_BYTES, tb, kx,
-                             w.n * TN + crank * B_SLICE_ROWS, full_bar(stage), CMASK);
+            if constexpr (CN > 1)
+              tma_load_2d_mc(sA + stage * A_BYTES + rn * A_SLICE_BYTES, ta, kx,
+                             w.m * TM + rn * A_SLICE_ROWS, full_bar(stage), mask_a);
+            else
+              tma_load_2d(sA + stage * A_BYTES, ta, kx, w.m * TM, full_bar(stage));
+            if constexpr (CM > 1)
+              tma_load_2d_mc(sB + stage * B_BYTES + rm * B_SLICE_BYTES, tb, kx,
+                             w.n * TN + rm * B_SLICE_ROWS, full_bar(stage), mask_b);
             else
               tma_load_2d(sB + stage * B_BYTES, tb, kx, w.n * TN, full_bar(stage));
           }
@@ -276,7 +314,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       int gc = 0;  // chunks issued by this CTA (selects the accumulator and its phase)
       for (int t = tile0; t < total && ok; t += tstep) {
-        const TileWork w = tile_work<CS>(p, t, crank);
+        const TileWork w = tile_work<CS>(p, t, rm, rn);
         for (int c0 = w.s0; c0 < w.s1 && ok; c0 += CHUNK, ++gc) {
           const int acc = gc & 1;
           const uint32_t aph = static_cast<uint32_t>((gc >> 1) & 1);
@@ -344,7 +382,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int gc = 0;
     bool ok = true;
     for (int t = tile0; t < total && ok; t += tstep) {
-      const TileWork w = tile_work<CS>(p, t, crank);
+      const TileWork w = tile_work<CS>(p, t, rm, rn);
       float sum[EPI_COLS];
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) sum[j] = 0.f;
@@ -596,7 +634,7 @@ cudaError_t launch_variant(int ctas, const CUtensorMap& mA0, const CUtensorMap& 
 
 template <int CS>
 cudaError_t prepare_cs() {
-  constexpr int c = CS == 1 ? 0 : 1;
+  constexpr int c = CS == 1 ? 0 : CS == 2 ? 1 : 2;
   cudaError_t e;
   if ((e = query_clusters<4, 1, 256, false, CS>(TC_LONG_256 + TC_NBASE * c)) != cudaSuccess) return e;
   if ((e = query_clusters<2, 4, 256, false, CS>(TC_SHORT_256 + TC_NBASE * c)) != cudaSuccess) return e;
@@ -621,13 +659,16 @@ cudaError_t launch_base(int base, int ctas, const CUtensorMap& mA0, const CUtens
 }
 }  // namespace
 
-int tc_gemm_cluster_size(int variant) { return variant >= TC_NBASE ? 2 : 1; }
+int tc_gemm_cluster_size(int variant) {
+  return variant >= 2 * TC_NBASE ? 4 : variant >= TC_NBASE ? 2 : 1;
+}
 
 cudaError_t tc_gemm_prepare() {
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
   if ((e = prepare_cs<1>()) != cudaSuccess) return e;
-  return prepare_cs<2>();
+  if ((e = prepare_cs<2>()) != cudaSuccess) return e;
+  return prepare_cs<4>();
 }
 
 bool tc_gemm_variant_valid(int variant, OpType t) {
@@ -638,9 +679,21 @@ bool tc_gemm_variant_valid(int variant, OpType t) {
 int tc_gemm_cell_tile() { return LIST_TILE; }
 int tc_gemm_k_block() { return TK; }
 
-int tc_gemm_default_variant(int Kd, OpType t) {
+int tc_gemm_default_variant(int Kd, OpType t, int F) {
   const int steps = ksteps_of(Kd, t);
-  return steps <= SHORT_MAX_STEPS ? TC_SHORT_256 : TC_LONG_256;
+  const bool split = op_split(t);
+  // short reductions: 2 stages and 4 output boxes; long ones: 4 stages, or for the hi + lo
+  // precisions both planes per stage (uca8 conv 6.01 against 6.06 ms, walls16 32.3 / 36.0)
+  const int base = steps <= SHORT_MAX_STEPS ? TC_SHORT_256 : split ? TC_FUSED3_256 : TC_LONG_256;
+  if (F < 2 * TM) return base;  // one frame tile: nothing to pair
+  // frame operands far beyond L2 (nested32 conv: 2 GB) are re-read from DRAM by every cell
+  // tile's CTAs unless clusters share them: 2 x 2 (BF16 1131 -> 720 ms, FP16 hi+lo 2989 ->
+  // 1397 ms); otherwise clusters of two for the hi + lo and the short reductions (uca8 conv
+  // 6.01 -> 5.89 ms, SLRI 0.148 -> 0.147), none for long single-plane ones (walls16 BF16
+  // conv 10.48 alone, 10.72 in pairs)
+  const double a_bytes = static_cast<double>(F) * Kd * op_bytes(t) * (split ? 2 : 1);
+  if (steps > SHORT_MAX_STEPS && a_bytes >= 1e9) return base + 2 * TC_NBASE;
+  return (split || steps <= SHORT_MAX_STEPS) ? base + TC_NBASE : base;
 }
 
 cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
@@ -648,7 +701,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   if (g.Kd % TK != 0 || g.Kd <= 0) return cudaErrorInvalidValue;
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
-  const int variant = g.variant >= 0 ? g.variant : tc_gemm_default_variant(g.Kd, g.t);
+  const int variant = g.variant >= 0 ? g.variant : tc_gemm_default_variant(g.Kd, g.t, g.F);
   if (!tc_gemm_variant_valid(variant, g.t)) return cudaErrorInvalidValue;
   const int base = variant % TC_NBASE;
   const bool fused = base == TC_FUSED3_256;
@@ -678,17 +731,22 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
   p.nslices = (g.kb_ptr || g.no_split) ? 1
               : g.force_slices > 0 ? g.force_slices
                                    : slices_for(g.F, g.J, g.Kd, g.t, num_sms, tn);
-  // clusters share the B tiles of the frame tiles of one cell tile; a split reduction (too
-  // few output tiles to fill the GPU) runs unclustered
-  int cs = p.nslices > 1 ? 1 : tc_gemm_cluster_size(variant);
-  const int max_cl = cs > 1 ? max_clusters(base + TC_NBASE) : 0;
+  // clusters share the B tiles of the frame tiles of one cell tile (and, 2 x 2, the A tiles
+  // of the cell tiles of one frame tile: dense reductions only, whose k-steps are the same
+  // for every cell tile); a single frame tile runs unclustered (its partner would only
+  // compute zero rows), a single cell tile or a block-sparse reduction in clusters of 2 x 1
+  int cs = p.nM < 2 ? 1 : tc_gemm_cluster_size(variant);
+  if (cs == 4 && (g.kb_ptr || p.nN < 2)) cs = 2;
+  const int max_cl = cs > 1 ? max_clusters(base + TC_NBASE * (cs == 2 ? 1 : 2)) : 0;
   if (cs > 1 && max_cl < 1) return cudaErrorNotReady;  // tc_gemm_prepare() did not run here
   CUtensorMap mA0, mA1, mB0, mB1, mZ;
-  const uint32_t b_rows = static_cast<uint32_t>(tn / cs);  // each CTA loads its slice of B
-  if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
+  // each CTA loads its slice of B (1/CM of the rows) and of A (1/CN)
+  const uint32_t b_rows = static_cast<uint32_t>(tn / (cs == 1 ? 1 : 2));
+  const uint32_t a_rows = static_cast<uint32_t>(TM / (cs == 4 ? 2 : 1));
+  if ((e = make_operand_map(&mA0, g.A, dt, g.Kd, g.F, a_rows, eb)) != cudaSuccess) return e;
   if ((e = make_operand_map(&mB0, g.B, dt, g.Kd, g.J, b_rows, eb)) != cudaSuccess) return e;
   if (split3) {
-    if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, TM, eb)) != cudaSuccess) return e;
+    if ((e = make_operand_map(&mA1, g.A_lo, dt, g.Kd, g.F, a_rows, eb)) != cudaSuccess) return e;
     if ((e = make_operand_map(&mB1, g.B_lo, dt, g.Kd, g.J, b_rows, eb)) != cudaSuccess) return e;
   } else {
     mA1 = mA0;
@@ -727,10 +785,12 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s) {
     e = launch_base<1>(base, grid, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
   } else {
     // persistent clusters: no more than can be resident at once, nor than tile groups
-    const int groups = (p.nM + cs - 1) / cs * p.nN;
+    const int cm = 2, cn = cs == 4 ? 2 : 1;
+    const int groups = (p.nM + cm - 1) / cm * ((p.nN + cn - 1) / cn) * p.nslices;
     int ncl = groups < max_cl ? groups : max_cl;
     if (g.max_ctas > 0 && ncl > g.max_ctas / cs) ncl = g.max_ctas / cs > 0 ? g.max_ctas / cs : 1;
-    e = launch_base<2>(base, ncl * cs, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
+    e = cs == 2 ? launch_base<2>(base, ncl * cs, mA0, mA1, mB0, mB1, mZ, p, idesc, s)
+                : launch_base<4>(base, ncl * cs, mA0, mA1, mB0, mB1, mZ, p, idesc, s);
   }
   if (e != cudaSuccess || p.nslices == 1) return e;
   return launch_split_reduce(g.split_ws, p.nslices, g.Z, g.keys, g.F, g.J, s, g.ldz, g.col0);

@@ -215,13 +215,14 @@ enum { TC_LONG_256 = 0,   // 128x256 tiles, 4 operand stages, 1 output box per e
        TC_LONG_128 = 2,   // 128x128 tiles, 4 stages, 2 boxes (small grids: twice the tiles)
        TC_FUSED3_256 = 3, // hi + lo precisions: 128x256 tiles, 2 stages each holding the hi and
                           // lo planes of A and B for one k-block (the three products in turn)
-       TC_NBASE = 4,      // variant v + 4: variant v in clusters of 2 CTAs that share each
-                          // B tile by TMA multicast
-       TC_NVARIANTS = 8 };
-// CTAs per cluster of a variant (1 or 2).
+       TC_NBASE = 4,      // variant v + 4: variant v in clusters of 2 CTAs (two frame tiles)
+                          // that share each B tile by TMA multicast; v + 8: clusters of
+                          // 2 x 2 that also share each A tile (dense reductions)
+       TC_NVARIANTS = 12 };
+// CTAs per cluster of a variant (1, 2 or 4).
 int tc_gemm_cluster_size(int variant);
 bool tc_gemm_variant_valid(int variant, OpType t);
-int tc_gemm_default_variant(int Kd, OpType t);
+int tc_gemm_default_variant(int Kd, OpType t, int F);
 cudaError_t launch_tc_gemm(const TcGemm& g, int num_sms, cudaStream_t s);
 int tc_gemm_slices(int F, int J, int Kd, OpType t, int num_sms);
 size_t tc_gemm_workspace_floats(int F_max, int J, int Kd, OpType t, int num_sms);

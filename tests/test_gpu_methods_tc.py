@@ -128,15 +128,41 @@ def test_uca8_full_size_tensor_cores_sampled(S):
     zo = O.srp_sspi(np.where(mask_g, R.lam("uca8"), 0.0), xi_o)
     assert R.per_frame_rel(z[fsel], zo).max() <= TOL
     check_argmax(z[fsel], am[fsel], zo)
-    # each kernel alone and in clusters of 2 CTAs that share the B tiles by multicast (16
+    # each kernel alone and in clusters of 2 (and 2 x 2: SLRI's dense reduction; SSPI's
+    # block-sparse one runs them as 2 x 1) CTAs that share operand tiles by multicast (16
     # frame tiles per cell tile): the same maps bit for bit
     for base in (0, 1, 3):
         plan.set_variant(base)
         zb, amb = _run(plan, frames)
-        plan.set_variant(base + 4)
-        zc, amc = _run(plan, frames)
+        for v in (base + 4, base + 8):
+            plan.set_variant(v)
+            zc, amc = _run(plan, frames)
+            plan.status()
+            assert np.array_equal(zc, zb) and np.array_equal(amc, amb), v
+
+
+@pytest.mark.parametrize("prec,base", [("fp16x3", 3), ("bf16", 0), ("tf32x3", 0)])
+def test_clusters_with_split_reduction_and_a_tile_past_F(S, prec, base):
+    """Conv on 330 frames (three frame tiles, the last ragged: the second cluster of a cell
+    tile runs a frame tile past F) and 4616 cells (19 cell tiles, the last ragged: a 2 x 2
+    cluster also runs a cell tile past J; 57 output tiles, so the reduction is split into
+    slices summed in FP64): the cluster variants' maps equal the unclustered kernel's bit
+    for bit, and match the oracle on sampled frames."""
+    w = R.workload("uca8", 330, 13)
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    plan = S.Plan(*args, method="conv", precision=prec, max_frames=330)
+    plan.set_variant(base)
+    zb, ab = _run(plan, w["frames"])
+    for v in (base + 4, base + 8):
+        plan.set_variant(v)
+        zc, ac = _run(plan, w["frames"])
         plan.status()
-        assert np.array_equal(zc, zb) and np.array_equal(amc, amb), base
+        assert np.array_equal(zc, zb) and np.array_equal(ac, ab), v
+    fsel = np.array([0, 129, 257, 329])
+    dt, *_ = R.geometry("uca8", 330, 13)
+    zo = O.srp_conv(R.psi_of(w["frames"][fsel]), dt, w["fs"])
+    assert R.per_frame_rel(zc[fsel], zo).max() <= dict(PRECS)[prec]
+    check_argmax(zc[fsel], ac[fsel], zo)
 
 
 @pytest.mark.parametrize("name,F,sub,rank,prec", [
@@ -171,9 +197,9 @@ def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
     """The four tcgen05 variants (128x256 4-stage, 128x256 2-stage 4-box, 128x128, and for
     the hi + lo precisions 128x256 with the hi and lo planes of one k-block per stage), each
     also in clusters of 2 CTAs sharing the B tiles by multicast, give the oracle's maps on
-    ragged tiles (70 frames: one frame tile, so the clusters also run a frame tile past F)
-    and the clustered maps equal the unclustered ones bit for bit; srp_plan_autotune times
-    them and keeps one; a BF16 plan refuses the hi + lo variants."""
+    ragged tiles (70 frames: one frame tile, which the cluster variants run unclustered) and
+    equal maps bit for bit; srp_plan_autotune times them and keeps one; a BF16 plan refuses
+    the hi + lo variants."""
     name, F, sub, w, psi, dt, lags, perm, xi_o = uca_small
     args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
     Lam = R.lam(name, F, sub)
@@ -191,7 +217,7 @@ def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
     if method == "sspi":  # Lambda masked by the plan's own (valid) selection
         zo = O.srp_sspi(np.where(_check_taps(plan, mask, perm, Lam), Lam, 0.0), xi_o)
     base = {}
-    for v in list(range(8)) + [-1]:
+    for v in list(range(12)) + [-1]:
         plan.set_variant(v)
         z, am = _run(plan, w["frames"])
         plan.status()
@@ -199,17 +225,17 @@ def test_every_tensor_core_variant_and_the_autotuner(S, uca_small, method, kw):
         check_argmax(z, am, zo)
         if 0 <= v < 4:
             base[v] = (z, am)
-        elif v >= 4:  # the same kernel with shared B tiles: the same maps bit for bit
+        elif v >= 4:  # the same kernel with shared operand tiles: the same maps bit for bit
             assert np.array_equal(z, base[v % 4][0]) and np.array_equal(am, base[v % 4][1]), v
     rep = plan.autotune(F=64)
-    assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 8
+    assert rep["variant"] in rep["ms"] and len(rep["ms"]) == 12
     z, am = _run(plan, w["frames"])
     assert R.per_frame_rel(z, zo).max() <= TOL
     single = S.Plan(*args, method=method, precision="bf16", max_frames=64, **kw)
-    for v in (3, 7):
+    for v in (3, 7, 11):
         with pytest.raises(S.SrpError):
             single.set_variant(v)
-    assert len(single.autotune(F=64)["ms"]) == 6
+    assert len(single.autotune(F=64)["ms"]) == 9
 
 
 @pytest.mark.parametrize("method,kw,prec,tol", [

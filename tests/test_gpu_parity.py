@@ -378,10 +378,11 @@ def test_uca8_full_size_sampled(S, uca_full):
     plan.set_variant(3)
     z3, am3 = _run(plan, frames)
     assert R.per_frame_rel(z3[fsel], zo).max() <= TOL
-    plan.set_variant(7)
-    zc, amc = _run(plan, frames)
-    plan.status()
-    assert np.array_equal(zc, z3) and np.array_equal(amc, am3)
+    for v in (7, 11):  # clusters of 2 and of 2 x 2
+        plan.set_variant(v)
+        zc, amc = _run(plan, frames)
+        plan.status()
+        assert np.array_equal(zc, z3) and np.array_equal(amc, am3), v
     del z3, zc
     # SLRI, R = 16
     tall, fat, s = R.slri("uca8", 16)
