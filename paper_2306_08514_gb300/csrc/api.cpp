@@ -241,7 +241,8 @@ cudaError_t contract(srp_plan_s* p, const void* A, const void* A_lo, const void*
 // Samples of the TD GCCs (Eq. xi_p_ifft / xi_computed) into out [F][cols] in operand type t
 // (zero padded beyond L): for short lag windows by the per-frame sampling GEMM on the
 // warp-level tensor cores, otherwise (or where its staged spectra would not fit in shared
-// memory) by the two-pairs-per-iFFT kernel; both write the operand directly.
+// memory) by the two-pairs-per-iFFT kernel -- for 2K = 1024 and 8-11-bit operands its
+// 32 x 32 form on the warp-level tensor cores; all write the operand directly.
 cudaError_t sample_to(srp_plan_s* p, const float2* yhat, int F, void* out, void* out_lo, int cols,
                       OpType t, cudaStream_t s) {
   const Geometry& g = p->g;
@@ -249,6 +250,9 @@ cudaError_t sample_to(srp_plan_s* p, const float2* yhat, int F, void* out, void*
   if (p->use_mma_sampling)
     return launch_gcc_mma(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L, p->d_stab,
                           p->max_Np, t, out, out_lo, cols, s);
+  if (p->use_dft_sampling && gcc_dft_supported(g.M, g.N, t))
+    return launch_gcc_dft(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L, p->d_stab,
+                          t, out, out_lo, cols, s);
   return launch_gcc_samples(yhat, F, g.M, g.P, g.N, p->d_pairs, p->d_Np, p->d_off, g.L,
                             p->d_twiddle, t, out, out_lo, cols, s);
 }
@@ -465,6 +469,8 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
                       front_conv_supported(g.M, g.N);
   p->use_mma_sampling = desc->method != SRP_CONV && desc->method != SRP_LR && !p->use_front &&
                         gcc_mma_supported(g.M, g.N, p->max_Np);
+  p->use_dft_sampling = desc->method != SRP_CONV && desc->method != SRP_LR && !p->use_front &&
+                        !p->use_mma_sampling && gcc_dft_supported(g.M, g.N, p->op);
   if (desc->method == SRP_SI || desc->method == SRP_TD ||
       (desc->method == SRP_SSPI && p->op != OpType::F32)) {
     const double bbytes = static_cast<double>(g.J) * p->Lpad * op_bytes(p->op) *
@@ -524,8 +530,11 @@ static srp_status create_plan(const srp_plan_desc* desc, void* stream, srp_plan_
   SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_twiddle, tw.data(), sizeof(float2) * g.N / 2, cudaMemcpyHostToDevice, s));
   SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_window, win.data(), sizeof(float) * g.N, cudaMemcpyHostToDevice, s));
   std::vector<uint4> stab;
-  if (p->use_front || p->use_mma_sampling) {
-    front_sampling_table(g.N, p->max_Np, stab);
+  if (p->use_front || p->use_mma_sampling || p->use_dft_sampling) {
+    if (p->use_dft_sampling)
+      dft_tables(stab);
+    else
+      front_sampling_table(g.N, p->max_Np, stab);
     SRP_ALLOC(p, p->d_stab, sizeof(uint4) * stab.size());
     SRP_PLAN_CUDA(p, cudaMemcpyAsync(p->d_stab, stab.data(), sizeof(uint4) * stab.size(),
                                      cudaMemcpyHostToDevice, s));

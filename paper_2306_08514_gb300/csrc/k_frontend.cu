@@ -585,6 +585,258 @@ cudaError_t launch_gcc_mma(const float2* yhat, int F, int M, int P, int N, const
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------
+// Sampling by iFFT for 2K = 1024 on the warp-level tensor cores, for operands that keep 8
+// to 11 bits (BF16, FP16, TF32 plans).  Each warp takes one complex transform of length
+// 1024 (two pairs, as gcc_samples_kernel: psi-bar_a + i psi-bar_b, two-sided and Hermitian,
+// so the inverse transform is xi-bar_a + i xi-bar_b) and splits it as 32 x 32
+// (Cooley-Tukey: input index 32 n1 + n2, output index k1 + 32 k2):
+//   Y[k1][n2] = sum_n1 e^{+2 pi i k1 n1 / 32} x[32 n1 + n2]        (real-form GEMM 64x64x32)
+//   Y[k1][n2] *= e^{+2 pi i k1 n2 / 1024}                           (twiddles)
+//   x-bar[k1 + 32 k2] = sum_n2 Y[k1][n2] e^{+2 pi i n2 k2 / 32}    (real-form GEMM 32x64x64)
+// on mma.sync m16n8k16 with FP16 operands and FP32 accumulation; the first product's
+// accumulators become the second's A fragments in registers.  One CTA of 256 threads per
+// frame stages the frame's spectra (rows padded 4 entries per 64 bins: the fragments'
+// gathers hit distinct banks) and the DFT tables (dft_tables) in shared memory.  Samples
+// are written in the operand type, zero padded beyond L.
+// ---------------------------------------------------------------------------------
+constexpr int kDftRow = 512 + 32;  // padded spectrum row (float2)
+constexpr int kTwRow = 36;         // twiddle row (float2): the 8 rows of a gather hit distinct banks
+constexpr int kDftTables = 512 + 512 + 32 * kTwRow / 2;  // uint4: A of step 1, B of step 2, twiddles
+__device__ __forceinline__ int dft_bin(int k) { return k + 4 * (k >> 6); }
+
+// f16 pair (x in the lower half)
+__device__ __forceinline__ unsigned pack_h2(float x, float y) {
+  const __half2 h = __floats2half2_rn(x, y);
+  return *reinterpret_cast<const unsigned*>(&h);
+}
+
+template <typename T>
+__global__ __launch_bounds__(256, 2) void gcc_dft1024_kernel(
+    const float2* __restrict__ yhat, int M, int P, const int2* __restrict__ pairs,
+    const int* __restrict__ Np, const int* __restrict__ off, int L,
+    const uint4* __restrict__ tables, void* out, int out_cols) {
+  constexpr int K = 512, NFFT = 1024;
+  extern __shared__ float2 dsm[];
+  float2* ys = dsm;                                          // [M][kDftRow]
+  uint4* ta = reinterpret_cast<uint4*>(ys + M * kDftRow);     // A of step 1: [4 i][4 s][32] uint4
+  uint2* tb = reinterpret_cast<uint2*>(ta + 512);             // B of step 2: [4 q][8 j][32] uint2
+  float2* tw = reinterpret_cast<float2*>(tb + 1024);          // [32 k1][kTwRow: 32 n2 + pad]
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  {
+    const float4* src = reinterpret_cast<const float4*>(yhat + static_cast<size_t>(f) * M * K);
+    for (int e = tid; e < M * (K / 2); e += 256) {  // two bins per float4
+      const int m = e / (K / 2), j = e - m * (K / 2);
+      *reinterpret_cast<float4*>(ys + m * kDftRow + dft_bin(2 * j)) = __ldg(src + e);
+    }
+    for (int e = tid; e < kDftTables; e += 256) ta[e] = __ldg(tables + e);
+  }
+  __syncthreads();
+  const size_t orow = static_cast<size_t>(f) * out_cols;
+  const int ntr = (P + 1) >> 1;
+  for (int tr = warp; tr < ntr; tr += 8) {
+    const int pa = 2 * tr, pb = pa + 1;
+    const bool hasb = pb < P;
+    const int2 qa = __ldg(pairs + pa);
+    const int2 qb = hasb ? __ldg(pairs + pb) : qa;
+    const int ya0 = qa.x * kDftRow, ya1 = qa.y * kDftRow;  // spectrum rows in ys
+    const int yb0 = qb.x * kDftRow, yb1 = qb.y * kDftRow;
+    // B fragments of step 1: rows 0..31 Re x[32 n1 + n2], rows 32..63 Im (n1 = row mod 32),
+    // columns n2; this thread holds n1 = 16 s + 2 t + {0, 1, 8, 9}, n2 = 8 j + g
+    unsigned b1[4][4][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float re[4], im[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int n1 = 16 * s + 2 * t + (e & 1) + 8 * (e >> 1);
+          const int k = 32 * n1 + 8 * j + g;  // bin of the two-sided spectrum
+          const int kk = k <= K ? k : NFFT - k;
+          float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+          if (kk != 0 && kk != K) {
+            const int o = dft_bin(kk);
+            a = cmul_conj(ys[ya0 + o], ys[ya1 + o]);
+            if (hasb) b = cmul_conj(ys[yb0 + o], ys[yb1 + o]);
+          }
+          // psi_a + i psi_b below the Nyquist bin, psi_a^* + i psi_b^* above it
+          re[e] = k <= K ? a.x - b.y : a.x + b.y;
+          im[e] = k <= K ? a.y + b.x : b.x - a.y;
+        }
+        b1[s][j][0] = pack_h2(re[0], re[1]);
+        b1[s][j][1] = pack_h2(re[2], re[3]);
+        b1[s + 2][j][0] = pack_h2(im[0], im[1]);
+        b1[s + 2][j][1] = pack_h2(im[2], im[3]);
+      }
+    // step 1: C1 [64 rows: Re Y (k1), Im Y (k1)][32 cols: n2], for k1 = 16 r .. 16 r + 15 at
+    // a time (m-tiles r and r + 2: the real and imaginary parts of the same rows); then the
+    // twiddles and the A fragments of step 2: rows k1, columns [Re Y (n2) | Im Y (n2)]
+    unsigned a2[2][4][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      float c1[2][4][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) c1[u][j][e] = 0.f;
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const uint4 av = ta[((r + 2 * u) * 4 + s) * 32 + lane];
+          const unsigned a[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) mma_16816(c1[u][j], a, b1[s][j][0], b1[s][j][1]);
+        }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float yr[4], yi[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k1 = 16 * r + g + 8 * (e >> 1), n2 = 8 * j + 2 * t + (e & 1);
+          const float2 w = tw[k1 * kTwRow + n2];
+          const float xr = c1[0][j][e], xi = c1[1][j][e];
+          yr[e] = xr * w.x - xi * w.y;
+          yi[e] = xr * w.y + xi * w.x;
+        }
+        // n-tile j (columns 8 j ..) is half of k-step j / 2 (Re) or 2 + j / 2 (Im)
+        const int q = j >> 1, h = (j & 1) * 2;
+        a2[r][q][h] = pack_h2(yr[0], yr[1]);
+        a2[r][q][h + 1] = pack_h2(yr[2], yr[3]);
+        a2[r][q + 2][h] = pack_h2(yi[0], yi[1]);
+        a2[r][q + 2][h + 1] = pack_h2(yi[2], yi[3]);
+      }
+    }
+    // step 2: C2 [32 rows k1][64 cols: Re Z (k2), Im Z (k2)]; x-bar[k1 + 32 k2] = Z[k1][k2]
+    const int na = __ldg(Np + pa), nb = hasb ? __ldg(Np + pb) : -1;
+    const size_t oa = orow + __ldg(off + pa) + na;          // lag 0 of pair a
+    const size_t ob = hasb ? orow + __ldg(off + pb) + nb : 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      // n-tile j holds output indices 256 (j mod 4) .. + 255 of pair a (j < 4) or b: lags
+      // 0..255, 256..511, -512..-257, -256..-1; windows narrower than 256 skip the middle two
+      const int nq = j < 4 ? na : nb, jj = j & 3;
+      if (nq < 0 || (jj == 1 && nq < 256) || (jj == 2 && nq < 257)) continue;  // warp-uniform
+      float c2[2][4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c2[r][e] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint2 bv = tb[(q * 8 + j) * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          // A fragment order: (row g, k 2t..), (row g+8, k 2t..), (row g, k 2t+8..), (row g+8, k 2t+8..)
+          const unsigned a[4] = {a2[r][q][0], a2[r][q][1], a2[r][q][2], a2[r][q][3]};
+          mma_16816(c2[r], a, bv.x, bv.y);
+        }
+      }
+      // columns 8 j + 2 t (+1): Re Z for j < 4 (pair a), Im Z for j >= 4 (pair b)
+      const size_t o = j < 4 ? oa : ob;
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k1 = 16 * r + g + 8 * (e >> 1);
+          const int k2 = 8 * (j & 3) + 2 * t + (e & 1);
+          const int idx = k1 + 32 * k2;
+          const int n = idx < K ? idx : idx - NFFT;  // lag (Eq. n_prime)
+          if (n >= -nq && n <= nq) op_store<T, false>(out, nullptr, o + n, c2[r][e]);
+        }
+    }
+  }
+  for (int c = L + tid; c < out_cols; c += 256) op_store<T, false>(out, nullptr, orow + c, 0.f);
+}
+
+size_t gcc_dft_smem_bytes(int M) {
+  return sizeof(float2) * static_cast<size_t>(M) * kDftRow + sizeof(uint4) * kDftTables;
+}
+
+bool gcc_dft_supported(int M, int N, OpType t) {
+  const bool narrow = t == OpType::BF16 || t == OpType::F16 || t == OpType::TF32;
+  return narrow && N == 1024 && gcc_dft_smem_bytes(M) <= 110 * 1024;
+}
+
+// Host tables of gcc_dft1024_kernel: A of step 1 (the real form [[C, -S], [S, C]] of
+// e^{+2 pi i k1 n1 / 32}) in m16n8k16 A-fragment order [4][4][32] uint4, B of step 2 ([[C, S],
+// [-S, C]] of e^{+2 pi i n2 k2 / 32}) in B-fragment order [4][8][32] uint2, and the twiddles
+// e^{+2 pi i k1 n2 / 1024} [32][kTwRow] float2: kDftTables uint4 in all.
+void dft_tables(std::vector<uint4>& tab) {
+  tab.assign(kDftTables, make_uint4(0, 0, 0, 0));
+  auto h = [](double v) {
+    const __half_raw r(__float2half_rn(static_cast<float>(v)));
+    return static_cast<unsigned>(r.x);
+  };
+  auto pk = [&](double lo, double hi) { return h(lo) | (h(hi) << 16); };
+  auto cs = [](int a, int b, int n, double& c, double& sn) {
+    const long long u = (static_cast<long long>(a) * b) % n;  // exact angle reduction
+    const double th = 2.0 * M_PI * static_cast<double>(u) / n;
+    c = std::cos(th);
+    sn = std::sin(th);
+  };
+  auto A1 = [&](int row, int col) {  // rows: Re out (k1), Im out; cols: Re in (n1), Im in
+    double c, sn;
+    cs(row & 31, col & 31, 32, c, sn);
+    const int rb = row >> 5, cb = col >> 5;
+    return rb == cb ? c : (rb == 0 ? -sn : sn);
+  };
+  auto B2 = [&](int row, int col) {  // rows: Re Y (n2), Im Y; cols: Re Z (k2), Im Z
+    double c, sn;
+    cs(row & 31, col & 31, 32, c, sn);
+    const int rb = row >> 5, cb = col >> 5;
+    return rb == cb ? c : (rb == 0 ? sn : -sn);
+  };
+  for (int i = 0; i < 4; ++i)
+    for (int s = 0; s < 4; ++s)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, t = lane & 3, r0 = 16 * i + g, c0 = 16 * s + 2 * t;
+        uint4& e = tab[(i * 4 + s) * 32 + lane];
+        e.x = pk(A1(r0, c0), A1(r0, c0 + 1));
+        e.y = pk(A1(r0 + 8, c0), A1(r0 + 8, c0 + 1));
+        e.z = pk(A1(r0, c0 + 8), A1(r0, c0 + 9));
+        e.w = pk(A1(r0 + 8, c0 + 8), A1(r0 + 8, c0 + 9));
+      }
+  uint2* tb = reinterpret_cast<uint2*>(tab.data() + 512);
+  for (int q = 0; q < 4; ++q)
+    for (int j = 0; j < 8; ++j)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, t = lane & 3, k0 = 16 * q + 2 * t, n = 8 * j + g;
+        uint2& e = tb[(q * 8 + j) * 32 + lane];
+        e.x = pk(B2(k0, n), B2(k0 + 1, n));
+        e.y = pk(B2(k0 + 8, n), B2(k0 + 9, n));
+      }
+  float2* tw = reinterpret_cast<float2*>(tab.data() + 1024);
+  for (int k1 = 0; k1 < 32; ++k1)
+    for (int n2 = 0; n2 < 32; ++n2) {
+      double c, sn;
+      cs(k1, n2, 1024, c, sn);
+      tw[k1 * kTwRow + n2] = make_float2(static_cast<float>(c), static_cast<float>(sn));
+    }
+}
+
+cudaError_t launch_gcc_dft(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                           const int* Np, const int* off, int L, const uint4* tables, OpType t,
+                           void* out, void* out_lo, int out_cols, cudaStream_t s) {
+  if (F <= 0) return cudaSuccess;
+  if (!gcc_dft_supported(M, N, t) || out_cols < L) return cudaErrorInvalidValue;
+  (void)out_lo;  // single-plane operand types only
+  const size_t smem = gcc_dft_smem_bytes(M);
+  void (*kern)(const float2*, int, int, const int2*, const int*, const int*, int, const uint4*,
+               void*, int) = t == OpType::BF16 ? gcc_dft1024_kernel<__nv_bfloat16>
+                            : t == OpType::F16 ? gcc_dft1024_kernel<__half>
+                                               : gcc_dft1024_kernel<tf32_t>;
+  cudaError_t e = allow_max_dynamic_smem(kern);
+  if (e != cudaSuccess) return e;
+  kern<<<F, 256, smem, s>>>(yhat, M, P, pairs, Np, off, L, tables, out, out_cols);
+  return cudaGetLastError();
+}
+
 // One CTA of 256 threads per frame; H = N/2 is the complex FFT length (= K), NTM bounds
 // the n-tiles of the sampling GEMM.
 template <int H, int NTM>

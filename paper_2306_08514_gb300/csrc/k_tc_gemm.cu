@@ -217,17 +217,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int total = tile_groups<CS>(p);
   const int crank = CS > 1 ? static_cast<int>(cluster_ctarank()) : 0;
   const int rm = crank % CM, rn = crank / CM;
-  // the CTAs sharing this CTA's B tile (same rn) and A tile (same rm)
-  const uint16_t mask_b = static_cast<uint16_t>(((1u << CM) - 1u) << (rn * CM));
-  uint16_t mask_a = 0;
-#pragma unroll
-  for (int j = 0; j < CN; ++j) mask_a |= static_cast<uint16_t>(1u << (rm + CM * j));
   const int tile0 = CS > 1 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
   const int tstep = CS > 1 ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
+      // the CTAs sharing this CTA's B tile (same rn) and A tile (same rm)
+      const uint16_t mask_b = static_cast<uint16_t>(((1u << CM) - 1u) << (rn * CM));
+      uint16_t mask_a = 0;
+#pragma unroll
+      for (int j = 0; j < CN; ++j) mask_a |= static_cast<uint16_t>(1u << (rm + CM * j));
       prefetch_tmap(&tmA0);
       prefetch_tmap(&tmB0);
       if (p.nseg > 1) {

@@ -122,6 +122,13 @@ int gcc_direct_max_lag();
 // tensor cores from y-hat [F][M][N/2] in global memory, written in operand type t into
 // out [F][out_cols] (zero padded beyond L); stab = front_sampling_table(N, max_Np).
 bool gcc_mma_supported(int M, int N, int max_Np);
+// The iFFT sampling for 2K = 1024 and operands of 8 to 11 bits (BF16, FP16, TF32) as 32 x 32
+// DFTs on the warp-level tensor cores; tables = dft_tables.
+bool gcc_dft_supported(int M, int N, OpType t);
+void dft_tables(std::vector<uint4>& tab);
+cudaError_t launch_gcc_dft(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
+                           const int* Np, const int* off, int L, const uint4* tables, OpType t,
+                           void* out, void* out_lo, int out_cols, cudaStream_t s);
 cudaError_t launch_gcc_mma(const float2* yhat, int F, int M, int P, int N, const int2* pairs,
                            const int* Np, const int* off, int L, const uint4* stab, int max_Np,
                            OpType t, void* out, void* out_lo, int out_cols, cudaStream_t s);
@@ -352,6 +359,7 @@ struct srp_plan_s {
   int tc_variant = -1;     // tensor-core kernel variant chosen by srp_plan_autotune (-1: heuristic)
   bool use_front = false;  // interpolation methods: one fused front-end launch per chunk
   bool use_mma_sampling = false;  // otherwise, short lag windows: sampling by gcc_mma
+  bool use_dft_sampling = false;  // otherwise, 2K = 1024, 8-11-bit operands: gcc_dft1024
   bool fat_gemm = false;   // SLRI with long sample vectors: u = Lambda_fat xi as a GEMM
   bool h_generated = false;  // conv FP32: SRP matrix generated inside the GEMM, not stored
   int h_slices = 0;          //   slices of each chunk's reduction (d_split holds the partials)
@@ -399,7 +407,8 @@ struct srp_plan_s {
   int* d_err = nullptr;  // non-zero after a bounded wait inside a kernel ran out
   bool use_front_conv = false;  // conv / LR operand from the fused front kernel
   bool stall_next = false;  // srp_debug_stall_next_contraction
-  uint4* d_stab = nullptr;  // fused front end or gcc_mma: the sampling operand (front_sampling_table)
+  uint4* d_stab = nullptr;  // fused front end or gcc_mma: the sampling operand (front_sampling_table);
+                            // gcc_dft1024: its DFT tables (dft_tables)
   uint4* d_ftab = nullptr;  // fused front end, SLRI: Lambda_fat (front_fat_table)
   // staging for srp_map_host, and its copy pipeline (two D2H streams and one H2D stream;
   // events recycled round-robin to order them against the compute stream)

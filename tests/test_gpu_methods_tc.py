@@ -168,13 +168,16 @@ def test_clusters_with_split_reduction_and_a_tile_past_F(S, prec, base):
 @pytest.mark.parametrize("name,F,sub,rank,prec", [
     ("nested32", 6, 400, 8, "fp32"), ("nested32", 6, 400, 32, "fp16x3"),
     ("nested32", 6, 400, 16, "bf16"), ("nested32", 6, 400, 16, "fp16"), ("nested32", 6, 400, 16, "tf32"),
-    ("walls16", 4, 300, 8, "fp32"), ("walls16", 4, 300, 16, "bf16"),
+    ("walls16", 4, 300, 8, "fp32"), ("walls16", 4, 300, 16, "bf16"), ("walls16", 4, 300, 16, "fp16"),
+    ("walls16", 4, 300, 16, "tf32"),
 ])
 def test_slri_long_sample_vectors(S, name, F, sub, rank, prec):
     """L = 7408 (nested32) and 43326 (walls16): the low-rank fit runs as a device subspace
     iteration; its singular values and maps match the oracle's SVD.  The nested32 frames
     (N = 2048) are sampled from spectra in global memory: with the three products of the
-    hi + lo split for FP32 and FP16 hi+lo, with one FP16 product for BF16, FP16 and TF32."""
+    hi + lo split for FP32 and FP16 hi+lo, with one FP16 product for BF16, FP16 and TF32; the
+    walls16 frames (N = 1024, lag windows up to 355) by iFFT: radix-8 in FP32, as 32 x 32
+    DFTs on the warp-level tensor cores for BF16, FP16 and TF32."""
     w = R.workload(name, F, sub)
     dt, Np, lags, perm = R.geometry(name, F, sub)
     xi_o, _ = O.gcc_samples_ifft(R.psi_of(w["frames"]), lags, w["N"] // 2)
