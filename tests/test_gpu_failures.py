@@ -122,6 +122,35 @@ def test_bounded_waits_run_out_and_the_plan_stays_usable(S, method, kw, variant)
     assert np.array_equal(z1, z0) and np.array_equal(a1, a0)
 
 
+@pytest.mark.parametrize("method,kw,variant", [("conv", {}, 4), ("conv", {}, 8), ("sspi", dict(taps=2.0), 8)])
+def test_bounded_waits_run_out_in_clusters(S, method, kw, variant):
+    """The stall hook on launches that do run in clusters (300 frames: three frame tiles;
+    4616 cells: 19 cell tiles): 2 x 1 and 2 x 2 for conv's dense reduction, SSPI's
+    block-sparse one as 2 x 1.  Every CTA of every cluster times out on its own barriers,
+    the cluster's closing barrier completes, the call reports SRP_ETIMEOUT within the bound
+    and the next call gives the maps of before."""
+    import torch
+    w = R.workload("uca8", 300, 13)
+    args = (w["mic_xyz"], w["grid_xyz"], w["fs"], w["N"])
+    fr = torch.from_numpy(np.ascontiguousarray(w["frames"])).cuda()
+    plan = S.Plan(*args, method=method, precision="bf16", max_frames=300, **kw)
+    plan.set_variant(variant)
+    z0, a0 = _maps(plan, fr)
+    plan.status()
+    plan.debug_stall_next_contraction()
+    t0 = time.time()
+    _maps(plan, fr)
+    elapsed = time.time() - t0
+    with pytest.raises(S.SrpError) as e:
+        plan.status()
+    assert e.value.status == S.SRP_ETIMEOUT
+    assert elapsed < 10.0
+    plan.status()
+    z1, a1 = _maps(plan, fr)
+    plan.status()
+    assert np.array_equal(z1, z0) and np.array_equal(a1, a0)
+
+
 def test_stall_hook_needs_a_tensor_core_plan(S):
     w, args = _square4(S)
     plan = S.Plan(*args, method="slri", rank=8, precision="fp32", max_frames=8)
