@@ -68,7 +68,7 @@ def parse(argv=None):
                     help="nvidia-smi sampling interval during the timed region (0: no sampling)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic kernel variants")
     ap.add_argument("--variant", type=int, default=None,
-                    help="pin the tensor-core kernel variant of every plan (0..3, as srp_plan_autotune)")
+                    help="pin the tensor-core kernel variant of every plan (0..11, as srp_plan_autotune)")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
     ap.add_argument("--no-other-workloads", action="store_true",
