@@ -132,6 +132,44 @@ def test_measured_traffic_goes_stale_with_the_kernel_source(tmp_path, monkeypatc
     assert bench.measured_traffic("uca8", 2000, "conv", "bf16") is None
 
 
+def test_committed_traffic_capture_matches_the_current_kernels():
+    """The committed DRAM capture of the benchmark step applies to the kernels as they are
+    (bench.py reports it as roofline.traffic only while their sources' sha256 match)."""
+    t = bench.measured_traffic("uca8", 2000, "conv", "fp16x3")
+    assert t is not None and 4.03e9 < t < 8.0e9
+
+
+def test_clock_sampler_off_and_samples_from_the_mark(tmp_path):
+    """--clock-ms 0 starts no sampler (stop() gives None); with samples, stop() keeps those
+    written after mark(), the start of the timed region."""
+    ck = bench.Clocks(0, interval_ms=0)
+    ck.start()
+    ck.mark()
+    assert ck.stop() is None
+    ck = bench.Clocks(0, interval_ms=20)
+    ck.proc = None
+    ck.n0 = 0
+    line = "0, {sm}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {pc}\n"
+    with open(ck.path, "w") as f:
+        f.write(line.format(sm=300, pc="Not Active"))
+    ck.n0 = ck._lines()  # the mark: one sample before the timed region
+    with open(ck.path, "a") as f:
+        f.write(line.format(sm=2070, pc="Active"))
+        f.write(line.format(sm=2070, pc="Not Active"))
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    ck.proc = Done()
+    ck.f = open(ck.path, "a")
+    r = ck.stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+
+
 def test_serving_mix_is_seeded_and_within_the_workload_ranges():
     """64 sessions, M in {4, 8, 16, 32}, N in {512, 1024}, hop 256, SLRI (R 16 / 32) or
     SSPI (t 2 / 4), grids inside the session's room; the same seed gives the same mix."""
